@@ -1,0 +1,500 @@
+"""Pins for the FP64 oracle: facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed-form
+values, Peskin's kernel conditions, exact derivatives by central finite
+differences, invariances of hyperelastic energies, conservation of total force
+and torque under spreading, exactness of interpolation on constant and linear
+fields, the discrete adjointness of spreading and interpolation (Section 4.4),
+and brute-force sums over every grid face.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22695_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rot(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a*a+b*b-c*c-d*d, 2*(b*c-a*d), 2*(b*d+a*c)],
+                     [2*(b*c+a*d), a*a-b*b+c*c-d*d, 2*(c*d-a*b)],
+                     [2*(b*d-a*c), 2*(c*d+a*b), a*a-b*b-c*c+d*d]])
+
+
+# ---------------------------------------------------------------------------
+# 4-point kernel
+# ---------------------------------------------------------------------------
+
+def test_phi_closed_form_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "peskin4_closed_form.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 10
+    for r, expr in rows:
+        want = eval(expr, {"sqrt": math.sqrt})
+        assert oracle.phi(float(r)) == pytest.approx(want, abs=1e-15), (r, expr)
+
+
+def test_phi_peskin_conditions():
+    # Peskin's conditions for the 4-point kernel: partition of unity, equal
+    # even/odd sums, vanishing first moment, sum of squares 3/8.
+    rng = np.random.default_rng(0)
+    for r in rng.uniform(-3, 3, size=200):
+        js = np.arange(-6, 7)
+        w = np.array([oracle.phi(r - j) for j in js])
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+        assert w[js % 2 == 0].sum() == pytest.approx(0.5, abs=1e-14)
+        assert ((r - js) * w).sum() == pytest.approx(0.0, abs=1e-14)
+        assert (w * w).sum() == pytest.approx(3.0 / 8.0, abs=1e-14)
+        assert (w >= 0).all() and np.count_nonzero(w) <= 4
+
+
+def test_dphi_is_derivative_and_c1():
+    rng = np.random.default_rng(1)
+    eps = 1e-6
+    for r in np.concatenate([rng.uniform(-2.2, 2.2, size=100), [0.3, -1.7]]):
+        if min(abs(abs(r) - 1), abs(abs(r) - 2), abs(r)) < 1e-4:
+            continue
+        fd = (oracle.phi(r + eps) - oracle.phi(r - eps)) / (2 * eps)
+        assert oracle.dphi(r) == pytest.approx(fd, abs=1e-8)
+    # C1 at |r| = 1 and |r| = 2; derivative sums to zero over the stencil
+    for k in (1.0, 2.0):
+        assert oracle.dphi(k - 1e-12) == pytest.approx(oracle.dphi(k + 1e-12), abs=1e-9)
+    for r in rng.uniform(-3, 3, size=50):
+        assert sum(oracle.dphi(r - j) for j in range(-6, 7)) == pytest.approx(0, abs=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# constitutive laws
+# ---------------------------------------------------------------------------
+
+MODELS = [
+    (I.NEO_HOOKEAN, (0.5, 100.0)),
+    (I.FIBRE1, I.FIBRE1_LEAFLET),
+    (I.HO, I.HO_DEFAULT),
+]
+
+
+def _rand_F(rng, amp=0.15):
+    F = np.eye(3) + rng.uniform(-amp, amp, size=(3, 3))
+    assert np.linalg.det(F) > 0
+    return F
+
+
+def _fibres(rng):
+    ef = rng.normal(size=3)
+    ef /= np.linalg.norm(ef)
+    es = rng.normal(size=3)
+    es -= es @ ef * ef
+    es /= np.linalg.norm(es)
+    return ef, es
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_stress_is_energy_derivative(model, params):
+    # P = dPsi/dF (Section 2: P = dW/dF) by central differences, away from the
+    # tension-only kink I4 = 1.
+    rng = np.random.default_rng(10 + model)
+    checked = 0
+    for _ in range(40):
+        F = _rand_F(rng)
+        ef, es = _fibres(rng)
+        I4 = [np.sum((F @ e) ** 2) for e in (ef, es)]
+        if min(abs(v - 1) for v in I4) < 1e-3:
+            continue
+        P, _ = oracle.stress(model, params, F, ef, es)
+        eps = 1e-6
+        fd = np.zeros((3, 3))
+        for i in range(3):
+            for j in range(3):
+                dF = np.zeros((3, 3))
+                dF[i, j] = eps
+                fd[i, j] = (oracle.stress(model, params, F + dF, ef, es)[1] -
+                            oracle.stress(model, params, F - dF, ef, es)[1]) / (2 * eps)
+        np.testing.assert_allclose(P, fd, rtol=1e-7, atol=1e-7 * np.abs(P).max())
+        checked += 1
+    assert checked > 20
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_stress_reference_state_and_frame_invariance(model, params):
+    rng = np.random.default_rng(20 + model)
+    ef, es = _fibres(rng)
+    P0, psi0 = oracle.stress(model, params, np.eye(3), ef, es)
+    assert np.abs(P0).max() < 1e-13 and abs(psi0) < 1e-13
+    for _ in range(10):
+        F = _rand_F(rng)
+        Q = rot(rng)
+        P, psi = oracle.stress(model, params, F, ef, es)
+        PQ, psiQ = oracle.stress(model, params, Q @ F, ef, es)
+        assert psiQ == pytest.approx(psi, rel=1e-12, abs=1e-14)
+        np.testing.assert_allclose(PQ, Q @ P, rtol=1e-10, atol=1e-12 * np.abs(P).max())
+
+
+def test_neo_hookean_small_strain_lame():
+    # a = mu/2: linearisation gives P = 2 mu eps + (kappa - 2 mu/3) tr(eps) I.
+    mu, kappa = 1.0, 100.0
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(3, 3))
+    d = 1e-6
+    P, _ = oracle.stress(I.NEO_HOOKEAN, (mu / 2, kappa), np.eye(3) + d * A)
+    eps = 0.5 * (A + A.T)
+    lin = 2 * mu * eps + (kappa - 2 * mu / 3) * np.trace(eps) * np.eye(3)
+    np.testing.assert_allclose(P / d, lin, rtol=1e-4, atol=1e-4)
+
+
+def test_ho_isotropic_limit_is_neo_hookean():
+    # a/(2b)(exp[b(I1bar-3)]-1) -> a/2 (I1bar-3) as b -> 0, so HO with no fibre
+    # stiffness reduces to neo-Hookean with a_NH = a/2.
+    rng = np.random.default_rng(4)
+    F = _rand_F(rng)
+    ef, es = _fibres(rng)
+    a, kappa = 0.7, 50.0
+    P_ho, psi_ho = oracle.stress(I.HO, (a, 1e-9, 0, 1, 0, 1, 0, 1, kappa), F, ef, es)
+    P_nh, psi_nh = oracle.stress(I.NEO_HOOKEAN, (a / 2, kappa), F)
+    np.testing.assert_allclose(P_ho, P_nh, rtol=1e-7, atol=1e-9)
+    assert psi_ho == pytest.approx(psi_nh, rel=1e-7)
+
+
+def test_fibres_carry_tension_only():
+    # I4* = max(I4, 1): a compressed fibre adds nothing (Psi_2 and Psi_4).
+    F = np.diag([0.9, 1.05, 1.0 / (0.9 * 1.05)])
+    ef, es = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    P1, _ = oracle.stress(I.FIBRE1, (1.0, 5.0, 2.0, 10.0), F, ef, es)
+    P0, _ = oracle.stress(I.FIBRE1, (1.0, 0.0, 2.0, 10.0), F, ef, es)
+    np.testing.assert_allclose(P1, P0, atol=1e-14)
+    P1, _ = oracle.stress(I.FIBRE1, (1.0, 5.0, 2.0, 10.0), F, es, ef)   # fibre along y, stretched
+    assert np.abs(P1 - P0).max() > 1e-3
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_stress_direction_derivative(model, params):
+    rng = np.random.default_rng(30 + model)
+    for _ in range(10):
+        F = _rand_F(rng)
+        ef, es = _fibres(rng)
+        dF = rng.normal(size=(3, 3))
+        eps = 1e-6
+        I4 = [np.sum((F @ e) ** 2) for e in (ef, es)]
+        if min(abs(v - 1) for v in I4) < 1e-3:
+            continue
+        fd = (oracle.stress(model, params, F + eps * dF, ef, es)[0] -
+              oracle.stress(model, params, F - eps * dF, ef, es)[0]) / (2 * eps)
+        dP = oracle.stress_dir(model, params, F, dF, ef, es)
+        np.testing.assert_allclose(dP, fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+# ---------------------------------------------------------------------------
+# FE force, mass
+# ---------------------------------------------------------------------------
+
+def tiny_mesh(model=I.HO, params=I.HO_DEFAULT, n=16, blocks=(2, 2, 1), seed=7, noise=0.15):
+    p = I.block_problem(seed=seed, n=n, blocks=blocks, noise=noise, fp64=True)
+    rng = np.random.default_rng(seed)
+    fib = np.zeros((6, p.n_elems))
+    for e in range(p.n_elems):
+        ef, es = _fibres(rng)
+        fib[:3, e], fib[3:, e] = ef, es
+    p.fibres = fib
+    p.materials = [I.Material(model, params)]
+    return p
+
+
+def test_mass_is_volume():
+    p = I.block_problem(fp64=True)
+    m = oracle.Model(p)
+    assert m.mass().sum() == pytest.approx(128 * p.grid.h ** 3, rel=1e-13)
+    assert (m.mass() > 0).all()
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_force_zero_in_reference_and_rigid_motion(model, params):
+    p = tiny_mesh(model, params)
+    m = oracle.Model(p)
+    G, E = m.fe_force(p.X)
+    scale = params[-1] * p.grid.h ** 2
+    assert np.abs(G).max() < 1e-12 * scale and abs(E) < 1e-15
+    Q = rot(np.random.default_rng(5))
+    x = Q @ (p.X - 0.5) + 0.5 + np.array([[0.01], [-0.02], [0.03]])
+    G, E = m.fe_force(x)
+    assert np.abs(G).max() < 1e-11 * scale and abs(E) < 1e-15
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_force_is_minus_energy_gradient(model, params):
+    p = tiny_mesh(model, params)
+    m = oracle.Model(p)
+    x = p.x
+    G, _ = m.fe_force(x)
+    # internal force: no net force and no net torque
+    assert np.abs(G.sum(axis=1)).max() < 1e-12 * np.abs(G).max()
+    torque = np.cross(x.T, G.T).sum(axis=0)
+    assert np.abs(torque).max() < 1e-12 * np.abs(G).max()
+    eps = 1e-6 * p.grid.h
+    rng = np.random.default_rng(8)
+    for _ in range(12):
+        a, i = rng.integers(p.n_nodes), rng.integers(3)
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = -(m.fe_force(xp)[1] - m.fe_force(xm)[1]) / (2 * eps)
+        assert G[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-8 * np.abs(G).max())
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_force_adjoint_hvp_and_params(model, params):
+    p = tiny_mesh(model, params)
+    m = oracle.Model(p)
+    x = p.x
+    rng = np.random.default_rng(9)
+    v = rng.normal(size=x.shape)
+    w = rng.normal(size=x.shape)
+    Hv, gp = m.fe_force_adj(x, v)
+    Hw, _ = m.fe_force_adj(x, w)
+    # symmetric Hessian: <w, Hv> = <v, Hw>
+    assert np.sum(w * Hv) == pytest.approx(np.sum(v * Hw), rel=1e-11)
+    eps = 1e-7 * p.grid.h
+    fd = (m.fe_force(x + eps * v)[0] - m.fe_force(x - eps * v)[0]) / (2 * eps)
+    np.testing.assert_allclose(Hv, fd, rtol=1e-5, atol=1e-6 * np.abs(Hv).max())
+    # dG/dtheta_k . v by differences in each parameter
+    for k in range(len(params)):
+        th = np.array(params, dtype=float)
+        d = 1e-6 * max(abs(th[k]), 1e-3)
+        tp, tm = th.copy(), th.copy()
+        tp[k] += d
+        tm[k] -= d
+        m.set_materials([I.Material(model, tuple(tp))])
+        Gp = m.fe_force(x)[0]
+        m.set_materials([I.Material(model, tuple(tm))])
+        Gm = m.fe_force(x)[0]
+        m.set_materials([I.Material(model, tuple(th))])
+        want = np.sum(v * (Gp - Gm)) / (2 * d)
+        assert gp[0, k] == pytest.approx(want, rel=1e-5, abs=1e-9 * np.abs(gp).max()), k
+
+
+# ---------------------------------------------------------------------------
+# spreading and interpolation
+# ---------------------------------------------------------------------------
+
+def small_problem(n=8, blocks=(2, 2, 1), seed=11, centre=None):
+    p = I.block_problem(seed=seed, n=n, blocks=blocks, noise=0.3, fp64=True, centre=centre)
+    rng = np.random.default_rng(seed)
+    G = rng.normal(size=(3, p.n_nodes))
+    return p, G
+
+
+@pytest.mark.parametrize("centre", [None, (0.02, 0.97, 0.5)])
+def test_spread_matches_brute_force_over_all_faces(centre):
+    # every face of the grid, every Gauss point, nearest periodic image;
+    # the second case straddles the periodic seam in x and y.
+    p, G = small_problem(centre=centre)
+    m = oracle.Model(p)
+    f = m.spread(p.x, G)
+    n = p.grid.n[0]
+    comp, idx = [], []
+    for c in range(3):
+        for i2 in range(n):
+            for i1 in range(n):
+                for i0 in range(n):
+                    comp.append(c)
+                    idx.append((i0, i1, i2))
+    bf = m.spread_at(p.x, G, comp, idx).reshape(3, n, n, n)
+    np.testing.assert_allclose(f, bf, rtol=1e-12, atol=1e-12 * np.abs(f).max())
+
+
+def test_spread_conserves_force_and_torque():
+    p, G = small_problem(n=16, blocks=(2, 3, 2))
+    m = oracle.Model(p)
+    f = m.spread(p.x, G)
+    h = p.grid.h
+    np.testing.assert_allclose(h ** 3 * f.reshape(3, -1).sum(axis=1), G.sum(axis=1),
+                               rtol=1e-12, atol=1e-12)
+    # torque: h^3 sum x_face x f = sum_q chi_q x P_q (first-moment condition),
+    # with x_face the staggered face position of each component.
+    n = p.grid.n[0]
+    ii = np.arange(n)
+    torque = np.zeros(3)
+    pos = []
+    for c in range(3):
+        s = [0.5, 0.5, 0.5]
+        s[c] = 0.0
+        z, y, x = np.meshgrid((ii + s[2]) * h, (ii + s[1]) * h, (ii + s[0]) * h, indexing="ij")
+        pos.append((x, y, z))
+    # tau = sum r x f: tau_x = y f_z - z f_y, etc.
+    torque[0] = np.sum(pos[2][1] * f[2]) - np.sum(pos[1][2] * f[1])
+    torque[1] = np.sum(pos[0][2] * f[0]) - np.sum(pos[2][0] * f[2])
+    torque[2] = np.sum(pos[1][0] * f[1]) - np.sum(pos[0][1] * f[0])
+    torque *= h ** 3
+    # same torque from the Lagrangian side: Gauss-point forces at chi_q equal
+    # the nodal forces redistributed with the lumped projection; compute it via
+    # interpolation of the linear fields x, y, z (exact by the first moment).
+    want = np.zeros(3)
+    lin = []
+    for d in range(3):
+        ud = np.zeros((3, n, n, n))
+        for c in range(3):
+            ud[c] = pos[c][d]
+        lin.append(ud)
+    # sum_q chi_q,d P_q,c = <G, interp(field that is x_d in component c)>
+    Gd = {}
+    for d in range(3):
+        for c in range(3):
+            u = np.zeros((3, n, n, n))
+            u[c] = pos[c][d]
+            U = m.interp(p.x, u)
+            Gd[(d, c)] = np.sum(G[c] * U[c])
+    want[0] = Gd[(1, 2)] - Gd[(2, 1)]
+    want[1] = Gd[(2, 0)] - Gd[(0, 2)]
+    want[2] = Gd[(0, 1)] - Gd[(1, 0)]
+    np.testing.assert_allclose(torque, want, rtol=1e-11, atol=1e-13)
+
+
+def test_interp_exact_on_constant_and_linear_fields():
+    p, _ = small_problem(n=16, blocks=(3, 2, 2))
+    m = oracle.Model(p)
+    n = p.grid.n[0]
+    h = p.grid.h
+    const = np.array([0.3, -1.2, 2.5])
+    u = np.broadcast_to(const[:, None, None, None], (3, n, n, n)).copy()
+    U = m.interp(p.x, u)
+    np.testing.assert_allclose(U, np.broadcast_to(const[:, None], U.shape), rtol=1e-13)
+    # linear field (the structure sits away from the seam): U^IB_q = A chi_q + b
+    A = np.random.default_rng(2).normal(size=(3, 3))
+    b = np.array([0.1, 0.2, -0.3])
+    ii = np.arange(n)
+    for c in range(3):
+        s = [0.5, 0.5, 0.5]
+        s[c] = 0.0
+        z, y, x = np.meshgrid((ii + s[2]) * h, (ii + s[1]) * h, (ii + s[0]) * h, indexing="ij")
+        u[c] = A[c, 0] * x + A[c, 1] * y + A[c, 2] * z + b[c]
+    _, Uq = m.interp(p.x, u, want_gauss=True)
+    # chi_q of a trilinear element at a Gauss point, written with the corner
+    # weights prod_d (1 + c_d xi_d)/8 (VTK corner signs)
+    g = 1 / math.sqrt(3)
+    for q in range(8):
+        xi = np.array([(2 * ((q >> d) & 1) - 1) * g for d in range(3)])
+        Nq = np.prod(1 + I.HEX_CORNERS * xi, axis=1) / 8
+        chi = np.einsum("a,iae->ie", Nq, p.x[:, p.conn])
+        np.testing.assert_allclose(Uq[:, q], A @ chi + b[:, None], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("centre", [None, (0.99, 0.5, 0.01)])
+def test_spread_interp_adjoint_identity(centre):
+    # Section 4.4: with the same quadrature, spreading and interpolation are
+    # discretely adjoint: h^3 sum f.u = sum_a G_a . U_a.
+    p, G = small_problem(n=16, blocks=(3, 3, 2), centre=centre)
+    m = oracle.Model(p)
+    rng = np.random.default_rng(12)
+    u = rng.normal(size=(3, 16, 16, 16))
+    f = m.spread(p.x, G)
+    U = m.interp(p.x, u)
+    lhs = p.grid.h ** 3 * np.sum(f * u)
+    rhs = np.sum(G * U)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_linear_adjoints():
+    p, G = small_problem(n=16, blocks=(3, 2, 2))
+    m = oracle.Model(p)
+    rng = np.random.default_rng(13)
+    gf = rng.normal(size=(3, 16, 16, 16))
+    gU = rng.normal(size=G.shape)
+    u = rng.normal(size=gf.shape)
+    gG, _ = m.spread_adj(p.x, G, gf, want_gx=False)
+    assert np.sum(gG * G) == pytest.approx(np.sum(gf * m.spread(p.x, G)), rel=1e-12)
+    gu, _ = m.interp_adj(p.x, u, gU, want_gx=False)
+    assert np.sum(gu * u) == pytest.approx(np.sum(gU * m.interp(p.x, u)), rel=1e-12)
+
+
+def test_position_adjoints_by_differences():
+    p, G = small_problem(n=16, blocks=(3, 2, 2))
+    m = oracle.Model(p)
+    rng = np.random.default_rng(14)
+    gf = rng.normal(size=(3, 16, 16, 16))
+    gU = rng.normal(size=G.shape)
+    u = m.spread(p.x, rng.normal(size=G.shape))   # a smooth-ish field
+    _, gx_s = m.spread_adj(p.x, G, gf)
+    _, gx_i = m.interp_adj(p.x, u, gU)
+    eps = 1e-6 * p.grid.h
+    for _ in range(4):
+        d = rng.normal(size=p.x.shape)
+        fd_s = (np.sum(gf * m.spread(p.x + eps * d, G)) -
+                np.sum(gf * m.spread(p.x - eps * d, G))) / (2 * eps)
+        assert np.sum(gx_s * d) == pytest.approx(fd_s, rel=1e-6)
+        fd_i = (np.sum(gU * m.interp(p.x + eps * d, u)) -
+                np.sum(gU * m.interp(p.x - eps * d, u))) / (2 * eps)
+        assert np.sum(gx_i * d) == pytest.approx(fd_i, rel=1e-6)
+
+
+def test_loss_gradient_chain_by_differences():
+    # the differentiation workload's loss on a small shell:
+    # L = sum_a |U_a|^2 + sqrt(h^3 sum |f|^2), gradients in x and the 8 HO
+    # parameters, against central differences on 20 seeded directions.
+    p = I.shell_problem(seed=4000, n=32, dims=(12, 8, 2), u_modes=3, fp64=True)
+    m = oracle.Model(p)
+    h3 = p.grid.h ** 3
+
+    def loss(x, th):
+        m.set_materials([I.Material(I.HO, tuple(th))])
+        G, _ = m.fe_force(x)
+        f = m.spread(x, G)
+        U = m.interp(x, p.u)
+        return np.sum(U * U) + math.sqrt(h3 * np.sum(f * f))
+
+    th0 = np.array(I.HO_DEFAULT)
+    x0 = p.x
+    m.set_materials([I.Material(I.HO, tuple(th0))])
+    G, _ = m.fe_force(x0)
+    f = m.spread(x0, G)
+    U = m.interp(x0, p.u)
+    nf = math.sqrt(h3 * np.sum(f * f))
+    _, gx_i = m.interp_adj(x0, p.u, 2 * U)
+    gG, gx_s = m.spread_adj(x0, G, h3 * f / nf)
+    Hv, gth = m.fe_force_adj(x0, gG)
+    gx = gx_i + gx_s + Hv
+    rng = np.random.Generator(np.random.PCG64(4001))
+    for _ in range(20):
+        dx = rng.normal(size=x0.shape) * p.grid.h
+        dth = rng.normal(size=9) * th0
+        dth[8] = 0.0
+        n = math.sqrt(np.sum((dx / p.grid.h) ** 2) + np.sum((dth / th0) ** 2))
+        dx /= n
+        dth /= n
+        eps = 1e-6
+        fd = (loss(x0 + eps * dx, th0 + eps * dth) - loss(x0 - eps * dx, th0 - eps * dth)) / (2 * eps)
+        an = np.sum(gx * dx) + np.sum(gth[0] * dth)
+        assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_material_table_conversions_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "material_tables.txt"))
+            if l.strip() and not l.startswith("#")]
+    lv = {r[1]: float(r[4]) for r in rows if r[0] == "LV"}
+    mv = {r[1]: float(r[4]) for r in rows if r[0] == "MV"}
+    for r in rows:
+        scale = {"dyn/cm2": 1e-4, "Pa": 1e-3, "-": 1.0}[r[3]]
+        assert float(r[2]) * scale == pytest.approx(float(r[4]), rel=1e-12)
+    # HO sheet/shear constants of the workloads are the LV table in kPa
+    assert I.HO_DEFAULT[4] == pytest.approx(lv["as"], rel=1e-3)
+    assert I.HO_DEFAULT[5] == pytest.approx(lv["bs"])
+    assert I.HO_DEFAULT[6] == pytest.approx(lv["afs"], rel=1e-3)
+    assert I.HO_DEFAULT[7] == pytest.approx(lv["bfs"])
+    assert I.HO_DEFAULT[8] == pytest.approx(lv["kappa"])
+    assert I.FIBRE1_LEAFLET[:3] == pytest.approx((mv["C1"], mv["af"], mv["bf"]))
+
+
+def test_workload_shapes_and_jacobians():
+    p = I.shell_problem()
+    assert (p.n_elems, p.n_nodes, p.n_gauss) == (14400, 17220, 115200)
+    m = oracle.Model(p)
+    w, J = m.gauss_info(p.x)
+    assert (w > 0).all()
+    assert J.min() > 0.9 and J.max() < 1.1
+    b = I.block_problem()
+    assert (b.n_elems, b.n_nodes, b.n_gauss) == (128, 243, 1024)
