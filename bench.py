@@ -1,0 +1,427 @@
+"""Benchmark of the immersed-boundary coupling step on GB300.
+
+One step = the forward coupling (FE force + spreading + interpolation,
+ib_forward) over the 256^3 workload: a Holzapfel-Ogden ventricle-like shell
+(160x100x10 hexes) plus two fibre-reinforced leaflet-like sheets (80x40x2
+each), 172,800 elements, 1,382,400 Gauss points, 16-mode velocity field.
+Inputs are seeded and synthetic (inputs.py).  The adjoint (interp_adj +
+spread_adj + fe_force_adj with parameter gradients) is timed the same way and
+reported as the adjoint/forward ratio.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (bounded sample
+of the same workload per step).  Under torchrun each rank runs an independent
+replica (its own seed); value = Gauss points of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IB force+spread+interp Gauss-pts/s, % HBM roofline; adjoint/forward time ratio"
+UNIT = "Gauss-pts/s"
+WORKLOAD = ("shell256: 256^3 periodic MAC grid; HO ventricle-like shell 160x100x10 hex + two "
+            "80x40x2 fibre-reinforced leaflet sheets; 172,800 trilinear hexes, 1,382,400 Gauss "
+            "points; 16 divergence-free Fourier velocity modes")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel]
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d["sha"]:
+            return None
+        return float(d["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def oracle_forward_rate(prob, min_seconds=10.0, max_reps=8):
+    """The oracle (single-threaded FP64) on the whole workload, repeated."""
+    import oracle
+    from paper_2503_22695_gb300 import inputs as I
+    m = oracle.Model(prob)
+    x = I.from_split(prob.cell, prob.off, prob.grid)
+    u = prob.u.astype("float64")
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        G, _ = m.fe_force(x)
+        m.spread(x, G)
+        m.interp(x, u)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds or reps >= max_reps:
+            break
+    support = m.support_count(x)
+    return prob.n_gauss * reps / dt, reps, dt, support
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2503_22695_gb300 import inputs as I
+    oracle.build()
+    prob = I.shell_sheets_problem()
+    m = oracle.Model(prob)
+    x = I.from_split(prob.cell, prob.off, prob.grid)
+    u = prob.u.astype(np.float64)
+    # per-step sample: whole elements of the mesh, sized so W + K steps take
+    # about two minutes in total
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    t0 = time.perf_counter()
+    G, _ = m.fe_force(x)
+    m.spread(x, G)
+    m.interp(x, u)
+    full = time.perf_counter() - t0
+    frac = min(1.0, budget / full)
+    E = prob.n_elems
+    k = max(1, int(E * frac))
+    if k < E:
+        conn = prob.conn[:, :k]
+        used = np.unique(conn)
+        remap = -np.ones(prob.n_nodes, dtype=np.int64)
+        remap[used] = np.arange(len(used))
+        sub = oracle.Model(grid=prob.grid, conn=remap[conn], X=prob.X[:, used],
+                           fibres=prob.fibres[:, :k], mat_id=prob.mat_id[:k],
+                           materials=prob.materials)
+        xs = x[:, used]
+    else:
+        sub, xs = m, x
+    for _ in range(args.warmup):
+        G, _ = sub.fe_force(xs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        G, _ = sub.fe_force(xs)
+        sub.spread(xs, G)
+        sub.interp(xs, u)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = 8 * k / t
+    sample = (f"first {k} of {E} elements ({8 * k} Gauss points) of the shell256 workload "
+              f"per step, full 256^3 grid (zero-fill and stencils included)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    from paper_2503_22695_gb300 import _build
+    _build.build()
+    from paper_2503_22695_gb300 import ibfe
+    from paper_2503_22695_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    prob = I.shell_sheets_problem(seed=3000 + 17 * rank)
+    Q, E, N = prob.n_gauss, prob.n_elems, prob.n_nodes
+    n = prob.grid.n[0]
+    conn = torch.from_numpy(prob.conn).to(dev)
+    X = torch.from_numpy(prob.X).to(dev)
+    fib = torch.from_numpy(prob.fibres).to(dev)
+    mid = torch.from_numpy(prob.mat_id).to(dev)
+    plan = ibfe.Plan(conn, X, prob.grid.n, prob.grid.h, fibres=fib, mat_id=mid)
+    cell = torch.from_numpy(prob.cell).to(dev)
+    off = torch.from_numpy(prob.off).to(dev)
+    pos = ibfe.Pos(cell=cell, off=off)
+    u = torch.from_numpy(prob.u).to(dev)
+    mats = [ibfe.Material(m.model, m.params) for m in prob.materials]
+    G = torch.empty((3, N), device=dev)
+    f = torch.empty(plan.grid_shape(), device=dev)
+    U = torch.empty((3, N), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(step_fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for a, b in evs:
+            flush.zero_()                      # L2 flush outside the timed interval
+            a.record(stream)
+            step_fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    fwd = lambda: ibfe.ib_forward(plan, mats, pos, u, G, f, U)
+    # --- forward ---------------------------------------------------------
+    for _ in range(args.warmup):
+        fwd()
+    barrier()
+    ibfe.ib_plan_profile(plan, reset=True)
+    ibfe.ib_plan_set_profiling(plan, True)
+    with ClockSampler(local) as clk:
+        ms = timed(fwd, args.steps)
+    ibfe.ib_plan_set_profiling(plan, False)
+    stages = ibfe.ib_plan_profile(plan, reset=True)
+    t_fwd = sum(ms) / len(ms)
+    barrier()
+
+    # --- adjoint ---------------------------------------------------------
+    rng = np.random.default_rng(77 + rank)
+    gU = torch.from_numpy(rng.normal(size=(3, N)).astype(np.float32)).to(dev)
+    gf = torch.from_numpy((rng.normal(size=(3, n, n, n)) * 1e-3).astype(np.float32)).to(dev)
+    gu = torch.empty_like(u)
+    gx1 = torch.empty((3, N), device=dev)
+    gx2 = torch.empty((3, N), device=dev)
+    gG = torch.empty((3, N), device=dev)
+    Hv = torch.empty((3, N), device=dev)
+
+    def adj():
+        ibfe.ib_interp_adj(plan, pos, u, gU, True, gu, gx1)
+        ibfe.ib_spread_adj(plan, pos, G, gf, True, gG, gx2)
+        ibfe.ib_fe_force_adj(plan, mats, pos, gG, True, Hv)
+
+    for _ in range(args.warmup):
+        adj()
+    barrier()
+    ms_adj = timed(adj, args.steps)
+    t_adj = sum(ms_adj) / len(ms_adj)
+    barrier()
+
+    # --- end to end through host buffers ---------------------------------
+    h_cell = cell.cpu().pin_memory()
+    h_off = off.cpu().pin_memory()
+    h_u = u.cpu().pin_memory()
+    h_G = torch.empty((3, N), pin_memory=True)
+    h_f = torch.empty(plan.grid_shape(), pin_memory=True)
+    h_U = torch.empty((3, N), pin_memory=True)
+    d_cell, d_off, d_u = torch.empty_like(cell), torch.empty_like(off), torch.empty_like(u)
+    pos_e = ibfe.Pos(cell=d_cell, off=d_off)
+
+    def e2e():
+        d_cell.copy_(h_cell, non_blocking=True)
+        d_off.copy_(h_off, non_blocking=True)
+        d_u.copy_(h_u, non_blocking=True)
+        ibfe.ib_forward(plan, mats, pos_e, d_u, G, f, U)
+        h_G.copy_(G, non_blocking=True)
+        h_f.copy_(f, non_blocking=True)
+        h_U.copy_(U, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e()
+    barrier()
+    ms_e2e = timed(e2e, args.steps)
+    t_e2e = sum(ms_e2e) / len(ms_e2e)
+    barrier()
+    h2d = (h_cell.numel() * 4 + h_off.numel() * 4 + h_u.numel() * 4)
+    d2h = (h_G.numel() + h_f.numel() + h_U.numel()) * 4
+
+    # --- max over ranks ----------------------------------------------------
+    tt = torch.tensor([t_fwd, t_adj, t_e2e], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_fwd, t_adj, t_e2e = tt.tolist()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # --- roofline of the dominant forward kernel --------------------------
+    hbm_peak, peak_kind = measured_peaks()
+    fwd_stages = {k: v for k, v in stages.items() if v[1] > 0}
+    dom = max(fwd_stages, key=lambda k: fwd_stages[k][0])
+    per_launch_ms = {k: v[0] / max(1, v[1]) for k, v in fwd_stages.items()}
+    spread_bytes = 12.0 * n ** 3            # the dense force field written once
+    roof = None
+    if dom == "spread":
+        achieved = spread_bytes / (per_launch_ms["spread"] * 1e-3) / 1e9
+        tr = kernel_traffic("k_spread")
+        roof = {"kernel": "k_spread", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": tr,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
+                "measured" else "fallback 6.8 TB/s"}
+    else:
+        # report the HBM view of the dominant stage's kernel and the spread kernel
+        achieved = spread_bytes / (per_launch_ms["spread"] * 1e-3) / 1e9
+        roof = {"kernel": "k_spread", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": kernel_traffic("k_spread"),
+                "note": f"dominant stage is {dom}; spread shown as the HBM-defining kernel"}
+
+    # cpu baseline (oracle, one core) and the support count for the bytes model
+    cpu_rate, reps, cpu_t, support = oracle_forward_rate(prob)
+    b_force = 56.0 * E + 52.0 * N
+    b_interp = 4.0 * support + 12.0 * N
+    b_fwd = b_force + spread_bytes + b_interp
+    fwd_gbs = b_fwd / (t_fwd * 1e-3) / 1e9
+    launches = sum(v[2] for v in stages.values())
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": Q * world / (t_fwd * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_fwd,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "precision": "FP32 arithmetic on split positions (int cell + FP32 offset); FP64 for "
+                     "J-1, ln J and the fibre exponentials",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [n, n, n], "elements": E, "nodes": N,
+                   "gauss_points": Q, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "adjoint_ms_per_step": t_adj,
+        "adjoint_forward_ratio": t_adj / t_fwd,
+        "roofline": roof,
+        "forward_roofline": {"bytes_per_step": b_fwd, "achieved_GBps": fwd_gbs,
+                             "frac": fwd_gbs / hbm_peak, "peak": hbm_peak,
+                             "support_faces": support,
+                             "model": "56E + 52N (force) + 12 n^3 (spread) + 4|S| + 12N (interp)"},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in fwd_stages.items()},
+        "gpu_launches": launches,
+        "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": UNIT, "ms_per_step": t_e2e,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the full shell256 forward (force+spread+interp), "
+                                   f"{reps} repetitions in {cpu_t:.1f} s"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * ibfe -- immersed-boundary coupling operators on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library libibfe.so.  It implements the Lagrangian-Eulerian
+ * coupling step of the matrix-free immersed-boundary method of arXiv
+ * 2503.22695 (Ma, Cai, Wang, Luo, Gao, "Fully GPU-Accelerated Immersed
+ * Boundary Method for Fluid-Structure Interaction in Complex Cardiac Models"):
+ *
+ *   ib_fe_force  nodal force of the hyperelastic structure, Section 4.4
+ *                F_i = -sum_{q in H_q} P(X_q) : grad_X phi_i(X_q) w_q with P from
+ *                the strain energies of Section 3 / Section 6.3
+ *   ib_spread    spreading f = E(X, F), Section 2 Eq. (1), discrete form of
+ *                Section 4.4 (quadrature by the element Gauss rule)
+ *   ib_interp    interpolation U = I(X, u), Section 2 Eq. (2), discrete form of
+ *                Section 4.4 (U^IB at Gauss points, then the lumped L2
+ *                projection onto the finite-element space)
+ *   and their adjoints (vector-Jacobian products).  The adjointness of
+ *   spreading and interpolation under one quadrature (Section 4.4) is the
+ *   identity  h^3 sum_faces f . u = sum_nodes G . U.
+ *
+ * Conventions
+ *   Grid    periodic box [origin, origin + n h); fields are [3][n2][n1][n0]
+ *           (x fastest).  Component c lives on the lower c-faces: face
+ *           (i0,i1,i2) of component c sits at origin_d + (i_d + s_cd) h with
+ *           s_cd = 0 if d == c and 1/2 otherwise (the MAC staggering of
+ *           Section 4.3).  Requires 8 <= n_d <= 1024 and n_d % 8 == 0.
+ *   Kernel  4-point Peskin delta, delta_h(x) = h^-3 prod_d phi(x_d / h).
+ *   Mesh    trilinear hexahedra (VTK corner order), conn [8][E] int32,
+ *           reference coordinates X [3][N]; 2x2x2 Gauss rule, unit weights.
+ *   Positions (ib_pos)
+ *           IB_FP32_SPLIT: cell int32 [3][N] + off float [3][N] in [0,1); the
+ *           node sits at origin + (cell + off) h.  Cells are NOT wrapped (a
+ *           structure may straddle the periodic seam).
+ *           IB_FP64: x64 double [3][N] absolute coordinates.
+ *   Mass    lumped: m_a = sum_{e,q} N_a(xi_q) w_q j0.
+ *   Units   G is the integrated nodal force; f is a force density (delta_h
+ *           carries h^-3); u, U are velocities.
+ *   Floating type of every array argument named "Real" below: float for
+ *   IB_FP32_SPLIT plans, double for IB_FP64 plans.
+ *
+ * Ownership, streams and errors
+ *   All array pointers are caller-owned DEVICE memory unless marked host.  The
+ *   plan keeps the mesh pointers given at creation (the caller keeps them
+ *   alive and unchanged) and owns only derived data and workspace, allocated
+ *   once in ib_plan_create; no operator call allocates.  Every call is
+ *   asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream)
+ *   except where a host output (energy, gparams) is requested: then it
+ *   synchronises the stream before returning.  Argument errors return
+ *   IB_ERR_INVALID_ARG before launching anything; launch failures return
+ *   IB_ERR_CUDA.  Conditions found on the device (non-finite or out-of-range
+ *   positions, inverted elements) are latched in the plan and reported by
+ *   ib_plan_sync_status.  A plan is not thread-safe: calls on one plan must
+ *   be ordered on one stream.
+ */
+#ifndef IBFE_H
+#define IBFE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IB_OK = 0,
+  IB_ERR_INVALID_ARG = 1,
+  IB_ERR_CUDA = 2,
+  IB_ERR_NONFINITE = 3,   /* device: a position offset outside [0,1) or NaN/Inf */
+  IB_ERR_CAPACITY = 4,    /* a size exceeds a documented limit */
+  IB_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  IB_ERR_UNSUPPORTED = 6, /* valid but unsupported configuration */
+  IB_ERR_INVERTED = 7     /* device: an element with det(dX/dxi) <= 0 */
+} ib_status;
+
+typedef enum {
+  IB_NEO_HOOKEAN = 0, /* Psi = a (I1bar - 3) + kappa/2 (ln J)^2 (Section 6.3); params {a, kappa} */
+  IB_FIBRE1 = 1,      /* Psi_2 of Section 3; params {C1, af, bf, kappa} */
+  IB_HO = 2           /* Psi_4 Holzapfel-Ogden (Section 3); params {a, b, af, bf, as, bs, afs, bfs, kappa} */
+} ib_model;
+
+typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1 } ib_precision;
+
+#define IB_MAX_MATERIALS 8
+
+typedef struct {
+  int32_t n_nodes, n_elems;
+  const int32_t* conn;   /* device [8][n_elems], VTK hexahedron order */
+  const void* X;         /* device Real [3][n_nodes] reference coordinates */
+  const void* fibres;    /* device Real [6][n_elems]: e_f then e_s, or NULL (e_f = x, e_s = y) */
+  const int32_t* mat_id; /* device [n_elems] index into the material table, or NULL (all 0) */
+} ib_mesh;
+
+typedef struct {
+  int32_t n[3];
+  double h;
+  double origin[3];
+} ib_grid;
+
+typedef struct {
+  const int32_t* cell; /* IB_FP32_SPLIT: device [3][N] */
+  const float* off;    /* IB_FP32_SPLIT: device [3][N], each in [0,1) */
+  const double* x64;   /* IB_FP64: device [3][N] */
+} ib_pos;
+
+typedef struct {
+  int32_t model;     /* ib_model */
+  int32_t n_params;  /* 2, 4 or 9 according to the model */
+  double params[9];  /* host values */
+} ib_material;
+
+typedef struct ib_plan ib_plan;
+
+/* Create a plan for one mesh on one grid: validates the mesh, builds the
+ * node->(element, corner) incidence lists (a gather index, not a matrix), the
+ * lumped mass and the Gauss weights w_q j0, and allocates all workspace.
+ * Synchronises `stream`.  Returns IB_ERR_INVERTED if an element has a
+ * non-positive reference Jacobian at a Gauss point. */
+ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t precision,
+                         void* stream, ib_plan** out);
+ib_status ib_plan_destroy(ib_plan* plan);
+
+/* Copy the plan's lumped mass m [N] (Real) into `mass` (device). */
+ib_status ib_lumped_mass(ib_plan* plan, void* mass, void* stream);
+
+/* Nodal forces G (device Real [3][N], overwritten) of Section 4.4 for the
+ * material table `mats` (host, n_mats <= IB_MAX_MATERIALS).  If energy is
+ * non-NULL (host) the total elastic energy sum_{e,q} Psi(F_q) w_q j0 is
+ * written there and the stream is synchronised.  G = -dE/dx. */
+ib_status ib_fe_force(ib_plan* plan, const ib_material* mats, int32_t n_mats,
+                      const ib_pos* x, void* G, double* energy, void* stream);
+
+/* Spreading: f (device Real [3][n2][n1][n0], every entry overwritten) from
+ * nodal forces G (device Real [3][N]): F_q = sum_a N_a G_a / m_a,
+ * f^c(face) = sum_q F_q^c w_q j0 delta_h(x_face - chi_q).  The result is
+ * bitwise reproducible (fixed summation order, no floating-point atomics). */
+ib_status ib_spread(ib_plan* plan, const ib_pos* x, const void* G, void* f, void* stream);
+
+/* Interpolation: U (device Real [3][N], overwritten) from the MAC velocity u
+ * (device Real [3][n2][n1][n0]): U^IB_q = sum_faces u h^3 delta_h(x_face - chi_q),
+ * U_a = m_a^-1 sum_q N_a w_q j0 U^IB_q. */
+ib_status ib_interp(ib_plan* plan, const ib_pos* x, const void* u, void* U, void* stream);
+
+/* Forward coupling in one call, sharing one Gauss-point sort:
+ * G = fe_force(x), f = spread(x, G), U = interp(x, u). */
+ib_status ib_forward(ib_plan* plan, const ib_material* mats, int32_t n_mats,
+                     const ib_pos* x, const void* u, void* G, void* f, void* U,
+                     void* stream);
+
+/* Adjoint of spreading for the cotangent gf (device Real [3][grid]):
+ * gG = (df/dG)^T gf (device Real [3][N]), and, if gx is non-NULL,
+ * gx = (df/dx)^T gf (device Real [3][N]).  Both overwritten. */
+ib_status ib_spread_adj(ib_plan* plan, const ib_pos* x, const void* G, const void* gf,
+                        void* gG, void* gx, void* stream);
+
+/* Adjoint of interpolation for the cotangent gU (device Real [3][N]):
+ * gu = (dU/du)^T gU (device Real [3][grid], every entry overwritten, bitwise
+ * reproducible), and, if gx is non-NULL, gx = (dU/dx)^T gU (device Real [3][N]). */
+ib_status ib_interp_adj(ib_plan* plan, const ib_pos* x, const void* u, const void* gU,
+                        void* gu, void* gx, void* stream);
+
+/* Adjoint of the nodal force for the cotangent v (device Real [3][N]):
+ * Hv = (dG/dx)^T v = (dG/dx) v = -(d^2 E/dx^2) v (device Real [3][N]), and, if
+ * gparams (host double [n_mats][9]) is non-NULL, gparams[m][k] =
+ * v . dG/dtheta_{m,k} for the n_params of material m (stream synchronised). */
+ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats,
+                          const ib_pos* x, const void* v, void* Hv, double* gparams,
+                          void* stream);
+
+/* Synchronise `stream` and return (then clear) the first device-detected
+ * condition latched since the last call (IB_OK if none). */
+ib_status ib_plan_sync_status(ib_plan* plan, void* stream);
+
+/* Per-stage profiling.  While enabled, every operator records a pair of
+ * CUDA events around each of its stages on its stream (a few microseconds
+ * of overhead per stage; do not enable during CUDA-graph capture).
+ * ib_plan_profile synchronises the stream and returns, per stage, the summed
+ * elapsed milliseconds (ms, host double[IB_STAGE_COUNT], nullable), the
+ * number of operator calls that ran the stage (calls, host int64[...],
+ * nullable) and the number of kernels launched in it (launches, host
+ * int64[...], nullable; counted whether or not profiling is enabled), since
+ * the last reset; reset != 0 clears the counters afterwards.  This is a
+ * measurement facility of this library, not part of the method. */
+typedef enum {
+  IB_STAGE_FORCE = 0,   /* per-element stress and corner forces */
+  IB_STAGE_GATHER = 1,  /* element -> node gathers */
+  IB_STAGE_POINTS = 2,  /* Gauss-point positions and carried values */
+  IB_STAGE_SORT = 3,    /* stable radix sort by Eulerian tile + reorder */
+  IB_STAGE_SPREAD = 4,  /* tile-owned spreading onto the grid */
+  IB_STAGE_INTERP = 5,  /* Gauss-point interpolation (and its gradients) */
+  IB_STAGE_PROJECT = 6, /* Gauss point -> element corner projection */
+  IB_STAGE_REDUCE = 7,  /* deterministic energy / parameter reductions */
+  IB_STAGE_COUNT = 8
+} ib_stage;
+ib_status ib_plan_set_profiling(ib_plan* plan, int32_t enable);
+ib_status ib_plan_profile(ib_plan* plan, void* stream, double* ms, int64_t* calls,
+                          int64_t* launches, int32_t reset);
+
+/* Static string for a status code. */
+const char* ib_status_str(ib_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t ib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

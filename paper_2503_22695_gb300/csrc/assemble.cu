@@ -1,0 +1,162 @@
+// Deterministic element<->node transfers and the plan's static geometry.
+//
+// No sparse matrix is formed (the paper's design rule, abstract): nodal sums
+// are gathers over a static node -> (element, corner) incidence list, visited
+// in a fixed order (ascending element, then corner), so every nodal value is
+// summed in the same order on every call and no floating-point atomics occur.
+#include "ib_device.cuh"
+
+namespace ibfe {
+namespace {
+
+constexpr int kIncShift = 28;  // incidence entry: corner << 28 | element
+
+// out[c][n] = scale[n] * sum_{(a,e) in inc(n)} elem[(a*ncomp + c)*E + e]
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__ inc_off,
+                                                     const int32_t* __restrict__ inc_idx,
+                                                     const Real* __restrict__ elem,
+                                                     const Real* __restrict__ scale, int N,
+                                                     int E, Real* __restrict__ out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  Real acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = Real(0);
+  const int b = __ldg(inc_off + n), en = __ldg(inc_off + n + 1);
+  for (int k = b; k < en; ++k) {
+    const int32_t v = __ldg(inc_idx + k);
+    const int a = v >> kIncShift, e = v & ((1 << kIncShift) - 1);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] += __ldg(elem + (int64_t)(a * NC + c) * E + e);
+  }
+  const Real s = scale ? __ldg(scale + n) : Real(1);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[(int64_t)c * N + n] = acc[c] * s;
+}
+
+// out[(a*NC + c)*E + e] = sum_q N_a(xi_q) vals[c][q*E + e]
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256) k_elem_project(const Real* __restrict__ vals, int E,
+                                                      Real* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int64_t Q = 8LL * E;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    Real v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldg(vals + c * Q + (int64_t)q * E + e);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      Real s = Real(0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += Real(shapeN(a, q)) * v[q];
+      out[(int64_t)(a * NC + c) * E + e] = s;
+    }
+  }
+}
+
+// w_q j0 at the eight Gauss points of each element (unit Gauss weights).
+template <typename Real>
+__global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
+                                             const Real* __restrict__ X, int E, int64_t N,
+                                             Real* __restrict__ wj0, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  Real dX[8][3];
+  const int n0 = __ldg(conn + e);
+  for (int a = 0; a < 8; ++a) {
+    const int n = __ldg(conn + a * E + e);
+    for (int d = 0; d < 3; ++d) dX[a][d] = __ldg(X + d * N + n) - __ldg(X + d * N + n0);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    Real J0[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Real s = Real(0);
+#pragma unroll
+        for (int a = 1; a < 8; ++a) s += dX[a][i] * Real(shape_dxi(a, q, j));
+        J0[i][j] = s;
+      }
+    const Real det = J0[0][0] * (J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1]) +
+                     J0[0][1] * (J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2]) +
+                     J0[0][2] * (J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0]);
+    if (!(det > Real(0))) bad = true;
+    wj0[(int64_t)q * E + e] = det;
+  }
+  if (bad) set_status(status, kStatInverted);
+}
+
+template <typename Real>
+__global__ void k_invert(const Real* __restrict__ m, Real* __restrict__ im, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  // nodes that belong to no element carry no mass and receive zero
+  if (n < N) im[n] = m[n] > Real(0) ? Real(1) / m[n] : Real(0);
+}
+
+template <typename Real>
+ib_status gather_t(ib_plan* p, const void* elem, const void* scale, void* out, int nc,
+                   cudaStream_t s) {
+  if (p->N == 0) return IB_OK;
+  const int blocks = (p->N + 255) / 256;
+  if (nc == 3)
+    k_node_gather<Real, 3><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
+                                                  (const Real*)scale, p->N, p->E, (Real*)out);
+  else
+    k_node_gather<Real, 1><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
+                                                  (const Real*)scale, p->N, p->E, (Real*)out);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+template <typename Real>
+ib_status project_t(ib_plan* p, const void* vals, void* out, int nc, cudaStream_t s) {
+  if (p->E == 0) return IB_OK;
+  const int blocks = (p->E + 255) / 256;
+  if (nc == 3)
+    k_elem_project<Real, 3><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+  else
+    k_elem_project<Real, 1><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+template <typename Real>
+ib_status static_t(ib_plan* p, cudaStream_t s) {
+  if (p->E > 0) {
+    k_wj0<Real><<<(p->E + 127) / 128, 128, 0, s>>>(p->conn, (const Real*)p->X, p->E, p->N,
+                                                   (Real*)p->wj0, p->dstatus);
+    if (cudaGetLastError() != cudaSuccess) return IB_ERR_CUDA;
+  }
+  // m_a = sum_{(e,q) containing a} N_a(xi_q) w_q j0
+  ib_status st = project_t<Real>(p, p->wj0, p->elem_scratch, 1, s);
+  if (st != IB_OK) return st;
+  st = gather_t<Real>(p, p->elem_scratch, nullptr, p->mass, 1, s);
+  if (st != IB_OK) return st;
+  if (p->N > 0)
+    k_invert<Real><<<(p->N + 255) / 256, 256, 0, s>>>((const Real*)p->mass, (Real*)p->inv_mass,
+                                                      p->N);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+}  // namespace
+
+ib_status launch_node_gather(ib_plan* p, const void* elem, const void* scale, void* out,
+                             cudaStream_t s) {
+  return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, out, 3, s)
+                                 : gather_t<float>(p, elem, scale, out, 3, s);
+}
+
+ib_status launch_elem_project(ib_plan* p, const void* vals, void* out, cudaStream_t s) {
+  return p->precision == IB_FP64 ? project_t<double>(p, vals, out, 3, s)
+                                 : project_t<float>(p, vals, out, 3, s);
+}
+
+ib_status launch_plan_static(ib_plan* p, cudaStream_t s) {
+  return p->precision == IB_FP64 ? static_t<double>(p, s) : static_t<float>(p, s);
+}
+
+}  // namespace ibfe

@@ -1,0 +1,499 @@
+// C ABI of libibfe: plan lifecycle, argument validation and the operator
+// entry points declared in include/ibfe.h.  Every operator is a short,
+// stream-ordered sequence of the kernels in this directory; nothing here
+// allocates after ib_plan_create.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ib_internal.cuh"
+
+namespace ibfe {
+int sort_hist_blocks(int64_t Q);
+}
+
+using namespace ibfe;
+
+namespace {
+
+constexpr int kIncShift = 28;
+
+bool ok(cudaError_t e) { return e == cudaSuccess; }
+
+template <typename T>
+bool dalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  return ok(cudaMalloc((void**)p, bytes));
+}
+
+void free_plan(ib_plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->inc_off, p->inc_idx, p->mass, p->inv_mass, p->wj0, p->elem_scratch,
+                  p->elem_scratch2, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist,
+                  p->tile_start, p->tile_end, p->q_cell, p->q_off, p->q_val, p->p_cell,
+                  p->p_off, p->p_val, p->p_idx, p->gq_a, p->gq_b, p->epart, p->ered,
+                  p->dstatus};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->ev) {
+    for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
+    delete[] p->ev;
+    delete[] p->ev_stage;
+  }
+  delete p;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+ib_status check_launch(ib_status st) {
+  if (st != IB_OK) return st;
+  return ok(cudaGetLastError()) ? IB_OK : IB_ERR_CUDA;
+}
+
+ib_status check_pos(const ib_plan* p, const ib_pos* x) {
+  if (!x) return IB_ERR_INVALID_ARG;
+  if (p->precision == IB_FP64) return x->x64 ? IB_OK : IB_ERR_INVALID_ARG;
+  return (x->cell && x->off) ? IB_OK : IB_ERR_INVALID_ARG;
+}
+
+const void* pos_a(const ib_plan* p, const ib_pos* x) {
+  return p->precision == IB_FP64 ? (const void*)x->x64 : (const void*)x->cell;
+}
+
+ib_status make_table(const ib_plan* p, const ib_material* mats, int32_t n_mats, MatTable& mt) {
+  if (!mats || n_mats <= 0 || n_mats > IB_MAX_MATERIALS || n_mats <= p->max_mat_id)
+    return IB_ERR_INVALID_ARG;
+  std::memset(&mt, 0, sizeof(mt));
+  mt.n = n_mats;
+  for (int m = 0; m < n_mats; ++m) {
+    const int model = mats[m].model;
+    const int np = model == IB_NEO_HOOKEAN ? 2 : (model == IB_FIBRE1 ? 4 : (model == IB_HO ? 9 : -1));
+    if (np < 0 || mats[m].n_params != np) return IB_ERR_INVALID_ARG;
+    for (int k = 0; k < np; ++k)
+      if (!std::isfinite(mats[m].params[k])) return IB_ERR_INVALID_ARG;
+    // exponential laws divide by their rate constants in the energy
+    if (model == IB_FIBRE1 && mats[m].params[2] == 0.0) return IB_ERR_INVALID_ARG;
+    if (model == IB_HO)
+      for (int k : {1, 3, 5, 7})
+        if (mats[m].params[k] == 0.0) return IB_ERR_INVALID_ARG;
+    mt.model[m] = model;
+    for (int k = 0; k < np; ++k) mt.p[m][k] = mats[m].params[k];
+  }
+  return IB_OK;
+}
+
+// Fold recorded event pairs into the per-stage sums (waits for them).
+void prof_flush(ib_plan* p) {
+  if (!p->ev_used) return;
+  cudaEventSynchronize(p->ev[p->ev_used - 1]);
+  for (int i = 0; i + 1 < p->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) == cudaSuccess)
+      p->prof_ms[p->ev_stage[i / 2]] += ms;
+  }
+  p->ev_used = 0;
+}
+
+// One stage of an operator: counts its kernel launches and, while profiling
+// is enabled, brackets it with CUDA events on the operator's stream.
+struct Stage {
+  ib_plan* p;
+  cudaStream_t s;
+  bool rec;
+  Stage(ib_plan* p_, int stage, cudaStream_t s_, int launches) : p(p_), s(s_), rec(false) {
+    p->prof_launches[stage] += launches;
+    p->prof_calls[stage] += 1;
+    if (p->prof_on && p->ev) {
+      if (p->ev_used + 2 > p->ev_cap) prof_flush(p);
+      p->ev_stage[p->ev_used / 2] = stage;
+      cudaEventRecord(p->ev[p->ev_used], s);
+      rec = true;
+    }
+  }
+  ~Stage() {
+    if (rec) {
+      cudaEventRecord(p->ev[p->ev_used + 1], s);
+      p->ev_used += 2;
+    }
+  }
+};
+
+int sort_launches(const ib_plan* p) {
+  int bits = 1;
+  while ((1 << bits) < p->ntiles) ++bits;
+  return 3 * ((bits + 7) / 8) + 2;
+}
+
+// forward pieces shared by the entry points
+ib_status do_points_sorted(ib_plan* p, const ib_pos* x, const void* nodal, cudaStream_t s) {
+  ib_status st;
+  {
+    Stage sc(p, IB_STAGE_POINTS, s, 1);
+    st = launch_points(p, pos_a(p, x), x->off, nodal, nodal ? 1 : 0, s);
+  }
+  if (st != IB_OK) return st;
+  Stage sc(p, IB_STAGE_SORT, s, sort_launches(p));
+  return launch_sort_points(p, nodal != nullptr, s);
+}
+
+ib_status do_interp(ib_plan* p, const void* u, int mode, double vs, double gs, cudaStream_t s) {
+  Stage sc(p, IB_STAGE_INTERP, s, 1);
+  return launch_interp_points(p, u, mode, vs, gs, s);
+}
+
+ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
+  Stage sc(p, IB_STAGE_PROJECT, s, 1);
+  return launch_elem_project(p, vals, elem, s);
+}
+
+ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, cudaStream_t s) {
+  Stage sc(p, IB_STAGE_GATHER, s, 1);
+  return launch_node_gather(p, elem, scale, out, s);
+}
+
+ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
+  Stage sc(p, IB_STAGE_SPREAD, s, 1);
+  return launch_spread(p, scale, f, s);
+}
+
+ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
+  Stage sc(p, IB_STAGE_REDUCE, s, 1);
+  return launch_reduce_parts(p, nvals, n_mats, s);
+}
+
+ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s) {
+  ib_status st = do_interp(p, u, 0, 1.0, 0.0, s);
+  if (st == IB_OK) st = do_project(p, p->gq_a, p->elem_scratch, s);
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, p->inv_mass, U, s);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ib_version(void) { return 100; }
+
+const char* ib_status_str(ib_status s) {
+  switch (s) {
+    case IB_OK: return "ok";
+    case IB_ERR_INVALID_ARG: return "invalid argument";
+    case IB_ERR_CUDA: return "CUDA error";
+    case IB_ERR_NONFINITE: return "position offset outside [0,1) or not finite";
+    case IB_ERR_CAPACITY: return "size exceeds a documented limit";
+    case IB_ERR_TIMEOUT: return "bounded device wait gave up";
+    case IB_ERR_UNSUPPORTED: return "unsupported configuration";
+    case IB_ERR_INVERTED: return "element with non-positive reference Jacobian";
+  }
+  return "unknown status";
+}
+
+ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t precision,
+                         void* stream, ib_plan** out) {
+  if (!out) return IB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !grid) return IB_ERR_INVALID_ARG;
+  if (precision != IB_FP32_SPLIT && precision != IB_FP64) return IB_ERR_INVALID_ARG;
+  if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || !mesh->conn || !mesh->X)
+    return IB_ERR_INVALID_ARG;
+  if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (!std::isfinite(grid->origin[d])) return IB_ERR_INVALID_ARG;
+    if (grid->n[d] < kTile || grid->n[d] > (1 << kPackBits)) return IB_ERR_UNSUPPORTED;
+    if (grid->n[d] % kTile) return IB_ERR_UNSUPPORTED;
+  }
+  if ((int64_t)mesh->n_elems >= (1LL << kIncShift) / 8) return IB_ERR_CAPACITY;
+  cudaStream_t s = S(stream);
+  const int64_t E = mesh->n_elems, N = mesh->n_nodes, Q = 8 * E;
+
+  // connectivity and materials to the host for validation and incidence lists
+  std::vector<int32_t> conn(8 * E), mid;
+  if (E > 0 && !ok(cudaMemcpyAsync(conn.data(), mesh->conn, sizeof(int32_t) * 8 * E,
+                                   cudaMemcpyDeviceToHost, s)))
+    return IB_ERR_CUDA;
+  if (mesh->mat_id) {
+    mid.resize(E);
+    if (E > 0 && !ok(cudaMemcpyAsync(mid.data(), mesh->mat_id, sizeof(int32_t) * E,
+                                     cudaMemcpyDeviceToHost, s)))
+      return IB_ERR_CUDA;
+  }
+  if (!ok(cudaStreamSynchronize(s))) return IB_ERR_CUDA;
+  for (int64_t k = 0; k < 8 * E; ++k)
+    if (conn[k] < 0 || conn[k] >= N) return IB_ERR_INVALID_ARG;
+  int max_mid = 0;
+  for (int32_t m : mid) {
+    if (m < 0 || m >= IB_MAX_MATERIALS) return IB_ERR_INVALID_ARG;
+    max_mid = m > max_mid ? m : max_mid;
+  }
+
+  // node -> (corner, element) incidence, ascending element then corner
+  std::vector<int32_t> inc_off(N + 1, 0), inc_idx(8 * E);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 8; ++a) inc_off[conn[a * E + e] + 1]++;
+  for (int64_t n = 0; n < N; ++n) inc_off[n + 1] += inc_off[n];
+  {
+    std::vector<int32_t> fill(inc_off.begin(), inc_off.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < 8; ++a) inc_idx[fill[conn[a * E + e]]++] = (a << kIncShift) | (int32_t)e;
+  }
+
+  ib_plan* p = new ib_plan;
+  std::memset(p, 0, sizeof(ib_plan));
+  p->precision = precision;
+  p->N = (int)N;
+  p->E = (int)E;
+  p->Q = Q;
+  p->rsize = precision == IB_FP64 ? sizeof(double) : sizeof(float);
+  for (int d = 0; d < 3; ++d) {
+    p->grid.n[d] = grid->n[d];
+    p->grid.nt[d] = grid->n[d] / kTile;
+    p->grid.origin[d] = grid->origin[d];
+  }
+  p->grid.h = grid->h;
+  p->ntiles = p->grid.nt[0] * p->grid.nt[1] * p->grid.nt[2];
+  p->conn = mesh->conn;
+  p->X = mesh->X;
+  p->fibres = mesh->fibres;
+  p->mat_id = mesh->mat_id;
+  p->max_mat_id = max_mid;
+  p->hist_blocks = sort_hist_blocks(Q);
+  const size_t rs = p->rsize;
+  bool good = dalloc(&p->inc_off, 4 * (N + 1)) && dalloc(&p->inc_idx, 4 * 8 * E) &&
+              dalloc(&p->mass, rs * N) && dalloc(&p->inv_mass, rs * N) &&
+              dalloc(&p->wj0, rs * Q) && dalloc(&p->elem_scratch, rs * 24 * E) &&
+              dalloc(&p->elem_scratch2, rs * 24 * E) && dalloc(&p->keys[0], 4 * Q) &&
+              dalloc(&p->keys[1], 4 * Q) && dalloc(&p->vals[0], 4 * Q) &&
+              dalloc(&p->vals[1], 4 * Q) && dalloc(&p->hist, 4 * 256 * (size_t)p->hist_blocks) &&
+              dalloc(&p->tile_start, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_end, 4 * (size_t)p->ntiles) && dalloc(&p->q_cell, 4 * Q) &&
+              dalloc(&p->q_off, rs * 3 * Q) && dalloc(&p->q_val, rs * 3 * Q) &&
+              dalloc(&p->p_cell, 4 * Q) && dalloc(&p->p_off, rs * 3 * Q) &&
+              dalloc(&p->p_val, rs * 3 * Q) && dalloc(&p->p_idx, 4 * Q) &&
+              dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
+              dalloc(&p->epart, 8 * 9 * (size_t)(E > 0 ? E : 1)) &&
+              dalloc(&p->ered, 8 * 9 * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16);
+  if (!good) {
+    free_plan(p);
+    cudaGetLastError();
+    return IB_ERR_CUDA;
+  }
+  good = ok(cudaMemcpyAsync(p->inc_off, inc_off.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s)) &&
+         (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * 8 * E,
+                                       cudaMemcpyHostToDevice, s))) &&
+         ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
+  if (!good || launch_plan_static(p, s) != IB_OK || !ok(cudaStreamSynchronize(s))) {
+    free_plan(p);
+    return IB_ERR_CUDA;
+  }
+  int st = 0;
+  if (!ok(cudaMemcpy(&st, p->dstatus, sizeof(int), cudaMemcpyDeviceToHost))) {
+    free_plan(p);
+    return IB_ERR_CUDA;
+  }
+  if (st & kStatInverted) {
+    free_plan(p);
+    return IB_ERR_INVERTED;
+  }
+  *out = p;
+  return IB_OK;
+}
+
+ib_status ib_plan_destroy(ib_plan* plan) {
+  if (!plan) return IB_ERR_INVALID_ARG;
+  free_plan(plan);
+  return IB_OK;
+}
+
+ib_status ib_lumped_mass(ib_plan* p, void* mass, void* stream) {
+  if (!p || !mass) return IB_ERR_INVALID_ARG;
+  return ok(cudaMemcpyAsync(mass, p->mass, p->rsize * p->N, cudaMemcpyDeviceToDevice, S(stream)))
+             ? IB_OK
+             : IB_ERR_CUDA;
+}
+
+ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                      void* G, double* energy, void* stream) {
+  if (!p || !G) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  {
+    Stage sc(p, IB_STAGE_FORCE, s, 1);
+    st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, energy != nullptr, s);
+  }
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK && energy) {
+    st = do_reduce(p, 1, n_mats, s);
+    double red[9 * IB_MAX_MATERIALS];
+    if (st == IB_OK &&
+        (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
+         !ok(cudaStreamSynchronize(s))))
+      st = IB_ERR_CUDA;
+    if (st == IB_OK) {
+      double en = 0.0;
+      for (int m = 0; m < n_mats; ++m) en += red[m * 9];
+      *energy = en;
+    }
+  }
+  return check_launch(st);
+}
+
+ib_status ib_spread(ib_plan* p, const ib_pos* x, const void* G, void* f, void* stream) {
+  if (!p || !G || !f) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  st = do_points_sorted(p, x, G, s);
+  if (st == IB_OK) st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s);
+  return check_launch(st);
+}
+
+ib_status ib_interp(ib_plan* p, const ib_pos* x, const void* u, void* U, void* stream) {
+  if (!p || !u || !U) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  st = do_points_sorted(p, x, nullptr, s);
+  if (st == IB_OK) st = do_interp_tail(p, u, U, s);
+  return check_launch(st);
+}
+
+ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                     const void* u, void* G, void* f, void* U, void* stream) {
+  if (!p || !u || !G || !f || !U) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  {
+    Stage sc(p, IB_STAGE_FORCE, s, 1);
+    st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
+  }
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK) st = do_points_sorted(p, x, G, s);
+  if (st == IB_OK) st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s);
+  if (st == IB_OK) st = do_interp_tail(p, u, U, s);
+  return check_launch(st);
+}
+
+ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* gf, void* gG,
+                        void* gx, void* stream) {
+  if (!p || !G || !gf || !gG) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
+  st = do_points_sorted(p, x, G, s);
+  if (st == IB_OK) st = do_interp(p, gf, gx ? 1 : 0, ih3, ih3 / h, s);
+  if (st == IB_OK) st = do_project(p, p->gq_a, p->elem_scratch, s);
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, p->inv_mass, gG, s);
+  if (st == IB_OK && gx) {
+    st = do_project(p, p->gq_b, p->elem_scratch2, s);
+    if (st == IB_OK) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
+  }
+  return check_launch(st);
+}
+
+ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* gU, void* gu,
+                        void* gx, void* stream) {
+  if (!p || !gU || !gu || (gx && !u)) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  st = do_points_sorted(p, x, gU, s);
+  if (st == IB_OK) st = do_spread(p, 1.0, gu, s);
+  if (st == IB_OK && gx) {
+    st = do_interp(p, u, 2, 0.0, 1.0 / p->grid.h, s);
+    if (st == IB_OK) st = do_project(p, p->gq_b, p->elem_scratch2, s);
+    if (st == IB_OK) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
+  }
+  return check_launch(st);
+}
+
+ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                          const void* v, void* Hv, double* gparams, void* stream) {
+  if (!p || !v || !Hv) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  {
+    Stage sc(p, IB_STAGE_FORCE, s, 1);
+    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, gparams != nullptr,
+                             s);
+  }
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s);
+  if (st == IB_OK && gparams) {
+    st = do_reduce(p, 9, n_mats, s);
+    double red[9 * IB_MAX_MATERIALS];
+    if (st == IB_OK &&
+        (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
+         !ok(cudaStreamSynchronize(s))))
+      st = IB_ERR_CUDA;
+    if (st == IB_OK)
+      for (int m = 0; m < n_mats; ++m)
+        for (int k = 0; k < 9; ++k) gparams[m * 9 + k] = red[m * 9 + k];
+  }
+  return check_launch(st);
+}
+
+ib_status ib_plan_set_profiling(ib_plan* p, int32_t enable) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  if (enable && !p->ev) {
+    const int cap = 8192;
+    p->ev = new cudaEvent_t[cap];
+    p->ev_stage = new int[cap / 2];
+    for (int i = 0; i < cap; ++i)
+      if (!ok(cudaEventCreate(&p->ev[i]))) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(p->ev[j]);
+        delete[] p->ev;
+        delete[] p->ev_stage;
+        p->ev = nullptr;
+        p->ev_stage = nullptr;
+        return IB_ERR_CUDA;
+      }
+    p->ev_cap = cap;
+    p->ev_used = 0;
+  }
+  p->prof_on = enable ? 1 : 0;
+  return IB_OK;
+}
+
+ib_status ib_plan_profile(ib_plan* p, void* stream, double* ms, int64_t* calls,
+                          int64_t* launches, int32_t reset) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  if (!ok(cudaStreamSynchronize(S(stream)))) return IB_ERR_CUDA;
+  prof_flush(p);
+  for (int i = 0; i < IB_STAGE_COUNT; ++i) {
+    if (ms) ms[i] = p->prof_ms[i];
+    if (calls) calls[i] = p->prof_calls[i];
+    if (launches) launches[i] = p->prof_launches[i];
+    if (reset) {
+      p->prof_ms[i] = 0.0;
+      p->prof_calls[i] = 0;
+      p->prof_launches[i] = 0;
+    }
+  }
+  return IB_OK;
+}
+
+ib_status ib_plan_sync_status(ib_plan* p, void* stream) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = S(stream);
+  int st = 0;
+  if (!ok(cudaStreamSynchronize(s)) ||
+      !ok(cudaMemcpy(&st, p->dstatus, sizeof(int), cudaMemcpyDeviceToHost)) ||
+      !ok(cudaMemset(p->dstatus, 0, sizeof(int))))
+    return IB_ERR_CUDA;
+  if (st & kStatNonfinite) return IB_ERR_NONFINITE;
+  if (st & kStatInverted) return IB_ERR_INVERTED;
+  return IB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,577 @@
+// Hyperelastic nodal force of the immersed structure (Section 4.4:
+// F_i = -sum_q P(X_q) : grad_X phi_i(X_q) w_q) and its adjoints, on trilinear
+// hexahedra with the 2x2x2 Gauss rule.  One thread per element; the eight
+// Gauss points are unrolled so every shape-function value is a compile-time
+// constant.
+//
+// Kinematics are carried as the displacement gradient H = F - I, formed from
+// node differences relative to corner 0 (split positions subtract their
+// integer cells exactly), so J - 1, I1 - 3 and I4 - 1 are evaluated without
+// cancellation:
+//   J - 1   = tr H + ((tr H)^2 - tr(H^2))/2 + det H
+//   I1 - 3  = 2 tr H + |H|^2
+//   I4 - 1  = (|e|^2 - 1) + 2 e.(H e) + |H e|^2
+//   I8      = e_f.e_s + e_f.(H e_s) + e_s.(H e_f) + (H e_f).(H e_s)
+// The scalars whose stability matters -- J - 1, ln J and the fibre
+// exponentials -- are evaluated in the type S (double).  Everything else is
+// in Real (float for split-precision plans, double for FP64 plans).
+//
+// With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
+//   H = Du J0^-1, and the corner forces are
+//   G_a -= (P J0^-T w j0) dN_a/dxi,
+// so the X-gradients of the shape functions are never formed.
+#include <cstdio>
+
+#include "ib_device.cuh"
+
+namespace ibfe {
+namespace {
+
+template <typename Real>
+struct FeArgs {
+  int E;
+  int64_t N;
+  const int32_t* conn;
+  const Real* X;
+  const Real* fib;       // [6][E] or null
+  const int32_t* mat_id; // [E] or null
+  NodeLoader<Real> pos;
+  Real h;
+  const Real* v;         // [3][N] direction (adjoint) or null
+  Real* out;             // [24][E] corner contributions
+  double* epart;         // [9][E] per-element partial sums or null
+  int* status;
+};
+
+template <typename T>
+__device__ __forceinline__ T det3(const T A[3][3]) {
+  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+         A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// cof(A)_ij = d det A / d A_ij
+template <typename T>
+__device__ __forceinline__ void cofactor(const T A[3][3], T C[3][3]) {
+  C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  C[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  C[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  C[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+  C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+  C[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+  C[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+  C[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+  C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+}
+
+// Quantities of one fibre family needed by the stress and its derivatives.
+template <typename Real, typename S>
+struct Fibre {
+  Real Fe[3];  // F e
+  S d;         // I4* - 1 = max(I4 - 1, 0)
+};
+
+template <typename Real, typename S>
+__device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S en1,
+                                          Fibre<Real, S>& f) {
+  Real He[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) He[i] = H[i][0] * e[0] + H[i][1] * e[1] + H[i][2] * e[2];
+  S eHe = S(e[0]) * S(He[0]) + S(e[1]) * S(He[1]) + S(e[2]) * S(He[2]);
+  S HeHe = S(He[0]) * S(He[0]) + S(He[1]) * S(He[1]) + S(He[2]) * S(He[2]);
+  S I4m1 = en1 + S(2) * eHe + HeHe;
+  f.d = I4m1 > S(0) ? I4m1 : S(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
+}
+
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
+__global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.E) return;
+  const int E = A.E;
+  int node[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) node[a] = __ldg(A.conn + a * E + e);
+
+  // reference and current coordinates relative to corner 0
+  Real dX[8][3], du[8][3];
+  int c0[3];
+  Real o0[3];
+  A.pos.load(node[0], c0, o0);
+  Real X0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + node[0]);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    int c[3];
+    Real o[3];
+    if (a == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) { dX[0][d] = Real(0); du[0][d] = Real(0); }
+      continue;
+    }
+    A.pos.load(node[a], c, o);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dX[a][d] = __ldg(A.X + d * A.N + node[a]) - X0[d];
+      Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
+      du[a][d] = dx - dX[a][d];
+    }
+  }
+  Real vv[kAdj ? 8 : 1][3];
+  if (kAdj) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) vv[a][d] = __ldg(A.v + d * A.N + node[a]);
+  }
+
+  const int mid = A.mat_id ? __ldg(A.mat_id + e) : 0;
+  const int model = mt.model[mid];
+  const double* prm = mt.p[mid];
+  Real ef[3] = {Real(1), Real(0), Real(0)}, es[3] = {Real(0), Real(1), Real(0)};
+  if (A.fib) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ef[i] = __ldg(A.fib + i * E + e);
+      es[i] = __ldg(A.fib + (3 + i) * E + e);
+    }
+  }
+  // |e|^2 - 1 and e_f . e_s, exact enough in S (squares of Real are exact in double)
+  const S efn1 = S(ef[0]) * S(ef[0]) + S(ef[1]) * S(ef[1]) + (S(ef[2]) * S(ef[2]) - S(1));
+  const S esn1 = S(es[0]) * S(es[0]) + S(es[1]) * S(es[1]) + (S(es[2]) * S(es[2]) - S(1));
+  const S efes = S(ef[0]) * S(es[0]) + S(ef[1]) * S(es[1]) + S(ef[2]) * S(es[2]);
+
+  const Real kap = Real(prm[model == 0 ? 1 : (model == 1 ? 3 : 8)]);
+
+  Real Ge[8][3];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
+  double en = 0.0;
+  double gp[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gp[k] = 0.0;
+  bool inverted = false;
+
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    // J0 = sum_a dX_a (x) dN_a/dxi ;  Du = sum_a du_a (x) dN_a/dxi
+    Real J0[3][3], Du[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Real s = Real(0), t = Real(0);
+#pragma unroll
+        for (int a = 1; a < 8; ++a) {
+          s += dX[a][i] * Real(shape_dxi(a, q, j));
+          t += du[a][i] * Real(shape_dxi(a, q, j));
+        }
+        J0[i][j] = s;
+        Du[i][j] = t;
+      }
+    Real cJ[3][3];
+    cofactor(J0, cJ);
+    const Real j0 = J0[0][0] * cJ[0][0] + J0[0][1] * cJ[0][1] + J0[0][2] * cJ[0][2];
+    if (!(j0 > Real(0))) inverted = true;
+    const Real ij0 = Real(1) / j0;
+    // J0^-1 = cof(J0)^T / det
+    Real Ji[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ji[i][j] = cJ[j][i] * ij0;
+    Real H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        H[i][j] = Du[i][0] * Ji[0][j] + Du[i][1] * Ji[1][j] + Du[i][2] * Ji[2][j];
+
+    // ---- invariants --------------------------------------------------------
+    const S trS = S(H[0][0]) + S(H[1][1]) + S(H[2][2]);
+    S trH2 = S(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) trH2 += S(H[i][j]) * S(H[j][i]);
+    S Hs[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Hs[i][j] = S(H[i][j]);
+    const S Jm1 = trS + S(0.5) * (trS * trS - trH2) + det3(Hs);
+    const S lnJs = log1p(Jm1);
+    const Real lnJ = Real(lnJs);
+    const Real J = Real(S(1) + Jm1);
+    Real F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? Real(1) : Real(0));
+    Real FiT[3][3];
+    cofactor(F, FiT);
+    const Real iJ = Real(1) / J;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) FiT[i][j] *= iJ;
+    Real HH = Real(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) HH += H[i][j] * H[i][j];
+    const Real I1m3 = Real(2) * Real(trS) + HH;
+    const Real Jm23m1 = expm1(Real(-2.0 / 3.0) * lnJ);
+    const Real Jm23 = Real(1) + Jm23m1;
+    const Real Ibm3 = Jm23 * I1m3 + Real(3) * Jm23m1;  // I1bar - 3
+    const Real I1o3 = Real(1) + I1m3 * Real(1.0 / 3.0);
+    Real Dv[3][3];  // J^-2/3 (F - I1/3 F^-T)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Dv[i][j] = Jm23 * (F[i][j] - I1o3 * FiT[i][j]);
+
+    // ---- constitutive law -----------------------------------------------------
+    Real ciso;
+    Real eiso = Real(1);  // HO: exp(b (I1bar - 3))
+    if (model == 0) {
+      ciso = Real(2.0 * prm[0]);
+    } else if (model == 1) {
+      ciso = Real(2.0 * prm[0]);
+    } else {
+      eiso = exp(Real(prm[1]) * Ibm3);
+      ciso = Real(prm[0]) * eiso;
+    }
+    Fibre<Real, S> f1, f2;
+    S cf1 = S(0), cf2 = S(0), ef1 = S(1), ef2 = S(1);
+    const bool has_f = model != 0;
+    const bool has_s = model == 2;
+    if (has_f) {
+      fibre_kin<Real, S>(H, ef, efn1, f1);
+      const S af = S(prm[model == 1 ? 1 : 2]), bf = S(prm[model == 1 ? 2 : 3]);
+      ef1 = exp(bf * f1.d * f1.d);
+      cf1 = S(2) * af * f1.d * ef1;
+    }
+    Real Fef[3], Fes[3];
+    S I8 = S(0), e8 = S(1), c8 = S(0);
+    if (has_s) {
+      fibre_kin<Real, S>(H, es, esn1, f2);
+      ef2 = exp(S(prm[5]) * f2.d * f2.d);
+      cf2 = S(2) * S(prm[4]) * f2.d * ef2;
+      Real Hef[3], Hes[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Hef[i] = H[i][0] * ef[0] + H[i][1] * ef[1] + H[i][2] * ef[2];
+        Hes[i] = H[i][0] * es[0] + H[i][1] * es[1] + H[i][2] * es[2];
+        Fef[i] = ef[i] + Hef[i];
+        Fes[i] = es[i] + Hes[i];
+      }
+      I8 = efes;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        I8 += S(ef[i]) * S(Hes[i]) + S(es[i]) * S(Hef[i]) + S(Hef[i]) * S(Hes[i]);
+      e8 = exp(S(prm[7]) * I8 * I8);
+      c8 = S(prm[6]) * I8 * e8;
+    }
+
+    if (kEnergy) {
+      double psi = 0.5 * double(kap) * double(lnJs) * double(lnJs);
+      if (model == 0 || model == 1) psi += prm[0] * double(Ibm3);
+      else psi += prm[0] / (2.0 * prm[1]) * expm1(prm[1] * double(Ibm3));
+      if (has_f) {
+        const double af = prm[model == 1 ? 1 : 2], bf = prm[model == 1 ? 2 : 3];
+        psi += af / (2.0 * bf) * expm1(bf * double(f1.d) * double(f1.d));
+      }
+      if (has_s) {
+        psi += prm[4] / (2.0 * prm[5]) * expm1(prm[5] * double(f2.d) * double(f2.d));
+        psi += prm[6] / (2.0 * prm[7]) * expm1(prm[7] * double(I8) * double(I8));
+      }
+      en += psi * double(j0);
+    }
+
+    // stress (forward) or its directional derivative (adjoint)
+    Real P[3][3];
+    if (!kAdj) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[i][j] = ciso * Dv[i][j] + kap * lnJ * FiT[i][j];
+      if (has_f) {
+        const Real c = Real(cf1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) P[i][j] += c * f1.Fe[i] * ef[j];
+      }
+      if (has_s) {
+        const Real c = Real(cf2), k8 = Real(c8);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            P[i][j] += c * f2.Fe[i] * es[j] + k8 * (Fef[i] * es[j] + Fes[i] * ef[j]);
+      }
+    } else {
+      // dF = Dvv J0^-1 with Dvv = sum_a v_a (x) dN_a/dxi
+      Real dF[3][3];
+      {
+        Real Dvv[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            Real s = Real(0);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) s += vv[a][i] * Real(shape_dxi(a, q, j));
+            Dvv[i][j] = s;
+          }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            dF[i][j] = Dvv[i][0] * Ji[0][j] + Dvv[i][1] * Ji[1][j] + Dvv[i][2] * Ji[2][j];
+      }
+      // delta = d ln J = F^-T : dF ; dI1 = 2 F : dF ; d F^-T = -F^-T dF^T F^-T
+      Real dl = Real(0), dI1 = Real(0), DdF = Real(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          dl += FiT[i][j] * dF[i][j];
+          dI1 += Real(2) * F[i][j] * dF[i][j];
+          DdF += Dv[i][j] * dF[i][j];
+        }
+      Real M[3][3];  // F^-T dF^T
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          M[i][j] = FiT[i][0] * dF[j][0] + FiT[i][1] * dF[j][1] + FiT[i][2] * dF[j][2];
+      Real dFiT[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          dFiT[i][j] = -(M[i][0] * FiT[0][j] + M[i][1] * FiT[1][j] + M[i][2] * FiT[2][j]);
+      const Real I1 = Real(3) + I1m3;
+      const Real dbeta = Jm23 * (dI1 - Real(2.0 / 3.0) * I1 * dl);
+      Real dciso = Real(0);
+      if (model == 2) dciso = ciso * Real(prm[1]) * dbeta;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const Real dD = Real(-2.0 / 3.0) * dl * Dv[i][j] +
+                          Jm23 * (dF[i][j] - dI1 * Real(1.0 / 3.0) * FiT[i][j] -
+                                  I1o3 * dFiT[i][j]);
+          P[i][j] = ciso * dD + dciso * Dv[i][j] + kap * (dl * FiT[i][j] + lnJ * dFiT[i][j]);
+        }
+      Real dI4f = Real(0), dI4s = Real(0), dI8 = Real(0);
+      if (has_f) {
+        Real dFe[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
+        dI4f = Real(2) * (f1.Fe[0] * dFe[0] + f1.Fe[1] * dFe[1] + f1.Fe[2] * dFe[2]);
+        const S bf = S(prm[model == 1 ? 2 : 3]), af = S(prm[model == 1 ? 1 : 2]);
+        const Real dc = f1.d > S(0)
+                            ? Real(S(2) * af * ef1 * (S(1) + S(2) * bf * f1.d * f1.d)) * dI4f
+                            : Real(0);
+        const Real c = Real(cf1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) P[i][j] += (dc * f1.Fe[i] + c * dFe[i]) * ef[j];
+      }
+      if (has_s) {
+        Real dFs[3], dFf[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dFs[i] = dF[i][0] * es[0] + dF[i][1] * es[1] + dF[i][2] * es[2];
+          dFf[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
+        }
+        dI4s = Real(2) * (f2.Fe[0] * dFs[0] + f2.Fe[1] * dFs[1] + f2.Fe[2] * dFs[2]);
+        const S bs = S(prm[5]), as = S(prm[4]);
+        const Real dc = f2.d > S(0)
+                            ? Real(S(2) * as * ef2 * (S(1) + S(2) * bs * f2.d * f2.d)) * dI4s
+                            : Real(0);
+        const Real c = Real(cf2);
+        dI8 = dFf[0] * Fes[0] + dFf[1] * Fes[1] + dFf[2] * Fes[2] + Fef[0] * dFs[0] +
+              Fef[1] * dFs[1] + Fef[2] * dFs[2];
+        const Real dk8 = Real(S(prm[6]) * e8 * (S(1) + S(2) * S(prm[7]) * I8 * I8)) * dI8;
+        const Real k8 = Real(c8);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            P[i][j] += (dc * f2.Fe[i] + c * dFs[i]) * es[j] +
+                       dk8 * (Fef[i] * es[j] + Fes[i] * ef[j]) +
+                       k8 * (dFf[i] * es[j] + dFs[i] * ef[j]);
+      }
+      if (kParams) {
+        // gparams_k = -sum_q w j0 (dP/dtheta_k : dF)
+        const double w = double(j0);
+        const double vol = double(lnJ) * double(dl);
+        if (model == 0) {
+          gp[0] -= w * 2.0 * double(DdF);
+          gp[1] -= w * vol;
+        } else if (model == 1) {
+          const double d = double(f1.d), ex = double(ef1);
+          gp[0] -= w * 2.0 * double(DdF);
+          gp[1] -= w * d * ex * double(dI4f);
+          gp[2] -= w * prm[1] * d * d * d * ex * double(dI4f);
+          gp[3] -= w * vol;
+        } else {
+          const double ei = double(eiso), be = double(Ibm3);
+          const double d1 = double(f1.d), x1 = double(ef1);
+          const double d2 = double(f2.d), x2 = double(ef2);
+          const double i8 = double(I8), x8 = double(e8);
+          gp[0] -= w * ei * double(DdF);
+          gp[1] -= w * prm[0] * be * ei * double(DdF);
+          gp[2] -= w * d1 * x1 * double(dI4f);
+          gp[3] -= w * prm[2] * d1 * d1 * d1 * x1 * double(dI4f);
+          gp[4] -= w * d2 * x2 * double(dI4s);
+          gp[5] -= w * prm[4] * d2 * d2 * d2 * x2 * double(dI4s);
+          gp[6] -= w * i8 * x8 * double(dI8);
+          gp[7] -= w * prm[6] * i8 * i8 * i8 * x8 * double(dI8);
+          gp[8] -= w * vol;
+        }
+      }
+    }
+
+    // corner forces: G_a -= (P J0^-T w j0) dN_a/dxi
+    Real Qm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        Qm[i][k] = (P[i][0] * Ji[k][0] + P[i][1] * Ji[k][1] + P[i][2] * Ji[k][2]) * j0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        Ge[a][i] -= Qm[i][0] * Real(shape_dxi(a, q, 0)) + Qm[i][1] * Real(shape_dxi(a, q, 1)) +
+                    Qm[i][2] * Real(shape_dxi(a, q, 2));
+  }
+
+  if (inverted) set_status(A.status, kStatInverted);
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) A.out[(a * 3 + i) * E + e] = Ge[a][i];
+  if (kEnergy) A.epart[e] = en;
+  if (kParams) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.epart[(int64_t)k * E + e] = gp[k];
+  }
+}
+
+// Deterministic per-material sums of per-element partials: one block per
+// (material, value); each thread sums a fixed stride of elements in order,
+// then a fixed-shape tree combines the threads.
+__global__ void __launch_bounds__(256) k_reduce_parts(const double* part, const int32_t* mat_id,
+                                                      int E, int nvals, double* out) {
+  const int m = blockIdx.x / nvals, k = blockIdx.x % nvals;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < E; e += blockDim.x)
+    if ((mat_id ? mat_id[e] : 0) == m) s += part[(int64_t)k * E + e];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[m * 9 + k] = sh[0];
+}
+
+template <typename Real>
+FeArgs<Real> make_args(ib_plan* p, const void* xa, const float* off, const void* v, void* out);
+
+template <>
+FeArgs<float> make_args<float>(ib_plan* p, const void* xa, const float* off, const void* v,
+                               void* out) {
+  FeArgs<float> A;
+  A.E = p->E;
+  A.N = p->N;
+  A.conn = p->conn;
+  A.X = (const float*)p->X;
+  A.fib = (const float*)p->fibres;
+  A.mat_id = p->mat_id;
+  A.pos.cell = (const int32_t*)xa;
+  A.pos.off = off;
+  A.pos.N = p->N;
+  A.h = (float)p->grid.h;
+  A.v = (const float*)v;
+  A.out = (float*)out;
+  A.epart = p->epart;
+  A.status = p->dstatus;
+  return A;
+}
+
+template <>
+FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*, const void* v,
+                                 void* out) {
+  FeArgs<double> A;
+  A.E = p->E;
+  A.N = p->N;
+  A.conn = p->conn;
+  A.X = (const double*)p->X;
+  A.fib = (const double*)p->fibres;
+  A.mat_id = p->mat_id;
+  A.pos.x64 = (const double*)xa;
+  A.pos.N = p->N;
+  for (int d = 0; d < 3; ++d) A.pos.origin[d] = p->grid.origin[d];
+  A.pos.inv_h = 1.0 / p->grid.h;
+  A.h = p->grid.h;
+  A.v = (const double*)v;
+  A.out = (double*)out;
+  A.epart = p->epart;
+  A.status = p->dstatus;
+  return A;
+}
+
+template <typename Real, bool kEnergy, bool kAdj, bool kParams>
+ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
+              void* out, cudaStream_t s) {
+  if (p->E == 0) return IB_OK;
+  FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
+  const int threads = 128;
+  const int blocks = (p->E + threads - 1) / threads;
+  k_fe<Real, double, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+}  // namespace
+
+ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
+                          void* out, bool energy, cudaStream_t s) {
+  if (p->precision == IB_FP64)
+    return energy ? run<double, true, false, false>(p, mt, xa, off, nullptr, out, s)
+                  : run<double, false, false, false>(p, mt, xa, off, nullptr, out, s);
+  return energy ? run<float, true, false, false>(p, mt, xa, off, nullptr, out, s)
+                : run<float, false, false, false>(p, mt, xa, off, nullptr, out, s);
+}
+
+ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
+                              const void* v, void* out, bool params, cudaStream_t s) {
+  if (p->precision == IB_FP64)
+    return params ? run<double, false, true, true>(p, mt, xa, off, v, out, s)
+                  : run<double, false, true, false>(p, mt, xa, off, v, out, s);
+  return params ? run<float, false, true, true>(p, mt, xa, off, v, out, s)
+                : run<float, false, true, false>(p, mt, xa, off, v, out, s);
+}
+
+ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
+  if (p->E == 0) {
+    cudaMemsetAsync(p->ered, 0, sizeof(double) * 9 * IB_MAX_MATERIALS, s);
+    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+  }
+  k_reduce_parts<<<n_mats * nvals, 256, 0, s>>>(p->epart, p->mat_id, p->E, nvals, p->ered);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+}  // namespace ibfe

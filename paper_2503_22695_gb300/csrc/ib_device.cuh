@@ -1,0 +1,151 @@
+// Device helpers: trilinear-hex Gauss tables, the 4-point delta weights and
+// position loading.  Shared by the kernels of libibfe (not by the oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ib_internal.cuh"
+
+namespace ibfe {
+
+// ---------------------------------------------------------------------------
+// Trilinear hexahedron at the 2x2x2 Gauss points (+-1/sqrt(3), unit weights).
+// Corner a has signs c_a in VTK order; Gauss point q = b0 + 2 b1 + 4 b2 has
+// signs s_q = 2 b - 1.  Per axis the linear factor (1 + c xi)/2 at xi = s g is
+// kA = (1+g)/2 when c == s and kB = (1-g)/2 otherwise; N_a(xi_q) is the
+// product of the three factors and dN_a/dxi_d = (c_ad / 2) * (product of the
+// other two factors).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int corner_sign(int a, int d) {
+  // VTK: 0(-,-,-) 1(+,-,-) 2(+,+,-) 3(-,+,-) 4(-,-,+) 5(+,-,+) 6(+,+,+) 7(-,+,+)
+  return d == 0 ? ((a & 3) == 1 || (a & 3) == 2 ? 1 : -1)
+                : (d == 1 ? ((a & 3) >= 2 ? 1 : -1) : (a >= 4 ? 1 : -1));
+}
+__host__ __device__ constexpr int gauss_sign(int q, int d) { return ((q >> d) & 1) ? 1 : -1; }
+constexpr double kG = 0.57735026918962576451;  // 1/sqrt(3)
+constexpr double kA = 0.5 * (1.0 + kG);
+constexpr double kB = 0.5 * (1.0 - kG);
+__host__ __device__ constexpr double lin_factor(int a, int q, int d) {
+  return corner_sign(a, d) == gauss_sign(q, d) ? kA : kB;
+}
+__host__ __device__ constexpr double shapeN(int a, int q) {
+  return lin_factor(a, q, 0) * lin_factor(a, q, 1) * lin_factor(a, q, 2);
+}
+__host__ __device__ constexpr double shape_dxi(int a, int q, int d) {
+  return 0.5 * corner_sign(a, d) *
+         (d == 0 ? lin_factor(a, q, 1) * lin_factor(a, q, 2)
+                 : (d == 1 ? lin_factor(a, q, 0) * lin_factor(a, q, 2)
+                           : lin_factor(a, q, 0) * lin_factor(a, q, 1)));
+}
+
+// ---------------------------------------------------------------------------
+// 4-point delta weights.  For a point at t (grid units, staggering removed)
+// with theta = t - floor(t) in [0,1), the four faces floor(t)-1 .. floor(t)+2
+// are at distances r = theta+1, theta, theta-1, theta-2.  With
+// q = sqrt(1 + 4 theta (1 - theta)) both branches of the kernel reduce to
+//   phi(theta+1) = (3 - 2 theta - q)/8      phi(theta)   = (3 - 2 theta + q)/8
+//   phi(theta-1) = (1 + 2 theta + q)/8      phi(theta-2) = (1 + 2 theta - q)/8
+// evaluated here with q - 1 = 4 theta (1-theta) / (1 + q) so that the two
+// weights that vanish at the support edge carry no cancellation error.
+// Derivatives d phi/dr at the same r, with g = (2 - 4 theta)/q:
+//   (-2 - g)/8, (-2 + g)/8, (2 + g)/8, (2 - g)/8.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__device__ __forceinline__ void delta_weights(Real th, Real w[4]) {
+  Real om = Real(1) - th;
+  Real p = Real(4) * th * om;
+  Real q = sqrt(Real(1) + p);
+  Real qm1 = p / (Real(1) + q);
+  w[0] = (Real(2) * om - qm1) * Real(0.125);
+  w[1] = (Real(2) * om + Real(2) + qm1) * Real(0.125);
+  w[2] = (Real(2) * th + Real(2) + qm1) * Real(0.125);
+  w[3] = (Real(2) * th - qm1) * Real(0.125);
+}
+
+template <typename Real>
+__device__ __forceinline__ void delta_weights_d(Real th, Real w[4], Real dw[4]) {
+  Real om = Real(1) - th;
+  Real p = Real(4) * th * om;
+  Real q = sqrt(Real(1) + p);
+  Real qm1 = p / (Real(1) + q);
+  w[0] = (Real(2) * om - qm1) * Real(0.125);
+  w[1] = (Real(2) * om + Real(2) + qm1) * Real(0.125);
+  w[2] = (Real(2) * th + Real(2) + qm1) * Real(0.125);
+  w[3] = (Real(2) * th - qm1) * Real(0.125);
+  Real g = (Real(2) - Real(4) * th) / q;
+  dw[0] = (Real(-2) - g) * Real(0.125);
+  dw[1] = (Real(-2) + g) * Real(0.125);
+  dw[2] = (Real(2) + g) * Real(0.125);
+  dw[3] = (Real(2) - g) * Real(0.125);
+}
+
+// Stencil start and fraction along one axis for a point with in-cell offset
+// `off` in [0,1) and staggering s (0 or 1/2): t = cell + off - s,
+// floor(t) = cell + (off < s ? -1 : 0); the first face is floor(t) - 1.
+template <typename Real>
+__device__ __forceinline__ int stencil_axis(Real off, bool half, Real& theta) {
+  if (!half) {
+    theta = off;
+    return -1;
+  }
+  if (off < Real(0.5)) {
+    theta = off + Real(0.5);
+    return -2;
+  }
+  theta = off - Real(0.5);
+  return -1;
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ int32_t pack_cell(int x, int y, int z) {
+  return x | (y << kPackBits) | (z << (2 * kPackBits));
+}
+__device__ __forceinline__ void unpack_cell(int32_t p, int& x, int& y, int& z) {
+  x = p & ((1 << kPackBits) - 1);
+  y = (p >> kPackBits) & ((1 << kPackBits) - 1);
+  z = (p >> (2 * kPackBits)) & ((1 << kPackBits) - 1);
+}
+
+// Node position as (integer cell, offset in cell units).  FP32 split plans
+// read the stored pair; FP64 plans derive it from the absolute coordinate.
+template <typename Real>
+struct NodeLoader;
+
+template <>
+struct NodeLoader<float> {
+  const int32_t* cell;
+  const float* off;
+  int64_t N;
+  __device__ __forceinline__ void load(int node, int c[3], float o[3]) const {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c[d] = __ldg(cell + d * N + node);
+      o[d] = __ldg(off + d * N + node);
+    }
+  }
+};
+
+template <>
+struct NodeLoader<double> {
+  const double* x64;
+  int64_t N;
+  double origin[3];
+  double inv_h;
+  __device__ __forceinline__ void load(int node, int c[3], double o[3]) const {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double t = (__ldg(x64 + d * N + node) - origin[d]) * inv_h;
+      double f = floor(t);
+      c[d] = (int)f;
+      o[d] = t - f;
+    }
+  }
+};
+
+__device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }
+
+}  // namespace ibfe

@@ -1,0 +1,135 @@
+// Internal declarations shared by the CUDA translation units of libibfe.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ibfe.h"
+
+namespace ibfe {
+
+constexpr int kTile = 8;            // Eulerian tile edge (cells) of the spread kernel
+constexpr int kTileShift = 3;
+constexpr int kSpreadWarps = 8;     // warps (private accumulators) per spread CTA
+constexpr int kPackBits = 10;       // packed wrapped cell: x | y << 10 | z << 20
+
+// Device-side status bits latched by kernels (read by ib_plan_sync_status).
+constexpr int kStatNonfinite = 1;
+constexpr int kStatInverted = 2;
+
+// Material table passed by value to kernels.
+struct MatTable {
+  int n;
+  int model[IB_MAX_MATERIALS];
+  double p[IB_MAX_MATERIALS][9];
+};
+
+// Grid description used on the device.
+struct GridDev {
+  int n[3];
+  int nt[3];          // tiles per dimension
+  double h;
+  double origin[3];
+};
+
+template <typename Real>
+struct PosDev {
+  const int32_t* cell;  // FP32 split
+  const float* off;
+  const double* x64;    // FP64
+};
+
+struct ib_plan_impl;
+
+}  // namespace ibfe
+
+// The opaque plan.
+struct ib_plan {
+  int precision;         // ib_precision
+  int N, E;
+  int64_t Q;             // Gauss points = 8 E
+  ibfe::GridDev grid;
+  int ntiles;
+  const int32_t* conn;
+  const void* X;
+  const void* fibres;
+  const int32_t* mat_id;
+  int max_mat_id;        // largest material id used by the mesh
+  size_t rsize;          // sizeof(Real)
+
+  // static derived data
+  int32_t* inc_off;      // [N+1]
+  int32_t* inc_idx;      // [8E]: corner*E + e
+  void* mass;            // Real [N]
+  void* inv_mass;        // Real [N]
+  void* wj0;             // Real [8E] (q-major: q*E + e)
+
+  // workspace
+  void* elem_scratch;    // Real [24][E]
+  void* elem_scratch2;   // Real [24][E]
+  uint32_t* keys[2];     // [Q]
+  int32_t* vals[2];      // [Q]
+  int32_t* hist;         // radix histogram / offsets
+  int hist_blocks;
+  int32_t* tile_start;   // [ntiles]
+  int32_t* tile_end;     // [ntiles]
+  int32_t* q_cell;       // packed wrapped cell per Gauss point (unsorted, gq order)
+  void* q_off;           // Real [3][Q]
+  void* q_val;           // Real [3][Q]
+  int32_t* p_cell;       // sorted copies
+  void* p_off;           // Real [3][Q]
+  void* p_val;           // Real [3][Q]
+  int32_t* p_idx;        // [Q] original gq
+  void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
+  void* gq_b;            // Real [3][Q]
+  double* epart;         // [9][E] per-element partial sums
+  double* ered;          // [IB_MAX_MATERIALS*9] reduced sums
+  int* dstatus;          // device status word
+
+  // per-stage profiling (host side; events only while prof_on)
+  int prof_on;
+  cudaEvent_t* ev;       // [ev_cap] start/stop pairs
+  int* ev_stage;         // [ev_cap / 2]
+  int ev_cap, ev_used;
+  double prof_ms[IB_STAGE_COUNT];
+  int64_t prof_calls[IB_STAGE_COUNT];
+  int64_t prof_launches[IB_STAGE_COUNT];
+};
+
+namespace ibfe {
+
+// ----------------------------------------------------------------------------
+// host-side launchers (each file implements its group)
+// ----------------------------------------------------------------------------
+// fe_force.cu
+ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* x_cell_or_x64,
+                          const float* off, void* elem_out, bool energy, cudaStream_t s);
+ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell_or_x64,
+                              const float* off, const void* v, void* elem_out, bool params,
+                              cudaStream_t s);
+ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
+
+// assemble.cu
+ib_status launch_node_gather(ib_plan* p, const void* elem, const void* node_scale, void* out,
+                             cudaStream_t s);
+ib_status launch_elem_project(ib_plan* p, const void* gq_vals, void* elem_out, cudaStream_t s);
+ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
+
+// points.cu
+// Build Gauss points (position + carried value) and sort them by tile.
+// val_kind: 0 = no value, 1 = w j0 sum_a N_a V_a / m_a from nodal V.
+ib_status launch_points(ib_plan* p, const void* x_cell_or_x64, const float* off,
+                        const void* nodal, int val_kind, cudaStream_t s);
+ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s);
+
+// spread.cu
+ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s);
+
+// interp.cu
+// mode 0: out_a[gq] = w j0 * sum u prod phi (U^IB times w j0)
+// mode 1: out_a[gq] = w j0 * vscale * sum u prod phi,
+//         out_b[gq] = gscale * sum_c val_c * grad_chi(sum u^c prod phi)
+// mode 2: only out_b (gradient) as in mode 1.
+ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
+                               double gscale, cudaStream_t s);
+
+}  // namespace ibfe

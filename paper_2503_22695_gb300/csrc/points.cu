@@ -1,0 +1,333 @@
+// Gauss points of the structure as Lagrangian markers, binned by Eulerian tile.
+//
+// k_points evaluates, per element and Gauss point q (index gq = q*E + e):
+//   chi_q = sum_a N_a(xi_q) x_a          (split: integer cell + offset in [0,1))
+//   V_q   = w_q j0 sum_a N_a(xi_q) V_a / m_a   (optional carried value; for the
+//           spreading of Section 4.4 V = G, the lumped projection of the nodal
+//           forces onto the FE space)
+// and the key of the 8^3-cell Eulerian tile containing chi_q (periodically
+// wrapped).  The points are then ordered by a stable LSD radix sort on the
+// tile key (8-bit digits, per-block digit histograms, one exclusive scan,
+// stable in-block ranks from warp match masks), so equal keys keep gq order
+// and the sorted sequence -- hence every downstream summation order -- is
+// identical on every call.
+#include "ib_device.cuh"
+
+namespace ibfe {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortChunk = kSortThreads * kSortItems;
+
+template <typename Real>
+struct PtArgs {
+  int E;
+  int64_t N;
+  const int32_t* conn;
+  NodeLoader<Real> pos;
+  const Real* V;         // [3][N] or null
+  const Real* inv_mass;  // [N]
+  const Real* wj0;       // [8][E]
+  GridDev g;
+  int32_t* q_cell;
+  Real* q_off;           // [3][Q]
+  Real* q_val;           // [3][Q]
+  uint32_t* key;
+  int32_t* val;
+  int* status;
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.E) return;
+  const int E = A.E;
+  const int64_t Q = 8LL * E;
+  int c0[3];
+  Real o0[3];
+  Real dl[8][3];
+  Real Vn[8][3];
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int node = __ldg(A.conn + a * E + e);
+    int c[3];
+    Real o[3];
+    A.pos.load(node, c, o);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (!(o[d] >= Real(0) && o[d] < Real(1))) bad = true;
+    if (a == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        c0[d] = c[d];
+        o0[d] = o[d];
+        dl[0][d] = Real(0);
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dl[a][d] = Real(c[d] - c0[d]) + (o[d] - o0[d]);
+    }
+    if (A.V) {
+      const Real im = __ldg(A.inv_mass + node);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Vn[a][d] = __ldg(A.V + d * A.N + node) * im;
+    }
+  }
+  if (bad) {  // keep indices in range; the caller sees IB_ERR_NONFINITE
+    set_status(A.status, kStatNonfinite);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c0[d] = 0;
+      o0[d] = Real(0);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) dl[a][d] = Real(0);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t gq = (int64_t)q * E + e;
+    int cw[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Real s = Real(0);
+#pragma unroll
+      for (int a = 1; a < 8; ++a) s += Real(shapeN(a, q)) * dl[a][d];
+      Real t = o0[d] + s;
+      Real k = floor(t);
+      Real off = t - k;
+      if (off >= Real(1)) {  // rounding guard: keep the offset in [0,1)
+        off = Real(0);
+        k += Real(1);
+      }
+      cw[d] = wrap_idx(c0[d] + (int)k, A.g.n[d]);
+      A.q_off[d * Q + gq] = off;
+    }
+    A.q_cell[gq] = pack_cell(cw[0], cw[1], cw[2]);
+    A.key[gq] = (uint32_t)((cw[0] >> kTileShift) +
+                           A.g.nt[0] * ((cw[1] >> kTileShift) + A.g.nt[1] * (cw[2] >> kTileShift)));
+    A.val[gq] = (int32_t)gq;
+    if (A.V) {
+      const Real w = __ldg(A.wj0 + gq);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Real s = Real(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) s += Real(shapeN(a, q)) * Vn[a][d];
+        A.q_val[d * Q + gq] = w * s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// radix sort pieces
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ key,
+                                                             int64_t Q, int shift, int nblk,
+                                                             int32_t* __restrict__ hist) {
+  __shared__ int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk;
+  for (int i = threadIdx.x; i < kSortChunk; i += kSortThreads) {
+    const int64_t k = b0 + i;
+    if (k < Q) atomicAdd(&cnt[(__ldg(key + k) >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// In-place exclusive scan of M ints by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan(int32_t* __restrict__ a, int M) {
+  __shared__ int sums[1024];
+  const int per = (M + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(M, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += a[i];
+  sums[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int v = threadIdx.x >= off ? sums[threadIdx.x - off] : 0;
+    __syncthreads();
+    sums[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = sums[threadIdx.x] - s;  // exclusive prefix of this thread's segment
+  for (int i = b; i < e; ++i) {
+    const int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t Q, int shift,
+    int nblk, const int32_t* __restrict__ offs, uint32_t* __restrict__ kout,
+    int32_t* __restrict__ vout) {
+  __shared__ int base[256];
+  __shared__ int wcnt[kSortThreads / 32][256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  base[t] = offs[t * nblk + blockIdx.x];
+  for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
+  __syncthreads();
+  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = b0 + (int64_t)r * kSortThreads + t;
+    const bool valid = i < Q;
+    uint32_t k = 0;
+    int32_t v = 0;
+    int d = 256 + lane;  // unique sentinel for lanes without an item
+    if (valid) {
+      k = kin[i];
+      v = vin[i];
+      d = (k >> shift) & 255;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int pre = 0;
+      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
+      const int pos = base[d] + pre + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    int tot = 0;
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      tot += wcnt[w][t];
+      wcnt[w][t] = 0;
+    }
+    base[t] += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_tile_bounds(const uint32_t* __restrict__ key, int64_t Q,
+                              int32_t* __restrict__ start, int32_t* __restrict__ end) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const uint32_t k = key[i];
+  if (i == 0 || key[i - 1] != k) start[k] = (int32_t)i;
+  if (i == Q - 1 || key[i + 1] != k) end[k] = (int32_t)(i + 1);
+}
+
+template <typename Real>
+__global__ void k_permute(const int32_t* __restrict__ order, int64_t Q,
+                          const int32_t* __restrict__ q_cell, const Real* __restrict__ q_off,
+                          const Real* __restrict__ q_val, int32_t* __restrict__ p_cell,
+                          Real* __restrict__ p_off, Real* __restrict__ p_val,
+                          int32_t* __restrict__ p_idx, bool with_val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const int32_t g = order[i];
+  p_idx[i] = g;
+  p_cell[i] = __ldg(q_cell + g);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p_off[d * Q + i] = __ldg(q_off + d * Q + g);
+  if (with_val) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p_val[d * Q + i] = __ldg(q_val + d * Q + g);
+  }
+}
+
+template <typename Real>
+ib_status points_t(ib_plan* p, const void* xa, const float* off, const void* nodal,
+                   cudaStream_t s);
+
+template <>
+ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const void* nodal,
+                          cudaStream_t s) {
+  PtArgs<float> A;
+  A.E = p->E;
+  A.N = p->N;
+  A.conn = p->conn;
+  A.pos.cell = (const int32_t*)xa;
+  A.pos.off = off;
+  A.pos.N = p->N;
+  A.V = (const float*)nodal;
+  A.inv_mass = (const float*)p->inv_mass;
+  A.wj0 = (const float*)p->wj0;
+  A.g = p->grid;
+  A.q_cell = p->q_cell;
+  A.q_off = (float*)p->q_off;
+  A.q_val = (float*)p->q_val;
+  A.key = p->keys[0];
+  A.val = p->vals[0];
+  A.status = p->dstatus;
+  k_points<float><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+template <>
+ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void* nodal,
+                           cudaStream_t s) {
+  PtArgs<double> A;
+  A.E = p->E;
+  A.N = p->N;
+  A.conn = p->conn;
+  A.pos.x64 = (const double*)xa;
+  A.pos.N = p->N;
+  for (int d = 0; d < 3; ++d) A.pos.origin[d] = p->grid.origin[d];
+  A.pos.inv_h = 1.0 / p->grid.h;
+  A.V = (const double*)nodal;
+  A.inv_mass = (const double*)p->inv_mass;
+  A.wj0 = (const double*)p->wj0;
+  A.g = p->grid;
+  A.q_cell = p->q_cell;
+  A.q_off = (double*)p->q_off;
+  A.q_val = (double*)p->q_val;
+  A.key = p->keys[0];
+  A.val = p->vals[0];
+  A.status = p->dstatus;
+  k_points<double><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+}  // namespace
+
+ib_status launch_points(ib_plan* p, const void* xa, const float* off, const void* nodal,
+                        int val_kind, cudaStream_t s) {
+  if (p->E == 0) return IB_OK;
+  const void* V = val_kind ? nodal : nullptr;
+  return p->precision == IB_FP64 ? points_t<double>(p, xa, off, V, s)
+                                 : points_t<float>(p, xa, off, V, s);
+}
+
+ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
+  const int64_t Q = p->Q;
+  cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
+  cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
+  if (Q == 0) return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+  int bits = 1;
+  while ((1 << bits) < p->ntiles) ++bits;
+  const int nblk = p->hist_blocks;
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], Q, shift, nblk, p->hist);
+    k_scan<<<1, 1024, 0, s>>>(p->hist, 256 * nblk);
+    k_radix_scatter<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], p->vals[cur], Q, shift, nblk,
+                                                  p->hist, p->keys[cur ^ 1], p->vals[cur ^ 1]);
+    cur ^= 1;
+  }
+  const int tb = 256;
+  const int nb = (int)((Q + tb - 1) / tb);
+  k_tile_bounds<<<nb, tb, 0, s>>>(p->keys[cur], Q, p->tile_start, p->tile_end);
+  if (p->precision == IB_FP64)
+    k_permute<double><<<nb, tb, 0, s>>>(p->vals[cur], Q, p->q_cell, (const double*)p->q_off,
+                                        (const double*)p->q_val, p->p_cell, (double*)p->p_off,
+                                        (double*)p->p_val, p->p_idx, with_val);
+  else
+    k_permute<float><<<nb, tb, 0, s>>>(p->vals[cur], Q, p->q_cell, (const float*)p->q_off,
+                                       (const float*)p->q_val, p->p_cell, (float*)p->p_off,
+                                       (float*)p->p_val, p->p_idx, with_val);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+int sort_hist_blocks(int64_t Q) { return (int)((Q + kSortChunk - 1) / kSortChunk); }
+
+}  // namespace ibfe

@@ -1,0 +1,397 @@
+"""Thin Python binding of libibfe (include/ibfe.h) over ctypes.
+
+Argument marshalling only: every operator runs in the CUDA library.  Arrays
+are torch tensors on the current CUDA device (PyTorch provides device memory
+and streams); every call is issued on torch's current stream.  The binding
+never falls back to another implementation: if the library cannot be loaded
+the import fails.
+
+Names follow the C ABI: ib_plan_create, ib_fe_force, ib_spread, ib_interp,
+ib_forward, ib_spread_adj, ib_interp_adj, ib_fe_force_adj, ib_lumped_mass,
+ib_plan_sync_status, ib_plan_destroy, ib_status_str, ib_version.  The
+torch.autograd.Function classes FEForce, Spread and Interp route their
+backward passes to the adjoint entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibfe.so")
+
+IB_OK, IB_ERR_INVALID_ARG, IB_ERR_CUDA, IB_ERR_NONFINITE = 0, 1, 2, 3
+IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 7
+IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO = 0, 1, 2
+IB_FP32_SPLIT, IB_FP64 = 0, 1
+IB_MAX_MATERIALS = 8
+STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
+N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9}
+
+
+class IBError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ib_status_str(code)} (status {code})")
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_elems", C.c_int32), ("conn", C.c_void_p),
+                ("X", C.c_void_p), ("fibres", C.c_void_p), ("mat_id", C.c_void_p)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("origin", C.c_double * 3)]
+
+
+class _Pos(C.Structure):
+    _fields_ = [("cell", C.c_void_p), ("off", C.c_void_p), ("x64", C.c_void_p)]
+
+
+class _Mat(C.Structure):
+    _fields_ = [("model", C.c_int32), ("n_params", C.c_int32), ("params", C.c_double * 9)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libibfe.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, dp = C.c_void_p, C.c_int32, C.POINTER(C.c_double)
+    sigs = {
+        "ib_plan_create": [C.POINTER(_Mesh), C.POINTER(_Grid), i32, vp, C.POINTER(vp)],
+        "ib_plan_destroy": [vp],
+        "ib_lumped_mass": [vp, vp, vp],
+        "ib_fe_force": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, dp, vp],
+        "ib_spread": [vp, C.POINTER(_Pos), vp, vp, vp],
+        "ib_interp": [vp, C.POINTER(_Pos), vp, vp, vp],
+        "ib_forward": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, vp, vp, vp],
+        "ib_spread_adj": [vp, C.POINTER(_Pos), vp, vp, vp, vp, vp],
+        "ib_interp_adj": [vp, C.POINTER(_Pos), vp, vp, vp, vp, vp],
+        "ib_fe_force_adj": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, dp, vp],
+        "ib_plan_sync_status": [vp, vp],
+        "ib_plan_set_profiling": [vp, i32],
+        "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.ib_status_str.argtypes = [C.c_int]
+    L.ib_status_str.restype = C.c_char_p
+    L.ib_version.argtypes = []
+    L.ib_version.restype = C.c_int32
+    return L
+
+
+_lib = _load()
+
+
+def ib_status_str(code: int) -> str:
+    return _lib.ib_status_str(int(code)).decode()
+
+
+def ib_version() -> int:
+    return int(_lib.ib_version())
+
+
+def _chk(code: int, what: str):
+    if code != IB_OK:
+        raise IBError(code, what)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Material:
+    model: int
+    params: Sequence[float]
+
+
+def _mats(mats: Sequence[Material]):
+    arr = (_Mat * len(mats))()
+    for i, m in enumerate(mats):
+        arr[i].model = int(m.model)
+        arr[i].n_params = len(m.params)
+        for k, v in enumerate(m.params):
+            arr[i].params[k] = float(v)
+    return arr, len(mats)
+
+
+class Pos:
+    """Node positions: split (cell int32 [3][N] + off float32 [3][N]) or x64 [3][N]."""
+
+    def __init__(self, cell: torch.Tensor = None, off: torch.Tensor = None,
+                 x64: torch.Tensor = None):
+        self.cell, self.off, self.x64 = cell, off, x64
+        self._s = _Pos(None if cell is None else cell.data_ptr(),
+                       None if off is None else off.data_ptr(),
+                       None if x64 is None else x64.data_ptr())
+
+
+class Plan:
+    """An ib_plan: one hexahedral mesh on one periodic MAC grid."""
+
+    def __init__(self, conn: torch.Tensor, X: torch.Tensor, n, h: float, origin=(0.0, 0.0, 0.0),
+                 fibres: torch.Tensor = None, mat_id: torch.Tensor = None,
+                 precision: int = IB_FP32_SPLIT):
+        self.dtype = torch.float64 if precision == IB_FP64 else torch.float32
+        _check(conn, torch.int32, (8, -1), "conn")
+        _check(X, self.dtype, (3, -1), "X")
+        if fibres is not None:
+            _check(fibres, self.dtype, (6, conn.shape[1]), "fibres")
+        if mat_id is not None:
+            _check(mat_id, torch.int32, (conn.shape[1],), "mat_id")
+        # the plan keeps these pointers: hold the tensors
+        self._keep = (conn, X, fibres, mat_id)
+        self.N, self.E = int(X.shape[1]), int(conn.shape[1])
+        self.n, self.h, self.origin = tuple(int(v) for v in n), float(h), tuple(origin)
+        self.precision = precision
+        mesh = _Mesh(self.N, self.E, conn.data_ptr(), X.data_ptr(),
+                     None if fibres is None else fibres.data_ptr(),
+                     None if mat_id is None else mat_id.data_ptr())
+        grid = _Grid((C.c_int32 * 3)(*self.n), self.h, (C.c_double * 3)(*origin))
+        out = C.c_void_p()
+        _chk(_lib.ib_plan_create(C.byref(mesh), C.byref(grid), precision, _stream(),
+                                 C.byref(out)), "ib_plan_create")
+        self._h = out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def grid_shape(self):
+        n0, n1, n2 = self.n
+        return (3, n2, n1, n0)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            try:
+                _lib.ib_plan_destroy(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def _check(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if len(shape) != t.dim() or any(s != -1 and s != d for s, d in zip(shape, t.shape)):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+
+
+def _pos(plan: Plan, x: Pos):
+    if plan.precision == IB_FP64:
+        _check(x.x64, torch.float64, (3, plan.N), "x64")
+    else:
+        _check(x.cell, torch.int32, (3, plan.N), "cell")
+        _check(x.off, torch.float32, (3, plan.N), "off")
+    return x._s
+
+
+def _out(t, plan, shape, name):
+    if t is None:
+        return torch.empty(shape, dtype=plan.dtype, device="cuda")
+    _check(t, plan.dtype, shape, name)
+    return t
+
+
+def ib_plan_create(conn, X, n, h, origin=(0.0, 0.0, 0.0), fibres=None, mat_id=None,
+                   precision=IB_FP32_SPLIT) -> Plan:
+    return Plan(conn, X, n, h, origin, fibres, mat_id, precision)
+
+
+def ib_plan_destroy(plan: Plan):
+    if plan._h:
+        _chk(_lib.ib_plan_destroy(plan._h), "ib_plan_destroy")
+        plan._h = None
+
+
+def ib_lumped_mass(plan: Plan, mass=None):
+    mass = _out(mass, plan, (plan.N,), "mass")
+    _chk(_lib.ib_lumped_mass(plan.handle, _ptr(mass), _stream()), "ib_lumped_mass")
+    return mass
+
+
+def ib_fe_force(plan: Plan, mats, x: Pos, G=None, energy: bool = False):
+    G = _out(G, plan, (3, plan.N), "G")
+    arr, nm = _mats(mats)
+    en = C.c_double(0.0)
+    _chk(_lib.ib_fe_force(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(G),
+                          C.byref(en) if energy else None, _stream()), "ib_fe_force")
+    return (G, en.value) if energy else G
+
+
+def ib_spread(plan: Plan, x: Pos, G, f=None):
+    _check(G, plan.dtype, (3, plan.N), "G")
+    f = _out(f, plan, plan.grid_shape(), "f")
+    _chk(_lib.ib_spread(plan.handle, C.byref(_pos(plan, x)), _ptr(G), _ptr(f), _stream()),
+         "ib_spread")
+    return f
+
+
+def ib_interp(plan: Plan, x: Pos, u, U=None):
+    _check(u, plan.dtype, plan.grid_shape(), "u")
+    U = _out(U, plan, (3, plan.N), "U")
+    _chk(_lib.ib_interp(plan.handle, C.byref(_pos(plan, x)), _ptr(u), _ptr(U), _stream()),
+         "ib_interp")
+    return U
+
+
+def ib_forward(plan: Plan, mats, x: Pos, u, G=None, f=None, U=None):
+    _check(u, plan.dtype, plan.grid_shape(), "u")
+    G = _out(G, plan, (3, plan.N), "G")
+    f = _out(f, plan, plan.grid_shape(), "f")
+    U = _out(U, plan, (3, plan.N), "U")
+    arr, nm = _mats(mats)
+    _chk(_lib.ib_forward(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(u), _ptr(G),
+                         _ptr(f), _ptr(U), _stream()), "ib_forward")
+    return G, f, U
+
+
+def ib_spread_adj(plan: Plan, x: Pos, G, gf, want_gx: bool = True, gG=None, gx=None):
+    _check(G, plan.dtype, (3, plan.N), "G")
+    _check(gf, plan.dtype, plan.grid_shape(), "gf")
+    gG = _out(gG, plan, (3, plan.N), "gG")
+    gx = _out(gx, plan, (3, plan.N), "gx") if want_gx else None
+    _chk(_lib.ib_spread_adj(plan.handle, C.byref(_pos(plan, x)), _ptr(G), _ptr(gf), _ptr(gG),
+                            _ptr(gx), _stream()), "ib_spread_adj")
+    return gG, gx
+
+
+def ib_interp_adj(plan: Plan, x: Pos, u, gU, want_gx: bool = True, gu=None, gx=None):
+    _check(gU, plan.dtype, (3, plan.N), "gU")
+    if want_gx:
+        _check(u, plan.dtype, plan.grid_shape(), "u")
+    gu = _out(gu, plan, plan.grid_shape(), "gu")
+    gx = _out(gx, plan, (3, plan.N), "gx") if want_gx else None
+    _chk(_lib.ib_interp_adj(plan.handle, C.byref(_pos(plan, x)), _ptr(u if want_gx else None),
+                            _ptr(gU), _ptr(gu), _ptr(gx), _stream()), "ib_interp_adj")
+    return gu, gx
+
+
+def ib_fe_force_adj(plan: Plan, mats, x: Pos, v, want_params: bool = True, Hv=None):
+    _check(v, plan.dtype, (3, plan.N), "v")
+    Hv = _out(Hv, plan, (3, plan.N), "Hv")
+    arr, nm = _mats(mats)
+    gp = (C.c_double * (9 * nm))()
+    _chk(_lib.ib_fe_force_adj(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(v), _ptr(Hv),
+                              gp if want_params else None, _stream()), "ib_fe_force_adj")
+    if not want_params:
+        return Hv, None
+    g = torch.tensor(list(gp), dtype=torch.float64).reshape(nm, 9)
+    return Hv, g
+
+
+def ib_plan_sync_status(plan: Plan) -> int:
+    return int(_lib.ib_plan_sync_status(plan.handle, _stream()))
+
+
+def ib_plan_set_profiling(plan: Plan, enable: bool):
+    _chk(_lib.ib_plan_set_profiling(plan.handle, 1 if enable else 0), "ib_plan_set_profiling")
+
+
+def ib_plan_profile(plan: Plan, reset: bool = True):
+    """{stage: (milliseconds, calls, kernel launches)} since the last reset."""
+    n = len(STAGES)
+    ms = (C.c_double * n)()
+    calls = (C.c_int64 * n)()
+    launches = (C.c_int64 * n)()
+    _chk(_lib.ib_plan_profile(plan.handle, _stream(), ms, calls, launches, 1 if reset else 0),
+         "ib_plan_profile")
+    return {s: (ms[i], int(calls[i]), int(launches[i])) for i, s in enumerate(STAGES)}
+
+
+# ---------------------------------------------------------------------------
+# autograd: positions enter as the split offset `off` (x = origin + (cell+off) h,
+# so dL/doff = h dL/dx); material parameters as a float64 CPU tensor [n_mats][9].
+# ---------------------------------------------------------------------------
+
+def _mats_from(models, params: torch.Tensor):
+    return [Material(m, params[i, :N_PARAMS[m]].tolist()) for i, m in enumerate(models)]
+
+
+class FEForce(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, models, cell, off, params):
+        x = Pos(cell=cell, off=off.detach())
+        G = ib_fe_force(plan, _mats_from(models, params.detach()), x)
+        ctx.plan, ctx.models = plan, models
+        ctx.save_for_backward(cell, off, params)
+        return G
+
+    @staticmethod
+    def backward(ctx, gG):
+        cell, off, params = ctx.saved_tensors
+        plan = ctx.plan
+        x = Pos(cell=cell, off=off.detach())
+        Hv, gp = ib_fe_force_adj(plan, _mats_from(ctx.models, params.detach()), x,
+                                 gG.contiguous())
+        gp = gp.clone()
+        for i, m in enumerate(ctx.models):
+            gp[i, N_PARAMS[m]:] = 0
+        return None, None, None, Hv * plan.h, gp
+
+
+class Spread(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, cell, off, G):
+        x = Pos(cell=cell, off=off.detach())
+        f = ib_spread(plan, x, G.detach().contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(cell, off, G)
+        return f
+
+    @staticmethod
+    def backward(ctx, gf):
+        cell, off, G = ctx.saved_tensors
+        x = Pos(cell=cell, off=off.detach())
+        gG, gx = ib_spread_adj(ctx.plan, x, G.detach().contiguous(), gf.contiguous())
+        return None, None, gx * ctx.plan.h, gG
+
+
+class Interp(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, cell, off, u):
+        x = Pos(cell=cell, off=off.detach())
+        U = ib_interp(plan, x, u.detach().contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(cell, off, u)
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        cell, off, u = ctx.saved_tensors
+        x = Pos(cell=cell, off=off.detach())
+        gu, gx = ib_interp_adj(ctx.plan, x, u.detach().contiguous(), gU.contiguous())
+        return None, None, gx * ctx.plan.h, gu
+
+
+class IBCoupling(torch.nn.Module):
+    """G = FE force(x; theta), f = spread(x, G), U = interp(x, u), differentiable in
+    the offsets, the material parameters and u."""
+
+    def __init__(self, plan: Plan, models):
+        super().__init__()
+        self.plan, self.models = plan, list(models)
+
+    def forward(self, cell, off, params, u):
+        G = FEForce.apply(self.plan, self.models, cell, off, params)
+        f = Spread.apply(self.plan, cell, off, G)
+        U = Interp.apply(self.plan, cell, off, u)
+        return G, f, U

@@ -1,0 +1,62 @@
+"""Shared helpers for the GPU parity tests: move a seeded Problem to the
+device and build the oracle's view of exactly the same values."""
+import numpy as np
+
+import oracle
+from paper_2503_22695_gb300 import inputs as I
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b.ravel())
+    return np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0)
+
+
+class Case:
+    """A problem on the GPU (through the C ABI) and in the oracle."""
+
+    def __init__(self, prob: I.Problem):
+        import torch
+        from paper_2503_22695_gb300 import ibfe
+        self.prob = prob
+        self.ibfe = ibfe
+        self.fp64 = prob.fp64
+        dt = torch.float64 if prob.fp64 else torch.float32
+        self.dt = dt
+        dev = "cuda"
+        self.conn = torch.from_numpy(prob.conn).to(dev)
+        self.X = torch.from_numpy(prob.X).to(dev, dt)
+        self.fib = torch.from_numpy(prob.fibres).to(dev, dt)
+        self.mat_id = torch.from_numpy(prob.mat_id).to(dev)
+        g = prob.grid
+        self.plan = ibfe.Plan(self.conn, self.X, g.n, g.h, g.origin, fibres=self.fib,
+                              mat_id=self.mat_id,
+                              precision=ibfe.IB_FP64 if prob.fp64 else ibfe.IB_FP32_SPLIT)
+        if prob.fp64:
+            self.x_np = prob.x.copy()
+            self.pos = ibfe.Pos(x64=torch.from_numpy(self.x_np).to(dev))
+        else:
+            self.cell = torch.from_numpy(prob.cell).to(dev)
+            self.off = torch.from_numpy(prob.off).to(dev)
+            self.pos = ibfe.Pos(cell=self.cell, off=self.off)
+            self.x_np = I.from_split(prob.cell, prob.off, g)
+        self.mats = [ibfe.Material(m.model, m.params) for m in prob.materials]
+        self.u = torch.from_numpy(prob.u).to(dev, dt)
+        # oracle sees the device values widened exactly to float64
+        self.orc = oracle.Model(grid=g, conn=prob.conn, X=prob.X.astype(np.float64),
+                                fibres=prob.fibres.astype(np.float64), mat_id=prob.mat_id,
+                                materials=prob.materials)
+        self.u_np = prob.u.astype(np.float64)
+
+    def to_dev(self, a):
+        import torch
+        return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", self.dt)
+
+    def rounded(self, a):
+        """Round an oracle array to the device precision (the value both sides see)."""
+        return np.asarray(a).astype(np.float64 if self.fp64 else np.float32).astype(np.float64)
+
+
+def np_(t):
+    return t.detach().double().cpu().numpy()

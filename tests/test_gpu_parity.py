@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Tolerances (relative L2 over each output):
+  FP32 split-precision plans -- nodal force 1e-5, spread force 1e-5,
+  interpolated velocity 1e-6 (the stated accuracy targets); adjoint outputs
+  2e-5 (their arithmetic is the forward one plus a derivative weight, see the
+  design notes).
+  FP64 plans -- 1e-12 for every output.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_22695_gb300 import inputs as I
+
+from helpers import Case, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = dict(G=1e-5, f=1e-5, U=1e-6, adj=2e-5)
+TOL64 = 1e-12
+
+
+def tol(case, key):
+    return TOL64 if case.fp64 else TOL32[key]
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        if name == "block64":
+            p = I.block_problem()                      # plain FP64, 32^3
+        elif name == "block32":
+            p = I.block_problem(fp64=False)            # same block, FP32 split
+        elif name == "seam32":
+            p = I.block_problem(seed=1001, fp64=False, centre=(0.01, 0.985, 0.5))
+        elif name == "seam64":
+            p = I.block_problem(seed=1002, fp64=True, centre=(0.99, 0.5, 0.012))
+        elif name == "shell128":
+            p = I.shell_problem()                      # 128^3 HO ventricle shell
+        elif name == "shell256":
+            p = I.shell_sheets_problem()               # 256^3 shell + two sheets
+        else:
+            raise KeyError(name)
+        _cache[name] = Case(p)
+    return _cache[name]
+
+
+SMALL = ["block64", "block32", "seam32", "seam64", "shell128"]
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fe_force_and_energy(name):
+    c = case(name)
+    G, en = c.ibfe.ib_fe_force(c.plan, c.mats, c.pos, energy=True)
+    Go, eno = c.orc.fe_force(c.x_np)
+    assert rel_l2(np_(G), Go) <= tol(c, "G")
+    assert en == pytest.approx(eno, rel=1e-10 if c.fp64 else 1e-5)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_spread(name):
+    c = case(name)
+    Go, _ = c.orc.fe_force(c.x_np)
+    G = c.rounded(Go)                        # the same nodal forces on both sides
+    f = c.ibfe.ib_spread(c.plan, c.pos, c.to_dev(G))
+    fo = c.orc.spread(c.x_np, G)
+    assert rel_l2(np_(f), fo) <= tol(c, "f")
+    # faces outside every stencil are exactly zero
+    assert np.all(np_(f)[fo == 0] == 0)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_interp(name):
+    c = case(name)
+    U = c.ibfe.ib_interp(c.plan, c.pos, c.u)
+    Uo = c.orc.interp(c.x_np, c.u_np)
+    assert rel_l2(np_(U), Uo) <= tol(c, "U")
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_forward_fused_matches_parts(name):
+    c = case(name)
+    G, f, U = c.ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)
+    G1 = c.ibfe.ib_fe_force(c.plan, c.mats, c.pos)
+    f1 = c.ibfe.ib_spread(c.plan, c.pos, G1)
+    U1 = c.ibfe.ib_interp(c.plan, c.pos, c.u)
+    assert np.array_equal(np_(G), np_(G1))
+    assert np.array_equal(np_(f), np_(f1))
+    assert np.array_equal(np_(U), np_(U1))
+    Go, _ = c.orc.fe_force(c.x_np)
+    assert rel_l2(np_(G), Go) <= tol(c, "G")
+    assert rel_l2(np_(f), c.orc.spread(c.x_np, Go)) <= tol(c, "f")
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_adjoint_identity_on_device(name):
+    # Section 4.4: h^3 sum f.u = sum G.U when both use one quadrature
+    c = case(name)
+    rng = np.random.default_rng(5)
+    G = c.rounded(rng.normal(size=(3, c.prob.n_nodes)))
+    f = np_(c.ibfe.ib_spread(c.plan, c.pos, c.to_dev(G)))
+    U = np_(c.ibfe.ib_interp(c.plan, c.pos, c.u))
+    lhs = c.prob.grid.h ** 3 * np.sum(f * c.u_np)
+    rhs = np.sum(G * U)
+    assert lhs == pytest.approx(rhs, rel=1e-11 if c.fp64 else 1e-5)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_spread_adjoint(name):
+    c = case(name)
+    rng = np.random.default_rng(6)
+    Go, _ = c.orc.fe_force(c.x_np)
+    G = c.rounded(Go)
+    gf = c.rounded(rng.normal(size=c.plan.grid_shape()))
+    gG, gx = c.ibfe.ib_spread_adj(c.plan, c.pos, c.to_dev(G), c.to_dev(gf))
+    gGo, gxo = c.orc.spread_adj(c.x_np, G, gf)
+    assert rel_l2(np_(gG), gGo) <= tol(c, "adj")
+    assert rel_l2(np_(gx), gxo) <= tol(c, "adj")
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_interp_adjoint(name):
+    c = case(name)
+    rng = np.random.default_rng(7)
+    gU = c.rounded(rng.normal(size=(3, c.prob.n_nodes)))
+    gu, gx = c.ibfe.ib_interp_adj(c.plan, c.pos, c.u, c.to_dev(gU))
+    guo, gxo = c.orc.interp_adj(c.x_np, c.u_np, gU)
+    assert rel_l2(np_(gu), guo) <= tol(c, "adj")
+    assert rel_l2(np_(gx), gxo) <= tol(c, "adj")
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fe_force_adjoint(name):
+    c = case(name)
+    rng = np.random.default_rng(8)
+    v = c.rounded(rng.normal(size=(3, c.prob.n_nodes)))
+    Hv, gp = c.ibfe.ib_fe_force_adj(c.plan, c.mats, c.pos, c.to_dev(v))
+    Hvo, gpo = c.orc.fe_force_adj(c.x_np, v)
+    assert rel_l2(np_(Hv), Hvo) <= tol(c, "adj")
+    for m, mat in enumerate(c.prob.materials):
+        k = I.N_PARAMS[mat.model]
+        assert rel_l2(gp[m, :k].numpy(), gpo[m, :k]) <= tol(c, "adj")
+
+
+def test_spread_bitwise_reproducible():
+    c = case("shell128")
+    Go, _ = c.orc.fe_force(c.x_np)
+    Gd = c.to_dev(c.rounded(Go))
+    f1 = np_(c.ibfe.ib_spread(c.plan, c.pos, Gd))
+    for _ in range(3):
+        f2 = np_(c.ibfe.ib_spread(c.plan, c.pos, Gd))
+        assert np.array_equal(f1, f2)
+    gU = c.to_dev(c.rounded(np.random.default_rng(1).normal(size=(3, c.prob.n_nodes))))
+    g1 = np_(c.ibfe.ib_interp_adj(c.plan, c.pos, c.u, gU)[0])
+    g2 = np_(c.ibfe.ib_interp_adj(c.plan, c.pos, c.u, gU)[0])
+    assert np.array_equal(g1, g2)
+
+
+# ---------------------------------------------------------------------------
+# full size: 256^3 grid, 172,800 elements, 1,382,400 Gauss points, launched
+# exactly as the benchmark launches it (ib_forward on the whole mesh)
+# ---------------------------------------------------------------------------
+
+def test_full_size_forward():
+    c = case("shell256")
+    G, f, U = c.ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)
+    Go, _ = c.orc.fe_force(c.x_np)
+    assert rel_l2(np_(G), Go) <= TOL32["G"]
+    Uo = c.orc.interp(c.x_np, c.u_np)
+    assert rel_l2(np_(U), Uo) <= TOL32["U"]
+    # spreading of the same (rounded) nodal forces, compared everywhere
+    G32 = c.rounded(Go)
+    f2 = np_(c.ibfe.ib_spread(c.plan, c.pos, c.to_dev(G32)))
+    fo = c.orc.spread(c.x_np, G32)
+    assert rel_l2(f2, fo) <= TOL32["f"]
+    # and, at sampled faces near the structure, against the brute-force sum
+    rng = np.random.default_rng(9)
+    nodes = rng.integers(0, c.prob.n_nodes, size=64)
+    n = c.prob.grid.n[0]
+    comp = rng.integers(0, 3, size=64)
+    idx = (c.prob.cell[:, nodes].T + rng.integers(-2, 3, size=(64, 3))) % n
+    bf = c.orc.spread_at(c.x_np, G32, comp, idx)
+    got = f2[comp, idx[:, 2], idx[:, 1], idx[:, 0]]
+    assert rel_l2(got, bf) <= TOL32["f"]
+
+
+def test_full_size_adjoints():
+    c = case("shell256")
+    rng = np.random.default_rng(10)
+    gU = c.rounded(rng.normal(size=(3, c.prob.n_nodes)))
+    gu, gx = c.ibfe.ib_interp_adj(c.plan, c.pos, c.u, c.to_dev(gU))
+    guo, gxo = c.orc.interp_adj(c.x_np, c.u_np, gU)
+    assert rel_l2(np_(gu), guo) <= TOL32["adj"]
+    assert rel_l2(np_(gx), gxo) <= TOL32["adj"]
+    v = c.rounded(rng.normal(size=(3, c.prob.n_nodes)))
+    Hv, gp = c.ibfe.ib_fe_force_adj(c.plan, c.mats, c.pos, c.to_dev(v))
+    Hvo, gpo = c.orc.fe_force_adj(c.x_np, v)
+    assert rel_l2(np_(Hv), Hvo) <= TOL32["adj"]
+    assert rel_l2(gp[0, :9].numpy(), gpo[0, :9]) <= TOL32["adj"]
+    assert rel_l2(gp[1, :4].numpy(), gpo[1, :4]) <= TOL32["adj"]
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_non_cubic_grid_at_maximum_extent():
+    # n0 at the 1024 limit; the block straddles the periodic seam in x
+    p = I.block_problem(seed=1010, n=16, blocks=(4, 3, 2), fp64=False, centre=(0.005, 0.5, 0.5))
+    h = 1.0 / 16
+    p.grid = I.Grid((1024, 16, 8), h, origin=(0.0, 0.0, 0.25))
+    p.cell, p.off = I.to_split(p.x, p.grid)
+    p.u = I.fourier_velocity(p.grid, 3, np.random.default_rng(3))
+    c = Case(p)
+    Go, _ = c.orc.fe_force(c.x_np)
+    G = c.rounded(Go)
+    f = np_(c.ibfe.ib_spread(c.plan, c.pos, c.to_dev(G)))
+    assert rel_l2(f, c.orc.spread(c.x_np, G)) <= TOL32["f"]
+    U = np_(c.ibfe.ib_interp(c.plan, c.pos, c.u))
+    assert rel_l2(U, c.orc.interp(c.x_np, c.u_np)) <= TOL32["U"]
+
+
+def test_empty_mesh():
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    conn = torch.zeros((8, 0), dtype=torch.int32, device="cuda")
+    X = torch.zeros((3, 5), dtype=torch.float32, device="cuda")
+    plan = ibfe.Plan(conn, X, (16, 16, 16), 1 / 16)
+    pos = ibfe.Pos(cell=torch.zeros((3, 5), dtype=torch.int32, device="cuda"),
+                   off=torch.zeros((3, 5), dtype=torch.float32, device="cuda"))
+    u = torch.ones((3, 16, 16, 16), device="cuda")
+    G, f, U = ibfe.ib_forward(plan, [ibfe.Material(0, (0.5, 100.0))], pos, u)
+    assert torch.count_nonzero(G) == 0 and torch.count_nonzero(f) == 0
+    assert torch.count_nonzero(U) == 0
+
+
+def test_unsupported_and_invalid_arguments():
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    c = case("block32")
+    with pytest.raises(ibfe.IBError) as e:
+        ibfe.Plan(c.conn, c.X, (36, 32, 32), 1 / 32)
+    assert e.value.code == ibfe.IB_ERR_UNSUPPORTED
+    with pytest.raises(ibfe.IBError) as e:   # wrong parameter count for the model
+        ibfe.ib_fe_force(c.plan, [ibfe.Material(ibfe.IB_HO, (1.0, 2.0))], c.pos)
+    assert e.value.code == ibfe.IB_ERR_INVALID_ARG
+    bad = c.conn.clone()
+    bad[0, 0] = c.prob.n_nodes + 5
+    with pytest.raises(ibfe.IBError) as e:
+        ibfe.Plan(bad, c.X, (32, 32, 32), 1 / 32)
+    assert e.value.code == ibfe.IB_ERR_INVALID_ARG
+    inv = c.conn.clone()
+    inv[[0, 1]] = inv[[1, 0]]               # mirror every element
+    with pytest.raises(ibfe.IBError) as e:
+        ibfe.Plan(inv, c.X, (32, 32, 32), 1 / 32)
+    assert e.value.code == ibfe.IB_ERR_INVERTED
+
+
+def test_nonfinite_positions_reported():
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    c = case("block32")
+    off = c.off.clone()
+    off[1, 7] = float("nan")
+    pos = ibfe.Pos(cell=c.cell, off=off)
+    assert ibfe.ib_plan_sync_status(c.plan) == ibfe.IB_OK
+    ibfe.ib_spread(c.plan, pos, torch.zeros((3, c.prob.n_nodes), device="cuda"))
+    assert ibfe.ib_plan_sync_status(c.plan) == ibfe.IB_ERR_NONFINITE
+    assert ibfe.ib_plan_sync_status(c.plan) == ibfe.IB_OK   # cleared
+
+
+# ---------------------------------------------------------------------------
+# autograd: the differentiation workload's loss, gradients in x and theta
+# ---------------------------------------------------------------------------
+
+def test_autograd_loss_gradient():
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    p = I.shell_problem(seed=4000, n=32, dims=(12, 8, 2), u_modes=3)
+    c = Case(p)
+    h3 = p.grid.h ** 3
+    params = torch.tensor([list(I.HO_DEFAULT)], dtype=torch.float64, requires_grad=True)
+    off = c.off.clone().requires_grad_(True)
+    u = c.u.clone().requires_grad_(True)
+    model = ibfe.IBCoupling(c.plan, [I.HO])
+    G, f, U = model(c.cell, off, params, u)
+    loss = (U.double() ** 2).sum() + torch.sqrt(h3 * (f.double() ** 2).sum())
+    loss.backward()
+    # oracle chain on the same inputs
+    o = c.orc
+    Go, _ = o.fe_force(c.x_np)
+    fo = o.spread(c.x_np, Go)
+    Uo = o.interp(c.x_np, c.u_np)
+    nf = math.sqrt(h3 * np.sum(fo * fo))
+    _, gx_i = o.interp_adj(c.x_np, c.u_np, 2 * Uo)
+    gG, gx_s = o.spread_adj(c.x_np, Go, h3 * fo / nf)
+    Hv, gth = o.fe_force_adj(c.x_np, gG)
+    gx = gx_i + gx_s + Hv
+    assert rel_l2(np_(off.grad), gx * p.grid.h) <= 1e-4
+    assert rel_l2(params.grad.numpy()[0], gth[0]) <= 1e-4
+    gu, _ = o.interp_adj(c.x_np, c.u_np, 2 * Uo, want_gx=False)
+    assert rel_l2(np_(u.grad), gu) <= 1e-4
