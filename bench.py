@@ -230,7 +230,10 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    prob = I.shell_sheets_problem(seed=3000 + 17 * rank)
+    if args.workload == "shell256":
+        prob = I.shell_sheets_problem(seed=3000 + 17 * rank)
+    else:   # smaller case for profiling captures: the 128^3 HO shell
+        prob = I.shell_problem(seed=2000 + 17 * rank)
     Q, E, N = prob.n_gauss, prob.n_elems, prob.n_nodes
     n = prob.grid.n[0]
     conn = torch.from_numpy(prob.conn).to(dev)
@@ -362,13 +365,19 @@ def run_ours(args):
                 "note": f"dominant stage is {dom}; spread shown as the HBM-defining kernel"}
 
     # cpu baseline (oracle, one core) and the support count for the bytes model
-    cpu_rate, reps, cpu_t, support = oracle_forward_rate(prob)
+    if args.no_cpu_baseline:
+        cpu_rate, reps, cpu_t, support = None, 0, 0.0, 0
+    else:
+        cpu_rate, reps, cpu_t, support = oracle_forward_rate(prob)
     b_force = 56.0 * E + 52.0 * N
     b_interp = 4.0 * support + 12.0 * N
     b_fwd = b_force + spread_bytes + b_interp
     fwd_gbs = b_fwd / (t_fwd * 1e-3) / 1e9
     launches = sum(v[2] for v in stages.values())
     clocks = clk.summary()
+    workload = WORKLOAD if args.workload == "shell256" else (
+        "shell128: 128^3 periodic MAC grid; HO ventricle-like shell 60x40x6 hex; 14,400 "
+        "elements, 115,200 Gauss points (profiling case)")
     line = {
         "metric": METRIC,
         "value": Q * world / (t_fwd * 1e-3),
@@ -384,7 +393,7 @@ def run_ours(args):
         "precision": "FP32 arithmetic on split positions (int cell + FP32 offset); FP64 for "
                      "J-1, ln J and the fibre exponentials",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [n, n, n], "elements": E, "nodes": N,
+        "config": {"workload": workload, "grid": [n, n, n], "elements": E, "nodes": N,
                    "gauss_points": Q, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "adjoint_ms_per_step": t_adj,
@@ -415,6 +424,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shell256", choices=["shell256", "shell128"],
+                    help="shell128 (128^3 ventricle shell) is a small case for profiling")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle timing (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -32,11 +32,16 @@ void free_plan(ib_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->inc_off, p->inc_idx, p->mass, p->inv_mass, p->wj0, p->elem_scratch,
                   p->elem_scratch2, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist,
-                  p->tile_start, p->tile_end, p->q_cell, p->q_off, p->q_val, p->p_cell,
+                  p->tile_start, p->tile_end, p->tile_slot, p->tile_nonempty, p->tile_near,
+                  p->tile_list, p->tile_list_near, p->tile_bcount, p->tile_counters,
+                  p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
                   p->p_off, p->p_val, p->p_idx, p->gq_a, p->gq_b, p->epart, p->ered,
                   p->dstatus};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->ev) {
     for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
     delete[] p->ev;
@@ -46,6 +51,8 @@ void free_plan(ib_plan* p) {
 }
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
 ib_status check_launch(ib_status st) {
   if (st != IB_OK) return st;
@@ -121,9 +128,8 @@ struct Stage {
 };
 
 int sort_launches(const ib_plan* p) {
-  int bits = 1;
-  while ((1 << bits) < p->ntiles) ++bits;
-  return 3 * ((bits + 7) / 8) + 2;
+  // radix passes (hist, digit scan, scatter), bounds, classify, compact, reorder
+  return 3 * ((sort_key_bits(p->ntiles) + 7) / 8) + 4;
 }
 
 // forward pieces shared by the entry points
@@ -154,12 +160,12 @@ ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, 
 }
 
 ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
-  Stage sc(p, IB_STAGE_SPREAD, s, 1);
+  Stage sc(p, IB_STAGE_SPREAD, s, spread_launches());
   return launch_spread(p, scale, f, s);
 }
 
 ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
-  Stage sc(p, IB_STAGE_REDUCE, s, 1);
+  Stage sc(p, IB_STAGE_REDUCE, s, 2);
   return launch_reduce_parts(p, nvals, n_mats, s);
 }
 
@@ -196,7 +202,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
   *out = nullptr;
   if (!mesh || !grid) return IB_ERR_INVALID_ARG;
   if (precision != IB_FP32_SPLIT && precision != IB_FP64) return IB_ERR_INVALID_ARG;
-  if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || !mesh->conn || !mesh->X)
+  if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
     return IB_ERR_INVALID_ARG;
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
@@ -267,7 +273,19 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
               dalloc(&p->keys[1], 4 * Q) && dalloc(&p->vals[0], 4 * Q) &&
               dalloc(&p->vals[1], 4 * Q) && dalloc(&p->hist, 4 * 256 * (size_t)p->hist_blocks) &&
               dalloc(&p->tile_start, 4 * (size_t)p->ntiles) &&
-              dalloc(&p->tile_end, 4 * (size_t)p->ntiles) && dalloc(&p->q_cell, 4 * Q) &&
+              dalloc(&p->tile_end, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_slot, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_nonempty, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_near, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_list, 4 * (size_t)max_work_items(p->ntiles, Q)) &&
+              dalloc(&p->tile_list_near, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_bcount, 8 * (size_t)classify_blocks(p->ntiles)) &&
+              dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
+              dalloc(&p->rpart, 8 * 9 * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
+              dalloc(&p->spread_scratch,
+                     spread_scratch_bytes(precision, Q < p->ntiles ? (Q > 0 ? Q : 1)
+                                                                   : max_work_items(p->ntiles, Q))) &&
+              dalloc(&p->q_cell, 4 * Q) &&
               dalloc(&p->q_off, rs * 3 * Q) && dalloc(&p->q_val, rs * 3 * Q) &&
               dalloc(&p->p_cell, 4 * Q) && dalloc(&p->p_off, rs * 3 * Q) &&
               dalloc(&p->p_val, rs * 3 * Q) && dalloc(&p->p_idx, 4 * Q) &&
@@ -283,6 +301,11 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
          (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * 8 * E,
                                        cudaMemcpyHostToDevice, s))) &&
          ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
+  if (good)
+    good = ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  if (good) good = spread_prepare(p) == IB_OK && interp_prepare(p) == IB_OK;
   if (!good || launch_plan_static(p, s) != IB_OK || !ok(cudaStreamSynchronize(s))) {
     free_plan(p);
     return IB_ERR_CUDA;
@@ -343,7 +366,7 @@ ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const
 }
 
 ib_status ib_spread(ib_plan* p, const ib_pos* x, const void* G, void* f, void* stream) {
-  if (!p || !G || !f) return IB_ERR_INVALID_ARG;
+  if (!p || !G || !f || !aligned16(f)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
   cudaStream_t s = S(stream);
@@ -364,7 +387,7 @@ ib_status ib_interp(ib_plan* p, const ib_pos* x, const void* u, void* U, void* s
 
 ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                      const void* u, void* G, void* f, void* U, void* stream) {
-  if (!p || !u || !G || !f || !U) return IB_ERR_INVALID_ARG;
+  if (!p || !u || !G || !f || !U || !aligned16(f)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
   MatTable mt;
@@ -401,7 +424,7 @@ ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* 
 
 ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* gU, void* gu,
                         void* gx, void* stream) {
-  if (!p || !gU || !gu || (gx && !u)) return IB_ERR_INVALID_ARG;
+  if (!p || !gU || !gu || (gx && !u) || !aligned16(gu)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
   cudaStream_t s = S(stream);

@@ -12,9 +12,15 @@
 //   I1 - 3  = 2 tr H + |H|^2
 //   I4 - 1  = (|e|^2 - 1) + 2 e.(H e) + |H e|^2
 //   I8      = e_f.e_s + e_f.(H e_s) + e_s.(H e_f) + (H e_f).(H e_s)
-// The scalars whose stability matters -- J - 1, ln J and the fibre
-// exponentials -- are evaluated in the type S (double).  Everything else is
-// in Real (float for split-precision plans, double for FP64 plans).
+// The scalars that carry cancellation are combined in the type S (double):
+// J - 1 (its terms are exact double products of the FP32 entries of H, so the
+// FP64 sum leaves J - 1 exact to double rounding), ln J = log1p(J - 1), and
+// the fibre invariants I4 - 1 and I8, which set the fibre stresses near
+// I4 = 1.  The exponentials are then taken of these FP64 arguments in Real:
+// exp is well conditioned (relative error of the argument times the argument,
+// which is small), so evaluating it beyond the precision of the FP32 stress
+// it multiplies adds nothing.  Everything else is in Real (float for
+// split-precision plans, double for FP64 plans).
 //
 // With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
 //   H = Du J0^-1, and the corner forces are
@@ -83,6 +89,30 @@ __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S
   f.d = I4m1 > S(0) ? I4m1 : S(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
+}
+
+// ln(1 + x) in double.  For |x| <= 1/8 it is 2 atanh(s) with s = x / (2 + x)
+// (|s| <= 1/17), summed as 2 s (1 + z/3 + z^2/5 + ... + z^7/15), z = s^2: the
+// first omitted term is below z^8/17 < 1e-20 relative.  1/(2 + x) comes from
+// an FP32 reciprocal refined by two Newton steps in double.  Outside that
+// range (|J - 1| > 1/8) the library log1p is used.
+__device__ __forceinline__ double log1p_d(double x) {
+  if (!(fabs(x) <= 0.125)) return log1p(x);
+  const double d = 2.0 + x;
+  double r = (double)__frcp_rn((float)d);
+  r = r * (2.0 - d * r);
+  r = r * (2.0 - d * r);
+  const double s = x * r;
+  const double z = s * s;
+  double t = 1.0 / 15.0;
+  t = fma(t, z, 1.0 / 13.0);
+  t = fma(t, z, 1.0 / 11.0);
+  t = fma(t, z, 1.0 / 9.0);
+  t = fma(t, z, 1.0 / 7.0);
+  t = fma(t, z, 1.0 / 5.0);
+  t = fma(t, z, 1.0 / 3.0);
+  t = fma(t, z, 1.0);
+  return 2.0 * s * t;
 }
 
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
@@ -192,19 +222,13 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
         H[i][j] = Du[i][0] * Ji[0][j] + Du[i][1] * Ji[1][j] + Du[i][2] * Ji[2][j];
 
     // ---- invariants --------------------------------------------------------
+    // J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H: the first two terms from
+    // exact double products of the entries of H; det H (third order) in Real.
     const S trS = S(H[0][0]) + S(H[1][1]) + S(H[2][2]);
-    S trH2 = S(0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) trH2 += S(H[i][j]) * S(H[j][i]);
-    S Hs[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Hs[i][j] = S(H[i][j]);
-    const S Jm1 = trS + S(0.5) * (trS * trS - trH2) + det3(Hs);
-    const S lnJs = log1p(Jm1);
+    S trH2 = S(H[0][0]) * S(H[0][0]) + S(H[1][1]) * S(H[1][1]) + S(H[2][2]) * S(H[2][2]);
+    trH2 += S(2) * (S(H[0][1]) * S(H[1][0]) + S(H[0][2]) * S(H[2][0]) + S(H[1][2]) * S(H[2][1]));
+    const S Jm1 = trS + S(0.5) * (trS * trS - trH2) + S(det3(H));
+    const S lnJs = log1p_d(double(Jm1));
     const Real lnJ = Real(lnJs);
     const Real J = Real(S(1) + Jm1);
     Real F[3][3];
@@ -253,14 +277,14 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
     if (has_f) {
       fibre_kin<Real, S>(H, ef, efn1, f1);
       const S af = S(prm[model == 1 ? 1 : 2]), bf = S(prm[model == 1 ? 2 : 3]);
-      ef1 = exp(bf * f1.d * f1.d);
+      ef1 = S(exp(Real(bf * f1.d * f1.d)));
       cf1 = S(2) * af * f1.d * ef1;
     }
     Real Fef[3], Fes[3];
     S I8 = S(0), e8 = S(1), c8 = S(0);
     if (has_s) {
       fibre_kin<Real, S>(H, es, esn1, f2);
-      ef2 = exp(S(prm[5]) * f2.d * f2.d);
+      ef2 = S(exp(Real(S(prm[5]) * f2.d * f2.d)));
       cf2 = S(2) * S(prm[4]) * f2.d * ef2;
       Real Hef[3], Hes[3];
 #pragma unroll
@@ -274,7 +298,7 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         I8 += S(ef[i]) * S(Hes[i]) + S(es[i]) * S(Hef[i]) + S(Hef[i]) * S(Hes[i]);
-      e8 = exp(S(prm[7]) * I8 * I8);
+      e8 = S(exp(Real(S(prm[7]) * I8 * I8)));
       c8 = S(prm[6]) * I8 * e8;
     }
 
@@ -469,23 +493,54 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
   }
 }
 
-// Deterministic per-material sums of per-element partials: one block per
-// (material, value); each thread sums a fixed stride of elements in order,
-// then a fixed-shape tree combines the threads.
-__global__ void __launch_bounds__(256) k_reduce_parts(const double* part, const int32_t* mat_id,
-                                                      int E, int nvals, double* out) {
-  const int m = blockIdx.x / nvals, k = blockIdx.x % nvals;
-  double s = 0.0;
-  for (int e = threadIdx.x; e < E; e += blockDim.x)
-    if ((mat_id ? mat_id[e] : 0) == m) s += part[(int64_t)k * E + e];
-  __shared__ double sh[256];
-  sh[threadIdx.x] = s;
+// Deterministic per-material sums of per-element partials in two levels:
+// CTA b reduces a contiguous chunk of elements with a fixed-shape tree
+// (warp shuffles, then warp sums), one (material, value) pair at a time;
+// one CTA then sums the per-CTA partials of each pair with the same tree.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   }
-  if (threadIdx.x == 0) out[m * 9 + k] = sh[0];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_reduce_l1(const double* __restrict__ part,
+                                                   const int32_t* __restrict__ mat_id, int E,
+                                                   int nvals, int n_mats,
+                                                   double* __restrict__ rpart) {
+  __shared__ double sh[32];
+  const int chunk = (E + gridDim.x - 1) / gridDim.x;
+  const int e0 = blockIdx.x * chunk, e1 = min(E, e0 + chunk);
+  for (int m = 0; m < n_mats; ++m)
+    for (int k = 0; k < nvals; ++k) {
+      double s = 0.0;
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+        if ((mat_id ? __ldg(mat_id + e) : 0) == m) s += __ldg(part + (int64_t)k * E + e);
+      s = block_sum(s, sh);
+      if (threadIdx.x == 0) rpart[((int64_t)blockIdx.x * n_mats + m) * 9 + k] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_l2(const double* __restrict__ rpart, int nblk,
+                                                   int nvals, int n_mats,
+                                                   double* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int m = 0; m < n_mats; ++m)
+    for (int k = 0; k < nvals; ++k) {
+      double s = 0.0;
+      for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += rpart[((int64_t)b * n_mats + m) * 9 + k];
+      s = block_sum(s, sh);
+      if (threadIdx.x == 0) out[m * 9 + k] = s;
+    }
 }
 
 template <typename Real>
@@ -570,7 +625,8 @@ ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s)
     cudaMemsetAsync(p->ered, 0, sizeof(double) * 9 * IB_MAX_MATERIALS, s);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
-  k_reduce_parts<<<n_mats * nvals, 256, 0, s>>>(p->epart, p->mat_id, p->E, nvals, p->ered);
+  k_reduce_l1<<<kReduceCTAs, 256, 0, s>>>(p->epart, p->mat_id, p->E, nvals, n_mats, p->rpart);
+  k_reduce_l2<<<1, 256, 0, s>>>(p->rpart, kReduceCTAs, nvals, n_mats, p->ered);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

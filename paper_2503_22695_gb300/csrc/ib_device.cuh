@@ -148,4 +148,34 @@ struct NodeLoader<double> {
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }
 
+// Exclusive prefix sum of one int per thread across the block (blockDim.x a
+// multiple of 32, at most 1024).  `tmp` is 32 ints of shared memory; `total`
+// receives the block sum.  Contains barriers: call from every thread.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int& total) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(full, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? tmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(full, w, o);
+      if (lane >= o) w += y;
+    }
+    tmp[lane] = w;
+  }
+  __syncthreads();
+  total = tmp[nw - 1];
+  const int pre = (warp > 0 ? tmp[warp - 1] : 0) + x - v;
+  __syncthreads();
+  return pre;
+}
+
 }  // namespace ibfe

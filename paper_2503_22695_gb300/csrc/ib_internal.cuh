@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/ibfe.h"
+#include "ibfe.h"
 
 namespace ibfe {
 
@@ -11,6 +11,7 @@ constexpr int kTile = 8;            // Eulerian tile edge (cells) of the spread 
 constexpr int kTileShift = 3;
 constexpr int kSpreadWarps = 8;     // warps (private accumulators) per spread CTA
 constexpr int kPackBits = 10;       // packed wrapped cell: x | y << 10 | z << 20
+constexpr int kChunk = 1024;        // maximum points per spread / interp work item
 
 // Device-side status bits latched by kernels (read by ib_plan_sync_status).
 constexpr int kStatNonfinite = 1;
@@ -72,6 +73,19 @@ struct ib_plan {
   int hist_blocks;
   int32_t* tile_start;   // [ntiles]
   int32_t* tile_end;     // [ntiles]
+  int32_t* tile_slot;    // [ntiles] first work item of each tile holding points (-1: none)
+  int32_t* tile_nonempty;// [ntiles] number of work items of the tile
+  int32_t* tile_near;    // [ntiles] 1 if a tile of its 3x3x3 neighbourhood holds points
+  int32_t* tile_list;    // [max work items] tile of each work item
+  int32_t* tile_list_near;// [ntiles] near tiles, ascending
+  int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
+  int32_t* tile_counters;// [8] non-empty count, work counters, near count
+  int32_t* digit_tot;    // [256] radix digit totals
+  double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*9] reduction partials
+  cudaStream_t side;     // second stream for work that overlaps the main one
+  cudaEvent_t ev_fork, ev_join;
+  int sm_count, push_ctas, merge_ctas, interp_ctas;
+  void* spread_scratch;  // Real [slots][3][12^3] halo'd per-tile blocks
   int32_t* q_cell;       // packed wrapped cell per Gauss point (unsorted, gq order)
   void* q_off;           // Real [3][Q]
   void* q_val;           // Real [3][Q]
@@ -123,6 +137,9 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s);
 
 // spread.cu
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s);
+ib_status spread_prepare(ib_plan* p);
+size_t spread_scratch_bytes(int precision, int64_t slots);
+int spread_launches();
 
 // interp.cu
 // mode 0: out_a[gq] = w j0 * sum u prod phi (U^IB times w j0)
@@ -131,5 +148,13 @@ ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s);
 // mode 2: only out_b (gradient) as in mode 1.
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
                                double gscale, cudaStream_t s);
+ib_status interp_prepare(ib_plan* p);
+
+// tiles.cu
+ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s);
+int classify_blocks(int ntiles);
+int64_t max_work_items(int ntiles, int64_t Q);
+int sort_key_bits(int ntiles);
+constexpr int kReduceCTAs = 128;
 
 }  // namespace ibfe

@@ -2,10 +2,14 @@
 //   U^IB_q^c = sum_faces u^c(face) prod_d phi(r_d)      (h^3 delta_h = prod phi)
 // and the position derivatives of the same sums, used by the adjoints:
 //   d/dchi_d sum_faces u^c prod phi = h^-1 sum_faces u^c phi'(r_d) prod_{d'!=d} phi(r_d').
-// One thread per Gauss point, visiting points in tile-sorted order so that the
-// 4x4x4 stencils of neighbouring threads overlap in cache; each result is
-// written at the point's original index gq = q*E + e for the element-wise
-// projection that follows.
+//
+// Persistent CTAs pull work items (at most 1024 consecutive points of one
+// 8^3-cell Eulerian tile) from a counter.  The tile's halo'd
+// 12^3 block of each velocity component (faces local -2..9 per axis, every
+// face any of its points can reach) is staged once in shared memory; then one
+// thread per point evaluates its three 4x4x4 stencils from shared memory.
+// Results are written at the point's original index gq = q*E + e for the
+// element-wise projection that follows.
 //
 // Modes
 //   0: a[c][gq] = w j0 * vscale * S_c                      (S_c = sum u^c prod phi)
@@ -16,10 +20,21 @@
 namespace ibfe {
 namespace {
 
+constexpr int kThreads = 256;
+constexpr int kB = 12;
+constexpr int kSY = kB;
+constexpr int kSZ = kB * kB + 1;
+constexpr int kComp = kB * kSZ;  // 1740
+
 template <typename Real>
 struct InterpArgs {
   GridDev g;
   int64_t Q;
+  const int32_t* tile_start;
+  const int32_t* tile_end;
+  const int32_t* tile_slot;  // first work item of each tile
+  const int32_t* tile_list;  // tile of each work item
+  int32_t* counters;      // [0] work items, [2] work counter
   const int32_t* p_cell;
   const Real* p_off;
   const Real* p_val;
@@ -31,88 +46,131 @@ struct InterpArgs {
   Real* out_b;
 };
 
-__device__ __forceinline__ int wrap_near(int i, int n) {
-  return i < 0 ? i + n : (i >= n ? i - n : i);
+template <typename Real, int MODE>
+__device__ __forceinline__ void interp_tile(const InterpArgs<Real>& A, int tile, Real* ub, int tid);
+
+template <typename Real, int MODE>
+__global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* ub = reinterpret_cast<Real*>(smem_raw);  // [3][12 * 145]
+  __shared__ int next;
+  const int tid = threadIdx.x;
+  const int count = A.counters[0];
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) next = atomicAdd(A.counters + 2, 1);
+    __syncthreads();
+    const int k = next;
+    if (k >= count) break;
+    interp_tile<Real, MODE>(A, k, ub, tid);
+  }
 }
 
 template <typename Real, int MODE>
-__global__ void __launch_bounds__(128) k_interp(InterpArgs<Real> A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.Q) return;
+__device__ __forceinline__ void interp_tile(const InterpArgs<Real>& A, int slot, Real* ub, int tid) {
+  const int tile = A.tile_list[slot];
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
+  const int e = min(A.tile_end[tile], s + kChunk);
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
   const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
   const int64_t cells = (int64_t)n0 * n1 * n2;
-  int cx, cy, cz;
-  unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
-  const Real off[3] = {__ldg(A.p_off + i), __ldg(A.p_off + A.Q + i), __ldg(A.p_off + 2 * A.Q + i)};
-  const int cc[3] = {cx, cy, cz};
-  const int nn[3] = {n0, n1, n2};
-  const int gq = __ldg(A.p_idx + i);
-  Real val[3] = {Real(0), Real(0), Real(0)};
-  if (MODE != 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) val[c] = __ldg(A.p_val + c * A.Q + i);
+  const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+
+  // stage the halo'd block: faces (x0-2 .. x0+9) etc., periodically wrapped
+  for (int idx = tid; idx < 3 * kB * kB * kB; idx += kThreads) {
+    const int c = idx / (kB * kB * kB), r = idx % (kB * kB * kB);
+    const int bz = r / (kB * kB), by = (r / kB) % kB, bx = r % kB;
+    int gx = x0 - 2 + bx, gy = y0 - 2 + by, gz = z0 - 2 + bz;  // within one period
+    gx += gx < 0 ? n0 : (gx >= n0 ? -n0 : 0);
+    gy += gy < 0 ? n1 : (gy >= n1 ? -n1 : 0);
+    gz += gz < 0 ? n2 : (gz >= n2 ? -n2 : 0);
+    ub[c * kComp + bz * kSZ + by * kSY + bx] =
+        __ldg(A.u + c * cells + ((int64_t)gz * n1 + gy) * n0 + gx);
   }
-  Real S[3];
-  Real grad[3] = {Real(0), Real(0), Real(0)};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Real w[3][4], dw[3][4];
-    int idx[3][4];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      Real th;
-      const int s = stencil_axis(off[d], d != c, th);
-      if (MODE == 0)
-        delta_weights(th, w[d]);
-      else
-        delta_weights_d(th, w[d], dw[d]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) idx[d][j] = wrap_near(cc[d] + s + j, nn[d]);
-    }
-    const Real* uc = A.u + c * cells;
-    Real tot = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
-#pragma unroll
-    for (int kz = 0; kz < 4; ++kz) {
-      Real py = Real(0), pdy = Real(0), pdx = Real(0);
-#pragma unroll
-      for (int ky = 0; ky < 4; ++ky) {
-        const Real* row = uc + ((int64_t)idx[2][kz] * n1 + idx[1][ky]) * n0;
-        Real rx = Real(0), rdx = Real(0);
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-          const Real v = __ldg(row + idx[0][kx]);
-          rx += w[0][kx] * v;
-          if (MODE != 0) rdx += dw[0][kx] * v;
-        }
-        py += w[1][ky] * rx;
-        if (MODE != 0) {
-          pdy += dw[1][ky] * rx;
-          pdx += w[1][ky] * rdx;
-        }
-      }
-      tot += w[2][kz] * py;
-      if (MODE != 0) {
-        gz += dw[2][kz] * py;
-        gy += w[2][kz] * pdy;
-        gx += w[2][kz] * pdx;
-      }
-    }
-    S[c] = tot;
+  __syncthreads();
+
+  for (int i = s + tid; i < e; i += kThreads) {
+    int cx, cy, cz;
+    unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
+    const int lc[3] = {cx - x0, cy - y0, cz - z0};
+    const Real off[3] = {__ldg(A.p_off + i), __ldg(A.p_off + A.Q + i),
+                         __ldg(A.p_off + 2 * A.Q + i)};
+    const int gq = __ldg(A.p_idx + i);
+    Real val[3] = {Real(0), Real(0), Real(0)};
     if (MODE != 0) {
-      grad[0] += val[c] * gx;
-      grad[1] += val[c] * gy;
-      grad[2] += val[c] * gz;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) val[c] = __ldg(A.p_val + c * A.Q + i);
+    }
+    // weights for both staggerings per axis: [d][0] = s 0, [d][1] = s 1/2
+    Real w[3][2][4], dw[3][2][4];
+    int b[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        Real th;
+        b[d][hf] = lc[d] + stencil_axis(off[d], hf == 1, th) + 2;
+        if (MODE == 0)
+          delta_weights(th, w[d][hf]);
+        else
+          delta_weights_d(th, w[d][hf], dw[d][hf]);
+      }
+    Real S[3];
+    Real grad[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int hx = c != 0, hy = c != 1, hz = c != 2;
+      const Real* uc = ub + c * kComp + b[2][hz] * kSZ + b[1][hy] * kSY + b[0][hx];
+      Real tot = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
+#pragma unroll
+      for (int kz = 0; kz < 4; ++kz) {
+        Real py = Real(0), pdy = Real(0), pdx = Real(0);
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+          const Real* row = uc + kz * kSZ + ky * kSY;
+          Real rx = Real(0), rdx = Real(0);
+#pragma unroll
+          for (int kx = 0; kx < 4; ++kx) {
+            const Real v = row[kx];
+            rx += w[0][hx][kx] * v;
+            if (MODE != 0) rdx += dw[0][hx][kx] * v;
+          }
+          py += w[1][hy][ky] * rx;
+          if (MODE != 0) {
+            pdy += dw[1][hy][ky] * rx;
+            pdx += w[1][hy][ky] * rdx;
+          }
+        }
+        tot += w[2][hz][kz] * py;
+        if (MODE != 0) {
+          gz += dw[2][hz][kz] * py;
+          gy += w[2][hz][kz] * pdy;
+          gx += w[2][hz][kz] * pdx;
+        }
+      }
+      S[c] = tot;
+      if (MODE != 0) {
+        grad[0] += val[c] * gx;
+        grad[1] += val[c] * gy;
+        grad[2] += val[c] * gz;
+      }
+    }
+    if (MODE != 2) {
+      const Real wq = __ldg(A.wj0 + gq) * A.vscale;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
+    }
+    if (MODE != 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = A.gscale * grad[d];
     }
   }
-  if (MODE != 2) {
-    const Real wq = __ldg(A.wj0 + gq) * A.vscale;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
-  }
-  if (MODE != 0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = A.gscale * grad[d];
-  }
+}
+
+template <typename Real>
+size_t smem_bytes() {
+  return sizeof(Real) * 3 * kComp;
 }
 
 template <typename Real>
@@ -122,6 +180,11 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   InterpArgs<Real> A;
   A.g = p->grid;
   A.Q = p->Q;
+  A.tile_start = p->tile_start;
+  A.tile_end = p->tile_end;
+  A.tile_slot = p->tile_slot;
+  A.tile_list = p->tile_list;
+  A.counters = p->tile_counters;
   A.p_cell = p->p_cell;
   A.p_off = (const Real*)p->p_off;
   A.p_val = (const Real*)p->p_val;
@@ -132,18 +195,40 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.gscale = (Real)gscale;
   A.out_a = (Real*)p->gq_a;
   A.out_b = (Real*)p->gq_b;
-  const int threads = 128;
-  const int blocks = (int)((p->Q + threads - 1) / threads);
+  const size_t smem = smem_bytes<Real>();
+  cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
+  const int ctas = min(p->ntiles, p->interp_ctas);
   if (mode == 0)
-    k_interp<Real, 0><<<blocks, threads, 0, s>>>(A);
+    k_interp_tile<Real, 0><<<ctas, kThreads, smem, s>>>(A);
   else if (mode == 1)
-    k_interp<Real, 1><<<blocks, threads, 0, s>>>(A);
+    k_interp_tile<Real, 1><<<ctas, kThreads, smem, s>>>(A);
   else
-    k_interp<Real, 2><<<blocks, threads, 0, s>>>(A);
+    k_interp_tile<Real, 2><<<ctas, kThreads, smem, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
+template <typename Real>
+ib_status prepare_t(ib_plan* p) {
+  const int smem = (int)smem_bytes<Real>();
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_tile<Real, 1>, kThreads,
+                                                    smem) != cudaSuccess || per_sm < 1)
+    return IB_ERR_CUDA;
+  p->interp_ctas = p->sm_count * per_sm;
+  cudaError_t e0 = cudaFuncSetAttribute(k_interp_tile<Real, 0>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e1 = cudaFuncSetAttribute(k_interp_tile<Real, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e2 = cudaFuncSetAttribute(k_interp_tile<Real, 2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return (e0 == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess) ? IB_OK : IB_ERR_CUDA;
+}
+
 }  // namespace
+
+ib_status interp_prepare(ib_plan* p) {
+  return p->precision == IB_FP64 ? prepare_t<double>(p) : prepare_t<float>(p);
+}
 
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
                                double gscale, cudaStream_t s) {

@@ -5,12 +5,14 @@
 //   V_q   = w_q j0 sum_a N_a(xi_q) V_a / m_a   (optional carried value; for the
 //           spreading of Section 4.4 V = G, the lumped projection of the nodal
 //           forces onto the FE space)
-// and the key of the 8^3-cell Eulerian tile containing chi_q (periodically
-// wrapped).  The points are then ordered by a stable LSD radix sort on the
-// tile key (8-bit digits, per-block digit histograms, one exclusive scan,
-// stable in-block ranks from warp match masks), so equal keys keep gq order
-// and the sorted sequence -- hence every downstream summation order -- is
-// identical on every call.
+// and the sort key tile * 512 + cell-in-tile of the (periodically wrapped)
+// cell containing chi_q, for 8^3-cell Eulerian tiles.  The points are then
+// ordered by a stable LSD radix sort on that key (8-bit digits, per-block
+// digit histograms, a per-digit scan across blocks, stable in-block ranks from
+// warp match masks): points are grouped by tile, ordered by cell inside a tile
+// (so neighbouring threads read neighbouring faces), and equal keys keep gq
+// order, so the sorted sequence -- hence every downstream summation order --
+// is identical on every call.
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -19,6 +21,7 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortChunk = kSortThreads * kSortItems;
+constexpr int kLocalBits = 9;  // cell within an 8^3 tile
 
 template <typename Real>
 struct PtArgs {
@@ -105,8 +108,11 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
       A.q_off[d * Q + gq] = off;
     }
     A.q_cell[gq] = pack_cell(cw[0], cw[1], cw[2]);
-    A.key[gq] = (uint32_t)((cw[0] >> kTileShift) +
-                           A.g.nt[0] * ((cw[1] >> kTileShift) + A.g.nt[1] * (cw[2] >> kTileShift)));
+    const uint32_t tile = (uint32_t)((cw[0] >> kTileShift) +
+                                     A.g.nt[0] * ((cw[1] >> kTileShift) +
+                                                  A.g.nt[1] * (cw[2] >> kTileShift)));
+    const uint32_t local = (uint32_t)((((cw[2] & 7) << 3) | (cw[1] & 7)) << 3 | (cw[0] & 7));
+    A.key[gq] = (tile << kLocalBits) | local;
     A.val[gq] = (int32_t)gq;
     if (A.V) {
       const Real w = __ldg(A.wj0 + gq);
@@ -139,37 +145,35 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   hist[threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// In-place exclusive scan of M ints by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan(int32_t* __restrict__ a, int M) {
-  __shared__ int sums[1024];
-  const int per = (M + 1023) / 1024;
-  const int b = threadIdx.x * per, e = min(M, b + per);
-  int s = 0;
-  for (int i = b; i < e; ++i) s += a[i];
-  sums[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    int v = threadIdx.x >= off ? sums[threadIdx.x - off] : 0;
-    __syncthreads();
-    sums[threadIdx.x] += v;
-    __syncthreads();
+// For each digit (one CTA per digit): exclusive scan, in place, of its
+// per-block counts hist[d*nblk .. d*nblk + nblk), and the digit total.
+__global__ void __launch_bounds__(1024) k_digit_scan(int32_t* __restrict__ hist, int nblk,
+                                                     int32_t* __restrict__ dtot) {
+  __shared__ int tmp[32];
+  int32_t* h = hist + (int64_t)blockIdx.x * nblk;
+  int carry = 0;
+  for (int b0 = 0; b0 < nblk; b0 += 1024) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < nblk ? h[i] : 0;
+    int tot;
+    const int pre = block_exclusive_scan(v, tmp, tot);
+    if (i < nblk) h[i] = carry + pre;
+    carry += tot;
   }
-  int run = sums[threadIdx.x] - s;  // exclusive prefix of this thread's segment
-  for (int i = b; i < e; ++i) {
-    const int v = a[i];
-    a[i] = run;
-    run += v;
-  }
+  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t Q, int shift,
-    int nblk, const int32_t* __restrict__ offs, uint32_t* __restrict__ kout,
-    int32_t* __restrict__ vout) {
+    int nblk, const int32_t* __restrict__ offs, const int32_t* __restrict__ dtot,
+    uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
   __shared__ int base[256];
   __shared__ int wcnt[kSortThreads / 32][256];
+  __shared__ int tmp[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  base[t] = offs[t * nblk + blockIdx.x];
+  int total;
+  const int dbase = block_exclusive_scan(dtot[t], tmp, total);  // start of digit t
+  base[t] = dbase + offs[t * nblk + blockIdx.x];
   for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
   __syncthreads();
   const int64_t b0 = (int64_t)blockIdx.x * kSortChunk;
@@ -211,9 +215,9 @@ __global__ void k_tile_bounds(const uint32_t* __restrict__ key, int64_t Q,
                               int32_t* __restrict__ start, int32_t* __restrict__ end) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Q) return;
-  const uint32_t k = key[i];
-  if (i == 0 || key[i - 1] != k) start[k] = (int32_t)i;
-  if (i == Q - 1 || key[i + 1] != k) end[k] = (int32_t)(i + 1);
+  const uint32_t k = key[i] >> kLocalBits;
+  if (i == 0 || (key[i - 1] >> kLocalBits) != k) start[k] = (int32_t)i;
+  if (i == Q - 1 || (key[i + 1] >> kLocalBits) != k) end[k] = (int32_t)(i + 1);
 }
 
 template <typename Real>
@@ -302,21 +306,22 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
   const int64_t Q = p->Q;
   cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
   cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
-  if (Q == 0) return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
-  int bits = 1;
-  while ((1 << bits) < p->ntiles) ++bits;
+  if (Q == 0) return launch_classify_tiles(p, s);
+  const int bits = sort_key_bits(p->ntiles);
   const int nblk = p->hist_blocks;
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
     k_radix_hist<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], Q, shift, nblk, p->hist);
-    k_scan<<<1, 1024, 0, s>>>(p->hist, 256 * nblk);
+    k_digit_scan<<<256, 1024, 0, s>>>(p->hist, nblk, p->digit_tot);
     k_radix_scatter<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], p->vals[cur], Q, shift, nblk,
-                                                  p->hist, p->keys[cur ^ 1], p->vals[cur ^ 1]);
+                                                  p->hist, p->digit_tot, p->keys[cur ^ 1],
+                                                  p->vals[cur ^ 1]);
     cur ^= 1;
   }
   const int tb = 256;
   const int nb = (int)((Q + tb - 1) / tb);
   k_tile_bounds<<<nb, tb, 0, s>>>(p->keys[cur], Q, p->tile_start, p->tile_end);
+  if (launch_classify_tiles(p, s) != IB_OK) return IB_ERR_CUDA;
   if (p->precision == IB_FP64)
     k_permute<double><<<nb, tb, 0, s>>>(p->vals[cur], Q, p->q_cell, (const double*)p->q_off,
                                         (const double*)p->q_val, p->p_cell, (double*)p->p_off,
@@ -329,5 +334,11 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
 }
 
 int sort_hist_blocks(int64_t Q) { return (int)((Q + kSortChunk - 1) / kSortChunk); }
+
+int sort_key_bits(int ntiles) {
+  int bits = 1;
+  while ((1 << bits) < ntiles) ++bits;
+  return bits + kLocalBits;
+}
 
 }  // namespace ibfe

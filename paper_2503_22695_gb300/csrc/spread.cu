@@ -3,28 +3,43 @@
 // with scale = h^-3 for forces (delta_h carries h^-3) and 1 for the adjoint
 // of interpolation.
 //
-// Design: every 8x8x8-cell Eulerian tile is owned by one CTA, which computes
-// all three components of its 3*512 faces and writes each exactly once, so
-// the whole field (including the zero-fill outside the structure) is written
-// in one pass with no global atomics.  The CTA pulls the points binned in its
-// tile and in the neighbouring tiles (a point's stencil reaches two cells
-// beyond its own cell) in a fixed order: neighbour tiles in (z, y, x) order,
-// points in sorted order within a tile.  Point k of that sequence goes to
-// warp k mod W; each warp accumulates into its own shared-memory copy of the
-// tile, one point at a time, its 32 lanes covering the 48 (component, dz, dy)
-// rows of the 4x4x4 stencil (the four dx entries of a row by one lane), so no
-// two lanes touch the same face in one step.  The W copies are then summed in
-// warp order.  Every face therefore sees its contributions in a fixed order,
-// and the result is bitwise reproducible.
+// Three kernels over 8^3-cell Eulerian tiles, no global floating-point
+// atomics, bitwise reproducible:
+//
+// k_spread_zero (side stream, concurrent with the push) -- one warp per
+//   "far" tile (no points in its 3x3x3 neighbourhood) writes its zeros with
+//   16-byte stores: the bulk of the field's HBM traffic overlaps the
+//   accumulation work.
+// k_spread_push (persistent CTAs pulling tiles from a work counter) -- a
+//   tile holding Gauss points accumulates every stencil entry of its own
+//   points into a halo'd 12^3 block per component (its points reach two cells
+//   beyond the tile; indices stay unwrapped), one component at a time.
+//   Points are staged in batches of 256 (one thread per point computes the
+//   3x4 kernel weights); point k of a batch goes to warp k mod 8, each warp
+//   adding into its own shared-memory copy, one point per step (32 lanes x 2
+//   entries = the 64 stencil entries of one component, all distinct faces),
+//   steps ordered by __syncwarp.  The eight copies are summed in warp order
+//   and the block is written to the work item's scratch block.  A work item is
+//   at most 1024 consecutive points of one tile, so densely populated tiles
+//   are shared by several CTAs.
+// k_spread_merge -- for every "near" tile, each face sums the blocks of its
+//   own tile and of the neighbours whose halo covers it (at most two per
+//   axis), in a fixed (z, y, x) source order and, within a source tile, in
+//   work-item order, and is written once.  Periodic
+//   wrap happens only here, through the neighbour-tile index.
 #include "ib_device.cuh"
 
 namespace ibfe {
 namespace {
 
-constexpr int W = kSpreadWarps;
-constexpr int kZS = 66;                    // z stride (bank spread across (z,y))
-constexpr int kCS = kTile * kZS + 1;       // component stride
-constexpr int kWS = 3 * kCS + 1;           // warp stride
+constexpr int W = kSpreadWarps;         // 8 warps
+constexpr int kThreads = W * 32;
+constexpr int kB = 12;                  // halo'd block edge: tile 8 + 2 + 2
+constexpr int kBlk = kB * kB * kB;      // 1728 faces per component
+constexpr int kSY = kB;                 // shared y stride
+constexpr int kSZ = kB * kB + 1;        // shared z stride (145: spreads (dz,dy) over banks)
+constexpr int kAcc = kB * kSZ;          // 1740 per warp copy
+constexpr int kBatch = kThreads;        // points staged per batch
 
 template <typename Real>
 struct SpreadArgs {
@@ -32,123 +47,204 @@ struct SpreadArgs {
   int64_t Q;
   const int32_t* tile_start;
   const int32_t* tile_end;
+  const int32_t* tile_slot;    // first work item of each tile
+  const int32_t* tile_nitems;  // work items of each tile
+  const int32_t* tile_near;
+  const int32_t* tile_list;    // tile of each work item
+  const int32_t* tile_list_near;
+  int32_t* counters;      // [0] non-empty tiles, [1] work counter, [3] near tiles
   const int32_t* p_cell;
   const Real* p_off;
   const Real* p_val;
   Real scale;
+  Real* scratch;   // [slots][3][12^3]
   Real* f;
 };
 
+// staged point: x/y/z weights, value, row origin in the halo'd block
 template <typename Real>
-__device__ __forceinline__ Real pick4(const Real w[4], int i) {
-  return i == 0 ? w[0] : (i == 1 ? w[1] : (i == 2 ? w[2] : w[3]));
+struct alignas(16) Staged {
+  Real wx[4];
+  Real wy[4];
+  Real wz[4];
+  Real val;
+  int org;
+  int pad[2];
+};
+
+__device__ __forceinline__ int tile_of(int tx, int ty, int tz, const GridDev& g) {
+  return wrap_idx(tx, g.nt[0]) + g.nt[0] * (wrap_idx(ty, g.nt[1]) + g.nt[1] * wrap_idx(tz, g.nt[2]));
+}
+
+// One lane adds into one face per step; __syncwarp between steps orders the
+// read-modify-writes of different lanes to the same face.
+template <typename Real>
+__device__ __forceinline__ void add_shared(Real* p, Real v) {
+  *p += v;
+}
+
+// Work item `slot`: points [start + j kChunk, min(end, start + (j+1) kChunk))
+// of `tile`, j = slot - first item of the tile.
+template <typename Real>
+__device__ __forceinline__ void push_tile(const SpreadArgs<Real>& A, int slot, Staged<Real>* stage,
+                                          Real* acc, int tid, int lane, int warp, int nt0,
+                                          int nt1) {
+  const int tile = A.tile_list[slot];
+  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
+  const int e = min(A.tile_end[tile], s + kChunk);
+  const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+  Real* my = acc + warp * kAcc;
+  // this lane's two stencil entries of a component: row (dz, dy), dx = 2h, 2h+1
+  const int r = lane >> 1, dz = r >> 2, dy = r & 3, hx = (lane & 1) * 2;
+  const int lane_off = dz * kSZ + dy * kSY + hx;
+
+  for (int c = 0; c < 3; ++c) {
+    for (int i = tid; i < W * kAcc; i += kThreads) acc[i] = Real(0);
+    for (int b0 = s; b0 < e; b0 += kBatch) {
+      const int nb = min(kBatch, e - b0);
+      __syncthreads();  // previous batch consumed, accumulators zeroed
+      if (tid < nb) {
+        const int i = b0 + tid;
+        int cx, cy, cz;
+        unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
+        Staged<Real> st;
+        Real th;
+        const int bx = cx - x0 + stencil_axis(__ldg(A.p_off + i), c != 0, th) + 2;
+        delta_weights(th, st.wx);
+        const int by = cy - y0 + stencil_axis(__ldg(A.p_off + A.Q + i), c != 1, th) + 2;
+        delta_weights(th, st.wy);
+        const int bz = cz - z0 + stencil_axis(__ldg(A.p_off + 2 * A.Q + i), c != 2, th) + 2;
+        delta_weights(th, st.wz);
+        st.val = __ldg(A.p_val + c * A.Q + i) * A.scale;
+        st.org = bz * kSZ + by * kSY + bx;
+        stage[tid] = st;
+      }
+      __syncthreads();
+      // software pipelined: the next point's staged values are read while the
+      // current point's read-modify-writes are in flight
+      int p = warp;
+      Real a0 = Real(0), a1 = Real(0);
+      int o = 0;
+      if (p < nb) {
+        const Staged<Real>& st = stage[p];
+        const Real w = st.val * st.wz[dz] * st.wy[dy];
+        a0 = w * st.wx[hx];
+        a1 = w * st.wx[hx + 1];
+        o = st.org + lane_off;
+      }
+      for (; p < nb; p += W) {
+        Real b0 = Real(0), b1 = Real(0);
+        int ob = 0;
+        if (p + W < nb) {
+          const Staged<Real>& st = stage[p + W];
+          const Real w = st.val * st.wz[dz] * st.wy[dy];
+          b0 = w * st.wx[hx];
+          b1 = w * st.wx[hx + 1];
+          ob = st.org + lane_off;
+        }
+        add_shared(my + o, a0);
+        add_shared(my + o + 1, a1);
+        __syncwarp();
+        a0 = b0;
+        a1 = b1;
+        o = ob;
+      }
+    }
+    __syncthreads();
+    Real* out = A.scratch + ((int64_t)slot * 3 + c) * kBlk;
+    for (int idx = tid; idx < kBlk; idx += kThreads) {
+      const int z = idx / (kB * kB), y = (idx / kB) % kB, x = idx % kB;
+      const int o = z * kSZ + y * kSY + x;
+      Real sum = Real(0);
+#pragma unroll
+      for (int w = 0; w < W; ++w) sum += acc[w * kAcc + o];
+      out[idx] = sum;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(W * 32) k_spread(SpreadArgs<Real> A) {
+__global__ void __launch_bounds__(kThreads) k_spread_push(SpreadArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* acc = reinterpret_cast<Real*>(smem_raw);
+  Staged<Real>* stage = reinterpret_cast<Staged<Real>*>(smem_raw);
+  Real* acc = reinterpret_cast<Real*>(smem_raw + sizeof(Staged<Real>) * kBatch);
+  __shared__ int next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1], nt2 = A.g.nt[2];
-  const int tile = blockIdx.x;
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int count = A.counters[0];
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) next = atomicAdd(A.counters + 1, 1);
+    __syncthreads();
+    const int k = next;
+    if (k >= count) break;
+    push_tile(A, k, stage, acc, tid, lane, warp, nt0, nt1);
+  }
+}
+
+// Far tiles: one warp per tile, 3 components x 64 rows x 2 x 16-byte zeros.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_spread_zero(SpreadArgs<Real> A) {
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * W + (threadIdx.x >> 5);
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  if (tile >= nt0 * nt1 * A.g.nt[2] || A.tile_near[tile]) return;
+  const int n0 = A.g.n[0], n1 = A.g.n[1];
+  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-  const int64_t cells = (int64_t)n0 * n1 * n2;
-
-  // neighbour tiles, deduplicated when a dimension has fewer than 3 tiles
-  int offs[3][3], cnt[3];
-  const int ntd[3] = {nt0, nt1, nt2};
-  for (int d = 0; d < 3; ++d) {
-    if (ntd[d] >= 3) {
-      cnt[d] = 3;
-      offs[d][0] = -1; offs[d][1] = 0; offs[d][2] = 1;
-    } else if (ntd[d] == 2) {
-      cnt[d] = 2;
-      offs[d][0] = 0; offs[d][1] = 1;
-    } else {
-      cnt[d] = 1;
-      offs[d][0] = 0;
-    }
-  }
-  int total = 0;
-  for (int a = 0; a < cnt[2]; ++a)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int c = 0; c < cnt[0]; ++c) {
-        const int nb = wrap_idx(tx + offs[0][c], nt0) +
-                       nt0 * (wrap_idx(ty + offs[1][b], nt1) + nt1 * wrap_idx(tz + offs[2][a], nt2));
-        total += A.tile_end[nb] - A.tile_start[nb];
-      }
-
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
-  if (total == 0) {  // nothing reaches this tile: zero-fill
-    for (int idx = tid; idx < 3 * 512; idx += W * 32) {
-      const int c = idx >> 9, r = idx & 511;
-      const int z = r >> 6, y = (r >> 3) & 7, x = r & 7;
-      A.f[c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + (x0 + x)] = Real(0);
-    }
-    return;
+  constexpr int kVec = 16 / sizeof(Real);          // reals per 16-byte store
+  constexpr int kPerRow = kTile / kVec;
+  for (int idx = lane; idx < 3 * 64 * kPerRow; idx += 32) {
+    const int c = idx / (64 * kPerRow), r = (idx / kPerRow) % 64, v = idx % kPerRow;
+    const int z = r >> 3, y = r & 7;
+    Real* row = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+    reinterpret_cast<float4*>(row)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
 
-  for (int i = tid; i < W * kWS; i += W * 32) acc[i] = Real(0);
-  __syncthreads();
-  Real* my = acc + warp * kWS;
-
-  int k0 = 0;
-  for (int a = 0; a < cnt[2]; ++a)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int c = 0; c < cnt[0]; ++c) {
-        const int nb = wrap_idx(tx + offs[0][c], nt0) +
-                       nt0 * (wrap_idx(ty + offs[1][b], nt1) + nt1 * wrap_idx(tz + offs[2][a], nt2));
-        const int s = A.tile_start[nb], e = A.tile_end[nb];
-        const int first = ((warp - k0) % W + W) % W;
-        for (int i = s + first; i < e; i += W) {
-          const int32_t pc = __ldg(A.p_cell + i);
-          int cx, cy, cz;
-          unpack_cell(pc, cx, cy, cz);
-          const Real ox = __ldg(A.p_off + i), oy = __ldg(A.p_off + A.Q + i),
-                     oz = __ldg(A.p_off + 2 * A.Q + i);
-          const Real v0 = __ldg(A.p_val + i), v1 = __ldg(A.p_val + A.Q + i),
-                     v2 = __ldg(A.p_val + 2 * A.Q + i);
-#pragma unroll
-          for (int rr = 0; rr < 2; ++rr) {
-            const int row = lane + 32 * rr;
-            if (row >= 48) break;
-            const int comp = row >> 4, dz = (row >> 2) & 3, dy = row & 3;
-            Real th;
-            const int sz = stencil_axis(oz, comp != 2, th);
-            const int rz = wrap_idx(cz + sz + dz, n2) - z0;
-            if ((unsigned)rz >= (unsigned)kTile) continue;
-            Real wz4[4];
-            delta_weights(th, wz4);
-            const int sy = stencil_axis(oy, comp != 1, th);
-            const int ry = wrap_idx(cy + sy + dy, n1) - y0;
-            if ((unsigned)ry >= (unsigned)kTile) continue;
-            Real wy4[4];
-            delta_weights(th, wy4);
-            const int sx = stencil_axis(ox, comp != 0, th);
-            Real wx4[4];
-            delta_weights(th, wx4);
-            const Real v = comp == 0 ? v0 : (comp == 1 ? v1 : v2);
-            const Real base = v * A.scale * pick4(wz4, dz) * pick4(wy4, dy);
-            Real* rowp = my + comp * kCS + rz * kZS + ry * kTile;
-#pragma unroll
-            for (int dx = 0; dx < 4; ++dx) {
-              const int rx = wrap_idx(cx + sx + dx, n0) - x0;
-              if ((unsigned)rx < (unsigned)kTile) rowp[rx] += base * wx4[dx];
-            }
+// Near tiles: fixed-order sum of the halo'd blocks that cover each face.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_spread_merge(SpreadArgs<Real> A) {
+  __shared__ int src_slot[27], src_n[27];
+  const int tid = threadIdx.x;
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int n0 = A.g.n[0], n1 = A.g.n[1];
+  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
+  const int count = A.counters[3];
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const int tile = A.tile_list_near[k];
+    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+    __syncthreads();
+    if (tid < 27) {
+      const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
+      const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
+      src_slot[tid] = A.tile_slot[nb];
+      src_n[tid] = A.tile_nitems[nb];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 3 * 512; idx += kThreads) {
+      const int c = idx >> 9, rr = idx & 511;
+      const int z = rr >> 6, y = (rr >> 3) & 7, x = rr & 7;
+      // source offsets along each axis: own tile, and the neighbour whose halo
+      // reaches this face (faces 0..1 from below, 6..7 from above)
+      const int lx = x <= 1 ? -1 : 0, ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
+      const int hx = x >= 6 ? 1 : 0, hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
+      Real sum = Real(0);
+      for (int oz = lz; oz <= hz; ++oz)
+        for (int oy = ly; oy <= hy; ++oy)
+          for (int ox = lx; ox <= hx; ++ox) {
+            const int si = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+            const int sl = src_slot[si], ns = src_n[si];
+            const int bx = x - ox * kTile + 2, by = y - oy * kTile + 2, bz = z - oz * kTile + 2;
+            for (int j = 0; j < ns; ++j)  // the tile's work items in order
+              sum += A.scratch[((int64_t)(sl + j) * 3 + c) * kBlk + (bz * kB + by) * kB + bx];
           }
-        }
-        k0 += e - s;
-      }
-  __syncthreads();
-  for (int idx = tid; idx < 3 * 512; idx += W * 32) {
-    const int c = idx >> 9, r = idx & 511;
-    const int z = r >> 6, y = (r >> 3) & 7, x = r & 7;
-    const int o = c * kCS + z * kZS + y * kTile + x;
-    Real sum = Real(0);
-#pragma unroll
-    for (int w = 0; w < W; ++w) sum += acc[w * kWS + o];
-    A.f[c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + (x0 + x)] = sum;
+      A.f[c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + (x0 + x)] = sum;
+    }
   }
 }
 
@@ -159,25 +255,72 @@ ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
   A.Q = p->Q;
   A.tile_start = p->tile_start;
   A.tile_end = p->tile_end;
+  A.tile_slot = p->tile_slot;
+  A.tile_nitems = p->tile_nonempty;
+  A.tile_near = p->tile_near;
+  A.tile_list = p->tile_list;
+  A.tile_list_near = p->tile_list_near;
+  A.counters = p->tile_counters;
   A.p_cell = p->p_cell;
   A.p_off = (const Real*)p->p_off;
   A.p_val = (const Real*)p->p_val;
   A.scale = (Real)scale;
+  A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;
-  const size_t smem = sizeof(Real) * W * kWS;
-  static bool attr_set[2] = {false, false};
-  const int which = sizeof(Real) == 8;
-  if (!attr_set[which]) {
-    if (cudaFuncSetAttribute(k_spread<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return IB_ERR_CUDA;
-    attr_set[which] = true;
-  }
-  k_spread<Real><<<p->ntiles, W * 32, smem, s>>>(A);
+  const size_t smem = sizeof(Staged<Real>) * kBatch + sizeof(Real) * W * kAcc;
+  cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
+  // far-tile zeros on the side stream, concurrent with the push
+  cudaEventRecord(p->ev_fork, s);
+  cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+  k_spread_zero<Real><<<(p->ntiles + W - 1) / W, kThreads, 0, p->side>>>(A);
+  cudaEventRecord(p->ev_join, p->side);
+  const int push_ctas = min(p->ntiles, p->push_ctas);
+  k_spread_push<Real><<<push_ctas, kThreads, smem, s>>>(A);
+  const int merge_ctas = min(p->ntiles, p->merge_ctas);
+  k_spread_merge<Real><<<merge_ctas, kThreads, 0, s>>>(A);
+  cudaStreamWaitEvent(s, p->ev_join, 0);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
 }  // namespace
+
+size_t spread_smem_bytes(int precision) {
+  return precision == IB_FP64 ? sizeof(Staged<double>) * kBatch + sizeof(double) * W * kAcc
+                              : sizeof(Staged<float>) * kBatch + sizeof(float) * W * kAcc;
+}
+
+size_t spread_scratch_bytes(int precision, int64_t slots) {
+  return (size_t)slots * 3 * kBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(float));
+}
+
+ib_status spread_prepare(ib_plan* p) {
+  const int smem = (int)spread_smem_bytes(p->precision);
+  int dev = 0, sms = 0, per_sm = 0, per_sm_merge = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return IB_ERR_CUDA;
+  cudaError_t e;
+  if (p->precision == IB_FP64) {
+    e = cudaFuncSetAttribute(k_spread_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<double>, kThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<double>, kThreads, 0);
+  } else {
+    e = cudaFuncSetAttribute(k_spread_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<float>, kThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<float>, kThreads, 0);
+  }
+  if (e != cudaSuccess || per_sm < 1 || per_sm_merge < 1) return IB_ERR_CUDA;
+  p->sm_count = sms;
+  p->push_ctas = sms * per_sm;
+  p->merge_ctas = sms * per_sm_merge;
+  return IB_OK;
+}
+
+int spread_launches() { return 3; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
   return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, s)
