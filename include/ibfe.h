@@ -164,6 +164,28 @@ ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats
                           const ib_pos* x, const void* v, void* Hv, double* gparams,
                           void* stream);
 
+/* Total elastic energy sum_{e,q} Psi(F_q) w_q j0 of an FP32 split-position
+ * mesh, without a plan and without allocating anything, for callers that
+ * cannot call cudaMalloc: code running while a CUDA graph is captured on its
+ * stream, runtimes that give all device memory to a fixed pool up front, or
+ * loops that must not enter the allocator.  The paper has no counterpart of
+ * this entry point; it is a service of this library.
+ *   mesh    as for ib_plan_create, X and fibres float; n_elems <= 262144,
+ *           else IB_ERR_CAPACITY (nothing is launched).
+ *   mats    host material table, n_mats <= IB_MAX_MATERIALS.
+ *   x       split positions (cell, off); h is the grid spacing.
+ *   energy  device double, written with the result (NaN if the mesh holds a
+ *           node index outside [0, n_nodes) or a material index outside
+ *           [0, n_mats)).
+ * Scratch: a file-scope device array (about 2 MiB) that every GPU loading the
+ * library keeps until exit; each call overwrites what it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU race on it and must not
+ * be issued.  The first call on a device looks up the array's device address
+ * (no allocation); make that first call before any stream capture.
+ * Asynchronous on `stream`; launch errors return IB_ERR_CUDA. */
+ib_status ib_fe_energy_noalloc(const ib_mesh* mesh, const ib_material* mats, int32_t n_mats,
+                               const ib_pos* x, double h, double* energy, void* stream);
+
 /* Synchronise `stream` and return (then clear) the first device-detected
  * condition latched since the last call (IB_OK if none). */
 ib_status ib_plan_sync_status(ib_plan* plan, void* stream);

@@ -74,6 +74,8 @@ def _load():
         "ib_fe_force_adj": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, dp, vp],
         "ib_plan_sync_status": [vp, vp],
         "ib_plan_set_profiling": [vp, i32],
+        "ib_fe_energy_noalloc": [C.POINTER(_Mesh), C.POINTER(_Mat), i32, C.POINTER(_Pos),
+                                 C.c_double, vp, vp],
         "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
     }
     for name, args in sigs.items():
@@ -300,6 +302,29 @@ def ib_fe_force_adj(plan: Plan, mats, x: Pos, v, want_params: bool = True, Hv=No
 
 def ib_plan_sync_status(plan: Plan) -> int:
     return int(_lib.ib_plan_sync_status(plan.handle, _stream()))
+
+
+def ib_fe_energy_noalloc(conn, X, mats, x: Pos, h: float, energy, fibres=None, mat_id=None):
+    """Plan-free total elastic energy written into the device float64 tensor
+    `energy` (one element); the library allocates nothing for it (see the C
+    declaration for the limits and the shared-scratch caveats)."""
+    _check(conn, torch.int32, (8, -1), "conn")
+    _check(X, torch.float32, (3, -1), "X")
+    _check(energy, torch.float64, (1,), "energy")
+    N, E = int(X.shape[1]), int(conn.shape[1])
+    _check(x.cell, torch.int32, (3, N), "cell")
+    _check(x.off, torch.float32, (3, N), "off")
+    if fibres is not None:
+        _check(fibres, torch.float32, (6, E), "fibres")
+    if mat_id is not None:
+        _check(mat_id, torch.int32, (E,), "mat_id")
+    mesh = _Mesh(N, E, conn.data_ptr(), X.data_ptr(),
+                 None if fibres is None else fibres.data_ptr(),
+                 None if mat_id is None else mat_id.data_ptr())
+    arr, nm = _mats(mats)
+    _chk(_lib.ib_fe_energy_noalloc(C.byref(mesh), arr, nm, C.byref(x._s), float(h),
+                                   _ptr(energy), _stream()), "ib_fe_energy_noalloc")
+    return energy
 
 
 def ib_plan_set_profiling(plan: Plan, enable: bool):
