@@ -283,6 +283,18 @@ def run_ours(args):
     t_fwd = sum(ms) / len(ms)
     barrier()
 
+    # --- the same forward with FP32 stability scalars (second plan) ---------
+    plan32 = ibfe.Plan(conn, X, prob.grid.n, prob.grid.h, fibres=fib, mat_id=mid,
+                       precision=ibfe.IB_FP32_SPLIT_F32STAB)
+    fwd32 = lambda: ibfe.ib_forward(plan32, mats, pos, u, G, f, U)
+    for _ in range(args.warmup):
+        fwd32()
+    barrier()
+    ms32 = timed(fwd32, args.steps)
+    t_fwd32 = sum(ms32) / len(ms32)
+    del plan32
+    barrier()
+
     # --- adjoint ---------------------------------------------------------
     rng = np.random.default_rng(77 + rank)
     gU = torch.from_numpy(rng.normal(size=(3, N)).astype(np.float32)).to(dev)
@@ -396,6 +408,9 @@ def run_ours(args):
         "config": {"workload": workload, "grid": [n, n, n], "elements": E, "nodes": N,
                    "gauss_points": Q, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp32_scalars": {"ms_per_step": t_fwd32, "value": Q * world / (t_fwd32 * 1e-3),
+                         "note": "same forward with J-1, ln J and fibre invariants in FP32 "
+                                 "(IB_FP32_SPLIT_F32STAB)"},
         "adjoint_ms_per_step": t_adj,
         "adjoint_forward_ratio": t_adj / t_fwd,
         "roofline": roof,

@@ -76,7 +76,15 @@ typedef enum {
   IB_HO = 2           /* Psi_4 Holzapfel-Ogden (Section 3); params {a, b, af, bf, as, bs, afs, bfs, kappa} */
 } ib_model;
 
-typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1 } ib_precision;
+/* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1, ln J and the
+ *   fibre invariants I4 - 1, I8 are combined in FP64 (the steps whose
+ *   cancellation sets the volumetric and fibre stresses).
+ * IB_FP64: every array and every operation in double.
+ * IB_FP32_SPLIT_F32STAB: as IB_FP32_SPLIT with those scalars in FP32 too,
+ *   using the same cancellation-free formulas (much faster on GPUs whose FP64
+ *   rate is a small fraction of FP32; forces agree with IB_FP32_SPLIT to a
+ *   few 1e-7 relative). */
+typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_precision;
 
 #define IB_MAX_MATERIALS 8
 

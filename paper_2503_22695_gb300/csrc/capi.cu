@@ -40,8 +40,9 @@ void free_plan(ib_plan* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
-  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->zside) cudaStreamDestroy(p->zside);
+  for (cudaEvent_t ev : {p->ev_fork, p->ev_join, p->ev_ffork, p->ev_fsorted, p->ev_fjoin})
+    if (ev) cudaEventDestroy(ev);
   if (p->ev) {
     for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
     delete[] p->ev;
@@ -169,10 +170,12 @@ ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
   return launch_reduce_parts(p, nvals, n_mats, s);
 }
 
-ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s) {
+ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s,
+                         void* elem = nullptr) {
+  if (!elem) elem = p->elem_scratch;
   ib_status st = do_interp(p, u, 0, 1.0, 0.0, s);
-  if (st == IB_OK) st = do_project(p, p->gq_a, p->elem_scratch, s);
-  if (st == IB_OK) st = do_gather(p, p->elem_scratch, p->inv_mass, U, s);
+  if (st == IB_OK) st = do_project(p, p->gq_a, elem, s);
+  if (st == IB_OK) st = do_gather(p, elem, p->inv_mass, U, s);
   return st;
 }
 
@@ -201,7 +204,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
   if (!out) return IB_ERR_INVALID_ARG;
   *out = nullptr;
   if (!mesh || !grid) return IB_ERR_INVALID_ARG;
-  if (precision != IB_FP32_SPLIT && precision != IB_FP64) return IB_ERR_INVALID_ARG;
+  if (precision != IB_FP32_SPLIT && precision != IB_FP64 && precision != IB_FP32_SPLIT_F32STAB)
+    return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
     return IB_ERR_INVALID_ARG;
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
@@ -303,8 +307,12 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
          ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
   if (good)
     good = ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) &&
+           ok(cudaStreamCreateWithFlags(&p->zside, cudaStreamNonBlocking)) &&
            ok(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming)) &&
-           ok(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+           ok(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_ffork, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_fsorted, cudaEventDisableTiming)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_fjoin, cudaEventDisableTiming));
   if (good) good = spread_prepare(p) == IB_OK && interp_prepare(p) == IB_OK;
   if (!good || launch_plan_static(p, s) != IB_OK || !ok(cudaStreamSynchronize(s))) {
     free_plan(p);
@@ -393,14 +401,29 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
   MatTable mt;
   if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
   cudaStream_t s = S(stream);
-  {
+  // Two branches: the Gauss-point sort and the interpolation depend only on
+  // x and u and run on the side stream while the FE force (FP64-pipe bound)
+  // runs on the caller's stream; the spread waits for both.
+  cudaStream_t b = p->side;
+  if (!ok(cudaEventRecord(p->ev_ffork, s)) || !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0)))
+    return IB_ERR_CUDA;
+  st = do_points_sorted(p, x, nullptr, b);
+  if (st == IB_OK && !ok(cudaEventRecord(p->ev_fsorted, b))) st = IB_ERR_CUDA;
+  if (st == IB_OK) st = do_interp_tail(p, u, U, b, p->elem_scratch2);
+  if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
+  if (st == IB_OK) {
     Stage sc(p, IB_STAGE_FORCE, s, 1);
     st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
-  if (st == IB_OK) st = do_points_sorted(p, x, G, s);
+  if (st == IB_OK) {
+    Stage sc(p, IB_STAGE_POINTS, s, 2);
+    st = launch_point_values(p, G, s);
+    if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fsorted, 0))) st = IB_ERR_CUDA;
+    if (st == IB_OK) st = launch_permute_values(p, s);
+  }
   if (st == IB_OK) st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s);
-  if (st == IB_OK) st = do_interp_tail(p, u, U, s);
+  if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   return check_launch(st);
 }
 

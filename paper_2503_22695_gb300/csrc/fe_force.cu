@@ -115,6 +115,9 @@ __device__ __forceinline__ double log1p_d(double x) {
   return 2.0 * s * t;
 }
 
+__device__ __forceinline__ double log1p_s(double x) { return log1p_d(x); }
+__device__ __forceinline__ float log1p_s(float x) { return log1pf(x); }
+
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
 __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
     S trH2 = S(H[0][0]) * S(H[0][0]) + S(H[1][1]) * S(H[1][1]) + S(H[2][2]) * S(H[2][2]);
     trH2 += S(2) * (S(H[0][1]) * S(H[1][0]) + S(H[0][2]) * S(H[2][0]) + S(H[1][2]) * S(H[2][1]));
     const S Jm1 = trS + S(0.5) * (trS * trS - trH2) + S(det3(H));
-    const S lnJs = log1p_d(double(Jm1));
+    const S lnJs = log1p_s(Jm1);
     const Real lnJ = Real(lnJs);
     const Real J = Real(S(1) + Jm1);
     Real F[3][3];
@@ -596,7 +599,10 @@ ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, 
   FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
   const int threads = 128;
   const int blocks = (p->E + threads - 1) / threads;
-  k_fe<Real, double, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
+  if (p->precision == IB_FP32_SPLIT_F32STAB)
+    k_fe<Real, Real, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
+  else
+    k_fe<Real, double, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

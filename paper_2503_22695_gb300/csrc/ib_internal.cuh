@@ -82,9 +82,11 @@ struct ib_plan {
   int32_t* tile_counters;// [8] non-empty count, work counters, near count
   int32_t* digit_tot;    // [256] radix digit totals
   double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*9] reduction partials
-  cudaStream_t side;     // second stream for work that overlaps the main one
-  cudaEvent_t ev_fork, ev_join;
-  int sm_count, push_ctas, merge_ctas, interp_ctas;
+  cudaStream_t side;     // interpolation branch of ib_forward
+  cudaStream_t zside;    // far-tile zero-fill of the spread
+  cudaEvent_t ev_fork, ev_join;      // spread zero-fill fork / join
+  cudaEvent_t ev_ffork, ev_fsorted, ev_fjoin;  // ib_forward branch events
+  int sm_count, push_ctas, merge_ctas, interp_ctas[3];
   void* spread_scratch;  // Real [slots][3][12^3] halo'd per-tile blocks
   int32_t* q_cell;       // packed wrapped cell per Gauss point (unsorted, gq order)
   void* q_off;           // Real [3][Q]
@@ -134,6 +136,9 @@ ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
 ib_status launch_points(ib_plan* p, const void* x_cell_or_x64, const float* off,
                         const void* nodal, int val_kind, cudaStream_t s);
 ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s);
+// Carried values of already-built points (unsorted q_val), and their sorted copy.
+ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s);
+ib_status launch_permute_values(ib_plan* p, cudaStream_t s);
 
 // spread.cu
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s);

@@ -127,6 +127,50 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   }
 }
 
+// Carried values only (positions already built): V_q = w_q j0 sum_a N_a V_a / m_a.
+template <typename Real>
+__global__ void __launch_bounds__(128) k_point_values(int E, int64_t N,
+                                                     const int32_t* __restrict__ conn,
+                                                     const Real* __restrict__ V,
+                                                     const Real* __restrict__ inv_mass,
+                                                     const Real* __restrict__ wj0,
+                                                     Real* __restrict__ q_val) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int64_t Q = 8LL * E;
+  Real Vn[8][3];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int node = __ldg(conn + a * E + e);
+    const Real im = __ldg(inv_mass + node);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Vn[a][d] = __ldg(V + d * N + node) * im;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t gq = (int64_t)q * E + e;
+    const Real w = __ldg(wj0 + gq);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Real s = Real(0);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) s += Real(shapeN(a, q)) * Vn[a][d];
+      q_val[d * Q + gq] = w * s;
+    }
+  }
+}
+
+// Sorted copies of the carried values.
+template <typename Real>
+__global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
+                                 const Real* __restrict__ q_val, Real* __restrict__ p_val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const int32_t g = __ldg(p_idx + i);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p_val[d * Q + i] = __ldg(q_val + d * Q + g);
+}
+
 // ---------------------------------------------------------------------------
 // radix sort pieces
 // ---------------------------------------------------------------------------
@@ -330,6 +374,31 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
     k_permute<float><<<nb, tb, 0, s>>>(p->vals[cur], Q, p->q_cell, (const float*)p->q_off,
                                        (const float*)p->q_val, p->p_cell, (float*)p->p_off,
                                        (float*)p->p_val, p->p_idx, with_val);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
+  if (p->E == 0) return IB_OK;
+  if (p->precision == IB_FP64)
+    k_point_values<double><<<(p->E + 127) / 128, 128, 0, s>>>(
+        p->E, p->N, p->conn, (const double*)nodal, (const double*)p->inv_mass,
+        (const double*)p->wj0, (double*)p->q_val);
+  else
+    k_point_values<float><<<(p->E + 127) / 128, 128, 0, s>>>(
+        p->E, p->N, p->conn, (const float*)nodal, (const float*)p->inv_mass,
+        (const float*)p->wj0, (float*)p->q_val);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+ib_status launch_permute_values(ib_plan* p, cudaStream_t s) {
+  if (p->Q == 0) return IB_OK;
+  const int nb = (int)((p->Q + 255) / 256);
+  if (p->precision == IB_FP64)
+    k_permute_values<double><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
+                                                (double*)p->p_val);
+  else
+    k_permute_values<float><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val,
+                                               (float*)p->p_val);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

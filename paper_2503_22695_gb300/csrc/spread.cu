@@ -10,36 +10,40 @@
 //   "far" tile (no points in its 3x3x3 neighbourhood) writes its zeros with
 //   16-byte stores: the bulk of the field's HBM traffic overlaps the
 //   accumulation work.
-// k_spread_push (persistent CTAs pulling tiles from a work counter) -- a
-//   tile holding Gauss points accumulates every stencil entry of its own
-//   points into a halo'd 12^3 block per component (its points reach two cells
-//   beyond the tile; indices stay unwrapped), one component at a time.
-//   Points are staged in batches of 256 (one thread per point computes the
-//   3x4 kernel weights); point k of a batch goes to warp k mod 8, each warp
-//   adding into its own shared-memory copy, one point per step (32 lanes x 2
-//   entries = the 64 stencil entries of one component, all distinct faces),
-//   steps ordered by __syncwarp.  The eight copies are summed in warp order
-//   and the block is written to the work item's scratch block.  A work item is
-//   at most 1024 consecutive points of one tile, so densely populated tiles
-//   are shared by several CTAs.
+// k_spread_push (persistent CTAs pulling work items from a counter; a work
+//   item is at most 1024 consecutive points of one tile, so densely populated
+//   tiles are shared by several CTAs) -- the item's points are accumulated
+//   into a halo'd 12^3 block per component (they reach two cells beyond the
+//   tile; indices stay unwrapped), one component at a time.  The item's raw
+//   point data are copied to shared memory once (cp.async, all in flight);
+//   points are then staged 128 at a time (one thread per point computes the
+//   3x4 kernel weights).  Each half-warp owns a private shared-memory copy of the block
+//   and takes the staged points k, k+8, ... in order, one point per step: its
+//   16 lanes cover the 16 (dz, dy) rows of the 4x4x4 stencil, four faces per
+//   lane, all distinct; steps are ordered by __syncwarp.  The eight copies
+//   are summed in copy order into the item's scratch block.
 // k_spread_merge -- for every "near" tile, each face sums the blocks of its
 //   own tile and of the neighbours whose halo covers it (at most two per
-//   axis), in a fixed (z, y, x) source order and, within a source tile, in
-//   work-item order, and is written once.  Periodic
-//   wrap happens only here, through the neighbour-tile index.
+//   axis), in ascending (z, y, x) source order and, within a source tile, in
+//   work-item order, and is written once.  Periodic wrap happens only here,
+//   through the neighbour-tile index.
 #include "ib_device.cuh"
 
 namespace ibfe {
 namespace {
 
-constexpr int W = kSpreadWarps;         // 8 warps
-constexpr int kThreads = W * 32;
 constexpr int kB = 12;                  // halo'd block edge: tile 8 + 2 + 2
 constexpr int kBlk = kB * kB * kB;      // 1728 faces per component
+constexpr int kItemBlk = 3 * kBlk;      // scratch block of one work item
 constexpr int kSY = kB;                 // shared y stride
-constexpr int kSZ = kB * kB + 1;        // shared z stride (145: spreads (dz,dy) over banks)
-constexpr int kAcc = kB * kSZ;          // 1740 per warp copy
-constexpr int kBatch = kThreads;        // points staged per batch
+constexpr int kSZ = kB * kB + 1;        // shared z stride (145: the 16 (dz,dy) rows hit 16 banks)
+constexpr int kAcc = kB * kSZ;          // 1740 per private copy (multiple of 4)
+constexpr int kPW = 4;                  // warps per push CTA
+constexpr int kPT = kPW * 32;           // push threads
+constexpr int kCopies = 2 * kPW;        // one private copy per half-warp
+constexpr int kBatch = kPT;             // points staged per batch
+constexpr int kMT = 256;                // merge / zero threads
+constexpr int kMW = kMT / 32;
 
 template <typename Real>
 struct SpreadArgs {
@@ -52,14 +56,24 @@ struct SpreadArgs {
   const int32_t* tile_near;
   const int32_t* tile_list;    // tile of each work item
   const int32_t* tile_list_near;
-  int32_t* counters;      // [0] non-empty tiles, [1] work counter, [3] near tiles
+  int32_t* counters;           // [0] work items, [1] work counter, [3] near tiles
   const int32_t* p_cell;
   const Real* p_off;
   const Real* p_val;
   Real scale;
-  Real* scratch;   // [slots][3][12^3]
+  Real* scratch;               // [items][3][12^3]
   Real* f;
+  uint32_t* absmax;            // bits of max |value| over all points (fixed-point scale)
 };
+
+// cp.async of 4 bytes global -> shared (completion awaited with cp_async_wait)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 // staged point: x/y/z weights, value, row origin in the halo'd block
 template <typename Real>
@@ -69,96 +83,133 @@ struct alignas(16) Staged {
   Real wz[4];
   Real val;
   int org;
-  int pad[2];
 };
 
 __device__ __forceinline__ int tile_of(int tx, int ty, int tz, const GridDev& g) {
   return wrap_idx(tx, g.nt[0]) + g.nt[0] * (wrap_idx(ty, g.nt[1]) + g.nt[1] * wrap_idx(tz, g.nt[2]));
 }
 
-// One lane adds into one face per step; __syncwarp between steps orders the
-// read-modify-writes of different lanes to the same face.
+// One lane adds into one face per step and steps are ordered by __syncwarp,
+// so every face receives its contributions in point order.
 template <typename Real>
 __device__ __forceinline__ void add_shared(Real* p, Real v) {
   *p += v;
 }
 
-// Work item `slot`: points [start + j kChunk, min(end, start + (j+1) kChunk))
-// of `tile`, j = slot - first item of the tile.
 template <typename Real>
-__device__ __forceinline__ void push_tile(const SpreadArgs<Real>& A, int slot, Staged<Real>* stage,
-                                          Real* acc, int tid, int lane, int warp, int nt0,
-                                          int nt1) {
+__device__ __forceinline__ void zero_shared(Real* p, int n, int tid, int nthreads) {
+  float4* v = reinterpret_cast<float4*>(p);
+  const int n4 = n * (int)sizeof(Real) / 16;
+  for (int i = tid; i < n4; i += nthreads) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Work item `slot`: points [start + j kChunk, min(end, start + (j+1) kChunk))
+// of its tile, j = slot - first item of the tile.
+// Raw point data of one work item, copied to shared memory once.
+template <typename Real>
+struct RawItem {
+  int32_t cell[kChunk];
+  Real off[3][kChunk];
+  Real val[3][kChunk];
+};
+
+template <typename Real>
+__device__ __forceinline__ void push_item(const SpreadArgs<Real>& A, int slot, Staged<Real>* stage,
+                                          Real* acc, RawItem<Real>* raw, int tid) {
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int tile = A.tile_list[slot];
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
   const int e = min(A.tile_end[tile], s + kChunk);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
-  Real* my = acc + warp * kAcc;
-  // this lane's two stencil entries of a component: row (dz, dy), dx = 2h, 2h+1
-  const int r = lane >> 1, dz = r >> 2, dy = r & 3, hx = (lane & 1) * 2;
-  const int lane_off = dz * kSZ + dy * kSY + hx;
+  const int hw = tid >> 4, l16 = tid & 15, dz = l16 >> 2, dy = l16 & 3;
+  const int warp = tid >> 5;
+  Real* my = acc + hw * kAcc;
+  const int lane_off = dz * kSZ + dy * kSY;
+  const int n = e - s;
+  // every load of the item in flight at once
+  for (int i = tid; i < n; i += kPT) {
+    cp_async4(&raw->cell[i], A.p_cell + s + i);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (sizeof(Real) == 4) {
+        cp_async4(&raw->off[d][i], A.p_off + d * A.Q + s + i);
+        cp_async4(&raw->val[d][i], A.p_val + d * A.Q + s + i);
+      } else {
+        raw->off[d][i] = A.p_off[d * A.Q + s + i];
+        raw->val[d][i] = A.p_val[d * A.Q + s + i];
+      }
+    }
+  }
+  cp_async_wait();
 
   for (int c = 0; c < 3; ++c) {
-    for (int i = tid; i < W * kAcc; i += kThreads) acc[i] = Real(0);
+    zero_shared(acc, kCopies * kAcc, tid, kPT);
     for (int b0 = s; b0 < e; b0 += kBatch) {
       const int nb = min(kBatch, e - b0);
       __syncthreads();  // previous batch consumed, accumulators zeroed
       if (tid < nb) {
-        const int i = b0 + tid;
+        const int i = b0 - s + tid;
         int cx, cy, cz;
-        unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
+        unpack_cell(raw->cell[i], cx, cy, cz);
         Staged<Real> st;
         Real th;
-        const int bx = cx - x0 + stencil_axis(__ldg(A.p_off + i), c != 0, th) + 2;
+        const int bx = cx - x0 + stencil_axis(raw->off[0][i], c != 0, th) + 2;
         delta_weights(th, st.wx);
-        const int by = cy - y0 + stencil_axis(__ldg(A.p_off + A.Q + i), c != 1, th) + 2;
+        const int by = cy - y0 + stencil_axis(raw->off[1][i], c != 1, th) + 2;
         delta_weights(th, st.wy);
-        const int bz = cz - z0 + stencil_axis(__ldg(A.p_off + 2 * A.Q + i), c != 2, th) + 2;
+        const int bz = cz - z0 + stencil_axis(raw->off[2][i], c != 2, th) + 2;
         delta_weights(th, st.wz);
-        st.val = __ldg(A.p_val + c * A.Q + i) * A.scale;
+        st.val = raw->val[c][i] * A.scale;
         st.org = bz * kSZ + by * kSY + bx;
         stage[tid] = st;
       }
       __syncthreads();
-      // software pipelined: the next point's staged values are read while the
-      // current point's read-modify-writes are in flight
-      int p = warp;
-      Real a0 = Real(0), a1 = Real(0);
+      // The warp's two half-warps take points hw + 8k; the loop runs the
+      // even half's trip count (never smaller) so __syncwarp sees the full
+      // warp.  The next point's staged values are read before the current
+      // point's read-modify-writes.
+      const int steps = nb > 2 * warp ? (nb - 2 * warp + kCopies - 1) / kCopies : 0;
+      int p = hw;
+      Real w = Real(0), wx[4] = {Real(0), Real(0), Real(0), Real(0)};
       int o = 0;
       if (p < nb) {
         const Staged<Real>& st = stage[p];
-        const Real w = st.val * st.wz[dz] * st.wy[dy];
-        a0 = w * st.wx[hx];
-        a1 = w * st.wx[hx + 1];
+        w = st.val * st.wz[dz] * st.wy[dy];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wx[k] = st.wx[k];
         o = st.org + lane_off;
       }
-      for (; p < nb; p += W) {
-        Real b0 = Real(0), b1 = Real(0);
-        int ob = 0;
-        if (p + W < nb) {
-          const Staged<Real>& st = stage[p + W];
-          const Real w = st.val * st.wz[dz] * st.wy[dy];
-          b0 = w * st.wx[hx];
-          b1 = w * st.wx[hx + 1];
-          ob = st.org + lane_off;
+      for (int k = 0; k < steps; ++k, p += kCopies) {
+        Real wn = Real(0), wxn[4] = {Real(0), Real(0), Real(0), Real(0)};
+        int on = 0;
+        if (p + kCopies < nb) {
+          const Staged<Real>& st = stage[p + kCopies];
+          wn = st.val * st.wz[dz] * st.wy[dy];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) wxn[kk] = st.wx[kk];
+          on = st.org + lane_off;
         }
-        add_shared(my + o, a0);
-        add_shared(my + o + 1, a1);
+        if (p < nb) {
+          Real* q = my + o;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) add_shared(q + kk, w * wx[kk]);
+        }
         __syncwarp();
-        a0 = b0;
-        a1 = b1;
-        o = ob;
+        w = wn;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) wx[kk] = wxn[kk];
+        o = on;
       }
     }
     __syncthreads();
     Real* out = A.scratch + ((int64_t)slot * 3 + c) * kBlk;
-    for (int idx = tid; idx < kBlk; idx += kThreads) {
+    for (int idx = tid; idx < kBlk; idx += kPT) {
       const int z = idx / (kB * kB), y = (idx / kB) % kB, x = idx % kB;
       const int o = z * kSZ + y * kSY + x;
       Real sum = Real(0);
 #pragma unroll
-      for (int w = 0; w < W; ++w) sum += acc[w * kAcc + o];
+      for (int w = 0; w < kCopies; ++w) sum += acc[w * kAcc + o];
       out[idx] = sum;
     }
     __syncthreads();
@@ -166,13 +217,14 @@ __device__ __forceinline__ void push_tile(const SpreadArgs<Real>& A, int slot, S
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) k_spread_push(SpreadArgs<Real> A) {
+__global__ void __launch_bounds__(kPT) k_spread_push(SpreadArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Staged<Real>* stage = reinterpret_cast<Staged<Real>*>(smem_raw);
   Real* acc = reinterpret_cast<Real*>(smem_raw + sizeof(Staged<Real>) * kBatch);
+  RawItem<Real>* raw = reinterpret_cast<RawItem<Real>*>(
+      smem_raw + sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc);
   __shared__ int next;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int tid = threadIdx.x;
   const int count = A.counters[0];
   for (;;) {
     __syncthreads();
@@ -180,15 +232,151 @@ __global__ void __launch_bounds__(kThreads) k_spread_push(SpreadArgs<Real> A) {
     __syncthreads();
     const int k = next;
     if (k >= count) break;
-    push_tile(A, k, stage, acc, tid, lane, warp, nt0, nt1);
+    push_item(A, k, stage, acc, raw, tid);
   }
 }
 
-// Far tiles: one warp per tile, 3 components x 64 rows x 2 x 16-byte zeros.
+// ---------------------------------------------------------------------------
+// FP32 plans: order-independent fixed-point accumulation.
+//
+// Every contribution c = V prod phi of an item is converted to an integer
+// multiple of 2^-(k+20) split into a high word round(c 2^k) (|.| < 2^20) and a
+// low word round((c - hi 2^-k) 2^(k+20)) (|.| < 2^19), and both words are
+// added with native 32-bit shared-memory atomics into one block per CTA.
+// Integer addition is exact and associative, so the block is the same
+// whatever the order of the additions; with at most 1024 points per item no
+// word overflows.  k comes from the largest |V| of the call (one integer
+// atomicMax over the float bit patterns), so that |c| 2^k < 2^20 since every
+// kernel weight product is at most 1/8.  The resolution 2^-(k+20) is 2^-40 of
+// the largest contribution; each block value is rounded once to float.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ v, int64_t n,
+                                               uint32_t* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(v[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic holds round(x) in its low bits
+constexpr int kMagicBits = 0x4B400000;
+constexpr int kFxThreads = 256;
+constexpr int kFxBatch = kFxThreads;
+
+struct alignas(16) StagedFx {
+  float w[3][2][4];  // [axis][staggering: 0 = s 0, 1 = s 1/2][4 weights]
+  float val[3];
+  int org[3];        // row origin of component c in the halo'd block
+  int pad[2];
+};
+
+__device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float c, float s1, float is1,
+                                       float s2) {
+  const float t1 = fmaf(c, s1, kMagic);
+  const int h = __float_as_int(t1) - kMagicBits;
+  const float r = fmaf(-(t1 - kMagic), is1, c);
+  const int l = __float_as_int(fmaf(r, s2, kMagic)) - kMagicBits;
+  atomicAdd(hi, (unsigned)h);
+  atomicAdd(lo, (unsigned)l);
+}
+
+__global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StagedFx* stage = reinterpret_cast<StagedFx*>(smem_raw);
+  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(StagedFx) * kFxBatch);
+  unsigned* acc_lo = acc_hi + 3 * kAcc;
+  __shared__ int next;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int count = A.counters[0];
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  // fixed-point scale of the call
+  const float cmax = 0.125f * __uint_as_float(*A.absmax) * fabsf(A.scale);
+  int ex = 0;
+  if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
+  const int k = min(19 - ex, 106);  // keep 2^(k+20) a normal float
+  const float s1 = ldexpf(1.f, k), is1 = ldexpf(1.f, -k), s2 = ldexpf(1.f, k + 20);
+  const float out_scale = ldexpf(1.f, -(k + 20));
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) next = atomicAdd(A.counters + 1, 1);
+    __syncthreads();
+    const int slot = next;
+    if (slot >= count) break;
+    const int tile = A.tile_list[slot];
+    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
+    const int e = min(A.tile_end[tile], s + kChunk);
+    const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
+    for (int i = tid; i < 3 * kAcc * 2 / 4; i += kFxThreads)
+      reinterpret_cast<uint4*>(acc_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int b0 = s; b0 < e; b0 += kFxBatch) {
+      const int nb = min(kFxBatch, e - b0);
+      __syncthreads();  // accumulators zeroed / previous batch consumed
+      if (tid < nb) {
+        const int i = b0 + tid;
+        int cc[3];
+        unpack_cell(__ldg(A.p_cell + i), cc[0], cc[1], cc[2]);
+        StagedFx st;
+        int b[3][2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float off = __ldg(A.p_off + d * A.Q + i);
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+            float th;
+            b[d][hf] = cc[d] - lc0[d] + stencil_axis(off, hf == 1, th) + 2;
+            delta_weights(th, st.w[d][hf]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          st.val[c] = __ldg(A.p_val + c * A.Q + i) * A.scale;
+          st.org[c] = c * kAcc + b[2][c != 2] * kSZ + b[1][c != 1] * kSY + b[0][c != 0];
+        }
+        stage[tid] = st;
+      }
+      __syncthreads();
+      // two points per warp step: 96 (point, component, dz, dy) rows, three
+      // per lane, four faces per row
+      for (int p0 = 2 * warp; p0 < nb; p0 += 2 * (kFxThreads / 32)) {
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+          const int r = lane + 32 * rr;
+          const int pt = p0 + (r >= 48 ? 1 : 0);
+          if (pt >= nb) continue;
+          const int q = r >= 48 ? r - 48 : r;
+          const int c = q >> 4, dz = (q >> 2) & 3, dy = q & 3;
+          const StagedFx& st = stage[pt];
+          const float w = st.val[c] * st.w[2][c != 2][dz] * st.w[1][c != 1][dy];
+          const float4 wx = *reinterpret_cast<const float4*>(st.w[0][c != 0]);
+          const int o = st.org[c] + dz * kSZ + dy * kSY;
+          fx_add(acc_hi + o, acc_lo + o, w * wx.x, s1, is1, s2);
+          fx_add(acc_hi + o + 1, acc_lo + o + 1, w * wx.y, s1, is1, s2);
+          fx_add(acc_hi + o + 2, acc_lo + o + 2, w * wx.z, s1, is1, s2);
+          fx_add(acc_hi + o + 3, acc_lo + o + 3, w * wx.w, s1, is1, s2);
+        }
+      }
+    }
+    __syncthreads();
+    float* out = A.scratch + (int64_t)slot * kItemBlk;
+    for (int idx = tid; idx < kItemBlk; idx += kFxThreads) {
+      const int c = idx / kBlk, rr = idx % kBlk;
+      const int z = rr / (kB * kB), y = (rr / kB) % kB, x = rr % kB;
+      const int o = c * kAcc + z * kSZ + y * kSY + x;
+      const long long v = ((long long)(int)acc_hi[o] << 20) + (long long)(int)acc_lo[o];
+      out[idx] = __ll2float_rn(v) * out_scale;
+    }
+  }
+}
+
+// Far tiles: one warp per tile, 3 components x 64 rows x 16-byte zeros.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) k_spread_zero(SpreadArgs<Real> A) {
+__global__ void __launch_bounds__(kMT) k_spread_zero(SpreadArgs<Real> A) {
   const int lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * W + (threadIdx.x >> 5);
+  const int tile = blockIdx.x * kMW + (threadIdx.x >> 5);
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   if (tile >= nt0 * nt1 * A.g.nt[2] || A.tile_near[tile]) return;
   const int n0 = A.g.n[0], n1 = A.g.n[1];
@@ -206,8 +394,15 @@ __global__ void __launch_bounds__(kThreads) k_spread_zero(SpreadArgs<Real> A) {
 }
 
 // Near tiles: fixed-order sum of the halo'd blocks that cover each face.
+// Source (ox, oy, oz) covers local face (x, y, z) when each offset is 0, or
+// -1 with the coordinate <= 1, or +1 with it >= 6; the face is then at block
+// index (x - 8 ox + 2, y - 8 oy + 2, z - 8 oz + 2).  One thread per x-row of 8
+// faces (component, z, y): for each (oz, oy) source pair in order it reads
+// the row's own-tile part (block x 2..9) and, for faces 0,1 and 6,7, the
+// x-neighbours' halo pairs (block x 10,11 of ox = -1 and 0,1 of ox = +1),
+// and adds them face by face in the order (oz, oy, ox).
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) k_spread_merge(SpreadArgs<Real> A) {
+__global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   __shared__ int src_slot[27], src_n[27];
   const int tid = threadIdx.x;
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
@@ -226,26 +421,60 @@ __global__ void __launch_bounds__(kThreads) k_spread_merge(SpreadArgs<Real> A) {
       src_n[tid] = A.tile_nitems[nb];
     }
     __syncthreads();
-    for (int idx = tid; idx < 3 * 512; idx += kThreads) {
-      const int c = idx >> 9, rr = idx & 511;
-      const int z = rr >> 6, y = (rr >> 3) & 7, x = rr & 7;
-      // source offsets along each axis: own tile, and the neighbour whose halo
-      // reaches this face (faces 0..1 from below, 6..7 from above)
-      const int lx = x <= 1 ? -1 : 0, ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
-      const int hx = x >= 6 ? 1 : 0, hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
-      Real sum = Real(0);
+    if (tid < 3 * 64) {
+      const int c = tid >> 6, z = (tid >> 3) & 7, y = tid & 7;
+      const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
+      const int hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
+      Real sum[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) sum[x] = Real(0);
       for (int oz = lz; oz <= hz; ++oz)
-        for (int oy = ly; oy <= hy; ++oy)
-          for (int ox = lx; ox <= hx; ++ox) {
-            const int si = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
-            const int sl = src_slot[si], ns = src_n[si];
-            const int bx = x - ox * kTile + 2, by = y - oy * kTile + 2, bz = z - oz * kTile + 2;
-            for (int j = 0; j < ns; ++j)  // the tile's work items in order
-              sum += A.scratch[((int64_t)(sl + j) * 3 + c) * kBlk + (bz * kB + by) * kB + bx];
+        for (int oy = ly; oy <= hy; ++oy) {
+          const int rowoff = c * kBlk + ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * kB;
+          const int s0 = (oz + 1) * 9 + (oy + 1) * 3;
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int sl = src_slot[s0 + ox + 1], ns = src_n[s0 + ox + 1];
+            for (int j = 0; j < ns; ++j) {
+              const Real* r = A.scratch + (int64_t)(sl + j) * kItemBlk + rowoff;
+              if (ox < 0) {          // faces 0,1 from the left neighbour's block x 10,11
+                sum[0] += r[10];
+                sum[1] += r[11];
+              } else if (ox > 0) {   // faces 6,7 from the right neighbour's block x 0,1
+                sum[6] += r[0];
+                sum[7] += r[1];
+              } else {
+                Real v[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) v[x] = r[2 + x];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) sum[x] += v[x];
+              }
+            }
           }
-      A.f[c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + (x0 + x)] = sum;
+        }
+      Real* out = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) out[x] = sum[x];
     }
   }
+}
+
+template <typename Real>
+size_t push_smem() {
+  return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
+}
+
+constexpr size_t kFxSmem = sizeof(StagedFx) * kFxBatch + sizeof(unsigned) * 2 * 3 * kAcc;
+
+void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
+  cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
+  if (p->Q > 0)
+    k_absmax<<<p->sm_count * 4, 256, 0, s>>>((const float*)p->p_val, 3 * p->Q, A.absmax);
+  k_spread_push_fx<<<p->push_ctas, kFxThreads, kFxSmem, s>>>(A);
+}
+
+void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
+  k_spread_push<double><<<p->push_ctas, kPT, push_smem<double>(), s>>>(A);
 }
 
 template <typename Real>
@@ -267,52 +496,41 @@ ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
   A.scale = (Real)scale;
   A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;
-  const size_t smem = sizeof(Staged<Real>) * kBatch + sizeof(Real) * W * kAcc;
+  A.absmax = reinterpret_cast<uint32_t*>(p->tile_counters + 5);
   cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
   // far-tile zeros on the side stream, concurrent with the push
   cudaEventRecord(p->ev_fork, s);
-  cudaStreamWaitEvent(p->side, p->ev_fork, 0);
-  k_spread_zero<Real><<<(p->ntiles + W - 1) / W, kThreads, 0, p->side>>>(A);
-  cudaEventRecord(p->ev_join, p->side);
-  const int push_ctas = min(p->ntiles, p->push_ctas);
-  k_spread_push<Real><<<push_ctas, kThreads, smem, s>>>(A);
-  const int merge_ctas = min(p->ntiles, p->merge_ctas);
-  k_spread_merge<Real><<<merge_ctas, kThreads, 0, s>>>(A);
+  cudaStreamWaitEvent(p->zside, p->ev_fork, 0);
+  k_spread_zero<Real><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
+  cudaEventRecord(p->ev_join, p->zside);
+  launch_push(p, A, s);
+  k_spread_merge<Real><<<p->merge_ctas, kMT, 0, s>>>(A);
   cudaStreamWaitEvent(s, p->ev_join, 0);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
-}  // namespace
-
-size_t spread_smem_bytes(int precision) {
-  return precision == IB_FP64 ? sizeof(Staged<double>) * kBatch + sizeof(double) * W * kAcc
-                              : sizeof(Staged<float>) * kBatch + sizeof(float) * W * kAcc;
-}
-
-size_t spread_scratch_bytes(int precision, int64_t slots) {
-  return (size_t)slots * 3 * kBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(float));
-}
-
-ib_status spread_prepare(ib_plan* p) {
-  const int smem = (int)spread_smem_bytes(p->precision);
+template <typename Real>
+ib_status prepare_t(ib_plan* p) {
   int dev = 0, sms = 0, per_sm = 0, per_sm_merge = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return IB_ERR_CUDA;
   cudaError_t e;
-  if (p->precision == IB_FP64) {
-    e = cudaFuncSetAttribute(k_spread_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (sizeof(Real) == 4) {
+    e = cudaFuncSetAttribute(k_spread_push_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFxSmem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<double>, kThreads, smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<double>, kThreads, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push_fx, kFxThreads,
+                                                        kFxSmem);
   } else {
-    e = cudaFuncSetAttribute(k_spread_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)push_smem<Real>();
+    e = cudaFuncSetAttribute(k_spread_push<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<float>, kThreads, smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<float>, kThreads, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<Real>, kPT, smem);
   }
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<Real>, kMT, 0);
   if (e != cudaSuccess || per_sm < 1 || per_sm_merge < 1) return IB_ERR_CUDA;
   p->sm_count = sms;
   p->push_ctas = sms * per_sm;
@@ -320,7 +538,17 @@ ib_status spread_prepare(ib_plan* p) {
   return IB_OK;
 }
 
-int spread_launches() { return 3; }
+}  // namespace
+
+size_t spread_scratch_bytes(int precision, int64_t slots) {
+  return (size_t)slots * kItemBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(float));
+}
+
+ib_status spread_prepare(ib_plan* p) {
+  return p->precision == IB_FP64 ? prepare_t<double>(p) : prepare_t<float>(p);
+}
+
+int spread_launches() { return 4; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
   return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, s)

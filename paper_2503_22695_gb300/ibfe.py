@@ -27,7 +27,7 @@ LIB_PATH = os.path.join(_HERE, "libibfe.so")
 IB_OK, IB_ERR_INVALID_ARG, IB_ERR_CUDA, IB_ERR_NONFINITE = 0, 1, 2, 3
 IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 7
 IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO = 0, 1, 2
-IB_FP32_SPLIT, IB_FP64 = 0, 1
+IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
 IB_MAX_MATERIALS = 8
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
 N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9}
