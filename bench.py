@@ -345,6 +345,46 @@ def run_ours(args):
     h2d = (h_cell.numel() * 4 + h_off.numel() * 4 + h_u.numel() * 4)
     d2h = (h_G.numel() + h_f.numel() + h_U.numel()) * 4
 
+    # --- batched workload: 48 HO shells on their own grids, one graph -----
+    batch_line = None
+    if not args.no_batch:
+        bprobs = I.batch_problems(seed=5000 + 97 * rank)
+        brng = np.random.default_rng(5 + rank)
+        binst = []
+        for bp in bprobs:
+            N_i, sh = bp.n_nodes, (3,) + tuple(bp.u.shape[1:])
+            binst.append(dict(
+                conn=torch.from_numpy(bp.conn).to(dev), X=torch.from_numpy(bp.X).to(dev),
+                fibres=torch.from_numpy(bp.fibres).to(dev),
+                mat_id=torch.from_numpy(bp.mat_id).to(dev), n=bp.grid.n, h=bp.grid.h,
+                mats=[ibfe.Material(m.model, m.params) for m in bp.materials],
+                cell=torch.from_numpy(bp.cell).to(dev), off=torch.from_numpy(bp.off).to(dev),
+                u=torch.from_numpy(bp.u).to(dev),
+                G=torch.empty((3, N_i), device=dev), f=torch.empty(sh, device=dev),
+                U=torch.empty((3, N_i), device=dev),
+                gU=torch.from_numpy(brng.normal(size=(3, N_i)).astype(np.float32)).to(dev),
+                gf=torch.from_numpy((brng.normal(size=sh) * 1e-3).astype(np.float32)).to(dev),
+                gu=torch.empty(sh, device=dev), gx=torch.empty((3, N_i), device=dev),
+                gG=torch.empty((3, N_i), device=dev), Hv=torch.empty((3, N_i), device=dev)))
+        batch = ibfe.Batch(binst)
+        for _ in range(args.warmup):
+            batch.forward()
+            batch.adjoint()
+        barrier()
+        ms_bf = timed(batch.forward, args.steps)
+        ms_ba = timed(batch.adjoint, args.steps)
+        qb = sum(bp.n_gauss for bp in bprobs)
+        tbf, tba = sum(ms_bf) / len(ms_bf), sum(ms_ba) / len(ms_ba)
+        batch_line = {
+            "workload": f"{len(bprobs)} HO ventricle-like shells, grids 32^3..128^3, "
+                        f"{min(bp.n_elems for bp in bprobs)}..{max(bp.n_elems for bp in bprobs)} "
+                        f"hexes each, {qb} Gauss points; one CUDA-graph launch per pass",
+            "gauss_points": qb, "forward_ms": tbf, "adjoint_ms": tba,
+            "forward_value": qb / (tbf * 1e-3), "unit": UNIT,
+            "adjoint_forward_ratio": tba / tbf}
+        del batch, binst
+        barrier()
+
     # --- max over ranks ----------------------------------------------------
     tt = torch.tensor([t_fwd, t_adj, t_e2e], device=dev, dtype=torch.float64)
     if world > 1:
@@ -411,6 +451,7 @@ def run_ours(args):
         "fp32_scalars": {"ms_per_step": t_fwd32, "value": Q * world / (t_fwd32 * 1e-3),
                          "note": "same forward with J-1, ln J and fibre invariants in FP32 "
                                  "(IB_FP32_SPLIT_F32STAB)"},
+        "batched": batch_line,
         "adjoint_ms_per_step": t_adj,
         "adjoint_forward_ratio": t_adj / t_fwd,
         "roofline": roof,
@@ -441,6 +482,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shell256", choices=["shell256", "shell128"],
                     help="shell128 (128^3 ventricle shell) is a small case for profiling")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
     args = ap.parse_args()

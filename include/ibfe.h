@@ -172,6 +172,49 @@ ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats
                           const ib_pos* x, const void* v, void* Hv, double* gparams,
                           void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent structures, each with its own mesh, grid
+ * and material table (a parameter sweep, for instance), run together.  The
+ * paper runs one structure at a time; batching is a service of this library.
+ * ib_batch_create builds one plan per instance and captures two CUDA graphs
+ * whose branches are the instances' forward coupling (ib_forward) and
+ * adjoint (ib_interp_adj with position gradient, ib_spread_adj with position
+ * gradient, ib_fe_force_adj of the spread cotangent's nodal part, parameter
+ * gradients kept on the device); each graph is then replayed with one
+ * launch.  All pointers in ib_instance are device memory that must stay
+ * valid and fixed for the batch's lifetime (the graphs bake them in); update
+ * the data in place between replays.  Synchronises `stream` at creation.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  ib_mesh mesh;
+  ib_grid grid;
+  int32_t n_mats;
+  ib_material mats[IB_MAX_MATERIALS]; /* host copy taken at creation */
+  ib_pos x;
+  const void* u;  /* [3][grid] */
+  void* G;        /* [3][N]   forward outputs */
+  void* f;        /* [3][grid] */
+  void* U;        /* [3][N] */
+  const void* gU; /* [3][N]    adjoint inputs (cotangents of U and f); NULL: no adjoint */
+  const void* gf; /* [3][grid] */
+  void* gu;       /* [3][grid] adjoint outputs: d/du */
+  void* gx;       /* [3][N]    d/dx from interpolation and spreading */
+  void* gG;       /* [3][N]    d/dG from spreading */
+  void* Hv;       /* [3][N]    (dG/dx) gG: the force kernel's position term */
+} ib_instance;
+
+typedef struct ib_batch ib_batch;
+
+ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision, void* stream,
+                          ib_batch** out);
+/* Replay the forward (resp. adjoint) graph on `stream` (asynchronous). */
+ib_status ib_batch_forward(ib_batch* batch, void* stream);
+ib_status ib_batch_adjoint(ib_batch* batch, void* stream);
+/* Parameter gradients v . dG/dtheta of every instance's last adjoint replay,
+ * host double [n][IB_MAX_MATERIALS][9]; synchronises `stream`. */
+ib_status ib_batch_gparams(ib_batch* batch, double* gparams, void* stream);
+ib_status ib_batch_destroy(ib_batch* batch);
+
 /* Total elastic energy sum_{e,q} Psi(F_q) w_q j0 of an FP32 split-position
  * mesh, without a plan and without allocating anything, for callers that
  * cannot call cudaMalloc: code running while a CUDA graph is captured on its

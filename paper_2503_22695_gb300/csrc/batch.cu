@@ -1,0 +1,188 @@
+// Batched form: independent structures, each with its own plan, run as the
+// branches of one CUDA graph.
+//
+// At creation every instance gets its plan and its own branch stream; the
+// forward and adjoint sequences of all instances are captured once into two
+// graphs (a root event fans out to the branch streams and every branch joins
+// back), so one cudaGraphLaunch replays the whole batch: no per-instance host
+// work, and the GPU overlaps the instances' kernels.  Each branch is exactly
+// the single-instance call sequence, so every instance's results are bitwise
+// those of the individual entry points.
+#include <cstring>
+#include <vector>
+
+#include "ib_device.cuh"
+
+struct ib_batch {
+  int n;
+  int precision;
+  std::vector<ib_instance> inst;
+  std::vector<ib_plan*> plans;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> done;
+  std::vector<void*> tmp_gx;  // spread part of d/dx, added into gx
+  cudaEvent_t root;
+  cudaStream_t cap;
+  cudaGraphExec_t fwd, adj;
+  bool has_adj;
+};
+
+namespace ibfe {
+namespace {
+
+template <typename Real>
+__global__ void k_add_into(Real* __restrict__ a, const Real* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += b[i];
+}
+
+void destroy(ib_batch* b) {
+  if (!b) return;
+  if (b->fwd) cudaGraphExecDestroy(b->fwd);
+  if (b->adj) cudaGraphExecDestroy(b->adj);
+  for (ib_plan* p : b->plans)
+    if (p) ib_plan_destroy(p);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done)
+    if (e) cudaEventDestroy(e);
+  for (void* t : b->tmp_gx)
+    if (t) cudaFree(t);
+  if (b->root) cudaEventDestroy(b->root);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+ib_status run_forward(ib_batch* b, int i, cudaStream_t s) {
+  const ib_instance& in = b->inst[i];
+  return ib_forward(b->plans[i], in.mats, in.n_mats, &in.x, in.u, in.G, in.f, in.U, s);
+}
+
+ib_status run_adjoint(ib_batch* b, int i, cudaStream_t s) {
+  const ib_instance& in = b->inst[i];
+  ib_plan* p = b->plans[i];
+  ib_status st = ib_interp_adj(p, &in.x, in.u, in.gU, in.gu, in.gx, s);
+  if (st == IB_OK) st = ib_spread_adj(p, &in.x, in.G, in.gf, in.gG, b->tmp_gx[i], s);
+  if (st == IB_OK) {
+    const int64_t n = 3LL * in.mesh.n_nodes;
+    if (b->precision == IB_FP64)
+      k_add_into<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double*)in.gx,
+                                                                      (const double*)b->tmp_gx[i], n);
+    else
+      k_add_into<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)in.gx,
+                                                                    (const float*)b->tmp_gx[i], n);
+    if (cudaGetLastError() != cudaSuccess) st = IB_ERR_CUDA;
+  }
+  if (st == IB_OK) st = fe_force_adj_async(p, in.mats, in.n_mats, &in.x, in.gG, in.Hv, true, s);
+  return st;
+}
+
+// Capture fn(b, i, branch_i) for every instance as branches of one graph.
+ib_status capture(ib_batch* b, ib_status (*fn)(ib_batch*, int, cudaStream_t),
+                  cudaGraphExec_t* out) {
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return IB_ERR_CUDA;
+  ib_status st = cudaEventRecord(b->root, b->cap) == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+  for (int i = 0; i < b->n && st == IB_OK; ++i) {
+    if (cudaStreamWaitEvent(b->branch[i], b->root, 0) != cudaSuccess) st = IB_ERR_CUDA;
+    if (st == IB_OK) st = fn(b, i, b->branch[i]);
+    if (st == IB_OK && (cudaEventRecord(b->done[i], b->branch[i]) != cudaSuccess ||
+                        cudaStreamWaitEvent(b->cap, b->done[i], 0) != cudaSuccess))
+      st = IB_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+  if (st == IB_OK && ec != cudaSuccess) st = IB_ERR_CUDA;
+  if (st == IB_OK && cudaGraphInstantiate(out, g, 0) != cudaSuccess) st = IB_ERR_CUDA;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return st;
+}
+
+}  // namespace
+}  // namespace ibfe
+
+using namespace ibfe;
+
+extern "C" {
+
+ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision, void* stream,
+                          ib_batch** out) {
+  if (!out) return IB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n <= 0 || !inst) return IB_ERR_INVALID_ARG;
+  bool has_adj = true;
+  for (int i = 0; i < n; ++i) {
+    const ib_instance& in = inst[i];
+    if (!in.u || !in.G || !in.f || !in.U) return IB_ERR_INVALID_ARG;
+    const bool a = in.gU && in.gf && in.gu && in.gx && in.gG && in.Hv;
+    if (!a) has_adj = false;
+  }
+  ib_batch* b = new ib_batch();
+  b->n = n;
+  b->precision = precision;
+  b->inst.assign(inst, inst + n);
+  b->plans.assign(n, nullptr);
+  b->branch.assign(n, nullptr);
+  b->done.assign(n, nullptr);
+  b->tmp_gx.assign(n, nullptr);
+  b->root = nullptr;
+  b->cap = nullptr;
+  b->fwd = b->adj = nullptr;
+  b->has_adj = has_adj;
+  const size_t rs = precision == IB_FP64 ? sizeof(double) : sizeof(float);
+  ib_status st = IB_OK;
+  for (int i = 0; i < n && st == IB_OK; ++i) {
+    st = ib_plan_create(&inst[i].mesh, &inst[i].grid, precision, stream, &b->plans[i]);
+    if (st == IB_OK && (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess))
+      st = IB_ERR_CUDA;
+    if (st == IB_OK && has_adj &&
+        cudaMalloc(&b->tmp_gx[i], rs * 3 * (size_t)inst[i].mesh.n_nodes) != cudaSuccess)
+      st = IB_ERR_CUDA;
+  }
+  if (st == IB_OK && (cudaEventCreateWithFlags(&b->root, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess))
+    st = IB_ERR_CUDA;
+  if (st == IB_OK) st = capture(b, run_forward, &b->fwd);
+  if (st == IB_OK && has_adj) st = capture(b, run_adjoint, &b->adj);
+  if (st != IB_OK) {
+    destroy(b);
+    return st;
+  }
+  *out = b;
+  return IB_OK;
+}
+
+ib_status ib_batch_forward(ib_batch* b, void* stream) {
+  if (!b || !b->fwd) return IB_ERR_INVALID_ARG;
+  return cudaGraphLaunch(b->fwd, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IB_OK
+             : IB_ERR_CUDA;
+}
+
+ib_status ib_batch_adjoint(ib_batch* b, void* stream) {
+  if (!b || !b->adj) return IB_ERR_INVALID_ARG;
+  return cudaGraphLaunch(b->adj, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? IB_OK
+             : IB_ERR_CUDA;
+}
+
+ib_status ib_batch_gparams(ib_batch* b, double* gparams, void* stream) {
+  if (!b || !gparams) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->n; ++i)
+    if (cudaMemcpyAsync(gparams + (size_t)i * 9 * IB_MAX_MATERIALS, b->plans[i]->ered,
+                        sizeof(double) * 9 * IB_MAX_MATERIALS, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess)
+      return IB_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+ib_status ib_batch_destroy(ib_batch* b) {
+  if (!b) return IB_ERR_INVALID_ARG;
+  destroy(b);
+  return IB_OK;
+}
+
+}  // extern "C"

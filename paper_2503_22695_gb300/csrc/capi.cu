@@ -461,32 +461,44 @@ ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* 
   return check_launch(st);
 }
 
-ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
-                          const void* v, void* Hv, double* gparams, void* stream) {
+}  // extern "C"
+
+namespace ibfe {
+// Adjoint of the nodal force without host output: Hv on the device and, if
+// `params`, the parameter gradients left in p->ered ([n_mats][9]).
+ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats,
+                             const ib_pos* x, const void* v, void* Hv, bool params,
+                             cudaStream_t s) {
   if (!p || !v || !Hv) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
   MatTable mt;
   if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
-  cudaStream_t s = S(stream);
   {
     Stage sc(p, IB_STAGE_FORCE, s, 1);
-    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, gparams != nullptr,
-                             s);
+    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, params, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s);
-  if (st == IB_OK && gparams) {
-    st = do_reduce(p, 9, n_mats, s);
-    double red[9 * IB_MAX_MATERIALS];
-    if (st == IB_OK &&
-        (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
-         !ok(cudaStreamSynchronize(s))))
-      st = IB_ERR_CUDA;
-    if (st == IB_OK)
-      for (int m = 0; m < n_mats; ++m)
-        for (int k = 0; k < 9; ++k) gparams[m * 9 + k] = red[m * 9 + k];
-  }
+  if (st == IB_OK && params) st = do_reduce(p, 9, n_mats, s);
   return check_launch(st);
+}
+}  // namespace ibfe
+
+extern "C" {
+
+ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                          const void* v, void* Hv, double* gparams, void* stream) {
+  cudaStream_t s = S(stream);
+  ib_status st = fe_force_adj_async(p, mats, n_mats, x, v, Hv, gparams != nullptr, s);
+  if (st == IB_OK && gparams) {
+    double red[9 * IB_MAX_MATERIALS];
+    if (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
+        !ok(cudaStreamSynchronize(s)))
+      return IB_ERR_CUDA;
+    for (int m = 0; m < n_mats; ++m)
+      for (int k = 0; k < 9; ++k) gparams[m * 9 + k] = red[m * 9 + k];
+  }
+  return st;
 }
 
 ib_status ib_plan_set_profiling(ib_plan* p, int32_t enable) {

@@ -155,6 +155,11 @@ ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscal
                                double gscale, cudaStream_t s);
 ib_status interp_prepare(ib_plan* p);
 
+// capi.cu
+ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats,
+                             const ib_pos* x, const void* v, void* Hv, bool params,
+                             cudaStream_t s);
+
 // tiles.cu
 ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s);
 int classify_blocks(int ntiles);

@@ -56,6 +56,13 @@ class _Mat(C.Structure):
     _fields_ = [("model", C.c_int32), ("n_params", C.c_int32), ("params", C.c_double * 9)]
 
 
+class _Instance(C.Structure):
+    _fields_ = [("mesh", _Mesh), ("grid", _Grid), ("n_mats", C.c_int32),
+                ("mats", _Mat * 8), ("x", _Pos), ("u", C.c_void_p), ("G", C.c_void_p),
+                ("f", C.c_void_p), ("U", C.c_void_p), ("gU", C.c_void_p), ("gf", C.c_void_p),
+                ("gu", C.c_void_p), ("gx", C.c_void_p), ("gG", C.c_void_p), ("Hv", C.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libibfe.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -74,6 +81,11 @@ def _load():
         "ib_fe_force_adj": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, dp, vp],
         "ib_plan_sync_status": [vp, vp],
         "ib_plan_set_profiling": [vp, i32],
+        "ib_batch_create": [i32, C.POINTER(_Instance), i32, vp, C.POINTER(vp)],
+        "ib_batch_forward": [vp, vp],
+        "ib_batch_adjoint": [vp, vp],
+        "ib_batch_gparams": [vp, dp, vp],
+        "ib_batch_destroy": [vp],
         "ib_fe_energy_noalloc": [C.POINTER(_Mesh), C.POINTER(_Mat), i32, C.POINTER(_Pos),
                                  C.c_double, vp, vp],
         "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
@@ -325,6 +337,67 @@ def ib_fe_energy_noalloc(conn, X, mats, x: Pos, h: float, energy, fibres=None, m
     _chk(_lib.ib_fe_energy_noalloc(C.byref(mesh), arr, nm, C.byref(x._s), float(h),
                                    _ptr(energy), _stream()), "ib_fe_energy_noalloc")
     return energy
+
+
+class Batch:
+    """Independent structures run as the branches of one captured CUDA graph.
+
+    `instances` is a list of dicts with the device tensors of each structure:
+    conn, X, fibres (or None), mat_id (or None), n, h, origin, mats (list of
+    Material), cell/off (FP32 split) or x64 (FP64), u, and the output tensors
+    G, f, U; for the adjoint also gU, gf, gu, gx, gG, Hv.  The tensors must
+    stay alive and in place: the graphs bake their addresses in."""
+
+    def __init__(self, instances, precision: int = IB_FP32_SPLIT):
+        n = len(instances)
+        arr = (_Instance * n)()
+        self._keep = instances
+        self.n = n
+        for i, d in enumerate(instances):
+            a = arr[i]
+            conn, X = d["conn"], d["X"]
+            fib, mid = d.get("fibres"), d.get("mat_id")
+            a.mesh = _Mesh(int(X.shape[1]), int(conn.shape[1]), conn.data_ptr(), X.data_ptr(),
+                           None if fib is None else fib.data_ptr(),
+                           None if mid is None else mid.data_ptr())
+            a.grid = _Grid((C.c_int32 * 3)(*d["n"]), float(d["h"]),
+                           (C.c_double * 3)(*d.get("origin", (0.0, 0.0, 0.0))))
+            mats = d["mats"]
+            a.n_mats = len(mats)
+            for k, m in enumerate(mats):
+                a.mats[k].model = int(m.model)
+                a.mats[k].n_params = len(m.params)
+                for j, v in enumerate(m.params):
+                    a.mats[k].params[j] = float(v)
+            a.x = _Pos(_p(d.get("cell")), _p(d.get("off")), _p(d.get("x64")))
+            for name in ("u", "G", "f", "U", "gU", "gf", "gu", "gx", "gG", "Hv"):
+                setattr(a, name, _p(d.get(name)))
+        out = C.c_void_p()
+        _chk(_lib.ib_batch_create(n, arr, precision, _stream(), C.byref(out)), "ib_batch_create")
+        self._h = out
+
+    def forward(self):
+        _chk(_lib.ib_batch_forward(self._h, _stream()), "ib_batch_forward")
+
+    def adjoint(self):
+        _chk(_lib.ib_batch_adjoint(self._h, _stream()), "ib_batch_adjoint")
+
+    def gparams(self):
+        out = (C.c_double * (self.n * IB_MAX_MATERIALS * 9))()
+        _chk(_lib.ib_batch_gparams(self._h, out, _stream()), "ib_batch_gparams")
+        return torch.tensor(list(out), dtype=torch.float64).reshape(self.n, IB_MAX_MATERIALS, 9)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            try:
+                _lib.ib_batch_destroy(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
 
 
 def ib_plan_set_profiling(plan: Plan, enable: bool):

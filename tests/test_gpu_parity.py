@@ -305,3 +305,32 @@ def test_autograd_loss_gradient():
     assert rel_l2(params.grad.numpy()[0], gth[0]) <= 1e-4
     gu, _ = o.interp_adj(c.x_np, c.u_np, 2 * Uo, want_gx=False)
     assert rel_l2(np_(u.grad), gu) <= 1e-4
+
+
+def test_differentiation_workload_full_size():
+    # 128^3 ventricle shell: L = sum |U|^2 + sqrt(h^3 sum |f|^2); gradients with
+    # respect to the node positions and the HO parameters, GPU (FP32, through
+    # the autograd wrappers) against the FP64 oracle's adjoint chain.
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    c = case("shell128")
+    p = c.prob
+    h3 = p.grid.h ** 3
+    params = torch.tensor([list(I.HO_DEFAULT)], dtype=torch.float64, requires_grad=True)
+    off = c.off.clone().requires_grad_(True)
+    model = ibfe.IBCoupling(c.plan, [I.HO])
+    G, f, U = model(c.cell, off, params, c.u)
+    loss = (U.double() ** 2).sum() + torch.sqrt(h3 * (f.double() ** 2).sum())
+    loss.backward()
+    o = c.orc
+    Go, _ = o.fe_force(c.x_np)
+    fo = o.spread(c.x_np, Go)
+    Uo = o.interp(c.x_np, c.u_np)
+    nf = math.sqrt(h3 * np.sum(fo * fo))
+    _, gx_i = o.interp_adj(c.x_np, c.u_np, 2 * Uo)
+    gG, gx_s = o.spread_adj(c.x_np, Go, h3 * fo / nf)
+    Hv, gth = o.fe_force_adj(c.x_np, gG)
+    gx = gx_i + gx_s + Hv
+    assert float(loss) == pytest.approx(np.sum(Uo * Uo) + nf, rel=1e-5)
+    assert rel_l2(np_(off.grad), gx * p.grid.h) <= 1e-4
+    assert rel_l2(params.grad.numpy()[0, :8], gth[0, :8]) <= 1e-4

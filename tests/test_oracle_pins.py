@@ -498,3 +498,51 @@ def test_workload_shapes_and_jacobians():
     assert J.min() > 0.9 and J.max() < 1.1
     b = I.block_problem()
     assert (b.n_elems, b.n_nodes, b.n_gauss) == (128, 243, 1024)
+
+
+def test_differentiation_workload_oracle_gradient_by_differences():
+    # The 128^3 ventricle shell: the oracle's adjoint gradient of
+    # L = sum |U|^2 + sqrt(h^3 sum |f|^2) with respect to x and the 8 HO
+    # parameters, against FP64 central differences (step 1e-6) along 20 seeded
+    # directions normalised in (x/h, theta/theta0).
+    p = I.shell_problem(fp64=True)
+    m = oracle.Model(p)
+    h3 = p.grid.h ** 3
+    u = p.u.astype(np.float64)
+
+    def loss(x, th):
+        m.set_materials([I.Material(I.HO, tuple(th))])
+        G, _ = m.fe_force(x)
+        f = m.spread(x, G)
+        U = m.interp(x, u)
+        return np.sum(U * U) + math.sqrt(h3 * np.sum(f * f))
+
+    th0 = np.array(I.HO_DEFAULT)
+    x0 = p.x
+    m.set_materials([I.Material(I.HO, tuple(th0))])
+    G, _ = m.fe_force(x0)
+    f = m.spread(x0, G)
+    U = m.interp(x0, u)
+    nf = math.sqrt(h3 * np.sum(f * f))
+    _, gx_i = m.interp_adj(x0, u, 2 * U)
+    gG, gx_s = m.spread_adj(x0, G, h3 * f / nf)
+    Hv, gth = m.fe_force_adj(x0, gG)
+    gx = gx_i + gx_s + Hv
+    L0 = loss(x0, th0)
+    rng = np.random.Generator(np.random.PCG64(4002))
+    for _ in range(20):
+        dx = rng.normal(size=x0.shape) * p.grid.h
+        dth = rng.normal(size=9) * th0
+        dth[8] = 0.0
+        nrm = math.sqrt(np.sum((dx / p.grid.h) ** 2) + np.sum((dth[:8] / th0[:8]) ** 2))
+        dx /= nrm
+        dth /= nrm
+        an = np.sum(gx * dx) + np.sum(gth[0] * dth)
+        # step 1e-6: the difference of two evaluations of L (~2.5e5) carries a
+        # rounding error of order eps_mach |L|, i.e. eps_mach |L| / step in
+        # the quotient; step 1e-5 leaves truncation below 1e-6 relative.
+        for step, rel, absol in ((1e-6, 1e-6, np.finfo(float).eps * abs(L0) / 1e-6),
+                                 (1e-5, 1e-5, 0.0)):
+            fd = (loss(x0 + step * dx, th0 + step * dth) -
+                  loss(x0 - step * dx, th0 - step * dth)) / (2 * step)
+            assert an == pytest.approx(fd, rel=rel, abs=absol), step
