@@ -76,14 +76,16 @@ typedef enum {
   IB_HO = 2           /* Psi_4 Holzapfel-Ogden (Section 3); params {a, b, af, bf, as, bs, afs, bfs, kappa} */
 } ib_model;
 
-/* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1, ln J and the
- *   fibre invariants I4 - 1, I8 are combined in FP64 (the steps whose
- *   cancellation sets the volumetric and fibre stresses).
+/* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1, ln J (the
+ *   volumetric term) and the fibre invariant I4f - 1 (the exponential fibre
+ *   term near I4f = 1) are combined in FP64.
  * IB_FP64: every array and every operation in double.
  * IB_FP32_SPLIT_F32STAB: as IB_FP32_SPLIT with those scalars in FP32 too,
- *   using the same cancellation-free formulas (much faster on GPUs whose FP64
- *   rate is a small fraction of FP32; forces agree with IB_FP32_SPLIT to a
- *   few 1e-7 relative). */
+ *   using the same cancellation-free formulas.  About 4x faster FE force on
+ *   GPUs whose FP64 rate is a small fraction of FP32; nodal forces stay
+ *   within 1e-5 relative L2 of the FP64 definition, but the Hessian-vector
+ *   product of ib_fe_force_adj loses accuracy (6.7e-5 relative on a 256^3
+ *   ventricle workload, against 2e-5 with IB_FP32_SPLIT). */
 typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_precision;
 
 #define IB_MAX_MATERIALS 8

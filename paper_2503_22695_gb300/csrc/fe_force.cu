@@ -12,15 +12,19 @@
 //   I1 - 3  = 2 tr H + |H|^2
 //   I4 - 1  = (|e|^2 - 1) + 2 e.(H e) + |H e|^2
 //   I8      = e_f.e_s + e_f.(H e_s) + e_s.(H e_f) + (H e_f).(H e_s)
-// The scalars that carry cancellation are combined in the type S (double):
-// J - 1 (its terms are exact double products of the FP32 entries of H, so the
-// FP64 sum leaves J - 1 exact to double rounding), ln J = log1p(J - 1), and
-// the fibre invariants I4 - 1 and I8, which set the fibre stresses near
-// I4 = 1.  The exponentials are then taken of these FP64 arguments in Real:
-// exp is well conditioned (relative error of the argument times the argument,
-// which is small), so evaluating it beyond the precision of the FP32 stress
-// it multiplies adds nothing.  Everything else is in Real (float for
-// split-precision plans, double for FP64 plans).
+// The scalars of the volumetric term and of the fibre term near I4f = 1 are
+// combined in the type S (double): J - 1 (its terms are exact double products
+// of the FP32 entries of H, so the FP64 sum leaves J - 1 exact to double
+// rounding), ln J = log1p(J - 1), and the fibre invariant I4f - 1 of the fibre
+// family e_f.  Once I4f - 1 is known, the fibre coefficient
+// 2 a_f (I4f - 1) exp(b_f (I4f - 1)^2) is a product of well-conditioned factors
+// and is formed in Real: exp has relative error (argument error) x (argument),
+// small here, so evaluating it beyond the precision of the FP32 stress it
+// multiplies adds nothing.  The sheet family e_s and the coupling I8 of
+// Holzapfel-Ogden use the same cancellation-free formulas in Real.  Everything
+// else is in Real (float for split-precision plans, double for FP64 plans).
+// On GB300 the FP64 pipe runs at about 1/64 of the FP32 rate, so this FP64 set
+// (about 50 double operations per Gauss point) sets the kernel's time.
 //
 // With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
 //   H = Du J0^-1, and the corner forces are
@@ -70,6 +74,9 @@ __device__ __forceinline__ void cofactor(const T A[3][3], T C[3][3]) {
   C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
 }
 
+__device__ __forceinline__ double fma_s(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_s(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Quantities of one fibre family needed by the stress and its derivatives.
 template <typename Real, typename S>
 struct Fibre {
@@ -83,43 +90,56 @@ __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S
   Real He[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) He[i] = H[i][0] * e[0] + H[i][1] * e[1] + H[i][2] * e[2];
-  S eHe = S(e[0]) * S(He[0]) + S(e[1]) * S(He[1]) + S(e[2]) * S(He[2]);
-  S HeHe = S(He[0]) * S(He[0]) + S(He[1]) * S(He[1]) + S(He[2]) * S(He[2]);
-  S I4m1 = en1 + S(2) * eHe + HeHe;
+  // 2 e.He + |He|^2 = He.(2e + He); 2e + He is exact in double
+  S I4m1 = en1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) I4m1 = fma_s(S(He[i]), S(Real(2) * e[i]) + S(He[i]), I4m1);
   f.d = I4m1 > S(0) ? I4m1 : S(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
 }
 
 // ln(1 + x) in double.  For |x| <= 1/8 it is 2 atanh(s) with s = x / (2 + x)
-// (|s| <= 1/17), summed as 2 s (1 + z/3 + z^2/5 + ... + z^7/15), z = s^2: the
-// first omitted term is below z^8/17 < 1e-20 relative.  1/(2 + x) comes from
-// an FP32 reciprocal refined by two Newton steps in double.  Outside that
-// range (|J - 1| > 1/8) the library log1p is used.
+// (|s| <= 1/17), summed as s (2 + 2z/3 + 2z^2/5 + ... + 2z^6/13), z = s^2: the
+// first omitted term, 2 z^7/15, is below 4e-19 relative.  1/(2 + x) comes from
+// an FP32 reciprocal refined by one Newton step in double, which leaves a
+// relative error near 1e-14 (the square of the FP32 reciprocal's).  Outside
+// that range (|J - 1| > 1/8) the library log1p is used.
 __device__ __forceinline__ double log1p_d(double x) {
   if (!(fabs(x) <= 0.125)) return log1p(x);
   const double d = 2.0 + x;
   double r = (double)__frcp_rn((float)d);
-  r = r * (2.0 - d * r);
-  r = r * (2.0 - d * r);
+  r = fma(r, fma(-d, r, 1.0), r);
   const double s = x * r;
   const double z = s * s;
-  double t = 1.0 / 15.0;
-  t = fma(t, z, 1.0 / 13.0);
-  t = fma(t, z, 1.0 / 11.0);
-  t = fma(t, z, 1.0 / 9.0);
-  t = fma(t, z, 1.0 / 7.0);
-  t = fma(t, z, 1.0 / 5.0);
-  t = fma(t, z, 1.0 / 3.0);
-  t = fma(t, z, 1.0);
-  return 2.0 * s * t;
+  double t = 2.0 / 13.0;
+  t = fma(t, z, 2.0 / 11.0);
+  t = fma(t, z, 2.0 / 9.0);
+  t = fma(t, z, 2.0 / 7.0);
+  t = fma(t, z, 2.0 / 5.0);
+  t = fma(t, z, 2.0 / 3.0);
+  t = fma(t, z, 2.0);
+  return s * t;
 }
 
 __device__ __forceinline__ double log1p_s(double x) { return log1p_d(x); }
 __device__ __forceinline__ float log1p_s(float x) { return log1pf(x); }
 
+// Resident 128-thread CTAs per SM requested from the register allocator.
+#ifndef IBFE_FE_MIN_BLOCKS
+#define IBFE_FE_MIN_BLOCKS 3
+#endif
+#ifndef IBFE_FE_MIN_BLOCKS_ADJ
+#define IBFE_FE_MIN_BLOCKS_ADJ 3
+#endif
+template <typename Real, bool kAdj>
+constexpr int fe_min_blocks() {
+  return sizeof(Real) == 8 ? 2 : (kAdj ? IBFE_FE_MIN_BLOCKS_ADJ : IBFE_FE_MIN_BLOCKS);
+}
+
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
-__global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
+__global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
+    k_fe(FeArgs<Real> A, MatTable mt) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.E) return;
   const int E = A.E;
@@ -175,8 +195,13 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
   const S efn1 = S(ef[0]) * S(ef[0]) + S(ef[1]) * S(ef[1]) + (S(ef[2]) * S(ef[2]) - S(1));
   const S esn1 = S(es[0]) * S(es[0]) + S(es[1]) * S(es[1]) + (S(es[2]) * S(es[2]) - S(1));
   const S efes = S(ef[0]) * S(es[0]) + S(ef[1]) * S(es[1]) + S(ef[2]) * S(es[2]);
+  const Real esn1r = Real(esn1), efesr = Real(efes);
 
+  // material constants (unused entries of a model are never read by its branches)
   const Real kap = Real(prm[model == 0 ? 1 : (model == 1 ? 3 : 8)]);
+  const Real pa = Real(prm[0]), pb = Real(prm[1]);
+  const Real paf = Real(prm[model == 1 ? 1 : 2]), pbf = Real(prm[model == 1 ? 2 : 3]);
+  const Real pas = Real(prm[4]), pbs = Real(prm[5]), pafs = Real(prm[6]), pbfs = Real(prm[7]);
 
   Real Ge[8][3];
 #pragma unroll
@@ -225,15 +250,19 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
         H[i][j] = Du[i][0] * Ji[0][j] + Du[i][1] * Ji[1][j] + Du[i][2] * Ji[2][j];
 
     // ---- invariants --------------------------------------------------------
-    // J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H: the first two terms from
-    // exact double products of the entries of H; det H (third order) in Real.
-    const S trS = S(H[0][0]) + S(H[1][1]) + S(H[2][2]);
-    S trH2 = S(H[0][0]) * S(H[0][0]) + S(H[1][1]) * S(H[1][1]) + S(H[2][2]) * S(H[2][2]);
-    trH2 += S(2) * (S(H[0][1]) * S(H[1][0]) + S(H[0][2]) * S(H[2][0]) + S(H[1][2]) * S(H[2][1]));
-    const S Jm1 = trS + S(0.5) * (trS * trS - trH2) + S(det3(H));
+    // J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H, the middle term written as
+    // the sum of the principal 2x2 minors H_ii H_jj - H_ij H_ji.  In S = double
+    // the sums and products of FP32 entries below are exact up to one rounding
+    // per fma; det H (third order) is taken in Real.
+    const S h11_22 = S(H[1][1]) + S(H[2][2]);
+    S m2 = fma_s(S(H[0][0]), h11_22, S(H[1][1]) * S(H[2][2]));
+    m2 = fma_s(-S(H[0][1]), S(H[1][0]), m2);
+    m2 = fma_s(-S(H[0][2]), S(H[2][0]), m2);
+    m2 = fma_s(-S(H[1][2]), S(H[2][1]), m2);
+    const S Jm1 = (S(H[0][0]) + h11_22) + m2 + S(det3(H));
     const S lnJs = log1p_s(Jm1);
     const Real lnJ = Real(lnJs);
-    const Real J = Real(S(1) + Jm1);
+    const Real J = Real(1) + Real(Jm1);
     Real F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -251,7 +280,7 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) HH += H[i][j] * H[i][j];
-    const Real I1m3 = Real(2) * Real(trS) + HH;
+    const Real I1m3 = Real(2) * (H[0][0] + H[1][1] + H[2][2]) + HH;
     const Real Jm23m1 = expm1(Real(-2.0 / 3.0) * lnJ);
     const Real Jm23 = Real(1) + Jm23m1;
     const Real Ibm3 = Jm23 * I1m3 + Real(3) * Jm23m1;  // I1bar - 3
@@ -265,30 +294,34 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
     // ---- constitutive law -----------------------------------------------------
     Real ciso;
     Real eiso = Real(1);  // HO: exp(b (I1bar - 3))
-    if (model == 0) {
-      ciso = Real(2.0 * prm[0]);
-    } else if (model == 1) {
-      ciso = Real(2.0 * prm[0]);
+    if (model == 2) {
+      eiso = exp(pb * Ibm3);
+      ciso = pa * eiso;
     } else {
-      eiso = exp(Real(prm[1]) * Ibm3);
-      ciso = Real(prm[0]) * eiso;
+      ciso = Real(2) * pa;
     }
-    Fibre<Real, S> f1, f2;
-    S cf1 = S(0), cf2 = S(0), ef1 = S(1), ef2 = S(1);
+    // Fibre family f (the fibre of Psi_2 and of Psi_4): I4f - 1 combined in S.
+    // Its exponential factor and coefficient are then products of that small
+    // number, with no cancellation left, and are formed in Real.
+    Fibre<Real, S> f1;
+    Fibre<Real, Real> f2;
+    Real d1 = Real(0), cf1 = Real(0), ef1 = Real(1), cf2 = Real(0), ef2 = Real(1);
     const bool has_f = model != 0;
     const bool has_s = model == 2;
     if (has_f) {
       fibre_kin<Real, S>(H, ef, efn1, f1);
-      const S af = S(prm[model == 1 ? 1 : 2]), bf = S(prm[model == 1 ? 2 : 3]);
-      ef1 = S(exp(Real(bf * f1.d * f1.d)));
-      cf1 = S(2) * af * f1.d * ef1;
+      d1 = Real(f1.d);
+      ef1 = exp(pbf * d1 * d1);
+      cf1 = Real(2) * paf * d1 * ef1;
     }
+    // Sheet family and the fibre-sheet coupling (HO only) in Real, with the
+    // same cancellation-free formulas.
     Real Fef[3], Fes[3];
-    S I8 = S(0), e8 = S(1), c8 = S(0);
+    Real I8 = Real(0), e8 = Real(1), c8 = Real(0);
     if (has_s) {
-      fibre_kin<Real, S>(H, es, esn1, f2);
-      ef2 = S(exp(Real(S(prm[5]) * f2.d * f2.d)));
-      cf2 = S(2) * S(prm[4]) * f2.d * ef2;
+      fibre_kin<Real, Real>(H, es, esn1r, f2);
+      ef2 = exp(pbs * f2.d * f2.d);
+      cf2 = Real(2) * pas * f2.d * ef2;
       Real Hef[3], Hes[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -297,12 +330,11 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
         Fef[i] = ef[i] + Hef[i];
         Fes[i] = es[i] + Hes[i];
       }
-      I8 = efes;
+      I8 = efesr;
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-        I8 += S(ef[i]) * S(Hes[i]) + S(es[i]) * S(Hef[i]) + S(Hef[i]) * S(Hes[i]);
-      e8 = S(exp(Real(S(prm[7]) * I8 * I8)));
-      c8 = S(prm[6]) * I8 * e8;
+      for (int i = 0; i < 3; ++i) I8 += ef[i] * Hes[i] + es[i] * Hef[i] + Hef[i] * Hes[i];
+      e8 = exp(pbfs * I8 * I8);
+      c8 = pafs * I8 * e8;
     }
 
     if (kEnergy) {
@@ -403,10 +435,9 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
         dI4f = Real(2) * (f1.Fe[0] * dFe[0] + f1.Fe[1] * dFe[1] + f1.Fe[2] * dFe[2]);
-        const S bf = S(prm[model == 1 ? 2 : 3]), af = S(prm[model == 1 ? 1 : 2]);
-        const Real dc = f1.d > S(0)
-                            ? Real(S(2) * af * ef1 * (S(1) + S(2) * bf * f1.d * f1.d)) * dI4f
-                            : Real(0);
+        const Real dc =
+            d1 > Real(0) ? Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f
+                         : Real(0);
         const Real c = Real(cf1);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -421,15 +452,15 @@ __global__ void __launch_bounds__(128) k_fe(FeArgs<Real> A, MatTable mt) {
           dFf[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
         }
         dI4s = Real(2) * (f2.Fe[0] * dFs[0] + f2.Fe[1] * dFs[1] + f2.Fe[2] * dFs[2]);
-        const S bs = S(prm[5]), as = S(prm[4]);
-        const Real dc = f2.d > S(0)
-                            ? Real(S(2) * as * ef2 * (S(1) + S(2) * bs * f2.d * f2.d)) * dI4s
-                            : Real(0);
+        const Real dc =
+            f2.d > Real(0)
+                ? Real(2) * pas * ef2 * (Real(1) + Real(2) * pbs * f2.d * f2.d) * dI4s
+                : Real(0);
         const Real c = Real(cf2);
         dI8 = dFf[0] * Fes[0] + dFf[1] * Fes[1] + dFf[2] * Fes[2] + Fef[0] * dFs[0] +
               Fef[1] * dFs[1] + Fef[2] * dFs[2];
-        const Real dk8 = Real(S(prm[6]) * e8 * (S(1) + S(2) * S(prm[7]) * I8 * I8)) * dI8;
-        const Real k8 = Real(c8);
+        const Real dk8 = pafs * e8 * (Real(1) + Real(2) * pbfs * I8 * I8) * dI8;
+        const Real k8 = c8;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
