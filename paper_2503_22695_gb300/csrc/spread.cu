@@ -239,16 +239,27 @@ __global__ void __launch_bounds__(kPT) k_spread_push(SpreadArgs<Real> A) {
 // ---------------------------------------------------------------------------
 // FP32 plans: order-independent fixed-point accumulation.
 //
-// Every contribution c = V prod phi of an item is converted to an integer
-// multiple of 2^-(k+20) split into a high word round(c 2^k) (|.| < 2^20) and a
-// low word round((c - hi 2^-k) 2^(k+20)) (|.| < 2^19), and both words are
-// added with native 32-bit shared-memory atomics into one block per CTA.
-// Integer addition is exact and associative, so the block is the same
-// whatever the order of the additions; with at most 1024 points per item no
-// word overflows.  k comes from the largest |V| of the call (one integer
-// atomicMax over the float bit patterns), so that |c| 2^k < 2^20 since every
-// kernel weight product is at most 1/8.  The resolution 2^-(k+20) is 2^-40 of
-// the largest contribution; each block value is rounded once to float.
+// Every contribution C = V prod phi of an item, in units of 2^-k, is split into
+// an integer part h = round(C) and a fraction l = round(2^11 (C - h)) (in
+// units of 2^-(k+11)), and both are added with native 32-bit shared-memory
+// atomics into one block per CTA.  Integer addition is exact and associative,
+// so the block is the same whatever the order of the additions.
+//
+// Both parts come from the magic-number rounding t = x + 1.5 2^23, whose bit
+// pattern is 0x4B400000 + round(x) for |x| < 2^22; three fmas per
+// contribution give both patterns, which are added as they are:
+//   t1 = C + M                 bits(t1) = Mb + h
+//   z  = M - 2^11 (t1 - M)     (exact: a multiple of 2^11 below 2^32)
+//   t2 = 2^11 C + z            bits(t2) = Mb + l,  |l| <= 2^10
+// After n contributions the words are hi = n Mb + H and lo = n Mb + L (mod
+// 2^32).  Mb = 301 2^22 has zero low 22 bits and |L| <= 2^20 (n <= 1024), so
+// L is the sign-extended low 22 bits of lo, and H = (hi - lo) + L.  k comes
+// from the largest |V| of the call (one integer atomicMax over the float bit
+// patterns) so that |C| < 2^19, since every kernel weight product is at most
+// 1/8; hence |H| < 2^29.  The resolution is 2^-(k+12), about 2^-31 of the
+// largest contribution; each block value H 2^11 + L is rounded to float by
+// one fma of the two parts converted to float (exact conversions while
+// |H| < 2^24); the same integers always give the same float.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ v, int64_t n,
                                                uint32_t* __restrict__ out) {
@@ -261,44 +272,58 @@ __global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ v, int
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic holds round(x) in its low bits
-constexpr int kMagicBits = 0x4B400000;
+constexpr float kMagic = 12582912.0f;            // M = 1.5 * 2^23
+constexpr float kMagicZ = 12582912.0f * 2049.0f; // M (1 + 2^11), exact in float
 constexpr int kFxThreads = 256;
-constexpr int kFxBatch = kFxThreads;
+constexpr int kFxWarps = kFxThreads / 32;
+constexpr int kFxBatch = 128;  // points staged per batch
+// Lane mapping: a warp takes one point at a time; lane (dz, dy, xh) adds the
+// faces xh and xh + 2 of stencil row (dz, dy), one instruction per face pair
+// and component.  With y stride 14 and z stride 168 the 16 row offsets
+// 168 dz + 14 dy are the 16 even residues mod 32, so the 32 lanes of every
+// atomic hit 32 distinct banks wherever the point lies.
+constexpr int kFxSY = 14;
+constexpr int kFxSZ = kB * kFxSY;       // 168
+constexpr int kFxAcc = kB * kFxSZ;      // 2016 words per component
 
-struct alignas(16) StagedFx {
-  float w[3][2][4];  // [axis][staggering: 0 = s 0, 1 = s 1/2][4 weights]
-  float val[3];
-  int org[3];        // row origin of component c in the halo'd block
-  int pad[2];
+// Staged points, one array per field (16- and 32-byte records keep the
+// one-thread-per-point stores at most 2-way bank conflicted).
+struct FxStage {
+  float4 val[kFxBatch];     // 2^k V^c * scale, c = 0..2
+  int4 org[kFxBatch];       // accumulator offset of the stencil's first face, per component
+  float2 wz[kFxBatch][4];   // [dz] = (w_z at s = 0, w_z at s = 1/2)
+  float2 wy[kFxBatch][4];   // [dy] likewise
+  float4 wx[kFxBatch][2];   // [xh] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
 };
 
-__device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float c, float s1, float is1,
-                                       float s2) {
-  const float t1 = fmaf(c, s1, kMagic);
-  const int h = __float_as_int(t1) - kMagicBits;
-  const float r = fmaf(-(t1 - kMagic), is1, c);
-  const int l = __float_as_int(fmaf(r, s2, kMagic)) - kMagicBits;
-  atomicAdd(hi, (unsigned)h);
-  atomicAdd(lo, (unsigned)l);
+// adds the contribution C = w wx (in units of 2^-k) at word offset a
+__device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float w, float w11, float wx) {
+  const float t1 = fmaf(w, wx, kMagic);
+  const float z = fmaf(t1, -2048.0f, kMagicZ);
+  const float t2 = fmaf(w11, wx, z);
+  atomicAdd(hi, __float_as_uint(t1));
+  atomicAdd(lo, __float_as_uint(t2));
 }
 
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StagedFx* stage = reinterpret_cast<StagedFx*>(smem_raw);
-  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(StagedFx) * kFxBatch);
-  unsigned* acc_lo = acc_hi + 3 * kAcc;
+  FxStage& stage = *reinterpret_cast<FxStage*>(smem_raw);
+  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(FxStage));
+  unsigned* acc_lo = acc_hi + 3 * kFxAcc;
   __shared__ int next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = A.counters[0];
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  // this lane's (dz, dy, xh) and its offset within a stencil
+  const int ldz = lane >> 3, ldy = (lane >> 1) & 3, lxh = lane & 1;
+  const int loff = ldz * kFxSZ + ldy * kFxSY + lxh;
   // fixed-point scale of the call
   const float cmax = 0.125f * __uint_as_float(*A.absmax) * fabsf(A.scale);
   int ex = 0;
   if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
-  const int k = min(19 - ex, 106);  // keep 2^(k+20) a normal float
-  const float s1 = ldexpf(1.f, k), is1 = ldexpf(1.f, -k), s2 = ldexpf(1.f, k + 20);
-  const float out_scale = ldexpf(1.f, -(k + 20));
+  const int k = min(19 - ex, 100);  // keep 2^(k+11) a normal float
+  const float vscale = A.scale * ldexpf(1.f, k);
+  const float out_scale = ldexpf(1.f, -(k + 11));
   for (;;) {
     __syncthreads();
     if (tid == 0) next = atomicAdd(A.counters + 1, 1);
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
     const int e = min(A.tile_end[tile], s + kChunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
-    for (int i = tid; i < 3 * kAcc * 2 / 4; i += kFxThreads)
+    for (int i = tid; i < 3 * kFxAcc * 2 / 4; i += kFxThreads)
       reinterpret_cast<uint4*>(acc_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int b0 = s; b0 < e; b0 += kFxBatch) {
       const int nb = min(kFxBatch, e - b0);
@@ -319,7 +344,7 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
         const int i = b0 + tid;
         int cc[3];
         unpack_cell(__ldg(A.p_cell + i), cc[0], cc[1], cc[2]);
-        StagedFx st;
+        float w[3][2][4];
         int b[3][2];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -328,46 +353,61 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
           for (int hf = 0; hf < 2; ++hf) {
             float th;
             b[d][hf] = cc[d] - lc0[d] + stencil_axis(off, hf == 1, th) + 2;
-            delta_weights(th, st.w[d][hf]);
+            delta_weights(th, w[d][hf]);
           }
         }
+        stage.val[tid] = make_float4(__ldg(A.p_val + i) * vscale, __ldg(A.p_val + A.Q + i) * vscale,
+                                     __ldg(A.p_val + 2 * A.Q + i) * vscale, 0.f);
+        int o[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          st.val[c] = __ldg(A.p_val + c * A.Q + i) * A.scale;
-          st.org[c] = c * kAcc + b[2][c != 2] * kSZ + b[1][c != 1] * kSY + b[0][c != 0];
+        for (int c = 0; c < 3; ++c)
+          o[c] = c * kFxAcc + b[2][c != 2] * kFxSZ + b[1][c != 1] * kFxSY + b[0][c != 0];
+        stage.org[tid] = make_int4(o[0], o[1], o[2], 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          stage.wz[tid][j] = make_float2(w[2][0][j], w[2][1][j]);
+          stage.wy[tid][j] = make_float2(w[1][0][j], w[1][1][j]);
         }
-        stage[tid] = st;
+#pragma unroll
+        for (int xh = 0; xh < 2; ++xh)
+          stage.wx[tid][xh] = make_float4(w[0][0][xh], w[0][0][xh + 2], w[0][1][xh], w[0][1][xh + 2]);
       }
       __syncthreads();
-      // two points per warp step: 96 (point, component, dz, dy) rows, three
-      // per lane, four faces per row
-      for (int p0 = 2 * warp; p0 < nb; p0 += 2 * (kFxThreads / 32)) {
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr) {
-          const int r = lane + 32 * rr;
-          const int pt = p0 + (r >= 48 ? 1 : 0);
-          if (pt >= nb) continue;
-          const int q = r >= 48 ? r - 48 : r;
-          const int c = q >> 4, dz = (q >> 2) & 3, dy = q & 3;
-          const StagedFx& st = stage[pt];
-          const float w = st.val[c] * st.w[2][c != 2][dz] * st.w[1][c != 1][dy];
-          const float4 wx = *reinterpret_cast<const float4*>(st.w[0][c != 0]);
-          const int o = st.org[c] + dz * kSZ + dy * kSY;
-          fx_add(acc_hi + o, acc_lo + o, w * wx.x, s1, is1, s2);
-          fx_add(acc_hi + o + 1, acc_lo + o + 1, w * wx.y, s1, is1, s2);
-          fx_add(acc_hi + o + 2, acc_lo + o + 2, w * wx.z, s1, is1, s2);
-          fx_add(acc_hi + o + 3, acc_lo + o + 3, w * wx.w, s1, is1, s2);
-        }
+      // one point per warp step: lane (dz, dy, xh) adds faces xh and xh + 2 of
+      // its (dz, dy) row, for each component
+      for (int pt = warp; pt < nb; pt += kFxWarps) {
+        const float4 v = stage.val[pt];
+        const int4 org = stage.org[pt];
+        const float2 wz = stage.wz[pt][ldz], wy = stage.wy[pt][ldy];
+        const float4 wx = stage.wx[pt][lxh];
+        // component 0: z, y at s = 1/2, x at s = 0
+        float wr = v.x * wz.y * wy.y;
+        int a = org.x + loff;
+        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.x);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.y);
+        // component 1: z at s = 1/2, y at s = 0, x at s = 1/2
+        wr = v.y * wz.y * wy.x;
+        a = org.y + loff;
+        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
+        // component 2: z at s = 0, y, x at s = 1/2
+        wr = v.z * wz.x * wy.y;
+        a = org.z + loff;
+        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
       }
     }
     __syncthreads();
+    // block values H 2^11 + L to float
     float* out = A.scratch + (int64_t)slot * kItemBlk;
     for (int idx = tid; idx < kItemBlk; idx += kFxThreads) {
       const int c = idx / kBlk, rr = idx % kBlk;
       const int z = rr / (kB * kB), y = (rr / kB) % kB, x = rr % kB;
-      const int o = c * kAcc + z * kSZ + y * kSY + x;
-      const long long v = ((long long)(int)acc_hi[o] << 20) + (long long)(int)acc_lo[o];
-      out[idx] = __ll2float_rn(v) * out_scale;
+      const int o = c * kFxAcc + z * kFxSZ + y * kFxSY + x;
+      const unsigned hw = acc_hi[o], lw = acc_lo[o];
+      const int L = (int)(lw << 10) >> 10;
+      const int H = (int)(hw - lw) + L;
+      out[idx] = fmaf((float)H, 2048.0f, (float)L) * out_scale;
     }
   }
 }
@@ -464,7 +504,7 @@ size_t push_smem() {
   return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
 }
 
-constexpr size_t kFxSmem = sizeof(StagedFx) * kFxBatch + sizeof(unsigned) * 2 * 3 * kAcc;
+constexpr size_t kFxSmem = sizeof(FxStage) + sizeof(unsigned) * 2 * 3 * kFxAcc;
 
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
   cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
