@@ -30,6 +30,7 @@
 //   H = Du J0^-1, and the corner forces are
 //   G_a -= (P J0^-T w j0) dN_a/dxi,
 // so the X-gradients of the shape functions are never formed.
+#include <algorithm>
 #include <cstdio>
 
 #include "ib_device.cuh"
@@ -132,16 +133,18 @@ __device__ __forceinline__ float log1p_s(float x) { return log1pf(x); }
 #ifndef IBFE_FE_MIN_BLOCKS_ADJ
 #define IBFE_FE_MIN_BLOCKS_ADJ 3
 #endif
+#ifndef IBFE_FE_CTAS_PER_SM
+#define IBFE_FE_CTAS_PER_SM 2
+#endif
+constexpr int kFeCtasPerSm = IBFE_FE_CTAS_PER_SM;  // CTAs per SM of the persistent forward grid
+
 template <typename Real, bool kAdj>
 constexpr int fe_min_blocks() {
   return sizeof(Real) == 8 ? 2 : (kAdj ? IBFE_FE_MIN_BLOCKS_ADJ : IBFE_FE_MIN_BLOCKS);
 }
 
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
-__global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
-    k_fe(FeArgs<Real> A, MatTable mt) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= A.E) return;
+__device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e) {
   const int E = A.E;
   int node[8];
 #pragma unroll
@@ -527,6 +530,16 @@ __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
   }
 }
 
+// Persistent grid (a fixed number of CTAs per SM, fewer than fit): the kernel
+// is bound by the FP64 pipe, and the SM room it leaves lets the Gauss-point
+// sort and the interpolation, issued on another stream, run beside it.
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
+__global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
+    k_fe(FeArgs<Real> A, MatTable mt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < A.E; e += gridDim.x * blockDim.x)
+    fe_element<Real, S, kEnergy, kAdj, kParams>(A, mt, e);
+}
+
 // Deterministic per-material sums of per-element partials in two levels:
 // CTA b reduces a contiguous chunk of elements with a fixed-shape tree
 // (warp shuffles, then warp sums), one (material, value) pair at a time;
@@ -629,7 +642,9 @@ ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, 
   if (p->E == 0) return IB_OK;
   FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
   const int threads = 128;
-  const int blocks = (p->E + threads - 1) / threads;
+  // the forward runs beside the sort and interpolation; the adjoint runs alone
+  const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : kFeCtasPerSm;
+  const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
   if (p->precision == IB_FP32_SPLIT_F32STAB)
     k_fe<Real, Real, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
   else

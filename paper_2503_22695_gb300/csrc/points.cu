@@ -174,29 +174,46 @@ __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
 // ---------------------------------------------------------------------------
 // radix sort pieces
 // ---------------------------------------------------------------------------
+// Each CTA takes a chunk of kSortChunk consecutive items; warp w of the CTA
+// owns the kWarpItems items [w kWarpItems, (w+1) kWarpItems) of the chunk, 32
+// per round.  Lanes holding the same digit in a round are found with a warp
+// match, and one leader lane adds their number.
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kWarpItems = kSortItems * 32;
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ key,
                                                              int64_t Q, int shift, int nblk,
                                                              int32_t* __restrict__ hist) {
   __shared__ int cnt[256];
-  cnt[threadIdx.x] = 0;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  cnt[t] = 0;
   __syncthreads();
-  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk;
-  for (int i = threadIdx.x; i < kSortChunk; i += kSortThreads) {
-    const int64_t k = b0 + i;
-    if (k < Q) atomicAdd(&cnt[(__ldg(key + k) >> shift) & 255], 1);
+  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk + (int64_t)warp * kWarpItems + lane;
+  uint32_t k[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = b0 + r * 32;
+    k[r] = i < Q ? __ldg(key + i) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = b0 + r * 32 < Q;
+    const int d = valid ? (int)((k[r] >> shift) & 255u) : 256 + lane;  // unique sentinel
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
   }
   __syncthreads();
-  hist[threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+  hist[t * nblk + blockIdx.x] = cnt[t];
 }
 
 // For each digit (one CTA per digit): exclusive scan, in place, of its
 // per-block counts hist[d*nblk .. d*nblk + nblk), and the digit total.
-__global__ void __launch_bounds__(1024) k_digit_scan(int32_t* __restrict__ hist, int nblk,
-                                                     int32_t* __restrict__ dtot) {
+__global__ void __launch_bounds__(256) k_digit_scan(int32_t* __restrict__ hist, int nblk,
+                                                    int32_t* __restrict__ dtot) {
   __shared__ int tmp[32];
   int32_t* h = hist + (int64_t)blockIdx.x * nblk;
   int carry = 0;
-  for (int b0 = 0; b0 < nblk; b0 += 1024) {
+  for (int b0 = 0; b0 < nblk; b0 += 256) {
     const int i = b0 + threadIdx.x;
     const int v = i < nblk ? h[i] : 0;
     int tot;
@@ -207,51 +224,61 @@ __global__ void __launch_bounds__(1024) k_digit_scan(int32_t* __restrict__ hist,
   if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+// Stable scatter of one digit pass.  Items keep their input order within a
+// digit: the chunk's position of digit d is split among the warps in warp
+// order (each warp's count of d), and inside a warp among the rounds in order
+// and the lanes of a round in lane order.
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t Q, int shift,
     int nblk, const int32_t* __restrict__ offs, const int32_t* __restrict__ dtot,
     uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
-  __shared__ int base[256];
-  __shared__ int wcnt[kSortThreads / 32][256];
+  __shared__ int wpos[kSortWarps][256];
   __shared__ int tmp[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  int total;
-  const int dbase = block_exclusive_scan(dtot[t], tmp, total);  // start of digit t
-  base[t] = dbase + offs[t * nblk + blockIdx.x];
-  for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
-  __syncthreads();
-  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk;
   const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < 256 / 32; ++j) wpos[warp][lane + 32 * j] = 0;
+  __syncwarp();
+  const int64_t b0 = (int64_t)blockIdx.x * kSortChunk + (int64_t)warp * kWarpItems + lane;
+  uint32_t k[kSortItems];
+  int32_t v[kSortItems];
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = b0 + (int64_t)r * kSortThreads + t;
-    const bool valid = i < Q;
-    uint32_t k = 0;
-    int32_t v = 0;
-    int d = 256 + lane;  // unique sentinel for lanes without an item
+    const int64_t i = b0 + r * 32;
+    k[r] = i < Q ? kin[i] : 0u;
+    v[r] = i < Q ? vin[i] : 0;
+  }
+  unsigned peers[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = b0 + r * 32 < Q;
+    const int d = valid ? (int)((k[r] >> shift) & 255u) : 256 + lane;
+    peers[r] = __match_any_sync(0xffffffffu, d);
+    if (valid && lane == __ffs(peers[r]) - 1) atomicAdd(&wpos[warp][d], __popc(peers[r]));
+  }
+  int total;
+  const int dstart = block_exclusive_scan(dtot[t], tmp, total);  // start of digit t
+  // (block_exclusive_scan ends with a barrier: every warp's counts are in)
+  int base = dstart + offs[t * nblk + blockIdx.x];
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const int c = wpos[w][t];
+    wpos[w][t] = base;
+    base += c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = b0 + r * 32 < Q;
     if (valid) {
-      k = kin[i];
-      v = vin[i];
-      d = (k >> shift) & 255;
+      const int d = (int)((k[r] >> shift) & 255u);
+      const int pos = wpos[warp][d] + __popc(peers[r] & lt);
+      kout[pos] = k[r];
+      vout[pos] = v[r];
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt);
-    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      int pre = 0;
-      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
-      const int pos = base[d] + pre + rank;
-      kout[pos] = k;
-      vout[pos] = v;
-    }
-    __syncthreads();
-    int tot = 0;
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      tot += wcnt[w][t];
-      wcnt[w][t] = 0;
-    }
-    base[t] += tot;
-    __syncthreads();
+    __syncwarp();
+    if (valid && lane == __ffs(peers[r]) - 1) wpos[warp][(k[r] >> shift) & 255u] += __popc(peers[r]);
+    __syncwarp();
   }
 }
 
@@ -356,7 +383,7 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
     k_radix_hist<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], Q, shift, nblk, p->hist);
-    k_digit_scan<<<256, 1024, 0, s>>>(p->hist, nblk, p->digit_tot);
+    k_digit_scan<<<256, 256, 0, s>>>(p->hist, nblk, p->digit_tot);
     k_radix_scatter<<<nblk, kSortThreads, 0, s>>>(p->keys[cur], p->vals[cur], Q, shift, nblk,
                                                   p->hist, p->digit_tot, p->keys[cur ^ 1],
                                                   p->vals[cur ^ 1]);
