@@ -551,6 +551,7 @@ ib_status ib_plan_sync_status(ib_plan* p, void* stream) {
     return IB_ERR_CUDA;
   if (st & kStatNonfinite) return IB_ERR_NONFINITE;
   if (st & kStatInverted) return IB_ERR_INVERTED;
+  if (st & kStatTimeout) return IB_ERR_TIMEOUT;
   return IB_OK;
 }
 

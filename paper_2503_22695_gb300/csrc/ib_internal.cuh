@@ -16,6 +16,7 @@ constexpr int kChunk = 1024;        // maximum points per spread / interp work i
 // Device-side status bits latched by kernels (read by ib_plan_sync_status).
 constexpr int kStatNonfinite = 1;
 constexpr int kStatInverted = 2;
+constexpr int kStatTimeout = 4;
 
 // Material table passed by value to kernels.
 struct MatTable {
@@ -87,6 +88,7 @@ struct ib_plan {
   cudaEvent_t ev_fork, ev_join;      // spread zero-fill fork / join
   cudaEvent_t ev_ffork, ev_fsorted, ev_fjoin;  // ib_forward branch events
   int sm_count, push_ctas, merge_ctas, interp_ctas[3];
+  int interp_tma, interp_ctas_tma[3];  // FP32: TMA-staged interpolation available
   void* spread_scratch;  // Real [slots][3][12^3] halo'd per-tile blocks
   int32_t* q_cell;       // packed wrapped cell per Gauss point (unsorted, gq order)
   void* q_off;           // Real [3][Q]

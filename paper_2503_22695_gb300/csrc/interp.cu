@@ -4,11 +4,20 @@
 //   d/dchi_d sum_faces u^c prod phi = h^-1 sum_faces u^c phi'(r_d) prod_{d'!=d} phi(r_d').
 //
 // Persistent CTAs pull work items (at most 1024 consecutive points of one
-// 8^3-cell Eulerian tile) from a counter.  The tile's halo'd
-// 12^3 block of each velocity component (faces local -2..9 per axis, every
-// face any of its points can reach) is staged in shared memory with cp.async,
-// one item ahead (double buffer), and one thread per point evaluates its
-// three 4x4x4 stencils from shared memory.
+// 8^3-cell Eulerian tile) from a counter.  The tile's halo'd 12^3 block of
+// each velocity component (faces local -2..9 per axis, every face any of its
+// points can reach) is staged in shared memory and one thread per point
+// evaluates its three 4x4x4 stencils from there.
+//
+// FP32 plans stage the block with the Tensor Memory Accelerator: one thread
+// issues a 4-D tiled bulk copy (x 16 from face -4 so that the start is
+// 16-byte aligned, y 12, z 12, all 3 components) of the next item into a
+// dense buffer while the CTA evaluates the current item; the dense box is
+// then rewritten into the padded block layout (z stride 145, odd in banks)
+// that keeps the per-thread stencil gathers spread over the banks.  Tiles
+// whose halo crosses the periodic boundary are staged with cp.async and
+// explicit wrapping instead.  FP64 plans use the cp.async path throughout,
+// one item ahead in a double buffer.
 // Results are written at the point's original index gq = q*E + e for the
 // element-wise projection that follows.
 //
@@ -16,6 +25,10 @@
 //   0: a[c][gq] = w j0 * vscale * S_c                      (S_c = sum u^c prod phi)
 //   1: a as mode 0, and b[d][gq] = gscale * sum_c val_c dS_c/dr_d
 //   2: b only.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -45,6 +58,8 @@ struct InterpArgs {
   Real vscale, gscale;
   Real* out_a;
   Real* out_b;
+  int* status;
+  int use_tma;            // FP32: interior tiles staged by the tensor map
 };
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -119,6 +134,138 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
     b ^= 1;
   }
   cp_async_wait_group<0>();
+}
+
+// ---------------------------------------------------------------------------
+// TMA path (FP32)
+// ---------------------------------------------------------------------------
+constexpr int kDX = 16;                             // dense box x extent (faces -4..11)
+constexpr int kDenseFloats = 3 * kB * kB * kDX;     // 6912
+constexpr uint32_t kDenseBytes = kDenseFloats * 4;  // 27648 = one box, the tx count
+constexpr int kTmaAlign = 1024;
+constexpr long long kWaitCycles = 2000000000LL;     // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+    __nanosleep(64);
+  }
+}
+
+__device__ __forceinline__ bool tile_interior(const GridDev& g, int tile) {
+  const int nt0 = g.nt[0], nt1 = g.nt[1];
+  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  return tx > 0 && ty > 0 && tz > 0 && tx < nt0 - 1 && ty < nt1 - 1 && tz < g.nt[2] - 1;
+}
+
+// Thread 0: bulk tensor copy of the box around the tile of item `slot`.
+// Only interior tiles: x start 8 tx - 4 >= 0 is a multiple of 4 floats (16
+// bytes) and the box lies inside the grid.
+__device__ __forceinline__ void issue_box(const CUtensorMap* tmap, const GridDev& g, int tile,
+                                          uint32_t dense, uint32_t bar) {
+  const int nt0 = g.nt[0], nt1 = g.nt[1];
+  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  const int x = tx * kTile - 4, y = ty * kTile - 2, z = tz * kTile - 2, c = 0;
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+               "r"(kDenseBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dense),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(bar)
+      : "memory");
+}
+
+// dense box (faces x -4..11) -> padded block (faces x -2..9), one x-row per thread
+__device__ __forceinline__ void relayout(const float* __restrict__ dense, float* __restrict__ ub,
+                                         int tid) {
+  for (int row = tid; row < 3 * kB * kB; row += kThreads) {
+    const int c = row / (kB * kB), zy = row % (kB * kB), z = zy / kB, y = zy % kB;
+    const float4* src = reinterpret_cast<const float4*>(dense + row * kDX);
+    const float4 a = src[0], b = src[1], d = src[2], e = src[3];
+    float* dst = ub + c * kComp + z * kSZ + y * kSY;
+    dst[0] = a.z;  dst[1] = a.w;
+    dst[2] = b.x;  dst[3] = b.y;  dst[4] = b.z;  dst[5] = b.w;
+    dst[6] = d.x;  dst[7] = d.y;  dst[8] = d.z;  dst[9] = d.w;
+    dst[10] = e.x; dst[11] = e.y;
+  }
+}
+
+template <typename Real, int MODE>
+__device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
+                                              int tid);
+
+// Per item: wait for its box (or stage it with cp.async), rewrite it into the
+// padded block, issue the next item's box, evaluate the points.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__ CUtensorMap tmap,
+                                                         InterpArgs<float> A) {
+  extern __shared__ unsigned char smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + kTmaAlign - 1) &
+                         ~static_cast<uintptr_t>(kTmaAlign - 1);
+  float* const dense = reinterpret_cast<float*>(base);
+  float* const ub = dense + kDenseFloats;
+  __shared__ __align__(8) uint64_t bar_store;
+  __shared__ int next, abort_flag;
+  const int tid = threadIdx.x;
+  const int count = A.counters[0];
+  const uint32_t bar = smem_u32(&bar_store), dense_s = smem_u32(dense);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+    next = atomicAdd(A.counters + 2, 1);
+  }
+  __syncthreads();
+  int cur = next;
+  bool cur_tma = cur < count && tile_interior(A.g, A.tile_list[cur]);
+  if (tid == 0 && cur_tma) issue_box(&tmap, A.g, A.tile_list[cur], dense_s, bar);
+  uint32_t parity = 0;
+  while (cur < count) {
+    if (cur_tma) {
+      if (mbar_wait(bar, parity))
+        parity ^= 1;
+      else
+        abort_flag = 1;
+    } else {
+      stage_block(A, cur, ub, tid);
+      cp_async_commit();
+      cp_async_wait_group<0>();
+    }
+    if (tid == 0) next = atomicAdd(A.counters + 2, 1);
+    __syncthreads();  // box landed everywhere; next item known
+    if (abort_flag) break;
+    if (cur_tma) {
+      relayout(dense, ub, tid);
+      __syncthreads();  // dense free, padded block complete
+    }
+    const int nxt = next;
+    const bool nxt_tma = nxt < count && tile_interior(A.g, A.tile_list[nxt]);
+    if (tid == 0 && nxt_tma) issue_box(&tmap, A.g, A.tile_list[nxt], dense_s, bar);
+    interp_points<float, MODE>(A, cur, ub, tid);
+    __syncthreads();  // padded block free; `next` consumed
+    cur = nxt;
+    cur_tma = nxt_tma;
+  }
+  if (abort_flag && tid == 0) {
+    atomicOr(A.status, kStatTimeout);
+    mbar_wait(bar, parity);  // let a late box land before the CTA exits (bounded)
+  }
 }
 
 template <typename Real, int MODE>
@@ -214,6 +361,42 @@ size_t smem_bytes() {
   return sizeof(Real) * 2 * 3 * kComp;
 }
 
+constexpr size_t kTmaSmem = kTmaAlign + kDenseBytes + sizeof(float) * 3 * kComp;
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+  });
+  return fn;
+}
+
+// Tensor map of the velocity field u [3][n2][n1][n0] (float), box 16 x 12 x 12 x 3.
+// False when the driver function is missing or u is not 16-byte aligned.
+bool make_velocity_map(const ib_plan* p, const void* u, CUtensorMap* m) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(u) & 15) != 0) return false;
+  const cuuint64_t n0 = p->grid.n[0], n1 = p->grid.n[1], n2 = p->grid.n[2];
+  const cuuint64_t dims[4] = {n0, n1, n2, 3};
+  const cuuint64_t strides[3] = {n0 * 4, n0 * n1 * 4, n0 * n1 * n2 * 4};
+  const cuuint32_t box[4] = {kDX, kB, kB, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(u), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename Real>
 ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gscale,
                    cudaStream_t s) {
@@ -236,8 +419,23 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.gscale = (Real)gscale;
   A.out_a = (Real*)p->gq_a;
   A.out_b = (Real*)p->gq_b;
+  A.status = p->dstatus;
+  A.use_tma = 0;
   const size_t smem = smem_bytes<Real>();
   cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
+  if constexpr (sizeof(Real) == 4) {
+    CUtensorMap tmap;
+    if (p->interp_tma && make_velocity_map(p, u, &tmap)) {
+      A.use_tma = 1;
+      if (mode == 0)
+        k_interp_tma<0><<<p->interp_ctas_tma[0], kThreads, kTmaSmem, s>>>(tmap, A);
+      else if (mode == 1)
+        k_interp_tma<1><<<p->interp_ctas_tma[1], kThreads, kTmaSmem, s>>>(tmap, A);
+      else
+        k_interp_tma<2><<<p->interp_ctas_tma[2], kThreads, kTmaSmem, s>>>(tmap, A);
+      return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+    }
+  }
   if (mode == 0)
     k_interp_tile<Real, 0><<<p->interp_ctas[0], kThreads, smem, s>>>(A);
   else if (mode == 1)
@@ -267,6 +465,28 @@ ib_status prepare_t(ib_plan* p) {
   for (int m = 0; m < 3; ++m) {
     if (per_sm[m] < 1) return IB_ERR_CUDA;
     p->interp_ctas[m] = p->sm_count * per_sm[m];
+  }
+  p->interp_tma = 0;
+  if constexpr (sizeof(Real) == 4) {
+    int tma_sm[3] = {0, 0, 0};
+    const int ts = (int)kTmaSmem;
+    if (encode_tiled() &&
+        cudaFuncSetAttribute(k_interp_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_interp_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_interp_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[0], k_interp_tma<0>, kThreads, ts) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[1], k_interp_tma<1>, kThreads, ts) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[2], k_interp_tma<2>, kThreads, ts) ==
+            cudaSuccess &&
+        tma_sm[0] > 0 && tma_sm[1] > 0 && tma_sm[2] > 0) {
+      for (int m = 0; m < 3; ++m) p->interp_ctas_tma[m] = p->sm_count * tma_sm[m];
+      p->interp_tma = 1;
+    }
   }
   return IB_OK;
 }

@@ -398,16 +398,26 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
       }
     }
     __syncthreads();
-    // block values H 2^11 + L to float
+    // block values H 2^11 + L to float, one 12-face x-row per thread (432 rows)
     float* out = A.scratch + (int64_t)slot * kItemBlk;
-    for (int idx = tid; idx < kItemBlk; idx += kFxThreads) {
-      const int c = idx / kBlk, rr = idx % kBlk;
-      const int z = rr / (kB * kB), y = (rr / kB) % kB, x = rr % kB;
-      const int o = c * kFxAcc + z * kFxSZ + y * kFxSY + x;
-      const unsigned hw = acc_hi[o], lw = acc_lo[o];
-      const int L = (int)(lw << 10) >> 10;
-      const int H = (int)(hw - lw) + L;
-      out[idx] = fmaf((float)H, 2048.0f, (float)L) * out_scale;
+    for (int row = tid; row < 3 * kB * kB; row += kFxThreads) {
+      const int c = row / (kB * kB), zy = row % (kB * kB);
+      const int z = zy / kB, y = zy % kB;
+      const int o = c * kFxAcc + z * kFxSZ + y * kFxSY;  // even: 8-byte aligned
+      float r[kB];
+#pragma unroll
+      for (int x = 0; x < kB; x += 2) {
+        const uint2 hw = *reinterpret_cast<const uint2*>(acc_hi + o + x);
+        const uint2 lw = *reinterpret_cast<const uint2*>(acc_lo + o + x);
+        const int L0 = (int)(lw.x << 10) >> 10, L1 = (int)(lw.y << 10) >> 10;
+        const int H0 = (int)(hw.x - lw.x) + L0, H1 = (int)(hw.y - lw.y) + L1;
+        r[x] = fmaf((float)H0, 2048.0f, (float)L0) * out_scale;
+        r[x + 1] = fmaf((float)H1, 2048.0f, (float)L1) * out_scale;
+      }
+      float4* dst = reinterpret_cast<float4*>(out + row * kB);  // 48-byte rows
+#pragma unroll
+      for (int j = 0; j < kB / 4; ++j)
+        dst[j] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
     }
   }
 }
