@@ -129,7 +129,9 @@ struct Stage {
 };
 
 int sort_launches(const ib_plan* p) {
-  // radix passes (hist, digit scan, scatter), bounds, classify, compact, reorder
+  // FP32 binning: classify, compact (ranges), scatter.  FP64: radix passes
+  // (hist, digit scan, scatter), bounds, classify, compact, reorder
+  if (p->precision != IB_FP64) return 3;
   return 3 * ((sort_key_bits(p->ntiles) + 7) / 8) + 4;
 }
 
@@ -283,7 +285,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
               dalloc(&p->tile_near, 4 * (size_t)p->ntiles) &&
               dalloc(&p->tile_list, 4 * (size_t)max_work_items(p->ntiles, Q)) &&
               dalloc(&p->tile_list_near, 4 * (size_t)p->ntiles) &&
-              dalloc(&p->tile_bcount, 8 * (size_t)classify_blocks(p->ntiles)) &&
+              dalloc(&p->tile_bcount, 12 * (size_t)classify_blocks(p->ntiles)) &&
               dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
               dalloc(&p->rpart, 8 * 9 * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
               dalloc(&p->spread_scratch,

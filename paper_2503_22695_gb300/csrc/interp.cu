@@ -103,7 +103,7 @@ __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot,
 
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid);
+                                              int tid, const short* order);
 
 // Persistent CTAs, two-stage pipeline: the velocity block of the next work
 // item is fetched while the points of the current one are evaluated.
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
     cp_async_commit();
     cp_async_wait_group<1>();  // the current item's block has landed
     __syncthreads();
-    interp_points<Real, MODE>(A, cur, buf0 + b * 3 * kComp, tid);
+    interp_points<Real, MODE>(A, cur, buf0 + b * 3 * kComp, tid, nullptr);
     cur = nxt;
     b ^= 1;
   }
@@ -208,12 +208,53 @@ __device__ __forceinline__ void relayout(const float* __restrict__ dense, float*
 
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid);
+                                              int tid, const short* order);
+
+// Binned points arrive in no particular order inside a tile; threads of a
+// warp then often gather the same bank.  Order the item's points by cell of
+// the tile (a counting sort over the 512 cells; points of one cell in any
+// order, which changes no result), so a warp covers a run of neighbouring
+// cells, as sorted points would.
+__device__ __forceinline__ void local_cell_order(const InterpArgs<float>& A, int slot, int* cnt,
+                                                 short* order, int* tmp, int tid) {
+  const int tile = A.tile_list[slot];
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
+  const int e = min(A.tile_end[tile], s + kChunk);
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int x0 = (tile % nt0) * kTile, y0 = ((tile / nt0) % nt1) * kTile,
+            z0 = (tile / (nt0 * nt1)) * kTile;
+  cnt[tid] = 0;
+  cnt[tid + kThreads] = 0;
+  __syncthreads();
+  int cell[kChunk / kThreads], rank[kChunk / kThreads];
+#pragma unroll
+  for (int k = 0; k < kChunk / kThreads; ++k) {
+    const int i = s + tid + k * kThreads;
+    if (i < e) {
+      int cx, cy, cz;
+      unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
+      cell[k] = ((cz - z0) * kTile + (cy - y0)) * kTile + (cx - x0);
+      rank[k] = atomicAdd(cnt + cell[k], 1);
+    }
+  }
+  __syncthreads();
+  const int c0 = cnt[2 * tid], c1 = cnt[2 * tid + 1];
+  int tot;
+  const int pre = block_exclusive_scan(c0 + c1, tmp, tot);
+  cnt[2 * tid] = pre;
+  cnt[2 * tid + 1] = pre + c0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kChunk / kThreads; ++k) {
+    const int i = s + tid + k * kThreads;
+    if (i < e) order[cnt[cell[k]] + rank[k]] = (short)(i - s);
+  }
+}
 
 // Per item: wait for its box (or stage it with cp.async), rewrite it into the
 // padded block, issue the next item's box, evaluate the points.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(const __grid_constant__ CUtensorMap tmap,
                                                          InterpArgs<float> A) {
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + kTmaAlign - 1) &
@@ -222,6 +263,8 @@ __global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__
   float* const ub = dense + kDenseFloats;
   __shared__ __align__(8) uint64_t bar_store;
   __shared__ int next, abort_flag;
+  __shared__ int cnt[2 * kThreads], tmp[32];
+  __shared__ short order[kChunk];
   const int tid = threadIdx.x;
   const int count = A.counters[0];
   const uint32_t bar = smem_u32(&bar_store), dense_s = smem_u32(dense);
@@ -237,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__
   if (tid == 0 && cur_tma) issue_box(&tmap, A.g, A.tile_list[cur], dense_s, bar);
   uint32_t parity = 0;
   while (cur < count) {
+    local_cell_order(A, cur, cnt, order, tmp, tid);  // while the box is in flight
     if (cur_tma) {
       if (mbar_wait(bar, parity))
         parity ^= 1;
@@ -257,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__
     const int nxt = next;
     const bool nxt_tma = nxt < count && tile_interior(A.g, A.tile_list[nxt]);
     if (tid == 0 && nxt_tma) issue_box(&tmap, A.g, A.tile_list[nxt], dense_s, bar);
-    interp_points<float, MODE>(A, cur, ub, tid);
+    interp_points<float, MODE>(A, cur, ub, tid, order);
     __syncthreads();  // padded block free; `next` consumed
     cur = nxt;
     cur_tma = nxt_tma;
@@ -270,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tma(const __grid_constant__
 
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid) {
+                                              int tid, const short* order) {
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
   const int e = min(A.tile_end[tile], s + kChunk);
@@ -278,7 +322,8 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
 
-  for (int i = s + tid; i < e; i += kThreads) {
+  for (int j = s + tid; j < e; j += kThreads) {
+    const int i = order ? s + order[j - s] : j;
     int cx, cy, cz;
     unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
     const int lc[3] = {cx - x0, cy - y0, cz - z0};

@@ -12,7 +12,15 @@
 // warp match masks): points are grouped by tile, ordered by cell inside a tile
 // (so neighbouring threads read neighbouring faces), and equal keys keep gq
 // order, so the sorted sequence -- hence every downstream summation order --
-// is identical on every call.
+// is identical on every call.  That path serves FP64 plans, whose spreading
+// sums doubles in point order.
+//
+// FP32 plans bin instead of sorting: their spreading accumulates exact
+// integers and their interpolation is per point, so a point's place inside
+// its tile does not change any result.  k_points counts the points of each
+// tile with warp-aggregated integer atomics and keeps each point's slot, one
+// scan turns the counts into tile ranges, and one scatter writes the
+// tile-grouped arrays.
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -38,10 +46,11 @@ struct PtArgs {
   Real* q_val;           // [3][Q]
   uint32_t* key;
   int32_t* val;
+  int32_t* count;        // binning: points per tile
   int* status;
 };
 
-template <typename Real>
+template <typename Real, bool kBin>
 __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.E) return;
@@ -111,9 +120,21 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
     const uint32_t tile = (uint32_t)((cw[0] >> kTileShift) +
                                      A.g.nt[0] * ((cw[1] >> kTileShift) +
                                                   A.g.nt[1] * (cw[2] >> kTileShift)));
-    const uint32_t local = (uint32_t)((((cw[2] & 7) << 3) | (cw[1] & 7)) << 3 | (cw[0] & 7));
-    A.key[gq] = (tile << kLocalBits) | local;
-    A.val[gq] = (int32_t)gq;
+    if (kBin) {
+      // slot of the point in its tile: one atomic per distinct tile of the warp
+      const unsigned act = __activemask();
+      const unsigned peers = __match_any_sync(act, tile);
+      const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(A.count + tile, __popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      A.key[gq] = tile;
+      A.val[gq] = base + __popc(peers & ((1u << lane) - 1u));
+    } else {
+      const uint32_t local = (uint32_t)((((cw[2] & 7) << 3) | (cw[1] & 7)) << 3 | (cw[0] & 7));
+      A.key[gq] = (tile << kLocalBits) | local;
+      A.val[gq] = (int32_t)gq;
+    }
     if (A.V) {
       const Real w = __ldg(A.wj0 + gq);
 #pragma unroll
@@ -282,6 +303,28 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
   }
 }
 
+// Binning: every point to start[tile] + slot, with its cell, offset, index
+// and (optionally) carried value.
+template <typename Real>
+__global__ void k_bin_scatter(int64_t Q, const uint32_t* __restrict__ tile,
+                              const int32_t* __restrict__ slot, const int32_t* __restrict__ start,
+                              const int32_t* __restrict__ q_cell, const Real* __restrict__ q_off,
+                              const Real* __restrict__ q_val, int32_t* __restrict__ p_cell,
+                              Real* __restrict__ p_off, Real* __restrict__ p_val,
+                              int32_t* __restrict__ p_idx, bool with_val) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Q) return;
+  const int64_t i = __ldg(start + __ldg(tile + g)) + __ldg(slot + g);
+  p_idx[i] = (int32_t)g;
+  p_cell[i] = __ldg(q_cell + g);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p_off[d * Q + i] = __ldg(q_off + d * Q + g);
+  if (with_val) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p_val[d * Q + i] = __ldg(q_val + d * Q + g);
+  }
+}
+
 __global__ void k_tile_bounds(const uint32_t* __restrict__ key, int64_t Q,
                               int32_t* __restrict__ start, int32_t* __restrict__ end) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,7 +377,10 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   A.key = p->keys[0];
   A.val = p->vals[0];
   A.status = p->dstatus;
-  k_points<float><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  A.count = p->tile_end;
+  cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
+  cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
+  k_points<float, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -359,7 +405,8 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
   A.key = p->keys[0];
   A.val = p->vals[0];
   A.status = p->dstatus;
-  k_points<double><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  A.count = nullptr;
+  k_points<double, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -375,6 +422,20 @@ ib_status launch_points(ib_plan* p, const void* xa, const float* off, const void
 
 ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
   const int64_t Q = p->Q;
+  if (p->precision != IB_FP64) {  // binning: counts in tile_end, tile_start zero
+    if (Q == 0) {  // no points were built: no counts either
+      cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
+      cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
+    }
+    if (launch_classify_tiles(p, s) != IB_OK) return IB_ERR_CUDA;  // also the ranges
+    if (Q == 0) return IB_OK;
+    const int nb = (int)((Q + 255) / 256);
+    k_bin_scatter<float><<<nb, 256, 0, s>>>(Q, p->keys[0], p->vals[0], p->tile_start, p->q_cell,
+                                            (const float*)p->q_off, (const float*)p->q_val,
+                                            p->p_cell, (float*)p->p_off, (float*)p->p_val,
+                                            p->p_idx, with_val);
+    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+  }
   cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
   cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
   if (Q == 0) return launch_classify_tiles(p, s);

@@ -305,6 +305,15 @@ __device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float w, floa
   atomicAdd(lo, __float_as_uint(t2));
 }
 
+// Fixed-point exponent k of the call: |C| = |V scale| prod phi < 2^19 in
+// units of 2^-k, since every kernel weight product is at most 1/8.
+__device__ __forceinline__ int fx_exponent(const SpreadArgs<float>& A) {
+  const float cmax = 0.125f * __uint_as_float(*A.absmax) * fabsf(A.scale);
+  int ex = 0;
+  if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
+  return min(19 - ex, 100);           // keep 2^(k+11) a normal float
+}
+
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FxStage& stage = *reinterpret_cast<FxStage*>(smem_raw);
@@ -317,13 +326,8 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
   // this lane's (dz, dy, xh) and its offset within a stencil
   const int ldz = lane >> 3, ldy = (lane >> 1) & 3, lxh = lane & 1;
   const int loff = ldz * kFxSZ + ldy * kFxSY + lxh;
-  // fixed-point scale of the call
-  const float cmax = 0.125f * __uint_as_float(*A.absmax) * fabsf(A.scale);
-  int ex = 0;
-  if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
-  const int k = min(19 - ex, 100);  // keep 2^(k+11) a normal float
+  const int k = fx_exponent(A);
   const float vscale = A.scale * ldexpf(1.f, k);
-  const float out_scale = ldexpf(1.f, -(k + 11));
   for (;;) {
     __syncthreads();
     if (tid == 0) next = atomicAdd(A.counters + 1, 1);
@@ -398,26 +402,20 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
       }
     }
     __syncthreads();
-    // block values H 2^11 + L to float, one 12-face x-row per thread (432 rows)
-    float* out = A.scratch + (int64_t)slot * kItemBlk;
+    // decoded words (H, L) of every face, exact, one 12-face x-row per thread
+    int2* out = reinterpret_cast<int2*>(A.scratch) + (int64_t)slot * kItemBlk;
     for (int row = tid; row < 3 * kB * kB; row += kFxThreads) {
       const int c = row / (kB * kB), zy = row % (kB * kB);
       const int z = zy / kB, y = zy % kB;
       const int o = c * kFxAcc + z * kFxSZ + y * kFxSY;  // even: 8-byte aligned
-      float r[kB];
+      int4* dst = reinterpret_cast<int4*>(out + row * kB);  // 96-byte rows
 #pragma unroll
       for (int x = 0; x < kB; x += 2) {
         const uint2 hw = *reinterpret_cast<const uint2*>(acc_hi + o + x);
         const uint2 lw = *reinterpret_cast<const uint2*>(acc_lo + o + x);
         const int L0 = (int)(lw.x << 10) >> 10, L1 = (int)(lw.y << 10) >> 10;
-        const int H0 = (int)(hw.x - lw.x) + L0, H1 = (int)(hw.y - lw.y) + L1;
-        r[x] = fmaf((float)H0, 2048.0f, (float)L0) * out_scale;
-        r[x + 1] = fmaf((float)H1, 2048.0f, (float)L1) * out_scale;
+        dst[x / 2] = make_int4((int)(hw.x - lw.x) + L0, L0, (int)(hw.y - lw.y) + L1, L1);
       }
-      float4* dst = reinterpret_cast<float4*>(out + row * kB);  // 48-byte rows
-#pragma unroll
-      for (int j = 0; j < kB / 4; ++j)
-        dst[j] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
     }
   }
 }
@@ -509,6 +507,89 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   }
 }
 
+// FP32 plans: the same fixed-order walk over the covering blocks, summing the
+// exact words of every face in integers (H in 64 bits, L in 32) and rounding
+// once: S = 2^11 sum H + sum L is below 2^47, split as 2^24 hi + lo with both
+// parts exact in float, so one fma gives the correctly rounded S, then scaled
+// by 2^-(k+11).  The result does not depend on how a tile's points were cut
+// into work items.
+__global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
+  __shared__ int src_slot[27], src_n[27];
+  const int tid = threadIdx.x;
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int n0 = A.g.n[0], n1 = A.g.n[1];
+  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
+  const int count = A.counters[3];
+  const float out_scale = ldexpf(1.f, -(fx_exponent(A) + 11));
+  const int4* scratch = reinterpret_cast<const int4*>(A.scratch);  // 2 faces per int4
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const int tile = A.tile_list_near[k];
+    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+    __syncthreads();
+    if (tid < 27) {
+      const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
+      const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
+      src_slot[tid] = A.tile_slot[nb];
+      src_n[tid] = A.tile_nitems[nb];
+    }
+    __syncthreads();
+    if (tid < 3 * 64) {
+      const int c = tid >> 6, z = (tid >> 3) & 7, y = tid & 7;
+      const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
+      const int hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
+      long long sh[8];
+      int sl[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        sh[x] = 0;
+        sl[x] = 0;
+      }
+      for (int oz = lz; oz <= hz; ++oz)
+        for (int oy = ly; oy <= hy; ++oy) {
+          // row of 12 faces = 6 int4 (96 bytes)
+          const int rowoff =
+              (c * kBlk + ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * kB) / 2;
+          const int s0 = (oz + 1) * 9 + (oy + 1) * 3;
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int slt = src_slot[s0 + ox + 1], ns = src_n[s0 + ox + 1];
+            for (int j = 0; j < ns; ++j) {
+              const int4* r = scratch + ((int64_t)(slt + j) * kItemBlk) / 2 + rowoff;
+              if (ox < 0) {          // faces 0,1 from the left neighbour's block x 10,11
+                const int4 v = r[5];
+                sh[0] += v.x; sl[0] += v.y; sh[1] += v.z; sl[1] += v.w;
+              } else if (ox > 0) {   // faces 6,7 from the right neighbour's block x 0,1
+                const int4 v = r[0];
+                sh[6] += v.x; sl[6] += v.y; sh[7] += v.z; sl[7] += v.w;
+              } else {               // block x 2..9
+                int4 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = r[1 + q];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  sh[2 * q] += v[q].x; sl[2 * q] += v[q].y;
+                  sh[2 * q + 1] += v[q].z; sl[2 * q + 1] += v[q].w;
+                }
+              }
+            }
+          }
+        }
+      float o[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const long long S = sh[x] * 2048 + sl[x];
+        const long long hi = S >> 24;
+        const int lo = (int)(S & 0xFFFFFF);
+        o[x] = fmaf((float)hi, 16777216.0f, (float)lo) * out_scale;
+      }
+      float4* out = reinterpret_cast<float4*>(A.f + c * cells +
+                                              ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0);
+      out[0] = make_float4(o[0], o[1], o[2], o[3]);
+      out[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+  }
+}
+
 template <typename Real>
 size_t push_smem() {
   return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
@@ -554,7 +635,10 @@ ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
   k_spread_zero<Real><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
   cudaEventRecord(p->ev_join, p->zside);
   launch_push(p, A, s);
-  k_spread_merge<Real><<<p->merge_ctas, kMT, 0, s>>>(A);
+  if constexpr (sizeof(Real) == 4)
+    k_spread_merge_fx<<<p->merge_ctas, kMT, 0, s>>>(A);
+  else
+    k_spread_merge<Real><<<p->merge_ctas, kMT, 0, s>>>(A);
   cudaStreamWaitEvent(s, p->ev_join, 0);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
@@ -579,8 +663,13 @@ ib_status prepare_t(ib_plan* p) {
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push<Real>, kPT, smem);
   }
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<Real>, kMT, 0);
+  if (e == cudaSuccess) {
+    if constexpr (sizeof(Real) == 4)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge_fx, kMT, 0);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<Real>, kMT,
+                                                        0);
+  }
   if (e != cudaSuccess || per_sm < 1 || per_sm_merge < 1) return IB_ERR_CUDA;
   p->sm_count = sms;
   p->push_ctas = sms * per_sm;
@@ -591,7 +680,8 @@ ib_status prepare_t(ib_plan* p) {
 }  // namespace
 
 size_t spread_scratch_bytes(int precision, int64_t slots) {
-  return (size_t)slots * kItemBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(float));
+  // FP64: one double per face; FP32: the exact word pair (H, L) per face
+  return (size_t)slots * kItemBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(int2));
 }
 
 ib_status spread_prepare(ib_plan* p) {

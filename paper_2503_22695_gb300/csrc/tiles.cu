@@ -25,12 +25,13 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
                                                  int32_t* __restrict__ bcount) {
   __shared__ int tmp[32];
   const int t = blockIdx.x * kT + threadIdx.x;
-  int ne = 0, nr = 0, nch = 0;
+  int ne = 0, nr = 0, nch = 0, npt = 0;
   if (t < ntiles) {
     const int nt0 = g.nt[0], nt1 = g.nt[1], nt2 = g.nt[2];
     const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
-    ne = end[t] > start[t];
-    nch = (end[t] - start[t] + kChunk - 1) / kChunk;
+    npt = end[t] - start[t];
+    ne = npt > 0;
+    nch = (npt + kChunk - 1) / kChunk;
     nr = ne;
     for (int a = -1; a <= 1 && !nr; ++a)
       for (int b = -1; b <= 1 && !nr; ++b)
@@ -42,53 +43,67 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
     nonempty[t] = nch;
     near[t] = nr;
   }
-  int cne;
+  int cne, cpt;
   block_exclusive_scan(nch, tmp, cne);
+  block_exclusive_scan(npt, tmp, cpt);
   const int cnr = __syncthreads_count(nr);
   if (threadIdx.x == 0) {
-    bcount[2 * blockIdx.x] = cne;
-    bcount[2 * blockIdx.x + 1] = cnr;
+    bcount[3 * blockIdx.x] = cne;
+    bcount[3 * blockIdx.x + 1] = cnr;
+    bcount[3 * blockIdx.x + 2] = cpt;
   }
 }
 
 // counters: [0] work items, [1] push / [2] interp work counters, [3] near tiles.
+// Also rewrites the tile point ranges as start = points of the tiles before,
+// end = start + points (the same ranges for sorted points; the ranges
+// themselves for binned points, whose counts arrive as start 0, end n).
 __global__ void __launch_bounds__(kT) k_compact(const int32_t* __restrict__ nonempty,
                                                 const int32_t* __restrict__ near, int ntiles,
                                                 const int32_t* __restrict__ bcount, int nblocks,
+                                                int32_t* __restrict__ start,
+                                                int32_t* __restrict__ end,
                                                 int32_t* __restrict__ slot,
                                                 int32_t* __restrict__ work,
                                                 int32_t* __restrict__ list_near,
                                                 int32_t* __restrict__ counters) {
   __shared__ int tmp[32];
-  __shared__ int base[2];
+  __shared__ int base[3];
   // offsets: sums of the counts of the CTAs before this one
-  int ne_before = 0, nr_before = 0, ne_all = 0, nr_all = 0;
+  int ne_before = 0, nr_before = 0, np_before = 0, ne_all = 0, nr_all = 0;
   for (int b = threadIdx.x; b < nblocks; b += kT) {
-    const int a = bcount[2 * b], c = bcount[2 * b + 1];
+    const int a = bcount[3 * b], c = bcount[3 * b + 1], d = bcount[3 * b + 2];
     if (b < (int)blockIdx.x) {
       ne_before += a;
       nr_before += c;
+      np_before += d;
     }
     ne_all += a;
     nr_all += c;
   }
-  int t0, t1, t2, t3;
+  int t0, t1, t2, t3, t4;
   block_exclusive_scan(ne_before, tmp, t0);
   block_exclusive_scan(nr_before, tmp, t1);
   block_exclusive_scan(ne_all, tmp, t2);
   block_exclusive_scan(nr_all, tmp, t3);
+  block_exclusive_scan(np_before, tmp, t4);
   if (threadIdx.x == 0) {
     base[0] = t0;
     base[1] = t1;
+    base[2] = t4;
   }
   __syncthreads();
   const int t = blockIdx.x * kT + threadIdx.x;
   const int ne = t < ntiles ? nonempty[t] : 0;
   const int nr = t < ntiles ? near[t] : 0;
+  const int np = t < ntiles ? end[t] - start[t] : 0;
   int tot;
   const int pne = block_exclusive_scan(ne, tmp, tot);
   const int pnr = block_exclusive_scan(nr, tmp, tot);
+  const int pnp = block_exclusive_scan(np, tmp, tot);
   if (t < ntiles) {
+    start[t] = base[2] + pnp;
+    end[t] = base[2] + pnp + np;
     slot[t] = ne ? base[0] + pne : -1;
     for (int j = 0; j < ne; ++j) work[base[0] + pne + j] = t;
     if (nr) list_near[base[1] + pnr] = t;
@@ -112,7 +127,8 @@ ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s) {
   k_classify<<<nb, kT, 0, s>>>(p->grid, p->tile_start, p->tile_end, nt, p->tile_nonempty,
                                p->tile_near, p->tile_bcount);
   k_compact<<<nb, kT, 0, s>>>(p->tile_nonempty, p->tile_near, nt, p->tile_bcount, nb,
-                              p->tile_slot, p->tile_list, p->tile_list_near, p->tile_counters);
+                              p->tile_start, p->tile_end, p->tile_slot, p->tile_list,
+                              p->tile_list_near, p->tile_counters);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
