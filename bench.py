@@ -4,9 +4,10 @@ One step = the forward coupling (FE force + spreading + interpolation,
 ib_forward) over the 256^3 workload: a Holzapfel-Ogden ventricle-like shell
 (160x100x10 hexes) plus two fibre-reinforced leaflet-like sheets (80x40x2
 each), 172,800 elements, 1,382,400 Gauss points, 16-mode velocity field.
-Inputs are seeded and synthetic (inputs.py).  The adjoint (interp_adj +
-spread_adj + fe_force_adj with parameter gradients) is timed the same way and
-reported as the adjoint/forward ratio.
+Inputs are seeded and synthetic (inputs.py).  The adjoint (ib_backward: the
+fused backward of the step for cotangents of f and U, with position, velocity
+and material-parameter gradients) is timed the same way and reported as the
+adjoint/forward ratio.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -300,15 +301,12 @@ def run_ours(args):
     gU = torch.from_numpy(rng.normal(size=(3, N)).astype(np.float32)).to(dev)
     gf = torch.from_numpy((rng.normal(size=(3, n, n, n)) * 1e-3).astype(np.float32)).to(dev)
     gu = torch.empty_like(u)
-    gx1 = torch.empty((3, N), device=dev)
-    gx2 = torch.empty((3, N), device=dev)
-    gG = torch.empty((3, N), device=dev)
-    Hv = torch.empty((3, N), device=dev)
+    gx = torch.empty((3, N), device=dev)
 
     def adj():
-        ibfe.ib_interp_adj(plan, pos, u, gU, True, gu, gx1)
-        ibfe.ib_spread_adj(plan, pos, G, gf, True, gG, gx2)
-        ibfe.ib_fe_force_adj(plan, mats, pos, gG, True, Hv)
+        # the backward of the forward step for cotangents of f and U: position,
+        # velocity and material-parameter gradients (one fused call)
+        ibfe.ib_backward(plan, mats, pos, u, G, None, gf, gU, gx, gu)
 
     for _ in range(args.warmup):
         adj()
@@ -364,8 +362,7 @@ def run_ours(args):
                 U=torch.empty((3, N_i), device=dev),
                 gU=torch.from_numpy(brng.normal(size=(3, N_i)).astype(np.float32)).to(dev),
                 gf=torch.from_numpy((brng.normal(size=sh) * 1e-3).astype(np.float32)).to(dev),
-                gu=torch.empty(sh, device=dev), gx=torch.empty((3, N_i), device=dev),
-                gG=torch.empty((3, N_i), device=dev), Hv=torch.empty((3, N_i), device=dev)))
+                gu=torch.empty(sh, device=dev), gx=torch.empty((3, N_i), device=dev)))
         batch = ibfe.Batch(binst)
         for _ in range(args.warmup):
             batch.forward()

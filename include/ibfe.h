@@ -174,16 +174,33 @@ ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats
                           const ib_pos* x, const void* v, void* Hv, double* gparams,
                           void* stream);
 
+/* Backward of ib_forward (its vector-Jacobian product), fused: given the
+ * cotangents gG [3][N], gf [3][grid] and gU [3][N] of the forward outputs G,
+ * f and U (device Real; any may be NULL, meaning zero), computes
+ *   gx = (dG/dx)^T gG_t + (df/dx)^T gf + (dU/dx)^T gU   (device Real [3][N]),
+ *        with gG_t = gG + (df/dG)^T gf, the spreading's share of the force cotangent;
+ *   gu = (dU/du)^T gU                                   (device Real [3][grid], if gu);
+ *   gparams[m][k] = gG_t . dG/dtheta_{m,k}              (device double [n_mats][9], if gparams).
+ * This is the composition of ib_spread_adj, ib_interp_adj and ib_fe_force_adj
+ * (Section 4.4: spreading and interpolation are adjoint to each other), with
+ * the Gauss points built and binned once and the force adjoint (FP64-pipe
+ * bound) run beside the interpolation adjoint.  G must be the nodal force of
+ * the forward at the same x (needed when gf is given).  gx is overwritten;
+ * gu must be given when gU is, and is overwritten (bitwise reproducible).
+ * Asynchronous on `stream`; errors: IB_ERR_INVALID_ARG (missing or
+ * misaligned arguments), the launch and device errors of its parts. */
+ib_status ib_backward(ib_plan* plan, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                      const void* u, const void* G, const void* gG, const void* gf,
+                      const void* gU, void* gx, void* gu, double* gparams, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched form: many independent structures, each with its own mesh, grid
  * and material table (a parameter sweep, for instance), run together.  The
  * paper runs one structure at a time; batching is a service of this library.
  * ib_batch_create builds one plan per instance and captures two CUDA graphs
  * whose branches are the instances' forward coupling (ib_forward) and
- * adjoint (ib_interp_adj with position gradient, ib_spread_adj with position
- * gradient, ib_fe_force_adj of the spread cotangent's nodal part, parameter
- * gradients kept on the device); each graph is then replayed with one
- * launch.  All pointers in ib_instance are device memory that must stay
+ * backward (ib_backward, parameter gradients kept on the device); each graph
+ * is then replayed with one launch.  All pointers in ib_instance are device memory that must stay
  * valid and fixed for the batch's lifetime (the graphs bake them in); update
  * the data in place between replays.  Synchronises `stream` at creation.
  * ------------------------------------------------------------------------- */
@@ -197,23 +214,23 @@ typedef struct {
   void* G;        /* [3][N]   forward outputs */
   void* f;        /* [3][grid] */
   void* U;        /* [3][N] */
-  const void* gU; /* [3][N]    adjoint inputs (cotangents of U and f); NULL: no adjoint */
+  const void* gU; /* [3][N]    backward inputs: cotangents of U, f (NULL: no backward) */
   const void* gf; /* [3][grid] */
-  void* gu;       /* [3][grid] adjoint outputs: d/du */
-  void* gx;       /* [3][N]    d/dx from interpolation and spreading */
-  void* gG;       /* [3][N]    d/dG from spreading */
-  void* Hv;       /* [3][N]    (dG/dx) gG: the force kernel's position term */
+  const void* gG; /* [3][N]    cotangent of G, or NULL (zero) */
+  void* gu;       /* [3][grid] backward outputs (ib_backward): d/du */
+  void* gx;       /* [3][N]    d/dx, all three terms */
 } ib_instance;
 
 typedef struct ib_batch ib_batch;
 
 ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision, void* stream,
                           ib_batch** out);
-/* Replay the forward (resp. adjoint) graph on `stream` (asynchronous). */
+/* Replay the forward (resp. backward) graph on `stream` (asynchronous). */
 ib_status ib_batch_forward(ib_batch* batch, void* stream);
 ib_status ib_batch_adjoint(ib_batch* batch, void* stream);
-/* Parameter gradients v . dG/dtheta of every instance's last adjoint replay,
- * host double [n][IB_MAX_MATERIALS][9]; synchronises `stream`. */
+/* Parameter gradients (ib_backward's gparams) of every instance's last
+ * backward replay, host double [n][IB_MAX_MATERIALS][9] (entries past an
+ * instance's n_mats are zero); synchronises `stream`. */
 ib_status ib_batch_gparams(ib_batch* batch, double* gparams, void* stream);
 ib_status ib_batch_destroy(ib_batch* batch);
 

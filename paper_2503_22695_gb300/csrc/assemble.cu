@@ -11,13 +11,14 @@ namespace {
 
 constexpr int kIncShift = 28;  // incidence entry: corner << 28 | element
 
-// out[c][n] = scale[n] * sum_{(a,e) in inc(n)} elem[(a*ncomp + c)*E + e]
+// out[c][n] = add[c][n] + scale[n] * sum_{(a,e) in inc(n)} elem[(a*ncomp + c)*E + e]
+// (add and scale optional; add may be out itself)
 template <typename Real, int NC>
 __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__ inc_off,
                                                      const int32_t* __restrict__ inc_idx,
                                                      const Real* __restrict__ elem,
-                                                     const Real* __restrict__ scale, int N,
-                                                     int E, Real* __restrict__ out) {
+                                                     const Real* __restrict__ scale,
+                                                     const Real* add, int N, int E, Real* out) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   Real acc[NC];
@@ -32,7 +33,10 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
   }
   const Real s = scale ? __ldg(scale + n) : Real(1);
 #pragma unroll
-  for (int c = 0; c < NC; ++c) out[(int64_t)c * N + n] = acc[c] * s;
+  for (int c = 0; c < NC; ++c) {
+    const int64_t o = (int64_t)c * N + n;
+    out[o] = add ? add[o] + acc[c] * s : acc[c] * s;
+  }
 }
 
 // out[(a*NC + c)*E + e] = sum_q N_a(xi_q) vals[c][q*E + e]
@@ -100,16 +104,18 @@ __global__ void k_invert(const Real* __restrict__ m, Real* __restrict__ im, int 
 }
 
 template <typename Real>
-ib_status gather_t(ib_plan* p, const void* elem, const void* scale, void* out, int nc,
-                   cudaStream_t s) {
+ib_status gather_t(ib_plan* p, const void* elem, const void* scale, const void* add, void* out,
+                   int nc, cudaStream_t s) {
   if (p->N == 0) return IB_OK;
   const int blocks = (p->N + 255) / 256;
   if (nc == 3)
     k_node_gather<Real, 3><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
-                                                  (const Real*)scale, p->N, p->E, (Real*)out);
+                                                  (const Real*)scale, (const Real*)add, p->N,
+                                                  p->E, (Real*)out);
   else
     k_node_gather<Real, 1><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
-                                                  (const Real*)scale, p->N, p->E, (Real*)out);
+                                                  (const Real*)scale, (const Real*)add, p->N,
+                                                  p->E, (Real*)out);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -134,7 +140,7 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
   // m_a = sum_{(e,q) containing a} N_a(xi_q) w_q j0
   ib_status st = project_t<Real>(p, p->wj0, p->elem_scratch, 1, s);
   if (st != IB_OK) return st;
-  st = gather_t<Real>(p, p->elem_scratch, nullptr, p->mass, 1, s);
+  st = gather_t<Real>(p, p->elem_scratch, nullptr, nullptr, p->mass, 1, s);
   if (st != IB_OK) return st;
   if (p->N > 0)
     k_invert<Real><<<(p->N + 255) / 256, 256, 0, s>>>((const Real*)p->mass, (Real*)p->inv_mass,
@@ -145,9 +151,9 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
 }  // namespace
 
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* scale, void* out,
-                             cudaStream_t s) {
-  return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, out, 3, s)
-                                 : gather_t<float>(p, elem, scale, out, 3, s);
+                             cudaStream_t s, const void* add) {
+  return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, add, out, 3, s)
+                                 : gather_t<float>(p, elem, scale, add, out, 3, s);
 }
 
 ib_status launch_elem_project(ib_plan* p, const void* vals, void* out, cudaStream_t s) {

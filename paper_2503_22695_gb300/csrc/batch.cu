@@ -6,8 +6,8 @@
 // graphs (a root event fans out to the branch streams and every branch joins
 // back), so one cudaGraphLaunch replays the whole batch: no per-instance host
 // work, and the GPU overlaps the instances' kernels.  Each branch is exactly
-// the single-instance call sequence, so every instance's results are bitwise
-// those of the individual entry points.
+// the single-instance call (ib_forward, ib_backward), so every instance's
+// results are bitwise those of the individual entry points.
 #include <cstring>
 #include <vector>
 
@@ -20,7 +20,7 @@ struct ib_batch {
   std::vector<ib_plan*> plans;
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> done;
-  std::vector<void*> tmp_gx;  // spread part of d/dx, added into gx
+  double* gparams;            // device [n][IB_MAX_MATERIALS][9]
   cudaEvent_t root;
   cudaStream_t cap;
   cudaGraphExec_t fwd, adj;
@@ -29,12 +29,6 @@ struct ib_batch {
 
 namespace ibfe {
 namespace {
-
-template <typename Real>
-__global__ void k_add_into(Real* __restrict__ a, const Real* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] += b[i];
-}
 
 void destroy(ib_batch* b) {
   if (!b) return;
@@ -46,8 +40,7 @@ void destroy(ib_batch* b) {
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->done)
     if (e) cudaEventDestroy(e);
-  for (void* t : b->tmp_gx)
-    if (t) cudaFree(t);
+  if (b->gparams) cudaFree(b->gparams);
   if (b->root) cudaEventDestroy(b->root);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -60,21 +53,8 @@ ib_status run_forward(ib_batch* b, int i, cudaStream_t s) {
 
 ib_status run_adjoint(ib_batch* b, int i, cudaStream_t s) {
   const ib_instance& in = b->inst[i];
-  ib_plan* p = b->plans[i];
-  ib_status st = ib_interp_adj(p, &in.x, in.u, in.gU, in.gu, in.gx, s);
-  if (st == IB_OK) st = ib_spread_adj(p, &in.x, in.G, in.gf, in.gG, b->tmp_gx[i], s);
-  if (st == IB_OK) {
-    const int64_t n = 3LL * in.mesh.n_nodes;
-    if (b->precision == IB_FP64)
-      k_add_into<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double*)in.gx,
-                                                                      (const double*)b->tmp_gx[i], n);
-    else
-      k_add_into<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)in.gx,
-                                                                    (const float*)b->tmp_gx[i], n);
-    if (cudaGetLastError() != cudaSuccess) st = IB_ERR_CUDA;
-  }
-  if (st == IB_OK) st = fe_force_adj_async(p, in.mats, in.n_mats, &in.x, in.gG, in.Hv, true, s);
-  return st;
+  return ib_backward(b->plans[i], in.mats, in.n_mats, &in.x, in.u, in.G, in.gG, in.gf, in.gU,
+                     in.gx, in.gu, b->gparams + (size_t)i * 9 * IB_MAX_MATERIALS, s);
 }
 
 // Capture fn(b, i, branch_i) for every instance as branches of one graph.
@@ -115,7 +95,7 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
   for (int i = 0; i < n; ++i) {
     const ib_instance& in = inst[i];
     if (!in.u || !in.G || !in.f || !in.U) return IB_ERR_INVALID_ARG;
-    const bool a = in.gU && in.gf && in.gu && in.gx && in.gG && in.Hv;
+    const bool a = in.gU && in.gf && in.gu && in.gx;
     if (!a) has_adj = false;
   }
   ib_batch* b = new ib_batch();
@@ -125,20 +105,20 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
   b->plans.assign(n, nullptr);
   b->branch.assign(n, nullptr);
   b->done.assign(n, nullptr);
-  b->tmp_gx.assign(n, nullptr);
+  b->gparams = nullptr;
   b->root = nullptr;
   b->cap = nullptr;
   b->fwd = b->adj = nullptr;
   b->has_adj = has_adj;
-  const size_t rs = precision == IB_FP64 ? sizeof(double) : sizeof(float);
-  ib_status st = IB_OK;
+  const size_t gbytes = sizeof(double) * 9 * IB_MAX_MATERIALS * (size_t)n;
+  ib_status st = cudaMalloc((void**)&b->gparams, gbytes) == cudaSuccess &&
+                         cudaMemset(b->gparams, 0, gbytes) == cudaSuccess
+                     ? IB_OK
+                     : IB_ERR_CUDA;
   for (int i = 0; i < n && st == IB_OK; ++i) {
     st = ib_plan_create(&inst[i].mesh, &inst[i].grid, precision, stream, &b->plans[i]);
     if (st == IB_OK && (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess))
-      st = IB_ERR_CUDA;
-    if (st == IB_OK && has_adj &&
-        cudaMalloc(&b->tmp_gx[i], rs * 3 * (size_t)inst[i].mesh.n_nodes) != cudaSuccess)
       st = IB_ERR_CUDA;
   }
   if (st == IB_OK && (cudaEventCreateWithFlags(&b->root, cudaEventDisableTiming) != cudaSuccess ||
@@ -171,11 +151,9 @@ ib_status ib_batch_adjoint(ib_batch* b, void* stream) {
 ib_status ib_batch_gparams(ib_batch* b, double* gparams, void* stream) {
   if (!b || !gparams) return IB_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int i = 0; i < b->n; ++i)
-    if (cudaMemcpyAsync(gparams + (size_t)i * 9 * IB_MAX_MATERIALS, b->plans[i]->ered,
-                        sizeof(double) * 9 * IB_MAX_MATERIALS, cudaMemcpyDeviceToHost,
-                        s) != cudaSuccess)
-      return IB_ERR_CUDA;
+  if (cudaMemcpyAsync(gparams, b->gparams, sizeof(double) * 9 * IB_MAX_MATERIALS * (size_t)b->n,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return IB_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -36,7 +36,7 @@ void free_plan(ib_plan* p) {
                   p->tile_list, p->tile_list_near, p->tile_bcount, p->tile_counters,
                   p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
                   p->p_off, p->p_val, p->p_idx, p->gq_a, p->gq_b, p->epart, p->ered,
-                  p->dstatus};
+                  p->dstatus, p->node_tmp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
@@ -157,9 +157,10 @@ ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
   return launch_elem_project(p, vals, elem, s);
 }
 
-ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, cudaStream_t s) {
+ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, cudaStream_t s,
+                    const void* add = nullptr) {
   Stage sc(p, IB_STAGE_GATHER, s, 1);
-  return launch_node_gather(p, elem, scale, out, s);
+  return launch_node_gather(p, elem, scale, out, s, add);
 }
 
 ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
@@ -295,6 +296,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
               dalloc(&p->q_off, rs * 3 * Q) && dalloc(&p->q_val, rs * 3 * Q) &&
               dalloc(&p->p_cell, 4 * Q) && dalloc(&p->p_off, rs * 3 * Q) &&
               dalloc(&p->p_val, rs * 3 * Q) && dalloc(&p->p_idx, 4 * Q) &&
+              dalloc(&p->node_tmp, rs * 6 * (size_t)N) &&
               dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
               dalloc(&p->epart, 8 * 9 * (size_t)(E > 0 ? E : 1)) &&
               dalloc(&p->ered, 8 * 9 * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16);
@@ -426,6 +428,72 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
   }
   if (st == IB_OK) st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
+  return check_launch(st);
+}
+
+ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                      const void* u, const void* G, const void* gG, const void* gf,
+                      const void* gU, void* gx, void* gu, double* gparams, void* stream) {
+  if (!p || !gx || (gf && !G) || (gU && (!gu || !u)) || (gu && !aligned16(gu)))
+    return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  cudaStream_t b = p->side;
+  const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
+  const size_t nbytes = p->rsize * 3 * (size_t)p->N;
+  void* gGt = p->node_tmp;  // the force cotangent gG + (df/dG)^T gf
+  const bool force = gG || gf;
+  // Gauss points built and binned once for both transfer adjoints
+  st = do_points_sorted(p, x, nullptr, s);
+  // spreading adjoint: an interpolation of gf (values and position weights)
+  if (st == IB_OK && gf) {
+    Stage sc(p, IB_STAGE_POINTS, s, 2);
+    st = launch_point_values(p, G, s);
+    if (st == IB_OK) st = launch_permute_values(p, s);
+  }
+  if (st == IB_OK && gf) st = do_interp(p, gf, 1, ih3, ih3 / h, s);
+  if (st == IB_OK && gf) st = do_project(p, p->gq_a, p->elem_scratch, s);
+  if (st == IB_OK && gf) st = do_gather(p, p->elem_scratch, p->inv_mass, gGt, s, gG);
+  if (st == IB_OK && gf) st = do_project(p, p->gq_b, p->elem_scratch2, s);
+  if (st == IB_OK && gf) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
+  if (st == IB_OK && !gf) {
+    if (!ok(cudaMemsetAsync(gx, 0, nbytes, s)) ||
+        !ok(gG ? cudaMemcpyAsync(gGt, gG, nbytes, cudaMemcpyDeviceToDevice, s)
+               : cudaMemsetAsync(gGt, 0, nbytes, s)))
+      st = IB_ERR_CUDA;
+  }
+  // interpolation adjoint (a spreading of gU) on the side stream ...
+  if (st == IB_OK && (!ok(cudaEventRecord(p->ev_ffork, s)) ||
+                      !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0))))
+    st = IB_ERR_CUDA;
+  if (st == IB_OK && gU) {
+    Stage sc(p, IB_STAGE_POINTS, b, 2);
+    st = launch_point_values(p, gU, b);
+    if (st == IB_OK) st = launch_permute_values(p, b);
+  }
+  if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b);
+  if (st == IB_OK && gU) st = do_interp(p, u, 2, 0.0, 1.0 / h, b);
+  if (st == IB_OK && gU) st = do_project(p, p->gq_b, p->elem_scratch2, b);
+  if (st == IB_OK && gU) st = do_gather(p, p->elem_scratch2, nullptr, gx, b, gx);
+  if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
+  // ... beside the force adjoint, whose nodal gather adds into gx after the join
+  if (st == IB_OK && force) {
+    Stage sc(p, IB_STAGE_FORCE, s, 1);
+    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch,
+                             gparams != nullptr, s);
+  }
+  if (st == IB_OK && force && gparams) st = do_reduce(p, 9, n_mats, s);
+  if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
+  if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx);
+  if (st == IB_OK && gparams) {
+    const size_t pb = sizeof(double) * 9 * (size_t)n_mats;
+    if (!ok(force ? cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)
+                  : cudaMemsetAsync(gparams, 0, pb, s)))
+      st = IB_ERR_CUDA;
+  }
   return check_launch(st);
 }
 

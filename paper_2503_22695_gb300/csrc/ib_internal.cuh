@@ -97,6 +97,7 @@ struct ib_plan {
   void* p_off;           // Real [3][Q]
   void* p_val;           // Real [3][Q]
   int32_t* p_idx;        // [Q] original gq
+  void* node_tmp;        // Real [2][3][N] nodal work vectors (fused backward)
   void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
   void* gq_b;            // Real [3][Q]
   double* epart;         // [9][E] per-element partial sums
@@ -127,8 +128,9 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
 
 // assemble.cu
+// out = add + node_scale * (gather of elem); add optional (may be out)
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* node_scale, void* out,
-                             cudaStream_t s);
+                             cudaStream_t s, const void* add = nullptr);
 ib_status launch_elem_project(ib_plan* p, const void* gq_vals, void* elem_out, cudaStream_t s);
 ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
 

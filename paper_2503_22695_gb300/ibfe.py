@@ -60,7 +60,7 @@ class _Instance(C.Structure):
     _fields_ = [("mesh", _Mesh), ("grid", _Grid), ("n_mats", C.c_int32),
                 ("mats", _Mat * 8), ("x", _Pos), ("u", C.c_void_p), ("G", C.c_void_p),
                 ("f", C.c_void_p), ("U", C.c_void_p), ("gU", C.c_void_p), ("gf", C.c_void_p),
-                ("gu", C.c_void_p), ("gx", C.c_void_p), ("gG", C.c_void_p), ("Hv", C.c_void_p)]
+                ("gG", C.c_void_p), ("gu", C.c_void_p), ("gx", C.c_void_p)]
 
 
 def _load():
@@ -79,6 +79,8 @@ def _load():
         "ib_spread_adj": [vp, C.POINTER(_Pos), vp, vp, vp, vp, vp],
         "ib_interp_adj": [vp, C.POINTER(_Pos), vp, vp, vp, vp, vp],
         "ib_fe_force_adj": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, dp, vp],
+        "ib_backward": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, vp, vp, vp, vp, vp,
+                        vp, vp],
         "ib_plan_sync_status": [vp, vp],
         "ib_plan_set_profiling": [vp, i32],
         "ib_batch_create": [i32, C.POINTER(_Instance), i32, vp, C.POINTER(vp)],
@@ -170,6 +172,7 @@ class Plan:
         self.N, self.E = int(X.shape[1]), int(conn.shape[1])
         self.n, self.h, self.origin = tuple(int(v) for v in n), float(h), tuple(origin)
         self.precision = precision
+        self.device = X.device
         mesh = _Mesh(self.N, self.E, conn.data_ptr(), X.data_ptr(),
                      None if fibres is None else fibres.data_ptr(),
                      None if mat_id is None else mat_id.data_ptr())
@@ -312,6 +315,32 @@ def ib_fe_force_adj(plan: Plan, mats, x: Pos, v, want_params: bool = True, Hv=No
     return Hv, g
 
 
+def ib_backward(plan: Plan, mats, x: Pos, u=None, G=None, gG=None, gf=None, gU=None,
+                gx=None, gu=None, want_params: bool = True):
+    """Fused backward of ib_forward: (gx, gu, gparams) for the cotangents
+    (gG, gf, gU) of (G, f, U); any cotangent may be None (zero).  gparams is a
+    device float64 tensor [n_mats][9] (None unless want_params); gu is None
+    unless gU is given."""
+    if gf is not None:
+        _check(gf, plan.dtype, plan.grid_shape(), "gf")
+        _check(G, plan.dtype, (3, plan.N), "G")
+    if gG is not None:
+        _check(gG, plan.dtype, (3, plan.N), "gG")
+    if gU is not None:
+        _check(gU, plan.dtype, (3, plan.N), "gU")
+        _check(u, plan.dtype, plan.grid_shape(), "u")
+        gu = _out(gu, plan, plan.grid_shape(), "gu")
+    else:
+        gu = None
+    gx = _out(gx, plan, (3, plan.N), "gx")
+    arr, nm = _mats(mats)
+    gp = torch.empty(nm, 9, dtype=torch.float64, device=plan.device) if want_params else None
+    _chk(_lib.ib_backward(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(u), _ptr(G),
+                          _ptr(gG), _ptr(gf), _ptr(gU), _ptr(gx), _ptr(gu), _ptr(gp),
+                          _stream()), "ib_backward")
+    return gx, gu, gp
+
+
 def ib_plan_sync_status(plan: Plan) -> int:
     return int(_lib.ib_plan_sync_status(plan.handle, _stream()))
 
@@ -345,8 +374,9 @@ class Batch:
     `instances` is a list of dicts with the device tensors of each structure:
     conn, X, fibres (or None), mat_id (or None), n, h, origin, mats (list of
     Material), cell/off (FP32 split) or x64 (FP64), u, and the output tensors
-    G, f, U; for the adjoint also gU, gf, gu, gx, gG, Hv.  The tensors must
-    stay alive and in place: the graphs bake their addresses in."""
+    G, f, U; for the backward (ib_backward) also the cotangents gU, gf and
+    optionally gG, and the outputs gu, gx.  The tensors must stay alive and in
+    place: the graphs bake their addresses in."""
 
     def __init__(self, instances, precision: int = IB_FP32_SPLIT):
         n = len(instances)
@@ -370,7 +400,7 @@ class Batch:
                 for j, v in enumerate(m.params):
                     a.mats[k].params[j] = float(v)
             a.x = _Pos(_p(d.get("cell")), _p(d.get("off")), _p(d.get("x64")))
-            for name in ("u", "G", "f", "U", "gU", "gf", "gu", "gx", "gG", "Hv"):
+            for name in ("u", "G", "f", "U", "gU", "gf", "gG", "gu", "gx"):
                 setattr(a, name, _p(d.get(name)))
         out = C.c_void_p()
         _chk(_lib.ib_batch_create(n, arr, precision, _stream(), C.byref(out)), "ib_batch_create")
@@ -480,16 +510,40 @@ class Interp(torch.autograd.Function):
         return None, None, gx * ctx.plan.h, gu
 
 
+class Coupling(torch.autograd.Function):
+    """The whole coupling step: ib_forward forward, ib_backward backward."""
+
+    @staticmethod
+    def forward(ctx, plan, models, cell, off, params, u):
+        ctx.set_materialize_grads(False)
+        x = Pos(cell=cell, off=off.detach())
+        G, f, U = ib_forward(plan, _mats_from(models, params.detach()), x,
+                             u.detach().contiguous())
+        ctx.plan, ctx.models = plan, models
+        ctx.save_for_backward(cell, off, params, u, G)
+        return G, f, U
+
+    @staticmethod
+    def backward(ctx, gG, gf, gU):
+        cell, off, params, u, G = ctx.saved_tensors
+        plan = ctx.plan
+        x = Pos(cell=cell, off=off.detach())
+        c = lambda t: None if t is None else t.contiguous()
+        gx, gu, gp = ib_backward(plan, _mats_from(ctx.models, params.detach()), x,
+                                 u.detach().contiguous(), G, c(gG), c(gf), c(gU))
+        gp = gp.cpu()
+        for i, m in enumerate(ctx.models):
+            gp[i, N_PARAMS[m]:] = 0
+        return None, None, None, gx * plan.h, gp, gu
+
+
 class IBCoupling(torch.nn.Module):
     """G = FE force(x; theta), f = spread(x, G), U = interp(x, u), differentiable in
-    the offsets, the material parameters and u."""
+    the offsets, the material parameters and u (one fused forward and backward)."""
 
     def __init__(self, plan: Plan, models):
         super().__init__()
         self.plan, self.models = plan, list(models)
 
     def forward(self, cell, off, params, u):
-        G = FEForce.apply(self.plan, self.models, cell, off, params)
-        f = Spread.apply(self.plan, cell, off, G)
-        U = Interp.apply(self.plan, cell, off, u)
-        return G, f, U
+        return Coupling.apply(self.plan, self.models, cell, off, params, u)

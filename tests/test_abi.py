@@ -27,7 +27,7 @@ def test_header_declares_the_operators():
     names = declared()
     for want in ("ib_plan_create", "ib_plan_destroy", "ib_fe_force", "ib_spread", "ib_interp",
                  "ib_spread_adj", "ib_interp_adj", "ib_fe_force_adj", "ib_forward",
-                 "ib_plan_sync_status", "ib_status_str"):
+                 "ib_backward", "ib_plan_sync_status", "ib_status_str"):
         assert want in names
 
 
@@ -47,5 +47,6 @@ def test_host_side_argument_checks(lib):
     for fn in ("ib_fe_force", "ib_spread", "ib_interp", "ib_spread_adj", "ib_interp_adj",
                "ib_fe_force_adj", "ib_forward"):
         assert getattr(lib, fn)(*([None] * 9)) == 1, fn
+    assert lib.ib_backward(*([None] * 13)) == 1
     assert lib.ib_plan_destroy(None) == 1
     assert lib.ib_plan_sync_status(None, None) == 1

@@ -147,6 +147,49 @@ def test_fe_force_adjoint(name):
         assert rel_l2(gp[m, :k].numpy(), gpo[m, :k]) <= tol(c, "adj")
 
 
+@pytest.mark.parametrize("name", SMALL + ["shell256"])
+def test_fused_backward(name):
+    """ib_backward against the oracle's adjoints, and against the composition
+    of the separate adjoint entry points on the device."""
+    c = case(name)
+    ib, g = c.ibfe, c.prob.grid
+    rng = np.random.default_rng(11)
+    n = c.prob.n_nodes
+    G = c.to_dev(c.rounded(c.orc.fe_force(c.x_np)[0]))
+    gG = c.rounded(rng.normal(size=(3, n)))
+    gU = c.rounded(rng.normal(size=(3, n)))
+    gf = c.rounded(rng.normal(size=c.plan.grid_shape()))
+    gx, gu, gp = ib.ib_backward(c.plan, c.mats, c.pos, c.u, G, c.to_dev(gG), c.to_dev(gf),
+                                c.to_dev(gU))
+    # oracle: gx = Hv(gG + S^T gf) + (dS/dx)^T gf + (dJ/dx)^T gU
+    Gn = np_(G)
+    guo, gxi = c.orc.interp_adj(c.x_np, c.u_np, gU)
+    gGs, gxs = c.orc.spread_adj(c.x_np, Gn, gf)
+    Hv, gpo = c.orc.fe_force_adj(c.x_np, gG + gGs)
+    t = tol(c, "adj")
+    assert rel_l2(np_(gx), gxi + gxs + Hv) <= t
+    assert rel_l2(np_(gu), guo) <= t
+    for m, mat in enumerate(c.prob.materials):
+        k = I.N_PARAMS[mat.model]
+        assert rel_l2(gp[m, :k].cpu().numpy(), gpo[m, :k]) <= t
+    # composition of the separate entry points
+    gu1, gx1 = ib.ib_interp_adj(c.plan, c.pos, c.u, c.to_dev(gU))
+    gGs1, gx2 = ib.ib_spread_adj(c.plan, c.pos, G, c.to_dev(gf))
+    Hv1, gp1 = ib.ib_fe_force_adj(c.plan, c.mats, c.pos, c.to_dev(gG) + gGs1)
+    assert rel_l2(np_(gu), np_(gu1)) <= (1e-15 if c.fp64 else 1e-7)
+    assert rel_l2(np_(gx), np_(gx1) + np_(gx2) + np_(Hv1)) <= (1e-13 if c.fp64 else 2e-6)
+    # missing cotangents are zeros
+    gx_u, gu_u, _ = ib.ib_backward(c.plan, c.mats, c.pos, c.u, None, None, None, c.to_dev(gU),
+                                   want_params=False)
+    assert rel_l2(np_(gu_u), np_(gu1)) <= (1e-15 if c.fp64 else 1e-7)
+    assert rel_l2(np_(gx_u), np_(gx1)) <= (1e-13 if c.fp64 else 1e-6)
+    gx_g, gu_g, gp_g = ib.ib_backward(c.plan, c.mats, c.pos, None, None, c.to_dev(gG))
+    Hv2, gp2 = ib.ib_fe_force_adj(c.plan, c.mats, c.pos, c.to_dev(gG))
+    assert gu_g is None
+    assert np.array_equal(np_(gx_g), np_(Hv2))
+    assert np.allclose(gp_g.cpu().numpy(), gp2.numpy(), rtol=1e-12, atol=0)
+
+
 @pytest.mark.parametrize("name", ["block32", "seam32", "shell128", "shell256"])
 def test_fp32_scalar_precision_option(name):
     """IB_FP32_SPLIT_F32STAB (the FP64 scalar set also in FP32, same
