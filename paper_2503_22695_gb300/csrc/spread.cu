@@ -3,30 +3,27 @@
 // with scale = h^-3 for forces (delta_h carries h^-3) and 1 for the adjoint
 // of interpolation.
 //
-// Three kernels over 8^3-cell Eulerian tiles, no global floating-point
-// atomics, bitwise reproducible:
+// Kernels over 8^3-cell Eulerian tiles, no floating-point atomics, bitwise
+// reproducible:
 //
 // k_spread_zero (side stream, concurrent with the push) -- one warp per
 //   "far" tile (no points in its 3x3x3 neighbourhood) writes its zeros with
 //   16-byte stores: the bulk of the field's HBM traffic overlaps the
 //   accumulation work.
-// k_spread_push (persistent CTAs pulling work items from a counter; a work
-//   item is at most 1024 consecutive points of one tile, so densely populated
-//   tiles are shared by several CTAs) -- the item's points are accumulated
-//   into a halo'd 12^3 block per component (they reach two cells beyond the
-//   tile; indices stay unwrapped), one component at a time.  The item's raw
-//   point data are copied to shared memory once (cp.async, all in flight);
-//   points are then staged 128 at a time (one thread per point computes the
-//   3x4 kernel weights).  Each half-warp owns a private shared-memory copy of the block
-//   and takes the staged points k, k+8, ... in order, one point per step: its
-//   16 lanes cover the 16 (dz, dy) rows of the 4x4x4 stencil, four faces per
-//   lane, all distinct; steps are ordered by __syncwarp.  The eight copies
-//   are summed in copy order into the item's scratch block.
-// k_spread_merge -- for every "near" tile, each face sums the blocks of its
-//   own tile and of the neighbours whose halo covers it (at most two per
-//   axis), in ascending (z, y, x) source order and, within a source tile, in
-//   work-item order, and is written once.  Periodic wrap happens only here,
-//   through the neighbour-tile index.
+// k_spread_push_fx (FP32 plans) / k_spread_push (FP64 plans) -- persistent
+//   CTAs pulling work items from a counter (a work item is at most 1024
+//   consecutive points of one tile, so densely populated tiles are shared by
+//   several CTAs) accumulate the item's points into a halo'd 12^3 block per
+//   component (they reach two cells beyond the tile; indices stay
+//   unwrapped).  FP32: exact fixed-point words with 32-bit shared atomics
+//   (see below); FP64: half-warp private copies in double, steps ordered by
+//   __syncwarp, summed in copy order.
+// k_spread_merge_fx / k_spread_merge -- for every "near" tile, each face
+//   sums the blocks of its own tile and of the neighbours whose halo covers
+//   it (at most two per axis), in ascending (z, y, x) source order and,
+//   within a source tile, in work-item order, and is written once: exact
+//   integer sums rounded once (FP32), doubles in that fixed order (FP64).
+//   Periodic wrap happens only here, through the neighbour-tile index.
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -578,7 +575,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
         const long long S = sh[x] * 2048 + sl[x];
-        const long long hi = S >> 24;
+        const int hi = (int)(S >> 24);  // |S| < 2^47: |hi| < 2^23, exact in float
         const int lo = (int)(S & 0xFFFFFF);
         o[x] = fmaf((float)hi, 16777216.0f, (float)lo) * out_scale;
       }
