@@ -52,6 +52,7 @@ struct FeArgs {
   Real* out;             // [24][E] corner contributions
   double* epart;         // [9][E] per-element partial sums or null
   int* status;
+  int* next;             // block counter, zero at launch
 };
 
 template <typename T>
@@ -212,9 +213,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
     for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
   double en = 0.0;
-  double gp[9];
+  Real gp[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) gp[k] = 0.0;
+  for (int k = 0; k < 9; ++k) gp[k] = Real(0);
   bool inverted = false;
 
 #pragma unroll
@@ -473,31 +474,27 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
                        k8 * (dFf[i] * es[j] + dFs[i] * ef[j]);
       }
       if (kParams) {
-        // gparams_k = -sum_q w j0 (dP/dtheta_k : dF)
-        const double w = double(j0);
-        const double vol = double(lnJ) * double(dl);
+        // gparams_k = -sum_q w j0 (dP/dtheta_k : dF): the element's eight
+        // terms in Real, the sums over elements in double
+        const Real w = j0;
+        const Real vol = lnJ * dl;
         if (model == 0) {
-          gp[0] -= w * 2.0 * double(DdF);
+          gp[0] -= w * Real(2) * DdF;
           gp[1] -= w * vol;
         } else if (model == 1) {
-          const double d = double(f1.d), ex = double(ef1);
-          gp[0] -= w * 2.0 * double(DdF);
-          gp[1] -= w * d * ex * double(dI4f);
-          gp[2] -= w * prm[1] * d * d * d * ex * double(dI4f);
+          gp[0] -= w * Real(2) * DdF;
+          gp[1] -= w * d1 * ef1 * dI4f;
+          gp[2] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
           gp[3] -= w * vol;
         } else {
-          const double ei = double(eiso), be = double(Ibm3);
-          const double d1 = double(f1.d), x1 = double(ef1);
-          const double d2 = double(f2.d), x2 = double(ef2);
-          const double i8 = double(I8), x8 = double(e8);
-          gp[0] -= w * ei * double(DdF);
-          gp[1] -= w * prm[0] * be * ei * double(DdF);
-          gp[2] -= w * d1 * x1 * double(dI4f);
-          gp[3] -= w * prm[2] * d1 * d1 * d1 * x1 * double(dI4f);
-          gp[4] -= w * d2 * x2 * double(dI4s);
-          gp[5] -= w * prm[4] * d2 * d2 * d2 * x2 * double(dI4s);
-          gp[6] -= w * i8 * x8 * double(dI8);
-          gp[7] -= w * prm[6] * i8 * i8 * i8 * x8 * double(dI8);
+          gp[0] -= w * eiso * DdF;
+          gp[1] -= w * pa * Ibm3 * eiso * DdF;
+          gp[2] -= w * d1 * ef1 * dI4f;
+          gp[3] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
+          gp[4] -= w * f2.d * ef2 * dI4s;
+          gp[5] -= w * pas * f2.d * f2.d * f2.d * ef2 * dI4s;
+          gp[6] -= w * I8 * e8 * dI8;
+          gp[7] -= w * pafs * I8 * I8 * I8 * e8 * dI8;
           gp[8] -= w * vol;
         }
       }
@@ -526,18 +523,28 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   if (kEnergy) A.epart[e] = en;
   if (kParams) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) A.epart[(int64_t)k * E + e] = gp[k];
+    for (int k = 0; k < 9; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
   }
 }
 
 // Persistent grid (a fixed number of CTAs per SM, fewer than fit): the kernel
 // is bound by the FP64 pipe, and the SM room it leaves lets the Gauss-point
-// sort and the interpolation, issued on another stream, run beside it.
+// binning and the interpolation, issued on another stream, run beside it.
+// CTAs take blocks of elements from a counter, so a CTA that becomes resident
+// late (its SM busy with those kernels) simply takes fewer.
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
 __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
     k_fe(FeArgs<Real> A, MatTable mt) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < A.E; e += gridDim.x * blockDim.x)
-    fe_element<Real, S, kEnergy, kAdj, kParams>(A, mt, e);
+  __shared__ int base;
+  for (;;) {
+    if (threadIdx.x == 0) base = atomicAdd(A.next, 1) * (int)blockDim.x;
+    __syncthreads();
+    const int b = base;
+    __syncthreads();
+    if (b >= A.E) break;
+    if (b + (int)threadIdx.x < A.E)
+      fe_element<Real, S, kEnergy, kAdj, kParams>(A, mt, b + (int)threadIdx.x);
+  }
 }
 
 // Deterministic per-material sums of per-element partials in two levels:
@@ -611,6 +618,7 @@ FeArgs<float> make_args<float>(ib_plan* p, const void* xa, const float* off, con
   A.out = (float*)out;
   A.epart = p->epart;
   A.status = p->dstatus;
+  A.next = p->tile_counters + 6;
   return A;
 }
 
@@ -633,6 +641,7 @@ FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*, const
   A.out = (double*)out;
   A.epart = p->epart;
   A.status = p->dstatus;
+  A.next = p->tile_counters + 6;
   return A;
 }
 
@@ -645,6 +654,7 @@ ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, 
   // the forward runs beside the sort and interpolation; the adjoint runs alone
   const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : kFeCtasPerSm;
   const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
+  if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
   if (p->precision == IB_FP32_SPLIT_F32STAB)
     k_fe<Real, Real, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
   else

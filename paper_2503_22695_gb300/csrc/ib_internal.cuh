@@ -80,7 +80,8 @@ struct ib_plan {
   int32_t* tile_list;    // [max work items] tile of each work item
   int32_t* tile_list_near;// [ntiles] near tiles, ascending
   int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
-  int32_t* tile_counters;// [8] non-empty count, work counters, near count
+  int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
+                         //     [5] spread absmax bits, [6] FE force block counter
   int32_t* digit_tot;    // [256] radix digit totals
   double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*9] reduction partials
   cudaStream_t side;     // interpolation branch of ib_forward
