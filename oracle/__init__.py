@@ -192,6 +192,47 @@ class Model:
                                       _p(gU), _p(gu), _p(gx)), "interp_adj")
         return gu, gx
 
+    # nodal quadrature rule (Section 4.4): the coupling points are the nodes
+    def spread_nodal(self, x, G):
+        x, G = _f64(x), _f64(G)
+        f = self._field()
+        self._chk(lib().or_spread_nodal(C.byref(self._grid), C.c_int64(self.N), _p(x), _p(G),
+                                        _p(f)), "spread_nodal")
+        return f
+
+    def spread_nodal_at(self, x, G, comp, idx):
+        x, G = _f64(x), _f64(G)
+        comp = np.ascontiguousarray(comp, dtype=np.int32)
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 3)
+        out = np.empty(len(comp))
+        self._chk(lib().or_spread_nodal_at(C.byref(self._grid), C.c_int64(self.N), _p(x), _p(G),
+                                           C.c_int64(len(comp)), _p(comp), _p(idx), _p(out)),
+                  "spread_nodal_at")
+        return out
+
+    def interp_nodal(self, x, u):
+        x, u = _f64(x), _f64(u)
+        U = np.empty((3, self.N))
+        self._chk(lib().or_interp_nodal(C.byref(self._grid), C.c_int64(self.N), _p(x), _p(u),
+                                        _p(U)), "interp_nodal")
+        return U
+
+    def spread_nodal_adj(self, x, G, gf, want_gx=True):
+        x, G, gf = _f64(x), _f64(G), _f64(gf)
+        gG = np.empty((3, self.N))
+        gx = np.empty((3, self.N)) if want_gx else None
+        self._chk(lib().or_spread_nodal_adj(C.byref(self._grid), C.c_int64(self.N), _p(x), _p(G),
+                                            _p(gf), _p(gG), _p(gx)), "spread_nodal_adj")
+        return gG, gx
+
+    def interp_nodal_adj(self, x, u, gU, want_gx=True):
+        x, u, gU = _f64(x), _f64(u), _f64(gU)
+        gu = self._field()
+        gx = np.empty((3, self.N)) if want_gx else None
+        self._chk(lib().or_interp_nodal_adj(C.byref(self._grid), C.c_int64(self.N), _p(x), _p(u),
+                                            _p(gU), _p(gu), _p(gx)), "interp_nodal_adj")
+        return gu, gx
+
     def support_count(self, x):
         x = _f64(x)
         r = lib().or_support_count(C.byref(self._grid), C.byref(self._mesh), _p(x))

@@ -707,6 +707,143 @@ int or_interp_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Nodal quadrature rule (Section 4.4, the rule N_q of the nodes): the
+// coupling points are the nodes' displaced positions x_a.
+//   U^IB_a = sum_faces u^c(face) prod_d phi(r_d)              (interpolation; with
+//            the nodal rule the lumped L2 projection leaves U_a = U^IB_a)
+//   f^c(face) = sum_a F_a^c delta_h(x_face - x_a) = h^-3 sum_a G_a^c prod phi
+//            (spreading of the mean nodal force contributions F_i = G)
+// ---------------------------------------------------------------------------
+int or_spread_nodal(const or_grid* g, int64_t N, const double* x, const double* G, double* f) {
+  if (!check_grid(g) || N < 0) return -1;
+  int64_t cells = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  std::memset(f, 0, sizeof(double) * 3 * cells);
+  double h3 = g->h * g->h * g->h;
+  for (int64_t a = 0; a < N; ++a) {
+    double chi[3] = {x[a], x[N + a], x[2 * N + a]};
+    for (int c = 0; c < 3; ++c) {
+      Stencil s;
+      stencil(g, c, chi, s);
+      for (int kz = 0; kz < 4; ++kz)
+        for (int ky = 0; ky < 4; ++ky)
+          for (int kx = 0; kx < 4; ++kx)
+            f[face_index(g, c, s.idx[0][kx], s.idx[1][ky], s.idx[2][kz])] +=
+                G[c * N + a] * s.w[0][kx] * s.w[1][ky] * s.w[2][kz] / h3;
+    }
+  }
+  return 0;
+}
+
+// Brute force at selected faces: every node, the nearest periodic image of
+// each distance, phi evaluated directly.
+int or_spread_nodal_at(const or_grid* g, int64_t N, const double* x, const double* G,
+                       int64_t n_sel, const int32_t* comp, const int32_t* idx, double* out) {
+  if (!check_grid(g) || N < 0) return -1;
+  double h3 = g->h * g->h * g->h;
+  for (int64_t k = 0; k < n_sel; ++k) {
+    int c = comp[k];
+    double acc = 0.0;
+    for (int64_t a = 0; a < N; ++a) {
+      double w = 1.0;
+      for (int d = 0; d < 3 && w != 0.0; ++d) {
+        double sh = (d == c) ? 0.0 : 0.5;
+        double r = (x[d * N + a] - g->origin[d]) / g->h - sh - idx[3 * k + d];
+        r -= g->n[d] * std::floor(r / g->n[d] + 0.5);
+        w *= phi(r);
+      }
+      acc += G[c * N + a] * w / h3;
+    }
+    out[k] = acc;
+  }
+  return 0;
+}
+
+int or_interp_nodal(const or_grid* g, int64_t N, const double* x, const double* u, double* U) {
+  if (!check_grid(g) || N < 0) return -1;
+  for (int64_t a = 0; a < N; ++a) {
+    double chi[3] = {x[a], x[N + a], x[2 * N + a]};
+    for (int c = 0; c < 3; ++c) {
+      Stencil s;
+      stencil(g, c, chi, s);
+      double acc = 0.0;
+      for (int kz = 0; kz < 4; ++kz)
+        for (int ky = 0; ky < 4; ++ky)
+          for (int kx = 0; kx < 4; ++kx)
+            acc += u[face_index(g, c, s.idx[0][kx], s.idx[1][ky], s.idx[2][kz])] *
+                   s.w[0][kx] * s.w[1][ky] * s.w[2][kz];
+      U[c * N + a] = acc;
+    }
+  }
+  return 0;
+}
+
+// Adjoint of nodal spreading: gG_a^c = h^-3 sum_faces gf^c prod phi and
+// gx_a,d = h^-4 sum_c G_a^c sum_faces gf^c phi'(r_d) prod_{d' != d} phi.
+int or_spread_nodal_adj(const or_grid* g, int64_t N, const double* x, const double* G,
+                        const double* gf, double* gG, double* gx) {
+  if (!check_grid(g) || N < 0) return -1;
+  double h = g->h, h3 = h * h * h;
+  for (int64_t a = 0; a < N; ++a) {
+    double chi[3] = {x[a], x[N + a], x[2 * N + a]}, gchi[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+      Stencil s;
+      stencil(g, c, chi, s);
+      double acc = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+      for (int kz = 0; kz < 4; ++kz)
+        for (int ky = 0; ky < 4; ++ky)
+          for (int kx = 0; kx < 4; ++kx) {
+            double v = gf[face_index(g, c, s.idx[0][kx], s.idx[1][ky], s.idx[2][kz])];
+            acc += v * s.w[0][kx] * s.w[1][ky] * s.w[2][kz];
+            d0 += v * s.dw[0][kx] * s.w[1][ky] * s.w[2][kz];
+            d1 += v * s.w[0][kx] * s.dw[1][ky] * s.w[2][kz];
+            d2 += v * s.w[0][kx] * s.w[1][ky] * s.dw[2][kz];
+          }
+      gG[c * N + a] = acc / h3;
+      gchi[0] += G[c * N + a] * d0 / (h3 * h);
+      gchi[1] += G[c * N + a] * d1 / (h3 * h);
+      gchi[2] += G[c * N + a] * d2 / (h3 * h);
+    }
+    if (gx)
+      for (int d = 0; d < 3; ++d) gx[d * N + a] = gchi[d];
+  }
+  return 0;
+}
+
+// Adjoint of nodal interpolation: gu^c(face) = sum_a gU_a^c prod phi and
+// gx_a,d = h^-1 sum_c gU_a^c sum_faces u^c phi'(r_d) prod_{d' != d} phi.
+int or_interp_nodal_adj(const or_grid* g, int64_t N, const double* x, const double* u,
+                        const double* gU, double* gu, double* gx) {
+  if (!check_grid(g) || N < 0) return -1;
+  int64_t cells = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  std::memset(gu, 0, sizeof(double) * 3 * cells);
+  double h = g->h;
+  for (int64_t a = 0; a < N; ++a) {
+    double chi[3] = {x[a], x[N + a], x[2 * N + a]}, gchi[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+      Stencil s;
+      stencil(g, c, chi, s);
+      double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+      for (int kz = 0; kz < 4; ++kz)
+        for (int ky = 0; ky < 4; ++ky)
+          for (int kx = 0; kx < 4; ++kx) {
+            int64_t fi = face_index(g, c, s.idx[0][kx], s.idx[1][ky], s.idx[2][kz]);
+            gu[fi] += gU[c * N + a] * s.w[0][kx] * s.w[1][ky] * s.w[2][kz];
+            double v = u ? u[fi] : 0.0;
+            d0 += v * s.dw[0][kx] * s.w[1][ky] * s.w[2][kz];
+            d1 += v * s.w[0][kx] * s.dw[1][ky] * s.w[2][kz];
+            d2 += v * s.w[0][kx] * s.w[1][ky] * s.dw[2][kz];
+          }
+      gchi[0] += gU[c * N + a] * d0 / h;
+      gchi[1] += gU[c * N + a] * d1 / h;
+      gchi[2] += gU[c * N + a] * d2 / h;
+    }
+    if (gx)
+      for (int d = 0; d < 3; ++d) gx[d * N + a] = gchi[d];
+  }
+  return 0;
+}
+
 int64_t or_support_count(const or_grid* g, const or_mesh* m, const double* x) {
   if (!check_grid(g) || !check_mesh(m)) return -1;
   int64_t E = m->n_elems;

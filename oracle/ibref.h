@@ -108,6 +108,20 @@ int or_spread_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
 int or_interp_adj(const or_grid* g, const or_mesh* m, const double* x, const double* u,
                   const double* gU, double* gu, double* gx);
 
+/* Nodal quadrature rule of Section 4.4: the coupling points are the N nodes'
+ * displaced positions x [3][N].  Spreading of the nodal forces G [3][N]
+ * (f = h^-3 sum_a G_a prod phi), interpolation U_a = sum u prod phi (the
+ * nodal rule makes the lumped projection the identity), a brute-force
+ * spreading at selected faces, and the two adjoints (gx optional). */
+int or_spread_nodal(const or_grid* g, int64_t N, const double* x, const double* G, double* f);
+int or_spread_nodal_at(const or_grid* g, int64_t N, const double* x, const double* G,
+                       int64_t n_sel, const int32_t* comp, const int32_t* idx, double* out);
+int or_interp_nodal(const or_grid* g, int64_t N, const double* x, const double* u, double* U);
+int or_spread_nodal_adj(const or_grid* g, int64_t N, const double* x, const double* G,
+                        const double* gf, double* gG, double* gx);
+int or_interp_nodal_adj(const or_grid* g, int64_t N, const double* x, const double* u,
+                        const double* gU, double* gu, double* gx);
+
 /* Number of distinct (component, face) pairs covered by the interpolation
  * stencils of all Gauss points (for the algorithmic-bytes count). */
 int64_t or_support_count(const or_grid* g, const or_mesh* m, const double* x);

@@ -432,6 +432,102 @@ def test_position_adjoints_by_differences():
         assert np.sum(gx_i * d) == pytest.approx(fd_i, rel=1e-6)
 
 
+# ---------------------------------------------------------------------------
+# nodal quadrature rule (Section 4.4): the coupling points are the nodes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("centre", [None, (0.02, 0.97, 0.5)])
+def test_nodal_spread_matches_brute_force_over_all_faces(centre):
+    p, G = small_problem(centre=centre)
+    m = oracle.Model(p)
+    f = m.spread_nodal(p.x, G)
+    n = p.grid.n[0]
+    comp, idx = [], []
+    for c in range(3):
+        for i2 in range(n):
+            for i1 in range(n):
+                for i0 in range(n):
+                    comp.append(c)
+                    idx.append((i0, i1, i2))
+    bf = m.spread_nodal_at(p.x, G, comp, idx).reshape(3, n, n, n)
+    np.testing.assert_allclose(f, bf, rtol=1e-12, atol=1e-12 * np.abs(f).max())
+
+
+def test_nodal_spread_conserves_force_and_torque():
+    # zeroth and first moments of the 4-point kernel: h^3 sum f = sum_a G_a and
+    # h^3 sum x_face x f = sum_a x_a x G_a
+    p, G = small_problem(n=16, blocks=(2, 3, 2))
+    m = oracle.Model(p)
+    f = m.spread_nodal(p.x, G)
+    h, n = p.grid.h, p.grid.n[0]
+    np.testing.assert_allclose(h ** 3 * f.reshape(3, -1).sum(axis=1), G.sum(axis=1),
+                               rtol=1e-12, atol=1e-12)
+    ii = np.arange(n)
+    pos = []
+    for c in range(3):
+        s = [0.5, 0.5, 0.5]
+        s[c] = 0.0
+        z, y, x = np.meshgrid((ii + s[2]) * h, (ii + s[1]) * h, (ii + s[0]) * h, indexing="ij")
+        pos.append((x, y, z))
+    torque = h ** 3 * np.array([
+        np.sum(pos[2][1] * f[2]) - np.sum(pos[1][2] * f[1]),
+        np.sum(pos[0][2] * f[0]) - np.sum(pos[2][0] * f[2]),
+        np.sum(pos[1][0] * f[1]) - np.sum(pos[0][1] * f[0])])
+    want = np.cross(p.x.T, G.T).sum(axis=0)
+    np.testing.assert_allclose(torque, want, rtol=1e-11, atol=1e-13)
+
+
+def test_nodal_interp_exact_on_constant_and_linear_fields():
+    p, _ = small_problem(n=16, blocks=(3, 2, 2))
+    m = oracle.Model(p)
+    n, h = p.grid.n[0], p.grid.h
+    const = np.array([0.3, -1.2, 2.5])
+    u = np.broadcast_to(const[:, None, None, None], (3, n, n, n)).copy()
+    np.testing.assert_allclose(m.interp_nodal(p.x, u),
+                               np.broadcast_to(const[:, None], (3, p.n_nodes)), rtol=1e-13)
+    A = np.random.default_rng(2).normal(size=(3, 3))
+    b = np.array([0.1, 0.2, -0.3])
+    ii = np.arange(n)
+    for c in range(3):
+        s = [0.5, 0.5, 0.5]
+        s[c] = 0.0
+        z, y, x = np.meshgrid((ii + s[2]) * h, (ii + s[1]) * h, (ii + s[0]) * h, indexing="ij")
+        u[c] = A[c, 0] * x + A[c, 1] * y + A[c, 2] * z + b[c]
+    np.testing.assert_allclose(m.interp_nodal(p.x, u), A @ p.x + b[:, None], rtol=1e-12,
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("centre", [None, (0.99, 0.5, 0.01)])
+def test_nodal_spread_interp_adjoint_identity(centre):
+    p, G = small_problem(n=16, blocks=(3, 3, 2), centre=centre)
+    m = oracle.Model(p)
+    u = np.random.default_rng(12).normal(size=(3, 16, 16, 16))
+    lhs = p.grid.h ** 3 * np.sum(m.spread_nodal(p.x, G) * u)
+    assert lhs == pytest.approx(np.sum(G * m.interp_nodal(p.x, u)), rel=1e-12)
+
+
+def test_nodal_linear_and_position_adjoints():
+    p, G = small_problem(n=16, blocks=(3, 2, 2))
+    m = oracle.Model(p)
+    rng = np.random.default_rng(15)
+    gf = rng.normal(size=(3, 16, 16, 16))
+    gU = rng.normal(size=G.shape)
+    u = m.spread_nodal(p.x, rng.normal(size=G.shape))
+    gG, gx_s = m.spread_nodal_adj(p.x, G, gf)
+    gu, gx_i = m.interp_nodal_adj(p.x, u, gU)
+    assert np.sum(gG * G) == pytest.approx(np.sum(gf * m.spread_nodal(p.x, G)), rel=1e-12)
+    assert np.sum(gu * u) == pytest.approx(np.sum(gU * m.interp_nodal(p.x, u)), rel=1e-12)
+    eps = 1e-6 * p.grid.h
+    for _ in range(4):
+        d = rng.normal(size=p.x.shape)
+        fd_s = (np.sum(gf * m.spread_nodal(p.x + eps * d, G)) -
+                np.sum(gf * m.spread_nodal(p.x - eps * d, G))) / (2 * eps)
+        assert np.sum(gx_s * d) == pytest.approx(fd_s, rel=1e-6)
+        fd_i = (np.sum(gU * m.interp_nodal(p.x + eps * d, u)) -
+                np.sum(gU * m.interp_nodal(p.x - eps * d, u))) / (2 * eps)
+        assert np.sum(gx_i * d) == pytest.approx(fd_i, rel=1e-6)
+
+
 def test_loss_gradient_chain_by_differences():
     # the differentiation workload's loss on a small shell:
     # L = sum_a |U_a|^2 + sqrt(h^3 sum |f|^2), gradients in x and the 8 HO
