@@ -298,6 +298,18 @@ def run_ours(args):
     del plan32
     barrier()
 
+    # --- the same forward with the nodal quadrature rule (N coupling points) ---
+    plann = ibfe.Plan(conn, X, prob.grid.n, prob.grid.h, fibres=fib, mat_id=mid,
+                      quad=ibfe.IB_QUAD_NODAL)
+    fwdn = lambda: ibfe.ib_forward(plann, mats, pos, u, G, f, U)
+    for _ in range(args.warmup):
+        fwdn()
+    barrier()
+    msn = timed(fwdn, args.steps)
+    t_fwdn = sum(msn) / len(msn)
+    del plann
+    barrier()
+
     # --- adjoint ---------------------------------------------------------
     rng = np.random.default_rng(77 + rank)
     gU = torch.from_numpy(rng.normal(size=(3, N)).astype(np.float32)).to(dev)
@@ -460,6 +472,9 @@ def run_ours(args):
                          "note": "same forward with J-1, ln J and I4f-1 in FP32 "
                                  "(IB_FP32_SPLIT_F32STAB; its Hessian-vector product misses the "
                                  "2e-5 adjoint tolerance at this size)"},
+        "nodal_rule": {"ms_per_step": t_fwdn, "points": N,
+                       "note": "the same forward with the nodal quadrature rule of Section 4.4 "
+                               "(coupling points = the N nodes; the force keeps the Gauss rule)"},
         "batched": batch_line,
         "adjoint_ms_per_step": t_adj,
         "adjoint_forward_ratio": t_adj / t_fwd,

@@ -18,6 +18,12 @@
  *   spreading and interpolation under one quadrature (Section 4.4) is the
  *   identity  h^3 sum_faces f . u = sum_nodes G . U.
  *
+ *   The coupling points are chosen per plan (ib_quad): the Gauss points of
+ *   the elements (IB_QUAD_GAUSS2, above) or the nodes themselves
+ *   (IB_QUAD_NODAL, the nodal quadrature rule N_q of Section 4.4: U_a is
+ *   U^IB at the node's displaced position, and f spreads the nodal forces
+ *   G_a from the nodes).  The nodal force is the Gauss-rule one in both.
+ *
  * Conventions
  *   Grid    periodic box [origin, origin + n h); fields are [3][n2][n1][n0]
  *           (x fastest).  Component c lives on the lower c-faces: face
@@ -118,13 +124,21 @@ typedef struct {
 
 typedef struct ib_plan ib_plan;
 
+/* Coupling points of spreading and interpolation (Section 4.4). */
+typedef enum {
+  IB_QUAD_GAUSS2 = 0, /* the 2x2x2 Gauss points of every element (8 E points) */
+  IB_QUAD_NODAL = 1   /* the nodes (N points): the nodal rule N_q, w_q = m_a */
+} ib_quad;
+
 /* Create a plan for one mesh on one grid: validates the mesh, builds the
  * node->(element, corner) incidence lists (a gather index, not a matrix), the
  * lumped mass and the Gauss weights w_q j0, and allocates all workspace.
- * Synchronises `stream`.  Returns IB_ERR_INVERTED if an element has a
- * non-positive reference Jacobian at a Gauss point. */
-ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t precision,
-                         void* stream, ib_plan** out);
+ * `quad` is an ib_quad, `precision` an ib_precision.  Synchronises `stream`.
+ * Returns IB_ERR_INVERTED if an element has a non-positive reference
+ * Jacobian at a Gauss point, IB_ERR_INVALID_ARG for an unknown quad or
+ * precision. */
+ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
+                         int32_t precision, void* stream, ib_plan** out);
 ib_status ib_plan_destroy(ib_plan* plan);
 
 /* Copy the plan's lumped mass m [N] (Real) into `mass` (device). */
@@ -138,14 +152,15 @@ ib_status ib_fe_force(ib_plan* plan, const ib_material* mats, int32_t n_mats,
                       const ib_pos* x, void* G, double* energy, void* stream);
 
 /* Spreading: f (device Real [3][n2][n1][n0], every entry overwritten) from
- * nodal forces G (device Real [3][N]): F_q = sum_a N_a G_a / m_a,
- * f^c(face) = sum_q F_q^c w_q j0 delta_h(x_face - chi_q).  The result is
- * bitwise reproducible (fixed summation order, no floating-point atomics). */
+ * nodal forces G (device Real [3][N]).  Gauss rule: F_q = sum_a N_a G_a / m_a,
+ * f^c(face) = sum_q F_q^c w_q j0 delta_h(x_face - chi_q).  Nodal rule:
+ * f^c(face) = sum_a G_a^c delta_h(x_face - x_a).  The result is bitwise
+ * reproducible (fixed summation order, no floating-point atomics). */
 ib_status ib_spread(ib_plan* plan, const ib_pos* x, const void* G, void* f, void* stream);
 
 /* Interpolation: U (device Real [3][N], overwritten) from the MAC velocity u
  * (device Real [3][n2][n1][n0]): U^IB_q = sum_faces u h^3 delta_h(x_face - chi_q),
- * U_a = m_a^-1 sum_q N_a w_q j0 U^IB_q. */
+ * Gauss rule: U_a = m_a^-1 sum_q N_a w_q j0 U^IB_q; nodal rule: U_a = U^IB at x_a. */
 ib_status ib_interp(ib_plan* plan, const ib_pos* x, const void* u, void* U, void* stream);
 
 /* Forward coupling in one call, sharing one Gauss-point sort:

@@ -61,6 +61,13 @@ __global__ void __launch_bounds__(256) k_elem_project(const Real* __restrict__ v
   }
 }
 
+// out[i] = add[i] + src[i] (add optional, may alias out)
+template <typename Real>
+__global__ void k_node_copy(const Real* __restrict__ src, const Real* add, int64_t n, Real* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = add ? add[i] + src[i] : src[i];
+}
+
 // w_q j0 at the eight Gauss points of each element (unit Gauss weights).
 template <typename Real>
 __global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
@@ -154,6 +161,20 @@ ib_status launch_node_gather(ib_plan* p, const void* elem, const void* scale, vo
                              cudaStream_t s, const void* add) {
   return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, add, out, 3, s)
                                  : gather_t<float>(p, elem, scale, add, out, 3, s);
+}
+
+ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* add,
+                           cudaStream_t s) {
+  const int64_t n = 3LL * p->N;
+  if (n == 0) return IB_OK;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (p->precision == IB_FP64)
+    k_node_copy<double><<<blocks, 256, 0, s>>>((const double*)src, (const double*)add, n,
+                                               (double*)out);
+  else
+    k_node_copy<float><<<blocks, 256, 0, s>>>((const float*)src, (const float*)add, n,
+                                              (float*)out);
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
 ib_status launch_elem_project(ib_plan* p, const void* vals, void* out, cudaStream_t s) {

@@ -163,6 +163,20 @@ ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, 
   return launch_node_gather(p, elem, scale, out, s, add);
 }
 
+// Coupling-point values gq [3][Q] to nodal values: Gauss rule, the lumped
+// projection out = add + scale * gather(project(gq)) (scale: the inverse mass
+// or none); nodal rule, the points are the nodes: out = add + gq.
+ib_status to_nodes(ib_plan* p, const void* gq, void* elem, const void* scale, void* out,
+                   cudaStream_t s, const void* add = nullptr) {
+  if (p->quad == IB_QUAD_NODAL) {
+    Stage sc(p, IB_STAGE_GATHER, s, 1);
+    return launch_node_copy(p, gq, out, add, s);
+  }
+  ib_status st = do_project(p, gq, elem, s);
+  if (st == IB_OK) st = do_gather(p, elem, scale, out, s, add);
+  return st;
+}
+
 ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
   Stage sc(p, IB_STAGE_SPREAD, s, spread_launches());
   return launch_spread(p, scale, f, s);
@@ -177,8 +191,7 @@ ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s,
                          void* elem = nullptr) {
   if (!elem) elem = p->elem_scratch;
   ib_status st = do_interp(p, u, 0, 1.0, 0.0, s);
-  if (st == IB_OK) st = do_project(p, p->gq_a, elem, s);
-  if (st == IB_OK) st = do_gather(p, elem, p->inv_mass, U, s);
+  if (st == IB_OK) st = to_nodes(p, p->gq_a, elem, p->inv_mass, U, s);
   return st;
 }
 
@@ -202,13 +215,14 @@ const char* ib_status_str(ib_status s) {
   return "unknown status";
 }
 
-ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t precision,
-                         void* stream, ib_plan** out) {
+ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
+                         int32_t precision, void* stream, ib_plan** out) {
   if (!out) return IB_ERR_INVALID_ARG;
   *out = nullptr;
   if (!mesh || !grid) return IB_ERR_INVALID_ARG;
   if (precision != IB_FP32_SPLIT && precision != IB_FP64 && precision != IB_FP32_SPLIT_F32STAB)
     return IB_ERR_INVALID_ARG;
+  if (quad != IB_QUAD_GAUSS2 && quad != IB_QUAD_NODAL) return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
     return IB_ERR_INVALID_ARG;
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
@@ -219,7 +233,9 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
   }
   if ((int64_t)mesh->n_elems >= (1LL << kIncShift) / 8) return IB_ERR_CAPACITY;
   cudaStream_t s = S(stream);
-  const int64_t E = mesh->n_elems, N = mesh->n_nodes, Q = 8 * E;
+  // Q coupling points: the Gauss points (8 per element) or the nodes
+  const int64_t E = mesh->n_elems, N = mesh->n_nodes;
+  const int64_t Q = quad == IB_QUAD_NODAL ? N : 8 * E;
 
   // connectivity and materials to the host for validation and incidence lists
   std::vector<int32_t> conn(8 * E), mid;
@@ -255,6 +271,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
   ib_plan* p = new ib_plan;
   std::memset(p, 0, sizeof(ib_plan));
   p->precision = precision;
+  p->quad = quad;
   p->N = (int)N;
   p->E = (int)E;
   p->Q = Q;
@@ -275,7 +292,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t preci
   const size_t rs = p->rsize;
   bool good = dalloc(&p->inc_off, 4 * (N + 1)) && dalloc(&p->inc_idx, 4 * 8 * E) &&
               dalloc(&p->mass, rs * N) && dalloc(&p->inv_mass, rs * N) &&
-              dalloc(&p->wj0, rs * Q) && dalloc(&p->elem_scratch, rs * 24 * E) &&
+              dalloc(&p->wj0, rs * 8 * E) && dalloc(&p->elem_scratch, rs * 24 * E) &&
               dalloc(&p->elem_scratch2, rs * 24 * E) && dalloc(&p->keys[0], 4 * Q) &&
               dalloc(&p->keys[1], 4 * Q) && dalloc(&p->vals[0], 4 * Q) &&
               dalloc(&p->vals[1], 4 * Q) && dalloc(&p->hist, 4 * 256 * (size_t)p->hist_blocks) &&
@@ -455,10 +472,8 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     if (st == IB_OK) st = launch_permute_values(p, s);
   }
   if (st == IB_OK && gf) st = do_interp(p, gf, 1, ih3, ih3 / h, s);
-  if (st == IB_OK && gf) st = do_project(p, p->gq_a, p->elem_scratch, s);
-  if (st == IB_OK && gf) st = do_gather(p, p->elem_scratch, p->inv_mass, gGt, s, gG);
-  if (st == IB_OK && gf) st = do_project(p, p->gq_b, p->elem_scratch2, s);
-  if (st == IB_OK && gf) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
+  if (st == IB_OK && gf) st = to_nodes(p, p->gq_a, p->elem_scratch, p->inv_mass, gGt, s, gG);
+  if (st == IB_OK && gf) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   if (st == IB_OK && !gf) {
     if (!ok(cudaMemsetAsync(gx, 0, nbytes, s)) ||
         !ok(gG ? cudaMemcpyAsync(gGt, gG, nbytes, cudaMemcpyDeviceToDevice, s)
@@ -476,8 +491,7 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
   }
   if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b);
   if (st == IB_OK && gU) st = do_interp(p, u, 2, 0.0, 1.0 / h, b);
-  if (st == IB_OK && gU) st = do_project(p, p->gq_b, p->elem_scratch2, b);
-  if (st == IB_OK && gU) st = do_gather(p, p->elem_scratch2, nullptr, gx, b, gx);
+  if (st == IB_OK && gU) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, b, gx);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   // ... beside the force adjoint, whose nodal gather adds into gx after the join
   if (st == IB_OK && force) {
@@ -506,12 +520,8 @@ ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* 
   const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
   st = do_points_sorted(p, x, G, s);
   if (st == IB_OK) st = do_interp(p, gf, gx ? 1 : 0, ih3, ih3 / h, s);
-  if (st == IB_OK) st = do_project(p, p->gq_a, p->elem_scratch, s);
-  if (st == IB_OK) st = do_gather(p, p->elem_scratch, p->inv_mass, gG, s);
-  if (st == IB_OK && gx) {
-    st = do_project(p, p->gq_b, p->elem_scratch2, s);
-    if (st == IB_OK) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
-  }
+  if (st == IB_OK) st = to_nodes(p, p->gq_a, p->elem_scratch, p->inv_mass, gG, s);
+  if (st == IB_OK && gx) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   return check_launch(st);
 }
 
@@ -525,8 +535,7 @@ ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* 
   if (st == IB_OK) st = do_spread(p, 1.0, gu, s);
   if (st == IB_OK && gx) {
     st = do_interp(p, u, 2, 0.0, 1.0 / p->grid.h, s);
-    if (st == IB_OK) st = do_project(p, p->gq_b, p->elem_scratch2, s);
-    if (st == IB_OK) st = do_gather(p, p->elem_scratch2, nullptr, gx, s);
+    if (st == IB_OK) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   }
   return check_launch(st);
 }

@@ -47,8 +47,9 @@ struct ib_plan_impl;
 // The opaque plan.
 struct ib_plan {
   int precision;         // ib_precision
+  int quad;              // ib_quad: coupling points are Gauss points or nodes
   int N, E;
-  int64_t Q;             // Gauss points = 8 E
+  int64_t Q;             // coupling points: 8 E Gauss points or N nodes
   ibfe::GridDev grid;
   int ntiles;
   const int32_t* conn;
@@ -129,6 +130,9 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
 
 // assemble.cu
+// out = add + src over 3 N values (add optional, may be out)
+ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* add,
+                           cudaStream_t s);
 // out = add + node_scale * (gather of elem); add optional (may be out)
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* node_scale, void* out,
                              cudaStream_t s, const void* add = nullptr);

@@ -53,7 +53,7 @@ struct InterpArgs {
   const Real* p_off;
   const Real* p_val;
   const int32_t* p_idx;
-  const Real* wj0;
+  const Real* wj0;        // w_q j0 per Gauss point, or null (nodal rule: weight 1)
   const Real* u;
   Real vscale, gscale;
   Real* out_a;
@@ -390,7 +390,7 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
       }
     }
     if (MODE != 2) {
-      const Real wq = __ldg(A.wj0 + gq) * A.vscale;
+      const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * A.vscale : A.vscale;
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
     }
@@ -458,7 +458,8 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.p_off = (const Real*)p->p_off;
   A.p_val = (const Real*)p->p_val;
   A.p_idx = p->p_idx;
-  A.wj0 = (const Real*)p->wj0;
+  // the projection weight w_q j0 of a Gauss point; none for the nodal rule
+  A.wj0 = p->quad == IB_QUAD_NODAL ? nullptr : (const Real*)p->wj0;
   A.u = (const Real*)u;
   A.vscale = (Real)vscale;
   A.gscale = (Real)gscale;

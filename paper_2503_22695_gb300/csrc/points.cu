@@ -50,6 +50,30 @@ struct PtArgs {
   int* status;
 };
 
+// Packed cell, and the tile key with either the point's slot in its tile
+// (binning: one atomic per distinct tile of the warp) or its index (sorting).
+template <typename Real, bool kBin>
+__device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, const int cw[3]) {
+  A.q_cell[gq] = pack_cell(cw[0], cw[1], cw[2]);
+  const uint32_t tile = (uint32_t)((cw[0] >> kTileShift) +
+                                   A.g.nt[0] * ((cw[1] >> kTileShift) +
+                                                A.g.nt[1] * (cw[2] >> kTileShift)));
+  if (kBin) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, tile);
+    const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(A.count + tile, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    A.key[gq] = tile;
+    A.val[gq] = base + __popc(peers & ((1u << lane) - 1u));
+  } else {
+    const uint32_t local = (uint32_t)((((cw[2] & 7) << 3) | (cw[1] & 7)) << 3 | (cw[0] & 7));
+    A.key[gq] = (tile << kLocalBits) | local;
+    A.val[gq] = (int32_t)gq;
+  }
+}
+
 template <typename Real, bool kBin>
 __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,25 +140,7 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
       cw[d] = wrap_idx(c0[d] + (int)k, A.g.n[d]);
       A.q_off[d * Q + gq] = off;
     }
-    A.q_cell[gq] = pack_cell(cw[0], cw[1], cw[2]);
-    const uint32_t tile = (uint32_t)((cw[0] >> kTileShift) +
-                                     A.g.nt[0] * ((cw[1] >> kTileShift) +
-                                                  A.g.nt[1] * (cw[2] >> kTileShift)));
-    if (kBin) {
-      // slot of the point in its tile: one atomic per distinct tile of the warp
-      const unsigned act = __activemask();
-      const unsigned peers = __match_any_sync(act, tile);
-      const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(A.count + tile, __popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      A.key[gq] = tile;
-      A.val[gq] = base + __popc(peers & ((1u << lane) - 1u));
-    } else {
-      const uint32_t local = (uint32_t)((((cw[2] & 7) << 3) | (cw[1] & 7)) << 3 | (cw[0] & 7));
-      A.key[gq] = (tile << kLocalBits) | local;
-      A.val[gq] = (int32_t)gq;
-    }
+    bin_point<Real, kBin>(A, gq, cw);
     if (A.V) {
       const Real w = __ldg(A.wj0 + gq);
 #pragma unroll
@@ -145,6 +151,41 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
         A.q_val[d * Q + gq] = w * s;
       }
     }
+  }
+}
+
+// Nodal quadrature rule (Section 4.4): the coupling points are the nodes,
+// chi_a = x_a (gq = a), and a carried value is V_a itself.
+template <typename Real, bool kBin>
+__global__ void __launch_bounds__(256) k_points_nodal(PtArgs<Real> A) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= A.N) return;
+  const int64_t N = A.N;
+  int c[3];
+  Real o[3];
+  A.pos.load(a, c, o);
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (!(o[d] >= Real(0) && o[d] < Real(1))) bad = true;
+  if (bad) {  // keep indices in range; the caller sees IB_ERR_NONFINITE
+    set_status(A.status, kStatNonfinite);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c[d] = 0;
+      o[d] = Real(0);
+    }
+  }
+  int cw[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cw[d] = wrap_idx(c[d], A.g.n[d]);
+    A.q_off[d * N + a] = o[d];
+  }
+  bin_point<Real, kBin>(A, a, cw);
+  if (A.V) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) A.q_val[d * N + a] = __ldg(A.V + d * N + a);
   }
 }
 
@@ -380,7 +421,10 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   A.count = p->tile_end;
   cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
   cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
-  k_points<float, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  if (p->quad == IB_QUAD_NODAL)
+    k_points_nodal<float, true><<<(p->N + 255) / 256, 256, 0, s>>>(A);
+  else
+    k_points<float, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -406,7 +450,10 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
   A.val = p->vals[0];
   A.status = p->dstatus;
   A.count = nullptr;
-  k_points<double, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+  if (p->quad == IB_QUAD_NODAL)
+    k_points_nodal<double, false><<<(p->N + 255) / 256, 256, 0, s>>>(A);
+  else
+    k_points<double, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -414,7 +461,7 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
 
 ib_status launch_points(ib_plan* p, const void* xa, const float* off, const void* nodal,
                         int val_kind, cudaStream_t s) {
-  if (p->E == 0) return IB_OK;
+  if (p->Q == 0) return IB_OK;
   const void* V = val_kind ? nodal : nullptr;
   return p->precision == IB_FP64 ? points_t<double>(p, xa, off, V, s)
                                  : points_t<float>(p, xa, off, V, s);
@@ -466,7 +513,12 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
 }
 
 ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
-  if (p->E == 0) return IB_OK;
+  if (p->Q == 0) return IB_OK;
+  if (p->quad == IB_QUAD_NODAL)  // the nodal values are the point values
+    return cudaMemcpyAsync(p->q_val, nodal, p->rsize * 3 * (size_t)p->N,
+                           cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? IB_OK
+               : IB_ERR_CUDA;
   if (p->precision == IB_FP64)
     k_point_values<double><<<(p->E + 127) / 128, 128, 0, s>>>(
         p->E, p->N, p->conn, (const double*)nodal, (const double*)p->inv_mass,

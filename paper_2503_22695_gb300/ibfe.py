@@ -28,6 +28,7 @@ IB_OK, IB_ERR_INVALID_ARG, IB_ERR_CUDA, IB_ERR_NONFINITE = 0, 1, 2, 3
 IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 7
 IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO = 0, 1, 2
 IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
+IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
 IB_MAX_MATERIALS = 8
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
 N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9}
@@ -69,7 +70,7 @@ def _load():
     L = C.CDLL(LIB_PATH)
     vp, i32, dp = C.c_void_p, C.c_int32, C.POINTER(C.c_double)
     sigs = {
-        "ib_plan_create": [C.POINTER(_Mesh), C.POINTER(_Grid), i32, vp, C.POINTER(vp)],
+        "ib_plan_create": [C.POINTER(_Mesh), C.POINTER(_Grid), i32, i32, vp, C.POINTER(vp)],
         "ib_plan_destroy": [vp],
         "ib_lumped_mass": [vp, vp, vp],
         "ib_fe_force": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, dp, vp],
@@ -159,8 +160,9 @@ class Plan:
 
     def __init__(self, conn: torch.Tensor, X: torch.Tensor, n, h: float, origin=(0.0, 0.0, 0.0),
                  fibres: torch.Tensor = None, mat_id: torch.Tensor = None,
-                 precision: int = IB_FP32_SPLIT):
+                 precision: int = IB_FP32_SPLIT, quad: int = IB_QUAD_GAUSS2):
         self.dtype = torch.float64 if precision == IB_FP64 else torch.float32
+        self.quad = quad
         _check(conn, torch.int32, (8, -1), "conn")
         _check(X, self.dtype, (3, -1), "X")
         if fibres is not None:
@@ -178,7 +180,7 @@ class Plan:
                      None if mat_id is None else mat_id.data_ptr())
         grid = _Grid((C.c_int32 * 3)(*self.n), self.h, (C.c_double * 3)(*origin))
         out = C.c_void_p()
-        _chk(_lib.ib_plan_create(C.byref(mesh), C.byref(grid), precision, _stream(),
+        _chk(_lib.ib_plan_create(C.byref(mesh), C.byref(grid), quad, precision, _stream(),
                                  C.byref(out)), "ib_plan_create")
         self._h = out
 
@@ -229,8 +231,8 @@ def _out(t, plan, shape, name):
 
 
 def ib_plan_create(conn, X, n, h, origin=(0.0, 0.0, 0.0), fibres=None, mat_id=None,
-                   precision=IB_FP32_SPLIT) -> Plan:
-    return Plan(conn, X, n, h, origin, fibres, mat_id, precision)
+                   precision=IB_FP32_SPLIT, quad=IB_QUAD_GAUSS2) -> Plan:
+    return Plan(conn, X, n, h, origin, fibres, mat_id, precision, quad)
 
 
 def ib_plan_destroy(plan: Plan):

@@ -16,7 +16,7 @@ def rel_l2(a, b):
 class Case:
     """A problem on the GPU (through the C ABI) and in the oracle."""
 
-    def __init__(self, prob: I.Problem):
+    def __init__(self, prob: I.Problem, quad: int = 0):
         import torch
         from paper_2503_22695_gb300 import ibfe
         self.prob = prob
@@ -32,7 +32,8 @@ class Case:
         g = prob.grid
         self.plan = ibfe.Plan(self.conn, self.X, g.n, g.h, g.origin, fibres=self.fib,
                               mat_id=self.mat_id,
-                              precision=ibfe.IB_FP64 if prob.fp64 else ibfe.IB_FP32_SPLIT)
+                              precision=ibfe.IB_FP64 if prob.fp64 else ibfe.IB_FP32_SPLIT,
+                              quad=quad)
         if prob.fp64:
             self.x_np = prob.x.copy()
             self.pos = ibfe.Pos(x64=torch.from_numpy(self.x_np).to(dev))

@@ -42,8 +42,8 @@ def test_host_side_argument_checks(lib):
     assert lib.ib_version() == 100
     out = C.c_void_p()
     # null mesh / grid / out pointer: rejected before touching the device
-    assert lib.ib_plan_create(None, None, 0, None, C.byref(out)) == 1
-    assert lib.ib_plan_create(None, None, 0, None, None) == 1
+    assert lib.ib_plan_create(None, None, 0, 0, None, C.byref(out)) == 1
+    assert lib.ib_plan_create(None, None, 0, 0, None, None) == 1
     for fn in ("ib_fe_force", "ib_spread", "ib_interp", "ib_spread_adj", "ib_interp_adj",
                "ib_fe_force_adj", "ib_forward"):
         assert getattr(lib, fn)(*([None] * 9)) == 1, fn
