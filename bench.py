@@ -248,6 +248,8 @@ def run_ours(args):
     off = torch.from_numpy(prob.off).to(dev)
     pos = ibfe.Pos(cell=cell, off=off)
     u = torch.from_numpy(prob.u).to(dev)
+    tuning = ibfe.ib_plan_autotune(plan, [ibfe.Material(m.model, m.params) for m in prob.materials],
+                                   pos, u)
     mats = [ibfe.Material(m.model, m.params) for m in prob.materials]
     G = torch.empty((3, N), device=dev)
     f = torch.empty(plan.grid_shape(), device=dev)
@@ -467,6 +469,9 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload, "grid": [n, n, n], "elements": E, "nodes": N,
                    "gauss_points": Q, "l2": "flushed before every timed step (256 MiB write)",
+                   "tuning": dict(zip(("points_per_item", "force_ctas_per_sm",
+                                       "spread_ctas_per_sm_cap", "interp_ctas_per_sm_cap"),
+                                      tuning)),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp32_scalars": {"ms_per_step": t_fwd32, "value": Q * world / (t_fwd32 * 1e-3),
                          "note": "same forward with J-1, ln J and I4f-1 in FP32 "

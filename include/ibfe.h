@@ -208,6 +208,29 @@ ib_status ib_backward(ib_plan* plan, const ib_material* mats, int32_t n_mats, co
                       const void* u, const void* G, const void* gG, const void* gf,
                       const void* gU, void* gx, void* gu, double* gparams, void* stream);
 
+/* Launch tuning of a plan, four entries:
+ *   [0] points per work item of spreading and interpolation, 512..1024
+ *       (a tile's points are cut into items of at most this many);
+ *   [1] FE-force CTAs per SM in ib_forward, 1..4 (its persistent grid leaves
+ *       the rest of each SM to the binning and interpolation beside it);
+ *   [2] cap on the spreading CTAs per SM, 1..8;
+ *   [3] cap on the interpolation CTAs per SM, 1..8.
+ * Defaults {1024, 2, 8, 8} (the caps above the occupancy limits mean none).
+ * Results do not depend on the tuning for FP32 plans (bitwise); FP64 plans
+ * change only in the summation order of the spreading.  get/set are host
+ * operations on the plan; set returns IB_ERR_INVALID_ARG out of range. */
+ib_status ib_plan_get_tuning(const ib_plan* plan, int32_t tuning[4]);
+ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
+
+/* Autotuner: times ib_forward on the given inputs for candidate tunings
+ * (coordinate descent over the four entries in order: items of 1024 or 512
+ * points; 2, 1 or 3 force CTAs per SM; spreading and interpolation caps 8, 3
+ * or 2; one warm-up and the median of three timed calls each) and keeps the
+ * fastest.  Writes the choice to `tuning` (host, 4 entries) if non-NULL.
+ * Allocates temporary output buffers and synchronises `stream`. */
+ib_status ib_plan_autotune(ib_plan* plan, const ib_material* mats, int32_t n_mats,
+                           const ib_pos* x, const void* u, void* stream, int32_t tuning[4]);
+
 /* ---------------------------------------------------------------------------
  * Batched form: many independent structures, each with its own mesh, grid
  * and material table (a parameter sweep, for instance), run together.  The
@@ -215,7 +238,8 @@ ib_status ib_backward(ib_plan* plan, const ib_material* mats, int32_t n_mats, co
  * ib_batch_create builds one plan per instance and captures two CUDA graphs
  * whose branches are the instances' forward coupling (ib_forward) and
  * backward (ib_backward, parameter gradients kept on the device); each graph
- * is then replayed with one launch.  All pointers in ib_instance are device memory that must stay
+ * is then replayed with one launch.  Each instance's plan is autotuned
+ * (ib_plan_autotune on its own inputs) before the capture.  All pointers in ib_instance are device memory that must stay
  * valid and fixed for the batch's lifetime (the graphs bake them in); update
  * the data in place between replays.  Synchronises `stream` at creation.
  * ------------------------------------------------------------------------- */

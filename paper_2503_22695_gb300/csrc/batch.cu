@@ -118,6 +118,9 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
   for (int i = 0; i < n && st == IB_OK; ++i) {
     st = ib_plan_create(&inst[i].mesh, &inst[i].grid, IB_QUAD_GAUSS2, precision, stream,
                         &b->plans[i]);
+    if (st == IB_OK)
+      st = ib_plan_autotune(b->plans[i], inst[i].mats, inst[i].n_mats, &inst[i].x, inst[i].u,
+                            stream, nullptr);
     if (st == IB_OK && (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess))
       st = IB_ERR_CUDA;

@@ -2,6 +2,7 @@
 // entry points declared in include/ibfe.h.  Every operator is a short,
 // stream-ordered sequence of the kernels in this directory; nothing here
 // allocates after ib_plan_create.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -272,6 +273,10 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   std::memset(p, 0, sizeof(ib_plan));
   p->precision = precision;
   p->quad = quad;
+  p->chunk = kChunk;
+  p->fe_ctas = 2;
+  p->push_per_sm = 8;
+  p->interp_per_sm = 8;
   p->N = (int)N;
   p->E = (int)E;
   p->Q = Q;
@@ -577,6 +582,88 @@ ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, c
     for (int m = 0; m < n_mats; ++m)
       for (int k = 0; k < 9; ++k) gparams[m * 9 + k] = red[m * 9 + k];
   }
+  return st;
+}
+
+ib_status ib_plan_get_tuning(const ib_plan* p, int32_t tuning[4]) {
+  if (!p || !tuning) return IB_ERR_INVALID_ARG;
+  tuning[0] = p->chunk;
+  tuning[1] = p->fe_ctas;
+  tuning[2] = p->push_per_sm;
+  tuning[3] = p->interp_per_sm;
+  return IB_OK;
+}
+
+ib_status ib_plan_set_tuning(ib_plan* p, const int32_t tuning[4]) {
+  if (!p || !tuning) return IB_ERR_INVALID_ARG;
+  if (tuning[0] < kMinChunk || tuning[0] > kChunk || tuning[1] < 1 || tuning[1] > 4 ||
+      tuning[2] < 1 || tuning[2] > 8 || tuning[3] < 1 || tuning[3] > 8)
+    return IB_ERR_INVALID_ARG;
+  p->chunk = tuning[0];
+  p->fe_ctas = tuning[1];
+  p->push_per_sm = tuning[2];
+  p->interp_per_sm = tuning[3];
+  return IB_OK;
+}
+
+ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
+                           const ib_pos* x, const void* u, void* stream, int32_t tuning[4]) {
+  if (!p || !u) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  const size_t rs = p->rsize;
+  const size_t field = rs * 3 * (size_t)p->grid.n[0] * p->grid.n[1] * p->grid.n[2];
+  void *G = nullptr, *f = nullptr, *U = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (!ok(cudaMalloc(&G, rs * 3 * (size_t)p->N)) || !ok(cudaMalloc(&f, field)) ||
+      !ok(cudaMalloc(&U, rs * 3 * (size_t)p->N)) || !ok(cudaEventCreate(&a)) ||
+      !ok(cudaEventCreate(&b)))
+    st = IB_ERR_CUDA;
+  // one warm-up call, then the median of three timed calls
+  auto time_forward = [&](float& ms) -> ib_status {
+    ib_status r = ib_forward(p, mats, n_mats, x, u, G, f, U, s);
+    float t[3];
+    for (int k = 0; k < 3 && r == IB_OK; ++k) {
+      if (!ok(cudaEventRecord(a, s))) return IB_ERR_CUDA;
+      r = ib_forward(p, mats, n_mats, x, u, G, f, U, s);
+      if (r == IB_OK && (!ok(cudaEventRecord(b, s)) || !ok(cudaEventSynchronize(b)) ||
+                         !ok(cudaEventElapsedTime(&t[k], a, b))))
+        r = IB_ERR_CUDA;
+    }
+    if (r != IB_OK) return r;
+    std::sort(t, t + 3);
+    ms = t[1];
+    return IB_OK;
+  };
+  int32_t cur[4];
+  ib_plan_get_tuning(p, cur);
+  const int32_t cand[4][3] = {{1024, 512, 0}, {2, 1, 3}, {8, 3, 2}, {8, 3, 2}};
+  for (int k = 0; k < 4 && st == IB_OK; ++k) {
+    int32_t best = cur[k];
+    float best_ms = 0.f;
+    bool first = true;
+    for (int j = 0; j < 3 && cand[k][j] && st == IB_OK; ++j) {
+      int32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
+      trial[k] = cand[k][j];
+      ib_plan_set_tuning(p, trial);
+      float ms = 0.f;
+      st = time_forward(ms);
+      if (st == IB_OK && (first || ms < best_ms)) {
+        best = cand[k][j];
+        best_ms = ms;
+        first = false;
+      }
+    }
+    cur[k] = best;
+    ib_plan_set_tuning(p, cur);
+  }
+  if (G) cudaFree(G);
+  if (f) cudaFree(f);
+  if (U) cudaFree(U);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st == IB_OK && tuning) ib_plan_get_tuning(p, tuning);
   return st;
 }
 

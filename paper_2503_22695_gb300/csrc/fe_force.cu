@@ -134,10 +134,6 @@ __device__ __forceinline__ float log1p_s(float x) { return log1pf(x); }
 #ifndef IBFE_FE_MIN_BLOCKS_ADJ
 #define IBFE_FE_MIN_BLOCKS_ADJ 3
 #endif
-#ifndef IBFE_FE_CTAS_PER_SM
-#define IBFE_FE_CTAS_PER_SM 2
-#endif
-constexpr int kFeCtasPerSm = IBFE_FE_CTAS_PER_SM;  // CTAs per SM of the persistent forward grid
 
 template <typename Real, bool kAdj>
 constexpr int fe_min_blocks() {
@@ -652,7 +648,7 @@ ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, 
   FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
   const int threads = 128;
   // the forward runs beside the sort and interpolation; the adjoint runs alone
-  const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : kFeCtasPerSm;
+  const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : p->fe_ctas;
   const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
   if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
   if (p->precision == IB_FP32_SPLIT_F32STAB)

@@ -12,6 +12,7 @@ constexpr int kTileShift = 3;
 constexpr int kSpreadWarps = 8;     // warps (private accumulators) per spread CTA
 constexpr int kPackBits = 10;       // packed wrapped cell: x | y << 10 | z << 20
 constexpr int kChunk = 1024;        // maximum points per spread / interp work item
+constexpr int kMinChunk = 512;      // smallest work item the tuning may choose
 
 // Device-side status bits latched by kernels (read by ib_plan_sync_status).
 constexpr int kStatNonfinite = 1;
@@ -91,6 +92,10 @@ struct ib_plan {
   cudaEvent_t ev_ffork, ev_fsorted, ev_fjoin;  // ib_forward branch events
   int sm_count, push_ctas, merge_ctas, interp_ctas[3];
   int interp_tma, interp_ctas_tma[3];  // FP32: TMA-staged interpolation available
+  // launch tuning (ib_plan_set_tuning / ib_plan_autotune): points per work
+  // item, FE-force CTAs per SM in the forward, caps on the spreading and
+  // interpolation CTAs per SM (the occupancy maxima above are per-SM * sm_count)
+  int chunk, fe_ctas, push_per_sm, interp_per_sm;
   void* spread_scratch;  // Real [slots][3][12^3] halo'd per-tile blocks
   int32_t* q_cell;       // packed wrapped cell per Gauss point (unsorted, gq order)
   void* q_off;           // Real [3][Q]

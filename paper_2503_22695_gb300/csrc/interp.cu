@@ -53,6 +53,7 @@ struct InterpArgs {
   const Real* p_off;
   const Real* p_val;
   const int32_t* p_idx;
+  int chunk;               // points per work item
   const Real* wj0;        // w_q j0 per Gauss point, or null (nodal rule: weight 1)
   const Real* u;
   Real vscale, gscale;
@@ -218,8 +219,8 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
 __device__ __forceinline__ void local_cell_order(const InterpArgs<float>& A, int slot, int* cnt,
                                                  short* order, int* tmp, int tid) {
   const int tile = A.tile_list[slot];
-  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
-  const int e = min(A.tile_end[tile], s + kChunk);
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
+  const int e = min(A.tile_end[tile], s + A.chunk);
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int x0 = (tile % nt0) * kTile, y0 = ((tile / nt0) % nt1) * kTile,
             z0 = (tile / (nt0 * nt1)) * kTile;
@@ -316,8 +317,8 @@ template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
                                               int tid, const short* order) {
   const int tile = A.tile_list[slot];
-  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
-  const int e = min(A.tile_end[tile], s + kChunk);
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
+  const int e = min(A.tile_end[tile], s + A.chunk);
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
@@ -458,6 +459,7 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.p_off = (const Real*)p->p_off;
   A.p_val = (const Real*)p->p_val;
   A.p_idx = p->p_idx;
+  A.chunk = p->chunk;
   // the projection weight w_q j0 of a Gauss point; none for the nodal rule
   A.wj0 = p->quad == IB_QUAD_NODAL ? nullptr : (const Real*)p->wj0;
   A.u = (const Real*)u;
@@ -467,6 +469,9 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.out_b = (Real*)p->gq_b;
   A.status = p->dstatus;
   A.use_tma = 0;
+  // persistent grid: the occupancy maximum, capped by the plan's tuning
+  const int cap_ctas = p->interp_per_sm * p->sm_count;
+  auto cap = [cap_ctas](int ctas) { return ctas < cap_ctas ? ctas : cap_ctas; };
   const size_t smem = smem_bytes<Real>();
   cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
   if constexpr (sizeof(Real) == 4) {
@@ -474,20 +479,20 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
     if (p->interp_tma && make_velocity_map(p, u, &tmap)) {
       A.use_tma = 1;
       if (mode == 0)
-        k_interp_tma<0><<<p->interp_ctas_tma[0], kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<0><<<cap(p->interp_ctas_tma[0]), kThreads, kTmaSmem, s>>>(tmap, A);
       else if (mode == 1)
-        k_interp_tma<1><<<p->interp_ctas_tma[1], kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<1><<<cap(p->interp_ctas_tma[1]), kThreads, kTmaSmem, s>>>(tmap, A);
       else
-        k_interp_tma<2><<<p->interp_ctas_tma[2], kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<2><<<cap(p->interp_ctas_tma[2]), kThreads, kTmaSmem, s>>>(tmap, A);
       return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
     }
   }
   if (mode == 0)
-    k_interp_tile<Real, 0><<<p->interp_ctas[0], kThreads, smem, s>>>(A);
+    k_interp_tile<Real, 0><<<cap(p->interp_ctas[0]), kThreads, smem, s>>>(A);
   else if (mode == 1)
-    k_interp_tile<Real, 1><<<p->interp_ctas[1], kThreads, smem, s>>>(A);
+    k_interp_tile<Real, 1><<<cap(p->interp_ctas[1]), kThreads, smem, s>>>(A);
   else
-    k_interp_tile<Real, 2><<<p->interp_ctas[2], kThreads, smem, s>>>(A);
+    k_interp_tile<Real, 2><<<cap(p->interp_ctas[2]), kThreads, smem, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -24,6 +24,8 @@
 //   within a source tile, in work-item order, and is written once: exact
 //   integer sums rounded once (FP32), doubles in that fixed order (FP64).
 //   Periodic wrap happens only here, through the neighbour-tile index.
+#include <algorithm>
+
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -57,6 +59,7 @@ struct SpreadArgs {
   const int32_t* p_cell;
   const Real* p_off;
   const Real* p_val;
+  int chunk;                   // points per work item
   Real scale;
   Real* scratch;               // [items][3][12^3]
   Real* f;
@@ -116,8 +119,8 @@ __device__ __forceinline__ void push_item(const SpreadArgs<Real>& A, int slot, S
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int tile = A.tile_list[slot];
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
-  const int e = min(A.tile_end[tile], s + kChunk);
+  const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
+  const int e = min(A.tile_end[tile], s + A.chunk);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   const int hw = tid >> 4, l16 = tid & 15, dz = l16 >> 2, dy = l16 & 3;
   const int warp = tid >> 5;
@@ -333,8 +336,8 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     if (slot >= count) break;
     const int tile = A.tile_list[slot];
     const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-    const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * kChunk;
-    const int e = min(A.tile_end[tile], s + kChunk);
+    const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
+    const int e = min(A.tile_end[tile], s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
     for (int i = tid; i < 3 * kFxAcc * 2 / 4; i += kFxThreads)
       reinterpret_cast<uint4*>(acc_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -598,11 +601,13 @@ void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
   cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
   if (p->Q > 0)
     k_absmax<<<p->sm_count * 4, 256, 0, s>>>((const float*)p->p_val, 3 * p->Q, A.absmax);
-  k_spread_push_fx<<<p->push_ctas, kFxThreads, kFxSmem, s>>>(A);
+  k_spread_push_fx<<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads, kFxSmem,
+                     s>>>(A);
 }
 
 void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
-  k_spread_push<double><<<p->push_ctas, kPT, push_smem<double>(), s>>>(A);
+  k_spread_push<double><<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kPT,
+                          push_smem<double>(), s>>>(A);
 }
 
 template <typename Real>
@@ -621,6 +626,7 @@ ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
   A.p_cell = p->p_cell;
   A.p_off = (const Real*)p->p_off;
   A.p_val = (const Real*)p->p_val;
+  A.chunk = p->chunk;
   A.scale = (Real)scale;
   A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;

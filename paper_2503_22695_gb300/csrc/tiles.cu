@@ -4,7 +4,7 @@
 //   near       a tile of its 3x3x3 neighbourhood holds points
 //                                                   -> its faces are merged
 //   far        otherwise                          -> its faces are zero
-// A non-empty tile is cut into work items ("chunks") of at most kChunk
+// A non-empty tile is cut into work items ("chunks") of at most `chunk`
 // consecutive points, so that a densely populated tile (mesh singularities
 // concentrate points) is shared by several CTAs.  Work items are numbered in
 // ascending (tile, chunk) order; a tile's first item number is its slot, and
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
                                                  const int32_t* __restrict__ end, int ntiles,
                                                  int32_t* __restrict__ nonempty,
                                                  int32_t* __restrict__ near,
-                                                 int32_t* __restrict__ bcount) {
+                                                 int32_t* __restrict__ bcount, int chunk) {
   __shared__ int tmp[32];
   const int t = blockIdx.x * kT + threadIdx.x;
   int ne = 0, nr = 0, nch = 0, npt = 0;
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
     const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
     npt = end[t] - start[t];
     ne = npt > 0;
-    nch = (npt + kChunk - 1) / kChunk;
+    nch = (npt + chunk - 1) / chunk;
     nr = ne;
     for (int a = -1; a <= 1 && !nr; ++a)
       for (int b = -1; b <= 1 && !nr; ++b)
@@ -120,12 +120,12 @@ __global__ void __launch_bounds__(kT) k_compact(const int32_t* __restrict__ none
 
 int classify_blocks(int ntiles) { return (ntiles + kT - 1) / kT; }
 
-int64_t max_work_items(int ntiles, int64_t Q) { return ntiles + Q / kChunk + 1; }
+int64_t max_work_items(int ntiles, int64_t Q) { return ntiles + Q / kMinChunk + 1; }
 
 ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s) {
   const int nt = p->ntiles, nb = classify_blocks(nt);
   k_classify<<<nb, kT, 0, s>>>(p->grid, p->tile_start, p->tile_end, nt, p->tile_nonempty,
-                               p->tile_near, p->tile_bcount);
+                               p->tile_near, p->tile_bcount, p->chunk);
   k_compact<<<nb, kT, 0, s>>>(p->tile_nonempty, p->tile_near, nt, p->tile_bcount, nb,
                               p->tile_start, p->tile_end, p->tile_slot, p->tile_list,
                               p->tile_list_near, p->tile_counters);

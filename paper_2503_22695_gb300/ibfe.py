@@ -83,6 +83,9 @@ def _load():
         "ib_backward": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, vp, vp, vp, vp, vp,
                         vp, vp],
         "ib_plan_sync_status": [vp, vp],
+        "ib_plan_get_tuning": [vp, C.POINTER(i32)],
+        "ib_plan_set_tuning": [vp, C.POINTER(i32)],
+        "ib_plan_autotune": [vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, C.POINTER(i32)],
         "ib_plan_set_profiling": [vp, i32],
         "ib_batch_create": [i32, C.POINTER(_Instance), i32, vp, C.POINTER(vp)],
         "ib_batch_forward": [vp, vp],
@@ -341,6 +344,28 @@ def ib_backward(plan: Plan, mats, x: Pos, u=None, G=None, gG=None, gf=None, gU=N
                           _ptr(gG), _ptr(gf), _ptr(gU), _ptr(gx), _ptr(gu), _ptr(gp),
                           _stream()), "ib_backward")
     return gx, gu, gp
+
+
+def ib_plan_get_tuning(plan: Plan):
+    """[points per work item, force CTAs/SM, spreading CTAs/SM cap, interpolation cap]"""
+    t = (C.c_int32 * 4)()
+    _chk(_lib.ib_plan_get_tuning(plan.handle, t), "ib_plan_get_tuning")
+    return list(t)
+
+
+def ib_plan_set_tuning(plan: Plan, tuning):
+    t = (C.c_int32 * 4)(*[int(v) for v in tuning])
+    _chk(_lib.ib_plan_set_tuning(plan.handle, t), "ib_plan_set_tuning")
+
+
+def ib_plan_autotune(plan: Plan, mats, x: Pos, u):
+    """Time ib_forward over candidate tunings, keep the fastest, return it."""
+    _check(u, plan.dtype, plan.grid_shape(), "u")
+    arr, nm = _mats(mats)
+    t = (C.c_int32 * 4)()
+    _chk(_lib.ib_plan_autotune(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(u), _stream(),
+                               t), "ib_plan_autotune")
+    return list(t)
 
 
 def ib_plan_sync_status(plan: Plan) -> int:

@@ -48,5 +48,8 @@ def test_host_side_argument_checks(lib):
                "ib_fe_force_adj", "ib_forward"):
         assert getattr(lib, fn)(*([None] * 9)) == 1, fn
     assert lib.ib_backward(*([None] * 13)) == 1
+    assert lib.ib_plan_get_tuning(None, None) == 1
+    assert lib.ib_plan_set_tuning(None, None) == 1
+    assert lib.ib_plan_autotune(*([None] * 7)) == 1
     assert lib.ib_plan_destroy(None) == 1
     assert lib.ib_plan_sync_status(None, None) == 1

@@ -401,3 +401,35 @@ def test_differentiation_workload_full_size():
     assert loss.item() == pytest.approx(np.sum(Uo * Uo) + nf, rel=1e-5)
     assert rel_l2(np_(off.grad), gx * p.grid.h) <= 1e-4
     assert rel_l2(params.grad.numpy()[0, :8], gth[0, :8]) <= 1e-4
+
+
+def test_tuning_is_validated_and_changes_no_result():
+    """ib_plan_set_tuning range checks; every tuning, and the autotuner's
+    choice, give the same FP32 outputs bit for bit (exact integer spreading,
+    per-point interpolation) and FP64 outputs up to summation order."""
+    from paper_2503_22695_gb300 import ibfe
+    for name in ("shell128", "block64"):
+        c = case(name)
+        base = ibfe.ib_plan_get_tuning(c.plan)
+        assert base == [1024, 2, 8, 8]
+        for bad in ([256, 2, 8, 8], [1024, 0, 8, 8], [1024, 2, 9, 8], [1024, 2, 8, 0]):
+            with pytest.raises(ibfe.IBError):
+                ibfe.ib_plan_set_tuning(c.plan, bad)
+        ref = [np_(t) for t in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
+        for t in ([512, 1, 3, 2], [768, 3, 2, 3], [1024, 2, 8, 8]):
+            ibfe.ib_plan_set_tuning(c.plan, t)
+            assert ibfe.ib_plan_get_tuning(c.plan) == t
+            out = [np_(v) for v in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
+            for a, b in zip(out, ref):
+                if c.fp64:
+                    assert rel_l2(a, b) <= 1e-13
+                else:
+                    assert np.array_equal(a, b)
+        chosen = ibfe.ib_plan_autotune(c.plan, c.mats, c.pos, c.u)
+        assert chosen == ibfe.ib_plan_get_tuning(c.plan)
+        assert chosen[0] in (1024, 512) and chosen[1] in (1, 2, 3)
+        assert chosen[2] in (8, 3, 2) and chosen[3] in (8, 3, 2)
+        out = [np_(v) for v in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
+        for a, b in zip(out, ref):
+            assert rel_l2(a, b) <= 1e-13 if c.fp64 else np.array_equal(a, b)
+        ibfe.ib_plan_set_tuning(c.plan, base)
