@@ -70,6 +70,20 @@ double dphi(double r) {
 // a_fs I8 exp(b_fs I8^2) F (e_f(x)e_s + e_s(x)e_f), and Psi_4's isotropic part
 // carries "-1" so that Psi(I) = 0.
 // ---------------------------------------------------------------------------
+// parameters per model: NH {a, kappa}; Psi_2 {C1, af, bf, kappa};
+// Psi_4 {a, b, af, bf, as, bs, afs, bfs, kappa}; Psi_1 {G_T, G_L, E_L, kappa};
+// Psi_3 {C10, C01, af, bf, kappa}
+int n_params_of(int model) {
+  switch (model) {
+    case 0: return 2;
+    case 1: return 4;
+    case 2: return 9;
+    case 3: return 4;
+    case 4: return 5;
+  }
+  return 0;
+}
+
 template <class T>
 void stress_t(int model, const T* p, const T F[3][3], const double* ef, const double* es,
               T P[3][3], T& psi) {
@@ -98,7 +112,7 @@ void stress_t(int model, const T* p, const T F[3][3], const double* ef, const do
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) dev[i][j] = Jm23 * (F[i][j] - I1 / T(3.0) * FiT[i][j]);
 
-  int np = model == 0 ? 2 : (model == 1 ? 4 : 9);
+  int np = n_params_of(model);
   T kappa = p[np - 1];
   // volumetric stabilisation U(J) = kappa/2 (ln J)^2 (Section 3)
   psi = kappa / T(2.0) * lnJ * lnJ;
@@ -109,12 +123,13 @@ void stress_t(int model, const T* p, const T F[3][3], const double* ef, const do
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) P[i][j] = P[i][j] + coef * dev[i][j];
   };
-  // fibre term a_i/(2 b_i) (exp[b_i (I4i* - 1)^2] - 1), I4i* = max(I4i, 1)
-  auto add_fibre = [&](const double* e, T ai, T bi) {
+  // fibre term a_i/(2 b_i) (exp[b_i (I4i* - 1)^2] - 1), I4i* = max(I4i, 1);
+  // with clamp false the plain I4i - 1 (Psi_3)
+  auto add_fibre = [&](const double* e, T ai, T bi, bool clamp = true) {
     T Fe[3];
     for (int i = 0; i < 3; ++i) Fe[i] = F[i][0] * e[0] + F[i][1] * e[1] + F[i][2] * e[2];
     T I4 = Fe[0] * Fe[0] + Fe[1] * Fe[1] + Fe[2] * Fe[2];
-    T d = val(I4) > 1.0 ? I4 - T(1.0) : T(0.0);
+    T d = (!clamp || val(I4) > 1.0) ? I4 - T(1.0) : T(0.0);
     T ex = exp(bi * d * d);
     psi = psi + ai / (T(2.0) * bi) * (ex - T(1.0));
     T coef = T(2.0) * ai * d * ex;
@@ -129,6 +144,34 @@ void stress_t(int model, const T* p, const T F[3][3], const double* ef, const do
     psi = psi + p[0] * (I1bar - T(3.0));
     add_iso(T(2.0) * p[0]);
     add_fibre(ef, p[1], p[2]);
+  } else if (model == 3) {
+    // Psi_1 modified standard reinforcing: G_T/2 (I1bar - 3)
+    //   + (G_T - G_L)/2 (2 I4f - I5f - 1) + (E_L + G_T - 4 G_L)/8 (I4f - 1)^2,
+    // dI5f/dF = 2 (F e (x) C e + F C e (x) e)
+    T GT = p[0], GL = p[1], EL = p[2];
+    psi = psi + GT / T(2.0) * (I1bar - T(3.0));
+    add_iso(GT);
+    T Fe[3], Ce[3], FCe[3];
+    for (int i = 0; i < 3; ++i) Fe[i] = F[i][0] * ef[0] + F[i][1] * ef[1] + F[i][2] * ef[2];
+    for (int j = 0; j < 3; ++j) Ce[j] = F[0][j] * Fe[0] + F[1][j] * Fe[1] + F[2][j] * Fe[2];
+    for (int i = 0; i < 3; ++i) FCe[i] = F[i][0] * Ce[0] + F[i][1] * Ce[1] + F[i][2] * Ce[2];
+    T I4 = Fe[0] * Fe[0] + Fe[1] * Fe[1] + Fe[2] * Fe[2];
+    T I5 = Ce[0] * Ce[0] + Ce[1] * Ce[1] + Ce[2] * Ce[2];
+    T k4 = (EL + GT - T(4.0) * GL);
+    psi = psi + (GT - GL) / T(2.0) * (T(2.0) * I4 - I5 - T(1.0)) +
+          k4 / T(8.0) * (I4 - T(1.0)) * (I4 - T(1.0));
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        P[i][j] = P[i][j] +
+                  (GT - GL) * (T(2.0) * Fe[i] * T(ef[j]) - Fe[i] * Ce[j] - FCe[i] * T(ef[j])) +
+                  k4 / T(2.0) * (I4 - T(1.0)) * Fe[i] * T(ef[j]);
+  } else if (model == 4) {
+    // Psi_3 fibre-reinforced model 2: C10 (exp[C01 (I1bar - 3)] - 1) + fibre
+    // term without the tension-only clamp
+    T ex = exp(p[1] * (I1bar - T(3.0)));
+    psi = psi + p[0] * (ex - T(1.0));
+    add_iso(T(2.0) * p[0] * p[1] * ex);
+    add_fibre(ef, p[2], p[3], false);
   } else {  // Psi_4 Holzapfel-Ogden
     T ex = exp(p[1] * (I1bar - T(3.0)));
     psi = psi + p[0] / (T(2.0) * p[1]) * (ex - T(1.0));
@@ -150,7 +193,6 @@ void stress_t(int model, const T* p, const T F[3][3], const double* ef, const do
   }
 }
 
-int n_params_of(int model) { return model == 0 ? 2 : (model == 1 ? 4 : 9); }
 
 const double kUnitX[3] = {1.0, 0.0, 0.0};
 const double kUnitY[3] = {0.0, 1.0, 0.0};
@@ -291,7 +333,7 @@ double or_dphi(double r) { return dphi(r); }
 
 int or_stress(int32_t model, const double* params, const double* F, const double* ef,
               const double* es, double* P, double* psi) {
-  if (model < 0 || model > 2) return -1;
+  if (n_params_of(model) == 0) return -1;
   double Fm[3][3], Pm[3][3], ps;
   for (int i = 0; i < 9; ++i) Fm[i / 3][i % 3] = F[i];
   stress_t<double>(model, params, Fm, ef ? ef : kUnitX, es ? es : kUnitY, Pm, ps);
@@ -302,7 +344,7 @@ int or_stress(int32_t model, const double* params, const double* F, const double
 
 int or_stress_dir(int32_t model, const double* params, const double* F, const double* dF,
                   const double* ef, const double* es, double* dP) {
-  if (model < 0 || model > 2) return -1;
+  if (n_params_of(model) == 0) return -1;
   Dual Fm[3][3], Pm[3][3], ps, pp[9];
   for (int k = 0; k < n_params_of(model); ++k) pp[k] = Dual(params[k], 0.0);
   for (int i = 0; i < 9; ++i) Fm[i / 3][i % 3] = Dual(F[i], dF[i]);

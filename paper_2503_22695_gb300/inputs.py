@@ -26,12 +26,16 @@ import numpy as np
 NEO_HOOKEAN = 0   # Psi = a (I1bar - 3) + kappa/2 (ln J)^2        (Section 6.3)
 FIBRE1 = 1        # fibre-reinforced model 1, Psi_2               (Section 3)
 HO = 2            # Holzapfel-Ogden, Psi_4                        (Section 3)
+STD_REINF = 3     # modified standard reinforcing, Psi_1 (I4f, I5f) (Section 3)
+FIBRE2 = 4        # fibre-reinforced model 2, Psi_3               (Section 3)
 
-N_PARAMS = {NEO_HOOKEAN: 2, FIBRE1: 4, HO: 9}
+N_PARAMS = {NEO_HOOKEAN: 2, FIBRE1: 4, HO: 9, STD_REINF: 4, FIBRE2: 5}
 PARAM_NAMES = {
     NEO_HOOKEAN: ("a", "kappa"),
     FIBRE1: ("C1", "af", "bf", "kappa"),
     HO: ("a", "b", "af", "bf", "as", "bs", "afs", "bfs", "kappa"),
+    STD_REINF: ("GT", "GL", "EL", "kappa"),
+    FIBRE2: ("C10", "C01", "af", "bf", "kappa"),
 }
 
 # Holzapfel-Ogden defaults in kPa-scaled units: a, b, af, bf are the centres of
@@ -41,6 +45,12 @@ PARAM_NAMES = {
 HO_DEFAULT = (0.059, 8.02, 18.47, 16.03, 0.5562, 0.7746, 0.3905, 1.695, 100.0)
 # Mitral anterior leaflet (Section 6.3 table) in kPa: C1 = 17.4, af = 31.3, bf = 55.93.
 FIBRE1_LEAFLET = (17.4, 31.3, 55.93, 100.0)
+# Cook's membrane (Section 4 table) in its printed unit dyn/cm^2:
+# G_T = 8, G_L = 160, E_L = 1200, kappa_stab = 112.
+STD_REINF_COOK = (8.0, 160.0, 1200.0, 112.0)
+# Aortic valve leaflets (Section 6.2 table) in kPa: C10 = 1.21, C01 = 7.99,
+# af = 24.23, bf = 57.62, kappa = 100.
+FIBRE2_AV = (1.21, 7.99, 24.23, 57.62, 100.0)
 
 # VTK hexahedron corner order in the reference cube [-1,1]^3.
 HEX_CORNERS = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],

@@ -78,6 +78,8 @@ MODELS = [
     (I.NEO_HOOKEAN, (0.5, 100.0)),
     (I.FIBRE1, I.FIBRE1_LEAFLET),
     (I.HO, I.HO_DEFAULT),
+    (I.STD_REINF, I.STD_REINF_COOK),
+    (I.FIBRE2, I.FIBRE2_AV),
 ]
 
 
@@ -160,6 +162,55 @@ def test_ho_isotropic_limit_is_neo_hookean():
     P_nh, psi_nh = oracle.stress(I.NEO_HOOKEAN, (a / 2, kappa), F)
     np.testing.assert_allclose(P_ho, P_nh, rtol=1e-7, atol=1e-9)
     assert psi_ho == pytest.approx(psi_nh, rel=1e-7)
+
+
+def test_standard_reinforcing_isotropic_limit_is_neo_hookean():
+    # Psi_1 with G_L = G_T and E_L = 3 G_T has no fibre terms
+    # (G_T - G_L = 0, E_L + G_T - 4 G_L = 0): neo-Hookean with a = G_T/2.
+    rng = np.random.default_rng(31)
+    ef, es = _fibres(rng)
+    for _ in range(4):
+        F = _rand_F(rng)
+        P1, psi1 = oracle.stress(I.STD_REINF, (2.0, 2.0, 6.0, 50.0), F, ef, es)
+        P0, psi0 = oracle.stress(I.NEO_HOOKEAN, (1.0, 50.0), F, ef, es)
+        np.testing.assert_allclose(P1, P0, rtol=1e-13, atol=1e-13)
+        assert psi1 == pytest.approx(psi0, rel=1e-13, abs=1e-15)
+
+
+def test_standard_reinforcing_fibre_terms_by_invariants():
+    # Psi_1's anisotropic energy against I4 and I5 computed directly from C
+    rng = np.random.default_rng(32)
+    ef, es = _fibres(rng)
+    GT, GL, EL, kap = I.STD_REINF_COOK
+    for _ in range(4):
+        F = _rand_F(rng)
+        C = F.T @ F
+        I4, I5 = ef @ C @ ef, ef @ C @ C @ ef
+        J = np.linalg.det(F)
+        I1b = J ** (-2 / 3) * np.trace(C)
+        want = (GT / 2 * (I1b - 3) + (GT - GL) / 2 * (2 * I4 - I5 - 1) +
+                (EL + GT - 4 * GL) / 8 * (I4 - 1) ** 2 + kap / 2 * np.log(J) ** 2)
+        _, psi = oracle.stress(I.STD_REINF, I.STD_REINF_COOK, F, ef, es)
+        assert psi == pytest.approx(want, rel=1e-12)
+
+
+def test_fibre_model_2_limits():
+    # Psi_3: C10 (exp[C01 (I1bar - 3)] - 1) tends to C10 C01 (I1bar - 3) as
+    # C01 -> 0 (neo-Hookean with a = C10 C01), and its fibre term acts in
+    # compression too (no tension-only clamp, unlike Psi_2).
+    rng = np.random.default_rng(33)
+    ef, es = _fibres(rng)
+    F = _rand_F(rng)
+    P3, _ = oracle.stress(I.FIBRE2, (2e6, 1e-6, 0.0, 1.0, 50.0), F, ef, es)
+    P0, _ = oracle.stress(I.NEO_HOOKEAN, (2.0, 50.0), F, ef, es)
+    np.testing.assert_allclose(P3, P0, rtol=1e-4, atol=1e-6)
+    Fc = np.diag([0.95, 1.02, 1.03])            # fibre along x compressed
+    x = np.array([1.0, 0.0, 0.0])
+    Pc, _ = oracle.stress(I.FIBRE2, (1.0, 1.0, 3.0, 2.0, 0.0), Fc, x, np.array([0, 1.0, 0]))
+    Pn, _ = oracle.stress(I.FIBRE2, (1.0, 1.0, 0.0, 2.0, 0.0), Fc, x, np.array([0, 1.0, 0]))
+    d = 0.95 ** 2 - 1
+    assert Pc[0, 0] - Pn[0, 0] == pytest.approx(2 * 3.0 * d * np.exp(2.0 * d * d) * 0.95,
+                                                rel=1e-12)
 
 
 def test_fibres_carry_tension_only():
@@ -583,6 +634,10 @@ def test_material_table_conversions_golden():
     assert I.HO_DEFAULT[7] == pytest.approx(lv["bfs"])
     assert I.HO_DEFAULT[8] == pytest.approx(lv["kappa"])
     assert I.FIBRE1_LEAFLET[:3] == pytest.approx((mv["C1"], mv["af"], mv["bf"]))
+    cm = {r[1]: float(r[2]) for r in rows if r[0] == "CM"}   # kept in dyn/cm^2
+    assert I.STD_REINF_COOK == pytest.approx((cm["GT"], cm["GL"], cm["EL"], cm["kappa"]))
+    av = {r[1]: float(r[4]) for r in rows if r[0] == "AV"}
+    assert I.FIBRE2_AV[:4] == pytest.approx((av["C10"], av["C01"], av["af"], av["bf"]))
 
 
 def test_workload_shapes_and_jacobians():
