@@ -79,7 +79,12 @@ typedef enum {
 typedef enum {
   IB_NEO_HOOKEAN = 0, /* Psi = a (I1bar - 3) + kappa/2 (ln J)^2 (Section 6.3); params {a, kappa} */
   IB_FIBRE1 = 1,      /* Psi_2 of Section 3; params {C1, af, bf, kappa} */
-  IB_HO = 2           /* Psi_4 Holzapfel-Ogden (Section 3); params {a, b, af, bf, as, bs, afs, bfs, kappa} */
+  IB_HO = 2,          /* Psi_4 Holzapfel-Ogden (Section 3); params {a, b, af, bf, as, bs, afs, bfs, kappa} */
+  IB_STD_REINF = 3,   /* Psi_1 modified standard reinforcing model (Section 3), transversely
+                         isotropic in I4f and I5f; params {G_T, G_L, E_L, kappa} */
+  IB_FIBRE2 = 4       /* Psi_3 fibre-reinforced model 2 (Section 3): C10 (exp[C01 (I1bar - 3)] - 1)
+                         + af/(2 bf)(exp[bf (I4f - 1)^2] - 1), fibres also resist compression;
+                         params {C10, C01, af, bf, kappa} */
 } ib_model;
 
 /* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1, ln J (the

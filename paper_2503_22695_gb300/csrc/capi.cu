@@ -77,18 +77,10 @@ ib_status make_table(const ib_plan* p, const ib_material* mats, int32_t n_mats, 
   std::memset(&mt, 0, sizeof(mt));
   mt.n = n_mats;
   for (int m = 0; m < n_mats; ++m) {
-    const int model = mats[m].model;
-    const int np = model == IB_NEO_HOOKEAN ? 2 : (model == IB_FIBRE1 ? 4 : (model == IB_HO ? 9 : -1));
-    if (np < 0 || mats[m].n_params != np) return IB_ERR_INVALID_ARG;
-    for (int k = 0; k < np; ++k)
-      if (!std::isfinite(mats[m].params[k])) return IB_ERR_INVALID_ARG;
     // exponential laws divide by their rate constants in the energy
-    if (model == IB_FIBRE1 && mats[m].params[2] == 0.0) return IB_ERR_INVALID_ARG;
-    if (model == IB_HO)
-      for (int k : {1, 3, 5, 7})
-        if (mats[m].params[k] == 0.0) return IB_ERR_INVALID_ARG;
-    mt.model[m] = model;
-    for (int k = 0; k < np; ++k) mt.p[m][k] = mats[m].params[k];
+    if (!material_valid(mats[m])) return IB_ERR_INVALID_ARG;
+    mt.model[m] = mats[m].model;
+    for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
   }
   return IB_OK;
 }

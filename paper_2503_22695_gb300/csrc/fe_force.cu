@@ -83,12 +83,12 @@ __device__ __forceinline__ float fma_s(float a, float b, float c) { return fmaf(
 template <typename Real, typename S>
 struct Fibre {
   Real Fe[3];  // F e
-  S d;         // I4* - 1 = max(I4 - 1, 0)
+  S d;         // I4* - 1 = max(I4 - 1, 0), or I4 - 1 without the clamp
 };
 
 template <typename Real, typename S>
 __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S en1,
-                                          Fibre<Real, S>& f) {
+                                          Fibre<Real, S>& f, bool clamp = true) {
   Real He[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) He[i] = H[i][0] * e[0] + H[i][1] * e[1] + H[i][2] * e[2];
@@ -96,7 +96,7 @@ __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S
   S I4m1 = en1;
 #pragma unroll
   for (int i = 0; i < 3; ++i) I4m1 = fma_s(S(He[i]), S(Real(2) * e[i]) + S(He[i]), I4m1);
-  f.d = I4m1 > S(0) ? I4m1 : S(0);
+  f.d = (!clamp || I4m1 > S(0)) ? I4m1 : S(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
 }
@@ -198,7 +198,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real esn1r = Real(esn1), efesr = Real(efes);
 
   // material constants (unused entries of a model are never read by its branches)
-  const Real kap = Real(prm[model == 0 ? 1 : (model == 1 ? 3 : 8)]);
+  const Real kap = Real(prm[model == 0 ? 1 : (model == 2 ? 8 : (model == 4 ? 4 : 3))]);
   const Real pa = Real(prm[0]), pb = Real(prm[1]);
   const Real paf = Real(prm[model == 1 ? 1 : 2]), pbf = Real(prm[model == 1 ? 2 : 3]);
   const Real pas = Real(prm[4]), pbs = Real(prm[5]), pafs = Real(prm[6]), pbfs = Real(prm[7]);
@@ -293,10 +293,15 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 
     // ---- constitutive law -----------------------------------------------------
     Real ciso;
-    Real eiso = Real(1);  // HO: exp(b (I1bar - 3))
+    Real eiso = Real(1);  // Psi_4: exp(b (I1bar - 3)); Psi_3: exp(C01 (I1bar - 3))
     if (model == 2) {
       eiso = exp(pb * Ibm3);
       ciso = pa * eiso;
+    } else if (model == 4) {
+      eiso = exp(pb * Ibm3);
+      ciso = Real(2) * pa * pb * eiso;
+    } else if (model == 3) {
+      ciso = pa;  // G_T
     } else {
       ciso = Real(2) * pa;
     }
@@ -308,11 +313,33 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     Real d1 = Real(0), cf1 = Real(0), ef1 = Real(1), cf2 = Real(0), ef2 = Real(1);
     const bool has_f = model != 0;
     const bool has_s = model == 2;
+    // Psi_1 (model 3): the I4f term (E_L + G_T - 4 G_L)/2 (I4f - 1) F e (x) e,
+    // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
+    // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
+    // with C e = e + w, w = H e + H^T e + H^T H e (no cancellation for small H)
+    const Real k4 = model == 3 ? Real(0.5) * (Real(prm[2]) + pa - Real(4) * pb) : Real(0);
+    const Real c5 = model == 3 ? pa - pb : Real(0);
+    Real w5[3] = {Real(0), Real(0), Real(0)}, Fw5[3] = {Real(0), Real(0), Real(0)};
     if (has_f) {
-      fibre_kin<Real, S>(H, ef, efn1, f1);
+      fibre_kin<Real, S>(H, ef, efn1, f1, model == 1 || model == 2);
       d1 = Real(f1.d);
-      ef1 = exp(pbf * d1 * d1);
-      cf1 = Real(2) * paf * d1 * ef1;
+      if (model == 3) {
+        cf1 = k4 * d1;
+        Real He[3], HtHe[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) He[i] = f1.Fe[i] - ef[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          HtHe[j] = H[0][j] * He[0] + H[1][j] * He[1] + H[2][j] * He[2];
+          w5[j] = He[j] + (H[0][j] * ef[0] + H[1][j] * ef[1] + H[2][j] * ef[2]) + HtHe[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          Fw5[i] = w5[i] + H[i][0] * w5[0] + H[i][1] * w5[1] + H[i][2] * w5[2];
+      } else {
+        ef1 = exp(pbf * d1 * d1);
+        cf1 = Real(2) * paf * d1 * ef1;
+      }
     }
     // Sheet family and the fibre-sheet coupling (HO only) in Real, with the
     // same cancellation-free formulas.
@@ -340,8 +367,13 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     if (kEnergy) {
       double psi = 0.5 * double(kap) * double(lnJs) * double(lnJs);
       if (model == 0 || model == 1) psi += prm[0] * double(Ibm3);
-      else psi += prm[0] / (2.0 * prm[1]) * expm1(prm[1] * double(Ibm3));
-      if (has_f) {
+      else if (model == 2) psi += prm[0] / (2.0 * prm[1]) * expm1(prm[1] * double(Ibm3));
+      else if (model == 3) psi += 0.5 * prm[0] * double(Ibm3);
+      else psi += prm[0] * expm1(prm[1] * double(Ibm3));
+      if (model == 3) {
+        const double ww = double(w5[0]) * w5[0] + double(w5[1]) * w5[1] + double(w5[2]) * w5[2];
+        psi += 0.5 * double(c5) * (double(efn1) - ww) + 0.25 * double(k4) * double(f1.d) * double(f1.d);
+      } else if (has_f) {
         const double af = prm[model == 1 ? 1 : 2], bf = prm[model == 1 ? 2 : 3];
         psi += af / (2.0 * bf) * expm1(bf * double(f1.d) * double(f1.d));
       }
@@ -365,6 +397,12 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int j = 0; j < 3; ++j) P[i][j] += c * f1.Fe[i] * ef[j];
+      }
+      if (model == 3) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) P[i][j] -= c5 * (f1.Fe[i] * w5[j] + Fw5[i] * ef[j]);
       }
       if (has_s) {
         const Real c = Real(cf2), k8 = Real(c8);
@@ -419,7 +457,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       const Real I1 = Real(3) + I1m3;
       const Real dbeta = Jm23 * (dI1 - Real(2.0 / 3.0) * I1 * dl);
       Real dciso = Real(0);
-      if (model == 2) dciso = ciso * Real(prm[1]) * dbeta;
+      if (model == 2 || model == 4) dciso = ciso * pb * dbeta;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -436,13 +474,44 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         for (int i = 0; i < 3; ++i) dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
         dI4f = Real(2) * (f1.Fe[0] * dFe[0] + f1.Fe[1] * dFe[1] + f1.Fe[2] * dFe[2]);
         const Real dc =
-            d1 > Real(0) ? Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f
-                         : Real(0);
+            model == 3 ? k4 * dI4f
+                       : ((model == 4 || d1 > Real(0))
+                              ? Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f
+                              : Real(0));
         const Real c = Real(cf1);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int j = 0; j < 3; ++j) P[i][j] += (dc * f1.Fe[i] + c * dFe[i]) * ef[j];
+      }
+      // Psi_1's I5f term: d[-(G_T - G_L)(Fe (x) w + Fw (x) e)] with
+      // dw = dF e + dF^T e + dF^T H e + H^T dF e
+      Real X5 = Real(0);  // (Fe (x) w + Fw (x) e) : dF
+      if (model == 3) {
+        Real dFe[3], dFw[3], dw[3], Fdw[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
+          dFw[i] = dF[i][0] * w5[0] + dF[i][1] * w5[1] + dF[i][2] * w5[2];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          Real t = dFe[j];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            t += dF[i][j] * f1.Fe[i] + H[i][j] * dFe[i];  // dF^T (e + He) + H^T dF e
+          dw[j] = t;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          Fdw[i] = dw[i] + H[i][0] * dw[0] + H[i][1] * dw[1] + H[i][2] * dw[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            P[i][j] -= c5 * (dFe[i] * w5[j] + f1.Fe[i] * dw[j] + dFw[i] * ef[j] + Fdw[i] * ef[j]);
+        X5 = f1.Fe[0] * dFw[0] + f1.Fe[1] * dFw[1] + f1.Fe[2] * dFw[2] + Fw5[0] * dFe[0] +
+             Fw5[1] * dFe[1] + Fw5[2] * dFe[2];
       }
       if (has_s) {
         Real dFs[3], dFf[3];
@@ -482,6 +551,18 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
           gp[1] -= w * d1 * ef1 * dI4f;
           gp[2] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
           gp[3] -= w * vol;
+        } else if (model == 3) {  // {G_T, G_L, E_L, kappa}; (Fe (x) e) : dF = dI4f / 2
+          const Real y4 = Real(0.5) * dI4f;
+          gp[0] -= w * (DdF - X5 + Real(0.5) * d1 * y4);
+          gp[1] -= w * (X5 - Real(2) * d1 * y4);
+          gp[2] -= w * (Real(0.5) * d1 * y4);
+          gp[3] -= w * vol;
+        } else if (model == 4) {  // {C10, C01, af, bf, kappa}
+          gp[0] -= w * Real(2) * pb * eiso * DdF;
+          gp[1] -= w * Real(2) * pa * eiso * (Real(1) + pb * Ibm3) * DdF;
+          gp[2] -= w * d1 * ef1 * dI4f;
+          gp[3] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
+          gp[4] -= w * vol;
         } else {
           gp[0] -= w * eiso * DdF;
           gp[1] -= w * pa * Ibm3 * eiso * DdF;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "ibfe.h"
 
 namespace ibfe {
@@ -42,6 +44,33 @@ struct PosDev {
 };
 
 struct ib_plan_impl;
+
+// Parameters of each ib_model, -1 for an unknown model.
+inline int model_n_params(int model) {
+  switch (model) {
+    case IB_NEO_HOOKEAN: return 2;
+    case IB_FIBRE1: return 4;
+    case IB_HO: return 9;
+    case IB_STD_REINF: return 4;
+    case IB_FIBRE2: return 5;
+    default: return -1;
+  }
+}
+
+// Host check of one material: known model, matching parameter count, finite
+// parameters and nonzero rate constants where the energy divides by them.
+inline bool material_valid(const ib_material& m) {
+  const int np = model_n_params(m.model);
+  if (np < 0 || m.n_params != np) return false;
+  for (int k = 0; k < np; ++k)
+    if (!std::isfinite(m.params[k])) return false;
+  if (m.model == IB_FIBRE1 && m.params[2] == 0.0) return false;
+  if (m.model == IB_FIBRE2 && m.params[3] == 0.0) return false;
+  if (m.model == IB_HO)
+    for (int k : {1, 3, 5, 7})
+      if (m.params[k] == 0.0) return false;
+  return true;
+}
 
 }  // namespace ibfe
 

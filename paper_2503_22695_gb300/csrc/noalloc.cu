@@ -38,7 +38,7 @@ __device__ __forceinline__ T det3_na(const T A[3][3]) {
 }
 
 // Strain energy of one element, sum over its 8 Gauss points of Psi w_q j0,
-// for the laws of Section 3 (Psi_2, Psi_4) and Section 6.3 (neo-Hookean),
+// for the laws of Section 3 (Psi_1 to Psi_4) and Section 6.3 (neo-Hookean),
 // with the same cancellation-free invariants as the force kernel.  Writes NaN
 // for an element with an out-of-range node or material index.
 __global__ void __launch_bounds__(128) k_energy_noalloc(const int32_t* __restrict__ conn,
@@ -124,22 +124,41 @@ __global__ void __launch_bounds__(128) k_energy_noalloc(const int32_t* __restric
     const double lnJ = log1p(Jm1);
     const double Jm23m1 = expm1(-2.0 / 3.0 * lnJ);
     const double Ibm3 = (1.0 + Jm23m1) * (2.0 * tr + HH) + 3.0 * Jm23m1;
-    auto fibre_d = [&](const float* v) {
+    auto fibre_d = [&](const float* v, bool clamp) {
       double I4m1 = double(v[0]) * v[0] + double(v[1]) * v[1] + (double(v[2]) * v[2] - 1.0);
       for (int i = 0; i < 3; ++i) {
         const double Hv = double(H[i][0]) * v[0] + double(H[i][1]) * v[1] + double(H[i][2]) * v[2];
         I4m1 += 2.0 * double(v[i]) * Hv + Hv * Hv;
       }
-      return I4m1 > 0.0 ? I4m1 : 0.0;
+      return (!clamp || I4m1 > 0.0) ? I4m1 : 0.0;
     };
     double psi;
     if (model == IB_NEO_HOOKEAN) {
       psi = p[0] * Ibm3 + 0.5 * p[1] * lnJ * lnJ;
     } else if (model == IB_FIBRE1) {
-      const double d = fibre_d(ef);
+      const double d = fibre_d(ef, true);
       psi = p[0] * Ibm3 + p[1] / (2.0 * p[2]) * expm1(p[2] * d * d) + 0.5 * p[3] * lnJ * lnJ;
+    } else if (model == IB_FIBRE2) {
+      const double d = fibre_d(ef, false);
+      psi = p[0] * expm1(p[1] * Ibm3) + p[2] / (2.0 * p[3]) * expm1(p[3] * d * d) +
+            0.5 * p[4] * lnJ * lnJ;
+    } else if (model == IB_STD_REINF) {
+      // 2 I4f - I5f - 1 = |e|^2 - 1 - |w|^2 with w = (C - I) e
+      //                 = H e + H^T e + H^T H e
+      const double d = fibre_d(ef, false);
+      double He[3], ww = 0.0;
+      for (int i = 0; i < 3; ++i)
+        He[i] = double(H[i][0]) * ef[0] + double(H[i][1]) * ef[1] + double(H[i][2]) * ef[2];
+      for (int j = 0; j < 3; ++j) {
+        double w = He[j];
+        for (int i = 0; i < 3; ++i) w += double(H[i][j]) * (double(ef[i]) + He[i]);
+        ww += w * w;
+      }
+      const double en1 = double(ef[0]) * ef[0] + double(ef[1]) * ef[1] + (double(ef[2]) * ef[2] - 1.0);
+      psi = 0.5 * p[0] * Ibm3 + 0.5 * (p[0] - p[1]) * (en1 - ww) +
+            0.125 * (p[2] + p[0] - 4.0 * p[1]) * d * d + 0.5 * p[3] * lnJ * lnJ;
     } else {
-      const double df = fibre_d(ef), ds = fibre_d(es);
+      const double df = fibre_d(ef, true), ds = fibre_d(es, true);
       double I8 = double(ef[0]) * es[0] + double(ef[1]) * es[1] + double(ef[2]) * es[2];
       for (int i = 0; i < 3; ++i) {
         const double Hf = double(H[i][0]) * ef[0] + double(H[i][1]) * ef[1] + double(H[i][2]) * ef[2];
@@ -210,15 +229,9 @@ extern "C" ib_status ib_fe_energy_noalloc(const ib_mesh* mesh, const ib_material
     for (int k = 0; k < 9; ++k) mt.p[m][k] = 0.0;
   }
   for (int m = 0; m < n_mats; ++m) {
-    const int model = mats[m].model;
-    const int np = model == IB_NEO_HOOKEAN ? 2 : (model == IB_FIBRE1 ? 4 : (model == IB_HO ? 9 : -1));
-    if (np < 0 || mats[m].n_params != np) return IB_ERR_INVALID_ARG;
-    if (model == IB_FIBRE1 && mats[m].params[2] == 0.0) return IB_ERR_INVALID_ARG;
-    if (model == IB_HO)
-      for (int k : {1, 3, 5, 7})
-        if (mats[m].params[k] == 0.0) return IB_ERR_INVALID_ARG;
-    mt.model[m] = model;
-    for (int k = 0; k < np; ++k) mt.p[m][k] = mats[m].params[k];
+    if (!material_valid(mats[m])) return IB_ERR_INVALID_ARG;
+    mt.model[m] = mats[m].model;
+    for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
   }
   // once per device, with that device current: the device address of the
   // scratch array (host code only sees a host-side stand-in for the symbol)

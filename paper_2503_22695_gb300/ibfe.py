@@ -26,12 +26,12 @@ LIB_PATH = os.path.join(_HERE, "libibfe.so")
 
 IB_OK, IB_ERR_INVALID_ARG, IB_ERR_CUDA, IB_ERR_NONFINITE = 0, 1, 2, 3
 IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 7
-IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO = 0, 1, 2
+IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO, IB_STD_REINF, IB_FIBRE2 = 0, 1, 2, 3, 4
 IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
 IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
 IB_MAX_MATERIALS = 8
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
-N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9}
+N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9, IB_STD_REINF: 4, IB_FIBRE2: 5}
 
 
 class IBError(RuntimeError):

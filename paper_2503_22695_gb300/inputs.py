@@ -69,6 +69,7 @@ class Grid:
 class Material:
     model: int
     params: tuple
+    active: float = 0.0   # active fibre tension T_a at the current time (Section 6.1)
 
 
 @dataclasses.dataclass
@@ -424,6 +425,31 @@ def shell_sheets_problem(seed: int = 3000, n: int = 256, dims=(160, 100, 10),
     x = smooth_deformation(X, rng)
     mats = [Material(HO, HO_DEFAULT), Material(FIBRE1, FIBRE1_LEAFLET)]
     return _finish("shell+sheets", grid, conn, X, fib, mat_id, mats, x, u_modes, rng)
+
+
+def material_mix_problem(seed: int = 6000, n: int = 64, dims=(30, 20, 4), models=None,
+                         fp64: bool = False, twist=0.3, amp=0.015, axial=0.02) -> Problem:
+    """The shell with elements cycling through several laws (mat_id = e mod k).
+
+    `models` lists the ib_model codes (default: all five laws of Section 3 and
+    Section 6.3), each with its standard parameter set: neo-Hookean a = 0.5,
+    kappa = 100; Psi_2 leaflet; Psi_4 HO; Psi_1 Cook's membrane constants;
+    Psi_3 aortic-valve constants.  The smooth twist stretches some fibres and
+    shortens others, so the tension-only clamp of Psi_2/Psi_4 and the
+    two-sided fibre term of Psi_3 are both exercised.
+    """
+    params = {NEO_HOOKEAN: (0.5, 100.0), FIBRE1: FIBRE1_LEAFLET, HO: HO_DEFAULT,
+              STD_REINF: STD_REINF_COOK, FIBRE2: FIBRE2_AV}
+    models = list(params) if models is None else list(models)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    grid = Grid((n, n, n), 1.0 / n)
+    conn, X, fib = ellipsoid_shell(*dims)
+    if not fp64:
+        X = X.astype(np.float32).astype(np.float64)
+    x = smooth_deformation(X, rng, twist=twist, amp=amp, axial=axial)
+    mats = [Material(m, tuple(params[m])) for m in models]
+    mat_id = np.arange(conn.shape[1]) % len(models)
+    return _finish("mix", grid, conn, X, fib, mat_id, mats, x, 4, rng, fp64)
 
 
 def batch_problems(seed: int = 5000, count: int = 48, sizes=(32, 64, 96, 128),
