@@ -58,6 +58,8 @@ def lib():
     with _lock:
         if _lib is None:
             L = C.CDLL(build())
+            L.or_active_tension.restype = C.c_double
+            L.or_active_tension.argtypes = [C.c_double]
             L.or_phi.restype = C.c_double
             L.or_phi.argtypes = [C.c_double]
             L.or_dphi.restype = C.c_double
@@ -101,10 +103,11 @@ class Model:
         self.materials = list(materials)
         nm = max(1, len(self.materials))
         self._models = np.zeros(nm, dtype=np.int32)
-        self._params = np.zeros((nm, 9), dtype=np.float64)
+        self._params = np.zeros((nm, 10), dtype=np.float64)
         for i, m in enumerate(self.materials):
             self._models[i] = m.model
             self._params[i, :len(m.params)] = m.params
+            self._params[i, 9] = getattr(m, "active", 0.0)
         self._mats = _Mats(len(self.materials), _p(self._models), _p(self._params))
 
     # -- positions -----------------------------------------------------------
@@ -142,7 +145,7 @@ class Model:
     def fe_force_adj(self, x, v):
         x, v = _f64(x), _f64(v)
         Hv = np.empty((3, self.N))
-        gp = np.zeros((len(self.materials), 9))
+        gp = np.zeros((len(self.materials), 10))
         self._chk(lib().or_fe_force_adj(C.byref(self._mesh), C.byref(self._mats), _p(x), _p(v),
                                         _p(Hv), _p(gp)), "fe_force_adj")
         return Hv, gp
@@ -241,6 +244,11 @@ class Model:
         return int(r)
 
 
+def active_tension(t: float) -> float:
+    """T_a(t) of Section 6.1 in Pa (period 0.8 s)."""
+    return lib().or_active_tension(float(t))
+
+
 def phi(r: float) -> float:
     return lib().or_phi(float(r))
 
@@ -249,10 +257,16 @@ def dphi(r: float) -> float:
     return lib().or_dphi(float(r))
 
 
-def stress(model: int, params, F, ef=(1, 0, 0), es=(0, 1, 0)):
-    """(P, Psi) for one deformation gradient F (3x3)."""
-    p = np.zeros(9)
+def _row(params, Ta):
+    p = np.zeros(10)
     p[:len(params)] = params
+    p[9] = Ta
+    return p
+
+
+def stress(model: int, params, F, ef=(1, 0, 0), es=(0, 1, 0), Ta=0.0):
+    """(P, Psi) for one deformation gradient F (3x3); Ta is the active tension."""
+    p = _row(params, Ta)
     F = _f64(np.asarray(F).reshape(9))
     ef, es = _f64(ef), _f64(es)
     P = np.empty(9)
@@ -263,9 +277,8 @@ def stress(model: int, params, F, ef=(1, 0, 0), es=(0, 1, 0)):
     return P.reshape(3, 3), psi.value
 
 
-def stress_dir(model: int, params, F, dF, ef=(1, 0, 0), es=(0, 1, 0)):
-    p = np.zeros(9)
-    p[:len(params)] = params
+def stress_dir(model: int, params, F, dF, ef=(1, 0, 0), es=(0, 1, 0), Ta=0.0):
+    p = _row(params, Ta)
     F = _f64(np.asarray(F).reshape(9))
     dF = _f64(np.asarray(dF).reshape(9))
     ef, es = _f64(ef), _f64(es)

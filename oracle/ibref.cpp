@@ -33,10 +33,12 @@ inline Dual operator/(Dual a, Dual b) {
 }
 inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, e * a.d); }
 inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual sqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
 inline double val(double a) { return a; }
 inline double val(const Dual& a) { return a.v; }
 using std::exp;
 using std::log;
+using std::sqrt;
 
 // ---------------------------------------------------------------------------
 // 4-point regularised delta kernel (Peskin 2002, cited in Section 2; the
@@ -72,7 +74,10 @@ double dphi(double r) {
 // ---------------------------------------------------------------------------
 // parameters per model: NH {a, kappa}; Psi_2 {C1, af, bf, kappa};
 // Psi_4 {a, b, af, bf, as, bs, afs, bfs, kappa}; Psi_1 {G_T, G_L, E_L, kappa};
-// Psi_3 {C10, C01, af, bf, kappa}
+// Psi_3 {C10, C01, af, bf, kappa}.  A parameter row holds kRow doubles: the
+// law's parameters first, the active tension T_a (Section 6.1) in the last.
+constexpr int kRow = 10;
+constexpr int kTa = 9;
 int n_params_of(int model) {
   switch (model) {
     case 0: return 2;
@@ -190,6 +195,25 @@ void stress_t(int model, const T* p, const T F[3][3], const double* ef, const do
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
         P[i][j] = P[i][j] + coef * (Fef[i] * T(es[j]) + Fes[i] * T(ef[j]));
+  }
+
+  // Active stress, Section 6.1: P^a = F S_a with S_a = T(t, I4f) e_f (x) e_f,
+  // T = T_a (1 + 4.9 (sqrt(I4f) - 1)); T_a = p[kTa] is the value of the
+  // waveform at the current time.  T depends on F only through I4f, so P^a
+  // = 2 dW_a/dI4f F e_f (x) e_f is the derivative of the potential
+  //   W_a = T_a/2 [(1 - 4.9)(I4f - 1) + 4.9 (2/3)(I4f^(3/2) - 1)],
+  // which is added to the energy.  No tension-only clamp; T_a = 0 adds zeros.
+  {
+    T Ta = p[kTa];
+    T Fe[3];
+    for (int i = 0; i < 3; ++i) Fe[i] = F[i][0] * ef[0] + F[i][1] * ef[1] + F[i][2] * ef[2];
+    T I4 = Fe[0] * Fe[0] + Fe[1] * Fe[1] + Fe[2] * Fe[2];
+    T s = sqrt(I4);
+    T tension = Ta * (T(1.0) + T(4.9) * (s - T(1.0)));
+    psi = psi + Ta / T(2.0) *
+                    (T(1.0 - 4.9) * (I4 - T(1.0)) + T(4.9 * 2.0 / 3.0) * (I4 * s - T(1.0)));
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) P[i][j] = P[i][j] + tension * Fe[i] * T(ef[j]);
   }
 }
 
@@ -328,6 +352,19 @@ void point_of(const GaussPt& gp, const double xe[8][3], double chi[3]) {
 
 extern "C" {
 
+// Active tension waveform T_a(t) of Section 6.1, in Pa: zero before 0.5 s, a
+// Gaussian-shaped rise 84260 (1 - exp(-(t - 0.5)^2 / 0.005)) to 0.65 s, the
+// mirrored fall 84260 (1 - exp(-(0.8 - t)^2 / 0.005)) to 0.8 s; repeated with
+// the 0.8 s period of the cardiac cycle.
+double or_active_tension(double t) {
+  const double period = 0.8, peak = 84260.0, width = 0.005;
+  double tc = std::fmod(t, period);
+  if (tc < 0.0) tc += period;
+  if (tc < 0.5) return 0.0;
+  const double r = tc < 0.65 ? tc - 0.5 : period - tc;
+  return peak * (1.0 - std::exp(-r * r / width));
+}
+
 double or_phi(double r) { return phi(r); }
 double or_dphi(double r) { return dphi(r); }
 
@@ -345,8 +382,8 @@ int or_stress(int32_t model, const double* params, const double* F, const double
 int or_stress_dir(int32_t model, const double* params, const double* F, const double* dF,
                   const double* ef, const double* es, double* dP) {
   if (n_params_of(model) == 0) return -1;
-  Dual Fm[3][3], Pm[3][3], ps, pp[9];
-  for (int k = 0; k < n_params_of(model); ++k) pp[k] = Dual(params[k], 0.0);
+  Dual Fm[3][3], Pm[3][3], ps, pp[kRow];
+  for (int k = 0; k < kRow; ++k) pp[k] = Dual(params[k], 0.0);
   for (int i = 0; i < 9; ++i) Fm[i / 3][i % 3] = Dual(F[i], dF[i]);
   stress_t<Dual>(model, pp, Fm, ef ? ef : kUnitX, es ? es : kUnitY, Pm, ps);
   for (int i = 0; i < 9; ++i) dP[i] = Pm[i / 3][i % 3].d;
@@ -407,7 +444,7 @@ int or_fe_force(const or_mesh* m, const or_mats* mats, const double* x, double* 
   for (int e = 0; e < E; ++e) {
     int mid = mat_of(m, e);
     if (mid < 0 || mid >= mats->n_mats) return -1;
-    const double* p = mats->params + 9 * mid;
+    const double* p = mats->params + kRow * mid;
     int model = mats->model[mid];
     double Xe[8][3], xe[8][3], ef[3], es[3];
     gather(m, m->X, e, Xe);
@@ -443,11 +480,11 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
   if (!check_mesh(m) || !mats || mats->n_mats <= 0) return -1;
   int64_t E = m->n_elems, N = m->n_nodes;
   std::memset(Hv, 0, sizeof(double) * 3 * N);
-  if (gparams) std::memset(gparams, 0, sizeof(double) * 9 * mats->n_mats);
+  if (gparams) std::memset(gparams, 0, sizeof(double) * kRow * mats->n_mats);
   for (int e = 0; e < E; ++e) {
     int mid = mat_of(m, e);
     if (mid < 0 || mid >= mats->n_mats) return -1;
-    const double* p = mats->params + 9 * mid;
+    const double* p = mats->params + kRow * mid;
     int model = mats->model[mid];
     int np = n_params_of(model);
     double Xe[8][3], xe[8][3], ve[8][3], ef[3], es[3];
@@ -466,8 +503,8 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
             dF[i][j] += ve[a][i] * gp.dNdX[a][j];
           }
       // directional derivative of P along dF
-      Dual Fd[3][3], Pd[3][3], psid, pd[9];
-      for (int k = 0; k < np; ++k) pd[k] = Dual(p[k], 0.0);
+      Dual Fd[3][3], Pd[3][3], psid, pd[kRow];
+      for (int k = 0; k < kRow; ++k) pd[k] = Dual(p[k], 0.0);
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) Fd[i][j] = Dual(F[i][j], dF[i][j]);
       stress_t<Dual>(model, pd, Fd, ef, es, Pd, psid);
@@ -480,15 +517,16 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
         }
       }
       if (gparams) {
-        for (int k = 0; k < np; ++k) {
-          for (int kk = 0; kk < np; ++kk) pd[kk] = Dual(p[kk], kk == k ? 1.0 : 0.0);
+        for (int k = 0; k < kRow; ++k) {
+          if (k >= np && k != kTa) continue;  // the law's parameters and T_a
+          for (int kk = 0; kk < kRow; ++kk) pd[kk] = Dual(p[kk], kk == k ? 1.0 : 0.0);
           for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) Fd[i][j] = Dual(F[i][j], 0.0);
           stress_t<Dual>(model, pd, Fd, ef, es, Pd, psid);
           double s = 0.0;
           for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) s += Pd[i][j].d * dF[i][j];
-          gparams[9 * mid + k] -= s * gp.wj0;
+          gparams[kRow * mid + k] -= s * gp.wj0;
         }
       }
     }

@@ -9,8 +9,10 @@
  *   - interpolation U = I(X, u)   Section 2 Eq. (2); Section 4.4 (U^IB, then the
  *                                 L2 projection onto the FE space, lumped)
  *   - nodal force F_i = -sum_q P(X_q):grad phi_i(X_q) w_q     Section 4.4
- *   - stresses P = dPsi/dF for neo-Hookean (Section 6.3), fibre-reinforced
- *     model 1 (Section 3, Psi_2) and Holzapfel-Ogden (Section 3, Psi_4)
+ *   - stresses P = dPsi/dF for neo-Hookean (Section 6.3), the modified
+ *     standard reinforcing model (Psi_1), fibre-reinforced models 1 and 2
+ *     (Psi_2, Psi_3) and Holzapfel-Ogden (Psi_4) of Section 3, plus the
+ *     active fibre stress of Section 6.1 (T_a given per material)
  *   - the 4-point regularised delta (Peskin, cited in Section 2)
  *   - adjoints (vector-Jacobian products) of the three operators.
  *
@@ -26,8 +28,10 @@
  *            cell + offset storage).  Cells are not wrapped; the grid index
  *            is taken modulo n.
  *   materials params per model: NH {a, kappa}; FIBRE1 {C1, af, bf, kappa};
- *            HO {a, b, af, bf, as, bs, afs, bfs, kappa}; mat_id [E] selects a
- *            row of the material table (stride 9 doubles).
+ *            HO {a, b, af, bf, as, bs, afs, bfs, kappa}; STD_REINF {G_T, G_L,
+ *            E_L, kappa}; FIBRE2 {C10, C01, af, bf, kappa}; the active tension
+ *            T_a in the row's last entry; mat_id [E] selects a row of the
+ *            material table (stride 10 doubles).
  *   mass     lumped: m_a = sum_{e,q} N_a(xi_q) w_q j0 (row-sum of the
  *            consistent mass; equal to the nodal-rule weight of Section 4.4).
  *
@@ -58,14 +62,18 @@ typedef struct {
 typedef struct {
   int32_t n_mats;
   const int32_t* model;  /* [n_mats] */
-  const double* params;  /* [n_mats][9] */
+  const double* params;  /* [n_mats][10]: the law's parameters, then T_a at [9] */
 } or_mats;
+
+/* Active tension waveform T_a(t) of Section 6.1 in Pa (period 0.8 s). */
+double or_active_tension(double t);
 
 /* 1-D kernel phi(r) and dphi/dr, r in units of h. */
 double or_phi(double r);
 double or_dphi(double r);
 
-/* Stress P (row-major 3x3, P[3*i+j]) and energy density Psi for one F. */
+/* Stress P (row-major 3x3, P[3*i+j]) and energy density Psi for one F;
+ * params holds 10 doubles (the law's parameters, then T_a at [9]). */
 int or_stress(int32_t model, const double* params, const double* F, const double* ef,
               const double* es, double* P, double* psi);
 /* Directional derivative dP = (d P / d F)[dF]. */
@@ -82,7 +90,8 @@ int or_lumped_mass(const or_mesh* m, double* mass);
 int or_fe_force(const or_mesh* m, const or_mats* mats, const double* x, double* G,
                 double* energy);
 
-/* Hv = (dG/dx) v  [3][N] and gparams[k] = v . dG/dtheta_k, [n_mats][9]. */
+/* Hv = (dG/dx) v  [3][N] and gparams[k] = v . dG/dtheta_k, [n_mats][10]
+ * (the law's parameters, then T_a at [9]). */
 int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
                     const double* v, double* Hv, double* gparams);
 

@@ -257,6 +257,133 @@ def tiny_mesh(model=I.HO, params=I.HO_DEFAULT, n=16, blocks=(2, 2, 1), seed=7, n
     return p
 
 
+# ---------------------------------------------------------------------------
+# active fibre stress (Section 6.1)
+# ---------------------------------------------------------------------------
+
+ACTIVE = [(I.HO, I.HO_DEFAULT, 60.0), (I.NEO_HOOKEAN, (0.5, 100.0), 30.0),
+          (I.FIBRE2, I.FIBRE2_AV, 45.0)]
+
+
+@pytest.mark.parametrize("model,params,Ta", ACTIVE)
+def test_active_stress_is_energy_derivative(model, params, Ta):
+    """P^a = F S_a has the potential W_a(I4f) at fixed t, so P = dPsi/dF holds
+    with the active term included (checked by central differences)."""
+    rng = np.random.default_rng(70 + model)
+    checked = 0
+    for _ in range(30):
+        F = _rand_F(rng)
+        ef, es = _fibres(rng)
+        I4 = [np.sum((F @ e) ** 2) for e in (ef, es)]
+        if min(abs(v - 1) for v in I4) < 1e-3:
+            continue
+        P, _ = oracle.stress(model, params, F, ef, es, Ta=Ta)
+        eps = 1e-6
+        fd = np.zeros((3, 3))
+        for i in range(3):
+            for j in range(3):
+                dF = np.zeros((3, 3))
+                dF[i, j] = eps
+                fd[i, j] = (oracle.stress(model, params, F + dF, ef, es, Ta=Ta)[1] -
+                            oracle.stress(model, params, F - dF, ef, es, Ta=Ta)[1]) / (2 * eps)
+        np.testing.assert_allclose(P, fd, rtol=1e-7, atol=1e-7 * np.abs(P).max())
+        checked += 1
+    assert checked > 15
+
+
+def test_active_stress_closed_forms():
+    """With no passive stiffness (neo-Hookean a = kappa = 0) the stress is the
+    active term alone.  At F = I it is T_a e_f (x) e_f (T = T_a at I4f = 1) for
+    any fibre direction; under a stretch lambda along e_f = x it is
+    P_11 = T_a (1 + 4.9 (lambda - 1)) lambda (P = F S with S_11 = T), every
+    other entry zero; its energy vanishes at F = I."""
+    Ta = 37.0
+    rng = np.random.default_rng(71)
+    for _ in range(5):
+        ef, es = _fibres(rng)
+        P, psi = oracle.stress(I.NEO_HOOKEAN, (0.0, 0.0), np.eye(3), ef, es, Ta=Ta)
+        np.testing.assert_allclose(P, Ta * np.outer(ef, ef), rtol=1e-14, atol=1e-14 * Ta)
+        assert abs(psi) < 1e-14 * Ta
+    for lam in (0.8, 0.95, 1.0, 1.1, 1.3):
+        F = np.diag([lam, 1.0, 1.0])
+        P, _ = oracle.stress(I.NEO_HOOKEAN, (0.0, 0.0), F, (1, 0, 0), (0, 1, 0), Ta=Ta)
+        want = np.zeros((3, 3))
+        want[0, 0] = Ta * (1 + 4.9 * (lam - 1)) * lam
+        np.testing.assert_allclose(P, want, rtol=1e-14, atol=1e-14 * Ta)
+
+
+@pytest.mark.parametrize("model,params,Ta", ACTIVE)
+def test_active_stress_linear_in_tension_and_objective(model, params, Ta):
+    rng = np.random.default_rng(72 + model)
+    for _ in range(8):
+        F = _rand_F(rng)
+        ef, es = _fibres(rng)
+        P0, psi0 = oracle.stress(model, params, F, ef, es)
+        P1, psi1 = oracle.stress(model, params, F, ef, es, Ta=Ta)
+        P2, psi2 = oracle.stress(model, params, F, ef, es, Ta=2 * Ta)
+        np.testing.assert_allclose(P2 - P0, 2 * (P1 - P0), rtol=1e-10, atol=1e-12 * Ta)
+        assert psi2 - psi0 == pytest.approx(2 * (psi1 - psi0), rel=1e-10, abs=1e-12 * Ta)
+        Q = rot(rng)
+        PQ, psiQ = oracle.stress(model, params, Q @ F, ef, es, Ta=Ta)
+        np.testing.assert_allclose(PQ, Q @ P1, rtol=1e-10, atol=1e-12 * np.abs(P1).max())
+        assert psiQ == pytest.approx(psi1, rel=1e-12, abs=1e-14)
+
+
+def test_active_tension_waveform():
+    """T_a(t) of Section 6.1: zero in diastole (t < 0.5 s), rising to its peak
+    84260 (1 - e^-4.5) Pa at 0.65 s, mirror-symmetric about 0.65 s, back to
+    zero at 0.8 s, repeated every 0.8 s (the cardiac cycle)."""
+    Ta = oracle.active_tension
+    for t in (0.0, 0.1, 0.3, 0.4999, 0.5, 0.8, 1.2, 1.6, 2.4):
+        assert Ta(t) == pytest.approx(0.0, abs=1e-9)
+    assert Ta(0.65) == pytest.approx(84260 * (1 - math.exp(-4.5)), rel=1e-14)
+    for s in (0.01, 0.05, 0.1, 0.149):
+        assert Ta(0.65 - s) == pytest.approx(Ta(0.65 + s), rel=1e-12)
+    ts = np.linspace(0.5, 0.65, 40)
+    v = [Ta(t) for t in ts]
+    assert all(b > a for a, b in zip(v, v[1:]))
+    assert max(Ta(t) for t in np.linspace(0, 0.8, 801)) <= Ta(0.65) + 1e-9
+    for t in (0.55, 0.6, 0.7, 0.75):
+        for k in (1, 2):
+            assert Ta(t + 0.8 * k) == pytest.approx(Ta(t), rel=1e-9)
+
+
+def test_active_force_gradients():
+    """With T_a on: G = -dE/dx, the Hessian-vector product and the T_a
+    gradient (column 9 of the parameter gradients) by central differences."""
+    p = tiny_mesh(I.HO, I.HO_DEFAULT)
+    Ta = 60.0
+    p.materials = [I.Material(I.HO, I.HO_DEFAULT, Ta)]
+    m = oracle.Model(p)
+    x = p.x
+    G, _ = m.fe_force(x)
+    eps = 1e-6 * p.grid.h
+    rng = np.random.default_rng(73)
+    for _ in range(8):
+        a, i = rng.integers(p.n_nodes), rng.integers(3)
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = -(m.fe_force(xp)[1] - m.fe_force(xm)[1]) / (2 * eps)
+        assert G[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-8 * np.abs(G).max())
+    v = rng.normal(size=x.shape)
+    Hv, gp = m.fe_force_adj(x, v)
+    e2 = 1e-7 * p.grid.h
+    fd = (m.fe_force(x + e2 * v)[0] - m.fe_force(x - e2 * v)[0]) / (2 * e2)
+    np.testing.assert_allclose(Hv, fd, rtol=1e-5, atol=1e-6 * np.abs(Hv).max())
+    d = 1e-4
+    m.set_materials([I.Material(I.HO, I.HO_DEFAULT, Ta + d)])
+    Gp = m.fe_force(x)[0]
+    m.set_materials([I.Material(I.HO, I.HO_DEFAULT, Ta - d)])
+    Gm = m.fe_force(x)[0]
+    assert gp[0, 9] == pytest.approx(np.sum(v * (Gp - Gm)) / (2 * d), rel=1e-7)
+    # the passive gradients do not depend on how T_a enters
+    m.set_materials([I.Material(I.HO, I.HO_DEFAULT)])
+    _, gp0 = m.fe_force_adj(x, v)
+    np.testing.assert_allclose(gp[0, :9], gp0[0, :9], rtol=1e-12)
+    assert gp0[0, 9] == pytest.approx(gp[0, 9], rel=1e-12)  # dP/dT_a does not involve T_a
+
+
 def test_mass_is_volume():
     p = I.block_problem(fp64=True)
     m = oracle.Model(p)
@@ -615,7 +742,7 @@ def test_loss_gradient_chain_by_differences():
         dth /= n
         eps = 1e-6
         fd = (loss(x0 + eps * dx, th0 + eps * dth) - loss(x0 - eps * dx, th0 - eps * dth)) / (2 * eps)
-        an = np.sum(gx * dx) + np.sum(gth[0] * dth)
+        an = np.sum(gx * dx) + np.sum(gth[0, :9] * dth)
         assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
@@ -688,7 +815,7 @@ def test_differentiation_workload_oracle_gradient_by_differences():
         nrm = math.sqrt(np.sum((dx / p.grid.h) ** 2) + np.sum((dth[:8] / th0[:8]) ** 2))
         dx /= nrm
         dth /= nrm
-        an = np.sum(gx * dx) + np.sum(gth[0] * dth)
+        an = np.sum(gx * dx) + np.sum(gth[0, :9] * dth)
         # step 1e-6: the difference of two evaluations of L (~2.5e5) carries a
         # rounding error of order eps_mach |L|, i.e. eps_mach |L| / step in
         # the quotient; step 1e-5 leaves truncation below 1e-6 relative.
