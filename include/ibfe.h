@@ -100,6 +100,9 @@ typedef enum {
 typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_precision;
 
 #define IB_MAX_MATERIALS 8
+/* Width of a parameter-gradient row: the law's n_params parameters from
+ * column 0, zeros up to column 8, d/dT_a in column 9. */
+#define IB_PARAM_ROW 10
 
 typedef struct {
   int32_t n_nodes, n_elems;
@@ -123,8 +126,13 @@ typedef struct {
 
 typedef struct {
   int32_t model;     /* ib_model */
-  int32_t n_params;  /* 2, 4 or 9 according to the model */
+  int32_t n_params;  /* the model's count: 2, 4, 9, 4 or 5 */
   double params[9];  /* host values */
+  double Ta;         /* active fibre tension T_a (Section 6.1) at the current time, in
+                        the units of params; 0 = passive.  Adds P^a = T F e_f (x) e_f,
+                        T = T_a (1 + 4.9 (sqrt(I4f) - 1)), to the law's stress, and its
+                        potential T_a/2 [(1 - 4.9)(I4f - 1) + 4.9 (2/3)(I4f^(3/2) - 1)]
+                        to the energy; finite (else IB_ERR_INVALID_ARG) */
 } ib_material;
 
 typedef struct ib_plan ib_plan;
@@ -188,8 +196,9 @@ ib_status ib_interp_adj(ib_plan* plan, const ib_pos* x, const void* u, const voi
 
 /* Adjoint of the nodal force for the cotangent v (device Real [3][N]):
  * Hv = (dG/dx)^T v = (dG/dx) v = -(d^2 E/dx^2) v (device Real [3][N]), and, if
- * gparams (host double [n_mats][9]) is non-NULL, gparams[m][k] =
- * v . dG/dtheta_{m,k} for the n_params of material m (stream synchronised). */
+ * gparams (host double [n_mats][IB_PARAM_ROW]) is non-NULL, gparams[m][k] =
+ * v . dG/dtheta_{m,k} for the n_params of material m, gparams[m][9] =
+ * v . dG/dT_a (stream synchronised). */
 ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats,
                           const ib_pos* x, const void* v, void* Hv, double* gparams,
                           void* stream);
@@ -200,7 +209,8 @@ ib_status ib_fe_force_adj(ib_plan* plan, const ib_material* mats, int32_t n_mats
  *   gx = (dG/dx)^T gG_t + (df/dx)^T gf + (dU/dx)^T gU   (device Real [3][N]),
  *        with gG_t = gG + (df/dG)^T gf, the spreading's share of the force cotangent;
  *   gu = (dU/du)^T gU                                   (device Real [3][grid], if gu);
- *   gparams[m][k] = gG_t . dG/dtheta_{m,k}              (device double [n_mats][9], if gparams).
+ *   gparams[m][k] = gG_t . dG/dtheta_{m,k}              (device double [n_mats][IB_PARAM_ROW],
+ *                                                         column 9 for T_a, if gparams).
  * This is the composition of ib_spread_adj, ib_interp_adj and ib_fe_force_adj
  * (Section 4.4: spreading and interpolation are adjoint to each other), with
  * the Gauss points built and binned once and the force adjoint (FP64-pipe
@@ -273,7 +283,7 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
 ib_status ib_batch_forward(ib_batch* batch, void* stream);
 ib_status ib_batch_adjoint(ib_batch* batch, void* stream);
 /* Parameter gradients (ib_backward's gparams) of every instance's last
- * backward replay, host double [n][IB_MAX_MATERIALS][9] (entries past an
+ * backward replay, host double [n][IB_MAX_MATERIALS][IB_PARAM_ROW] (entries past an
  * instance's n_mats are zero); synchronises `stream`. */
 ib_status ib_batch_gparams(ib_batch* batch, double* gparams, void* stream);
 ib_status ib_batch_destroy(ib_batch* batch);
@@ -328,6 +338,13 @@ typedef enum {
 ib_status ib_plan_set_profiling(ib_plan* plan, int32_t enable);
 ib_status ib_plan_profile(ib_plan* plan, void* stream, double* ms, int64_t* calls,
                           int64_t* launches, int32_t reset);
+
+/* Active tension waveform T_a(t) of Section 6.1 in Pa, t in seconds: 0 for
+ * t < 0.5; 84260 (1 - exp(-(t - 0.5)^2 / 0.005)) up to 0.65;
+ * 84260 (1 - exp(-(0.8 - t)^2 / 0.005)) up to 0.8; periodic with the 0.8 s
+ * cardiac cycle.  Host function (no device work); divide by 1000 for
+ * parameter sets in kPa.  The value goes into ib_material.Ta. */
+double ib_active_tension(double t);
 
 /* Static string for a status code. */
 const char* ib_status_str(ib_status s);

@@ -20,7 +20,7 @@ struct ib_batch {
   std::vector<ib_plan*> plans;
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> done;
-  double* gparams;            // device [n][IB_MAX_MATERIALS][9]
+  double* gparams;            // device [n][IB_MAX_MATERIALS][kParamRow]
   cudaEvent_t root;
   cudaStream_t cap;
   cudaGraphExec_t fwd, adj;
@@ -54,7 +54,7 @@ ib_status run_forward(ib_batch* b, int i, cudaStream_t s) {
 ib_status run_adjoint(ib_batch* b, int i, cudaStream_t s) {
   const ib_instance& in = b->inst[i];
   return ib_backward(b->plans[i], in.mats, in.n_mats, &in.x, in.u, in.G, in.gG, in.gf, in.gU,
-                     in.gx, in.gu, b->gparams + (size_t)i * 9 * IB_MAX_MATERIALS, s);
+                     in.gx, in.gu, b->gparams + (size_t)i * kParamRow * IB_MAX_MATERIALS, s);
 }
 
 // Capture fn(b, i, branch_i) for every instance as branches of one graph.
@@ -110,7 +110,7 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
   b->cap = nullptr;
   b->fwd = b->adj = nullptr;
   b->has_adj = has_adj;
-  const size_t gbytes = sizeof(double) * 9 * IB_MAX_MATERIALS * (size_t)n;
+  const size_t gbytes = sizeof(double) * kParamRow * IB_MAX_MATERIALS * (size_t)n;
   ib_status st = cudaMalloc((void**)&b->gparams, gbytes) == cudaSuccess &&
                          cudaMemset(b->gparams, 0, gbytes) == cudaSuccess
                      ? IB_OK
@@ -155,7 +155,7 @@ ib_status ib_batch_adjoint(ib_batch* b, void* stream) {
 ib_status ib_batch_gparams(ib_batch* b, double* gparams, void* stream) {
   if (!b || !gparams) return IB_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(gparams, b->gparams, sizeof(double) * 9 * IB_MAX_MATERIALS * (size_t)b->n,
+  if (cudaMemcpyAsync(gparams, b->gparams, sizeof(double) * kParamRow * IB_MAX_MATERIALS * (size_t)b->n,
                       cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? IB_OK : IB_ERR_CUDA;

@@ -81,6 +81,7 @@ ib_status make_table(const ib_plan* p, const ib_material* mats, int32_t n_mats, 
     if (!material_valid(mats[m])) return IB_ERR_INVALID_ARG;
     mt.model[m] = mats[m].model;
     for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
+    mt.p[m][kTa] = mats[m].Ta;
   }
   return IB_OK;
 }
@@ -194,6 +195,15 @@ extern "C" {
 
 int32_t ib_version(void) { return 100; }
 
+double ib_active_tension(double t) {
+  const double period = 0.8, peak = 84260.0, width = 0.005;
+  double tc = std::fmod(t, period);
+  if (tc < 0.0) tc += period;
+  if (tc < 0.5) return 0.0;
+  const double r = tc < 0.65 ? tc - 0.5 : period - tc;  // rise, then mirrored fall
+  return peak * (1.0 - std::exp(-r * r / width));
+}
+
 const char* ib_status_str(ib_status s) {
   switch (s) {
     case IB_OK: return "ok";
@@ -302,7 +312,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->tile_list_near, 4 * (size_t)p->ntiles) &&
               dalloc(&p->tile_bcount, 12 * (size_t)classify_blocks(p->ntiles)) &&
               dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
-              dalloc(&p->rpart, 8 * 9 * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
+              dalloc(&p->rpart, 8 * kParamRow * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
               dalloc(&p->spread_scratch,
                      spread_scratch_bytes(precision, Q < p->ntiles ? (Q > 0 ? Q : 1)
                                                                    : max_work_items(p->ntiles, Q))) &&
@@ -312,8 +322,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->p_val, rs * 3 * Q) && dalloc(&p->p_idx, 4 * Q) &&
               dalloc(&p->node_tmp, rs * 6 * (size_t)N) &&
               dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
-              dalloc(&p->epart, 8 * 9 * (size_t)(E > 0 ? E : 1)) &&
-              dalloc(&p->ered, 8 * 9 * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16);
+              dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
+              dalloc(&p->ered, 8 * kParamRow * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16);
   if (!good) {
     free_plan(p);
     cudaGetLastError();
@@ -377,14 +387,14 @@ ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
   if (st == IB_OK && energy) {
     st = do_reduce(p, 1, n_mats, s);
-    double red[9 * IB_MAX_MATERIALS];
+    double red[kParamRow * IB_MAX_MATERIALS];
     if (st == IB_OK &&
         (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
          !ok(cudaStreamSynchronize(s))))
       st = IB_ERR_CUDA;
     if (st == IB_OK) {
       double en = 0.0;
-      for (int m = 0; m < n_mats; ++m) en += red[m * 9];
+      for (int m = 0; m < n_mats; ++m) en += red[m * kParamRow];
       *energy = en;
     }
   }
@@ -496,11 +506,11 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch,
                              gparams != nullptr, s);
   }
-  if (st == IB_OK && force && gparams) st = do_reduce(p, 9, n_mats, s);
+  if (st == IB_OK && force && gparams) st = do_reduce(p, kParamRow, n_mats, s);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx);
   if (st == IB_OK && gparams) {
-    const size_t pb = sizeof(double) * 9 * (size_t)n_mats;
+    const size_t pb = sizeof(double) * kParamRow * (size_t)n_mats;
     if (!ok(force ? cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)
                   : cudaMemsetAsync(gparams, 0, pb, s)))
       st = IB_ERR_CUDA;
@@ -541,7 +551,7 @@ ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* 
 
 namespace ibfe {
 // Adjoint of the nodal force without host output: Hv on the device and, if
-// `params`, the parameter gradients left in p->ered ([n_mats][9]).
+// `params`, the parameter gradients left in p->ered ([n_mats][kParamRow]).
 ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats,
                              const ib_pos* x, const void* v, void* Hv, bool params,
                              cudaStream_t s) {
@@ -555,7 +565,7 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, params, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s);
-  if (st == IB_OK && params) st = do_reduce(p, 9, n_mats, s);
+  if (st == IB_OK && params) st = do_reduce(p, kParamRow, n_mats, s);
   return check_launch(st);
 }
 }  // namespace ibfe
@@ -567,12 +577,12 @@ ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, c
   cudaStream_t s = S(stream);
   ib_status st = fe_force_adj_async(p, mats, n_mats, x, v, Hv, gparams != nullptr, s);
   if (st == IB_OK && gparams) {
-    double red[9 * IB_MAX_MATERIALS];
+    double red[kParamRow * IB_MAX_MATERIALS];
     if (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
         !ok(cudaStreamSynchronize(s)))
       return IB_ERR_CUDA;
     for (int m = 0; m < n_mats; ++m)
-      for (int k = 0; k < 9; ++k) gparams[m * 9 + k] = red[m * 9 + k];
+      for (int k = 0; k < kParamRow; ++k) gparams[m * kParamRow + k] = red[m * kParamRow + k];
   }
   return st;
 }

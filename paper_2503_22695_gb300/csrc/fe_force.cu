@@ -50,7 +50,7 @@ struct FeArgs {
   Real h;
   const Real* v;         // [3][N] direction (adjoint) or null
   Real* out;             // [24][E] corner contributions
-  double* epart;         // [9][E] per-element partial sums or null
+  double* epart;         // [kParamRow][E] per-element partial sums or null
   int* status;
   int* next;             // block counter, zero at launch
 };
@@ -84,6 +84,7 @@ template <typename Real, typename S>
 struct Fibre {
   Real Fe[3];  // F e
   S d;         // I4* - 1 = max(I4 - 1, 0), or I4 - 1 without the clamp
+  S d4;        // I4 - 1
 };
 
 template <typename Real, typename S>
@@ -96,6 +97,7 @@ __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S
   S I4m1 = en1;
 #pragma unroll
   for (int i = 0; i < 3; ++i) I4m1 = fma_s(S(He[i]), S(Real(2) * e[i]) + S(He[i]), I4m1);
+  f.d4 = I4m1;
   f.d = (!clamp || I4m1 > S(0)) ? I4m1 : S(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
@@ -202,6 +204,10 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real pa = Real(prm[0]), pb = Real(prm[1]);
   const Real paf = Real(prm[model == 1 ? 1 : 2]), pbf = Real(prm[model == 1 ? 2 : 3]);
   const Real pas = Real(prm[4]), pbs = Real(prm[5]), pafs = Real(prm[6]), pbfs = Real(prm[7]);
+  // active fibre tension (Section 6.1); the parameter adjoint always needs
+  // its fibre kinematics for d/dT_a
+  const Real Ta = Real(prm[kTa]);
+  const bool act = kParams || prm[kTa] != 0.0;
 
   Real Ge[8][3];
 #pragma unroll
@@ -209,9 +215,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
     for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
   double en = 0.0;
-  Real gp[9];
+  Real gp[kParamRow];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) gp[k] = Real(0);
+  for (int k = 0; k < kParamRow; ++k) gp[k] = Real(0);
   bool inverted = false;
 
 #pragma unroll
@@ -311,8 +317,12 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     Fibre<Real, S> f1;
     Fibre<Real, Real> f2;
     Real d1 = Real(0), cf1 = Real(0), ef1 = Real(1), cf2 = Real(0), ef2 = Real(1);
-    const bool has_f = model != 0;
+    const bool has_f = model != 0 || act;
     const bool has_s = model == 2;
+    // active stress P^a = T F e (x) e, T = T_a g, g = 1 + 4.9 (sqrt(I4f) - 1)
+    // with sqrt(I4f) - 1 = (I4f - 1)/(sqrt(I4f) + 1); T is added to the fibre
+    // coefficient cf1
+    Real sq4 = Real(1), gact = Real(1), Tact = Real(0);
     // Psi_1 (model 3): the I4f term (E_L + G_T - 4 G_L)/2 (I4f - 1) F e (x) e,
     // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
     // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
@@ -336,9 +346,15 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           Fw5[i] = w5[i] + H[i][0] * w5[0] + H[i][1] * w5[1] + H[i][2] * w5[2];
-      } else {
+      } else if (model != 0) {
         ef1 = exp(pbf * d1 * d1);
         cf1 = Real(2) * paf * d1 * ef1;
+      }
+      if (act) {
+        const Real d4 = Real(f1.d4);
+        sq4 = sqrt(Real(1) + d4);
+        gact = Real(1) + Real(4.9) * (d4 / (sq4 + Real(1)));
+        Tact = Ta * gact;
       }
     }
     // Sheet family and the fibre-sheet coupling (HO only) in Real, with the
@@ -373,13 +389,19 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       if (model == 3) {
         const double ww = double(w5[0]) * w5[0] + double(w5[1]) * w5[1] + double(w5[2]) * w5[2];
         psi += 0.5 * double(c5) * (double(efn1) - ww) + 0.25 * double(k4) * double(f1.d) * double(f1.d);
-      } else if (has_f) {
+      } else if (model != 0) {  // the exponential fibre term of Psi_2, Psi_3, Psi_4
         const double af = prm[model == 1 ? 1 : 2], bf = prm[model == 1 ? 2 : 3];
         psi += af / (2.0 * bf) * expm1(bf * double(f1.d) * double(f1.d));
       }
       if (has_s) {
         psi += prm[4] / (2.0 * prm[5]) * expm1(prm[5] * double(f2.d) * double(f2.d));
         psi += prm[6] / (2.0 * prm[7]) * expm1(prm[7] * double(I8) * double(I8));
+      }
+      if (act) {
+        // T_a/2 [(1 - 4.9)(I4 - 1) + 4.9 (2/3)(I4^(3/2) - 1)] with
+        // I4^(3/2) - 1 = (I4 - 1)(I4 + sqrt(I4) + 1)/(sqrt(I4) + 1)
+        const double d4 = double(f1.d4), r = sqrt(1.0 + d4);
+        psi += 0.5 * prm[kTa] * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
       }
       en += psi * double(j0);
     }
@@ -392,7 +414,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
         for (int j = 0; j < 3; ++j) P[i][j] = ciso * Dv[i][j] + kap * lnJ * FiT[i][j];
       if (has_f) {
-        const Real c = Real(cf1);
+        const Real c = cf1 + Tact;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -473,12 +495,13 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
         for (int i = 0; i < 3; ++i) dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
         dI4f = Real(2) * (f1.Fe[0] * dFe[0] + f1.Fe[1] * dFe[1] + f1.Fe[2] * dFe[2]);
-        const Real dc =
-            model == 3 ? k4 * dI4f
-                       : ((model == 4 || d1 > Real(0))
-                              ? Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f
-                              : Real(0));
-        const Real c = Real(cf1);
+        Real dc = Real(0);
+        if (model == 3)
+          dc = k4 * dI4f;
+        else if (model == 4 || (model != 0 && d1 > Real(0)))
+          dc = Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f;
+        if (act) dc += Ta * Real(4.9 / 2.0) * dI4f / sq4;  // dT = T_a 4.9 dI4f / (2 sqrt(I4f))
+        const Real c = cf1 + Tact;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -543,6 +566,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         // terms in Real, the sums over elements in double
         const Real w = j0;
         const Real vol = lnJ * dl;
+        gp[kTa] -= w * gact * Real(0.5) * dI4f;  // (g F e (x) e) : dF
         if (model == 0) {
           gp[0] -= w * Real(2) * DdF;
           gp[1] -= w * vol;
@@ -600,7 +624,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   if (kEnergy) A.epart[e] = en;
   if (kParams) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+    for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
   }
 }
 
@@ -657,7 +681,7 @@ __global__ void __launch_bounds__(256) k_reduce_l1(const double* __restrict__ pa
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
         if ((mat_id ? __ldg(mat_id + e) : 0) == m) s += __ldg(part + (int64_t)k * E + e);
       s = block_sum(s, sh);
-      if (threadIdx.x == 0) rpart[((int64_t)blockIdx.x * n_mats + m) * 9 + k] = s;
+      if (threadIdx.x == 0) rpart[((int64_t)blockIdx.x * n_mats + m) * kParamRow + k] = s;
     }
 }
 
@@ -668,9 +692,9 @@ __global__ void __launch_bounds__(256) k_reduce_l2(const double* __restrict__ rp
   for (int m = 0; m < n_mats; ++m)
     for (int k = 0; k < nvals; ++k) {
       double s = 0.0;
-      for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += rpart[((int64_t)b * n_mats + m) * 9 + k];
+      for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += rpart[((int64_t)b * n_mats + m) * kParamRow + k];
       s = block_sum(s, sh);
-      if (threadIdx.x == 0) out[m * 9 + k] = s;
+      if (threadIdx.x == 0) out[m * kParamRow + k] = s;
     }
 }
 
@@ -761,7 +785,7 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
 
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
   if (p->E == 0) {
-    cudaMemsetAsync(p->ered, 0, sizeof(double) * 9 * IB_MAX_MATERIALS, s);
+    cudaMemsetAsync(p->ered, 0, sizeof(double) * kParamRow * IB_MAX_MATERIALS, s);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
   k_reduce_l1<<<kReduceCTAs, 256, 0, s>>>(p->epart, p->mat_id, p->E, nvals, n_mats, p->rpart);

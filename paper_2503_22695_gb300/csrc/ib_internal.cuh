@@ -21,11 +21,15 @@ constexpr int kStatNonfinite = 1;
 constexpr int kStatInverted = 2;
 constexpr int kStatTimeout = 4;
 
+// Parameter row: the law's parameters from column 0, T_a in column kTa.
+constexpr int kParamRow = IB_PARAM_ROW;
+constexpr int kTa = IB_PARAM_ROW - 1;
+
 // Material table passed by value to kernels.
 struct MatTable {
   int n;
   int model[IB_MAX_MATERIALS];
-  double p[IB_MAX_MATERIALS][9];
+  double p[IB_MAX_MATERIALS][kParamRow];
 };
 
 // Grid description used on the device.
@@ -64,6 +68,7 @@ inline bool material_valid(const ib_material& m) {
   if (np < 0 || m.n_params != np) return false;
   for (int k = 0; k < np; ++k)
     if (!std::isfinite(m.params[k])) return false;
+  if (!std::isfinite(m.Ta)) return false;
   if (m.model == IB_FIBRE1 && m.params[2] == 0.0) return false;
   if (m.model == IB_FIBRE2 && m.params[3] == 0.0) return false;
   if (m.model == IB_HO)
@@ -114,7 +119,7 @@ struct ib_plan {
   int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
                          //     [5] spread absmax bits, [6] FE force block counter
   int32_t* digit_tot;    // [256] radix digit totals
-  double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*9] reduction partials
+  double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*kParamRow] reduction partials
   cudaStream_t side;     // interpolation branch of ib_forward
   cudaStream_t zside;    // far-tile zero-fill of the spread
   cudaEvent_t ev_fork, ev_join;      // spread zero-fill fork / join
@@ -136,8 +141,8 @@ struct ib_plan {
   void* node_tmp;        // Real [2][3][N] nodal work vectors (fused backward)
   void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
   void* gq_b;            // Real [3][Q]
-  double* epart;         // [9][E] per-element partial sums
-  double* ered;          // [IB_MAX_MATERIALS*9] reduced sums
+  double* epart;         // [kParamRow][E] per-element partial sums
+  double* ered;          // [IB_MAX_MATERIALS*kParamRow] reduced sums
   int* dstatus;          // device status word
 
   // per-stage profiling (host side; events only while prof_on)

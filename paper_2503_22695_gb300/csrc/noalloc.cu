@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(128) k_energy_noalloc(const int32_t* __restric
             p[4] / (2.0 * p[5]) * expm1(p[5] * ds * ds) + p[6] / (2.0 * p[7]) * expm1(p[7] * I8 * I8) +
             0.5 * p[8] * lnJ * lnJ;
     }
+    if (p[kTa] != 0.0) {  // potential of the active fibre stress (Section 6.1)
+      const double d4 = fibre_d(ef, false), r = sqrt(1.0 + d4);
+      psi += 0.5 * p[kTa] * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
+    }
     en += psi * double(j0);
   }
   part[e] = en;
@@ -226,12 +230,13 @@ extern "C" ib_status ib_fe_energy_noalloc(const ib_mesh* mesh, const ib_material
   mt.n = n_mats;
   for (int m = 0; m < IB_MAX_MATERIALS; ++m) {
     mt.model[m] = 0;
-    for (int k = 0; k < 9; ++k) mt.p[m][k] = 0.0;
+    for (int k = 0; k < kParamRow; ++k) mt.p[m][k] = 0.0;
   }
   for (int m = 0; m < n_mats; ++m) {
     if (!material_valid(mats[m])) return IB_ERR_INVALID_ARG;
     mt.model[m] = mats[m].model;
     for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
+    mt.p[m][kTa] = mats[m].Ta;
   }
   // once per device, with that device current: the device address of the
   // scratch array (host code only sees a host-side stand-in for the symbol)

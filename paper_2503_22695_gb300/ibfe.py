@@ -30,6 +30,7 @@ IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO, IB_STD_REINF, IB_FIBRE2 = 0, 1, 2, 3, 4
 IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
 IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
 IB_MAX_MATERIALS = 8
+IB_PARAM_ROW = 10   # gradient row: the law's parameters, zeros, d/dT_a in column 9
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
 N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9, IB_STD_REINF: 4, IB_FIBRE2: 5}
 
@@ -54,7 +55,8 @@ class _Pos(C.Structure):
 
 
 class _Mat(C.Structure):
-    _fields_ = [("model", C.c_int32), ("n_params", C.c_int32), ("params", C.c_double * 9)]
+    _fields_ = [("model", C.c_int32), ("n_params", C.c_int32), ("params", C.c_double * 9),
+                ("Ta", C.c_double)]
 
 
 class _Instance(C.Structure):
@@ -104,6 +106,8 @@ def _load():
     L.ib_status_str.restype = C.c_char_p
     L.ib_version.argtypes = []
     L.ib_version.restype = C.c_int32
+    L.ib_active_tension.argtypes = [C.c_double]
+    L.ib_active_tension.restype = C.c_double
     return L
 
 
@@ -116,6 +120,12 @@ def ib_status_str(code: int) -> str:
 
 def ib_version() -> int:
     return int(_lib.ib_version())
+
+
+def ib_active_tension(t: float) -> float:
+    """T_a(t) of Section 6.1 in Pa (period 0.8 s); Material.Ta takes it (in the
+    parameter set's units)."""
+    return float(_lib.ib_active_tension(float(t)))
 
 
 def _chk(code: int, what: str):
@@ -135,6 +145,7 @@ def _ptr(t: Optional[torch.Tensor]):
 class Material:
     model: int
     params: Sequence[float]
+    Ta: float = 0.0   # active fibre tension at the current time (Section 6.1)
 
 
 def _mats(mats: Sequence[Material]):
@@ -144,6 +155,7 @@ def _mats(mats: Sequence[Material]):
         arr[i].n_params = len(m.params)
         for k, v in enumerate(m.params):
             arr[i].params[k] = float(v)
+        arr[i].Ta = float(getattr(m, "Ta", 0.0))
     return arr, len(mats)
 
 
@@ -311,12 +323,12 @@ def ib_fe_force_adj(plan: Plan, mats, x: Pos, v, want_params: bool = True, Hv=No
     _check(v, plan.dtype, (3, plan.N), "v")
     Hv = _out(Hv, plan, (3, plan.N), "Hv")
     arr, nm = _mats(mats)
-    gp = (C.c_double * (9 * nm))()
+    gp = (C.c_double * (IB_PARAM_ROW * nm))()
     _chk(_lib.ib_fe_force_adj(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(v), _ptr(Hv),
                               gp if want_params else None, _stream()), "ib_fe_force_adj")
     if not want_params:
         return Hv, None
-    g = torch.tensor(list(gp), dtype=torch.float64).reshape(nm, 9)
+    g = torch.tensor(list(gp), dtype=torch.float64).reshape(nm, IB_PARAM_ROW)
     return Hv, g
 
 
@@ -324,7 +336,7 @@ def ib_backward(plan: Plan, mats, x: Pos, u=None, G=None, gG=None, gf=None, gU=N
                 gx=None, gu=None, want_params: bool = True):
     """Fused backward of ib_forward: (gx, gu, gparams) for the cotangents
     (gG, gf, gU) of (G, f, U); any cotangent may be None (zero).  gparams is a
-    device float64 tensor [n_mats][9] (None unless want_params); gu is None
+    device float64 tensor [n_mats][IB_PARAM_ROW] (None unless want_params); gu is None
     unless gU is given."""
     if gf is not None:
         _check(gf, plan.dtype, plan.grid_shape(), "gf")
@@ -339,7 +351,8 @@ def ib_backward(plan: Plan, mats, x: Pos, u=None, G=None, gG=None, gf=None, gU=N
         gu = None
     gx = _out(gx, plan, (3, plan.N), "gx")
     arr, nm = _mats(mats)
-    gp = torch.empty(nm, 9, dtype=torch.float64, device=plan.device) if want_params else None
+    gp = (torch.empty(nm, IB_PARAM_ROW, dtype=torch.float64, device=plan.device)
+          if want_params else None)
     _chk(_lib.ib_backward(plan.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(u), _ptr(G),
                           _ptr(gG), _ptr(gf), _ptr(gU), _ptr(gx), _ptr(gu), _ptr(gp),
                           _stream()), "ib_backward")
@@ -426,6 +439,7 @@ class Batch:
                 a.mats[k].n_params = len(m.params)
                 for j, v in enumerate(m.params):
                     a.mats[k].params[j] = float(v)
+                a.mats[k].Ta = float(getattr(m, "Ta", 0.0))
             a.x = _Pos(_p(d.get("cell")), _p(d.get("off")), _p(d.get("x64")))
             for name in ("u", "G", "f", "U", "gU", "gf", "gG", "gu", "gx"):
                 setattr(a, name, _p(d.get(name)))
@@ -440,9 +454,10 @@ class Batch:
         _chk(_lib.ib_batch_adjoint(self._h, _stream()), "ib_batch_adjoint")
 
     def gparams(self):
-        out = (C.c_double * (self.n * IB_MAX_MATERIALS * 9))()
+        out = (C.c_double * (self.n * IB_MAX_MATERIALS * IB_PARAM_ROW))()
         _chk(_lib.ib_batch_gparams(self._h, out, _stream()), "ib_batch_gparams")
-        return torch.tensor(list(out), dtype=torch.float64).reshape(self.n, IB_MAX_MATERIALS, 9)
+        return torch.tensor(list(out), dtype=torch.float64).reshape(self.n, IB_MAX_MATERIALS,
+                                                                    IB_PARAM_ROW)
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -474,11 +489,21 @@ def ib_plan_profile(plan: Plan, reset: bool = True):
 
 # ---------------------------------------------------------------------------
 # autograd: positions enter as the split offset `off` (x = origin + (cell+off) h,
-# so dL/doff = h dL/dx); material parameters as a float64 CPU tensor [n_mats][9].
+# so dL/doff = h dL/dx); material parameters as a float64 CPU tensor [n_mats][9]
+# (the law's parameters) or [n_mats][10] (then column 9 is the active tension T_a).
 # ---------------------------------------------------------------------------
 
 def _mats_from(models, params: torch.Tensor):
-    return [Material(m, params[i, :N_PARAMS[m]].tolist()) for i, m in enumerate(models)]
+    Ta = params[:, 9].tolist() if params.shape[1] > 9 else [0.0] * len(models)
+    return [Material(m, params[i, :N_PARAMS[m]].tolist(), Ta[i]) for i, m in enumerate(models)]
+
+
+def _param_grad(gp: torch.Tensor, models, params: torch.Tensor) -> torch.Tensor:
+    # zero the unused columns of each row; keep d/dT_a only when params carries T_a
+    gp = gp[:, :params.shape[1]].clone()
+    for i, m in enumerate(models):
+        gp[i, N_PARAMS[m]:9] = 0
+    return gp
 
 
 class FEForce(torch.autograd.Function):
@@ -497,10 +522,7 @@ class FEForce(torch.autograd.Function):
         x = Pos(cell=cell, off=off.detach())
         Hv, gp = ib_fe_force_adj(plan, _mats_from(ctx.models, params.detach()), x,
                                  gG.contiguous())
-        gp = gp.clone()
-        for i, m in enumerate(ctx.models):
-            gp[i, N_PARAMS[m]:] = 0
-        return None, None, None, Hv * plan.h, gp
+        return None, None, None, Hv * plan.h, _param_grad(gp, ctx.models, params)
 
 
 class Spread(torch.autograd.Function):
@@ -558,10 +580,7 @@ class Coupling(torch.autograd.Function):
         c = lambda t: None if t is None else t.contiguous()
         gx, gu, gp = ib_backward(plan, _mats_from(ctx.models, params.detach()), x,
                                  u.detach().contiguous(), G, c(gG), c(gf), c(gU))
-        gp = gp.cpu()
-        for i, m in enumerate(ctx.models):
-            gp[i, N_PARAMS[m]:] = 0
-        return None, None, None, gx * plan.h, gp, gu
+        return None, None, None, gx * plan.h, _param_grad(gp.cpu(), ctx.models, params), gu
 
 
 class IBCoupling(torch.nn.Module):

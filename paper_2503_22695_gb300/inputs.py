@@ -428,7 +428,8 @@ def shell_sheets_problem(seed: int = 3000, n: int = 256, dims=(160, 100, 10),
 
 
 def material_mix_problem(seed: int = 6000, n: int = 64, dims=(30, 20, 4), models=None,
-                         fp64: bool = False, twist=0.3, amp=0.015, axial=0.02) -> Problem:
+                         fp64: bool = False, twist=0.3, amp=0.015, axial=0.02,
+                         active=0.0) -> Problem:
     """The shell with elements cycling through several laws (mat_id = e mod k).
 
     `models` lists the ib_model codes (default: all five laws of Section 3 and
@@ -436,7 +437,8 @@ def material_mix_problem(seed: int = 6000, n: int = 64, dims=(30, 20, 4), models
     kappa = 100; Psi_2 leaflet; Psi_4 HO; Psi_1 Cook's membrane constants;
     Psi_3 aortic-valve constants.  The smooth twist stretches some fibres and
     shortens others, so the tension-only clamp of Psi_2/Psi_4 and the
-    two-sided fibre term of Psi_3 are both exercised.
+    two-sided fibre term of Psi_3 are both exercised.  `active` is the active
+    tension T_a of every material (Section 6.1), or a list with one per model.
     """
     params = {NEO_HOOKEAN: (0.5, 100.0), FIBRE1: FIBRE1_LEAFLET, HO: HO_DEFAULT,
               STD_REINF: STD_REINF_COOK, FIBRE2: FIBRE2_AV}
@@ -447,7 +449,8 @@ def material_mix_problem(seed: int = 6000, n: int = 64, dims=(30, 20, 4), models
     if not fp64:
         X = X.astype(np.float32).astype(np.float64)
     x = smooth_deformation(X, rng, twist=twist, amp=amp, axial=axial)
-    mats = [Material(m, tuple(params[m])) for m in models]
+    Ta = list(active) if isinstance(active, (list, tuple)) else [float(active)] * len(models)
+    mats = [Material(m, tuple(params[m]), Ta[i]) for i, m in enumerate(models)]
     mat_id = np.arange(conn.shape[1]) % len(models)
     return _finish("mix", grid, conn, X, fib, mat_id, mats, x, 4, rng, fp64)
 

@@ -42,7 +42,7 @@ class Case:
             self.off = torch.from_numpy(prob.off).to(dev)
             self.pos = ibfe.Pos(cell=self.cell, off=self.off)
             self.x_np = I.from_split(prob.cell, prob.off, g)
-        self.mats = [ibfe.Material(m.model, m.params) for m in prob.materials]
+        self.mats = [ibfe.Material(m.model, m.params, m.active) for m in prob.materials]
         self.u = torch.from_numpy(prob.u).to(dev, dt)
         # oracle sees the device values widened exactly to float64
         self.orc = oracle.Model(grid=g, conn=prob.conn, X=prob.X.astype(np.float64),

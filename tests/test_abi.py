@@ -40,6 +40,13 @@ def test_host_side_argument_checks(lib):
     lib.ib_status_str.restype = C.c_char_p
     assert lib.ib_status_str(0) == b"ok"
     assert lib.ib_version() == 100
+    # the active-tension waveform is host arithmetic: same values as the oracle's
+    import oracle
+    lib.ib_active_tension.restype = C.c_double
+    lib.ib_active_tension.argtypes = [C.c_double]
+    for t in [i * 0.0137 for i in range(200)] + [-0.3, 0.65, 0.8, 2.45]:
+        assert lib.ib_active_tension(t) == pytest.approx(oracle.active_tension(t), rel=1e-14,
+                                                         abs=1e-9)
     out = C.c_void_p()
     # null mesh / grid / out pointer: rejected before touching the device
     assert lib.ib_plan_create(None, None, 0, 0, None, C.byref(out)) == 1

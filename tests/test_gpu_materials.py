@@ -3,9 +3,10 @@
 Psi_3 fibre model 2, Psi_4 Holzapfel-Ogden) against the FP64 oracle.
 
 Each law alone on a twisted shell, and all five mixed element by element
-(mat_id = e mod 5), in both precisions: nodal force and energy, the
-Hessian-vector product of ib_fe_force_adj and the parameter gradients of
-every material.  Tolerances are those of the main parity suite: FP32 split
+(mat_id = e mod 5), in both precisions, passive and with the active fibre
+tension of Section 6.1: nodal force and energy, the Hessian-vector product
+of ib_fe_force_adj and the parameter gradients of every material (T_a's in
+column 9).  Tolerances are those of the main parity suite: FP32 split
 plans 1e-5 (force, energy) and 2e-5 (adjoint outputs), FP64 plans 1e-12.
 """
 import numpy as np
@@ -23,55 +24,63 @@ TOL64 = 1e-12
 _cache = {}
 
 
-def case(models, fp64):
-    key = (tuple(models), fp64)
+def case(models, fp64, active=0.0):
+    key = (tuple(models), fp64, tuple(active) if isinstance(active, list) else active)
     if key not in _cache:
         _cache[key] = Case(I.material_mix_problem(seed=6000 + len(_cache), models=models,
-                                                  fp64=fp64))
+                                                  fp64=fp64, active=active))
     return _cache[key]
 
 
 LAWS = [I.NEO_HOOKEAN, I.STD_REINF, I.FIBRE1, I.FIBRE2, I.HO]
-CASES = [([m], fp) for m in (I.STD_REINF, I.FIBRE2) for fp in (False, True)] + \
-        [(LAWS, False), (LAWS, True)]
+# active fibre tension (Section 6.1) in the kPa units of the parameter sets:
+# the printed peak of 84.26 kPa on HO, and a different value per law in the mix
+ACT_MIX = [30.0, 0.0, 12.0, 45.0, 84.26]
+CASES = [([m], fp, 0.0) for m in (I.STD_REINF, I.FIBRE2) for fp in (False, True)] + \
+        [(LAWS, False, 0.0), (LAWS, True, 0.0)] + \
+        [([I.HO], fp, 84.26) for fp in (False, True)] + \
+        [(LAWS, False, ACT_MIX), (LAWS, True, ACT_MIX)]
 IDS = [f"{'+'.join(I.PARAM_NAMES[m][0] for m in ms)}-{'f64' if fp else 'f32'}"
-       for ms, fp in CASES]
+       f"{'-active' if act else ''}" for ms, fp, act in CASES]
 
 
 def _tol(c, key):
     return TOL64 if c.fp64 else TOL32[key]
 
 
-@pytest.mark.parametrize("models,fp64", CASES, ids=IDS)
-def test_force_and_energy(models, fp64):
-    c = case(models, fp64)
+@pytest.mark.parametrize("models,fp64,active", CASES, ids=IDS)
+def test_force_and_energy(models, fp64, active):
+    c = case(models, fp64, active)
     G, en = c.ibfe.ib_fe_force(c.plan, c.mats, c.pos, energy=True)
     Go, eno = c.orc.fe_force(c.x_np)
     assert rel_l2(np_(G), Go) <= _tol(c, "G")
     assert en == pytest.approx(eno, rel=_tol(c, "G"))
 
 
-@pytest.mark.parametrize("models,fp64", CASES, ids=IDS)
-def test_hessian_vector_and_param_gradients(models, fp64):
-    c = case(models, fp64)
+@pytest.mark.parametrize("models,fp64,active", CASES, ids=IDS)
+def test_hessian_vector_and_param_gradients(models, fp64, active):
+    c = case(models, fp64, active)
     v = c.rounded(np.random.default_rng(21).normal(size=(3, c.prob.n_nodes)))
     Hv, gp = c.ibfe.ib_fe_force_adj(c.plan, c.mats, c.pos, c.to_dev(v))
     Hvo, gpo = c.orc.fe_force_adj(c.x_np, v)
     assert rel_l2(np_(Hv), Hvo) <= _tol(c, "adj")
     for m, mat in enumerate(c.prob.materials):
         k = I.N_PARAMS[mat.model]
-        for j in range(k):  # every parameter on its own: their scales differ widely
-            assert abs(float(gp[m, j]) - gpo[m, j]) <= _tol(c, "adj") * np.linalg.norm(gpo[m, :k]) \
-                + 1e-300, (m, j)
-        assert np.all(gp[m, k:].numpy() == 0.0)
+        cols = list(range(k)) + [9]  # the law's parameters and T_a
+        ref = np.linalg.norm(gpo[m, cols])
+        for j in cols:  # every parameter on its own: their scales differ widely
+            assert abs(float(gp[m, j]) - gpo[m, j]) <= _tol(c, "adj") * ref, (m, j)
+        assert np.all(gp[m, k:9].numpy() == 0.0)
 
 
-def test_noalloc_energy_all_laws():
-    """The plan-free energy kernel evaluates the same five laws."""
+@pytest.mark.parametrize("active", [0.0, ACT_MIX], ids=["passive", "active"])
+def test_noalloc_energy_all_laws(active):
+    """The plan-free energy kernel evaluates the same five laws and the
+    active term."""
     import ctypes as C
 
     import torch
-    c = case(LAWS, False)
+    c = case(LAWS, False, active)
     ib = c.ibfe
     _, want = ib.ib_fe_force(c.plan, c.mats, c.pos, energy=True)
     mesh = ib._Mesh(c.prob.n_nodes, c.prob.n_elems, c.conn.data_ptr(), c.X.data_ptr(),
@@ -89,6 +98,7 @@ def test_rejects_bad_parameter_sets():
     c = case([I.STD_REINF], False)
     ib = c.ibfe
     bad = [ib.Material(ib.IB_STD_REINF, (1.0, 2.0, 3.0)),            # 3 of 4 parameters
+           ib.Material(ib.IB_HO, I.HO_DEFAULT, float("inf")),        # non-finite T_a
            ib.Material(ib.IB_FIBRE2, (1.0, 2.0, 3.0, 0.0, 5.0)),     # zero fibre rate
            ib.Material(ib.IB_FIBRE2, (1.0, 2.0, float("nan"), 4.0, 5.0)),
            ib.Material(5, (1.0, 2.0))]
