@@ -1,652 +1,13 @@
-// Hyperelastic nodal force of the immersed structure (Section 4.4:
-// F_i = -sum_q P(X_q) : grad_X phi_i(X_q) w_q) and its adjoints, on trilinear
-// hexahedra with the 2x2x2 Gauss rule.  One thread per element; the eight
-// Gauss points are unrolled so every shape-function value is a compile-time
-// constant.
-//
-// Kinematics are carried as the displacement gradient H = F - I, formed from
-// node differences relative to corner 0 (split positions subtract their
-// integer cells exactly), so J - 1, I1 - 3 and I4 - 1 are evaluated without
-// cancellation:
-//   J - 1   = tr H + ((tr H)^2 - tr(H^2))/2 + det H
-//   I1 - 3  = 2 tr H + |H|^2
-//   I4 - 1  = (|e|^2 - 1) + 2 e.(H e) + |H e|^2
-//   I8      = e_f.e_s + e_f.(H e_s) + e_s.(H e_f) + (H e_f).(H e_s)
-// The scalars of the volumetric term and of the fibre term near I4f = 1 are
-// combined in the type S (double): J - 1 (its terms are exact double products
-// of the FP32 entries of H, so the FP64 sum leaves J - 1 exact to double
-// rounding), ln J = log1p(J - 1), and the fibre invariant I4f - 1 of the fibre
-// family e_f.  Once I4f - 1 is known, the fibre coefficient
-// 2 a_f (I4f - 1) exp(b_f (I4f - 1)^2) is a product of well-conditioned factors
-// and is formed in Real: exp has relative error (argument error) x (argument),
-// small here, so evaluating it beyond the precision of the FP32 stress it
-// multiplies adds nothing.  The sheet family e_s and the coupling I8 of
-// Holzapfel-Ogden use the same cancellation-free formulas in Real.  Everything
-// else is in Real (float for split-precision plans, double for FP64 plans).
-// On GB300 the FP64 pipe runs at about 1/64 of the FP32 rate, so this FP64 set
-// (about 50 double operations per Gauss point) sets the kernel's time.
-//
-// With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
-//   H = Du J0^-1, and the corner forces are
-//   G_a -= (P J0^-T w j0) dN_a/dxi,
-// so the X-gradients of the shape functions are never formed.
+// Host side of the hyperelastic nodal force (Section 4.4) and its adjoints:
+// the choice of kernel instantiation per call, and the deterministic
+// per-material reductions of energies and parameter gradients.  The device
+// code is in fe_kernel.cuh.
 #include <algorithm>
-#include <cstdio>
 
 #include "ib_device.cuh"
 
 namespace ibfe {
 namespace {
-
-template <typename Real>
-struct FeArgs {
-  int E;
-  int64_t N;
-  const int32_t* conn;
-  const Real* X;
-  const Real* fib;       // [6][E] or null
-  const int32_t* mat_id; // [E] or null
-  NodeLoader<Real> pos;
-  Real h;
-  const Real* v;         // [3][N] direction (adjoint) or null
-  Real* out;             // [24][E] corner contributions
-  double* epart;         // [kParamRow][E] per-element partial sums or null
-  int* status;
-  int* next;             // block counter, zero at launch
-};
-
-template <typename T>
-__device__ __forceinline__ T det3(const T A[3][3]) {
-  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-         A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-}
-
-// cof(A)_ij = d det A / d A_ij
-template <typename T>
-__device__ __forceinline__ void cofactor(const T A[3][3], T C[3][3]) {
-  C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
-  C[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
-  C[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
-  C[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
-  C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
-  C[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
-  C[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-  C[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
-  C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-}
-
-__device__ __forceinline__ double fma_s(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fma_s(float a, float b, float c) { return fmaf(a, b, c); }
-
-// Quantities of one fibre family needed by the stress and its derivatives.
-template <typename Real, typename S>
-struct Fibre {
-  Real Fe[3];  // F e
-  S d;         // I4* - 1 = max(I4 - 1, 0), or I4 - 1 without the clamp
-  S d4;        // I4 - 1
-};
-
-template <typename Real, typename S>
-__device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S en1,
-                                          Fibre<Real, S>& f, bool clamp = true) {
-  Real He[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) He[i] = H[i][0] * e[0] + H[i][1] * e[1] + H[i][2] * e[2];
-  // 2 e.He + |He|^2 = He.(2e + He); 2e + He is exact in double
-  S I4m1 = en1;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) I4m1 = fma_s(S(He[i]), S(Real(2) * e[i]) + S(He[i]), I4m1);
-  f.d4 = I4m1;
-  f.d = (!clamp || I4m1 > S(0)) ? I4m1 : S(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) f.Fe[i] = e[i] + He[i];
-}
-
-// ln(1 + x) in double.  For |x| <= 1/8 it is 2 atanh(s) with s = x / (2 + x)
-// (|s| <= 1/17), summed as s (2 + 2z/3 + 2z^2/5 + ... + 2z^6/13), z = s^2: the
-// first omitted term, 2 z^7/15, is below 4e-19 relative.  1/(2 + x) comes from
-// an FP32 reciprocal refined by one Newton step in double, which leaves a
-// relative error near 1e-14 (the square of the FP32 reciprocal's).  Outside
-// that range (|J - 1| > 1/8) the library log1p is used.
-__device__ __forceinline__ double log1p_d(double x) {
-  if (!(fabs(x) <= 0.125)) return log1p(x);
-  const double d = 2.0 + x;
-  double r = (double)__frcp_rn((float)d);
-  r = fma(r, fma(-d, r, 1.0), r);
-  const double s = x * r;
-  const double z = s * s;
-  double t = 2.0 / 13.0;
-  t = fma(t, z, 2.0 / 11.0);
-  t = fma(t, z, 2.0 / 9.0);
-  t = fma(t, z, 2.0 / 7.0);
-  t = fma(t, z, 2.0 / 5.0);
-  t = fma(t, z, 2.0 / 3.0);
-  t = fma(t, z, 2.0);
-  return s * t;
-}
-
-__device__ __forceinline__ double log1p_s(double x) { return log1p_d(x); }
-__device__ __forceinline__ float log1p_s(float x) { return log1pf(x); }
-
-// Resident 128-thread CTAs per SM requested from the register allocator.
-#ifndef IBFE_FE_MIN_BLOCKS
-#define IBFE_FE_MIN_BLOCKS 3
-#endif
-#ifndef IBFE_FE_MIN_BLOCKS_ADJ
-#define IBFE_FE_MIN_BLOCKS_ADJ 3
-#endif
-
-template <typename Real, bool kAdj>
-constexpr int fe_min_blocks() {
-  return sizeof(Real) == 8 ? 2 : (kAdj ? IBFE_FE_MIN_BLOCKS_ADJ : IBFE_FE_MIN_BLOCKS);
-}
-
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
-__device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e) {
-  const int E = A.E;
-  int node[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) node[a] = __ldg(A.conn + a * E + e);
-
-  // reference and current coordinates relative to corner 0
-  Real dX[8][3], du[8][3];
-  int c0[3];
-  Real o0[3];
-  A.pos.load(node[0], c0, o0);
-  Real X0[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + node[0]);
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    int c[3];
-    Real o[3];
-    if (a == 0) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) { dX[0][d] = Real(0); du[0][d] = Real(0); }
-      continue;
-    }
-    A.pos.load(node[a], c, o);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      dX[a][d] = __ldg(A.X + d * A.N + node[a]) - X0[d];
-      Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
-      du[a][d] = dx - dX[a][d];
-    }
-  }
-  Real vv[kAdj ? 8 : 1][3];
-  if (kAdj) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) vv[a][d] = __ldg(A.v + d * A.N + node[a]);
-  }
-
-  const int mid = A.mat_id ? __ldg(A.mat_id + e) : 0;
-  const int model = mt.model[mid];
-  const double* prm = mt.p[mid];
-  Real ef[3] = {Real(1), Real(0), Real(0)}, es[3] = {Real(0), Real(1), Real(0)};
-  if (A.fib) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      ef[i] = __ldg(A.fib + i * E + e);
-      es[i] = __ldg(A.fib + (3 + i) * E + e);
-    }
-  }
-  // |e|^2 - 1 and e_f . e_s, exact enough in S (squares of Real are exact in double)
-  const S efn1 = S(ef[0]) * S(ef[0]) + S(ef[1]) * S(ef[1]) + (S(ef[2]) * S(ef[2]) - S(1));
-  const S esn1 = S(es[0]) * S(es[0]) + S(es[1]) * S(es[1]) + (S(es[2]) * S(es[2]) - S(1));
-  const S efes = S(ef[0]) * S(es[0]) + S(ef[1]) * S(es[1]) + S(ef[2]) * S(es[2]);
-  const Real esn1r = Real(esn1), efesr = Real(efes);
-
-  // material constants (unused entries of a model are never read by its branches)
-  const Real kap = Real(prm[model == 0 ? 1 : (model == 2 ? 8 : (model == 4 ? 4 : 3))]);
-  const Real pa = Real(prm[0]), pb = Real(prm[1]);
-  const Real paf = Real(prm[model == 1 ? 1 : 2]), pbf = Real(prm[model == 1 ? 2 : 3]);
-  const Real pas = Real(prm[4]), pbs = Real(prm[5]), pafs = Real(prm[6]), pbfs = Real(prm[7]);
-  // active fibre tension (Section 6.1); the parameter adjoint always needs
-  // its fibre kinematics for d/dT_a
-  const Real Ta = Real(prm[kTa]);
-  const bool act = kParams || prm[kTa] != 0.0;
-
-  Real Ge[8][3];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
-  double en = 0.0;
-  Real gp[kParamRow];
-#pragma unroll
-  for (int k = 0; k < kParamRow; ++k) gp[k] = Real(0);
-  bool inverted = false;
-
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    // J0 = sum_a dX_a (x) dN_a/dxi ;  Du = sum_a du_a (x) dN_a/dxi
-    Real J0[3][3], Du[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        Real s = Real(0), t = Real(0);
-#pragma unroll
-        for (int a = 1; a < 8; ++a) {
-          s += dX[a][i] * Real(shape_dxi(a, q, j));
-          t += du[a][i] * Real(shape_dxi(a, q, j));
-        }
-        J0[i][j] = s;
-        Du[i][j] = t;
-      }
-    Real cJ[3][3];
-    cofactor(J0, cJ);
-    const Real j0 = J0[0][0] * cJ[0][0] + J0[0][1] * cJ[0][1] + J0[0][2] * cJ[0][2];
-    if (!(j0 > Real(0))) inverted = true;
-    const Real ij0 = Real(1) / j0;
-    // J0^-1 = cof(J0)^T / det
-    Real Ji[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Ji[i][j] = cJ[j][i] * ij0;
-    Real H[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        H[i][j] = Du[i][0] * Ji[0][j] + Du[i][1] * Ji[1][j] + Du[i][2] * Ji[2][j];
-
-    // ---- invariants --------------------------------------------------------
-    // J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H, the middle term written as
-    // the sum of the principal 2x2 minors H_ii H_jj - H_ij H_ji.  In S = double
-    // the sums and products of FP32 entries below are exact up to one rounding
-    // per fma; det H (third order) is taken in Real.
-    const S h11_22 = S(H[1][1]) + S(H[2][2]);
-    S m2 = fma_s(S(H[0][0]), h11_22, S(H[1][1]) * S(H[2][2]));
-    m2 = fma_s(-S(H[0][1]), S(H[1][0]), m2);
-    m2 = fma_s(-S(H[0][2]), S(H[2][0]), m2);
-    m2 = fma_s(-S(H[1][2]), S(H[2][1]), m2);
-    const S Jm1 = (S(H[0][0]) + h11_22) + m2 + S(det3(H));
-    const S lnJs = log1p_s(Jm1);
-    const Real lnJ = Real(lnJs);
-    const Real J = Real(1) + Real(Jm1);
-    Real F[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? Real(1) : Real(0));
-    Real FiT[3][3];
-    cofactor(F, FiT);
-    const Real iJ = Real(1) / J;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) FiT[i][j] *= iJ;
-    Real HH = Real(0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) HH += H[i][j] * H[i][j];
-    const Real I1m3 = Real(2) * (H[0][0] + H[1][1] + H[2][2]) + HH;
-    const Real Jm23m1 = expm1(Real(-2.0 / 3.0) * lnJ);
-    const Real Jm23 = Real(1) + Jm23m1;
-    const Real Ibm3 = Jm23 * I1m3 + Real(3) * Jm23m1;  // I1bar - 3
-    const Real I1o3 = Real(1) + I1m3 * Real(1.0 / 3.0);
-    Real Dv[3][3];  // J^-2/3 (F - I1/3 F^-T)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Dv[i][j] = Jm23 * (F[i][j] - I1o3 * FiT[i][j]);
-
-    // ---- constitutive law -----------------------------------------------------
-    Real ciso;
-    Real eiso = Real(1);  // Psi_4: exp(b (I1bar - 3)); Psi_3: exp(C01 (I1bar - 3))
-    if (model == 2) {
-      eiso = exp(pb * Ibm3);
-      ciso = pa * eiso;
-    } else if (model == 4) {
-      eiso = exp(pb * Ibm3);
-      ciso = Real(2) * pa * pb * eiso;
-    } else if (model == 3) {
-      ciso = pa;  // G_T
-    } else {
-      ciso = Real(2) * pa;
-    }
-    // Fibre family f (the fibre of Psi_2 and of Psi_4): I4f - 1 combined in S.
-    // Its exponential factor and coefficient are then products of that small
-    // number, with no cancellation left, and are formed in Real.
-    Fibre<Real, S> f1;
-    Fibre<Real, Real> f2;
-    Real d1 = Real(0), cf1 = Real(0), ef1 = Real(1), cf2 = Real(0), ef2 = Real(1);
-    const bool has_f = model != 0 || act;
-    const bool has_s = model == 2;
-    // active stress P^a = T F e (x) e, T = T_a g, g = 1 + 4.9 (sqrt(I4f) - 1)
-    // with sqrt(I4f) - 1 = (I4f - 1)/(sqrt(I4f) + 1); T is added to the fibre
-    // coefficient cf1
-    Real sq4 = Real(1), gact = Real(1), Tact = Real(0);
-    // Psi_1 (model 3): the I4f term (E_L + G_T - 4 G_L)/2 (I4f - 1) F e (x) e,
-    // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
-    // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
-    // with C e = e + w, w = H e + H^T e + H^T H e (no cancellation for small H)
-    const Real k4 = model == 3 ? Real(0.5) * (Real(prm[2]) + pa - Real(4) * pb) : Real(0);
-    const Real c5 = model == 3 ? pa - pb : Real(0);
-    Real w5[3] = {Real(0), Real(0), Real(0)}, Fw5[3] = {Real(0), Real(0), Real(0)};
-    if (has_f) {
-      fibre_kin<Real, S>(H, ef, efn1, f1, model == 1 || model == 2);
-      d1 = Real(f1.d);
-      if (model == 3) {
-        cf1 = k4 * d1;
-        Real He[3], HtHe[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) He[i] = f1.Fe[i] - ef[i];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          HtHe[j] = H[0][j] * He[0] + H[1][j] * He[1] + H[2][j] * He[2];
-          w5[j] = He[j] + (H[0][j] * ef[0] + H[1][j] * ef[1] + H[2][j] * ef[2]) + HtHe[j];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          Fw5[i] = w5[i] + H[i][0] * w5[0] + H[i][1] * w5[1] + H[i][2] * w5[2];
-      } else if (model != 0) {
-        ef1 = exp(pbf * d1 * d1);
-        cf1 = Real(2) * paf * d1 * ef1;
-      }
-      if (act) {
-        const Real d4 = Real(f1.d4);
-        sq4 = sqrt(Real(1) + d4);
-        gact = Real(1) + Real(4.9) * (d4 / (sq4 + Real(1)));
-        Tact = Ta * gact;
-      }
-    }
-    // Sheet family and the fibre-sheet coupling (HO only) in Real, with the
-    // same cancellation-free formulas.
-    Real Fef[3], Fes[3];
-    Real I8 = Real(0), e8 = Real(1), c8 = Real(0);
-    if (has_s) {
-      fibre_kin<Real, Real>(H, es, esn1r, f2);
-      ef2 = exp(pbs * f2.d * f2.d);
-      cf2 = Real(2) * pas * f2.d * ef2;
-      Real Hef[3], Hes[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        Hef[i] = H[i][0] * ef[0] + H[i][1] * ef[1] + H[i][2] * ef[2];
-        Hes[i] = H[i][0] * es[0] + H[i][1] * es[1] + H[i][2] * es[2];
-        Fef[i] = ef[i] + Hef[i];
-        Fes[i] = es[i] + Hes[i];
-      }
-      I8 = efesr;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) I8 += ef[i] * Hes[i] + es[i] * Hef[i] + Hef[i] * Hes[i];
-      e8 = exp(pbfs * I8 * I8);
-      c8 = pafs * I8 * e8;
-    }
-
-    if (kEnergy) {
-      double psi = 0.5 * double(kap) * double(lnJs) * double(lnJs);
-      if (model == 0 || model == 1) psi += prm[0] * double(Ibm3);
-      else if (model == 2) psi += prm[0] / (2.0 * prm[1]) * expm1(prm[1] * double(Ibm3));
-      else if (model == 3) psi += 0.5 * prm[0] * double(Ibm3);
-      else psi += prm[0] * expm1(prm[1] * double(Ibm3));
-      if (model == 3) {
-        const double ww = double(w5[0]) * w5[0] + double(w5[1]) * w5[1] + double(w5[2]) * w5[2];
-        psi += 0.5 * double(c5) * (double(efn1) - ww) + 0.25 * double(k4) * double(f1.d) * double(f1.d);
-      } else if (model != 0) {  // the exponential fibre term of Psi_2, Psi_3, Psi_4
-        const double af = prm[model == 1 ? 1 : 2], bf = prm[model == 1 ? 2 : 3];
-        psi += af / (2.0 * bf) * expm1(bf * double(f1.d) * double(f1.d));
-      }
-      if (has_s) {
-        psi += prm[4] / (2.0 * prm[5]) * expm1(prm[5] * double(f2.d) * double(f2.d));
-        psi += prm[6] / (2.0 * prm[7]) * expm1(prm[7] * double(I8) * double(I8));
-      }
-      if (act) {
-        // T_a/2 [(1 - 4.9)(I4 - 1) + 4.9 (2/3)(I4^(3/2) - 1)] with
-        // I4^(3/2) - 1 = (I4 - 1)(I4 + sqrt(I4) + 1)/(sqrt(I4) + 1)
-        const double d4 = double(f1.d4), r = sqrt(1.0 + d4);
-        psi += 0.5 * prm[kTa] * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
-      }
-      en += psi * double(j0);
-    }
-
-    // stress (forward) or its directional derivative (adjoint)
-    Real P[3][3];
-    if (!kAdj) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) P[i][j] = ciso * Dv[i][j] + kap * lnJ * FiT[i][j];
-      if (has_f) {
-        const Real c = cf1 + Tact;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) P[i][j] += c * f1.Fe[i] * ef[j];
-      }
-      if (model == 3) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) P[i][j] -= c5 * (f1.Fe[i] * w5[j] + Fw5[i] * ef[j]);
-      }
-      if (has_s) {
-        const Real c = Real(cf2), k8 = Real(c8);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            P[i][j] += c * f2.Fe[i] * es[j] + k8 * (Fef[i] * es[j] + Fes[i] * ef[j]);
-      }
-    } else {
-      // dF = Dvv J0^-1 with Dvv = sum_a v_a (x) dN_a/dxi
-      Real dF[3][3];
-      {
-        Real Dvv[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            Real s = Real(0);
-#pragma unroll
-            for (int a = 0; a < 8; ++a) s += vv[a][i] * Real(shape_dxi(a, q, j));
-            Dvv[i][j] = s;
-          }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            dF[i][j] = Dvv[i][0] * Ji[0][j] + Dvv[i][1] * Ji[1][j] + Dvv[i][2] * Ji[2][j];
-      }
-      // delta = d ln J = F^-T : dF ; dI1 = 2 F : dF ; d F^-T = -F^-T dF^T F^-T
-      Real dl = Real(0), dI1 = Real(0), DdF = Real(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          dl += FiT[i][j] * dF[i][j];
-          dI1 += Real(2) * F[i][j] * dF[i][j];
-          DdF += Dv[i][j] * dF[i][j];
-        }
-      Real M[3][3];  // F^-T dF^T
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          M[i][j] = FiT[i][0] * dF[j][0] + FiT[i][1] * dF[j][1] + FiT[i][2] * dF[j][2];
-      Real dFiT[3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          dFiT[i][j] = -(M[i][0] * FiT[0][j] + M[i][1] * FiT[1][j] + M[i][2] * FiT[2][j]);
-      const Real I1 = Real(3) + I1m3;
-      const Real dbeta = Jm23 * (dI1 - Real(2.0 / 3.0) * I1 * dl);
-      Real dciso = Real(0);
-      if (model == 2 || model == 4) dciso = ciso * pb * dbeta;
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const Real dD = Real(-2.0 / 3.0) * dl * Dv[i][j] +
-                          Jm23 * (dF[i][j] - dI1 * Real(1.0 / 3.0) * FiT[i][j] -
-                                  I1o3 * dFiT[i][j]);
-          P[i][j] = ciso * dD + dciso * Dv[i][j] + kap * (dl * FiT[i][j] + lnJ * dFiT[i][j]);
-        }
-      Real dI4f = Real(0), dI4s = Real(0), dI8 = Real(0);
-      if (has_f) {
-        Real dFe[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
-        dI4f = Real(2) * (f1.Fe[0] * dFe[0] + f1.Fe[1] * dFe[1] + f1.Fe[2] * dFe[2]);
-        Real dc = Real(0);
-        if (model == 3)
-          dc = k4 * dI4f;
-        else if (model == 4 || (model != 0 && d1 > Real(0)))
-          dc = Real(2) * paf * ef1 * (Real(1) + Real(2) * pbf * d1 * d1) * dI4f;
-        if (act) dc += Ta * Real(4.9 / 2.0) * dI4f / sq4;  // dT = T_a 4.9 dI4f / (2 sqrt(I4f))
-        const Real c = cf1 + Tact;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) P[i][j] += (dc * f1.Fe[i] + c * dFe[i]) * ef[j];
-      }
-      // Psi_1's I5f term: d[-(G_T - G_L)(Fe (x) w + Fw (x) e)] with
-      // dw = dF e + dF^T e + dF^T H e + H^T dF e
-      Real X5 = Real(0);  // (Fe (x) w + Fw (x) e) : dF
-      if (model == 3) {
-        Real dFe[3], dFw[3], dw[3], Fdw[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dFe[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
-          dFw[i] = dF[i][0] * w5[0] + dF[i][1] * w5[1] + dF[i][2] * w5[2];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          Real t = dFe[j];
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-            t += dF[i][j] * f1.Fe[i] + H[i][j] * dFe[i];  // dF^T (e + He) + H^T dF e
-          dw[j] = t;
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          Fdw[i] = dw[i] + H[i][0] * dw[0] + H[i][1] * dw[1] + H[i][2] * dw[2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            P[i][j] -= c5 * (dFe[i] * w5[j] + f1.Fe[i] * dw[j] + dFw[i] * ef[j] + Fdw[i] * ef[j]);
-        X5 = f1.Fe[0] * dFw[0] + f1.Fe[1] * dFw[1] + f1.Fe[2] * dFw[2] + Fw5[0] * dFe[0] +
-             Fw5[1] * dFe[1] + Fw5[2] * dFe[2];
-      }
-      if (has_s) {
-        Real dFs[3], dFf[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dFs[i] = dF[i][0] * es[0] + dF[i][1] * es[1] + dF[i][2] * es[2];
-          dFf[i] = dF[i][0] * ef[0] + dF[i][1] * ef[1] + dF[i][2] * ef[2];
-        }
-        dI4s = Real(2) * (f2.Fe[0] * dFs[0] + f2.Fe[1] * dFs[1] + f2.Fe[2] * dFs[2]);
-        const Real dc =
-            f2.d > Real(0)
-                ? Real(2) * pas * ef2 * (Real(1) + Real(2) * pbs * f2.d * f2.d) * dI4s
-                : Real(0);
-        const Real c = Real(cf2);
-        dI8 = dFf[0] * Fes[0] + dFf[1] * Fes[1] + dFf[2] * Fes[2] + Fef[0] * dFs[0] +
-              Fef[1] * dFs[1] + Fef[2] * dFs[2];
-        const Real dk8 = pafs * e8 * (Real(1) + Real(2) * pbfs * I8 * I8) * dI8;
-        const Real k8 = c8;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            P[i][j] += (dc * f2.Fe[i] + c * dFs[i]) * es[j] +
-                       dk8 * (Fef[i] * es[j] + Fes[i] * ef[j]) +
-                       k8 * (dFf[i] * es[j] + dFs[i] * ef[j]);
-      }
-      if (kParams) {
-        // gparams_k = -sum_q w j0 (dP/dtheta_k : dF): the element's eight
-        // terms in Real, the sums over elements in double
-        const Real w = j0;
-        const Real vol = lnJ * dl;
-        gp[kTa] -= w * gact * Real(0.5) * dI4f;  // (g F e (x) e) : dF
-        if (model == 0) {
-          gp[0] -= w * Real(2) * DdF;
-          gp[1] -= w * vol;
-        } else if (model == 1) {
-          gp[0] -= w * Real(2) * DdF;
-          gp[1] -= w * d1 * ef1 * dI4f;
-          gp[2] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
-          gp[3] -= w * vol;
-        } else if (model == 3) {  // {G_T, G_L, E_L, kappa}; (Fe (x) e) : dF = dI4f / 2
-          const Real y4 = Real(0.5) * dI4f;
-          gp[0] -= w * (DdF - X5 + Real(0.5) * d1 * y4);
-          gp[1] -= w * (X5 - Real(2) * d1 * y4);
-          gp[2] -= w * (Real(0.5) * d1 * y4);
-          gp[3] -= w * vol;
-        } else if (model == 4) {  // {C10, C01, af, bf, kappa}
-          gp[0] -= w * Real(2) * pb * eiso * DdF;
-          gp[1] -= w * Real(2) * pa * eiso * (Real(1) + pb * Ibm3) * DdF;
-          gp[2] -= w * d1 * ef1 * dI4f;
-          gp[3] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
-          gp[4] -= w * vol;
-        } else {
-          gp[0] -= w * eiso * DdF;
-          gp[1] -= w * pa * Ibm3 * eiso * DdF;
-          gp[2] -= w * d1 * ef1 * dI4f;
-          gp[3] -= w * paf * d1 * d1 * d1 * ef1 * dI4f;
-          gp[4] -= w * f2.d * ef2 * dI4s;
-          gp[5] -= w * pas * f2.d * f2.d * f2.d * ef2 * dI4s;
-          gp[6] -= w * I8 * e8 * dI8;
-          gp[7] -= w * pafs * I8 * I8 * I8 * e8 * dI8;
-          gp[8] -= w * vol;
-        }
-      }
-    }
-
-    // corner forces: G_a -= (P J0^-T w j0) dN_a/dxi
-    Real Qm[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        Qm[i][k] = (P[i][0] * Ji[k][0] + P[i][1] * Ji[k][1] + P[i][2] * Ji[k][2]) * j0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        Ge[a][i] -= Qm[i][0] * Real(shape_dxi(a, q, 0)) + Qm[i][1] * Real(shape_dxi(a, q, 1)) +
-                    Qm[i][2] * Real(shape_dxi(a, q, 2));
-  }
-
-  if (inverted) set_status(A.status, kStatInverted);
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) A.out[(a * 3 + i) * E + e] = Ge[a][i];
-  if (kEnergy) A.epart[e] = en;
-  if (kParams) {
-#pragma unroll
-    for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
-  }
-}
-
-// Persistent grid (a fixed number of CTAs per SM, fewer than fit): the kernel
-// is bound by the FP64 pipe, and the SM room it leaves lets the Gauss-point
-// binning and the interpolation, issued on another stream, run beside it.
-// CTAs take blocks of elements from a counter, so a CTA that becomes resident
-// late (its SM busy with those kernels) simply takes fewer.
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams>
-__global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
-    k_fe(FeArgs<Real> A, MatTable mt) {
-  __shared__ int base;
-  for (;;) {
-    if (threadIdx.x == 0) base = atomicAdd(A.next, 1) * (int)blockDim.x;
-    __syncthreads();
-    const int b = base;
-    __syncthreads();
-    if (b >= A.E) break;
-    if (b + (int)threadIdx.x < A.E)
-      fe_element<Real, S, kEnergy, kAdj, kParams>(A, mt, b + (int)threadIdx.x);
-  }
-}
 
 // Deterministic per-material sums of per-element partials in two levels:
 // CTA b reduces a contiguous chunk of elements with a fixed-shape tree
@@ -698,90 +59,61 @@ __global__ void __launch_bounds__(256) k_reduce_l2(const double* __restrict__ rp
     }
 }
 
-template <typename Real>
-FeArgs<Real> make_args(ib_plan* p, const void* xa, const float* off, const void* v, void* out);
-
-template <>
-FeArgs<float> make_args<float>(ib_plan* p, const void* xa, const float* off, const void* v,
-                               void* out) {
-  FeArgs<float> A;
-  A.E = p->E;
-  A.N = p->N;
-  A.conn = p->conn;
-  A.X = (const float*)p->X;
-  A.fib = (const float*)p->fibres;
-  A.mat_id = p->mat_id;
-  A.pos.cell = (const int32_t*)xa;
-  A.pos.off = off;
-  A.pos.N = p->N;
-  A.h = (float)p->grid.h;
-  A.v = (const float*)v;
-  A.out = (float*)out;
-  A.epart = p->epart;
-  A.status = p->dstatus;
-  A.next = p->tile_counters + 6;
-  return A;
-}
-
-template <>
-FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*, const void* v,
-                                 void* out) {
-  FeArgs<double> A;
-  A.E = p->E;
-  A.N = p->N;
-  A.conn = p->conn;
-  A.X = (const double*)p->X;
-  A.fib = (const double*)p->fibres;
-  A.mat_id = p->mat_id;
-  A.pos.x64 = (const double*)xa;
-  A.pos.N = p->N;
-  for (int d = 0; d < 3; ++d) A.pos.origin[d] = p->grid.origin[d];
-  A.pos.inv_h = 1.0 / p->grid.h;
-  A.h = p->grid.h;
-  A.v = (const double*)v;
-  A.out = (double*)out;
-  A.epart = p->epart;
-  A.status = p->dstatus;
-  A.next = p->tile_counters + 6;
-  return A;
-}
-
-template <typename Real, bool kEnergy, bool kAdj, bool kParams>
-ib_status run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
-              void* out, cudaStream_t s) {
-  if (p->E == 0) return IB_OK;
-  FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
-  const int threads = 128;
-  // the forward runs beside the sort and interpolation; the adjoint runs alone
-  const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : p->fe_ctas;
-  const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
-  if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
-  if (p->precision == IB_FP32_SPLIT_F32STAB)
-    k_fe<Real, Real, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
-  else
-    k_fe<Real, double, kEnergy, kAdj, kParams><<<blocks, threads, 0, s>>>(A, mt);
-  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+// The smallest instantiated law set covering the material table (every
+// model in it, the active term if a material has T_a != 0 or the parameter
+// gradients are wanted: they include d/dT_a).
+int law_set(const MatTable& mt, bool params) {
+  int need = params ? kLawAct : 0;
+  for (int m = 0; m < mt.n; ++m) {
+    need |= 1 << mt.model[m];
+    if (mt.p[m][kTa] != 0.0) need |= kLawAct;
+  }
+  if ((need & ~kLawBase) == 0) return kLawBase;
+  if ((need & ~kLawBaseAct) == 0) return kLawBaseAct;
+  return kLawAll;
 }
 
 }  // namespace
 
+#define IBFE_FE_ARGS p, mt, xa, off, v, out, s
+
 ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                           void* out, bool energy, cudaStream_t s) {
+  const void* v = nullptr;
+  const int set = law_set(mt, false);
   if (p->precision == IB_FP64)
-    return energy ? run<double, true, false, false>(p, mt, xa, off, nullptr, out, s)
-                  : run<double, false, false, false>(p, mt, xa, off, nullptr, out, s);
-  return energy ? run<float, true, false, false>(p, mt, xa, off, nullptr, out, s)
-                : run<float, false, false, false>(p, mt, xa, off, nullptr, out, s);
+    return energy ? fe_run<double, double, true, false, false, kLawAll>(IBFE_FE_ARGS)
+                  : fe_run<double, double, false, false, false, kLawAll>(IBFE_FE_ARGS);
+  if (p->precision == IB_FP32_SPLIT_F32STAB) {
+    if (energy) return fe_run<float, float, true, false, false, kLawAll>(IBFE_FE_ARGS);
+    return set == kLawBase ? fe_run<float, float, false, false, false, kLawBase>(IBFE_FE_ARGS)
+                           : fe_run<float, float, false, false, false, kLawAll>(IBFE_FE_ARGS);
+  }
+  if (energy) return fe_run<float, double, true, false, false, kLawAll>(IBFE_FE_ARGS);
+  if (set == kLawBase) return fe_run<float, double, false, false, false, kLawBase>(IBFE_FE_ARGS);
+  if (set == kLawBaseAct)
+    return fe_run<float, double, false, false, false, kLawBaseAct>(IBFE_FE_ARGS);
+  return fe_run<float, double, false, false, false, kLawAll>(IBFE_FE_ARGS);
 }
 
 ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                               const void* v, void* out, bool params, cudaStream_t s) {
+  const int set = law_set(mt, params);
   if (p->precision == IB_FP64)
-    return params ? run<double, false, true, true>(p, mt, xa, off, v, out, s)
-                  : run<double, false, true, false>(p, mt, xa, off, v, out, s);
-  return params ? run<float, false, true, true>(p, mt, xa, off, v, out, s)
-                : run<float, false, true, false>(p, mt, xa, off, v, out, s);
+    return params ? fe_run<double, double, false, true, true, kLawAll>(IBFE_FE_ARGS)
+                  : fe_run<double, double, false, true, false, kLawAll>(IBFE_FE_ARGS);
+  if (p->precision == IB_FP32_SPLIT_F32STAB)
+    return params ? fe_run<float, float, false, true, true, kLawAll>(IBFE_FE_ARGS)
+                  : fe_run<float, float, false, true, false, kLawAll>(IBFE_FE_ARGS);
+  if (params)
+    return set == kLawBaseAct ? fe_run<float, double, false, true, true, kLawBaseAct>(IBFE_FE_ARGS)
+                              : fe_run<float, double, false, true, true, kLawAll>(IBFE_FE_ARGS);
+  if (set == kLawBase) return fe_run<float, double, false, true, false, kLawBase>(IBFE_FE_ARGS);
+  if (set == kLawBaseAct) return fe_run<float, double, false, true, false, kLawBaseAct>(IBFE_FE_ARGS);
+  return fe_run<float, double, false, true, false, kLawAll>(IBFE_FE_ARGS);
 }
+
+#undef IBFE_FE_ARGS
 
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
   if (p->E == 0) {

@@ -25,6 +25,14 @@ constexpr int kStatTimeout = 4;
 constexpr int kParamRow = IB_PARAM_ROW;
 constexpr int kTa = IB_PARAM_ROW - 1;
 
+// Law sets of the force kernel's instantiations: bit m for ib_model m, and
+// kLawAct for the active fibre stress.  The host launches the smallest
+// instantiated set that covers the material table.
+constexpr int kLawAct = 1 << 5;
+constexpr int kLawBase = (1 << IB_NEO_HOOKEAN) | (1 << IB_FIBRE1) | (1 << IB_HO);
+constexpr int kLawBaseAct = kLawBase | kLawAct;
+constexpr int kLawAll = kLawBase | (1 << IB_STD_REINF) | (1 << IB_FIBRE2) | kLawAct;
+
 // Material table passed by value to kernels.
 struct MatTable {
   int n;
@@ -167,6 +175,11 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell
                               const float* off, const void* v, void* elem_out, bool params,
                               cudaStream_t s);
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
+// one instantiation of the force kernel's launcher (fe_kernel.cuh; explicit
+// instantiations in fe_force_f32.cu, fe_force_adj.cu, fe_force_var.cu)
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
+                 void* out, cudaStream_t s);
 
 // assemble.cu
 // out = add + src over 3 N values (add optional, may be out)

@@ -106,3 +106,28 @@ def test_rejects_bad_parameter_sets():
         with pytest.raises(ib.IBError) as ei:
             ib.ib_fe_force(c.plan, [m], c.pos)
         assert ei.value.code == ib.IB_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("fp64", [False, True], ids=["f32", "f64"])
+def test_law_set_instantiations_agree(fp64):
+    """The force kernel is instantiated per law set (the laws of Section 6.3
+    and Psi_2/Psi_4 alone, with the active term, or all five); the host picks
+    the smallest set covering the material table.  An unused material of
+    another law, or a zero active tension, must not change the result beyond
+    rounding: the same HO shell through the three instantiations."""
+    c = case([I.HO], fp64)
+    ib = c.ibfe
+    ho = c.mats[0]
+    v = c.to_dev(c.rounded(np.random.default_rng(22).normal(size=(3, c.prob.n_nodes))))
+    tables = {"base": [ho],
+              "base+active": [ho, ib.Material(ib.IB_NEO_HOOKEAN, (0.5, 100.0), 1.0)],
+              "all": [ho, ib.Material(ib.IB_FIBRE2, I.FIBRE2_AV)]}
+    res = {}
+    for k, mats in tables.items():
+        G = np_(ib.ib_fe_force(c.plan, mats, c.pos))
+        Hv, gp = ib.ib_fe_force_adj(c.plan, mats, c.pos, v)
+        res[k] = (G, np_(Hv), gp[0].numpy())
+    t = 1e-13 if fp64 else 1e-6
+    for k in ("base+active", "all"):
+        for a, b in zip(res[k], res["base"]):
+            assert rel_l2(a, b) <= t, k
