@@ -288,6 +288,58 @@ ib_status ib_batch_adjoint(ib_batch* batch, void* stream);
 ib_status ib_batch_gparams(ib_batch* batch, double* gparams, void* stream);
 ib_status ib_batch_destroy(ib_batch* batch);
 
+/* ---------------------------------------------------------------------------
+ * Fluid step and the explicit IB step (Section 4.2).  The momentum equation
+ * is split by Chorin's projection on the periodic MAC grid of a plan:
+ *   rho/dt (u* - u^n) - mu Lap_h u* = f,   Lap_h p = div_h u* / dt,
+ *   u^{n+1} = u* - dt grad_h p,
+ * with (div u)(i) = sum_c (u^c(i+e_c) - u^c(i))/h, (grad p)^c(i) =
+ * (p(i) - p(i-e_c))/h and the 7-point Lap_h = div_h grad_h; both solves by
+ * geometric multigrid V-cycles (red-black Gauss-Seidel, 2 pre- and 2
+ * post-sweeps; levels halve every dimension while all are even and the
+ * largest exceeds 16; the coarsest is solved in one CTA's shared memory).
+ * The cycle counts are fixed (default 2 Helmholtz, 8 Poisson), so a step
+ * involves no host round trip; ib_fluid_step can report the residuals
+ * reached.  Fields: u, f, u_next device Real [3][n2][n1][n0] (component c on
+ * the lower c-faces, as everywhere in this API), p device Real [n2][n1][n0]
+ * at cell centres with zero mean.  Real is float for the split precisions and
+ * double for IB_FP64.  The box is periodic; the paper's no-slip walls are not
+ * modelled.
+ * ------------------------------------------------------------------------- */
+typedef struct ib_fluid ib_fluid;
+
+/* Fluid solver for `grid` (every n_d even, 4..4096; IB_ERR_UNSUPPORTED for an
+ * odd size or a coarsest level above 8192 cells) with density rho > 0,
+ * viscosity mu >= 0 and time step dt > 0.  Allocates its multigrid hierarchy
+ * (about 1.6 field volumes) on the current device. */
+ib_status ib_fluid_create(const ib_grid* grid, int32_t precision, double rho, double mu,
+                          double dt, void* stream, ib_fluid** out);
+ib_status ib_fluid_destroy(ib_fluid* fluid);
+/* V-cycles per Helmholtz solve (all three components together) and per
+ * Poisson solve, each in [1, 100]. */
+ib_status ib_fluid_set_cycles(ib_fluid* fluid, int32_t helmholtz_cycles, int32_t poisson_cycles);
+/* Number of multigrid levels (the finest included). */
+ib_status ib_fluid_levels(const ib_fluid* fluid, int32_t* levels);
+/* One projection step: u_next (may alias u) and p (NULL: kept internally)
+ * from u and the force density f (NULL: no force).  If residuals (host,
+ * 2 doubles) is non-NULL, also the relative residuals ||rhs - A x|| / ||rhs||
+ * of the Helmholtz and Poisson solves (synchronises `stream`).  Asynchronous
+ * otherwise. */
+ib_status ib_fluid_step(ib_fluid* fluid, const void* u, const void* f, void* u_next, void* p,
+                        double* residuals, void* stream);
+
+/* One explicit IB step (Section 4.2) on the plan's structure and the fluid's
+ * grid (same lattice, spacing and precision as the plan, else
+ * IB_ERR_INVALID_ARG): the nodal force G of the configuration x^n, the force
+ * density f spread from it at x^n, the fluid step from u^n to u^{n+1}, the
+ * new velocity interpolated at x^n (U, onto the nodes as in ib_interp), and
+ * the nodes moved by dt U.  x is updated in place (split positions carry
+ * whole cells into `cell`, offsets stay in [0,1)); u holds u^n on entry and
+ * u^{n+1} on return; G [3][N], f [3][grid], U [3][N] and p [grid] (NULL:
+ * kept internally) are outputs.  Asynchronous on `stream`. */
+ib_status ib_step(ib_plan* plan, ib_fluid* fluid, const ib_material* mats, int32_t n_mats,
+                  const ib_pos* x, void* u, void* G, void* f, void* U, void* p, void* stream);
+
 /* Total elastic energy sum_{e,q} Psi(F_q) w_q j0 of an FP32 split-position
  * mesh, without a plan and without allocating anything, for callers that
  * cannot call cudaMalloc: code running while a CUDA graph is captured on its

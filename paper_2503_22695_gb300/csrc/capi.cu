@@ -455,6 +455,33 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
   return check_launch(st);
 }
 
+ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_mats,
+                  const ib_pos* x, void* u, void* G, void* f, void* U, void* pr, void* stream) {
+  if (!p || !fl || !u || !G || !f || !U || !aligned16(f) || !aligned16(u) ||
+      !fluid_matches(fl, p))
+    return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  const double h = p->grid.h;
+  // nodal force of x^n, spread at x^n
+  {
+    Stage sc(p, IB_STAGE_FORCE, s, 1);
+    st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
+  }
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK) st = do_points_sorted(p, x, G, s);
+  if (st == IB_OK) st = do_spread(p, 1.0 / (h * h * h), f, s);
+  // u^n -> u^{n+1} in place
+  if (st == IB_OK) st = fluid_step_async(fl, u, f, u, pr, nullptr, s);
+  // U = interpolation of u^{n+1} at the same (binned) points, then x += dt U
+  if (st == IB_OK) st = do_interp_tail(p, u, U, s);
+  if (st == IB_OK) st = launch_advance_positions(p, x, U, fluid_dt(fl), s);
+  return check_launch(st);
+}
+
 ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                       const void* u, const void* G, const void* gG, const void* gf,
                       const void* gU, void* gx, void* gu, double* gparams, void* stream) {

@@ -221,6 +221,15 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
                              const ib_pos* x, const void* v, void* Hv, bool params,
                              cudaStream_t s);
 
+// fluid.cu
+ib_status fluid_step_async(ib_fluid* fl, const void* u, const void* f, void* u_next, void* p,
+                           double* residuals, cudaStream_t s);
+bool fluid_matches(const ib_fluid* fl, const ib_plan* p);
+double fluid_dt(const ib_fluid* fl);
+// x += dt U on the plan's position storage (split cells carry whole cells)
+ib_status launch_advance_positions(ib_plan* p, const ib_pos* x, const void* U, double dt,
+                                   cudaStream_t s);
+
 // tiles.cu
 ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s);
 int classify_blocks(int ntiles);

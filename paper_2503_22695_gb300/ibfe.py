@@ -97,6 +97,13 @@ def _load():
         "ib_fe_energy_noalloc": [C.POINTER(_Mesh), C.POINTER(_Mat), i32, C.POINTER(_Pos),
                                  C.c_double, vp, vp],
         "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
+        "ib_fluid_create": [C.POINTER(_Grid), i32, C.c_double, C.c_double, C.c_double, vp,
+                            C.POINTER(vp)],
+        "ib_fluid_destroy": [vp],
+        "ib_fluid_set_cycles": [vp, i32, i32],
+        "ib_fluid_levels": [vp, C.POINTER(i32)],
+        "ib_fluid_step": [vp, vp, vp, vp, vp, dp, vp],
+        "ib_step": [vp, vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -214,6 +221,83 @@ class Plan:
             except Exception:
                 pass
             self._h = None
+
+
+class Fluid:
+    """The fluid solver of Section 4.2 on a periodic MAC grid (ib_fluid_create)."""
+
+    def __init__(self, n, h: float, rho: float, mu: float, dt: float,
+                 precision: int = IB_FP32_SPLIT, origin=(0.0, 0.0, 0.0)):
+        self.dtype = torch.float64 if precision == IB_FP64 else torch.float32
+        self.n, self.h = tuple(int(v) for v in n), float(h)
+        self.rho, self.mu, self.dt = float(rho), float(mu), float(dt)
+        self.precision = precision
+        grid = _Grid((C.c_int32 * 3)(*self.n), self.h, (C.c_double * 3)(*origin))
+        out = C.c_void_p()
+        _chk(_lib.ib_fluid_create(C.byref(grid), precision, self.rho, self.mu, self.dt,
+                                  _stream(), C.byref(out)), "ib_fluid_create")
+        self._h = out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def grid_shape(self):
+        n0, n1, n2 = self.n
+        return (3, n2, n1, n0)
+
+    def levels(self) -> int:
+        v = C.c_int32()
+        _chk(_lib.ib_fluid_levels(self._h, C.byref(v)), "ib_fluid_levels")
+        return int(v.value)
+
+    def set_cycles(self, helmholtz: int, poisson: int):
+        _chk(_lib.ib_fluid_set_cycles(self._h, int(helmholtz), int(poisson)),
+             "ib_fluid_set_cycles")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            try:
+                _lib.ib_fluid_destroy(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def ib_fluid_step(fluid: Fluid, u, f=None, u_next=None, p=None, residuals: bool = False):
+    """One projection step: (u_next, p, residuals or None); u_next may be u."""
+    sh = fluid.grid_shape()
+    _check(u, fluid.dtype, sh, "u")
+    if f is not None:
+        _check(f, fluid.dtype, sh, "f")
+    if u_next is None:
+        u_next = torch.empty_like(u)
+    _check(u_next, fluid.dtype, sh, "u_next")
+    if p is None:
+        p = torch.empty(sh[1:], dtype=fluid.dtype, device=u.device)
+    _check(p, fluid.dtype, sh[1:], "p")
+    res = (C.c_double * 2)() if residuals else None
+    _chk(_lib.ib_fluid_step(fluid.handle, _ptr(u), _ptr(f), _ptr(u_next), _ptr(p), res,
+                            _stream()), "ib_fluid_step")
+    return u_next, p, (list(res) if residuals else None)
+
+
+def ib_step(plan: Plan, fluid: Fluid, mats, x: Pos, u, G=None, f=None, U=None, p=None):
+    """One explicit IB step (Section 4.2): x and u advance in place; returns
+    (G, f, U, p) -- the nodal force and force density of x^n, the new velocity
+    at x^n and the pressure."""
+    sh = plan.grid_shape()
+    _check(u, plan.dtype, sh, "u")
+    G = _out(G, plan, (3, plan.N), "G")
+    f = _out(f, plan, sh, "f")
+    U = _out(U, plan, (3, plan.N), "U")
+    if p is None:
+        p = torch.empty(sh[1:], dtype=plan.dtype, device=u.device)
+    _check(p, plan.dtype, sh[1:], "p")
+    arr, nm = _mats(mats)
+    _chk(_lib.ib_step(plan.handle, fluid.handle, arr, nm, C.byref(_pos(plan, x)), _ptr(u),
+                      _ptr(G), _ptr(f), _ptr(U), _ptr(p), _stream()), "ib_step")
+    return G, f, U, p
 
 
 def _check(t, dtype, shape, name):
