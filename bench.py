@@ -34,6 +34,9 @@ METRIC = "IB force+spread+interp Gauss-pts/s, % HBM roofline; adjoint/forward ti
 FP64_OPS_PER_GP = 52.0   # FP64-pipe operations of the FE force per Gauss point
 FP64_PEAK_GOPS = 625.0   # nominal GB300 FP64: 1.25 TFLOP/s = 625 G FMA-slots/s
 UNIT = "Gauss-pts/s"
+# fluid of the explicit IB step (synthetic, unit periodic box): density,
+# viscosity and time step
+FLUID_RHO, FLUID_MU, FLUID_DT = 1.0, 0.01, 1e-4
 WORKLOAD = ("shell256: 256^3 periodic MAC grid; HO ventricle-like shell 160x100x10 hex + two "
             "80x40x2 fibre-reinforced leaflet sheets; 172,800 trilinear hexes, 1,382,400 Gauss "
             "points; 16 divergence-free Fourier velocity modes")
@@ -366,6 +369,64 @@ def run_ours(args):
     h2d = (h_cell.numel() * 4 + h_off.numel() * 4 + h_u.numel() * 4)
     d2h = (h_G.numel() + h_f.numel() + h_U.numel()) * 4
 
+    # --- fluid step and the explicit IB step (Section 4.2) at the same grid --
+    fluid_line = None
+    if not args.no_fluid:
+        fl = ibfe.Fluid(prob.grid.n, prob.grid.h, FLUID_RHO, FLUID_MU, FLUID_DT)
+        uf = torch.empty_like(u)
+        pf = torch.empty(plan.grid_shape()[1:], device=dev)
+        fstep = lambda: ibfe.ib_fluid_step(fl, u, f, uf, pf)
+        for _ in range(args.warmup):
+            fstep()
+        barrier()
+        ms_fl = timed(fstep, args.steps)
+        _, _, res = ibfe.ib_fluid_step(fl, u, f, uf, pf, residuals=True)
+        # the step advances x and u in place: both are restored from copies
+        # outside the timed interval so every timed step starts from x^0, u^0
+        cell0, off0, u0 = cell.clone(), off.clone(), u.clone()
+        cs, os_, us = cell.clone(), off.clone(), u.clone()
+        pos_s = ibfe.Pos(cell=cs, off=os_)
+
+        def restore():
+            cs.copy_(cell0)
+            os_.copy_(off0)
+            us.copy_(u0)
+
+        def ibstep():
+            ibfe.ib_step(plan, fl, mats, pos_s, us, G, f, U, pf)
+
+        for _ in range(args.warmup):
+            restore()
+            ibstep()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, b in ev:
+            restore()
+            flush.zero_()
+            a.record(stream)
+            ibstep()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_st = [a.elapsed_time(b) for a, b in ev]
+        cells = n ** 3
+        t_fl, t_st = sum(ms_fl) / len(ms_fl), sum(ms_st) / len(ms_st)
+        fluid_line = {
+            "grid": [n, n, n], "rho": FLUID_RHO, "mu": FLUID_MU, "dt": FLUID_DT,
+            "multigrid": {"levels": fl.levels(), "helmholtz_cycles": fl.cycles()[0],
+                          "poisson_cycles": fl.cycles()[1],
+                          "smoothing": "red-black Gauss-Seidel, 2 pre + 2 post sweeps",
+                          "launch": "one CUDA graph per step"},
+            "fluid_step_ms": t_fl, "cells_per_s": cells / (t_fl * 1e-3),
+            "relative_residuals": {"helmholtz": res[0], "poisson": res[1]},
+            "ib_step_ms": t_st,
+            "ib_step_gauss_points_per_s": Q * world / (t_st * 1e-3),
+            "note": "ib_step = nodal force + spread at x^n, fluid step, interpolation of "
+                    "u^{n+1} at x^n, position update; x and u restored outside the timed "
+                    "interval"}
+        del fl, uf, cs, os_, us, cell0, off0, u0
+        barrier()
+
     # --- batched workload: 48 HO shells on their own grids, one graph -----
     batch_line = None
     if not args.no_batch:
@@ -488,6 +549,7 @@ def run_ours(args):
                        "note": "the same forward with the nodal quadrature rule of Section 4.4 "
                                "(coupling points = the N nodes; the force keeps the Gauss rule)"},
         "batched": batch_line,
+        "fluid": fluid_line,
         "adjoint_ms_per_step": t_adj,
         "adjoint_forward_ratio": t_adj / t_fwd,
         "roofline": roof,
@@ -524,9 +586,11 @@ def main():
     ap.add_argument("--workload", default="shell256", choices=["shell256", "shell128"],
                     help="shell128 (128^3 ventricle shell) is a small case for profiling")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-fluid", action="store_true",
+                    help="skip the fluid step and the explicit IB step")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
-    ap.add_argument("--profile-once", choices=["forward", "backward"],
+    ap.add_argument("--profile-once", choices=["forward", "backward", "fluid", "step"],
                     help="run one ib_forward (or ib_backward) between cudaProfilerStart/Stop "
                          "after warm-up, for ncu --profile-from-start off; prints no bench line")
     args = ap.parse_args()
@@ -560,6 +624,21 @@ def profile_once(args):
     gf = torch.from_numpy((rng.normal(size=p.u.shape) * 1e-3).astype(np.float32)).to(dev)
 
     ibfe.ib_plan_autotune(plan, mats, pos, u)   # the launch shapes the bench times
+    if args.profile_once in ("fluid", "step"):
+        fl = ibfe.Fluid(p.grid.n, p.grid.h, FLUID_RHO, FLUID_MU, FLUID_DT)
+        f = torch.from_numpy((rng.normal(size=p.u.shape) * 50.0).astype(np.float32)).to(dev)
+        if args.profile_once == "fluid":
+            run = lambda: ibfe.ib_fluid_step(fl, u, f)
+        else:
+            run = lambda: ibfe.ib_step(plan, fl, mats, pos, u.clone())
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        run()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return 0
     for _ in range(2):
         G = ibfe.ib_forward(plan, mats, pos, u)[0]
         if args.profile_once == "backward":

@@ -296,11 +296,13 @@ ib_status ib_batch_destroy(ib_batch* batch);
  * with (div u)(i) = sum_c (u^c(i+e_c) - u^c(i))/h, (grad p)^c(i) =
  * (p(i) - p(i-e_c))/h and the 7-point Lap_h = div_h grad_h; both solves by
  * geometric multigrid V-cycles (red-black Gauss-Seidel, 2 pre- and 2
- * post-sweeps; levels halve every dimension while all are even and the
- * largest exceeds 16; the coarsest is solved in one CTA's shared memory).
- * The cycle counts are fixed (default 2 Helmholtz, 8 Poisson), so a step
- * involves no host round trip; ib_fluid_step can report the residuals
- * reached.  Fields: u, f, u_next device Real [3][n2][n1][n0] (component c on
+ * post-sweeps; levels halve every dimension while all are even, none is
+ * below 4 and the largest exceeds 8; the coarsest is solved in one CTA's
+ * shared memory).
+ * The cycle counts are fixed (default 2 Helmholtz and 6 Poisson cycles in
+ * FP32, 3 and 12 in FP64), so a step involves no host round trip (without
+ * residuals it runs as one CUDA graph, captured per set of field pointers);
+ * ib_fluid_step can report the residuals reached.  Fields: u, f, u_next device Real [3][n2][n1][n0] (component c on
  * the lower c-faces, as everywhere in this API), p device Real [n2][n1][n0]
  * at cell centres with zero mean.  Real is float for the split precisions and
  * double for IB_FP64.  The box is periodic; the paper's no-slip walls are not
@@ -309,7 +311,8 @@ ib_status ib_batch_destroy(ib_batch* batch);
 typedef struct ib_fluid ib_fluid;
 
 /* Fluid solver for `grid` (every n_d even, 4..4096; IB_ERR_UNSUPPORTED for an
- * odd size or a coarsest level above 8192 cells) with density rho > 0,
+ * odd size or a coarsest level above 8192 cells, IB_ERR_CAPACITY for
+ * 3 n0 n1 n2 >= 2^31) with density rho > 0,
  * viscosity mu >= 0 and time step dt > 0.  Allocates its multigrid hierarchy
  * (about 1.6 field volumes) on the current device. */
 ib_status ib_fluid_create(const ib_grid* grid, int32_t precision, double rho, double mu,
@@ -318,6 +321,7 @@ ib_status ib_fluid_destroy(ib_fluid* fluid);
 /* V-cycles per Helmholtz solve (all three components together) and per
  * Poisson solve, each in [1, 100]. */
 ib_status ib_fluid_set_cycles(ib_fluid* fluid, int32_t helmholtz_cycles, int32_t poisson_cycles);
+ib_status ib_fluid_get_cycles(const ib_fluid* fluid, int32_t cycles[2]);
 /* Number of multigrid levels (the finest included). */
 ib_status ib_fluid_levels(const ib_fluid* fluid, int32_t* levels);
 /* One projection step: u_next (may alias u) and p (NULL: kept internally)

@@ -102,6 +102,7 @@ def _load():
         "ib_fluid_destroy": [vp],
         "ib_fluid_set_cycles": [vp, i32, i32],
         "ib_fluid_levels": [vp, C.POINTER(i32)],
+        "ib_fluid_get_cycles": [vp, C.POINTER(i32)],
         "ib_fluid_step": [vp, vp, vp, vp, vp, dp, vp],
         "ib_step": [vp, vp, C.POINTER(_Mat), i32, C.POINTER(_Pos), vp, vp, vp, vp, vp, vp],
     }
@@ -250,6 +251,12 @@ class Fluid:
         v = C.c_int32()
         _chk(_lib.ib_fluid_levels(self._h, C.byref(v)), "ib_fluid_levels")
         return int(v.value)
+
+    def cycles(self):
+        """[Helmholtz, Poisson] V-cycles per step."""
+        t = (C.c_int32 * 2)()
+        _chk(_lib.ib_fluid_get_cycles(self._h, t), "ib_fluid_get_cycles")
+        return list(t)
 
     def set_cycles(self, helmholtz: int, poisson: int):
         _chk(_lib.ib_fluid_set_cycles(self._h, int(helmholtz), int(poisson)),

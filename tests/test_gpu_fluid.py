@@ -69,6 +69,11 @@ def test_fluid_step_in_place_and_reproducible():
     c, pc, _ = ibfe.ib_fluid_step(fl, uin, fd, u_next=uin)
     assert c.data_ptr() == uin.data_ptr()
     assert torch.equal(c, a) and torch.equal(pc, pa)
+    # the graph replay (no residuals) and the direct launches (residuals)
+    # run the same kernels in the same order
+    d, pd, res = ibfe.ib_fluid_step(fl, ud, fd, residuals=True)
+    assert torch.equal(d, a) and torch.equal(pd, pa) and res[1] < 1e-5
+    assert fl.cycles() == [2, 6]
     # no force: the same as a zero force
     z, pz, _ = ibfe.ib_fluid_step(fl, ud, None)
     z2, pz2, _ = ibfe.ib_fluid_step(fl, ud, torch.zeros_like(fd))
@@ -77,8 +82,8 @@ def test_fluid_step_in_place_and_reproducible():
 
 def test_fluid_levels_and_argument_checks():
     from paper_2503_22695_gb300 import ibfe
-    assert ibfe.Fluid((256, 256, 256), 1 / 256, 1.0, 0.01, 1e-4).levels() == 5   # 256 .. 16
-    assert ibfe.Fluid((32, 16, 48), 1 / 32, 1.0, 0.01, 1e-4).levels() == 3      # 48 .. 12
+    assert ibfe.Fluid((256, 256, 256), 1 / 256, 1.0, 0.01, 1e-4).levels() == 6   # 256 .. 8
+    assert ibfe.Fluid((32, 16, 48), 1 / 32, 1.0, 0.01, 1e-4).levels() == 4      # .. (4, 2, 6)
     assert ibfe.Fluid((40, 40, 6), 1 / 40, 1.0, 0.01, 1e-4).levels() == 2       # (20, 20, 3)
     with pytest.raises(ibfe.IBError) as e:
         ibfe.Fluid((33, 32, 32), 1 / 32, 1.0, 0.01, 1e-4)
