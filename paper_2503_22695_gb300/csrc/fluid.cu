@@ -301,17 +301,20 @@ __global__ void __launch_bounds__(256) k_project(Real* __restrict__ u, const Rea
   u[2 * cells + t] -= scale * (pc - p[L.at(i, j, wrap_dn(k, L.n2))]);
 }
 
-// Fixed-shape sums: CTA b sums a contiguous chunk of x into part[b].
+// Fixed-shape sums: CTA b sums a contiguous chunk of x into part[b].  Each
+// thread accumulates its (about 64) elements in Real, the CTA's threads in
+// double: the sum only sets a mean that is removed, and on GB300 a double
+// add per element would make this pass FP64-bound.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_sums_l1(const Real* __restrict__ x, int n,
                                                  double* __restrict__ part) {
   __shared__ double sh[32];
   const int chunk = (n + gridDim.x - 1) / gridDim.x;
   const int e0 = blockIdx.x * chunk, e1 = min(n, e0 + chunk);
-  double s = 0.0;
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) s += double(x[e]);
-  s = block_sum_fl(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  Real s = Real(0);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) s += x[e];
+  const double t = block_sum_fl(double(s), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // Squared residual of A phi = rhs and squared rhs, one partial pair per CTA
