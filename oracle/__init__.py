@@ -142,6 +142,21 @@ class Model:
                                     C.byref(en)), "fe_force")
         return G, en.value
 
+    def penalty(self, x, nodes, kappa, weights=None):
+        """Penalty tethers of the solid boundary (Section 5: the fixed face of
+        Cook's membrane, the fixed tube of the aortic valve): each listed node
+        is pulled to its reference position by G_a = -kappa w_a (x_a - X_a),
+        w_a the lumped mass (volume weight of the node, the nodal-rule weight
+        of Section 4.4) unless weights are given; the energy is
+        kappa/2 sum_a w_a |x_a - X_a|^2.  Returns (G [3][N], energy)."""
+        x = _f64(x)
+        nodes = np.asarray(nodes, dtype=np.int64)
+        w = self.mass()[nodes] if weights is None else _f64(weights)
+        d = x[:, nodes] - self.X[:, nodes]
+        G = np.zeros((3, self.N))
+        G[:, nodes] = -kappa * w * d
+        return G, 0.5 * kappa * float(np.sum(w * np.sum(d * d, axis=0)))
+
     def fe_force_adj(self, x, v):
         x, v = _f64(x), _f64(v)
         Hv = np.empty((3, self.N))

@@ -824,3 +824,48 @@ def test_differentiation_workload_oracle_gradient_by_differences():
             fd = (loss(x0 + step * dx, th0 + step * dth) -
                   loss(x0 - step * dx, th0 - step * dth)) / (2 * step)
             assert an == pytest.approx(fd, rel=rel, abs=absol), step
+
+
+# ---------------------------------------------------------------------------
+# penalty tethers of the solid boundary (Section 5)
+# ---------------------------------------------------------------------------
+
+def _tethered(p):
+    """The nodes of the block's x-minimum face (the 'fixed left face')."""
+    return np.flatnonzero(p.X[0] <= p.X[0].min() + 1e-12)
+
+
+def test_penalty_zero_at_reference_and_closed_form_translation():
+    p = tiny_mesh(I.NEO_HOOKEAN, (0.5, 100.0))
+    m = oracle.Model(p)
+    nodes = _tethered(p)
+    kappa = 1e6
+    G, E = m.penalty(p.X, nodes, kappa)
+    assert np.abs(G).max() == 0.0 and E == 0.0
+    d = np.array([1e-3, -2e-3, 5e-4])[:, None]
+    G, E = m.penalty(p.X + d, nodes, kappa)
+    w = m.mass()[nodes]
+    np.testing.assert_allclose(G[:, nodes], -kappa * w * d, rtol=1e-10)  # (X + d) - X rounds
+    assert np.abs(np.delete(G, nodes, axis=1)).max() == 0.0
+    assert E == pytest.approx(0.5 * kappa * w.sum() * float(np.sum(d * d)), rel=1e-10)
+    # with the elastic force: a rigid translation strains nothing, so the
+    # total force is the tethers' alone
+    Ge, _ = m.fe_force(p.X + d)
+    assert np.abs((Ge + G).sum(axis=1) + kappa * w.sum() * d[:, 0]).max() < 1e-9 * kappa * w.sum()
+
+
+def test_penalty_force_is_minus_energy_gradient():
+    p = tiny_mesh(I.NEO_HOOKEAN, (0.5, 100.0))
+    m = oracle.Model(p)
+    nodes = _tethered(p)
+    rng = np.random.default_rng(31)
+    w = rng.uniform(0.5, 2.0, size=len(nodes)) * p.grid.h ** 2
+    G, _ = m.penalty(p.x, nodes, 5e6, weights=w)
+    eps = 1e-6 * p.grid.h
+    for _ in range(10):
+        a, i = rng.choice(nodes), rng.integers(3)
+        xp, xm = p.x.copy(), p.x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = -(m.penalty(xp, nodes, 5e6, w)[1] - m.penalty(xm, nodes, 5e6, w)[1]) / (2 * eps)
+        assert G[i, a] == pytest.approx(fd, rel=1e-6)
