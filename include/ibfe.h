@@ -246,6 +246,22 @@ ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
 ib_status ib_plan_autotune(ib_plan* plan, const ib_material* mats, int32_t n_mats,
                            const ib_pos* x, const void* u, void* stream, int32_t tuning[4]);
 
+/* Penalty tethers of the solid boundary (Section 5: Cook's membrane's fixed
+ * face, kappa = 1e6; the aortic valve's fixed outer tube, kappa = 5e6).  From
+ * this call on, the nodal force of the plan's entry points (ib_fe_force,
+ * ib_forward, ib_step) includes G_a -= kappa w_a (x_a - X_a) for each listed
+ * node a, and the energy kappa/2 sum w_a |x_a - X_a|^2; the force adjoints
+ * (ib_fe_force_adj, ib_backward) include its Jacobian, -kappa w_a on the
+ * listed nodes (no parameter gradient for kappa).  nodes: device int32 [n],
+ * distinct node indices (entries outside [0, N) are ignored); weights: device
+ * Real [n], or NULL for the lumped mass m_a (the volume weight of the node).
+ * Both arrays are the caller's and must stay valid while set.  n = 0 or
+ * kappa = 0 removes the tethers.  Not available to the batched form.
+ * Errors: IB_ERR_INVALID_ARG (n < 0 or > N, nodes NULL with n > 0, kappa
+ * negative or not finite). */
+ib_status ib_plan_set_penalty(ib_plan* plan, const int32_t* nodes, int32_t n,
+                              const void* weights, double kappa);
+
 /* ---------------------------------------------------------------------------
  * Batched form: many independent structures, each with its own mesh, grid
  * and material table (a parameter sweep, for instance), run together.  The

@@ -37,7 +37,7 @@ void free_plan(ib_plan* p) {
                   p->tile_list, p->tile_list_near, p->tile_bcount, p->tile_counters,
                   p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
                   p->p_off, p->p_val, p->p_idx, p->gq_a, p->gq_b, p->epart, p->ered,
-                  p->dstatus, p->node_tmp};
+                  p->dstatus, p->node_tmp, p->pen_part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
@@ -323,7 +323,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->node_tmp, rs * 6 * (size_t)N) &&
               dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
               dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
-              dalloc(&p->ered, 8 * kParamRow * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16);
+              dalloc(&p->ered, 8 * kParamRow * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16) &&
+              dalloc(&p->pen_part, 8 * penalty_scratch_doubles());
   if (!good) {
     free_plan(p);
     cudaGetLastError();
@@ -385,15 +386,19 @@ ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, energy != nullptr, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK) st = launch_penalty(p, x, G, energy != nullptr, s);
   if (st == IB_OK && energy) {
     st = do_reduce(p, 1, n_mats, s);
     double red[kParamRow * IB_MAX_MATERIALS];
+    double pen = 0.0;
     if (st == IB_OK &&
         (!ok(cudaMemcpyAsync(red, p->ered, sizeof(red), cudaMemcpyDeviceToHost, s)) ||
+         (penalty_on(p) && !ok(cudaMemcpyAsync(&pen, penalty_energy_dev(p), sizeof(double),
+                                               cudaMemcpyDeviceToHost, s))) ||
          !ok(cudaStreamSynchronize(s))))
       st = IB_ERR_CUDA;
     if (st == IB_OK) {
-      double en = 0.0;
+      double en = pen;
       for (int m = 0; m < n_mats; ++m) en += red[m * kParamRow];
       *energy = en;
     }
@@ -444,6 +449,7 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
     st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK) st = launch_penalty(p, x, G, false, s);
   if (st == IB_OK) {
     Stage sc(p, IB_STAGE_POINTS, s, 2);
     st = launch_point_values(p, G, s);
@@ -472,6 +478,7 @@ ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_m
     st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
+  if (st == IB_OK) st = launch_penalty(p, x, G, false, s);
   if (st == IB_OK) st = do_points_sorted(p, x, G, s);
   if (st == IB_OK) st = do_spread(p, 1.0 / (h * h * h), f, s);
   // u^n -> u^{n+1} in place
@@ -536,6 +543,7 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
   if (st == IB_OK && force && gparams) st = do_reduce(p, kParamRow, n_mats, s);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx);
+  if (st == IB_OK && force) st = launch_penalty_adj(p, gGt, gx, s);
   if (st == IB_OK && gparams) {
     const size_t pb = sizeof(double) * kParamRow * (size_t)n_mats;
     if (!ok(force ? cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)
@@ -592,6 +600,7 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, params, s);
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s);
+  if (st == IB_OK) st = launch_penalty_adj(p, v, Hv, s);
   if (st == IB_OK && params) st = do_reduce(p, kParamRow, n_mats, s);
   return check_launch(st);
 }

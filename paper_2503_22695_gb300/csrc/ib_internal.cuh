@@ -147,6 +147,12 @@ struct ib_plan {
   void* p_val;           // Real [3][Q]
   int32_t* p_idx;        // [Q] original gq
   void* node_tmp;        // Real [2][3][N] nodal work vectors (fused backward)
+  // penalty tethers (ib_plan_set_penalty; caller-owned device arrays)
+  const int32_t* pen_nodes;
+  int pen_n;
+  const void* pen_w;
+  double pen_kappa;
+  double* pen_part;      // energy partials and their sum
   void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
   void* gq_b;            // Real [3][Q]
   double* epart;         // [kParamRow][E] per-element partial sums
@@ -220,6 +226,13 @@ ib_status interp_prepare(ib_plan* p);
 ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats,
                              const ib_pos* x, const void* v, void* Hv, bool params,
                              cudaStream_t s);
+
+// penalty.cu: tethers of the solid boundary, applied after the nodal gather
+bool penalty_on(const ib_plan* p);
+ib_status launch_penalty(ib_plan* p, const ib_pos* x, void* G, bool energy, cudaStream_t s);
+const double* penalty_energy_dev(const ib_plan* p);
+ib_status launch_penalty_adj(ib_plan* p, const void* v, void* Hv, cudaStream_t s);
+size_t penalty_scratch_doubles();
 
 // fluid.cu
 ib_status fluid_step_async(ib_fluid* fl, const void* u, const void* f, void* u_next, void* p,

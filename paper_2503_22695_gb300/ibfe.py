@@ -97,6 +97,7 @@ def _load():
         "ib_fe_energy_noalloc": [C.POINTER(_Mesh), C.POINTER(_Mat), i32, C.POINTER(_Pos),
                                  C.c_double, vp, vp],
         "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
+        "ib_plan_set_penalty": [vp, vp, i32, vp, C.c_double],
         "ib_fluid_create": [C.POINTER(_Grid), i32, C.c_double, C.c_double, C.c_double, vp,
                             C.POINTER(vp)],
         "ib_fluid_destroy": [vp],
@@ -448,6 +449,22 @@ def ib_backward(plan: Plan, mats, x: Pos, u=None, G=None, gG=None, gf=None, gU=N
                           _ptr(gG), _ptr(gf), _ptr(gU), _ptr(gx), _ptr(gu), _ptr(gp),
                           _stream()), "ib_backward")
     return gx, gu, gp
+
+
+def ib_plan_set_penalty(plan: Plan, nodes=None, kappa: float = 0.0, weights=None):
+    """Tether the listed nodes (device int32 [n]) to their reference positions
+    with stiffness kappa (weights: device Real [n], default the lumped mass);
+    nodes=None removes the tethers.  The plan keeps the tensors alive."""
+    if nodes is None or nodes.numel() == 0:
+        plan._pen = None
+        _chk(_lib.ib_plan_set_penalty(plan.handle, None, 0, None, 0.0), "ib_plan_set_penalty")
+        return
+    _check(nodes, torch.int32, (-1,), "nodes")
+    if weights is not None:
+        _check(weights, plan.dtype, (nodes.numel(),), "weights")
+    plan._pen = (nodes, weights)
+    _chk(_lib.ib_plan_set_penalty(plan.handle, _ptr(nodes), int(nodes.numel()), _ptr(weights),
+                                  float(kappa)), "ib_plan_set_penalty")
 
 
 def ib_plan_get_tuning(plan: Plan):
