@@ -46,7 +46,7 @@ class _Grid(C.Structure):
 class _Mesh(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_elems", C.c_int32),
                 ("conn", C.c_void_p), ("X", C.c_void_p), ("fibres", C.c_void_p),
-                ("mat_id", C.c_void_p)]
+                ("mat_id", C.c_void_p), ("elem", C.c_int32)]
 
 
 class _Mats(C.Structure):
@@ -92,8 +92,10 @@ class Model:
         self.mat_id = None if mat_id is None else np.ascontiguousarray(mat_id, dtype=np.int32)
         self.N = self.X.shape[1]
         self.E = self.conn.shape[1]
+        self.elem = 1 if self.conn.shape[0] == 4 else 0     # tetrahedra or hexahedra
+        self.nq = 4 if self.elem == 1 else 8                # points of the element rule
         self._mesh = _Mesh(self.N, self.E, _p(self.conn), _p(self.X), _p(self.fibres),
-                           _p(self.mat_id))
+                           _p(self.mat_id), self.elem)
         if grid is not None:
             self._grid = _Grid((C.c_int32 * 3)(*grid.n), float(grid.h),
                                (C.c_double * 3)(*[float(v) for v in grid.origin]))
@@ -129,8 +131,8 @@ class Model:
 
     def gauss_info(self, x):
         x = _f64(x)
-        w = np.empty((8, self.E))
-        J = np.empty((8, self.E))
+        w = np.empty((self.nq, self.E))
+        J = np.empty((self.nq, self.E))
         self._chk(lib().or_gauss_info(C.byref(self._mesh), _p(x), _p(w), _p(J)), "gauss_info")
         return w, J
 
@@ -189,7 +191,7 @@ class Model:
     def interp(self, x, u, want_gauss=False):
         x, u = _f64(x), _f64(u)
         U = np.empty((3, self.N))
-        Uq = np.empty((3, 8, self.E)) if want_gauss else None
+        Uq = np.empty((3, self.nq, self.E)) if want_gauss else None
         self._chk(lib().or_interp(C.byref(self._grid), C.byref(self._mesh), _p(x), _p(u), _p(U),
                                   _p(Uq)), "interp")
         return (U, Uq) if want_gauss else U

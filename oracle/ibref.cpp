@@ -222,11 +222,22 @@ const double kUnitX[3] = {1.0, 0.0, 0.0};
 const double kUnitY[3] = {0.0, 1.0, 0.0};
 
 // ---------------------------------------------------------------------------
-// Trilinear hexahedron and the 2x2x2 Gauss rule (the element rule H_q of
-// Section 4.4).  VTK corner order.
+// Elements and their rules (the element rule H_q of Section 4.4):
+//   elem 0: trilinear hexahedron, VTK corner order, 2x2x2 Gauss rule at
+//           +-1/sqrt(3) with unit weights;
+//   elem 1: linear tetrahedron (P1; VTK order, positive volume), N_0 =
+//           1 - xi - eta - zeta, N_1 = xi, N_2 = eta, N_3 = zeta on the unit
+//           reference tetrahedron, with the symmetric 4-point rule of degree 2:
+//           barycentric coordinates (a, b, b, b) and permutations,
+//           a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights 1/24 each
+//           (the reference volume 1/6 in four).  The force integrand of P1 is
+//           constant per element, so this rule gives it exactly too.
 // ---------------------------------------------------------------------------
 const int kCorner[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
                            {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+int nc_of(const or_mesh* m) { return m->elem == 1 ? 4 : 8; }  // corners
+int nq_of(const or_mesh* m) { return m->elem == 1 ? 4 : 8; }  // rule points
 
 struct GaussPt {
   double N[8];
@@ -234,20 +245,33 @@ struct GaussPt {
   double wj0;
 };
 
-bool gauss_point(const double Xe[8][3], int q, GaussPt& g) {
-  double xi[3];
-  for (int d = 0; d < 3; ++d) xi[d] = (((q >> d) & 1) ? 1.0 : -1.0) / std::sqrt(3.0);
-  double dNdxi[8][3];
-  for (int a = 0; a < 8; ++a) {
-    double f[3];
-    for (int d = 0; d < 3; ++d) f[d] = 1.0 + kCorner[a][d] * xi[d];
-    g.N[a] = f[0] * f[1] * f[2] / 8.0;
-    dNdxi[a][0] = kCorner[a][0] * f[1] * f[2] / 8.0;
-    dNdxi[a][1] = kCorner[a][1] * f[0] * f[2] / 8.0;
-    dNdxi[a][2] = kCorner[a][2] * f[0] * f[1] / 8.0;
+bool gauss_point(const or_mesh* m, const double Xe[8][3], int q, GaussPt& g) {
+  const int nc = nc_of(m);
+  double dNdxi[8][3] = {{0}};
+  double wq = 1.0;
+  for (int a = 0; a < 8; ++a) g.N[a] = 0.0;
+  if (m->elem == 1) {
+    const double ta = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, tb = (5.0 - std::sqrt(5.0)) / 20.0;
+    for (int a = 0; a < 4; ++a) g.N[a] = a == q ? ta : tb;
+    for (int d = 0; d < 3; ++d) {
+      dNdxi[0][d] = -1.0;
+      dNdxi[1 + d][d] = 1.0;
+    }
+    wq = 1.0 / 24.0;
+  } else {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) xi[d] = (((q >> d) & 1) ? 1.0 : -1.0) / std::sqrt(3.0);
+    for (int a = 0; a < 8; ++a) {
+      double f[3];
+      for (int d = 0; d < 3; ++d) f[d] = 1.0 + kCorner[a][d] * xi[d];
+      g.N[a] = f[0] * f[1] * f[2] / 8.0;
+      dNdxi[a][0] = kCorner[a][0] * f[1] * f[2] / 8.0;
+      dNdxi[a][1] = kCorner[a][1] * f[0] * f[2] / 8.0;
+      dNdxi[a][2] = kCorner[a][2] * f[0] * f[1] / 8.0;
+    }
   }
   double J0[3][3] = {{0}};
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < nc; ++a)
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) J0[i][j] += Xe[a][i] * dNdxi[a][j];
   double det = J0[0][0] * (J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1]) -
@@ -271,14 +295,18 @@ bool gauss_point(const double Xe[8][3], int q, GaussPt& g) {
       for (int j = 0; j < 3; ++j) s += dNdxi[a][j] * inv[j][i];
       g.dNdX[a][i] = s;
     }
-  g.wj0 = 1.0 * det;  // unit Gauss weights
+  g.wj0 = wq * det;
   return true;
 }
 
-// Gather an element's 8 corners of a [3][N] array.
+// Gather an element's corners of a [3][N] array (zeros past the last corner).
 void gather(const or_mesh* m, const double* A, int e, double out[8][3]) {
   int64_t E = m->n_elems, N = m->n_nodes;
   for (int a = 0; a < 8; ++a) {
+    if (a >= nc_of(m)) {
+      for (int i = 0; i < 3; ++i) out[a][i] = 0.0;
+      continue;
+    }
     int64_t node = m->conn[(int64_t)a * E + e];
     for (int i = 0; i < 3; ++i) out[a][i] = A[(int64_t)i * N + node];
   }
@@ -286,7 +314,8 @@ void gather(const or_mesh* m, const double* A, int e, double out[8][3]) {
 
 bool check_mesh(const or_mesh* m) {
   if (!m || m->n_nodes <= 0 || m->n_elems < 0 || !m->conn || !m->X) return false;
-  for (int64_t k = 0; k < 8LL * m->n_elems; ++k)
+  if (m->elem != 0 && m->elem != 1) return false;
+  for (int64_t k = 0; k < (int64_t)nc_of(m) * m->n_elems; ++k)
     if (m->conn[k] < 0 || m->conn[k] >= m->n_nodes) return false;
   return true;
 }
@@ -397,12 +426,12 @@ int or_gauss_info(const or_mesh* m, const double* x, double* wj0, double* detF) 
     double Xe[8][3], xe[8][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       wj0[q * E + e] = gp.wj0;
       double F[3][3] = {{0}};
-      for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < nc_of(m); ++a)
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j) F[i][j] += xe[a][i] * gp.dNdX[a][j];
       detF[q * E + e] = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
@@ -423,10 +452,10 @@ int or_lumped_mass(const or_mesh* m, double* mass) {
   for (int e = 0; e < E; ++e) {
     double Xe[8][3];
     gather(m, m->X, e, Xe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
-      for (int a = 0; a < 8; ++a) mass[m->conn[a * E + e]] += gp.N[a] * gp.wj0;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
+      for (int a = 0; a < nc_of(m); ++a) mass[m->conn[a * E + e]] += gp.N[a] * gp.wj0;
     }
   }
   return 0;
@@ -450,16 +479,16 @@ int or_fe_force(const or_mesh* m, const or_mats* mats, const double* x, double* 
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     fibres_of(m, e, ef, es);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double F[3][3] = {{0}}, P[3][3], psi;
-      for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < nc_of(m); ++a)
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j) F[i][j] += xe[a][i] * gp.dNdX[a][j];
       stress_t<double>(model, p, F, ef, es, P, psi);
       en += psi * gp.wj0;
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < nc_of(m); ++a) {
         int64_t node = m->conn[a * E + e];
         for (int i = 0; i < 3; ++i) {
           double s = 0.0;
@@ -492,11 +521,11 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
     gather(m, x, e, xe);
     gather(m, v, e, ve);
     fibres_of(m, e, ef, es);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double F[3][3] = {{0}}, dF[3][3] = {{0}};
-      for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < nc_of(m); ++a)
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j) {
             F[i][j] += xe[a][i] * gp.dNdX[a][j];
@@ -508,7 +537,7 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) Fd[i][j] = Dual(F[i][j], dF[i][j]);
       stress_t<Dual>(model, pd, Fd, ef, es, Pd, psid);
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < nc_of(m); ++a) {
         int64_t node = m->conn[a * E + e];
         for (int i = 0; i < 3; ++i) {
           double s = 0.0;
@@ -556,14 +585,14 @@ int or_spread(const or_grid* g, const or_mesh* m, const double* x, const double*
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, Fn.data(), e, Fe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double chi[3], Pq[3];
       point_of(gp, xe, chi);
       for (int i = 0; i < 3; ++i) {
         Pq[i] = 0.0;
-        for (int a = 0; a < 8; ++a) Pq[i] += gp.N[a] * Fe[a][i];
+        for (int a = 0; a < nc_of(m); ++a) Pq[i] += gp.N[a] * Fe[a][i];
         Pq[i] *= gp.wj0;
       }
       for (int c = 0; c < 3; ++c) {
@@ -585,7 +614,7 @@ int or_spread(const or_grid* g, const or_mesh* m, const double* x, const double*
 int or_spread_at(const or_grid* g, const or_mesh* m, const double* x, const double* G,
                  int64_t n_sel, const int32_t* comp, const int32_t* idx, double* out) {
   if (!check_grid(g) || !check_mesh(m)) return -1;
-  int64_t E = m->n_elems, N = m->n_nodes, Q = 8 * E;
+  int64_t E = m->n_elems, N = m->n_nodes, Q = (int64_t)nq_of(m) * E;
   std::vector<double> mass(N);
   int rc = or_lumped_mass(m, mass.data());
   if (rc) return rc;
@@ -595,15 +624,15 @@ int or_spread_at(const or_grid* g, const or_mesh* m, const double* x, const doub
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, G, e, Ge);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double c3[3];
       point_of(gp, xe, c3);
       for (int i = 0; i < 3; ++i) {
         chi[3 * (q * E + e) + i] = c3[i];
         double s = 0.0;
-        for (int a = 0; a < 8; ++a) s += gp.N[a] * Ge[a][i] / mass[m->conn[a * E + e]];
+        for (int a = 0; a < nc_of(m); ++a) s += gp.N[a] * Ge[a][i] / mass[m->conn[a * E + e]];
         Pq[3 * (q * E + e) + i] = s * gp.wj0;
       }
     }
@@ -642,9 +671,9 @@ int or_interp(const or_grid* g, const or_mesh* m, const double* x, const double*
     double Xe[8][3], xe[8][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double chi[3], UIB[3];
       point_of(gp, xe, chi);
       for (int c = 0; c < 3; ++c) {
@@ -657,9 +686,9 @@ int or_interp(const or_grid* g, const or_mesh* m, const double* x, const double*
               acc += u[face_index(g, c, s.idx[0][kx], s.idx[1][ky], s.idx[2][kz])] *
                      s.w[0][kx] * s.w[1][ky] * s.w[2][kz];
         UIB[c] = acc;
-        if (Uq) Uq[(int64_t)c * 8 * E + q * E + e] = acc;
+        if (Uq) Uq[(int64_t)c * nq_of(m) * E + q * E + e] = acc;
       }
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < nc_of(m); ++a) {
         int64_t node = m->conn[a * E + e];
         for (int c = 0; c < 3; ++c) U[c * N + node] += gp.N[a] * gp.wj0 * UIB[c];
       }
@@ -689,14 +718,14 @@ int or_spread_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, G, e, Ge);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double chi[3], Pq[3], gP[3], gchi[3] = {0, 0, 0};
       point_of(gp, xe, chi);
       for (int i = 0; i < 3; ++i) {
         Pq[i] = 0.0;
-        for (int a = 0; a < 8; ++a) Pq[i] += gp.N[a] * Ge[a][i] / mass[m->conn[a * E + e]];
+        for (int a = 0; a < nc_of(m); ++a) Pq[i] += gp.N[a] * Ge[a][i] / mass[m->conn[a * E + e]];
         Pq[i] *= gp.wj0;
       }
       for (int c = 0; c < 3; ++c) {
@@ -717,7 +746,7 @@ int or_spread_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
         gchi[1] += Pq[c] * d1 / (h3 * h);
         gchi[2] += Pq[c] * d2 / (h3 * h);
       }
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < nc_of(m); ++a) {
         int64_t node = m->conn[a * E + e];
         for (int c = 0; c < 3; ++c) {
           gG[c * N + node] += gp.N[a] * gp.wj0 * gP[c] / mass[node];
@@ -749,14 +778,14 @@ int or_interp_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, gU, e, gUe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double chi[3], gq[3], gchi[3] = {0, 0, 0};
       point_of(gp, xe, chi);
       for (int i = 0; i < 3; ++i) {
         gq[i] = 0.0;
-        for (int a = 0; a < 8; ++a) gq[i] += gp.N[a] * gUe[a][i] / mass[m->conn[a * E + e]];
+        for (int a = 0; a < nc_of(m); ++a) gq[i] += gp.N[a] * gUe[a][i] / mass[m->conn[a * E + e]];
         gq[i] *= gp.wj0;
       }
       for (int c = 0; c < 3; ++c) {
@@ -778,7 +807,7 @@ int or_interp_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
         gchi[2] += gq[c] * d2 / h;
       }
       if (gx)
-        for (int a = 0; a < 8; ++a) {
+        for (int a = 0; a < nc_of(m); ++a) {
           int64_t node = m->conn[a * E + e];
           for (int c = 0; c < 3; ++c) gx[c * N + node] += gp.N[a] * gchi[c];
         }
@@ -933,9 +962,9 @@ int64_t or_support_count(const or_grid* g, const or_mesh* m, const double* x) {
     double Xe[8][3], xe[8][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
-      if (!gauss_point(Xe, q, gp)) return -2;
+      if (!gauss_point(m, Xe, q, gp)) return -2;
       double chi[3];
       point_of(gp, xe, chi);
       for (int c = 0; c < 3; ++c) {

@@ -98,7 +98,8 @@ class Problem:
 
     @property
     def n_gauss(self) -> int:
-        return 8 * self.n_elems
+        """Points of the element rule: 8 per hexahedron, 4 per tetrahedron."""
+        return (4 if self.conn.shape[0] == 4 else 8) * self.n_elems
 
 
 # ----------------------------------------------------------------------------
@@ -145,6 +146,30 @@ def _orient(conn: np.ndarray, X: np.ndarray) -> np.ndarray:
         conn = conn.copy()
         conn[:, bad] = conn[perm][:, bad]
     return conn
+
+
+# The six tetrahedra of a hexahedron around its 0-6 diagonal (VTK corners):
+# the paths 0->1->2->6, 0->1->5->6, 0->3->2->6, 0->3->7->6, 0->4->5->6,
+# 0->4->7->6.  Hexahedra of one structured grid all split this way agree on
+# every shared face diagonal, so the tetrahedral mesh is conforming.
+_HEX_TETS = ((0, 1, 2, 6), (0, 1, 5, 6), (0, 3, 2, 6), (0, 3, 7, 6), (0, 4, 5, 6), (0, 4, 7, 6))
+
+
+def hex_to_tets(conn: np.ndarray, X: np.ndarray, *per_elem):
+    """Split hexahedra [8][E] into tetrahedra [4][6E] with positive volume
+    (two corners swapped where the triple product is negative); per-element
+    arrays ([k][E] or [E]) are repeated for the six children."""
+    E = conn.shape[1]
+    tets = np.stack([conn[list(t)] for t in _HEX_TETS], axis=2).reshape(4, 6 * E)
+    p0 = X[:, tets[0]]
+    vol = np.einsum("ie,ie->e", np.cross((X[:, tets[1]] - p0).T, (X[:, tets[2]] - p0).T).T,
+                    X[:, tets[3]] - p0)
+    flip = vol < 0
+    tets[1, flip], tets[2, flip] = tets[2, flip].copy(), tets[1, flip].copy()
+    out = [np.ascontiguousarray(tets)]
+    for a in per_elem:
+        out.append(np.repeat(a, 6, axis=-1))
+    return tuple(out)
 
 
 def box_block(nx: int, ny: int, nz: int, edge: float, centre) -> tuple:
@@ -453,6 +478,15 @@ def material_mix_problem(seed: int = 6000, n: int = 64, dims=(30, 20, 4), models
     mats = [Material(m, tuple(params[m]), Ta[i]) for i, m in enumerate(models)]
     mat_id = np.arange(conn.shape[1]) % len(models)
     return _finish("mix", grid, conn, X, fib, mat_id, mats, x, 4, rng, fp64)
+
+
+def tet_problem(base: Problem) -> Problem:
+    """The same structure and inputs with every hexahedron split into six
+    linear tetrahedra (the element of the paper's valve meshes)."""
+    conn, fib, mid = hex_to_tets(base.conn, base.X.astype(np.float64), base.fibres, base.mat_id)
+    return dataclasses.replace(base, name=base.name + "-tet", conn=conn.astype(np.int32),
+                               fibres=np.ascontiguousarray(fib.astype(base.fibres.dtype)),
+                               mat_id=np.ascontiguousarray(mid.astype(np.int32)))
 
 
 def batch_problems(seed: int = 5000, count: int = 48, sizes=(32, 64, 96, 128),

@@ -869,3 +869,98 @@ def test_penalty_force_is_minus_energy_gradient():
         xm[i, a] -= eps
         fd = -(m.penalty(xp, nodes, 5e6, w)[1] - m.penalty(xm, nodes, 5e6, w)[1]) / (2 * eps)
         assert G[i, a] == pytest.approx(fd, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# linear tetrahedra (P1) with the 4-point rule
+# ---------------------------------------------------------------------------
+
+def tiny_tets(model=I.HO, params=I.HO_DEFAULT, seed=7, blocks=(2, 2, 1)):
+    return I.tet_problem(tiny_mesh(model, params, seed=seed, blocks=blocks))
+
+
+def test_tet_rule_mass_and_volume():
+    """The 4-point rule's weights sum to the element volume and each node's
+    lumped mass is a quarter of its elements' volumes (P1 row sums)."""
+    p = tiny_tets()
+    m = oracle.Model(p)
+    X = p.X
+    w, _ = m.gauss_info(X)
+    vol = np.zeros(p.n_elems)
+    for e in range(p.n_elems):
+        a, b, c, d = (X[:, p.conn[k, e]] for k in range(4))
+        vol[e] = np.dot(np.cross(b - a, c - a), d - a) / 6.0
+    assert (vol > 0).all()
+    np.testing.assert_allclose(w.sum(axis=0), vol, rtol=1e-13)
+    np.testing.assert_allclose(w, np.broadcast_to(vol / 4, w.shape), rtol=1e-13)
+    mass = np.zeros(p.n_nodes)
+    for k in range(4):
+        np.add.at(mass, p.conn[k], vol / 4)
+    np.testing.assert_allclose(m.mass(), mass, rtol=1e-13)
+    # six tetrahedra fill each cube of the block exactly
+    assert vol.sum() == pytest.approx(2 * 2 * 1 * p.grid.h ** 3, rel=1e-13)
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_tet_patch_test_and_energy_gradient(model, params):
+    """P1 patch test: under an affine deformation every element has the same
+    F, so interior nodes carry no force; G = -dE/dx by differences on a
+    perturbed mesh; zero force at the reference and under rigid motion."""
+    p = tiny_tets(model, params, blocks=(2, 2, 2))
+    p.fibres = np.ascontiguousarray(np.repeat(p.fibres[:, :1], p.n_elems, axis=1))  # homogeneous
+    m = oracle.Model(p)
+    A = np.eye(3) + np.array([[0.05, 0.02, -0.01], [0.0, -0.03, 0.04], [0.01, 0.0, 0.02]])
+    x = A @ (p.X - 0.5) + 0.5
+    G, _ = m.fe_force(x)
+    _, detF = m.gauss_info(x)
+    np.testing.assert_allclose(detF, np.linalg.det(A), rtol=1e-12)
+    X = p.X
+    interior = np.flatnonzero(np.all([(X[d] > X[d].min() + 1e-12) & (X[d] < X[d].max() - 1e-12)
+                                      for d in range(3)], axis=0))
+    assert len(interior) > 0
+    assert np.abs(G[:, interior]).max() < 1e-10 * np.abs(G).max()
+    scale = params[-1] * p.grid.h ** 2
+    G0, E0 = m.fe_force(X)
+    assert np.abs(G0).max() < 1e-12 * scale and abs(E0) < 1e-15
+    Q = rot(np.random.default_rng(6))
+    G1, E1 = m.fe_force(Q @ (X - 0.5) + 0.5)
+    assert np.abs(G1).max() < 1e-11 * scale and abs(E1) < 1e-15
+    x = p.x
+    G, _ = m.fe_force(x)
+    eps = 1e-6 * p.grid.h
+    rng = np.random.default_rng(12)
+    for _ in range(8):
+        a, i = rng.integers(p.n_nodes), rng.integers(3)
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = -(m.fe_force(xp)[1] - m.fe_force(xm)[1]) / (2 * eps)
+        assert G[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-8 * np.abs(G).max())
+
+
+def test_tet_adjoints_and_transfer_identities():
+    """On the tetrahedral mesh: the force adjoint by differences, the spread
+    against the brute-force sum over every face, force conservation, and the
+    discrete adjointness of spreading and interpolation."""
+    p = tiny_tets()
+    m = oracle.Model(p)
+    x = p.x
+    rng = np.random.default_rng(13)
+    v = rng.normal(size=x.shape)
+    Hv, _ = m.fe_force_adj(x, v)
+    eps = 1e-7 * p.grid.h
+    fd = (m.fe_force(x + eps * v)[0] - m.fe_force(x - eps * v)[0]) / (2 * eps)
+    np.testing.assert_allclose(Hv, fd, rtol=1e-5, atol=1e-6 * np.abs(Hv).max())
+    G = rng.normal(size=x.shape)
+    f = m.spread(x, G)
+    n0, n1, n2 = p.grid.n
+    comp = np.repeat(np.arange(3), n0 * n1 * n2).astype(np.int32)
+    kk, jj, ii = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    idx = np.tile(np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1), (3, 1))
+    np.testing.assert_allclose(f.ravel(), m.spread_at(x, G, comp, idx), rtol=1e-12,
+                               atol=1e-12 * np.abs(f).max())
+    h3 = p.grid.h ** 3
+    np.testing.assert_allclose(f.sum(axis=(1, 2, 3)) * h3, G.sum(axis=1), rtol=1e-12)
+    u = rng.normal(size=(3, n2, n1, n0))
+    U = m.interp(x, u)
+    assert h3 * np.sum(f * u) == pytest.approx(np.sum(G * U), rel=1e-12)
