@@ -104,12 +104,20 @@ typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_pr
  * column 0, zeros up to column 8, d/dT_a in column 9. */
 #define IB_PARAM_ROW 10
 
+/* Element types.  IB_ELEM_HEX8: trilinear hexahedra, VTK corner order, the
+ * 2x2x2 Gauss rule (8 coupling points per element).  IB_ELEM_TET4: linear
+ * tetrahedra (the element of the paper's valve meshes, Section 5), VTK order
+ * with positive volume, the symmetric 4-point rule of degree 2 (4 coupling
+ * points per element); the P1 force is evaluated exactly at the centroid. */
+typedef enum { IB_ELEM_HEX8 = 0, IB_ELEM_TET4 = 1 } ib_elem;
+
 typedef struct {
   int32_t n_nodes, n_elems;
-  const int32_t* conn;   /* device [8][n_elems], VTK hexahedron order */
+  const int32_t* conn;   /* device [8][n_elems] (hexahedra) or [4][n_elems] (tetrahedra) */
   const void* X;         /* device Real [3][n_nodes] reference coordinates */
   const void* fibres;    /* device Real [6][n_elems]: e_f then e_s, or NULL (e_f = x, e_s = y) */
   const int32_t* mat_id; /* device [n_elems] index into the material table, or NULL (all 0) */
+  int32_t elem_type;     /* ib_elem; 0 (hexahedra) when zero-initialised */
 } ib_mesh;
 
 typedef struct {
@@ -361,8 +369,8 @@ ib_status ib_step(ib_plan* plan, ib_fluid* fluid, const ib_material* mats, int32
                   const ib_pos* x, void* u, void* G, void* f, void* U, void* p, void* stream);
 
 /* Total elastic energy sum_{e,q} Psi(F_q) w_q j0 of an FP32 split-position
- * mesh, without a plan and without allocating anything, for callers that
- * cannot call cudaMalloc: code running while a CUDA graph is captured on its
+ * hexahedral mesh (IB_ERR_UNSUPPORTED for tetrahedra), without a plan and
+ * without allocating anything, for callers that cannot call cudaMalloc: code running while a CUDA graph is captured on its
  * stream, runtimes that give all device memory to a fixed pool up front, or
  * loops that must not enter the allocator.  The paper has no counterpart of
  * this entry point; it is a service of this library.

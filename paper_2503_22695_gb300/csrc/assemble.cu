@@ -40,22 +40,23 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
 }
 
 // out[(a*NC + c)*E + e] = sum_q N_a(xi_q) vals[c][q*E + e]
-template <typename Real, int NC>
+template <typename Real, int NC, int kEl>
 __global__ void __launch_bounds__(256) k_elem_project(const Real* __restrict__ vals, int E,
                                                       Real* __restrict__ out) {
+  using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  const int64_t Q = 8LL * E;
+  const int64_t Q = (int64_t)EL::Q * E;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    Real v[8];
+    Real v[EL::Q];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __ldg(vals + c * Q + (int64_t)q * E + e);
+    for (int q = 0; q < EL::Q; ++q) v[q] = __ldg(vals + c * Q + (int64_t)q * E + e);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
+    for (int a = 0; a < EL::C; ++a) {
       Real s = Real(0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += Real(shapeN(a, q)) * v[q];
+      for (int q = 0; q < EL::Q; ++q) s += Real(EL::N(a, q)) * v[q];
       out[(int64_t)(a * NC + c) * E + e] = s;
     }
   }
@@ -68,22 +69,24 @@ __global__ void k_node_copy(const Real* __restrict__ src, const Real* add, int64
   if (i < n) out[i] = add ? add[i] + src[i] : src[i];
 }
 
-// w_q j0 at the eight Gauss points of each element (unit Gauss weights).
-template <typename Real>
+// w_q j0 at the coupling points of each element (the element rule's weight
+// times det dX/dxi; for the tetrahedron the Jacobian is constant).
+template <typename Real, int kEl>
 __global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
                                              const Real* __restrict__ X, int E, int64_t N,
                                              Real* __restrict__ wj0, int* status) {
+  using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  Real dX[8][3];
+  Real dX[EL::C][3];
   const int n0 = __ldg(conn + e);
-  for (int a = 0; a < 8; ++a) {
+  for (int a = 0; a < EL::C; ++a) {
     const int n = __ldg(conn + a * E + e);
     for (int d = 0; d < 3; ++d) dX[a][d] = __ldg(X + d * N + n) - __ldg(X + d * N + n0);
   }
   bool bad = false;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < EL::Q; ++q) {
     Real J0[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -91,14 +94,14 @@ __global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
       for (int j = 0; j < 3; ++j) {
         Real s = Real(0);
 #pragma unroll
-        for (int a = 1; a < 8; ++a) s += dX[a][i] * Real(shape_dxi(a, q, j));
+        for (int a = 1; a < EL::C; ++a) s += dX[a][i] * Real(EL::dxi(a, q, j));
         J0[i][j] = s;
       }
     const Real det = J0[0][0] * (J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1]) +
                      J0[0][1] * (J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2]) +
                      J0[0][2] * (J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0]);
     if (!(det > Real(0))) bad = true;
-    wj0[(int64_t)q * E + e] = det;
+    wj0[(int64_t)q * E + e] = Real(EL::wQ) * det;
   }
   if (bad) set_status(status, kStatInverted);
 }
@@ -130,18 +133,32 @@ template <typename Real>
 ib_status project_t(ib_plan* p, const void* vals, void* out, int nc, cudaStream_t s) {
   if (p->E == 0) return IB_OK;
   const int blocks = (p->E + 255) / 256;
-  if (nc == 3)
-    k_elem_project<Real, 3><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
-  else
-    k_elem_project<Real, 1><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+  if (p->elem == IB_ELEM_TET4) {
+    if (nc == 3)
+      k_elem_project<Real, 3, IB_ELEM_TET4><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
+                                                                   (Real*)out);
+    else
+      k_elem_project<Real, 1, IB_ELEM_TET4><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
+                                                                   (Real*)out);
+  } else if (nc == 3) {
+    k_elem_project<Real, 3, IB_ELEM_HEX8><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
+                                                                 (Real*)out);
+  } else {
+    k_elem_project<Real, 1, IB_ELEM_HEX8><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
+                                                                 (Real*)out);
+  }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
 template <typename Real>
 ib_status static_t(ib_plan* p, cudaStream_t s) {
   if (p->E > 0) {
-    k_wj0<Real><<<(p->E + 127) / 128, 128, 0, s>>>(p->conn, (const Real*)p->X, p->E, p->N,
-                                                   (Real*)p->wj0, p->dstatus);
+    if (p->elem == IB_ELEM_TET4)
+      k_wj0<Real, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(
+          p->conn, (const Real*)p->X, p->E, p->N, (Real*)p->wj0, p->dstatus);
+    else
+      k_wj0<Real, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(
+          p->conn, (const Real*)p->X, p->E, p->N, (Real*)p->wj0, p->dstatus);
     if (cudaGetLastError() != cudaSuccess) return IB_ERR_CUDA;
   }
   // m_a = sum_{(e,q) containing a} N_a(xi_q) w_q j0

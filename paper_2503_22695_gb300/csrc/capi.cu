@@ -228,6 +228,9 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   if (quad != IB_QUAD_GAUSS2 && quad != IB_QUAD_NODAL) return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
     return IB_ERR_INVALID_ARG;
+  if (mesh->elem_type != IB_ELEM_HEX8 && mesh->elem_type != IB_ELEM_TET4)
+    return IB_ERR_INVALID_ARG;
+  const int nc = mesh->elem_type == IB_ELEM_TET4 ? 4 : 8;  // corners = coupling points
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (!std::isfinite(grid->origin[d])) return IB_ERR_INVALID_ARG;
@@ -236,13 +239,14 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   }
   if ((int64_t)mesh->n_elems >= (1LL << kIncShift) / 8) return IB_ERR_CAPACITY;
   cudaStream_t s = S(stream);
-  // Q coupling points: the Gauss points (8 per element) or the nodes
+  // Q coupling points: the element rule's points (8 per hexahedron, 4 per
+  // tetrahedron) or the nodes
   const int64_t E = mesh->n_elems, N = mesh->n_nodes;
-  const int64_t Q = quad == IB_QUAD_NODAL ? N : 8 * E;
+  const int64_t Q = quad == IB_QUAD_NODAL ? N : nc * E;
 
   // connectivity and materials to the host for validation and incidence lists
-  std::vector<int32_t> conn(8 * E), mid;
-  if (E > 0 && !ok(cudaMemcpyAsync(conn.data(), mesh->conn, sizeof(int32_t) * 8 * E,
+  std::vector<int32_t> conn(nc * E), mid;
+  if (E > 0 && !ok(cudaMemcpyAsync(conn.data(), mesh->conn, sizeof(int32_t) * nc * E,
                                    cudaMemcpyDeviceToHost, s)))
     return IB_ERR_CUDA;
   if (mesh->mat_id) {
@@ -252,7 +256,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
       return IB_ERR_CUDA;
   }
   if (!ok(cudaStreamSynchronize(s))) return IB_ERR_CUDA;
-  for (int64_t k = 0; k < 8 * E; ++k)
+  for (int64_t k = 0; k < nc * E; ++k)
     if (conn[k] < 0 || conn[k] >= N) return IB_ERR_INVALID_ARG;
   int max_mid = 0;
   for (int32_t m : mid) {
@@ -261,20 +265,23 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   }
 
   // node -> (corner, element) incidence, ascending element then corner
-  std::vector<int32_t> inc_off(N + 1, 0), inc_idx(8 * E);
+  std::vector<int32_t> inc_off(N + 1, 0), inc_idx(nc * E);
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 8; ++a) inc_off[conn[a * E + e] + 1]++;
+    for (int a = 0; a < nc; ++a) inc_off[conn[a * E + e] + 1]++;
   for (int64_t n = 0; n < N; ++n) inc_off[n + 1] += inc_off[n];
   {
     std::vector<int32_t> fill(inc_off.begin(), inc_off.end() - 1);
     for (int64_t e = 0; e < E; ++e)
-      for (int a = 0; a < 8; ++a) inc_idx[fill[conn[a * E + e]]++] = (a << kIncShift) | (int32_t)e;
+      for (int a = 0; a < nc; ++a) inc_idx[fill[conn[a * E + e]]++] = (a << kIncShift) | (int32_t)e;
   }
 
   ib_plan* p = new ib_plan;
   std::memset(p, 0, sizeof(ib_plan));
   p->precision = precision;
   p->quad = quad;
+  p->elem = mesh->elem_type;
+  p->nc = nc;
+  p->nq = nc;
   p->chunk = kChunk;
   p->fe_ctas = 2;
   p->push_per_sm = 8;
@@ -297,10 +304,10 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   p->max_mat_id = max_mid;
   p->hist_blocks = sort_hist_blocks(Q);
   const size_t rs = p->rsize;
-  bool good = dalloc(&p->inc_off, 4 * (N + 1)) && dalloc(&p->inc_idx, 4 * 8 * E) &&
+  bool good = dalloc(&p->inc_off, 4 * (N + 1)) && dalloc(&p->inc_idx, 4 * nc * E) &&
               dalloc(&p->mass, rs * N) && dalloc(&p->inv_mass, rs * N) &&
-              dalloc(&p->wj0, rs * 8 * E) && dalloc(&p->elem_scratch, rs * 24 * E) &&
-              dalloc(&p->elem_scratch2, rs * 24 * E) && dalloc(&p->keys[0], 4 * Q) &&
+              dalloc(&p->wj0, rs * nc * E) && dalloc(&p->elem_scratch, rs * 3 * nc * E) &&
+              dalloc(&p->elem_scratch2, rs * 3 * nc * E) && dalloc(&p->keys[0], 4 * Q) &&
               dalloc(&p->keys[1], 4 * Q) && dalloc(&p->vals[0], 4 * Q) &&
               dalloc(&p->vals[1], 4 * Q) && dalloc(&p->hist, 4 * 256 * (size_t)p->hist_blocks) &&
               dalloc(&p->tile_start, 4 * (size_t)p->ntiles) &&
@@ -331,7 +338,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
     return IB_ERR_CUDA;
   }
   good = ok(cudaMemcpyAsync(p->inc_off, inc_off.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s)) &&
-         (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * 8 * E,
+         (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * nc * E,
                                        cudaMemcpyHostToDevice, s))) &&
          ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
   if (good)

@@ -76,43 +76,79 @@ int law_set(const MatTable& mt, bool params) {
 }  // namespace
 
 #define IBFE_FE_ARGS p, mt, xa, off, v, out, s
+#define HEX IB_ELEM_HEX8
+
+namespace {
+// Tetrahedral meshes: one instantiation per precision and output (all laws).
+ib_status tet_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
+                    const void* v, void* out, bool energy, bool adj, bool params,
+                    cudaStream_t s) {
+  constexpr int T = IB_ELEM_TET4, L = kLawAll;
+  if (p->precision == IB_FP64) {
+    if (adj)
+      return params ? fe_run<double, double, false, true, true, L, T>(IBFE_FE_ARGS)
+                    : fe_run<double, double, false, true, false, L, T>(IBFE_FE_ARGS);
+    return energy ? fe_run<double, double, true, false, false, L, T>(IBFE_FE_ARGS)
+                  : fe_run<double, double, false, false, false, L, T>(IBFE_FE_ARGS);
+  }
+  if (p->precision == IB_FP32_SPLIT_F32STAB) {
+    if (adj)
+      return params ? fe_run<float, float, false, true, true, L, T>(IBFE_FE_ARGS)
+                    : fe_run<float, float, false, true, false, L, T>(IBFE_FE_ARGS);
+    return energy ? fe_run<float, float, true, false, false, L, T>(IBFE_FE_ARGS)
+                  : fe_run<float, float, false, false, false, L, T>(IBFE_FE_ARGS);
+  }
+  if (adj)
+    return params ? fe_run<float, double, false, true, true, L, T>(IBFE_FE_ARGS)
+                  : fe_run<float, double, false, true, false, L, T>(IBFE_FE_ARGS);
+  return energy ? fe_run<float, double, true, false, false, L, T>(IBFE_FE_ARGS)
+                : fe_run<float, double, false, false, false, L, T>(IBFE_FE_ARGS);
+}
+}  // namespace
 
 ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                           void* out, bool energy, cudaStream_t s) {
   const void* v = nullptr;
+  if (p->elem == IB_ELEM_TET4) return tet_force(p, mt, xa, off, v, out, energy, false, false, s);
   const int set = law_set(mt, false);
   if (p->precision == IB_FP64)
-    return energy ? fe_run<double, double, true, false, false, kLawAll>(IBFE_FE_ARGS)
-                  : fe_run<double, double, false, false, false, kLawAll>(IBFE_FE_ARGS);
+    return energy ? fe_run<double, double, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS)
+                  : fe_run<double, double, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
   if (p->precision == IB_FP32_SPLIT_F32STAB) {
-    if (energy) return fe_run<float, float, true, false, false, kLawAll>(IBFE_FE_ARGS);
-    return set == kLawBase ? fe_run<float, float, false, false, false, kLawBase>(IBFE_FE_ARGS)
-                           : fe_run<float, float, false, false, false, kLawAll>(IBFE_FE_ARGS);
+    if (energy) return fe_run<float, float, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
+    return set == kLawBase
+               ? fe_run<float, float, false, false, false, kLawBase, HEX>(IBFE_FE_ARGS)
+               : fe_run<float, float, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
   }
-  if (energy) return fe_run<float, double, true, false, false, kLawAll>(IBFE_FE_ARGS);
-  if (set == kLawBase) return fe_run<float, double, false, false, false, kLawBase>(IBFE_FE_ARGS);
+  if (energy) return fe_run<float, double, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
+  if (set == kLawBase)
+    return fe_run<float, double, false, false, false, kLawBase, HEX>(IBFE_FE_ARGS);
   if (set == kLawBaseAct)
-    return fe_run<float, double, false, false, false, kLawBaseAct>(IBFE_FE_ARGS);
-  return fe_run<float, double, false, false, false, kLawAll>(IBFE_FE_ARGS);
+    return fe_run<float, double, false, false, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
+  return fe_run<float, double, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
 }
 
 ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                               const void* v, void* out, bool params, cudaStream_t s) {
+  if (p->elem == IB_ELEM_TET4) return tet_force(p, mt, xa, off, v, out, false, true, params, s);
   const int set = law_set(mt, params);
   if (p->precision == IB_FP64)
-    return params ? fe_run<double, double, false, true, true, kLawAll>(IBFE_FE_ARGS)
-                  : fe_run<double, double, false, true, false, kLawAll>(IBFE_FE_ARGS);
+    return params ? fe_run<double, double, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS)
+                  : fe_run<double, double, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
   if (p->precision == IB_FP32_SPLIT_F32STAB)
-    return params ? fe_run<float, float, false, true, true, kLawAll>(IBFE_FE_ARGS)
-                  : fe_run<float, float, false, true, false, kLawAll>(IBFE_FE_ARGS);
+    return params ? fe_run<float, float, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS)
+                  : fe_run<float, float, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
   if (params)
-    return set == kLawBaseAct ? fe_run<float, double, false, true, true, kLawBaseAct>(IBFE_FE_ARGS)
-                              : fe_run<float, double, false, true, true, kLawAll>(IBFE_FE_ARGS);
-  if (set == kLawBase) return fe_run<float, double, false, true, false, kLawBase>(IBFE_FE_ARGS);
-  if (set == kLawBaseAct) return fe_run<float, double, false, true, false, kLawBaseAct>(IBFE_FE_ARGS);
-  return fe_run<float, double, false, true, false, kLawAll>(IBFE_FE_ARGS);
+    return set == kLawBaseAct
+               ? fe_run<float, double, false, true, true, kLawBaseAct, HEX>(IBFE_FE_ARGS)
+               : fe_run<float, double, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS);
+  if (set == kLawBase) return fe_run<float, double, false, true, false, kLawBase, HEX>(IBFE_FE_ARGS);
+  if (set == kLawBaseAct)
+    return fe_run<float, double, false, true, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
+  return fe_run<float, double, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
 }
 
+#undef HEX
 #undef IBFE_FE_ARGS
 
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {

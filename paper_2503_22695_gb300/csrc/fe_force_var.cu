@@ -6,8 +6,8 @@
 namespace ibfe {
 
 #define IBFE_FE_RUN(R, S, E, A, P, L)                                                        \
-  template ib_status fe_run<R, S, E, A, P, L>(ib_plan*, const MatTable&, const void*,      \
-                                              const float*, const void*, void*, cudaStream_t)
+  template ib_status fe_run<R, S, E, A, P, L, IB_ELEM_HEX8>(                                 \
+      ib_plan*, const MatTable&, const void*, const float*, const void*, void*, cudaStream_t)
 
 IBFE_FE_RUN(float, float, false, false, false, kLawBase);
 IBFE_FE_RUN(float, float, false, false, false, kLawAll);

@@ -28,7 +28,7 @@
 //
 // With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
 //   H = Du J0^-1, and the corner forces are
-//   G_a -= (P J0^-T w j0) dN_a/dxi,
+//   G_a -= (P J0^-T w j0) dN_a/dxi  (w: the force rule's weight),
 // so the X-gradients of the shape functions are never formed.
 //
 // This header holds the device code and the launcher template fe_run; the
@@ -149,15 +149,16 @@ constexpr int fe_min_blocks() {
   return sizeof(Real) == 8 ? 2 : (kAdj ? IBFE_FE_MIN_BLOCKS_ADJ : IBFE_FE_MIN_BLOCKS);
 }
 
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e) {
+  using EL = El<kEl>;
   const int E = A.E;
-  int node[8];
+  int node[EL::C];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) node[a] = __ldg(A.conn + a * E + e);
+  for (int a = 0; a < EL::C; ++a) node[a] = __ldg(A.conn + a * E + e);
 
   // reference and current coordinates relative to corner 0
-  Real dX[8][3], du[8][3];
+  Real dX[EL::C][3], du[EL::C][3];
   int c0[3];
   Real o0[3];
   A.pos.load(node[0], c0, o0);
@@ -165,7 +166,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
   for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + node[0]);
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
+  for (int a = 0; a < EL::C; ++a) {
     int c[3];
     Real o[3];
     if (a == 0) {
@@ -181,10 +182,10 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       du[a][d] = dx - dX[a][d];
     }
   }
-  Real vv[kAdj ? 8 : 1][3];
+  Real vv[kAdj ? EL::C : 1][3];
   if (kAdj) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < EL::C; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) vv[a][d] = __ldg(A.v + d * A.N + node[a]);
   }
@@ -225,9 +226,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real Ta = Real(prm[kTa]);
   const bool act = (kLaws & kLawAct) && (kParams || prm[kTa] != 0.0);
 
-  Real Ge[8][3];
+  Real Ge[EL::C][3];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < EL::C; ++a)
 #pragma unroll
     for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
   double en = 0.0;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   bool inverted = false;
 
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < EL::QF; ++q) {
     // J0 = sum_a dX_a (x) dN_a/dxi ;  Du = sum_a du_a (x) dN_a/dxi
     Real J0[3][3], Du[3][3];
 #pragma unroll
@@ -246,9 +247,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       for (int j = 0; j < 3; ++j) {
         Real s = Real(0), t = Real(0);
 #pragma unroll
-        for (int a = 1; a < 8; ++a) {
-          s += dX[a][i] * Real(shape_dxi(a, q, j));
-          t += du[a][i] * Real(shape_dxi(a, q, j));
+        for (int a = 1; a < EL::C; ++a) {
+          s += dX[a][i] * Real(EL::dxi(a, q, j));
+          t += du[a][i] * Real(EL::dxi(a, q, j));
         }
         J0[i][j] = s;
         Du[i][j] = t;
@@ -257,6 +258,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     cofactor(J0, cJ);
     const Real j0 = J0[0][0] * cJ[0][0] + J0[0][1] * cJ[0][1] + J0[0][2] * cJ[0][2];
     if (!(j0 > Real(0))) inverted = true;
+    const Real wj = j0 * Real(EL::wF);  // the force rule's weight times det dX/dxi
     const Real ij0 = Real(1) / j0;
     // J0^-1 = cof(J0)^T / det
     Real Ji[3][3];
@@ -419,7 +421,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         const double d4 = double(f1.d4), r = sqrt(1.0 + d4);
         psi += 0.5 * prm[kTa] * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
       }
-      en += psi * double(j0);
+      en += psi * double(wj);
     }
 
     // stress (forward) or its directional derivative (adjoint)
@@ -461,7 +463,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
           for (int j = 0; j < 3; ++j) {
             Real s = Real(0);
 #pragma unroll
-            for (int a = 0; a < 8; ++a) s += vv[a][i] * Real(shape_dxi(a, q, j));
+            for (int a = 0; a < EL::C; ++a) s += vv[a][i] * Real(EL::dxi(a, q, j));
             Dvv[i][j] = s;
           }
 #pragma unroll
@@ -580,7 +582,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       if (kParams) {
         // gparams_k = -sum_q w j0 (dP/dtheta_k : dF): the element's eight
         // terms in Real, the sums over elements in double
-        const Real w = j0;
+        const Real w = wj;
         const Real vol = lnJ * dl;
         gp[kTa] -= w * gact * Real(0.5) * dI4f;  // (g F e (x) e) : dF
         if (lawNH) {
@@ -623,18 +625,18 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        Qm[i][k] = (P[i][0] * Ji[k][0] + P[i][1] * Ji[k][1] + P[i][2] * Ji[k][2]) * j0;
+        Qm[i][k] = (P[i][0] * Ji[k][0] + P[i][1] * Ji[k][1] + P[i][2] * Ji[k][2]) * wj;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < EL::C; ++a)
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        Ge[a][i] -= Qm[i][0] * Real(shape_dxi(a, q, 0)) + Qm[i][1] * Real(shape_dxi(a, q, 1)) +
-                    Qm[i][2] * Real(shape_dxi(a, q, 2));
+        Ge[a][i] -= Qm[i][0] * Real(EL::dxi(a, q, 0)) + Qm[i][1] * Real(EL::dxi(a, q, 1)) +
+                    Qm[i][2] * Real(EL::dxi(a, q, 2));
   }
 
   if (inverted) set_status(A.status, kStatInverted);
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < EL::C; ++a)
 #pragma unroll
     for (int i = 0; i < 3; ++i) A.out[(a * 3 + i) * E + e] = Ge[a][i];
   if (kEnergy) A.epart[e] = en;
@@ -649,7 +651,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 // binning and the interpolation, issued on another stream, run beside it.
 // CTAs take blocks of elements from a counter, so a CTA that becomes resident
 // late (its SM busy with those kernels) simply takes fewer.
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
     k_fe(FeArgs<Real> A, MatTable mt) {
   __shared__ int base;
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
     __syncthreads();
     if (b >= A.E) break;
     if (b + (int)threadIdx.x < A.E)
-      fe_element<Real, S, kEnergy, kAdj, kParams, kLaws>(A, mt, b + (int)threadIdx.x);
+      fe_element<Real, S, kEnergy, kAdj, kParams, kLaws, kEl>(A, mt, b + (int)threadIdx.x);
   }
 }
 
@@ -714,8 +716,8 @@ inline FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*
 
 }  // namespace
 
-// Launch the force kernel for one (precision, output, law set) choice.
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+// Launch the force kernel for one (precision, output, law set, element) choice.
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
                  void* out, cudaStream_t s) {
   if (p->E == 0) return IB_OK;
@@ -725,7 +727,7 @@ ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* of
   const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : p->fe_ctas;
   const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
   if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
-  k_fe<Real, S, kEnergy, kAdj, kParams, kLaws><<<blocks, threads, 0, s>>>(A, mt);
+  k_fe<Real, S, kEnergy, kAdj, kParams, kLaws, kEl><<<blocks, threads, 0, s>>>(A, mt);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

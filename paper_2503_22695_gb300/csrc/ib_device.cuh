@@ -39,6 +39,44 @@ __host__ __device__ constexpr double shape_dxi(int a, int q, int d) {
 }
 
 // ---------------------------------------------------------------------------
+// Element types.  El<IB_ELEM_HEX8>: the trilinear hexahedron above; its force
+// and its coupling points use the 2x2x2 Gauss rule (unit weights).
+// El<IB_ELEM_TET4>: the linear tetrahedron on the unit reference tetrahedron
+// (N_0 = 1 - xi - eta - zeta, N_1 = xi, N_2 = eta, N_3 = zeta; constant
+// gradients); its coupling points are the symmetric 4-point rule of degree 2
+// (barycentric (a, b, b, b) and permutations, point q nearest corner q,
+// weights 1/24), and its force, whose integrand is constant, is evaluated
+// once at the centroid with the whole reference volume 1/6.
+//   C: corners, Q: coupling points, QF: force points, N(a, q): shape value at
+//   coupling point q, dxi(a, q, d): reference gradient at force point q,
+//   wQ / wF: reference weights of the two rules.
+// ---------------------------------------------------------------------------
+template <int kEl>
+struct El;
+
+template <>
+struct El<IB_ELEM_HEX8> {
+  static constexpr int C = 8, Q = 8, QF = 8;
+  static constexpr double wQ = 1.0, wF = 1.0;
+  __host__ __device__ static constexpr double N(int a, int q) { return shapeN(a, q); }
+  __host__ __device__ static constexpr double dxi(int a, int q, int d) {
+    return shape_dxi(a, q, d);
+  }
+};
+
+template <>
+struct El<IB_ELEM_TET4> {
+  static constexpr int C = 4, Q = 4, QF = 1;
+  static constexpr double wQ = 1.0 / 24.0, wF = 1.0 / 6.0;
+  static constexpr double kTa = 0.58541019662496845446;  // (5 + 3 sqrt 5) / 20
+  static constexpr double kTb = 0.13819660112501051518;  // (5 - sqrt 5) / 20
+  __host__ __device__ static constexpr double N(int a, int q) { return a == q ? kTa : kTb; }
+  __host__ __device__ static constexpr double dxi(int a, int, int d) {
+    return a == 0 ? -1.0 : (a - 1 == d ? 1.0 : 0.0);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // 4-point delta weights.  For a point at t (grid units, staggering removed)
 // with theta = t - floor(t) in [0,1), the four faces floor(t)-1 .. floor(t)+2
 // are at distances r = theta+1, theta, theta-1, theta-2.  With

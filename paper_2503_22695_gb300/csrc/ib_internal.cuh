@@ -91,6 +91,8 @@ inline bool material_valid(const ib_material& m) {
 struct ib_plan {
   int precision;         // ib_precision
   int quad;              // ib_quad: coupling points are Gauss points or nodes
+  int elem;              // ib_elem
+  int nc, nq;            // corners and coupling points per element (8, 8 or 4, 4)
   int N, E;
   int64_t Q;             // coupling points: 8 E Gauss points or N nodes
   ibfe::GridDev grid;
@@ -110,8 +112,8 @@ struct ib_plan {
   void* wj0;             // Real [8E] (q-major: q*E + e)
 
   // workspace
-  void* elem_scratch;    // Real [24][E]
-  void* elem_scratch2;   // Real [24][E]
+  void* elem_scratch;    // Real [3 nc][E]
+  void* elem_scratch2;   // Real [3 nc][E]
   uint32_t* keys[2];     // [Q]
   int32_t* vals[2];      // [Q]
   int32_t* hist;         // radix histogram / offsets
@@ -183,7 +185,7 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
 // one instantiation of the force kernel's launcher (fe_kernel.cuh; explicit
 // instantiations in fe_force_f32.cu, fe_force_adj.cu, fe_force_var.cu)
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
                  void* out, cudaStream_t s);
 

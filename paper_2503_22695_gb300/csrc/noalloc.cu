@@ -223,6 +223,7 @@ extern "C" ib_status ib_fe_energy_noalloc(const ib_mesh* mesh, const ib_material
   if (!mesh || !mats || !x || !energy || !x->cell || !x->off || !mesh->X) return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn))
     return IB_ERR_INVALID_ARG;
+  if (mesh->elem_type != IB_ELEM_HEX8) return IB_ERR_UNSUPPORTED;  // hexahedra only
   if (!(h > 0.0)) return IB_ERR_INVALID_ARG;
   if (mesh->n_elems > kNoAllocMaxElems) return IB_ERR_CAPACITY;
   if (n_mats <= 0 || n_mats > IB_MAX_MATERIALS) return IB_ERR_INVALID_ARG;

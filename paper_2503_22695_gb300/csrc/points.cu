@@ -39,7 +39,7 @@ struct PtArgs {
   NodeLoader<Real> pos;
   const Real* V;         // [3][N] or null
   const Real* inv_mass;  // [N]
-  const Real* wj0;       // [8][E]
+  const Real* wj0;       // [nq][E]
   GridDev g;
   int32_t* q_cell;
   Real* q_off;           // [3][Q]
@@ -74,19 +74,20 @@ __device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, con
   }
 }
 
-template <typename Real, bool kBin>
+template <typename Real, bool kBin, int kEl>
 __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
+  using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.E) return;
   const int E = A.E;
-  const int64_t Q = 8LL * E;
+  const int64_t Q = (int64_t)EL::Q * E;
   int c0[3];
   Real o0[3];
-  Real dl[8][3];
-  Real Vn[8][3];
+  Real dl[EL::C][3];
+  Real Vn[EL::C][3];
   bool bad = false;
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
+  for (int a = 0; a < EL::C; ++a) {
     const int node = __ldg(A.conn + a * E + e);
     int c[3];
     Real o[3];
@@ -118,18 +119,18 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
       c0[d] = 0;
       o0[d] = Real(0);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) dl[a][d] = Real(0);
+      for (int a = 0; a < EL::C; ++a) dl[a][d] = Real(0);
     }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < EL::Q; ++q) {
     const int64_t gq = (int64_t)q * E + e;
     int cw[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       Real s = Real(0);
 #pragma unroll
-      for (int a = 1; a < 8; ++a) s += Real(shapeN(a, q)) * dl[a][d];
+      for (int a = 1; a < EL::C; ++a) s += Real(EL::N(a, q)) * dl[a][d];
       Real t = o0[d] + s;
       Real k = floor(t);
       Real off = t - k;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
       for (int d = 0; d < 3; ++d) {
         Real s = Real(0);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) s += Real(shapeN(a, q)) * Vn[a][d];
+        for (int a = 0; a < EL::C; ++a) s += Real(EL::N(a, q)) * Vn[a][d];
         A.q_val[d * Q + gq] = w * s;
       }
     }
@@ -190,33 +191,34 @@ __global__ void __launch_bounds__(256) k_points_nodal(PtArgs<Real> A) {
 }
 
 // Carried values only (positions already built): V_q = w_q j0 sum_a N_a V_a / m_a.
-template <typename Real>
+template <typename Real, int kEl>
 __global__ void __launch_bounds__(128) k_point_values(int E, int64_t N,
                                                      const int32_t* __restrict__ conn,
                                                      const Real* __restrict__ V,
                                                      const Real* __restrict__ inv_mass,
                                                      const Real* __restrict__ wj0,
                                                      Real* __restrict__ q_val) {
+  using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  const int64_t Q = 8LL * E;
-  Real Vn[8][3];
+  const int64_t Q = (int64_t)EL::Q * E;
+  Real Vn[EL::C][3];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
+  for (int a = 0; a < EL::C; ++a) {
     const int node = __ldg(conn + a * E + e);
     const Real im = __ldg(inv_mass + node);
 #pragma unroll
     for (int d = 0; d < 3; ++d) Vn[a][d] = __ldg(V + d * N + node) * im;
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < EL::Q; ++q) {
     const int64_t gq = (int64_t)q * E + e;
     const Real w = __ldg(wj0 + gq);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       Real s = Real(0);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) s += Real(shapeN(a, q)) * Vn[a][d];
+      for (int a = 0; a < EL::C; ++a) s += Real(EL::N(a, q)) * Vn[a][d];
       q_val[d * Q + gq] = w * s;
     }
   }
@@ -423,8 +425,10 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
   if (p->quad == IB_QUAD_NODAL)
     k_points_nodal<float, true><<<(p->N + 255) / 256, 256, 0, s>>>(A);
+  else if (p->elem == IB_ELEM_TET4)
+    k_points<float, true, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   else
-    k_points<float, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    k_points<float, true, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -452,8 +456,10 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
   A.count = nullptr;
   if (p->quad == IB_QUAD_NODAL)
     k_points_nodal<double, false><<<(p->N + 255) / 256, 256, 0, s>>>(A);
+  else if (p->elem == IB_ELEM_TET4)
+    k_points<double, false, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   else
-    k_points<double, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    k_points<double, false, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -519,14 +525,17 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
                            cudaMemcpyDeviceToDevice, s) == cudaSuccess
                ? IB_OK
                : IB_ERR_CUDA;
-  if (p->precision == IB_FP64)
-    k_point_values<double><<<(p->E + 127) / 128, 128, 0, s>>>(
-        p->E, p->N, p->conn, (const double*)nodal, (const double*)p->inv_mass,
-        (const double*)p->wj0, (double*)p->q_val);
-  else
-    k_point_values<float><<<(p->E + 127) / 128, 128, 0, s>>>(
-        p->E, p->N, p->conn, (const float*)nodal, (const float*)p->inv_mass,
-        (const float*)p->wj0, (float*)p->q_val);
+  const int g = (p->E + 127) / 128;
+  const bool tet = p->elem == IB_ELEM_TET4;
+  if (p->precision == IB_FP64) {
+    auto k = tet ? k_point_values<double, IB_ELEM_TET4> : k_point_values<double, IB_ELEM_HEX8>;
+    k<<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const double*)nodal, (const double*)p->inv_mass,
+                        (const double*)p->wj0, (double*)p->q_val);
+  } else {
+    auto k = tet ? k_point_values<float, IB_ELEM_TET4> : k_point_values<float, IB_ELEM_HEX8>;
+    k<<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const float*)nodal, (const float*)p->inv_mass,
+                        (const float*)p->wj0, (float*)p->q_val);
+  }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -29,6 +29,7 @@ IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 
 IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO, IB_STD_REINF, IB_FIBRE2 = 0, 1, 2, 3, 4
 IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
 IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
+IB_ELEM_HEX8, IB_ELEM_TET4 = 0, 1
 IB_MAX_MATERIALS = 8
 IB_PARAM_ROW = 10   # gradient row: the law's parameters, zeros, d/dT_a in column 9
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
@@ -43,7 +44,8 @@ class IBError(RuntimeError):
 
 class _Mesh(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_elems", C.c_int32), ("conn", C.c_void_p),
-                ("X", C.c_void_p), ("fibres", C.c_void_p), ("mat_id", C.c_void_p)]
+                ("X", C.c_void_p), ("fibres", C.c_void_p), ("mat_id", C.c_void_p),
+                ("elem_type", C.c_int32)]
 
 
 class _Grid(C.Structure):
@@ -187,7 +189,9 @@ class Plan:
                  precision: int = IB_FP32_SPLIT, quad: int = IB_QUAD_GAUSS2):
         self.dtype = torch.float64 if precision == IB_FP64 else torch.float32
         self.quad = quad
-        _check(conn, torch.int32, (8, -1), "conn")
+        # hexahedra [8][E] or tetrahedra [4][E]
+        self.elem = IB_ELEM_TET4 if conn.dim() == 2 and conn.shape[0] == 4 else IB_ELEM_HEX8
+        _check(conn, torch.int32, (4 if self.elem == IB_ELEM_TET4 else 8, -1), "conn")
         _check(X, self.dtype, (3, -1), "X")
         if fibres is not None:
             _check(fibres, self.dtype, (6, conn.shape[1]), "fibres")
@@ -201,7 +205,7 @@ class Plan:
         self.device = X.device
         mesh = _Mesh(self.N, self.E, conn.data_ptr(), X.data_ptr(),
                      None if fibres is None else fibres.data_ptr(),
-                     None if mat_id is None else mat_id.data_ptr())
+                     None if mat_id is None else mat_id.data_ptr(), self.elem)
         grid = _Grid((C.c_int32 * 3)(*self.n), self.h, (C.c_double * 3)(*origin))
         out = C.c_void_p()
         _chk(_lib.ib_plan_create(C.byref(mesh), C.byref(grid), quad, precision, _stream(),
@@ -537,7 +541,8 @@ class Batch:
             fib, mid = d.get("fibres"), d.get("mat_id")
             a.mesh = _Mesh(int(X.shape[1]), int(conn.shape[1]), conn.data_ptr(), X.data_ptr(),
                            None if fib is None else fib.data_ptr(),
-                           None if mid is None else mid.data_ptr())
+                           None if mid is None else mid.data_ptr(),
+                           IB_ELEM_TET4 if conn.shape[0] == 4 else IB_ELEM_HEX8)
             a.grid = _Grid((C.c_int32 * 3)(*d["n"]), float(d["h"]),
                            (C.c_double * 3)(*d.get("origin", (0.0, 0.0, 0.0))))
             mats = d["mats"]
