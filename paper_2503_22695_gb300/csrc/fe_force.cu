@@ -4,6 +4,7 @@
 // code is in fe_kernel.cuh.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -99,10 +100,10 @@ ib_status tet_force(ib_plan* p, const MatTable& mt, const void* xa, const float*
                   : fe_run<float, float, false, false, false, L, T>(IBFE_FE_ARGS);
   }
   if (adj)
-    return params ? fe_run<float, double, false, true, true, L, T>(IBFE_FE_ARGS)
-                  : fe_run<float, double, false, true, false, L, T>(IBFE_FE_ARGS);
-  return energy ? fe_run<float, double, true, false, false, L, T>(IBFE_FE_ARGS)
-                : fe_run<float, double, false, false, false, L, T>(IBFE_FE_ARGS);
+    return params ? fe_run<float, df, false, true, true, L, T>(IBFE_FE_ARGS)
+                  : fe_run<float, df, false, true, false, L, T>(IBFE_FE_ARGS);
+  return energy ? fe_run<float, df, true, false, false, L, T>(IBFE_FE_ARGS)
+                : fe_run<float, df, false, false, false, L, T>(IBFE_FE_ARGS);
 }
 }  // namespace
 
@@ -120,12 +121,12 @@ ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const 
                ? fe_run<float, float, false, false, false, kLawBase, HEX>(IBFE_FE_ARGS)
                : fe_run<float, float, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
   }
-  if (energy) return fe_run<float, double, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
+  if (energy) return fe_run<float, df, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
   if (set == kLawBase)
-    return fe_run<float, double, false, false, false, kLawBase, HEX>(IBFE_FE_ARGS);
+    return fe_run<float, df, false, false, false, kLawBase, HEX>(IBFE_FE_ARGS);
   if (set == kLawBaseAct)
-    return fe_run<float, double, false, false, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
-  return fe_run<float, double, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
+    return fe_run<float, df, false, false, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
+  return fe_run<float, df, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
 }
 
 ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
@@ -140,12 +141,12 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
                   : fe_run<float, float, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
   if (params)
     return set == kLawBaseAct
-               ? fe_run<float, double, false, true, true, kLawBaseAct, HEX>(IBFE_FE_ARGS)
-               : fe_run<float, double, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS);
-  if (set == kLawBase) return fe_run<float, double, false, true, false, kLawBase, HEX>(IBFE_FE_ARGS);
+               ? fe_run<float, df, false, true, true, kLawBaseAct, HEX>(IBFE_FE_ARGS)
+               : fe_run<float, df, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS);
+  if (set == kLawBase) return fe_run<float, df, false, true, false, kLawBase, HEX>(IBFE_FE_ARGS);
   if (set == kLawBaseAct)
-    return fe_run<float, double, false, true, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
-  return fe_run<float, double, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
+    return fe_run<float, df, false, true, false, kLawBaseAct, HEX>(IBFE_FE_ARGS);
+  return fe_run<float, df, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);
 }
 
 #undef HEX

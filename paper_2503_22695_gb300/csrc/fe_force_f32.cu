@@ -9,9 +9,9 @@ namespace ibfe {
   template ib_status fe_run<R, S, E, A, P, L, IB_ELEM_HEX8>(                                 \
       ib_plan*, const MatTable&, const void*, const float*, const void*, void*, cudaStream_t)
 
-IBFE_FE_RUN(float, double, false, false, false, kLawBase);
-IBFE_FE_RUN(float, double, false, false, false, kLawBaseAct);
-IBFE_FE_RUN(float, double, false, false, false, kLawAll);
-IBFE_FE_RUN(float, double, true, false, false, kLawAll);
+IBFE_FE_RUN(float, df, false, false, false, kLawBase);
+IBFE_FE_RUN(float, df, false, false, false, kLawBaseAct);
+IBFE_FE_RUN(float, df, false, false, false, kLawAll);
+IBFE_FE_RUN(float, df, true, false, false, kLawAll);
 
 }  // namespace ibfe

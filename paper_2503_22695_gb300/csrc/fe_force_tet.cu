@@ -8,10 +8,10 @@ namespace ibfe {
   template ib_status fe_run<R, S, E, A, P, kLawAll, IB_ELEM_TET4>(                           \
       ib_plan*, const MatTable&, const void*, const float*, const void*, void*, cudaStream_t)
 
-IBFE_FE_RUN(float, double, false, false, false);
-IBFE_FE_RUN(float, double, true, false, false);
-IBFE_FE_RUN(float, double, false, true, false);
-IBFE_FE_RUN(float, double, false, true, true);
+IBFE_FE_RUN(float, df, false, false, false);
+IBFE_FE_RUN(float, df, true, false, false);
+IBFE_FE_RUN(float, df, false, true, false);
+IBFE_FE_RUN(float, df, false, true, true);
 IBFE_FE_RUN(float, float, false, false, false);
 IBFE_FE_RUN(float, float, true, false, false);
 IBFE_FE_RUN(float, float, false, true, false);

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "dfloat.cuh"
 #include "ib_device.cuh"
 
 namespace ibfe {
@@ -83,8 +84,6 @@ __device__ __forceinline__ void cofactor(const T A[3][3], T C[3][3]) {
   C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
 }
 
-__device__ __forceinline__ double fma_s(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fma_s(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Quantities of one fibre family needed by the stress and its derivatives.
 template <typename Real, typename S>
@@ -100,10 +99,12 @@ __device__ __forceinline__ void fibre_kin(const Real H[3][3], const Real e[3], S
   Real He[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) He[i] = H[i][0] * e[0] + H[i][1] * e[1] + H[i][2] * e[2];
-  // 2 e.He + |He|^2 = He.(2e + He); 2e + He is exact in double
+  // I4 - 1 = (|e|^2 - 1) + He.(2e + He): the products are exact in S, the
+  // sum compensated; 2e + He carries a rounding of order ulp(1) |He|, far
+  // below the result's
   S I4m1 = en1;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) I4m1 = fma_s(S(He[i]), S(Real(2) * e[i]) + S(He[i]), I4m1);
+  for (int i = 0; i < 3; ++i) I4m1 = dacc(I4m1, He[i], Real(2) * e[i] + He[i]);
   f.d4 = I4m1;
   f.d = (!clamp || I4m1 > S(0)) ? I4m1 : S(0);
 #pragma unroll
@@ -209,10 +210,10 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
       es[i] = __ldg(A.fib + (3 + i) * E + e);
     }
   }
-  // |e|^2 - 1 and e_f . e_s, exact enough in S (squares of Real are exact in double)
-  const S efn1 = S(ef[0]) * S(ef[0]) + S(ef[1]) * S(ef[1]) + (S(ef[2]) * S(ef[2]) - S(1));
-  const S esn1 = S(es[0]) * S(es[0]) + S(es[1]) * S(es[1]) + (S(es[2]) * S(es[2]) - S(1));
-  const S efes = S(ef[0]) * S(es[0]) + S(ef[1]) * S(es[1]) + S(ef[2]) * S(es[2]);
+  // |e|^2 - 1 and e_f . e_s as compensated sums of exact products in S
+  const S efn1 = dacc(dacc(dacc(S(-1), ef[0], ef[0]), ef[1], ef[1]), ef[2], ef[2]);
+  const S esn1 = dacc(dacc(dacc(S(-1), es[0], es[0]), es[1], es[1]), es[2], es[2]);
+  const S efes = dacc(dacc(dacc(S(0), ef[0], es[0]), ef[1], es[1]), ef[2], es[2]);
   const Real esn1r = Real(esn1), efesr = Real(efes);
 
   // material constants (unused entries of a model are never read by its branches)
@@ -275,15 +276,17 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 
     // ---- invariants --------------------------------------------------------
     // J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H, the middle term written as
-    // the sum of the principal 2x2 minors H_ii H_jj - H_ij H_ji.  In S = double
-    // the sums and products of FP32 entries below are exact up to one rounding
-    // per fma; det H (third order) is taken in Real.
-    const S h11_22 = S(H[1][1]) + S(H[2][2]);
-    S m2 = fma_s(S(H[0][0]), h11_22, S(H[1][1]) * S(H[2][2]));
-    m2 = fma_s(-S(H[0][1]), S(H[1][0]), m2);
-    m2 = fma_s(-S(H[0][2]), S(H[2][0]), m2);
-    m2 = fma_s(-S(H[1][2]), S(H[2][1]), m2);
-    const S Jm1 = (S(H[0][0]) + h11_22) + m2 + S(det3(H));
+    // the sum of the principal 2x2 minors H_ii H_jj - H_ij H_ji: a compensated
+    // sum in S of the FP32 entries of H and of their exact pairwise products
+    // (near incompressibility tr H cancels to |J - 1| << |H|); det H (third
+    // order) is taken in Real.
+    S Jm1 = dacc(S(0), H[0][0], H[1][1]);
+    Jm1 = dacc(Jm1, H[0][0], H[2][2]);
+    Jm1 = dacc(Jm1, H[1][1], H[2][2]);
+    Jm1 = dacc(Jm1, -H[0][1], H[1][0]);
+    Jm1 = dacc(Jm1, -H[0][2], H[2][0]);
+    Jm1 = dacc(Jm1, -H[1][2], H[2][1]);
+    Jm1 = sacc(sacc(sacc(sacc(Jm1, H[0][0]), H[1][1]), H[2][2]), det3(H));
     const S lnJs = log1p_s(Jm1);
     const Real lnJ = Real(lnJs);
     const Real J = Real(1) + Real(Jm1);

@@ -210,7 +210,10 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s);
 ib_status launch_permute_values(ib_plan* p, cudaStream_t s);
 
 // spread.cu
-ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s);
+// zero_fill false: the far-tile zeros were issued by launch_spread_zero
+ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true);
+// zeros of the tiles no coupling point reaches (needs the points binned)
+ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s);
 ib_status spread_prepare(ib_plan* p);
 size_t spread_scratch_bytes(int precision, int64_t slots);
 int spread_launches();

@@ -611,7 +611,7 @@ void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
 }
 
 template <typename Real>
-ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
+SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f) {
   SpreadArgs<Real> A;
   A.g = p->grid;
   A.Q = p->Q;
@@ -631,18 +631,27 @@ ib_status spread_t(ib_plan* p, double scale, void* f, cudaStream_t s) {
   A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;
   A.absmax = reinterpret_cast<uint32_t*>(p->tile_counters + 5);
+  return A;
+}
+
+template <typename Real>
+ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s) {
+  SpreadArgs<Real> A = spread_args<Real>(p, scale, f);
   cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
-  // far-tile zeros on the side stream, concurrent with the push
-  cudaEventRecord(p->ev_fork, s);
-  cudaStreamWaitEvent(p->zside, p->ev_fork, 0);
-  k_spread_zero<Real><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
-  cudaEventRecord(p->ev_join, p->zside);
+  // far-tile zeros on the side stream, concurrent with the push (unless the
+  // caller has already issued them)
+  if (zero_fill) {
+    cudaEventRecord(p->ev_fork, s);
+    cudaStreamWaitEvent(p->zside, p->ev_fork, 0);
+    k_spread_zero<Real><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
+    cudaEventRecord(p->ev_join, p->zside);
+  }
   launch_push(p, A, s);
   if constexpr (sizeof(Real) == 4)
     k_spread_merge_fx<<<p->merge_ctas, kMT, 0, s>>>(A);
   else
     k_spread_merge<Real><<<p->merge_ctas, kMT, 0, s>>>(A);
-  cudaStreamWaitEvent(s, p->ev_join, 0);
+  if (zero_fill) cudaStreamWaitEvent(s, p->ev_join, 0);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -693,9 +702,20 @@ ib_status spread_prepare(ib_plan* p) {
 
 int spread_launches() { return 4; }
 
-ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s) {
-  return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, s)
-                                 : spread_t<float>(p, scale, f, s);
+ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill) {
+  return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s)
+                                 : spread_t<float>(p, scale, f, zero_fill, s);
+}
+
+ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s) {
+  if (p->precision == IB_FP64) {
+    SpreadArgs<double> A = spread_args<double>(p, 1.0, f);
+    k_spread_zero<double><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
+  } else {
+    SpreadArgs<float> A = spread_args<float>(p, 1.0, f);
+    k_spread_zero<float><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
+  }
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
 }  // namespace ibfe
