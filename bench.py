@@ -31,8 +31,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IB force+spread+interp Gauss-pts/s, % HBM roofline; adjoint/forward time ratio"
-FP64_OPS_PER_GP = 52.0   # FP64-pipe operations of the FE force per Gauss point
-FP64_PEAK_GOPS = 625.0   # nominal GB300 FP64: 1.25 TFLOP/s = 625 G FMA-slots/s
+# The spread's accumulation kernel: each Gauss point adds 3 components x 64
+# stencil faces, each as two exact 32-bit words, with shared-memory integer
+# atomics: 384 lane operations per point.  Their rate on GB300, 29.6 lane
+# operations per clock per SM, comes from a conflict-free shared atomicAdd
+# (u32) probe on this part; x 152 SMs x the SM clock gives the peak.
+PUSH_ATOMS_PER_POINT = 384.0
+SHARED_ATOMS_PER_CLK_SM = 29.6
+# FE force: FP32 operations per Gauss point (fadd + fmul + 2 ffma, counted by
+# ncu for k_fe<float, df, ..., law set NH/Psi_2/Psi_4> on this workload);
+# FP32 peak = 152 SMs x 128 lanes x 2 (fma) x the SM clock.
+FE_FLOPS_PER_GP = 1024.5
+FP32_LANES_PER_SM = 128
 UNIT = "Gauss-pts/s"
 # fluid of the explicit IB step (synthetic, unit periodic box): density,
 # viscosity and time step
@@ -117,6 +127,14 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measured_sm_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def kernel_traffic(kernel: str):
@@ -296,6 +314,16 @@ def run_ours(args):
     timed(fwd, args.steps)
     ibfe.ib_plan_set_profiling(plan, False)
     stages = ibfe.ib_plan_profile(plan, reset=True)
+    # the spreading alone (ib_spread: its far-tile zeros, push and merge; in
+    # ib_forward the zeros overlap the force) for its HBM roofline
+    Gs = G.clone()
+    for _ in range(args.warmup):
+        ibfe.ib_spread(plan, pos, Gs, f)
+    barrier()
+    ibfe.ib_plan_set_profiling(plan, True)
+    timed(lambda: ibfe.ib_spread(plan, pos, Gs, f), args.steps)
+    ibfe.ib_plan_set_profiling(plan, False)
+    spread_alone = ibfe.ib_plan_profile(plan, reset=True)["spread"]
     barrier()
 
     # --- the same forward with FP32 stability scalars (second plan) ---------
@@ -493,26 +521,41 @@ def run_ours(args):
         return 0
 
     # --- roofline of the dominant forward kernel --------------------------
-    # k_fe (the FE force) has the largest share of the forward's kernel time
-    # (ncu launch list); it is bound by the FP64 pipe.  Its algorithmic FP64
-    # work is FP64_OPS_PER_GP pipe operations per Gauss point (the J - 1,
-    # ln J and I4f - 1 steps, counted from the source); the peak is GB300's
-    # nominal FP64 rate, 1.25 TFLOP/s = 625 G FMA-slots/s.
+    # k_spread_push_fx has the largest share of the forward's kernel time
+    # (ncu launch list); its binding unit is the shared-memory integer atomic
+    # (bound "alu": no bytes or flops model fits it).  Work per launch =
+    # PUSH_ATOMS_PER_POINT x Q lane operations; its launch time is the
+    # library's own event interval around that kernel (IB_STAGE_SPREAD_PUSH,
+    # on the stream it is launched on).
     hbm_peak, peak_kind = measured_peaks()
-    fwd_stages = {k: v for k, v in stages.items() if v[1] > 0}
-    per_launch_ms = {k: v[0] / max(1, v[1]) for k, v in fwd_stages.items()}
+    sm_mhz_max = measured_sm_mhz()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fwd_stages = {k: v for k, v in stages.items() if v[1] > 0 and k != "spread_push"}
+    per_launch_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items() if v[1] > 0}
     spread_bytes = 12.0 * n ** 3            # the dense force field written once
-    force_ms = per_launch_ms["force"]
-    fp64_achieved = FP64_OPS_PER_GP * Q / (force_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_fe", "bound": "alu", "achieved": fp64_achieved,
-            "peak": FP64_PEAK_GOPS, "unit": "G FP64-pipe op/s",
-            "frac": fp64_achieved / FP64_PEAK_GOPS, "traffic": kernel_traffic("k_fe"),
+    push_ms = per_launch_ms["spread_push"]
+    atom_peak = SHARED_ATOMS_PER_CLK_SM * n_sm * sm_mhz_max * 1e6 / 1e9   # G ops/s
+    atom_work = PUSH_ATOMS_PER_POINT * Q
+    atom_achieved = atom_work / (push_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_spread_push_fx", "bound": "alu", "achieved": atom_achieved,
+            "peak": atom_peak, "unit": "G shared-atomic lane-op/s",
+            "frac": atom_achieved / atom_peak, "traffic": kernel_traffic("k_spread_push_fx"),
             "traffic_unit": "DRAM bytes per launch",
-            "work_per_launch": FP64_OPS_PER_GP * Q,
-            "launch_ms": force_ms,
-            "peak_source": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)"}
-    spread_ms = per_launch_ms["spread"]
-    spread_roof = {"kernels": "k_spread_zero + k_absmax + k_spread_push_fx + k_spread_merge_fx",
+            "work_per_launch": atom_work, "launch_ms": push_ms,
+            "peak_source": f"29.6 u32 shared atomics/clk/SM (probe on this part) x {n_sm} SMs "
+                           f"x {sm_mhz_max:.0f} MHz"}
+    force_ms = per_launch_ms["force"]
+    fp32_peak = FP32_LANES_PER_SM * 2 * n_sm * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+    fe_achieved = FE_FLOPS_PER_GP * Q / (force_ms * 1e-3) / 1e12
+    force_roof = {"kernel": "k_fe", "bound": "alu", "achieved": fe_achieved,
+                  "peak": fp32_peak, "unit": "TFLOP/s (FP32)", "frac": fe_achieved / fp32_peak,
+                  "traffic": kernel_traffic("k_fe"), "traffic_unit": "DRAM bytes per launch",
+                  "work_per_launch": FE_FLOPS_PER_GP * Q, "launch_ms": force_ms,
+                  "peak_source": f"128 FP32 lanes x 2 x {n_sm} SMs x {sm_mhz_max:.0f} MHz",
+                  "note": "no FP64 instruction (J - 1 and I4f - 1 by compensated FP32 sums)"}
+    spread_ms = spread_alone[0] / max(1, spread_alone[1])
+    spread_roof = {"kernels": "k_spread_zero + k_absmax + k_spread_push_fx + k_spread_merge_fx "
+                              "(ib_spread alone)",
                    "bound": "hbm", "achieved": spread_bytes / (spread_ms * 1e-3) / 1e9,
                    "peak": hbm_peak, "unit": "GB/s",
                    "frac": spread_bytes / (spread_ms * 1e-3) / 1e9 / hbm_peak,
@@ -548,8 +591,9 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "precision": "FP32 arithmetic on split positions (int cell + FP32 offset); FP64 for "
-                     "J-1, ln J and the fibre invariant I4f-1",
+        "precision": "FP32 arithmetic on split positions (int cell + FP32 offset); J-1 and the "
+                     "fibre invariant I4f-1 as compensated FP32 pairs (twice-FP32 precision, "
+                     "no FP64 instructions)",
         "data": "synthetic",
         "config": {"workload": workload, "grid": [n, n, n], "elements": E, "nodes": N,
                    "gauss_points": Q, "l2": "flushed before every timed step (256 MiB write)",
@@ -558,7 +602,7 @@ def run_ours(args):
                                       tuning)),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp32_scalars": {"ms_per_step": t_fwd32, "value": Q * world / (t_fwd32 * 1e-3),
-                         "note": "same forward with J-1, ln J and I4f-1 in FP32 "
+                         "note": "same forward with J-1 and I4f-1 as plain FP32 sums "
                                  "(IB_FP32_SPLIT_F32STAB; its Hessian-vector product misses the "
                                  "2e-5 adjoint tolerance at this size)"},
         "nodal_rule": {"ms_per_step": t_fwdn, "points": N,
@@ -573,6 +617,7 @@ def run_ours(args):
         "adjoint_ms_per_step": t_adj,
         "adjoint_forward_ratio": t_adj / t_fwd,
         "roofline": roof,
+        "force_roofline": force_roof,
         "spread_roofline": spread_roof,
         "forward_roofline": {"bytes_per_step": b_fwd, "achieved_GBps": fwd_gbs,
                              "frac": fwd_gbs / hbm_peak, "peak": hbm_peak,

@@ -87,16 +87,17 @@ typedef enum {
                          params {C10, C01, af, bf, kappa} */
 } ib_model;
 
-/* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1, ln J (the
- *   volumetric term) and the fibre invariant I4f - 1 (the exponential fibre
- *   term near I4f = 1) are combined in FP64.
+/* IB_FP32_SPLIT: FP32 arithmetic on split positions; J - 1 (the volumetric
+ *   term) and the fibre invariant I4f - 1 (the exponential fibre term near
+ *   I4f = 1) are accumulated as compensated FP32 pairs (error-free products
+ *   and sums), as accurate as twice the working precision, without FP64
+ *   instructions.
  * IB_FP64: every array and every operation in double.
- * IB_FP32_SPLIT_F32STAB: as IB_FP32_SPLIT with those scalars in FP32 too,
- *   using the same cancellation-free formulas.  About 4x faster FE force on
- *   GPUs whose FP64 rate is a small fraction of FP32; nodal forces stay
- *   within 1e-5 relative L2 of the FP64 definition, but the Hessian-vector
- *   product of ib_fe_force_adj loses accuracy (6.7e-5 relative on a 256^3
- *   ventricle workload, against 2e-5 with IB_FP32_SPLIT). */
+ * IB_FP32_SPLIT_F32STAB: as IB_FP32_SPLIT with those sums in plain FP32,
+ *   using the same cancellation-free formulas.  Nodal forces stay within
+ *   1e-5 relative L2 of the FP64 definition, but the Hessian-vector product
+ *   of ib_fe_force_adj loses accuracy (6.7e-5 relative on a 256^3 ventricle
+ *   workload, against 2e-5 with IB_FP32_SPLIT) for no speed gain on GB300. */
 typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_precision;
 
 #define IB_MAX_MATERIALS 8
@@ -413,7 +414,9 @@ typedef enum {
   IB_STAGE_INTERP = 5,  /* Gauss-point interpolation (and its gradients) */
   IB_STAGE_PROJECT = 6, /* Gauss point -> element corner projection */
   IB_STAGE_REDUCE = 7,  /* deterministic energy / parameter reductions */
-  IB_STAGE_COUNT = 8
+  IB_STAGE_SPREAD_PUSH = 8, /* the accumulation kernel inside IB_STAGE_SPREAD (FP32 plans; a
+                               sub-interval, not additive; its launches count in the stage) */
+  IB_STAGE_COUNT = 9
 } ib_stage;
 ib_status ib_plan_set_profiling(ib_plan* plan, int32_t enable);
 ib_status ib_plan_profile(ib_plan* plan, void* stream, double* ms, int64_t* calls,

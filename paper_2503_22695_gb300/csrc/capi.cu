@@ -98,28 +98,46 @@ void prof_flush(ib_plan* p) {
   p->ev_used = 0;
 }
 
+}  // namespace
+
+// Profiler intervals: a begin reserves an event pair and records its first
+// event; the end records the second.  Intervals may nest (a kernel inside a
+// stage); the ring is emptied only when none is open, and an interval that
+// finds it full while another is open is not timed.
+int ibfe::prof_begin(ib_plan* p, int stage, cudaStream_t s) {
+  int idx = -1;
+  if (p->prof_on && p->ev) {
+    if (p->ev_used + 2 > p->ev_cap && p->prof_depth == 0) prof_flush(p);
+    if (p->ev_used + 2 <= p->ev_cap) {
+      idx = p->ev_used;
+      p->ev_used += 2;
+      p->ev_stage[idx / 2] = stage;
+      cudaEventRecord(p->ev[idx], s);
+    }
+  }
+  p->prof_depth++;
+  return idx;
+}
+
+void ibfe::prof_end(ib_plan* p, int idx, cudaStream_t s) {
+  p->prof_depth--;
+  if (idx >= 0) cudaEventRecord(p->ev[idx + 1], s);
+}
+
+namespace {
+
 // One stage of an operator: counts its kernel launches and, while profiling
 // is enabled, brackets it with CUDA events on the operator's stream.
 struct Stage {
   ib_plan* p;
   cudaStream_t s;
-  bool rec;
-  Stage(ib_plan* p_, int stage, cudaStream_t s_, int launches) : p(p_), s(s_), rec(false) {
+  int idx;
+  Stage(ib_plan* p_, int stage, cudaStream_t s_, int launches) : p(p_), s(s_) {
     p->prof_launches[stage] += launches;
     p->prof_calls[stage] += 1;
-    if (p->prof_on && p->ev) {
-      if (p->ev_used + 2 > p->ev_cap) prof_flush(p);
-      p->ev_stage[p->ev_used / 2] = stage;
-      cudaEventRecord(p->ev[p->ev_used], s);
-      rec = true;
-    }
+    idx = prof_begin(p, stage, s);
   }
-  ~Stage() {
-    if (rec) {
-      cudaEventRecord(p->ev[p->ev_used + 1], s);
-      p->ev_used += 2;
-    }
-  }
+  ~Stage() { prof_end(p, idx, s); }
 };
 
 int sort_launches(const ib_plan* p) {

@@ -13,18 +13,19 @@
 //   I4 - 1  = (|e|^2 - 1) + 2 e.(H e) + |H e|^2
 //   I8      = e_f.e_s + e_f.(H e_s) + e_s.(H e_f) + (H e_f).(H e_s)
 // The scalars of the volumetric term and of the fibre term near I4f = 1 are
-// combined in the type S (double): J - 1 (its terms are exact double products
-// of the FP32 entries of H, so the FP64 sum leaves J - 1 exact to double
-// rounding), ln J = log1p(J - 1), and the fibre invariant I4f - 1 of the fibre
-// family e_f.  Once I4f - 1 is known, the fibre coefficient
+// accumulated in the type S: J - 1 and the fibre invariant I4f - 1 are short
+// sums of FP32 numbers and of products of two of them, so with S = df
+// (split-precision plans) they are compensated FP32 pairs, exact products and
+// error-free sums (dfloat.cuh), as accurate as twice the working precision and
+// free of FP64 instructions (GB300 executes FP64 at 1/64 of the FP32 rate);
+// with S = double (FP64 plans) plain double, with S = float (the all-FP32
+// option) plain float.  ln J is then log1p of the accurately rounded J - 1.
+// Once I4f - 1 is known, the fibre coefficient
 // 2 a_f (I4f - 1) exp(b_f (I4f - 1)^2) is a product of well-conditioned factors
 // and is formed in Real: exp has relative error (argument error) x (argument),
-// small here, so evaluating it beyond the precision of the FP32 stress it
-// multiplies adds nothing.  The sheet family e_s and the coupling I8 of
-// Holzapfel-Ogden use the same cancellation-free formulas in Real.  Everything
-// else is in Real (float for split-precision plans, double for FP64 plans).
-// On GB300 the FP64 pipe runs at about 1/64 of the FP32 rate, so this FP64 set
-// (about 50 double operations per Gauss point) sets the kernel's time.
+// small here.  The sheet family e_s and the coupling I8 of Holzapfel-Ogden use
+// the same cancellation-free formulas in Real.  Everything else is in Real
+// (float for split-precision plans, double for FP64 plans).
 //
 // With Du = sum_a du_a (x) dN_a/dxi (3x3) and J0 = sum_a dX_a (x) dN_a/dxi:
 //   H = Du J0^-1, and the corner forces are

@@ -166,6 +166,7 @@ struct ib_plan {
   cudaEvent_t* ev;       // [ev_cap] start/stop pairs
   int* ev_stage;         // [ev_cap / 2]
   int ev_cap, ev_used;
+  int prof_depth;        // open profiler intervals
   double prof_ms[IB_STAGE_COUNT];
   int64_t prof_calls[IB_STAGE_COUNT];
   int64_t prof_launches[IB_STAGE_COUNT];
@@ -228,6 +229,10 @@ ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscal
 ib_status interp_prepare(ib_plan* p);
 
 // capi.cu
+// profiler interval around a kernel inside a stage (sub-stage timing; its
+// launches are counted by the enclosing stage)
+int prof_begin(ib_plan* p, int stage, cudaStream_t s);
+void prof_end(ib_plan* p, int idx, cudaStream_t s);
 ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats,
                              const ib_pos* x, const void* v, void* Hv, bool params,
                              cudaStream_t s);

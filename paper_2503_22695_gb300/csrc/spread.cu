@@ -601,8 +601,11 @@ void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
   cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
   if (p->Q > 0)
     k_absmax<<<p->sm_count * 4, 256, 0, s>>>((const float*)p->p_val, 3 * p->Q, A.absmax);
+  p->prof_calls[IB_STAGE_SPREAD_PUSH] += 1;
+  const int ev = prof_begin(p, IB_STAGE_SPREAD_PUSH, s);
   k_spread_push_fx<<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads, kFxSmem,
                      s>>>(A);
+  prof_end(p, ev, s);
 }
 
 void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {

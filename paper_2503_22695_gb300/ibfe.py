@@ -32,7 +32,8 @@ IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
 IB_ELEM_HEX8, IB_ELEM_TET4 = 0, 1
 IB_MAX_MATERIALS = 8
 IB_PARAM_ROW = 10   # gradient row: the law's parameters, zeros, d/dT_a in column 9
-STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce")
+STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce",
+          "spread_push")
 N_PARAMS = {IB_NEO_HOOKEAN: 2, IB_FIBRE1: 4, IB_HO: 9, IB_STD_REINF: 4, IB_FIBRE2: 5}
 
 
