@@ -429,6 +429,16 @@ ib_status ib_plan_profile(ib_plan* plan, void* stream, double* ms, int64_t* call
  * parameter sets in kPa.  The value goes into ib_material.Ta. */
 double ib_active_tension(double t);
 
+/* Failure-path diagnostic: one kernel arms an mbarrier for a transaction no
+ * copy will deliver and runs the library's bounded wait (the one that guards
+ * every TMA box of the interpolation) with a budget of `ms` milliseconds
+ * (0 < ms <= 10000); the wait gives up, the kernel latches the timeout bit and
+ * returns, and the call returns IB_ERR_TIMEOUT with the context intact.
+ * Synchronises `stream`.  Error-path tests may also set the environment
+ * variable IBFE_FAULT="entry[:code]", which makes that C entry point (for
+ * example ib_forward) return `code` (default IB_ERR_CUDA) before any work. */
+ib_status ib_diag_wait_timeout(double ms, void* stream);
+
 /* Static string for a status code. */
 const char* ib_status_str(ib_status s);
 

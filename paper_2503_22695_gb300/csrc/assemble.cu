@@ -106,6 +106,35 @@ __global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
   if (bad) set_status(status, kStatInverted);
 }
 
+// Lumped mass in double from the FP32 weights of an FP32 plan: per corner
+// sum_q N_a(xi_q) w_q j0 in double, then the node gather in double.  The
+// rounded FP32 mass is then, in practice, independent of the order in which
+// the elements are listed (the point values carried by spreading divide by
+// it).
+template <int kEl>
+__global__ void __launch_bounds__(256) k_mass_corner_d(const float* __restrict__ wj0, int E,
+                                                       double* __restrict__ out) {
+  using EL = El<kEl>;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+#pragma unroll
+  for (int a = 0; a < EL::C; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < EL::Q; ++q) s += EL::N(a, q) * double(__ldg(wj0 + (int64_t)q * E + e));
+    out[(int64_t)a * E + e] = s;
+  }
+}
+
+__global__ void k_mass_round(const double* __restrict__ md, float* __restrict__ m,
+                             float* __restrict__ im, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  m[n] = float(md[n]);
+  // nodes that belong to no element carry no mass and receive zero
+  im[n] = md[n] > 0.0 ? float(1.0 / md[n]) : 0.f;
+}
+
 template <typename Real>
 __global__ void k_invert(const Real* __restrict__ m, Real* __restrict__ im, int N) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,6 +191,30 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
     if (cudaGetLastError() != cudaSuccess) return IB_ERR_CUDA;
   }
   // m_a = sum_{(e,q) containing a} N_a(xi_q) w_q j0
+  if (sizeof(Real) == 4) {  // accumulated in double, rounded once
+    double *ed = nullptr, *md = nullptr;
+    if (cudaMalloc(&ed, sizeof(double) * p->nc * (size_t)(p->E > 0 ? p->E : 1)) != cudaSuccess ||
+        cudaMalloc(&md, sizeof(double) * (size_t)p->N) != cudaSuccess) {
+      cudaFree(ed);
+      return IB_ERR_CUDA;
+    }
+    if (p->E > 0) {
+      if (p->elem == IB_ELEM_TET4)
+        k_mass_corner_d<IB_ELEM_TET4><<<(p->E + 255) / 256, 256, 0, s>>>((const float*)p->wj0,
+                                                                         p->E, ed);
+      else
+        k_mass_corner_d<IB_ELEM_HEX8><<<(p->E + 255) / 256, 256, 0, s>>>((const float*)p->wj0,
+                                                                         p->E, ed);
+    }
+    k_node_gather<double, 1><<<(p->N + 255) / 256, 256, 0, s>>>(
+        p->inc_off, p->inc_idx, ed, nullptr, nullptr, p->N, p->E, md);
+    k_mass_round<<<(p->N + 255) / 256, 256, 0, s>>>(md, (float*)p->mass, (float*)p->inv_mass,
+                                                    p->N);
+    const bool good = cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(ed);
+    cudaFree(md);
+    return good && cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+  }
   ib_status st = project_t<Real>(p, p->wj0, p->elem_scratch, 1, s);
   if (st != IB_OK) return st;
   st = gather_t<Real>(p, p->elem_scratch, nullptr, nullptr, p->mass, 1, s);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -53,6 +54,19 @@ void free_plan(ib_plan* p) {
 }
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Host-side fault injection for error-path tests: IBFE_FAULT="entry[:code]"
+// makes that C entry point return `code` (default IB_ERR_CUDA) before doing
+// anything.  Read on every call; no device is touched.
+ib_status injected(const char* entry) {
+  const char* spec = std::getenv("IBFE_FAULT");
+  if (!spec) return IB_OK;
+  const char* colon = std::strchr(spec, ':');
+  const size_t n = colon ? (size_t)(colon - spec) : std::strlen(spec);
+  if (n != std::strlen(entry) || std::strncmp(spec, entry, n) != 0) return IB_OK;
+  const int code = colon ? std::atoi(colon + 1) : (int)IB_ERR_CUDA;
+  return code > 0 ? (ib_status)code : IB_ERR_CUDA;
+}
 
 bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
@@ -238,6 +252,7 @@ const char* ib_status_str(ib_status s) {
 
 ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
                          int32_t precision, void* stream, ib_plan** out) {
+  if (const ib_status f = injected("ib_plan_create")) return f;
   if (!out) return IB_ERR_INVALID_ARG;
   *out = nullptr;
   if (!mesh || !grid) return IB_ERR_INVALID_ARG;
@@ -400,6 +415,7 @@ ib_status ib_lumped_mass(ib_plan* p, void* mass, void* stream) {
 
 ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                       void* G, double* energy, void* stream) {
+  if (const ib_status f = injected("ib_fe_force")) return f;
   if (!p || !G) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -432,6 +448,7 @@ ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const
 }
 
 ib_status ib_spread(ib_plan* p, const ib_pos* x, const void* G, void* f, void* stream) {
+  if (const ib_status f = injected("ib_spread")) return f;
   if (!p || !G || !f || !aligned16(f)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -442,6 +459,7 @@ ib_status ib_spread(ib_plan* p, const ib_pos* x, const void* G, void* f, void* s
 }
 
 ib_status ib_interp(ib_plan* p, const ib_pos* x, const void* u, void* U, void* stream) {
+  if (const ib_status f = injected("ib_interp")) return f;
   if (!p || !u || !U) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -453,6 +471,7 @@ ib_status ib_interp(ib_plan* p, const ib_pos* x, const void* u, void* U, void* s
 
 ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                      const void* u, void* G, void* f, void* U, void* stream) {
+  if (const ib_status f = injected("ib_forward")) return f;
   if (!p || !u || !G || !f || !U || !aligned16(f)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -498,6 +517,7 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
 
 ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_mats,
                   const ib_pos* x, void* u, void* G, void* f, void* U, void* pr, void* stream) {
+  if (const ib_status f = injected("ib_step")) return f;
   if (!p || !fl || !u || !G || !f || !U || !aligned16(f) || !aligned16(u) ||
       !fluid_matches(fl, p))
     return IB_ERR_INVALID_ARG;
@@ -527,6 +547,7 @@ ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_m
 ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                       const void* u, const void* G, const void* gG, const void* gf,
                       const void* gU, void* gx, void* gu, double* gparams, void* stream) {
+  if (const ib_status f = injected("ib_backward")) return f;
   if (!p || !gx || (gf && !G) || (gU && (!gu || !u)) || (gu && !aligned16(gu)))
     return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
@@ -590,6 +611,7 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
 
 ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* gf, void* gG,
                         void* gx, void* stream) {
+  if (const ib_status f = injected("ib_spread_adj")) return f;
   if (!p || !G || !gf || !gG) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -604,6 +626,7 @@ ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* 
 
 ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* gU, void* gu,
                         void* gx, void* stream) {
+  if (const ib_status f = injected("ib_interp_adj")) return f;
   if (!p || !gU || !gu || (gx && !u) || !aligned16(gu)) return IB_ERR_INVALID_ARG;
   ib_status st = check_pos(p, x);
   if (st != IB_OK) return st;
@@ -645,6 +668,7 @@ extern "C" {
 
 ib_status ib_fe_force_adj(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
                           const void* v, void* Hv, double* gparams, void* stream) {
+  if (const ib_status f = injected("ib_fe_force_adj")) return f;
   cudaStream_t s = S(stream);
   ib_status st = fe_force_adj_async(p, mats, n_mats, x, v, Hv, gparams != nullptr, s);
   if (st == IB_OK && gparams) {
@@ -778,6 +802,22 @@ ib_status ib_plan_profile(ib_plan* p, void* stream, double* ms, int64_t* calls,
     }
   }
   return IB_OK;
+}
+
+ib_status ib_diag_wait_timeout(double ms, void* stream) {
+  if (!(ms > 0.0) || ms > 10000.0) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = S(stream);
+  int* d = nullptr;
+  int h = 0;
+  if (!ok(cudaMalloc(&d, sizeof(int)))) return IB_ERR_CUDA;
+  ib_status st = ok(cudaMemsetAsync(d, 0, sizeof(int), s)) ? launch_wait_probe(d, ms, s)
+                                                            : IB_ERR_CUDA;
+  if (st == IB_OK && (!ok(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+                      !ok(cudaStreamSynchronize(s))))
+    st = IB_ERR_CUDA;
+  cudaFree(d);
+  if (st != IB_OK) return st;
+  return (h & kStatTimeout) ? IB_ERR_TIMEOUT : IB_OK;
 }
 
 ib_status ib_plan_sync_status(ib_plan* p, void* stream) {

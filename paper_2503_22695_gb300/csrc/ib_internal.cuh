@@ -227,6 +227,8 @@ int spread_launches();
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
                                double gscale, cudaStream_t s);
 ib_status interp_prepare(ib_plan* p);
+// the bounded-wait diagnostic (latches kStatTimeout into *status after ms)
+ib_status launch_wait_probe(int* status, double ms, cudaStream_t s);
 
 // capi.cu
 // profiler interval around a kernel inside a stage (sub-stage timing; its

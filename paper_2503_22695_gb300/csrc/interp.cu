@@ -150,8 +150,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for phase `parity` of an mbarrier; false after `budget`
+// cycles (about 1 s by default).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long budget = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -162,7 +164,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
     __nanosleep(64);
   }
 }
@@ -543,6 +545,33 @@ ib_status prepare_t(ib_plan* p) {
 }
 
 }  // namespace
+
+// Diagnostic of the failure path of the bounded wait: one thread arms an
+// mbarrier for 16 bytes of transaction that no copy will deliver, so the wait
+// gives up after `budget` cycles and the kernel latches the timeout bit, as the
+// interpolation does when a TMA box never lands.  No copy is in flight, so
+// nothing is left to wait for on exit.
+__global__ void k_wait_probe(int* status, long long budget) {
+  __shared__ __align__(8) uint64_t bar_s;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_s);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(16)
+                 : "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(bar, 0, budget)) set_status(status, kStatTimeout);
+}
+
+ib_status launch_wait_probe(int* status, double ms, cudaStream_t s) {
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess)
+    return IB_ERR_CUDA;
+  k_wait_probe<<<1, 32, 0, s>>>(status, (long long)(ms * khz));
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
 
 ib_status interp_prepare(ib_plan* p) {
   return p->precision == IB_FP64 ? prepare_t<double>(p) : prepare_t<float>(p);

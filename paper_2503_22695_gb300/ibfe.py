@@ -101,6 +101,7 @@ def _load():
                                  C.c_double, vp, vp],
         "ib_plan_profile": [vp, vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32],
         "ib_plan_set_penalty": [vp, vp, i32, vp, C.c_double],
+        "ib_diag_wait_timeout": [C.c_double, vp],
         "ib_fluid_create": [C.POINTER(_Grid), i32, C.c_double, C.c_double, C.c_double, vp,
                             C.POINTER(vp)],
         "ib_fluid_destroy": [vp],
@@ -470,6 +471,11 @@ def ib_plan_set_penalty(plan: Plan, nodes=None, kappa: float = 0.0, weights=None
     plan._pen = (nodes, weights)
     _chk(_lib.ib_plan_set_penalty(plan.handle, _ptr(nodes), int(nodes.numel()), _ptr(weights),
                                   float(kappa)), "ib_plan_set_penalty")
+
+
+def ib_diag_wait_timeout(ms: float = 20.0) -> int:
+    """Run the bounded-wait diagnostic; returns the status (IB_ERR_TIMEOUT)."""
+    return int(_lib.ib_diag_wait_timeout(float(ms), _stream()))
 
 
 def ib_plan_get_tuning(plan: Plan):

@@ -60,3 +60,24 @@ def test_host_side_argument_checks(lib):
     assert lib.ib_plan_autotune(*([None] * 7)) == 1
     assert lib.ib_plan_destroy(None) == 1
     assert lib.ib_plan_sync_status(None, None) == 1
+
+
+def test_host_fault_injection(lib, monkeypatch):
+    """IBFE_FAULT makes the named entry point fail before any work (host only),
+    so error propagation can be tested without a GPU fault."""
+    out = C.c_void_p()
+    monkeypatch.setenv("IBFE_FAULT", "ib_plan_create:5")
+    assert lib.ib_plan_create(None, None, 0, 0, None, C.byref(out)) == 5  # IB_ERR_TIMEOUT
+    monkeypatch.setenv("IBFE_FAULT", "ib_forward")
+    assert lib.ib_forward(*([None] * 9)) == 2                              # IB_ERR_CUDA
+    assert lib.ib_plan_create(None, None, 0, 0, None, C.byref(out)) == 1  # not injected
+    monkeypatch.delenv("IBFE_FAULT")
+    assert lib.ib_forward(*([None] * 9)) == 1
+    # the Python binding turns the injected status into IBError
+    from paper_2503_22695_gb300 import ibfe
+    monkeypatch.setenv("IBFE_FAULT", "ib_forward:3")
+    args = (None, None, 0, None, None, None, None, None, None)
+    assert ibfe._lib.ib_forward(*args) == ibfe.IB_ERR_NONFINITE
+    with pytest.raises(ibfe.IBError) as e:
+        ibfe._chk(ibfe._lib.ib_forward(*args), "ib_forward")
+    assert e.value.code == ibfe.IB_ERR_NONFINITE
