@@ -486,14 +486,12 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
     return IB_ERR_CUDA;
   st = do_points_sorted(p, x, nullptr, b);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fsorted, b))) st = IB_ERR_CUDA;
-  // the far-tile zeros of f (HBM writes) on a third stream, beside the
-  // FP64-bound force and the interpolation
-  if (st == IB_OK && (!ok(cudaStreamWaitEvent(p->zside, p->ev_fsorted, 0)))) st = IB_ERR_CUDA;
+  // the far-tile zeros of f (HBM writes) on the side branch, beside the
+  // force kernel and ahead of the interpolation
   if (st == IB_OK) {
     p->prof_launches[IB_STAGE_SPREAD] += 1;  // overlapped: not in the spread stage's time
-    st = launch_spread_zero(p, f, p->zside);
+    st = launch_spread_zero(p, f, b);
   }
-  if (st == IB_OK && !ok(cudaEventRecord(p->ev_join, p->zside))) st = IB_ERR_CUDA;
   if (st == IB_OK) st = do_interp_tail(p, u, U, b, p->elem_scratch2);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   if (st == IB_OK) {
@@ -511,7 +509,6 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
   if (st == IB_OK)
     st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s, /*zero_fill=*/false);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
-  if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_join, 0))) st = IB_ERR_CUDA;
   return check_launch(st);
 }
 

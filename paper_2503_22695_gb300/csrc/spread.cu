@@ -276,7 +276,7 @@ constexpr float kMagic = 12582912.0f;            // M = 1.5 * 2^23
 constexpr float kMagicZ = 12582912.0f * 2049.0f; // M (1 + 2^11), exact in float
 constexpr int kFxThreads = 256;
 constexpr int kFxWarps = kFxThreads / 32;
-constexpr int kFxBatch = 128;  // points staged per batch
+constexpr int kFxGroup = 16;  // points a warp stages at a time
 // Lane mapping: a warp takes one point at a time; lane (dz, dy, xh) adds the
 // faces xh and xh + 2 of stencil row (dz, dy), one instruction per face pair
 // and component.  With y stride 14 and z stride 168 the 16 row offsets
@@ -286,14 +286,18 @@ constexpr int kFxSY = 14;
 constexpr int kFxSZ = kB * kFxSY;       // 168
 constexpr int kFxAcc = kB * kFxSZ;      // 2016 words per component
 
-// Staged points, one array per field (16- and 32-byte records keep the
-// one-thread-per-point stores at most 2-way bank conflicted).
-struct FxStage {
-  float4 val[kFxBatch];     // 2^k V^c * scale, c = 0..2
-  int4 org[kFxBatch];       // accumulator offset of the stencil's first face, per component
-  float2 wz[kFxBatch][4];   // [dz] = (w_z at s = 0, w_z at s = 1/2)
-  float2 wy[kFxBatch][4];   // [dy] likewise
-  float4 wx[kFxBatch][2];   // [xh] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
+// The points a warp has staged, one array per field.  Each warp owns one
+// group: staging needs no CTA barrier, only the warp's own __syncwarp.  The
+// weight arrays are stencil-index major with rows padded by one record, so
+// the staging stores of 16 consecutive points are contiguous and the per-point
+// reads of the 2 or 4 distinct rows fall in distinct banks (one wavefront).
+constexpr int kFxRow = kFxGroup + 1;
+struct FxGroup {
+  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2
+  int4 org[kFxGroup];       // accumulator offset of the stencil's first face, per component
+  float2 wz[4][kFxRow];     // [dz][pt] = (w_z at s = 0, w_z at s = 1/2)
+  float2 wy[4][kFxRow];     // [dy][pt] likewise
+  float4 wx[2][kFxRow];     // [xh][pt] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
 };
 
 // adds the contribution C = w wx (in units of 2^-k) at word offset a
@@ -314,10 +318,67 @@ __device__ __forceinline__ int fx_exponent(const SpreadArgs<float>& A) {
   return min(19 - ex, 100);           // keep 2^(k+11) a normal float
 }
 
+// Raw data of one point, loaded a group ahead so that the loads are in
+// flight while the warp accumulates the current group.
+struct FxRaw {
+  int32_t cell;
+  float off[3];
+  float val[3];
+};
+
+__device__ __forceinline__ void fx_fetch(const SpreadArgs<float>& A, int i, bool want_val,
+                                         FxRaw& r) {
+  r.cell = __ldg(A.p_cell + i);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) r.off[d] = __ldg(A.p_off + d * A.Q + i);
+  if (want_val) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r.val[c] = __ldg(A.p_val + c * A.Q + i);
+  }
+}
+
+// Lanes pt and pt + 16 stage point pt of the group: each evaluates three of
+// the six 1-D weight sets (lane half 0: x at s = 0 and 1/2, y at s = 0;
+// lane half 1: y at s = 1/2, z at s = 0 and 1/2), so both halves run the
+// same instructions.
+__device__ __forceinline__ void fx_stage(FxGroup& G, int pt, int part, const FxRaw& r,
+                                         const int lc0[3], float vscale) {
+  int cc[3];
+  unpack_cell(r.cell, cc[0], cc[1], cc[2]);
+  int b[3][2];
+  float th[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) b[d][hf] = cc[d] - lc0[d] + stencil_axis(r.off[d], hf == 1, th[d][hf]) + 2;
+  float wa[4], wb[4], wc[4];
+  delta_weights(part ? th[1][1] : th[0][0], wa);
+  delta_weights(part ? th[2][0] : th[0][1], wb);
+  delta_weights(part ? th[2][1] : th[1][0], wc);
+  if (part == 0) {
+    G.wx[0][pt] = make_float4(wa[0], wa[2], wb[0], wb[2]);
+    G.wx[1][pt] = make_float4(wa[1], wa[3], wb[1], wb[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) G.wy[j][pt].x = wc[j];
+    G.val[pt] = make_float4(r.val[0] * vscale, r.val[1] * vscale, r.val[2] * vscale, 0.f);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      G.wy[j][pt].y = wa[j];
+      G.wz[j][pt] = make_float2(wb[j], wc[j]);
+    }
+    int o[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      o[c] = c * kFxAcc + b[2][c != 2] * kFxSZ + b[1][c != 1] * kFxSY + b[0][c != 0];
+    G.org[pt] = make_int4(o[0], o[1], o[2], 0);
+  }
+}
+
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FxStage& stage = *reinterpret_cast<FxStage*>(smem_raw);
-  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(FxStage));
+  FxGroup* groups = reinterpret_cast<FxGroup*>(smem_raw);
+  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + kFxWarps * sizeof(FxGroup));
   unsigned* acc_lo = acc_hi + 3 * kFxAcc;
   __shared__ int next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -326,10 +387,13 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
   // this lane's (dz, dy, xh) and its offset within a stencil
   const int ldz = lane >> 3, ldy = (lane >> 1) & 3, lxh = lane & 1;
   const int loff = ldz * kFxSZ + ldy * kFxSY + lxh;
+  // this lane's staging role: point pt of the group, lane half `part`
+  const int pt = lane & (kFxGroup - 1), part = lane >> 4;
+  FxGroup& G = groups[warp];
   const int k = fx_exponent(A);
   const float vscale = A.scale * ldexpf(1.f, k);
   for (;;) {
-    __syncthreads();
+    __syncthreads();  // previous item decoded
     if (tid == 0) next = atomicAdd(A.counters + 1, 1);
     __syncthreads();
     const int slot = next;
@@ -339,51 +403,26 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
     const int e = min(A.tile_end[tile], s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
+    // warp w takes the groups starting at s + 16 (w + 8 j)
+    FxRaw raw;
+    int g0 = s + warp * kFxGroup;
+    if (g0 + pt < e) fx_fetch(A, g0 + pt, part == 0, raw);
     for (int i = tid; i < 3 * kFxAcc * 2 / 4; i += kFxThreads)
       reinterpret_cast<uint4*>(acc_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int b0 = s; b0 < e; b0 += kFxBatch) {
-      const int nb = min(kFxBatch, e - b0);
-      __syncthreads();  // accumulators zeroed / previous batch consumed
-      if (tid < nb) {
-        const int i = b0 + tid;
-        int cc[3];
-        unpack_cell(__ldg(A.p_cell + i), cc[0], cc[1], cc[2]);
-        float w[3][2][4];
-        int b[3][2];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float off = __ldg(A.p_off + d * A.Q + i);
-#pragma unroll
-          for (int hf = 0; hf < 2; ++hf) {
-            float th;
-            b[d][hf] = cc[d] - lc0[d] + stencil_axis(off, hf == 1, th) + 2;
-            delta_weights(th, w[d][hf]);
-          }
-        }
-        stage.val[tid] = make_float4(__ldg(A.p_val + i) * vscale, __ldg(A.p_val + A.Q + i) * vscale,
-                                     __ldg(A.p_val + 2 * A.Q + i) * vscale, 0.f);
-        int o[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          o[c] = c * kFxAcc + b[2][c != 2] * kFxSZ + b[1][c != 1] * kFxSY + b[0][c != 0];
-        stage.org[tid] = make_int4(o[0], o[1], o[2], 0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          stage.wz[tid][j] = make_float2(w[2][0][j], w[2][1][j]);
-          stage.wy[tid][j] = make_float2(w[1][0][j], w[1][1][j]);
-        }
-#pragma unroll
-        for (int xh = 0; xh < 2; ++xh)
-          stage.wx[tid][xh] = make_float4(w[0][0][xh], w[0][0][xh + 2], w[0][1][xh], w[0][1][xh + 2]);
-      }
-      __syncthreads();
+    __syncthreads();  // accumulators zeroed
+    for (; g0 < e; g0 += kFxWarps * kFxGroup) {
+      const int ng = min(kFxGroup, e - g0);
+      if (pt < ng) fx_stage(G, pt, part, raw, lc0, vscale);
+      __syncwarp();
+      const int gn = g0 + kFxWarps * kFxGroup;
+      if (gn + pt < e) fx_fetch(A, gn + pt, part == 0, raw);
       // one point per warp step: lane (dz, dy, xh) adds faces xh and xh + 2 of
       // its (dz, dy) row, for each component
-      for (int pt = warp; pt < nb; pt += kFxWarps) {
-        const float4 v = stage.val[pt];
-        const int4 org = stage.org[pt];
-        const float2 wz = stage.wz[pt][ldz], wy = stage.wy[pt][ldy];
-        const float4 wx = stage.wx[pt][lxh];
+      for (int q = 0; q < ng; ++q) {
+        const float4 v = G.val[q];
+        const int4 org = G.org[q];
+        const float2 wz = G.wz[ldz][q], wy = G.wy[ldy][q];
+        const float4 wx = G.wx[lxh][q];
         // component 0: z, y at s = 1/2, x at s = 0
         float wr = v.x * wz.y * wy.y;
         int a = org.x + loff;
@@ -400,6 +439,7 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
         fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
         fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
       }
+      __syncwarp();  // group consumed before it is restaged
     }
     __syncthreads();
     // decoded words (H, L) of every face, exact, one 12-face x-row per thread
@@ -514,6 +554,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
 // by 2^-(k+11).  The result does not depend on how a tile's points were cut
 // into work items.
 __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
+  static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
   __shared__ int src_slot[27], src_n[27];
   const int tid = threadIdx.x;
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
@@ -522,6 +563,12 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
   const int count = A.counters[3];
   const float out_scale = ldexpf(1.f, -(fx_exponent(A) + 11));
   const int4* scratch = reinterpret_cast<const int4*>(A.scratch);  // 2 faces per int4
+  // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y), all three components
+  const int z = tid >> 5, y = (tid >> 2) & 7, xq = tid & 3;
+  const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
+  const int hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
+  // x neighbours: the left tile's block reaches faces 0, 1, the right one's 6, 7
+  const int lx = xq == 0 ? -1 : 0, hx = xq == 3 ? 1 : 0;
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
     const int tile = A.tile_list_near[k];
     const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
@@ -534,58 +581,41 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
       src_n[tid] = A.tile_nitems[nb];
     }
     __syncthreads();
-    if (tid < 3 * 64) {
-      const int c = tid >> 6, z = (tid >> 3) & 7, y = tid & 7;
-      const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
-      const int hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
-      long long sh[8];
-      int sl[8];
+    long long sh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int sl[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int oz = lz; oz <= hz; ++oz)
+      for (int oy = ly; oy <= hy; ++oy)
+        for (int ox = lx; ox <= hx; ++ox) {
+          // this face pair in the source tile's halo'd block (int4 units)
+          const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
+                        (kTile / 2) * ox;
+          const int src = (oz + 1) * 9 + (oy + 1) * 3 + ox + 1;
+          const int slt = src_slot[src], ns = src_n[src];
+          const int4* r = scratch + (int64_t)slt * (kItemBlk / 2) + q;
+#pragma unroll 2
+          for (int j = 0; j < ns; ++j, r += kItemBlk / 2) {
+            int4 v[3];
 #pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        sh[x] = 0;
-        sl[x] = 0;
-      }
-      for (int oz = lz; oz <= hz; ++oz)
-        for (int oy = ly; oy <= hy; ++oy) {
-          // row of 12 faces = 6 int4 (96 bytes)
-          const int rowoff =
-              (c * kBlk + ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * kB) / 2;
-          const int s0 = (oz + 1) * 9 + (oy + 1) * 3;
-          for (int ox = -1; ox <= 1; ++ox) {
-            const int slt = src_slot[s0 + ox + 1], ns = src_n[s0 + ox + 1];
-            for (int j = 0; j < ns; ++j) {
-              const int4* r = scratch + ((int64_t)(slt + j) * kItemBlk) / 2 + rowoff;
-              if (ox < 0) {          // faces 0,1 from the left neighbour's block x 10,11
-                const int4 v = r[5];
-                sh[0] += v.x; sl[0] += v.y; sh[1] += v.z; sl[1] += v.w;
-              } else if (ox > 0) {   // faces 6,7 from the right neighbour's block x 0,1
-                const int4 v = r[0];
-                sh[6] += v.x; sl[6] += v.y; sh[7] += v.z; sl[7] += v.w;
-              } else {               // block x 2..9
-                int4 v[4];
+            for (int c = 0; c < 3; ++c) v[c] = __ldg(r + c * (kBlk / 2));
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = r[1 + q];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  sh[2 * q] += v[q].x; sl[2 * q] += v[q].y;
-                  sh[2 * q + 1] += v[q].z; sl[2 * q + 1] += v[q].w;
-                }
-              }
+            for (int c = 0; c < 3; ++c) {
+              sh[c][0] += v[c].x; sl[c][0] += v[c].y;
+              sh[c][1] += v[c].z; sl[c][1] += v[c].w;
             }
           }
         }
-      float o[8];
 #pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const long long S = sh[x] * 2048 + sl[x];
+    for (int c = 0; c < 3; ++c) {
+      float o[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const long long S = sh[c][i] * 2048 + sl[c][i];
         const int hi = (int)(S >> 24);  // |S| < 2^47: |hi| < 2^23, exact in float
         const int lo = (int)(S & 0xFFFFFF);
-        o[x] = fmaf((float)hi, 16777216.0f, (float)lo) * out_scale;
+        o[i] = fmaf((float)hi, 16777216.0f, (float)lo) * out_scale;
       }
-      float4* out = reinterpret_cast<float4*>(A.f + c * cells +
-                                              ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0);
-      out[0] = make_float4(o[0], o[1], o[2], o[3]);
-      out[1] = make_float4(o[4], o[5], o[6], o[7]);
+      float* row = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+      reinterpret_cast<float2*>(row)[xq] = make_float2(o[0], o[1]);
     }
   }
 }
@@ -595,7 +625,7 @@ size_t push_smem() {
   return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
 }
 
-constexpr size_t kFxSmem = sizeof(FxStage) + sizeof(unsigned) * 2 * 3 * kFxAcc;
+constexpr size_t kFxSmem = kFxWarps * sizeof(FxGroup) + sizeof(unsigned) * 2 * 3 * kFxAcc;
 
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
   cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
