@@ -92,8 +92,8 @@ class Model:
         self.mat_id = None if mat_id is None else np.ascontiguousarray(mat_id, dtype=np.int32)
         self.N = self.X.shape[1]
         self.E = self.conn.shape[1]
-        self.elem = 1 if self.conn.shape[0] == 4 else 0     # tetrahedra or hexahedra
-        self.nq = 4 if self.elem == 1 else 8                # points of the element rule
+        self.elem = {8: 0, 4: 1, 10: 2}[self.conn.shape[0]]  # hexahedra, P1 or P2 tetrahedra
+        self.nq = 8 if self.elem == 0 else 4                  # points of the element rule
         self._mesh = _Mesh(self.N, self.E, _p(self.conn), _p(self.X), _p(self.fibres),
                            _p(self.mat_id), self.elem)
         if grid is not None:

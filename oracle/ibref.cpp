@@ -232,30 +232,55 @@ const double kUnitY[3] = {0.0, 1.0, 0.0};
 //           a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights 1/24 each
 //           (the reference volume 1/6 in four).  The force integrand of P1 is
 //           constant per element, so this rule gives it exactly too.
+//   elem 2: quadratic tetrahedron (P2, the element of the Cook membrane of
+//           Section 5), VTK order: vertices 0-3 as in P1, then the mid-edge
+//           nodes of edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).  With the
+//           barycentric coordinates L_0..L_3 above, N = L_i (2 L_i - 1) at a
+//           vertex and N = 4 L_i L_j at the node of edge (i, j).  The same
+//           4-point rule of degree 2 serves the force (its integrand
+//           P : grad N is of degree 2 on an affine element under an affine
+//           deformation, so the patch test holds) and the coupling.
 // ---------------------------------------------------------------------------
+constexpr int kMaxC = 10;  // nodes of the largest element
 const int kCorner[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
                            {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+// P2 edge nodes: the two vertices of each edge, VTK order
+const int kTetEdge[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
 
-int nc_of(const or_mesh* m) { return m->elem == 1 ? 4 : 8; }  // corners
-int nq_of(const or_mesh* m) { return m->elem == 1 ? 4 : 8; }  // rule points
+int nc_of(const or_mesh* m) { return m->elem == 2 ? 10 : (m->elem == 1 ? 4 : 8); }  // nodes
+int nq_of(const or_mesh* m) { return m->elem == 0 ? 8 : 4; }  // rule points
 
 struct GaussPt {
-  double N[8];
-  double dNdX[8][3];
+  double N[kMaxC];
+  double dNdX[kMaxC][3];
   double wj0;
 };
 
-bool gauss_point(const or_mesh* m, const double Xe[8][3], int q, GaussPt& g) {
+bool gauss_point(const or_mesh* m, const double Xe[kMaxC][3], int q, GaussPt& g) {
   const int nc = nc_of(m);
-  double dNdxi[8][3] = {{0}};
+  double dNdxi[kMaxC][3] = {{0}};
   double wq = 1.0;
-  for (int a = 0; a < 8; ++a) g.N[a] = 0.0;
-  if (m->elem == 1) {
+  for (int a = 0; a < kMaxC; ++a) g.N[a] = 0.0;
+  if (m->elem == 1 || m->elem == 2) {
     const double ta = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, tb = (5.0 - std::sqrt(5.0)) / 20.0;
-    for (int a = 0; a < 4; ++a) g.N[a] = a == q ? ta : tb;
-    for (int d = 0; d < 3; ++d) {
-      dNdxi[0][d] = -1.0;
-      dNdxi[1 + d][d] = 1.0;
+    // barycentric coordinates of rule point q and their xi-gradients
+    double L[4], dL[4][3] = {{-1.0, -1.0, -1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+    for (int i = 0; i < 4; ++i) L[i] = i == q ? ta : tb;
+    if (m->elem == 1) {
+      for (int a = 0; a < 4; ++a) {
+        g.N[a] = L[a];
+        for (int d = 0; d < 3; ++d) dNdxi[a][d] = dL[a][d];
+      }
+    } else {
+      for (int a = 0; a < 4; ++a) {
+        g.N[a] = L[a] * (2.0 * L[a] - 1.0);
+        for (int d = 0; d < 3; ++d) dNdxi[a][d] = (4.0 * L[a] - 1.0) * dL[a][d];
+      }
+      for (int k = 0; k < 6; ++k) {
+        const int i = kTetEdge[k][0], j = kTetEdge[k][1];
+        g.N[4 + k] = 4.0 * L[i] * L[j];
+        for (int d = 0; d < 3; ++d) dNdxi[4 + k][d] = 4.0 * (L[i] * dL[j][d] + L[j] * dL[i][d]);
+      }
     }
     wq = 1.0 / 24.0;
   } else {
@@ -289,7 +314,7 @@ bool gauss_point(const or_mesh* m, const double Xe[8][3], int q, GaussPt& g) {
   inv[2][1] = (J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1]) / det;
   inv[2][2] = (J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0]) / det;
   // dN/dX_i = sum_j dN/dxi_j (dxi_j/dX_i), dxi/dX = J0^-1
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < kMaxC; ++a)
     for (int i = 0; i < 3; ++i) {
       double s = 0.0;
       for (int j = 0; j < 3; ++j) s += dNdxi[a][j] * inv[j][i];
@@ -300,9 +325,9 @@ bool gauss_point(const or_mesh* m, const double Xe[8][3], int q, GaussPt& g) {
 }
 
 // Gather an element's corners of a [3][N] array (zeros past the last corner).
-void gather(const or_mesh* m, const double* A, int e, double out[8][3]) {
+void gather(const or_mesh* m, const double* A, int e, double out[kMaxC][3]) {
   int64_t E = m->n_elems, N = m->n_nodes;
-  for (int a = 0; a < 8; ++a) {
+  for (int a = 0; a < kMaxC; ++a) {
     if (a >= nc_of(m)) {
       for (int i = 0; i < 3; ++i) out[a][i] = 0.0;
       continue;
@@ -314,7 +339,7 @@ void gather(const or_mesh* m, const double* A, int e, double out[8][3]) {
 
 bool check_mesh(const or_mesh* m) {
   if (!m || m->n_nodes <= 0 || m->n_elems < 0 || !m->conn || !m->X) return false;
-  if (m->elem != 0 && m->elem != 1) return false;
+  if (m->elem != 0 && m->elem != 1 && m->elem != 2) return false;
   for (int64_t k = 0; k < (int64_t)nc_of(m) * m->n_elems; ++k)
     if (m->conn[k] < 0 || m->conn[k] >= m->n_nodes) return false;
   return true;
@@ -370,10 +395,10 @@ bool check_grid(const or_grid* g) {
 }
 
 // Per Gauss point data shared by spread and interp: chi_q = sum_a N_a x_a.
-void point_of(const GaussPt& gp, const double xe[8][3], double chi[3]) {
+void point_of(const GaussPt& gp, const double xe[kMaxC][3], double chi[3]) {
   for (int i = 0; i < 3; ++i) {
     chi[i] = 0.0;
-    for (int a = 0; a < 8; ++a) chi[i] += gp.N[a] * xe[a][i];
+    for (int a = 0; a < kMaxC; ++a) chi[i] += gp.N[a] * xe[a][i];
   }
 }
 
@@ -423,7 +448,7 @@ int or_gauss_info(const or_mesh* m, const double* x, double* wj0, double* detF) 
   if (!check_mesh(m)) return -1;
   int64_t E = m->n_elems;
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     for (int q = 0; q < nq_of(m); ++q) {
@@ -442,21 +467,34 @@ int or_gauss_info(const or_mesh* m, const double* x, double* wj0, double* detF) 
   return 0;
 }
 
-// Lumped mass: row sums of the consistent mass matrix int phi_a phi_b dX by
-// the element Gauss rule; equals the nodal quadrature weight w_q = int phi_q
-// of Section 4.4.
+// Lumped mass.  Hexahedra and P1: row sums of the consistent mass matrix
+// int phi_a phi_b dX by the element Gauss rule; equals the nodal quadrature
+// weight w_q = int phi_q of Section 4.4.  P2: the row sums of a vertex are
+// negative (int N_vertex dX = -V/20), so the element's diagonal is scaled
+// instead (Hinton, Rock and Zienkiewicz 1976): m_a = d_a V / sum_b d_b with
+// d_a = sum_q w_q j0 N_a(xi_q)^2 and V = sum_q w_q j0, by the same rule;
+// every m_a > 0 and the element's masses sum to its volume.
 int or_lumped_mass(const or_mesh* m, double* mass) {
   if (!check_mesh(m)) return -1;
   std::memset(mass, 0, sizeof(double) * m->n_nodes);
   int64_t E = m->n_elems;
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3];
+    double Xe[kMaxC][3];
     gather(m, m->X, e, Xe);
+    double d[kMaxC] = {0}, V = 0.0;
     for (int q = 0; q < nq_of(m); ++q) {
       GaussPt gp;
       if (!gauss_point(m, Xe, q, gp)) return -2;
-      for (int a = 0; a < nc_of(m); ++a) mass[m->conn[a * E + e]] += gp.N[a] * gp.wj0;
+      V += gp.wj0;
+      for (int a = 0; a < nc_of(m); ++a)
+        d[a] += m->elem == 2 ? gp.N[a] * gp.N[a] * gp.wj0 : gp.N[a] * gp.wj0;
     }
+    if (m->elem == 2) {
+      double D = 0.0;
+      for (int a = 0; a < nc_of(m); ++a) D += d[a];
+      for (int a = 0; a < nc_of(m); ++a) d[a] *= V / D;
+    }
+    for (int a = 0; a < nc_of(m); ++a) mass[m->conn[a * E + e]] += d[a];
   }
   return 0;
 }
@@ -475,7 +513,7 @@ int or_fe_force(const or_mesh* m, const or_mats* mats, const double* x, double* 
     if (mid < 0 || mid >= mats->n_mats) return -1;
     const double* p = mats->params + kRow * mid;
     int model = mats->model[mid];
-    double Xe[8][3], xe[8][3], ef[3], es[3];
+    double Xe[kMaxC][3], xe[kMaxC][3], ef[3], es[3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     fibres_of(m, e, ef, es);
@@ -516,7 +554,7 @@ int or_fe_force_adj(const or_mesh* m, const or_mats* mats, const double* x,
     const double* p = mats->params + kRow * mid;
     int model = mats->model[mid];
     int np = n_params_of(model);
-    double Xe[8][3], xe[8][3], ve[8][3], ef[3], es[3];
+    double Xe[kMaxC][3], xe[kMaxC][3], ve[kMaxC][3], ef[3], es[3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, v, e, ve);
@@ -581,7 +619,7 @@ int or_spread(const or_grid* g, const or_mesh* m, const double* x, const double*
     for (int64_t a = 0; a < N; ++a) Fn[i * N + a] = G[i * N + a] / mass[a];
   double h3 = g->h * g->h * g->h;
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3], Fe[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3], Fe[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, Fn.data(), e, Fe);
@@ -620,7 +658,7 @@ int or_spread_at(const or_grid* g, const or_mesh* m, const double* x, const doub
   if (rc) return rc;
   std::vector<double> chi(3 * Q), Pq(3 * Q);
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3], Ge[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3], Ge[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, G, e, Ge);
@@ -668,7 +706,7 @@ int or_interp(const or_grid* g, const or_mesh* m, const double* x, const double*
   if (rc) return rc;
   std::memset(U, 0, sizeof(double) * 3 * N);
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     for (int q = 0; q < nq_of(m); ++q) {
@@ -714,7 +752,7 @@ int or_spread_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
   if (gx) std::memset(gx, 0, sizeof(double) * 3 * N);
   double h = g->h, h3 = h * h * h;
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3], Ge[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3], Ge[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, G, e, Ge);
@@ -774,7 +812,7 @@ int or_interp_adj(const or_grid* g, const or_mesh* m, const double* x, const dou
   if (gx) std::memset(gx, 0, sizeof(double) * 3 * N);
   double h = g->h;
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3], gUe[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3], gUe[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     gather(m, gU, e, gUe);
@@ -959,7 +997,7 @@ int64_t or_support_count(const or_grid* g, const or_mesh* m, const double* x) {
   int64_t cells = (int64_t)g->n[0] * g->n[1] * g->n[2];
   std::vector<unsigned char> mark(3 * cells, 0);
   for (int e = 0; e < E; ++e) {
-    double Xe[8][3], xe[8][3];
+    double Xe[kMaxC][3], xe[kMaxC][3];
     gather(m, m->X, e, Xe);
     gather(m, x, e, xe);
     for (int q = 0; q < nq_of(m); ++q) {

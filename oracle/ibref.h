@@ -25,7 +25,9 @@
  *            reference coordinates X [3][N]; 2x2x2 Gauss rule at +-1/sqrt(3),
  *            Gauss point q = b0 + 2 b1 + 4 b2 with xi_d = (2 b_d - 1)/sqrt(3);
  *            or linear tetrahedra (elem 1), conn [4][E], with the symmetric
- *            4-point rule of degree 2 (point q nearest corner q).
+ *            4-point rule of degree 2 (point q nearest corner q); or
+ *            quadratic tetrahedra (elem 2), conn [10][E] (VTK order: 4
+ *            vertices, then edges 01, 12, 02, 03, 13, 23), the same rule.
  *   positions x [3][N] (double; tests rebuild them exactly from the split
  *            cell + offset storage).  Cells are not wrapped; the grid index
  *            is taken modulo n.
@@ -55,11 +57,11 @@ typedef struct {
 
 typedef struct {
   int32_t n_nodes, n_elems;
-  const int32_t* conn;   /* [8][E] hexahedra or [4][E] tetrahedra */
+  const int32_t* conn;   /* [8][E] hexahedra, [4][E] or [10][E] tetrahedra */
   const double* X;       /* [3][N] */
   const double* fibres;  /* [6][E] or NULL */
   const int32_t* mat_id; /* [E] or NULL */
-  int32_t elem;          /* 0: trilinear hexahedron, 1: linear tetrahedron */
+  int32_t elem;          /* 0: trilinear hexahedron, 1: linear, 2: quadratic tetrahedron */
 } or_mesh;
 
 typedef struct {

@@ -98,8 +98,9 @@ class Problem:
 
     @property
     def n_gauss(self) -> int:
-        """Points of the element rule: 8 per hexahedron, 4 per tetrahedron."""
-        return (4 if self.conn.shape[0] == 4 else 8) * self.n_elems
+        """Points of the element rule: 8 per hexahedron, 4 per tetrahedron
+        (linear or quadratic)."""
+        return (8 if self.conn.shape[0] == 8 else 4) * self.n_elems
 
 
 # ----------------------------------------------------------------------------
@@ -487,6 +488,48 @@ def tet_problem(base: Problem) -> Problem:
     return dataclasses.replace(base, name=base.name + "-tet", conn=conn.astype(np.int32),
                                fibres=np.ascontiguousarray(fib.astype(base.fibres.dtype)),
                                mat_id=np.ascontiguousarray(mid.astype(np.int32)))
+
+
+# P2 edge nodes in VTK order: the vertex pair of each of the six edges
+TET10_EDGES = ((0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3))
+
+
+def tets_to_quadratic(conn4: np.ndarray, n_nodes: int):
+    """Quadratic tetrahedra [10][E] from linear ones [4][E]: one new node per
+    distinct edge, numbered n_nodes, n_nodes + 1, ... in ascending order of
+    the edge's (smaller, larger) vertex pair.  Returns (conn10, edges) with
+    edges [2][n_edges] the vertex pair of each new node."""
+    E = conn4.shape[1]
+    a = np.stack([conn4[i] for i, _ in TET10_EDGES]).astype(np.int64)
+    b = np.stack([conn4[j] for _, j in TET10_EDGES]).astype(np.int64)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keys = (lo * n_nodes + hi).ravel()
+    uniq, inv = np.unique(keys, return_inverse=True)
+    conn10 = np.concatenate([conn4, (n_nodes + inv).reshape(6, E)], axis=0)
+    return np.ascontiguousarray(conn10.astype(np.int32)), np.stack([uniq // n_nodes,
+                                                                   uniq % n_nodes])
+
+
+def tet10_problem(base: Problem, seed: int = 77, bend: float = 0.05) -> Problem:
+    """The same structure as quadratic (P2) tetrahedra, the element of the
+    paper's Cook membrane (Section 5): every hexahedron split into six
+    tetrahedra, a node added at the middle of every edge.  The new nodes sit
+    at the edge midpoints in the reference configuration (straight-sided
+    elements) and at the midpoints of the current edge ends displaced by a
+    seeded uniform +-bend*h, so that the current elements are curved."""
+    t = tet_problem(base)
+    conn10, edges = tets_to_quadratic(t.conn, t.n_nodes)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X64 = t.X.astype(np.float64)
+    Xm = 0.5 * (X64[:, edges[0]] + X64[:, edges[1]])
+    xm = 0.5 * (t.x[:, edges[0]] + t.x[:, edges[1]])
+    xm = xm + rng.uniform(-bend, bend, size=xm.shape) * t.grid.h
+    X = np.concatenate([X64, Xm], axis=1).astype(t.X.dtype)
+    x = np.concatenate([t.x, xm], axis=1)
+    cell, off = to_split(x, t.grid)
+    return dataclasses.replace(t, name=base.name + "-tet10", conn=conn10,
+                               X=np.ascontiguousarray(X), x=x,
+                               cell=np.ascontiguousarray(cell), off=np.ascontiguousarray(off))
 
 
 def batch_problems(seed: int = 5000, count: int = 48, sizes=(32, 64, 96, 128),

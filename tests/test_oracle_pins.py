@@ -7,6 +7,7 @@ and torque under spreading, exactness of interpolation on constant and linear
 fields, the discrete adjointness of spreading and interpolation (Section 4.4),
 and brute-force sums over every grid face.
 """
+import dataclasses
 import math
 import os
 
@@ -964,3 +965,152 @@ def test_tet_adjoints_and_transfer_identities():
     u = rng.normal(size=(3, n2, n1, n0))
     U = m.interp(x, u)
     assert h3 * np.sum(f * u) == pytest.approx(np.sum(G * U), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# quadratic tetrahedra (P2) with the 4-point rule
+# ---------------------------------------------------------------------------
+
+def tiny_tet10(model=I.HO, params=I.HO_DEFAULT, seed=7, blocks=(2, 2, 1)):
+    return I.tet10_problem(tiny_mesh(model, params, seed=seed, blocks=blocks))
+
+
+_TA = (5 + 3 * np.sqrt(5)) / 20   # barycentric coordinates of the 4-point rule
+_TB = (5 - np.sqrt(5)) / 20
+
+
+def _rule_points_ref(p):
+    """Reference positions of the rule points, from the vertices alone (the
+    reference elements are straight-sided): X_q = a X_q + b sum_{i != q} X_i."""
+    V = [p.X[:, p.conn[i]].astype(np.float64) for i in range(4)]
+    return np.stack([_TB * sum(V) + (_TA - _TB) * V[q] for q in range(4)])  # [4][3][E]
+
+
+def _quad_map(X):
+    """A smooth quadratic deformation and its gradient, in closed form."""
+    c = X - 0.5
+    x = np.stack([c[0] + 0.3 * c[0] * c[1] + 0.2 * c[2] ** 2,
+                  c[1] - 0.25 * c[0] ** 2 + 0.1 * c[1] * c[2],
+                  c[2] + 0.15 * c[0] * c[2] - 0.2 * c[1] ** 2]) + 0.5
+    F = np.zeros((3, 3) + X.shape[1:])
+    F[0, 0], F[0, 1], F[0, 2] = 1 + 0.3 * c[1], 0.3 * c[0], 0.4 * c[2]
+    F[1, 0], F[1, 1], F[1, 2] = -0.5 * c[0], 1 + 0.1 * c[2], 0.1 * c[1]
+    F[2, 0], F[2, 1], F[2, 2] = 0.15 * c[2], -0.4 * c[1], 1 + 0.15 * c[0]
+    return x, F
+
+
+def test_tet10_quadratic_fields_are_reproduced():
+    """P2 reproduces quadratic maps exactly: under x = phi(X) quadratic, det F
+    at every rule point equals det grad phi there, and interpolating the
+    coordinate field (the 4-point kernel reproduces linear functions) gives
+    back the rule points phi(X_q): this pins the ten shape functions, their
+    gradients and the rule's points (each from its closed form)."""
+    p = tiny_tet10(blocks=(2, 2, 2))
+    m = oracle.Model(p)
+    x, _ = _quad_map(p.X)
+    _, detF = m.gauss_info(x)
+    Xq = _rule_points_ref(p)                         # [4][3][E]
+    for q in range(4):
+        _, Fq = _quad_map(Xq[q])
+        np.testing.assert_allclose(detF[q], np.linalg.det(np.moveaxis(Fq, -1, 0)), rtol=1e-12)
+    # coordinate field on the faces: u^c(face) = its c coordinate (no wrap
+    # near the structure, which sits in the middle of the box)
+    n0, n1, n2 = p.grid.n
+    h = p.grid.h
+    u = np.zeros((3, n2, n1, n0))
+    u[0] += (np.arange(n0) * h)[None, None, :]
+    u[1] += (np.arange(n1) * h)[None, :, None]
+    u[2] += (np.arange(n2) * h)[:, None, None]
+    _, Uq = m.interp(x, u, want_gauss=True)
+    for q in range(4):
+        chi, _ = _quad_map(Xq[q])
+        # faces of component c sit at i h in direction c (no staggering there)
+        np.testing.assert_allclose(Uq[:, q], chi, rtol=0, atol=1e-12)
+
+
+def test_tet10_mass_is_the_scaled_diagonal():
+    """Lumped P2 mass (diagonal scaling of Hinton, Rock and Zienkiewicz):
+    positive, the element masses sum to the volume, and on a straight-sided
+    element vertex : edge masses are the rule's sums of N^2, in closed form
+    from the rule's barycentric coordinates: N_vertex = +-1/10 at the four
+    points, N_edge = (1 + sqrt 5)/10 at two and (3 - sqrt 5)/10 at two."""
+    p = tiny_tet10()
+    m = oracle.Model(p)
+    M = m.mass()
+    assert (M > 0).all()
+    assert M.sum() == pytest.approx(2 * 2 * 1 * p.grid.h ** 3, rel=1e-13)
+    sv = 4 * 0.01
+    se = 2 * ((1 + np.sqrt(5)) / 10) ** 2 + 2 * ((3 - np.sqrt(5)) / 10) ** 2
+    one = dataclasses.replace(p, conn=np.ascontiguousarray(p.conn[:, :1]))
+    M1 = oracle.Model(one).mass()
+    V = np.dot(np.cross(*(p.X[:, p.conn[k, 0]] - p.X[:, p.conn[0, 0]] for k in (1, 2))),
+               p.X[:, p.conn[3, 0]] - p.X[:, p.conn[0, 0]]) / 6
+    np.testing.assert_allclose(M1[p.conn[:4, 0]], V * 0.01 / (sv + 6 * se / 4), rtol=1e-12)
+    np.testing.assert_allclose(M1[p.conn[4:, 0]], V * (se / 4) / (sv + 6 * se / 4), rtol=1e-12)
+
+
+@pytest.mark.parametrize("model,params", MODELS)
+def test_tet10_patch_test_and_energy_gradient(model, params):
+    """P2 patch test (interior nodes free of force under an affine
+    deformation), G = -dE/dx by differences, zero force at the reference and
+    under rigid motion."""
+    p = tiny_tet10(model, params, blocks=(2, 2, 2))
+    p.fibres = np.ascontiguousarray(np.repeat(p.fibres[:, :1], p.n_elems, axis=1))
+    m = oracle.Model(p)
+    A = np.eye(3) + np.array([[0.05, 0.02, -0.01], [0.0, -0.03, 0.04], [0.01, 0.0, 0.02]])
+    G, _ = m.fe_force(A @ (p.X - 0.5) + 0.5)
+    X = p.X
+    interior = np.flatnonzero(np.all([(X[d] > X[d].min() + 1e-12) & (X[d] < X[d].max() - 1e-12)
+                                      for d in range(3)], axis=0))
+    assert len(interior) > 8
+    assert np.abs(G[:, interior]).max() < 1e-10 * np.abs(G).max()
+    scale = params[-1] * p.grid.h ** 2
+    G0, E0 = m.fe_force(X)
+    assert np.abs(G0).max() < 1e-12 * scale and abs(E0) < 1e-15
+    Q = rot(np.random.default_rng(6))
+    G1, E1 = m.fe_force(Q @ (X - 0.5) + 0.5)
+    assert np.abs(G1).max() < 1e-11 * scale and abs(E1) < 1e-15
+    x = p.x
+    G, _ = m.fe_force(x)
+    eps = 1e-6 * p.grid.h
+    rng = np.random.default_rng(12)
+    for _ in range(8):
+        a, i = rng.integers(p.n_nodes), rng.integers(3)
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = -(m.fe_force(xp)[1] - m.fe_force(xm)[1]) / (2 * eps)
+        assert G[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-8 * np.abs(G).max())
+
+
+def test_tet10_adjoints_and_transfer_identities():
+    """On the P2 mesh: the force adjoint by differences, the spread against
+    the brute-force sum over every face, the discrete adjointness of spreading
+    and interpolation, and a uniform force density (nodal forces g m_a) spread
+    to a field whose total is g times the structure's volume (the shape
+    functions sum to one at every rule point)."""
+    p = tiny_tet10()
+    m = oracle.Model(p)
+    x = p.x
+    rng = np.random.default_rng(13)
+    v = rng.normal(size=x.shape)
+    Hv, _ = m.fe_force_adj(x, v)
+    eps = 1e-7 * p.grid.h
+    fd = (m.fe_force(x + eps * v)[0] - m.fe_force(x - eps * v)[0]) / (2 * eps)
+    np.testing.assert_allclose(Hv, fd, rtol=1e-5, atol=1e-6 * np.abs(Hv).max())
+    G = rng.normal(size=x.shape)
+    f = m.spread(x, G)
+    n0, n1, n2 = p.grid.n
+    comp = np.repeat(np.arange(3), n0 * n1 * n2).astype(np.int32)
+    kk, jj, ii = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    idx = np.tile(np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1), (3, 1))
+    np.testing.assert_allclose(f.ravel(), m.spread_at(x, G, comp, idx), rtol=1e-12,
+                               atol=1e-12 * np.abs(f).max())
+    h3 = p.grid.h ** 3
+    u = rng.normal(size=(3, n2, n1, n0))
+    U = m.interp(x, u)
+    assert h3 * np.sum(f * u) == pytest.approx(np.sum(G * U), rel=1e-12)
+    g = np.array([0.3, -1.2, 0.7])
+    fu = m.spread(x, g[:, None] * m.mass()[None, :])
+    w, _ = m.gauss_info(x)
+    np.testing.assert_allclose(fu.sum(axis=(1, 2, 3)) * h3, g * w.sum(), rtol=1e-12)
