@@ -366,6 +366,27 @@ def run_ours(args):
     del plant
     barrier()
 
+    # --- quadratic (P2) tetrahedra: a node added at every edge's middle -----
+    qprob = I.tet10_problem(prob)
+    planq = ibfe.Plan(torch.from_numpy(qprob.conn).to(dev),
+                      torch.from_numpy(qprob.X).to(dev), prob.grid.n, prob.grid.h,
+                      fibres=torch.from_numpy(qprob.fibres).to(dev),
+                      mat_id=torch.from_numpy(qprob.mat_id).to(dev))
+    posq = ibfe.Pos(cell=torch.from_numpy(qprob.cell).to(dev),
+                    off=torch.from_numpy(qprob.off).to(dev))
+    ibfe.ib_plan_autotune(planq, mats, posq, u)
+    Gq = torch.empty((3, qprob.n_nodes), device=dev)
+    Uq = torch.empty((3, qprob.n_nodes), device=dev)
+    fwdq = lambda: ibfe.ib_forward(planq, mats, posq, u, Gq, f, Uq)
+    for _ in range(args.warmup):
+        fwdq()
+    barrier()
+    msq = timed(fwdq, args.steps)
+    t_fwdq = sum(msq) / len(msq)
+    Eq, Nq, Qq = qprob.n_elems, qprob.n_nodes, qprob.n_gauss
+    del planq, posq, Gq, Uq, qprob
+    barrier()
+
     # --- adjoint ---------------------------------------------------------
     rng = np.random.default_rng(77 + rank)
     gU = torch.from_numpy(rng.normal(size=(3, N)).astype(np.float32)).to(dev)
@@ -634,6 +655,11 @@ def run_ours(args):
                        "value": Qt * world / (t_fwdt * 1e-3), "unit": UNIT,
                        "note": "the same forward with every hexahedron split into six linear "
                                "tetrahedra (4-point coupling rule; force at the centroid)"},
+        "tetrahedra_p2": {"ms_per_step": t_fwdq, "elements": Eq, "nodes": Nq, "points": Qq,
+                          "value": Qq * world / (t_fwdq * 1e-3), "unit": UNIT,
+                          "note": "the same forward on quadratic tetrahedra (the six tetrahedra "
+                                  "per hexahedron with a node at every edge's middle; 4-point "
+                                  "rule for force and coupling)"},
         "batched": batch_line,
         "fluid": fluid_line,
         "adjoint_ms_per_step": t_adj,

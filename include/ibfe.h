@@ -109,12 +109,18 @@ typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_pr
  * 2x2x2 Gauss rule (8 coupling points per element).  IB_ELEM_TET4: linear
  * tetrahedra (the element of the paper's valve meshes, Section 5), VTK order
  * with positive volume, the symmetric 4-point rule of degree 2 (4 coupling
- * points per element); the P1 force is evaluated exactly at the centroid. */
-typedef enum { IB_ELEM_HEX8 = 0, IB_ELEM_TET4 = 1 } ib_elem;
+ * points per element); the P1 force is evaluated exactly at the centroid.
+ * IB_ELEM_TET10: quadratic tetrahedra (P2, the element of the paper's Cook
+ * membrane, Section 5), VTK order: the 4 vertices, then the nodes of edges
+ * 01, 12, 02, 03, 13, 23; the same 4-point rule for the force and the
+ * coupling (4 coupling points per element); lumped mass by diagonal scaling
+ * (the element's sums of w j0 N_a^2, scaled to its volume), since the P2 row
+ * sums of a vertex are negative. */
+typedef enum { IB_ELEM_HEX8 = 0, IB_ELEM_TET4 = 1, IB_ELEM_TET10 = 2 } ib_elem;
 
 typedef struct {
   int32_t n_nodes, n_elems;
-  const int32_t* conn;   /* device [8][n_elems] (hexahedra) or [4][n_elems] (tetrahedra) */
+  const int32_t* conn;   /* device [8][n_elems] (hexahedra), [4][n_elems] or [10][n_elems] (tetrahedra) */
   const void* X;         /* device Real [3][n_nodes] reference coordinates */
   const void* fibres;    /* device Real [6][n_elems]: e_f then e_s, or NULL (e_f = x, e_s = y) */
   const int32_t* mat_id; /* device [n_elems] index into the material table, or NULL (all 0) */

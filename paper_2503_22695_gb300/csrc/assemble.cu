@@ -9,7 +9,7 @@
 namespace ibfe {
 namespace {
 
-constexpr int kIncShift = 28;  // incidence entry: corner << 28 | element
+constexpr int kIncShift = 28;  // incidence entry: corner << 28 | element (as uint32)
 
 // out[c][n] = add[c][n] + scale[n] * sum_{(a,e) in inc(n)} elem[(a*ncomp + c)*E + e]
 // (add and scale optional; add may be out itself)
@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
   for (int c = 0; c < NC; ++c) acc[c] = Real(0);
   const int b = __ldg(inc_off + n), en = __ldg(inc_off + n + 1);
   for (int k = b; k < en; ++k) {
-    const int32_t v = __ldg(inc_idx + k);
-    const int a = v >> kIncShift, e = v & ((1 << kIncShift) - 1);
+    // unsigned: corners 8 and 9 of a P2 element set the top bit
+    const uint32_t v = static_cast<uint32_t>(__ldg(inc_idx + k));
+    const int a = (int)(v >> kIncShift), e = (int)(v & ((1u << kIncShift) - 1u));
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] += __ldg(elem + (int64_t)(a * NC + c) * E + e);
   }
@@ -106,24 +107,36 @@ __global__ void __launch_bounds__(128) k_wj0(const int32_t* __restrict__ conn,
   if (bad) set_status(status, kStatInverted);
 }
 
-// Lumped mass in double from the FP32 weights of an FP32 plan: per corner
-// sum_q N_a(xi_q) w_q j0 in double, then the node gather in double.  The
-// rounded FP32 mass is then, in practice, independent of the order in which
-// the elements are listed (the point values carried by spreading divide by
-// it).
-template <int kEl>
-__global__ void __launch_bounds__(256) k_mass_corner_d(const float* __restrict__ wj0, int E,
+// Per-element lumped mass in double from the weights w_q j0 (Real): for
+// hexahedra and P1 the row sums sum_q N_a(xi_q) w_q j0; for P2 the diagonal
+// d_a = sum_q N_a(xi_q)^2 w_q j0 scaled by V / sum_b d_b, V = sum_q w_q j0
+// (every mass positive, the element's masses summing to its volume).  The
+// node gather then sums in double, so the rounded FP32 mass is, in
+// practice, independent of the order in which the elements are listed (the
+// point values carried by spreading divide by it).
+template <typename Real, int kEl>
+__global__ void __launch_bounds__(256) k_mass_corner_d(const Real* __restrict__ wj0, int E,
                                                        double* __restrict__ out) {
   using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
+  double w[EL::Q], d[EL::C], V = 0.0, D = 0.0;
+#pragma unroll
+  for (int q = 0; q < EL::Q; ++q) {
+    w[q] = double(__ldg(wj0 + (int64_t)q * E + e));
+    V += w[q];
+  }
 #pragma unroll
   for (int a = 0; a < EL::C; ++a) {
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < EL::Q; ++q) s += EL::N(a, q) * double(__ldg(wj0 + (int64_t)q * E + e));
-    out[(int64_t)a * E + e] = s;
+    for (int q = 0; q < EL::Q; ++q)
+      s += (EL::kScaledMass ? EL::N(a, q) * EL::N(a, q) : EL::N(a, q)) * w[q];
+    d[a] = s;
+    D += s;
   }
+#pragma unroll
+  for (int a = 0; a < EL::C; ++a) out[(int64_t)a * E + e] = EL::kScaledMass ? d[a] * (V / D) : d[a];
 }
 
 __global__ void k_mass_round(const double* __restrict__ md, float* __restrict__ m,
@@ -162,54 +175,49 @@ template <typename Real>
 ib_status project_t(ib_plan* p, const void* vals, void* out, int nc, cudaStream_t s) {
   if (p->E == 0) return IB_OK;
   const int blocks = (p->E + 255) / 256;
-  if (p->elem == IB_ELEM_TET4) {
+  with_elem(p->elem, [&](auto el) {
+    constexpr int kE = decltype(el)::value;
     if (nc == 3)
-      k_elem_project<Real, 3, IB_ELEM_TET4><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
-                                                                   (Real*)out);
+      k_elem_project<Real, 3, kE><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
     else
-      k_elem_project<Real, 1, IB_ELEM_TET4><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
-                                                                   (Real*)out);
-  } else if (nc == 3) {
-    k_elem_project<Real, 3, IB_ELEM_HEX8><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
-                                                                 (Real*)out);
-  } else {
-    k_elem_project<Real, 1, IB_ELEM_HEX8><<<blocks, 256, 0, s>>>((const Real*)vals, p->E,
-                                                                 (Real*)out);
-  }
+      k_elem_project<Real, 1, kE><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+  });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
 template <typename Real>
 ib_status static_t(ib_plan* p, cudaStream_t s) {
   if (p->E > 0) {
-    if (p->elem == IB_ELEM_TET4)
-      k_wj0<Real, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(
-          p->conn, (const Real*)p->X, p->E, p->N, (Real*)p->wj0, p->dstatus);
-    else
-      k_wj0<Real, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(
-          p->conn, (const Real*)p->X, p->E, p->N, (Real*)p->wj0, p->dstatus);
+    with_elem(p->elem, [&](auto el) {
+      constexpr int kE = decltype(el)::value;
+      k_wj0<Real, kE><<<(p->E + 127) / 128, 128, 0, s>>>(p->conn, (const Real*)p->X, p->E, p->N,
+                                                       (Real*)p->wj0, p->dstatus);
+    });
     if (cudaGetLastError() != cudaSuccess) return IB_ERR_CUDA;
   }
-  // m_a = sum_{(e,q) containing a} N_a(xi_q) w_q j0
-  if (sizeof(Real) == 4) {  // accumulated in double, rounded once
+  // m_a = sum over the elements containing a of the element's lumped mass
+  if (sizeof(Real) == 4 || p->elem == IB_ELEM_TET10) {  // accumulated in double
     double *ed = nullptr, *md = nullptr;
     if (cudaMalloc(&ed, sizeof(double) * p->nc * (size_t)(p->E > 0 ? p->E : 1)) != cudaSuccess ||
         cudaMalloc(&md, sizeof(double) * (size_t)p->N) != cudaSuccess) {
       cudaFree(ed);
       return IB_ERR_CUDA;
     }
-    if (p->E > 0) {
-      if (p->elem == IB_ELEM_TET4)
-        k_mass_corner_d<IB_ELEM_TET4><<<(p->E + 255) / 256, 256, 0, s>>>((const float*)p->wj0,
-                                                                         p->E, ed);
-      else
-        k_mass_corner_d<IB_ELEM_HEX8><<<(p->E + 255) / 256, 256, 0, s>>>((const float*)p->wj0,
-                                                                         p->E, ed);
-    }
+    if (p->E > 0)
+      with_elem(p->elem, [&](auto el) {
+        constexpr int kE = decltype(el)::value;
+        k_mass_corner_d<Real, kE><<<(p->E + 255) / 256, 256, 0, s>>>((const Real*)p->wj0, p->E,
+                                                                     ed);
+      });
     k_node_gather<double, 1><<<(p->N + 255) / 256, 256, 0, s>>>(
         p->inc_off, p->inc_idx, ed, nullptr, nullptr, p->N, p->E, md);
-    k_mass_round<<<(p->N + 255) / 256, 256, 0, s>>>(md, (float*)p->mass, (float*)p->inv_mass,
-                                                    p->N);
+    if (sizeof(Real) == 4)
+      k_mass_round<<<(p->N + 255) / 256, 256, 0, s>>>(md, (float*)p->mass, (float*)p->inv_mass,
+                                                      p->N);
+    else if (p->N > 0) {
+      cudaMemcpyAsync(p->mass, md, sizeof(double) * p->N, cudaMemcpyDeviceToDevice, s);
+      k_invert<double><<<(p->N + 255) / 256, 256, 0, s>>>(md, (double*)p->inv_mass, p->N);
+    }
     const bool good = cudaStreamSynchronize(s) == cudaSuccess;
     cudaFree(ed);
     cudaFree(md);

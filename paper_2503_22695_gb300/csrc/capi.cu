@@ -261,9 +261,12 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   if (quad != IB_QUAD_GAUSS2 && quad != IB_QUAD_NODAL) return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
     return IB_ERR_INVALID_ARG;
-  if (mesh->elem_type != IB_ELEM_HEX8 && mesh->elem_type != IB_ELEM_TET4)
+  if (mesh->elem_type != IB_ELEM_HEX8 && mesh->elem_type != IB_ELEM_TET4 &&
+      mesh->elem_type != IB_ELEM_TET10)
     return IB_ERR_INVALID_ARG;
-  const int nc = mesh->elem_type == IB_ELEM_TET4 ? 4 : 8;  // corners = coupling points
+  // nodes and coupling points per element
+  const int nc = mesh->elem_type == IB_ELEM_TET10 ? 10 : (mesh->elem_type == IB_ELEM_TET4 ? 4 : 8);
+  const int nq = mesh->elem_type == IB_ELEM_HEX8 ? 8 : 4;
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (!std::isfinite(grid->origin[d])) return IB_ERR_INVALID_ARG;
@@ -275,7 +278,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   // Q coupling points: the element rule's points (8 per hexahedron, 4 per
   // tetrahedron) or the nodes
   const int64_t E = mesh->n_elems, N = mesh->n_nodes;
-  const int64_t Q = quad == IB_QUAD_NODAL ? N : nc * E;
+  const int64_t Q = quad == IB_QUAD_NODAL ? N : nq * E;
 
   // connectivity and materials to the host for validation and incidence lists
   std::vector<int32_t> conn(nc * E), mid;
@@ -305,7 +308,9 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   {
     std::vector<int32_t> fill(inc_off.begin(), inc_off.end() - 1);
     for (int64_t e = 0; e < E; ++e)
-      for (int a = 0; a < nc; ++a) inc_idx[fill[conn[a * E + e]]++] = (a << kIncShift) | (int32_t)e;
+      for (int a = 0; a < nc; ++a)
+        inc_idx[fill[conn[a * E + e]]++] =
+            static_cast<int32_t>((static_cast<uint32_t>(a) << kIncShift) | static_cast<uint32_t>(e));
   }
 
   ib_plan* p = new ib_plan;
@@ -314,7 +319,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   p->quad = quad;
   p->elem = mesh->elem_type;
   p->nc = nc;
-  p->nq = nc;
+  p->nq = nq;
   p->chunk = kChunk;
   p->fe_ctas = 2;
   p->push_per_sm = 8;

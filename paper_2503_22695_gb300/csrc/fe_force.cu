@@ -80,11 +80,13 @@ int law_set(const MatTable& mt, bool params) {
 #define HEX IB_ELEM_HEX8
 
 namespace {
-// Tetrahedral meshes: one instantiation per precision and output (all laws).
+// Tetrahedral meshes (P1 and P2): one instantiation per precision and
+// output (all laws).
+template <int T>
 ib_status tet_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                     const void* v, void* out, bool energy, bool adj, bool params,
                     cudaStream_t s) {
-  constexpr int T = IB_ELEM_TET4, L = kLawAll;
+  constexpr int L = kLawAll;
   if (p->precision == IB_FP64) {
     if (adj)
       return params ? fe_run<double, double, false, true, true, L, T>(IBFE_FE_ARGS)
@@ -110,7 +112,10 @@ ib_status tet_force(ib_plan* p, const MatTable& mt, const void* xa, const float*
 ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                           void* out, bool energy, cudaStream_t s) {
   const void* v = nullptr;
-  if (p->elem == IB_ELEM_TET4) return tet_force(p, mt, xa, off, v, out, energy, false, false, s);
+  if (p->elem == IB_ELEM_TET4)
+    return tet_force<IB_ELEM_TET4>(p, mt, xa, off, v, out, energy, false, false, s);
+  if (p->elem == IB_ELEM_TET10)
+    return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, energy, false, false, s);
   const int set = law_set(mt, false);
   if (p->precision == IB_FP64)
     return energy ? fe_run<double, double, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS)
@@ -131,7 +136,10 @@ ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const 
 
 ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
                               const void* v, void* out, bool params, cudaStream_t s) {
-  if (p->elem == IB_ELEM_TET4) return tet_force(p, mt, xa, off, v, out, false, true, params, s);
+  if (p->elem == IB_ELEM_TET4)
+    return tet_force<IB_ELEM_TET4>(p, mt, xa, off, v, out, false, true, params, s);
+  if (p->elem == IB_ELEM_TET10)
+    return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, false, true, params, s);
   const int set = law_set(mt, params);
   if (p->precision == IB_FP64)
     return params ? fe_run<double, double, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS)

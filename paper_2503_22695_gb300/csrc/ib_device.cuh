@@ -47,7 +47,14 @@ __host__ __device__ constexpr double shape_dxi(int a, int q, int d) {
 // (barycentric (a, b, b, b) and permutations, point q nearest corner q,
 // weights 1/24), and its force, whose integrand is constant, is evaluated
 // once at the centroid with the whole reference volume 1/6.
-//   C: corners, Q: coupling points, QF: force points, N(a, q): shape value at
+// El<IB_ELEM_TET10>: the quadratic tetrahedron (P2), VTK node order (the 4
+// vertices, then the nodes of edges 01, 12, 02, 03, 13, 23); with the
+// barycentric coordinates L_i of P1, N = L_i (2 L_i - 1) at a vertex and
+// 4 L_i L_j at the node of edge (i, j).  The same 4-point rule serves the
+// force (degree 2: exact for P : grad N of an affine element under an affine
+// deformation) and the coupling; its lumped mass scales the element's
+// diagonal sum_q w_q j0 N_a^2 to the element's volume (kScaledMass).
+//   C: nodes, Q: coupling points, QF: force points, N(a, q): shape value at
 //   coupling point q, dxi(a, q, d): reference gradient at force point q,
 //   wQ / wF: reference weights of the two rules.
 // ---------------------------------------------------------------------------
@@ -58,6 +65,7 @@ template <>
 struct El<IB_ELEM_HEX8> {
   static constexpr int C = 8, Q = 8, QF = 8;
   static constexpr double wQ = 1.0, wF = 1.0;
+  static constexpr bool kScaledMass = false;
   __host__ __device__ static constexpr double N(int a, int q) { return shapeN(a, q); }
   __host__ __device__ static constexpr double dxi(int a, int q, int d) {
     return shape_dxi(a, q, d);
@@ -68,11 +76,36 @@ template <>
 struct El<IB_ELEM_TET4> {
   static constexpr int C = 4, Q = 4, QF = 1;
   static constexpr double wQ = 1.0 / 24.0, wF = 1.0 / 6.0;
+  static constexpr bool kScaledMass = false;
   static constexpr double kTa = 0.58541019662496845446;  // (5 + 3 sqrt 5) / 20
   static constexpr double kTb = 0.13819660112501051518;  // (5 - sqrt 5) / 20
   __host__ __device__ static constexpr double N(int a, int q) { return a == q ? kTa : kTb; }
   __host__ __device__ static constexpr double dxi(int a, int, int d) {
     return a == 0 ? -1.0 : (a - 1 == d ? 1.0 : 0.0);
+  }
+};
+
+template <>
+struct El<IB_ELEM_TET10> {
+  static constexpr int C = 10, Q = 4, QF = 4;
+  static constexpr double wQ = 1.0 / 24.0, wF = 1.0 / 24.0;
+  static constexpr bool kScaledMass = true;
+  // barycentric coordinate i at rule point q and its (constant) xi-gradient
+  __host__ __device__ static constexpr double L(int i, int q) {
+    return i == q ? El<IB_ELEM_TET4>::kTa : El<IB_ELEM_TET4>::kTb;
+  }
+  __host__ __device__ static constexpr double dL(int i, int d) {
+    return El<IB_ELEM_TET4>::dxi(i, 0, d);
+  }
+  // vertices of the edge of node 4 + k
+  __host__ __device__ static constexpr int ev0(int k) { return k == 1 ? 1 : (k == 4 ? 1 : (k == 5 ? 2 : 0)); }
+  __host__ __device__ static constexpr int ev1(int k) { return k == 0 ? 1 : (k <= 2 ? 2 : 3); }
+  __host__ __device__ static constexpr double N(int a, int q) {
+    return a < 4 ? L(a, q) * (2.0 * L(a, q) - 1.0) : 4.0 * L(ev0(a - 4), q) * L(ev1(a - 4), q);
+  }
+  __host__ __device__ static constexpr double dxi(int a, int q, int d) {
+    return a < 4 ? (4.0 * L(a, q) - 1.0) * dL(a, d)
+                 : 4.0 * (L(ev0(a - 4), q) * dL(ev1(a - 4), d) + L(ev1(a - 4), q) * dL(ev0(a - 4), d));
   }
 };
 

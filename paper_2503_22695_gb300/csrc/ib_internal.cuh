@@ -4,10 +4,22 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "ibfe.h"
 
 namespace ibfe {
+
+// Calls f(std::integral_constant<int, kEl>) for the plan's element type.
+template <typename F>
+void with_elem(int elem, F&& f) {
+  if (elem == IB_ELEM_TET4)
+    f(std::integral_constant<int, IB_ELEM_TET4>{});
+  else if (elem == IB_ELEM_TET10)
+    f(std::integral_constant<int, IB_ELEM_TET10>{});
+  else
+    f(std::integral_constant<int, IB_ELEM_HEX8>{});
+}
 
 constexpr int kTile = 8;            // Eulerian tile edge (cells) of the spread kernel
 constexpr int kTileShift = 3;
@@ -92,7 +104,7 @@ struct ib_plan {
   int precision;         // ib_precision
   int quad;              // ib_quad: coupling points are Gauss points or nodes
   int elem;              // ib_elem
-  int nc, nq;            // corners and coupling points per element (8, 8 or 4, 4)
+  int nc, nq;            // nodes and coupling points per element (hex 8, 8; P1 4, 4; P2 10, 4)
   int N, E;
   int64_t Q;             // coupling points: 8 E Gauss points or N nodes
   ibfe::GridDev grid;

@@ -425,10 +425,10 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   cudaMemsetAsync(p->tile_end, 0, sizeof(int32_t) * p->ntiles, s);
   if (p->quad == IB_QUAD_NODAL)
     k_points_nodal<float, true><<<(p->N + 255) / 256, 256, 0, s>>>(A);
-  else if (p->elem == IB_ELEM_TET4)
-    k_points<float, true, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   else
-    k_points<float, true, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    with_elem(p->elem, [&](auto el) {
+      k_points<float, true, decltype(el)::value><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -456,10 +456,10 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
   A.count = nullptr;
   if (p->quad == IB_QUAD_NODAL)
     k_points_nodal<double, false><<<(p->N + 255) / 256, 256, 0, s>>>(A);
-  else if (p->elem == IB_ELEM_TET4)
-    k_points<double, false, IB_ELEM_TET4><<<(p->E + 127) / 128, 128, 0, s>>>(A);
   else
-    k_points<double, false, IB_ELEM_HEX8><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    with_elem(p->elem, [&](auto el) {
+      k_points<double, false, decltype(el)::value><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+    });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -526,16 +526,17 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
                ? IB_OK
                : IB_ERR_CUDA;
   const int g = (p->E + 127) / 128;
-  const bool tet = p->elem == IB_ELEM_TET4;
-  if (p->precision == IB_FP64) {
-    auto k = tet ? k_point_values<double, IB_ELEM_TET4> : k_point_values<double, IB_ELEM_HEX8>;
-    k<<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const double*)nodal, (const double*)p->inv_mass,
-                        (const double*)p->wj0, (double*)p->q_val);
-  } else {
-    auto k = tet ? k_point_values<float, IB_ELEM_TET4> : k_point_values<float, IB_ELEM_HEX8>;
-    k<<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const float*)nodal, (const float*)p->inv_mass,
-                        (const float*)p->wj0, (float*)p->q_val);
-  }
+  with_elem(p->elem, [&](auto el) {
+    constexpr int kE = decltype(el)::value;
+    if (p->precision == IB_FP64)
+      k_point_values<double, kE><<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const double*)nodal,
+                                                   (const double*)p->inv_mass,
+                                                   (const double*)p->wj0, (double*)p->q_val);
+    else
+      k_point_values<float, kE><<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const float*)nodal,
+                                                  (const float*)p->inv_mass,
+                                                  (const float*)p->wj0, (float*)p->q_val);
+  });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -29,7 +29,9 @@ IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 
 IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO, IB_STD_REINF, IB_FIBRE2 = 0, 1, 2, 3, 4
 IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
 IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
-IB_ELEM_HEX8, IB_ELEM_TET4 = 0, 1
+IB_ELEM_HEX8, IB_ELEM_TET4, IB_ELEM_TET10 = 0, 1, 2
+_ELEM_OF_NODES = {8: IB_ELEM_HEX8, 4: IB_ELEM_TET4, 10: IB_ELEM_TET10}
+_NODES_OF_ELEM = {v: k for k, v in _ELEM_OF_NODES.items()}
 IB_MAX_MATERIALS = 8
 IB_PARAM_ROW = 10   # gradient row: the law's parameters, zeros, d/dT_a in column 9
 STAGES = ("force", "gather", "points", "sort", "spread", "interp", "project", "reduce",
@@ -184,16 +186,16 @@ class Pos:
 
 
 class Plan:
-    """An ib_plan: one hexahedral mesh on one periodic MAC grid."""
+    """An ib_plan: one hexahedral or tetrahedral mesh on one periodic MAC grid."""
 
     def __init__(self, conn: torch.Tensor, X: torch.Tensor, n, h: float, origin=(0.0, 0.0, 0.0),
                  fibres: torch.Tensor = None, mat_id: torch.Tensor = None,
                  precision: int = IB_FP32_SPLIT, quad: int = IB_QUAD_GAUSS2):
         self.dtype = torch.float64 if precision == IB_FP64 else torch.float32
         self.quad = quad
-        # hexahedra [8][E] or tetrahedra [4][E]
-        self.elem = IB_ELEM_TET4 if conn.dim() == 2 and conn.shape[0] == 4 else IB_ELEM_HEX8
-        _check(conn, torch.int32, (4 if self.elem == IB_ELEM_TET4 else 8, -1), "conn")
+        # hexahedra [8][E], linear [4][E] or quadratic [10][E] tetrahedra
+        self.elem = _ELEM_OF_NODES.get(int(conn.shape[0]) if conn.dim() == 2 else 8, IB_ELEM_HEX8)
+        _check(conn, torch.int32, (_NODES_OF_ELEM[self.elem], -1), "conn")
         _check(X, self.dtype, (3, -1), "X")
         if fibres is not None:
             _check(fibres, self.dtype, (6, conn.shape[1]), "fibres")
@@ -549,7 +551,7 @@ class Batch:
             a.mesh = _Mesh(int(X.shape[1]), int(conn.shape[1]), conn.data_ptr(), X.data_ptr(),
                            None if fib is None else fib.data_ptr(),
                            None if mid is None else mid.data_ptr(),
-                           IB_ELEM_TET4 if conn.shape[0] == 4 else IB_ELEM_HEX8)
+                           _ELEM_OF_NODES.get(int(conn.shape[0]), IB_ELEM_HEX8))
             a.grid = _Grid((C.c_int32 * 3)(*d["n"]), float(d["h"]),
                            (C.c_double * 3)(*d.get("origin", (0.0, 0.0, 0.0))))
             mats = d["mats"]

@@ -510,20 +510,30 @@ def tets_to_quadratic(conn4: np.ndarray, n_nodes: int):
                                                                    uniq % n_nodes])
 
 
-def tet10_problem(base: Problem, seed: int = 77, bend: float = 0.05) -> Problem:
+def tet10_problem(base: Problem, seed: int = 77, bend: float = 0.1) -> Problem:
     """The same structure as quadratic (P2) tetrahedra, the element of the
     paper's Cook membrane (Section 5): every hexahedron split into six
     tetrahedra, a node added at the middle of every edge.  The new nodes sit
     at the edge midpoints in the reference configuration (straight-sided
-    elements) and at the midpoints of the current edge ends displaced by a
-    seeded uniform +-bend*h, so that the current elements are curved."""
+    elements) and, in the current one, at the midpoints of the current edge
+    ends displaced by a seeded uniform +-bend r per coordinate, r the
+    smallest inradius (3 volume / surface) of the current tetrahedra sharing
+    the edge, so that the current elements are curved but far from
+    inverted."""
     t = tet_problem(base)
     conn10, edges = tets_to_quadratic(t.conn, t.n_nodes)
     rng = np.random.Generator(np.random.PCG64(seed))
     X64 = t.X.astype(np.float64)
     Xm = 0.5 * (X64[:, edges[0]] + X64[:, edges[1]])
     xm = 0.5 * (t.x[:, edges[0]] + t.x[:, edges[1]])
-    xm = xm + rng.uniform(-bend, bend, size=xm.shape) * t.grid.h
+    v = [t.x[:, t.conn[i]] for i in range(4)]
+    vol = np.abs(np.einsum("ie,ie->e", np.cross((v[1] - v[0]).T, (v[2] - v[0]).T).T,
+                           v[3] - v[0])) / 6.0
+    area = sum(0.5 * np.linalg.norm(np.cross((v[j] - v[i]).T, (v[k] - v[i]).T), axis=1)
+               for i, j, k in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)))
+    r = np.full(edges.shape[1], np.inf)
+    np.minimum.at(r, (conn10[4:] - t.n_nodes).ravel(), np.tile(3.0 * vol / area, 6))
+    xm = xm + rng.uniform(-bend, bend, size=xm.shape) * r
     X = np.concatenate([X64, Xm], axis=1).astype(t.X.dtype)
     x = np.concatenate([t.x, xm], axis=1)
     cell, off = to_split(x, t.grid)

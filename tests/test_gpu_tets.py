@@ -1,7 +1,9 @@
-"""GPU parity on linear tetrahedral meshes (the element of the paper's valve
-meshes, Section 5): the block and the 128^3 shell with every hexahedron split
-into six tetrahedra, against the FP64 oracle with the same 4-point rule.
-Tolerances as in the main parity suite: FP32 split plans 1e-5 (force,
+"""GPU parity on tetrahedral meshes: linear (P1, the element of the paper's
+valve meshes, Section 5) and quadratic (P2, the element of its Cook
+membrane): the block and the 128^3 shell with every hexahedron split into six
+tetrahedra (and, for P2, a node added at the middle of every edge, displaced
+in the current configuration), against the FP64 oracle with the same 4-point
+rule.  Tolerances as in the main parity suite: FP32 split plans 1e-5 (force,
 spread), 1e-6 (interpolation), 2e-5 (adjoint outputs); FP64 plans 1e-12."""
 import numpy as np
 import pytest
@@ -18,13 +20,14 @@ TOL32 = dict(G=1e-5, f=1e-5, U=1e-6, adj=2e-5)
 _cache = {}
 
 
-def case(name, quad=0):
-    key = (name, quad)
+def case(name, quad=0, order=1):
+    key = (name, quad, order)
     if key not in _cache:
         base = {"block32": lambda: I.block_problem(fp64=False),
                 "block64": lambda: I.block_problem(),
                 "shell128": lambda: I.shell_problem()}[name]()
-        _cache[key] = Case(I.tet_problem(base), quad=quad)
+        prob = I.tet_problem(base) if order == 1 else I.tet10_problem(base)
+        _cache[key] = Case(prob, quad=quad)
     return _cache[key]
 
 
@@ -33,12 +36,14 @@ def tol(c, k):
 
 
 NAMES = ["block32", "block64", "shell128"]
+ORDERS = [1, 2]
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", NAMES)
-def test_tet_force_energy_and_adjoint(name):
-    c = case(name)
-    assert c.plan.elem == c.ibfe.IB_ELEM_TET4
+def test_tet_force_energy_and_adjoint(name, order):
+    c = case(name, order=order)
+    assert c.plan.elem == (c.ibfe.IB_ELEM_TET4 if order == 1 else c.ibfe.IB_ELEM_TET10)
     G, en = c.ibfe.ib_fe_force(c.plan, c.mats, c.pos, energy=True)
     Go, eno = c.orc.fe_force(c.x_np)
     assert rel_l2(np_(G), Go) <= tol(c, "G")
@@ -51,9 +56,10 @@ def test_tet_force_energy_and_adjoint(name):
     assert rel_l2(gp[0, :k].numpy(), gpo[0, :k]) <= tol(c, "adj")
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", NAMES)
-def test_tet_spread_interp_and_mass(name):
-    c = case(name)
+def test_tet_spread_interp_and_mass(name, order):
+    c = case(name, order=order)
     ib = c.ibfe
     m = np_(ib.ib_lumped_mass(c.plan))
     assert rel_l2(m, c.orc.mass()) <= (1e-14 if c.fp64 else 1e-6)
@@ -69,9 +75,10 @@ def test_tet_spread_interp_and_mass(name):
     assert rel_l2(np_(U2), np_(U)) <= (1e-15 if c.fp64 else 1e-7)
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", ["block32", "block64"])
-def test_tet_fused_backward(name):
-    c = case(name)
+def test_tet_fused_backward(name, order):
+    c = case(name, order=order)
     ib = c.ibfe
     rng = np.random.default_rng(42)
     n = c.prob.n_nodes
@@ -91,15 +98,16 @@ def test_tet_fused_backward(name):
     assert rel_l2(gp[0, :k].cpu().numpy(), gpo[0, :k]) <= t
 
 
-def test_tet_nodal_rule_and_ib_step():
+@pytest.mark.parametrize("order", ORDERS)
+def test_tet_nodal_rule_and_ib_step(order):
     """The nodal quadrature rule on tetrahedra, and one explicit IB step."""
     from paper_2503_22695_gb300 import ibfe
-    c = case("block32", quad=ibfe.IB_QUAD_NODAL)
+    c = case("block32", quad=ibfe.IB_QUAD_NODAL, order=order)
     Go, _ = c.orc.fe_force(c.x_np)
     G = c.rounded(Go)
     f = ibfe.ib_spread(c.plan, c.pos, c.to_dev(G))
     assert rel_l2(np_(f), c.orc.spread_nodal(c.x_np, G)) <= 1e-5
-    c2 = case("block32")
+    c2 = case("block32", order=order)
     fl = ibfe.Fluid(c2.prob.grid.n, c2.prob.grid.h, 1.0, 0.02, 1e-3)
     u = c2.u.clone()
     x0 = c2.x_np.copy()
