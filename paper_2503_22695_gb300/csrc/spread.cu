@@ -293,8 +293,7 @@ constexpr int kFxAcc = kB * kFxSZ;      // 2016 words per component
 // reads of the 2 or 4 distinct rows fall in distinct banks (one wavefront).
 constexpr int kFxRow = kFxGroup + 1;
 struct FxGroup {
-  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2
-  int4 org[kFxGroup];       // accumulator offset of the stencil's first face, per component
+  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2; w: the packed stencil origin (fx_origin)
   float2 wz[4][kFxRow];     // [dz][pt] = (w_z at s = 0, w_z at s = 1/2)
   float2 wy[4][kFxRow];     // [dy][pt] likewise
   float4 wx[2][kFxRow];     // [xh][pt] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
@@ -316,6 +315,16 @@ __device__ __forceinline__ int fx_exponent(const SpreadArgs<float>& A) {
   int ex = 0;
   if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
   return min(19 - ex, 100);           // keep 2^(k+11) a normal float
+}
+
+// The accumulator offsets of a stencil's first face, one per component, in
+// 14 bits: with b_d the half-shifted (s = 1/2) start along axis d and g_d = 1
+// when the unshifted (s = 0) start is one face further (0 otherwise),
+// B = 168 b_z + 14 b_y + b_x < 2^11 and
+//   o_0 = B + g_x,   o_1 = A + B + 14 g_y,   o_2 = 2 A + B + 168 g_z   (A = kFxAcc).
+__device__ __forceinline__ int fx_pack_origin(const int b[3][2]) {
+  const int B = b[2][1] * kFxSZ + b[1][1] * kFxSY + b[0][1];
+  return B | (b[0][0] - b[0][1]) << 11 | (b[1][0] - b[1][1]) << 12 | (b[2][0] - b[2][1]) << 13;
 }
 
 // Raw data of one point, loaded a group ahead so that the loads are in
@@ -360,18 +369,14 @@ __device__ __forceinline__ void fx_stage(FxGroup& G, int pt, int part, const FxR
     G.wx[1][pt] = make_float4(wa[1], wa[3], wb[1], wb[3]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) G.wy[j][pt].x = wc[j];
-    G.val[pt] = make_float4(r.val[0] * vscale, r.val[1] * vscale, r.val[2] * vscale, 0.f);
+    G.val[pt] = make_float4(r.val[0] * vscale, r.val[1] * vscale, r.val[2] * vscale,
+                            __int_as_float(fx_pack_origin(b)));
   } else {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       G.wy[j][pt].y = wa[j];
       G.wz[j][pt] = make_float2(wb[j], wc[j]);
     }
-    int o[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      o[c] = c * kFxAcc + b[2][c != 2] * kFxSZ + b[1][c != 1] * kFxSY + b[0][c != 0];
-    G.org[pt] = make_int4(o[0], o[1], o[2], 0);
   }
 }
 
@@ -420,42 +425,43 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
       // its (dz, dy) row, for each component
       for (int q = 0; q < ng; ++q) {
         const float4 v = G.val[q];
-        const int4 org = G.org[q];
+        const int pk = __float_as_int(v.w);
+        const int B = (pk & 0x7FF) + loff;
+        const int4 org = make_int4(B + ((pk >> 11) & 1), kFxAcc + B + kFxSY * ((pk >> 12) & 1),
+                                   2 * kFxAcc + B + kFxSZ * ((pk >> 13) & 1), 0);
         const float2 wz = G.wz[ldz][q], wy = G.wy[ldy][q];
         const float4 wx = G.wx[lxh][q];
         // component 0: z, y at s = 1/2, x at s = 0
         float wr = v.x * wz.y * wy.y;
-        int a = org.x + loff;
+        int a = org.x;
         fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.x);
         fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.y);
         // component 1: z at s = 1/2, y at s = 0, x at s = 1/2
         wr = v.y * wz.y * wy.x;
-        a = org.y + loff;
+        a = org.y;
         fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
         fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
         // component 2: z at s = 0, y, x at s = 1/2
         wr = v.z * wz.x * wy.y;
-        a = org.z + loff;
+        a = org.z;
         fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
         fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
       }
       __syncwarp();  // group consumed before it is restaged
     }
     __syncthreads();
-    // decoded words (H, L) of every face, exact, one 12-face x-row per thread
-    int2* out = reinterpret_cast<int2*>(A.scratch) + (int64_t)slot * kItemBlk;
-    for (int row = tid; row < 3 * kB * kB; row += kFxThreads) {
+    // decoded words (H, L) of every face, exact; consecutive threads take
+    // consecutive face pairs of the 12-face x-rows (conflict-free reads,
+    // contiguous 16-byte stores)
+    int4* out = reinterpret_cast<int4*>(A.scratch) + (int64_t)slot * (kItemBlk / 2);
+    for (int u = tid; u < 3 * kB * kB * (kB / 2); u += kFxThreads) {
+      const int row = u / (kB / 2), x = 2 * (u % (kB / 2));
       const int c = row / (kB * kB), zy = row % (kB * kB);
-      const int z = zy / kB, y = zy % kB;
-      const int o = c * kFxAcc + z * kFxSZ + y * kFxSY;  // even: 8-byte aligned
-      int4* dst = reinterpret_cast<int4*>(out + row * kB);  // 96-byte rows
-#pragma unroll
-      for (int x = 0; x < kB; x += 2) {
-        const uint2 hw = *reinterpret_cast<const uint2*>(acc_hi + o + x);
-        const uint2 lw = *reinterpret_cast<const uint2*>(acc_lo + o + x);
-        const int L0 = (int)(lw.x << 10) >> 10, L1 = (int)(lw.y << 10) >> 10;
-        dst[x / 2] = make_int4((int)(hw.x - lw.x) + L0, L0, (int)(hw.y - lw.y) + L1, L1);
-      }
+      const int o = c * kFxAcc + (zy / kB) * kFxSZ + (zy % kB) * kFxSY + x;  // even: 8-byte aligned
+      const uint2 hw = *reinterpret_cast<const uint2*>(acc_hi + o);
+      const uint2 lw = *reinterpret_cast<const uint2*>(acc_lo + o);
+      const int L0 = (int)(lw.x << 10) >> 10, L1 = (int)(lw.y << 10) >> 10;
+      out[u] = make_int4((int)(hw.x - lw.x) + L0, L0, (int)(hw.y - lw.y) + L1, L1);
     }
   }
 }
