@@ -1114,3 +1114,25 @@ def test_tet10_adjoints_and_transfer_identities():
     fu = m.spread(x, g[:, None] * m.mass()[None, :])
     w, _ = m.gauss_info(x)
     np.testing.assert_allclose(fu.sum(axis=(1, 2, 3)) * h3, g * w.sum(), rtol=1e-12)
+
+
+def test_tet10_mesh_construction():
+    """The P2 generator shares one node per edge: on an nx x ny x nz block
+    split into six tetrahedra per cube (all around the 0-6 diagonal) the
+    distinct edges are the lattice edges, one face diagonal per face and one
+    body diagonal per cube; every edge node sits at its edge's middle in the
+    reference configuration and the quadratic mesh covers the same volume."""
+    nx, ny, nz = 3, 2, 2
+    p = tiny_mesh(blocks=(nx, ny, nz))
+    q = I.tet10_problem(p)
+    nv = (nx + 1) * (ny + 1) * (nz + 1)
+    lattice = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
+    faces = nx * ny * (nz + 1) + nx * (ny + 1) * nz + (nx + 1) * ny * nz
+    cubes = nx * ny * nz
+    assert q.n_nodes == nv + lattice + faces + cubes
+    assert q.conn.shape == (10, 6 * cubes)
+    for k, (i, j) in enumerate(I.TET10_EDGES):
+        np.testing.assert_allclose(q.X[:, q.conn[4 + k]],
+                                   0.5 * (q.X[:, q.conn[i]] + q.X[:, q.conn[j]]), rtol=0, atol=1e-15)
+    w, _ = oracle.Model(q).gauss_info(q.X)
+    assert w.sum() == pytest.approx(cubes * p.grid.h ** 3, rel=1e-13)
