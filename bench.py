@@ -451,6 +451,25 @@ def run_ours(args):
         raise RuntimeError("end-to-end outputs differ from ib_forward's")
     ms_e2e = timed(e2e, args.steps)
     t_e2e = sum(ms_e2e) / len(ms_e2e)
+    # the link alone: the two large copies of the step (velocity up, field
+    # down), each by itself and both at once on two streams
+    up = lambda: d_u.copy_(h_u, non_blocking=True)
+    down = lambda: h_f.copy_(fe, non_blocking=True)
+
+    def both():
+        with torch.cuda.stream(s_u):
+            s_u.wait_stream(stream)
+            up()
+        down()
+        stream.wait_stream(s_u)
+
+    link = {}
+    for key, fn in (("h2d_ms", up), ("d2h_ms", down), ("both_ms", both)):
+        fn()
+        ms_l = timed(fn, args.steps)
+        link[key] = sum(ms_l) / len(ms_l)
+    link["h2d_GBps"] = u.numel() * 4 / (link["h2d_ms"] * 1e-3) / 1e9
+    link["d2h_GBps"] = f.numel() * 4 / (link["d2h_ms"] * 1e-3) / 1e9
     del plan_i
     barrier()
     h2d = (h_cell.numel() * 4 + h_off.numel() * 4 + h_u.numel() * 4)
@@ -681,7 +700,10 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipeline": "ib_fe_force + ib_spread on the caller's stream; velocity upload + "
                             "ib_interp on a second stream and plan; downloads as each output "
-                            "is ready (outputs checked equal to ib_forward's)"},
+                            "is ready (outputs checked equal to ib_forward's)",
+                "link": {k: round(v, 4) for k, v in link.items()},
+                "link_note": "the 201 MB velocity upload and field download alone, each by "
+                             "itself and both at once (pinned host buffers)"},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"the full shell256 forward (force+spread+interp), "
                                    f"{reps} repetitions in {cpu_t:.1f} s"},
