@@ -293,7 +293,7 @@ constexpr int kFxAcc = kB * kFxSZ;      // 2016 words per component
 // reads of the 2 or 4 distinct rows fall in distinct banks (one wavefront).
 constexpr int kFxRow = kFxGroup + 1;
 struct FxGroup {
-  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2; w: the packed stencil origin (fx_origin)
+  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2; w: the packed stencil origin (fx_pack_origin)
   float2 wz[4][kFxRow];     // [dz][pt] = (w_z at s = 0, w_z at s = 1/2)
   float2 wy[4][kFxRow];     // [dy][pt] likewise
   float4 wx[2][kFxRow];     // [xh][pt] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
