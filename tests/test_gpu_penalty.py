@@ -1,7 +1,8 @@
 """GPU parity of the penalty tethers of the solid boundary (Section 5)
 against the oracle: nodal force and energy, the force adjoint, the fused
 forward/backward and the explicit IB step with the x-minimum face of the
-block tethered, in FP32 (1e-5 force, 2e-5 adjoint) and FP64 (1e-12)."""
+block tethered (hexahedra; the force and adjoint also on quadratic
+tetrahedra), in FP32 (1e-5 force, 2e-5 adjoint) and FP64 (1e-12)."""
 import numpy as np
 import pytest
 
@@ -15,9 +16,10 @@ pytestmark = pytest.mark.gpu
 KAPPA = 1e6
 
 
-def _case(fp64, weighted):
+def _case(fp64, weighted, p2=False):
     import torch
-    c = Case(I.block_problem(fp64=fp64))
+    base = I.block_problem(fp64=fp64)
+    c = Case(I.tet10_problem(base) if p2 else base)
     X = c.prob.X
     nodes = np.flatnonzero(X[0] <= X[0].min() + 1e-12).astype(np.int32)
     w = None
@@ -31,9 +33,13 @@ def _case(fp64, weighted):
     return c
 
 
-@pytest.mark.parametrize("fp64,weighted", [(False, False), (False, True), (True, False)])
-def test_penalty_force_energy_and_adjoint(fp64, weighted):
-    c = _case(fp64, weighted)
+@pytest.mark.parametrize("fp64,weighted,p2", [(False, False, False), (False, True, False),
+                                               (True, False, False), (False, False, True),
+                                               (True, False, True)])
+def test_penalty_force_energy_and_adjoint(fp64, weighted, p2):
+    """Hexahedra, and quadratic tetrahedra (whose tether weights are the
+    scaled-diagonal lumped masses)."""
+    c = _case(fp64, weighted, p2)
     t = 1e-12 if fp64 else 1e-5
     G, en = c.ibfe.ib_fe_force(c.plan, c.mats, c.pos, energy=True)
     Ge, ee = c.orc.fe_force(c.x_np)
