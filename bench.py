@@ -58,6 +58,23 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(times, device="cpu"):
+    """Per-step times reduced to their maximum over the ranks (replicas: the
+    job ends when the slowest replica does).  No collective with one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(times), device=device, dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all replicas processed over the
+    slowest replica's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -573,10 +590,7 @@ def run_ours(args):
         barrier()
 
     # --- max over ranks ----------------------------------------------------
-    tt = torch.tensor([t_fwd, t_adj, t_e2e], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_fwd, t_adj, t_e2e = tt.tolist()
+    t_fwd, t_adj, t_e2e = max_over_ranks([t_fwd, t_adj, t_e2e], dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -643,7 +657,7 @@ def run_ours(args):
         "elements, 115,200 Gauss points (profiling case)")
     line = {
         "metric": METRIC,
-        "value": Q * world / (t_fwd * 1e-3),
+        "value": job_rate(Q, world, t_fwd),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -696,7 +710,7 @@ def run_ours(args):
                                       "replaced by the stencil support 4|S|"},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in fwd_stages.items()},
         "gpu_launches": launches,
-        "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": UNIT, "ms_per_step": t_e2e,
+        "e2e": {"value": job_rate(Q, world, t_e2e), "unit": UNIT, "ms_per_step": t_e2e,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipeline": "ib_fe_force + ib_spread on the caller's stream; velocity upload + "
                             "ib_interp on a second stream and plan; downloads as each output "
