@@ -104,7 +104,11 @@ __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot,
 
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid, const short* order);
+                                              int tid);
+template <typename Real, int MODE>
+__device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real* ub,
+                                           const int lc[3], const Real off[3], int gq,
+                                           const Real val[3]);
 
 // Persistent CTAs, two-stage pipeline: the velocity block of the next work
 // item is fetched while the points of the current one are evaluated.
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
     cp_async_commit();
     cp_async_wait_group<1>();  // the current item's block has landed
     __syncthreads();
-    interp_points<Real, MODE>(A, cur, buf0 + b * 3 * kComp, tid, nullptr);
+    interp_points<Real, MODE>(A, cur, buf0 + b * 3 * kComp, tid);
     cur = nxt;
     b ^= 1;
   }
@@ -209,17 +213,25 @@ __device__ __forceinline__ void relayout(const float* __restrict__ dense, float*
   }
 }
 
-template <typename Real, int MODE>
-__device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid, const short* order);
 
 // Binned points arrive in no particular order inside a tile; threads of a
-// warp then often gather the same bank.  Order the item's points by cell of
-// the tile (a counting sort over the 512 cells; points of one cell in any
-// order, which changes no result), so a warp covers a run of neighbouring
-// cells, as sorted points would.
-__device__ __forceinline__ void local_cell_order(const InterpArgs<float>& A, int slot, int* cnt,
-                                                 short* order, int* tmp, int tid) {
+// warp then often gather the same bank.  The item's points are ordered by
+// cell of the tile (a counting sort over the 512 cells; points of one cell in
+// any order, which changes no result), so a warp covers a run of neighbouring
+// cells, as sorted points would.  Their data are read once, coalesced, in
+// binned order and stored in that cell order in shared memory, so the
+// evaluation reads them with plain shared loads.
+template <int MODE>
+struct PtStage {
+  float off[3][kChunk];
+  float val[MODE != 0 ? 3 : 1][MODE != 0 ? kChunk : 1];
+  int idx[kChunk];
+  short lc[kChunk];  // local cell: x + 8 y + 64 z
+};
+
+template <int MODE>
+__device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int slot, int* cnt,
+                                                PtStage<MODE>& P, int* tmp, int tid) {
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
@@ -250,8 +262,19 @@ __device__ __forceinline__ void local_cell_order(const InterpArgs<float>& A, int
 #pragma unroll
   for (int k = 0; k < kChunk / kThreads; ++k) {
     const int i = s + tid + k * kThreads;
-    if (i < e) order[cnt[cell[k]] + rank[k]] = (short)(i - s);
+    if (i < e) {
+      const int q = cnt[cell[k]] + rank[k];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) P.off[d][q] = __ldg(A.p_off + d * A.Q + i);
+      if (MODE != 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P.val[c][q] = __ldg(A.p_val + c * A.Q + i);
+      }
+      P.idx[q] = __ldg(A.p_idx + i);
+      P.lc[q] = (short)cell[k];
+    }
   }
+  return e - s;
 }
 
 // Per item: wait for its box (or stage it with cp.async), rewrite it into the
@@ -267,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
   __shared__ __align__(8) uint64_t bar_store;
   __shared__ int next, abort_flag;
   __shared__ int cnt[2 * kThreads], tmp[32];
-  __shared__ short order[kChunk];
+  PtStage<MODE>& pts = *reinterpret_cast<PtStage<MODE>*>(ub + 3 * kComp);
   const int tid = threadIdx.x;
   const int count = A.counters[0];
   const uint32_t bar = smem_u32(&bar_store), dense_s = smem_u32(dense);
@@ -283,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
   if (tid == 0 && cur_tma) issue_box(&tmap, A.g, A.tile_list[cur], dense_s, bar);
   uint32_t parity = 0;
   while (cur < count) {
-    local_cell_order(A, cur, cnt, order, tmp, tid);  // while the box is in flight
+    const int np = local_cell_stage<MODE>(A, cur, cnt, pts, tmp, tid);  // box in flight
     if (cur_tma) {
       if (mbar_wait(bar, parity))
         parity ^= 1;
@@ -304,7 +327,18 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
     const int nxt = next;
     const bool nxt_tma = nxt < count && tile_interior(A.g, A.tile_list[nxt]);
     if (tid == 0 && nxt_tma) issue_box(&tmap, A.g, A.tile_list[nxt], dense_s, bar);
-    interp_points<float, MODE>(A, cur, ub, tid, order);
+    // the points in cell order, from the staged copy
+    for (int j = tid; j < np; j += kThreads) {
+      const int c = pts.lc[j];
+      const int lc[3] = {c & (kTile - 1), (c >> kTileShift) & (kTile - 1), c >> (2 * kTileShift)};
+      const float off[3] = {pts.off[0][j], pts.off[1][j], pts.off[2][j]};
+      float val[3] = {0.f, 0.f, 0.f};
+      if (MODE != 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) val[k] = pts.val[k][j];
+      }
+      interp_one<float, MODE>(A, ub, lc, off, pts.idx[j], val);
+    }
     __syncthreads();  // padded block free; `next` consumed
     cur = nxt;
     cur_tma = nxt_tma;
@@ -315,92 +349,100 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
   }
 }
 
+// One point: the three stencil sums at local cell lc with offsets off, and
+// (MODE != 0) their position derivatives weighted by val; results written at
+// the point's original index gq.
+template <typename Real, int MODE>
+__device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real* ub,
+                                           const int lc[3], const Real off[3], int gq,
+                                           const Real val[3]) {
+  // weights for both staggerings per axis: [d][0] = s 0, [d][1] = s 1/2
+  Real w[3][2][4], dw[3][2][4];
+  int b[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      Real th;
+      b[d][hf] = lc[d] + stencil_axis(off[d], hf == 1, th) + 2;
+      if (MODE == 0)
+        delta_weights(th, w[d][hf]);
+      else
+        delta_weights_d(th, w[d][hf], dw[d][hf]);
+    }
+  Real S[3];
+  Real grad[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int hx = c != 0, hy = c != 1, hz = c != 2;
+    const Real* uc = ub + c * kComp + b[2][hz] * kSZ + b[1][hy] * kSY + b[0][hx];
+    Real tot = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+      Real py = Real(0), pdy = Real(0), pdx = Real(0);
+#pragma unroll
+      for (int ky = 0; ky < 4; ++ky) {
+        const Real* row = uc + kz * kSZ + ky * kSY;
+        Real rx = Real(0), rdx = Real(0);
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+          const Real v = row[kx];
+          rx += w[0][hx][kx] * v;
+          if (MODE != 0) rdx += dw[0][hx][kx] * v;
+        }
+        py += w[1][hy][ky] * rx;
+        if (MODE != 0) {
+          pdy += dw[1][hy][ky] * rx;
+          pdx += w[1][hy][ky] * rdx;
+        }
+      }
+      tot += w[2][hz][kz] * py;
+      if (MODE != 0) {
+        gz += dw[2][hz][kz] * py;
+        gy += w[2][hz][kz] * pdy;
+        gx += w[2][hz][kz] * pdx;
+      }
+    }
+    S[c] = tot;
+    if (MODE != 0) {
+      grad[0] += val[c] * gx;
+      grad[1] += val[c] * gy;
+      grad[2] += val[c] * gz;
+    }
+  }
+  if (MODE != 2) {
+    const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * A.vscale : A.vscale;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
+  }
+  if (MODE != 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = A.gscale * grad[d];
+  }
+}
+
+// The points of work item `slot`, read from global memory in binned order.
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
-                                              int tid, const short* order) {
+                                              int tid) {
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
-
-  for (int j = s + tid; j < e; j += kThreads) {
-    const int i = order ? s + order[j - s] : j;
+  for (int i = s + tid; i < e; i += kThreads) {
     int cx, cy, cz;
     unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
     const int lc[3] = {cx - x0, cy - y0, cz - z0};
     const Real off[3] = {__ldg(A.p_off + i), __ldg(A.p_off + A.Q + i),
                          __ldg(A.p_off + 2 * A.Q + i)};
-    const int gq = __ldg(A.p_idx + i);
     Real val[3] = {Real(0), Real(0), Real(0)};
     if (MODE != 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) val[c] = __ldg(A.p_val + c * A.Q + i);
     }
-    // weights for both staggerings per axis: [d][0] = s 0, [d][1] = s 1/2
-    Real w[3][2][4], dw[3][2][4];
-    int b[3][2];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        Real th;
-        b[d][hf] = lc[d] + stencil_axis(off[d], hf == 1, th) + 2;
-        if (MODE == 0)
-          delta_weights(th, w[d][hf]);
-        else
-          delta_weights_d(th, w[d][hf], dw[d][hf]);
-      }
-    Real S[3];
-    Real grad[3] = {Real(0), Real(0), Real(0)};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int hx = c != 0, hy = c != 1, hz = c != 2;
-      const Real* uc = ub + c * kComp + b[2][hz] * kSZ + b[1][hy] * kSY + b[0][hx];
-      Real tot = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
-#pragma unroll
-      for (int kz = 0; kz < 4; ++kz) {
-        Real py = Real(0), pdy = Real(0), pdx = Real(0);
-#pragma unroll
-        for (int ky = 0; ky < 4; ++ky) {
-          const Real* row = uc + kz * kSZ + ky * kSY;
-          Real rx = Real(0), rdx = Real(0);
-#pragma unroll
-          for (int kx = 0; kx < 4; ++kx) {
-            const Real v = row[kx];
-            rx += w[0][hx][kx] * v;
-            if (MODE != 0) rdx += dw[0][hx][kx] * v;
-          }
-          py += w[1][hy][ky] * rx;
-          if (MODE != 0) {
-            pdy += dw[1][hy][ky] * rx;
-            pdx += w[1][hy][ky] * rdx;
-          }
-        }
-        tot += w[2][hz][kz] * py;
-        if (MODE != 0) {
-          gz += dw[2][hz][kz] * py;
-          gy += w[2][hz][kz] * pdy;
-          gx += w[2][hz][kz] * pdx;
-        }
-      }
-      S[c] = tot;
-      if (MODE != 0) {
-        grad[0] += val[c] * gx;
-        grad[1] += val[c] * gy;
-        grad[2] += val[c] * gz;
-      }
-    }
-    if (MODE != 2) {
-      const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * A.vscale : A.vscale;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
-    }
-    if (MODE != 0) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = A.gscale * grad[d];
-    }
+    interp_one<Real, MODE>(A, ub, lc, off, __ldg(A.p_idx + i), val);
   }
 }
 
@@ -409,7 +451,10 @@ size_t smem_bytes() {
   return sizeof(Real) * 2 * 3 * kComp;
 }
 
-constexpr size_t kTmaSmem = kTmaAlign + kDenseBytes + sizeof(float) * 3 * kComp;
+template <int MODE>
+constexpr size_t tma_smem() {
+  return kTmaAlign + kDenseBytes + sizeof(float) * 3 * kComp + sizeof(PtStage<MODE>);
+}
 
 // cuTensorMapEncodeTiled from the driver, looked up once.
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -481,11 +526,11 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
     if (p->interp_tma && make_velocity_map(p, u, &tmap)) {
       A.use_tma = 1;
       if (mode == 0)
-        k_interp_tma<0><<<cap(p->interp_ctas_tma[0]), kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<0><<<cap(p->interp_ctas_tma[0]), kThreads, tma_smem<0>(), s>>>(tmap, A);
       else if (mode == 1)
-        k_interp_tma<1><<<cap(p->interp_ctas_tma[1]), kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<1><<<cap(p->interp_ctas_tma[1]), kThreads, tma_smem<1>(), s>>>(tmap, A);
       else
-        k_interp_tma<2><<<cap(p->interp_ctas_tma[2]), kThreads, kTmaSmem, s>>>(tmap, A);
+        k_interp_tma<2><<<cap(p->interp_ctas_tma[2]), kThreads, tma_smem<2>(), s>>>(tmap, A);
       return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
     }
   }
@@ -522,19 +567,18 @@ ib_status prepare_t(ib_plan* p) {
   p->interp_tma = 0;
   if constexpr (sizeof(Real) == 4) {
     int tma_sm[3] = {0, 0, 0};
-    const int ts = (int)kTmaSmem;
     if (encode_tiled() &&
-        cudaFuncSetAttribute(k_interp_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+        cudaFuncSetAttribute(k_interp_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<0>()) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(k_interp_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+        cudaFuncSetAttribute(k_interp_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<1>()) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(k_interp_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts) ==
+        cudaFuncSetAttribute(k_interp_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<2>()) ==
             cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[0], k_interp_tma<0>, kThreads, ts) ==
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[0], k_interp_tma<0>, kThreads, tma_smem<0>()) ==
             cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[1], k_interp_tma<1>, kThreads, ts) ==
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[1], k_interp_tma<1>, kThreads, tma_smem<1>()) ==
             cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[2], k_interp_tma<2>, kThreads, ts) ==
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[2], k_interp_tma<2>, kThreads, tma_smem<2>()) ==
             cudaSuccess &&
         tma_sm[0] > 0 && tma_sm[1] > 0 && tma_sm[2] > 0) {
       for (int m = 0; m < 3; ++m) p->interp_ctas_tma[m] = p->sm_count * tma_sm[m];
