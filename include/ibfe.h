@@ -169,7 +169,12 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
                          int32_t precision, void* stream, ib_plan** out);
 ib_status ib_plan_destroy(ib_plan* plan);
 
-/* Copy the plan's lumped mass m [N] (Real) into `mass` (device). */
+/* Copy the plan's lumped mass m [N] (Real) into `mass` (device).  m_a is the
+ * row sum sum_{e,q} N_a(xi_q) w_q j0 of the consistent mass by the element
+ * rule (hexahedra, P1 tetrahedra: the nodal-rule weight of Section 4.4), and
+ * for P2 tetrahedra the element diagonal sum_q N_a(xi_q)^2 w_q j0 scaled to
+ * the element's volume, summed over the node's elements.  Nodes in no element
+ * have m = 0 and receive zero from the projection. */
 ib_status ib_lumped_mass(ib_plan* plan, void* mass, void* stream);
 
 /* Nodal forces G (device Real [3][N], overwritten) of Section 4.4 for the
