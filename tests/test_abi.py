@@ -81,3 +81,28 @@ def test_host_fault_injection(lib, monkeypatch):
     with pytest.raises(ibfe.IBError) as e:
         ibfe._chk(ibfe._lib.ib_forward(*args), "ib_forward")
     assert e.value.code == ibfe.IB_ERR_NONFINITE
+
+
+def test_plan_creation_checks_the_element_type_before_the_device(lib):
+    """Element type and grid checks of ib_plan_create run on the host, for
+    every element (P2 tetrahedra included), before any CUDA call."""
+    from paper_2503_22695_gb300 import ibfe
+    conn = (C.c_int32 * 10)(*range(10))
+    X = (C.c_float * 30)()
+    out = C.c_void_p()
+    grid_ok = ibfe._Grid((C.c_int32 * 3)(16, 16, 16), 1.0 / 16, (C.c_double * 3)(0, 0, 0))
+    grid_bad_h = ibfe._Grid((C.c_int32 * 3)(16, 16, 16), 0.0, (C.c_double * 3)(0, 0, 0))
+    grid_ragged = ibfe._Grid((C.c_int32 * 3)(16, 12, 16), 1.0 / 16, (C.c_double * 3)(0, 0, 0))
+    for elem in (ibfe.IB_ELEM_HEX8, ibfe.IB_ELEM_TET4, ibfe.IB_ELEM_TET10):
+        mesh = ibfe._Mesh(10, 1, C.cast(conn, C.c_void_p), C.cast(X, C.c_void_p), None, None,
+                          elem)
+        assert lib.ib_plan_create(C.byref(mesh), C.byref(grid_bad_h), 0, 0, None,
+                                  C.byref(out)) == ibfe.IB_ERR_INVALID_ARG
+        assert lib.ib_plan_create(C.byref(mesh), C.byref(grid_ragged), 0, 0, None,
+                                  C.byref(out)) == ibfe.IB_ERR_UNSUPPORTED
+    for bad in (3, -1):
+        mesh = ibfe._Mesh(10, 1, C.cast(conn, C.c_void_p), C.cast(X, C.c_void_p), None, None,
+                          bad)
+        assert lib.ib_plan_create(C.byref(mesh), C.byref(grid_ok), 0, 0, None,
+                                  C.byref(out)) == ibfe.IB_ERR_INVALID_ARG
+    assert out.value is None
