@@ -165,6 +165,62 @@ def test_ho_isotropic_limit_is_neo_hookean():
     assert psi_ho == pytest.approx(psi_nh, rel=1e-7)
 
 
+HO_SETS = [
+    I.HO_DEFAULT,
+    (0.5, 2.0, 3.0, 4.0, 1.5, 2.5, 0.8, 3.5, 40.0),
+    (1.3, 0.4, 0.7, 9.0, 2.2, 0.3, 4.1, 0.6, 7.0),
+]
+
+
+@pytest.mark.parametrize("params", HO_SETS)
+def test_ho_simple_shear_closed_form(params):
+    # Psi_4 (Section 3) under simple shear of the fibre-sheet plane.  With e_f
+    # and e_s orthonormal and F = I + g e_f (x) e_s: J = 1, I1bar - 3 = g^2,
+    # I4f = 1, I4s = 1 + g^2, I8fs = e_f.C e_s = g, so
+    #   Psi = a/(2b)(e^{b g^2} - 1) + a_s/(2b_s)(e^{b_s g^4} - 1)
+    #       + a_fs/(2b_fs)(e^{b_fs g^2} - 1)
+    # and its g-derivative is the shear stress e_f.P e_s = P : (e_f (x) e_s):
+    #   a g e^{b g^2} + 2 a_s g^3 e^{b_s g^4} + a_fs g e^{b_fs g^2}.
+    # Shearing the other way (F = I + g e_s (x) e_f) swaps the roles of the
+    # fibre and sheet families (I4f = 1 + g^2, I4s = 1).  Each term has its own
+    # exponent and prefactor, so a dropped square (I8 for I8^2), a missing 1/2
+    # or a wrong rate constant in any of them fails here.
+    a, b, af, bf, as_, bs, afs, bfs, kap = params
+    rng = np.random.default_rng(41)
+    for _ in range(3):
+        ef, es = _fibres(rng)
+        for g in (-0.45, -0.1, 0.03, 0.2, 0.6):
+            for fam, (u, v, a4, b4) in enumerate(((ef, es, as_, bs), (es, ef, af, bf))):
+                F = np.eye(3) + g * np.outer(u, v)
+                P, psi = oracle.stress(I.HO, params, F, ef, es)
+                want = (a / (2 * b) * np.expm1(b * g * g) + a4 / (2 * b4) * np.expm1(b4 * g ** 4)
+                        + afs / (2 * bfs) * np.expm1(bfs * g * g))
+                assert psi == pytest.approx(want, rel=1e-13, abs=1e-15)
+                shear = (a * g * np.exp(b * g * g) + 2 * a4 * g ** 3 * np.exp(b4 * g ** 4)
+                         + afs * g * np.exp(bfs * g * g))
+                assert u @ P @ v == pytest.approx(shear, rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("params", HO_SETS)
+def test_ho_dilation_closed_form(params):
+    # F = lam I: J = lam^3, I1bar = 3, I8fs = lam^2 e_f.e_s = 0 and
+    # I4f = I4s = lam^2, so only the volumetric and the two fibre terms remain:
+    #   Psi = kappa/2 (3 ln lam)^2 + sum_{i=f,s} a_i/(2b_i)(e^{b_i(lam^2-1)^2} - 1)
+    # (the fibres carry tension only: zero for lam < 1); the pressure-like
+    # derivative dPsi/dlam = P : I.
+    a, b, af, bf, as_, bs, afs, bfs, kap = params
+    ef, es = _fibres(np.random.default_rng(42))
+    for lam in (0.93, 0.99, 1.02, 1.08):
+        P, psi = oracle.stress(I.HO, params, lam * np.eye(3), ef, es)
+        d = lam * lam - 1 if lam > 1 else 0.0
+        want = kap / 2 * (3 * np.log(lam)) ** 2 + sum(
+            ai / (2 * bi) * np.expm1(bi * d * d) for ai, bi in ((af, bf), (as_, bs)))
+        assert psi == pytest.approx(want, rel=1e-13, abs=1e-15)
+        dpsi = kap * 9 * np.log(lam) / lam + sum(
+            2 * ai * d * lam * np.exp(bi * d * d) for ai, bi in ((af, bf), (as_, bs)))
+        assert np.trace(P) == pytest.approx(dpsi, rel=1e-12, abs=1e-14)
+
+
 def test_standard_reinforcing_isotropic_limit_is_neo_hookean():
     # Psi_1 with G_L = G_T and E_L = 3 G_T has no fibre terms
     # (G_T - G_L = 0, E_L + G_T - 4 G_L = 0): neo-Hookean with a = G_T/2.
