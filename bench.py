@@ -31,13 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IB force+spread+interp Gauss-pts/s, % HBM roofline; adjoint/forward time ratio"
-# The spread's accumulation kernel: each Gauss point adds 3 components x 64
-# stencil faces, each as two exact 32-bit words, with shared-memory integer
-# atomics: 384 lane operations per point.  Their rate on GB300, 29.6 lane
-# operations per clock per SM, comes from a conflict-free shared atomicAdd
-# (u32) probe on this part; x 152 SMs x the SM clock gives the peak.
-PUSH_ATOMS_PER_POINT = 384.0
-SHARED_ATOMS_PER_CLK_SM = 29.6
+# The kernels of the spreading step as ib_spread runs them alone.
+SPREAD_KERNELS = ("k_spread_zero<float>", "k_spread_push_fx", "k_spread_merge_fx")
 # FE force: FP32 operations per Gauss point (fadd + fmul + 2 ffma, counted by
 # ncu for k_fe<float, df, ..., law set NH/Psi_2/Psi_4> on this workload);
 # FP32 peak = 152 SMs x 128 lanes x 2 (fma) x the SM clock.
@@ -154,6 +149,12 @@ def measured_sm_mhz():
         return 2070.0
 
 
+def sum_traffic(kernels):
+    """Sum of kernel_traffic over kernels (None if any is unknown)."""
+    vals = [kernel_traffic(k) for k in kernels]
+    return None if any(v is None for v in vals) else sum(vals)
+
+
 def kernel_traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if the kernel's
     source is unchanged since the counters were taken."""
@@ -190,62 +191,134 @@ def oracle_forward_rate(prob, min_seconds=10.0, max_reps=8):
 
 
 # ---------------------------------------------------------------------------
+# the oracle on every host core: the unchanged single-threaded oracle in one
+# process per core, each on its own contiguous slice of the elements (the
+# force, spreading and interpolation numerators are sums over elements, so
+# the slices together are the whole forward)
+# ---------------------------------------------------------------------------
+def _sub_mesh(prob, e0, e1, x):
+    """Elements [e0, e1) of a problem as a self-contained mesh (nodes renumbered)."""
+    import numpy as np
+    conn = prob.conn[:, e0:e1]
+    used = np.unique(conn)
+    remap = -np.ones(prob.n_nodes, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    return dict(grid=prob.grid, conn=remap[conn].astype(np.int32), X=prob.X[:, used],
+                fibres=prob.fibres[:, e0:e1], mat_id=prob.mat_id[e0:e1],
+                materials=prob.materials), np.ascontiguousarray(x[:, used])
+
+
+def _oracle_worker(mesh, xs, shm_name, u_shape, min_s, steps, barrier, out):
+    import numpy as np
+    from multiprocessing import shared_memory
+    import oracle
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        u = np.ndarray(u_shape, dtype=np.float64, buffer=shm.buf)
+        m = oracle.Model(**mesh)
+        q = 8 * m.E if m.conn.shape[0] == 8 else 4 * m.E
+        barrier.wait()
+        times = []
+        for k in range(steps if steps else 1 << 30):
+            t0 = time.perf_counter()
+            G, _ = m.fe_force(xs)
+            m.spread(xs, G)
+            m.interp(xs, u)
+            times.append(time.perf_counter() - t0)
+            if steps:
+                barrier.wait()          # steps end together (reference arm)
+            elif sum(times) >= min_s:
+                break
+        out.put((q, times))
+    finally:
+        del u
+        shm.close()
+
+
+def oracle_pool_rate(prob, workers, min_s=3.0, steps=0, n_elems=None):
+    """The oracle on `workers` host processes over the first n_elems elements
+    (all by default).  steps = 0: every worker repeats the forward on its
+    slice for at least min_s seconds; returns (Gauss points/s over the wall
+    time, per-worker repetitions, wall seconds).  steps > 0: that many
+    synchronised steps; returns (points per step, per-step wall seconds)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    from paper_2503_22695_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")           # never fork a CUDA process
+    x = I.from_split(prob.cell, prob.off, prob.grid)
+    E = prob.n_elems if n_elems is None else n_elems
+    bounds = [E * i // workers for i in range(workers + 1)]
+    shm = shared_memory.SharedMemory(create=True, size=prob.u.size * 8)
+    try:
+        np.ndarray(prob.u.shape, dtype=np.float64, buffer=shm.buf)[...] = prob.u
+        barrier = ctx.Barrier(workers + 1)
+        out = ctx.Queue()
+        procs = []
+        for i in range(workers):
+            mesh, xs = _sub_mesh(prob, bounds[i], bounds[i + 1], x)
+            pr = ctx.Process(target=_oracle_worker,
+                             args=(mesh, xs, shm.name, prob.u.shape, min_s, steps, barrier, out))
+            pr.start()
+            procs.append(pr)
+        barrier.wait()                      # every worker has built its slice
+        t0 = time.perf_counter()
+        step_t = []
+        if steps:
+            for _ in range(steps):
+                barrier.wait()
+                t1 = time.perf_counter()
+                step_t.append(t1 - t0)
+                t0 = t1
+        res = [out.get() for _ in procs]
+        wall = time.perf_counter() - t0
+        for pr in procs:
+            pr.join()
+    finally:
+        shm.close()
+        shm.unlink()
+    if steps:
+        return sum(q for q, _ in res), step_t
+    pts = sum(q * len(t) for q, t in res)
+    return pts / wall, [len(t) for _, t in res], wall
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    import numpy as np
     import oracle
     from paper_2503_22695_gb300 import inputs as I
     oracle.build()
     prob = I.shell_sheets_problem()
-    m = oracle.Model(prob)
-    x = I.from_split(prob.cell, prob.off, prob.grid)
-    u = prob.u.astype(np.float64)
-    # per-step sample: whole elements of the mesh, sized so W + K steps take
-    # about two minutes in total
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    t0 = time.perf_counter()
-    G, _ = m.fe_force(x)
-    m.spread(x, G)
-    m.interp(x, u)
-    full = time.perf_counter() - t0
-    frac = min(1.0, budget / full)
+    workers = os.cpu_count() or 1
     E = prob.n_elems
-    k = max(1, int(E * frac))
-    if k < E:
-        conn = prob.conn[:, :k]
-        used = np.unique(conn)
-        remap = -np.ones(prob.n_nodes, dtype=np.int64)
-        remap[used] = np.arange(len(used))
-        sub = oracle.Model(grid=prob.grid, conn=remap[conn], X=prob.X[:, used],
-                           fibres=prob.fibres[:, :k], mat_id=prob.mat_id[:k],
-                           materials=prob.materials)
-        xs = x[:, used]
-    else:
-        sub, xs = m, x
-    for _ in range(args.warmup):
-        G, _ = sub.fe_force(xs)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        G, _ = sub.fe_force(xs)
-        sub.spread(xs, G)
-        sub.interp(xs, u)
-        times.append(time.perf_counter() - t0)
-    t = sum(times) / len(times)
-    value = 8 * k / t
-    sample = (f"first {k} of {E} elements ({8 * k} Gauss points) of the shell256 workload "
-              f"per step, full 256^3 grid (zero-fill and stencils included)")
+    # per-step sample: the first k elements of the mesh (whole elements, the
+    # full 256^3 grid), split over one oracle process per host core, sized
+    # from a one-core probe so that W + K steps take about two minutes
+    k0 = max(workers, E // 64)
+    _, t_probe = oracle_pool_rate(prob, 1, steps=1, n_elems=k0)
+    per_elem = t_probe[0] / k0
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    k = int(min(E, max(workers, budget * workers / per_elem)))
+    pts, step_t = oracle_pool_rate(prob, workers, steps=args.warmup + args.steps, n_elems=k)
+    t = sum(step_t[args.warmup:]) / args.steps
+    value = pts / t
+    sample = (f"first {k} of {E} elements ({pts} Gauss points) of the shell256 workload per "
+              f"step, full 256^3 grid (zero-fill and stencils included), split over "
+              f"{workers} single-threaded oracle processes")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -596,62 +669,68 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # --- roofline of the dominant forward kernel --------------------------
-    # k_spread_push_fx has the largest share of the forward's kernel time
-    # (ncu launch list); its binding unit is the shared-memory integer atomic
-    # (bound "alu": no bytes or flops model fits it).  Work per launch =
-    # PUSH_ATOMS_PER_POINT x Q lane operations; its launch time is the
-    # library's own event interval around that kernel (IB_STAGE_SPREAD_PUSH,
-    # on the stream it is launched on).
+    # --- rooflines ----------------------------------------------------------
+    # The headline roofline is the spreading step against HBM: its result is
+    # the dense force field, 12 n^3 bytes written once (the spreading's
+    # algorithmic bytes), over the step's own time when it runs alone
+    # (ib_spread: far-tile zeros, accumulation and merge, timed by the
+    # library's events on the stream its kernels are launched on).
     hbm_peak, peak_kind = measured_peaks()
-    sm_mhz_max = measured_sm_mhz()
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or measured_sm_mhz()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fwd_stages = {k: v for k, v in stages.items() if v[1] > 0 and k != "spread_push"}
+    fwd_stages = {k: v for k, v in stages.items() if v[1] > 0}
     per_launch_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items() if v[1] > 0}
+    peak_src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s")
     spread_bytes = 12.0 * n ** 3            # the dense force field written once
-    push_ms = per_launch_ms["spread_push"]
-    atom_peak = SHARED_ATOMS_PER_CLK_SM * n_sm * sm_mhz_max * 1e6 / 1e9   # G ops/s
-    atom_work = PUSH_ATOMS_PER_POINT * Q
-    atom_achieved = atom_work / (push_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_spread_push_fx", "bound": "alu", "achieved": atom_achieved,
-            "peak": atom_peak, "unit": "G shared-atomic lane-op/s",
-            "frac": atom_achieved / atom_peak, "traffic": kernel_traffic("k_spread_push_fx"),
-            "traffic_unit": "DRAM bytes per launch",
-            "work_per_launch": atom_work, "launch_ms": push_ms,
-            "peak_source": f"29.6 u32 shared atomics/clk/SM (probe on this part) x {n_sm} SMs "
-                           f"x {sm_mhz_max:.0f} MHz"}
+    spread_ms = spread_alone[0] / max(1, spread_alone[1])
+    spread_gbs = spread_bytes / (spread_ms * 1e-3) / 1e9
+    roof = {"kernel": "spreading step (ib_spread alone: " + " + ".join(SPREAD_KERNELS) + ")",
+            "bound": "hbm", "achieved": spread_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": spread_gbs / hbm_peak,
+            "traffic": sum_traffic(SPREAD_KERNELS),
+            "traffic_unit": "DRAM bytes per step (ncu, sum over the step's kernels)",
+            "bytes_per_launch": spread_bytes, "launch_ms": spread_ms,
+            "peak_source": peak_src}
     force_ms = per_launch_ms["force"]
-    fp32_peak = FP32_LANES_PER_SM * 2 * n_sm * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = FP32_LANES_PER_SM * 2 * n_sm * sm_mhz * 1e6 / 1e12   # TFLOP/s
     fe_achieved = FE_FLOPS_PER_GP * Q / (force_ms * 1e-3) / 1e12
     force_roof = {"kernel": "k_fe", "bound": "alu", "achieved": fe_achieved,
                   "peak": fp32_peak, "unit": "TFLOP/s (FP32)", "frac": fe_achieved / fp32_peak,
                   "traffic": kernel_traffic("k_fe"), "traffic_unit": "DRAM bytes per launch",
                   "work_per_launch": FE_FLOPS_PER_GP * Q, "launch_ms": force_ms,
-                  "peak_source": f"128 FP32 lanes x 2 x {n_sm} SMs x {sm_mhz_max:.0f} MHz",
+                  "peak_source": f"128 FP32 lanes x 2 x {n_sm} SMs x {sm_mhz:.0f} MHz (median "
+                                 f"SM clock sampled during the timed steps)",
                   "note": "no FP64 instruction (J - 1 and I4f - 1 by compensated FP32 sums)"}
-    spread_ms = spread_alone[0] / max(1, spread_alone[1])
-    spread_roof = {"kernels": "k_spread_zero + k_absmax + k_spread_push_fx + k_spread_merge_fx "
-                              "(ib_spread alone)",
-                   "bound": "hbm", "achieved": spread_bytes / (spread_ms * 1e-3) / 1e9,
-                   "peak": hbm_peak, "unit": "GB/s",
-                   "frac": spread_bytes / (spread_ms * 1e-3) / 1e9 / hbm_peak,
-                   "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)"
-                                   if peak_kind == "measured" else "fallback 6.8 TB/s"),
-                   "bytes_per_launch": spread_bytes, "stage_ms": spread_ms}
 
-    # cpu baseline (oracle, one core) and the support count for the bytes model
+    # cpu baseline (the oracle on one core, then on every host core) and the
+    # stencil-support count for the bytes model
     if args.no_cpu_baseline:
         cpu_rate, reps, cpu_t, support = None, 0, 0.0, 0
+        pool_rate, pool_reps, pool_t, cores = None, [], 0.0, 0
     else:
         cpu_rate, reps, cpu_t, support = oracle_forward_rate(prob)
+        cores = os.cpu_count() or 1
+        pool_rate, pool_reps, pool_t = oracle_pool_rate(prob, cores)
     b_force = 56.0 * E + 52.0 * N
     b_interp = 4.0 * support + 12.0 * N
     b_fwd = b_force + spread_bytes + b_interp
     fwd_gbs = b_fwd / (t_fwd * 1e-3) / 1e9
     b_sup = b_force + 4.0 * support + b_interp
     sup_gbs = b_sup / (t_fwd * 1e-3) / 1e9
+    # the interpolation kernel: velocity read on the stencil support (4|S|),
+    # the points' split positions in (16 B) and w j0 U^IB out (12 B)
+    interp_ms = per_launch_ms["interp"]
+    b_ik = 4.0 * support + 28.0 * Q
+    interp_roof = {"kernel": "k_interp_tma<0>", "bound": "hbm",
+                   "achieved": b_ik / (interp_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                   "unit": "GB/s", "frac": b_ik / (interp_ms * 1e-3) / 1e9 / hbm_peak,
+                   "traffic": kernel_traffic("k_interp_tma<0>"),
+                   "traffic_unit": "DRAM bytes per launch", "bytes_per_launch": b_ik,
+                   "launch_ms": interp_ms, "peak_source": peak_src,
+                   "model": "4|S| (u on the stencil support) + 16 Q (positions) + 12 Q (values)"}
     launches = sum(v[2] for v in stages.values())
-    clocks = clk.summary()
     workload = WORKLOAD if args.workload == "shell256" else (
         "shell128: 128^3 periodic MAC grid; HO ventricle-like shell 60x40x6 hex; 14,400 "
         "elements, 115,200 Gauss points (profiling case)")
@@ -699,7 +778,7 @@ def run_ours(args):
         "adjoint_forward_ratio": t_adj / t_fwd,
         "roofline": roof,
         "force_roofline": force_roof,
-        "spread_roofline": spread_roof,
+        "interp_roofline": interp_roof,
         "forward_roofline": {"bytes_per_step": b_fwd, "achieved_GBps": fwd_gbs,
                              "frac": fwd_gbs / hbm_peak, "peak": hbm_peak,
                              "support_faces": support,
@@ -718,9 +797,14 @@ def run_ours(args):
                 "link": {k: round(v, 4) for k, v in link.items()},
                 "link_note": "the 201 MB velocity upload and field download alone, each by "
                              "itself and both at once (pinned host buffers)"},
-        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"the full shell256 forward (force+spread+interp), "
-                                   f"{reps} repetitions in {cpu_t:.1f} s"},
+        "cpu_baseline": {"value": pool_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the full shell256 forward (force+spread+interp) split by "
+                                   f"elements over {cores} single-threaded oracle processes, "
+                                   f"{min(pool_reps) if pool_reps else 0}+ repetitions each in "
+                                   f"{pool_t:.1f} s",
+                         "single_core": {"value": cpu_rate, "unit": UNIT, "cores": 1,
+                                         "sample": f"the full shell256 forward, {reps} "
+                                                   f"repetitions in {cpu_t:.1f} s"}},
         "clocks": clocks,
     }
     print(json.dumps(line))
