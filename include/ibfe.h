@@ -97,8 +97,23 @@ typedef enum {
  *   using the same cancellation-free formulas.  Nodal forces stay within
  *   1e-5 relative L2 of the FP64 definition, but the Hessian-vector product
  *   of ib_fe_force_adj loses accuracy (6.7e-5 relative on a 256^3 ventricle
- *   workload, against 2e-5 with IB_FP32_SPLIT) for no speed gain on GB300. */
-typedef enum { IB_FP32_SPLIT = 0, IB_FP64 = 1, IB_FP32_SPLIT_F32STAB = 2 } ib_precision;
+ *   workload, against 2e-5 with IB_FP32_SPLIT) for no speed gain on GB300.
+ * IB_FP32_SPLIT_DFVOL: as IB_FP32_SPLIT, with J - 1 at every force point from
+ *   double-float kinematics: node differences formed without rounding from
+ *   the split positions and the reference coordinates, the Jacobians
+ *   DX = dX/dxi and DU = du/dxi, and det(DX + DU) - det(DX) expanded, all in
+ *   pairs of FP32 numbers (no FP64 instruction).  For nearly incompressible
+ *   materials, where |J - 1| << |F - I|: there J - 1 from the FP32
+ *   displacement gradient (IB_FP32_SPLIT) carries a relative error near
+ *   1e-7 |F - I| / |J - 1| (1.3e-3 in the nodal force at kappa / a = 2e4,
+ *   |J - 1| <= 6e-5), this option one near 1e-13 |F - I| / |J - 1|.  The
+ *   force kernel costs about three times as much. */
+typedef enum {
+  IB_FP32_SPLIT = 0,
+  IB_FP64 = 1,
+  IB_FP32_SPLIT_F32STAB = 2,
+  IB_FP32_SPLIT_DFVOL = 3
+} ib_precision;
 
 #define IB_MAX_MATERIALS 8
 /* Width of a parameter-gradient row: the law's n_params parameters from
@@ -137,6 +152,12 @@ typedef struct {
   const int32_t* cell; /* IB_FP32_SPLIT: device [3][N] */
   const float* off;    /* IB_FP32_SPLIT: device [3][N], each in [0,1) */
   const double* x64;   /* IB_FP64: device [3][N] */
+  double grad_unit;    /* position derivatives returned by the adjoints (gx of
+                          ib_spread_adj, ib_interp_adj, ib_backward; Hv of
+                          ib_fe_force_adj) are per displacement of this length:
+                          0 (or 1) = per unit of the grid's length (d/dx); h =
+                          per unit of the split offset (d/d off).  Not
+                          finite or negative: IB_ERR_INVALID_ARG */
 } ib_pos;
 
 typedef struct {

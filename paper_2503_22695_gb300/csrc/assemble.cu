@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
                                                      const int32_t* __restrict__ inc_idx,
                                                      const Real* __restrict__ elem,
                                                      const Real* __restrict__ scale,
-                                                     const Real* add, int N, int E, Real* out) {
+                                                     const Real* add, int N, int E, Real* out,
+                                                     Real mul) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   Real acc[NC];
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] += __ldg(elem + (int64_t)(a * NC + c) * E + e);
   }
-  const Real s = scale ? __ldg(scale + n) : Real(1);
+  const Real s = (scale ? __ldg(scale + n) : Real(1)) * mul;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const int64_t o = (int64_t)c * N + n;
@@ -157,17 +158,17 @@ __global__ void k_invert(const Real* __restrict__ m, Real* __restrict__ im, int 
 
 template <typename Real>
 ib_status gather_t(ib_plan* p, const void* elem, const void* scale, const void* add, void* out,
-                   int nc, cudaStream_t s) {
+                   int nc, cudaStream_t s, double mul = 1.0) {
   if (p->N == 0) return IB_OK;
   const int blocks = (p->N + 255) / 256;
   if (nc == 3)
     k_node_gather<Real, 3><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
                                                   (const Real*)scale, (const Real*)add, p->N,
-                                                  p->E, (Real*)out);
+                                                  p->E, (Real*)out, (Real)mul);
   else
     k_node_gather<Real, 1><<<blocks, 256, 0, s>>>(p->inc_off, p->inc_idx, (const Real*)elem,
                                                   (const Real*)scale, (const Real*)add, p->N,
-                                                  p->E, (Real*)out);
+                                                  p->E, (Real*)out, (Real)mul);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
@@ -210,7 +211,7 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
                                                                      ed);
       });
     k_node_gather<double, 1><<<(p->N + 255) / 256, 256, 0, s>>>(
-        p->inc_off, p->inc_idx, ed, nullptr, nullptr, p->N, p->E, md);
+        p->inc_off, p->inc_idx, ed, nullptr, nullptr, p->N, p->E, md, 1.0);
     if (sizeof(Real) == 4)
       k_mass_round<<<(p->N + 255) / 256, 256, 0, s>>>(md, (float*)p->mass, (float*)p->inv_mass,
                                                       p->N);
@@ -236,9 +237,9 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
 }  // namespace
 
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* scale, void* out,
-                             cudaStream_t s, const void* add) {
-  return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, add, out, 3, s)
-                                 : gather_t<float>(p, elem, scale, add, out, 3, s);
+                             cudaStream_t s, const void* add, double mul) {
+  return p->precision == IB_FP64 ? gather_t<double>(p, elem, scale, add, out, 3, s, mul)
+                                 : gather_t<float>(p, elem, scale, add, out, 3, s, mul);
 }
 
 ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* add,

@@ -35,9 +35,9 @@ void free_plan(ib_plan* p) {
   void* ptrs[] = {p->inc_off, p->inc_idx, p->mass, p->inv_mass, p->wj0, p->elem_scratch,
                   p->elem_scratch2, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist,
                   p->tile_start, p->tile_end, p->tile_slot, p->tile_nonempty, p->tile_near,
-                  p->tile_list, p->tile_list_near, p->tile_bcount, p->tile_counters,
+                  p->tile_list, p->tile_list_near, p->tile_vmax, p->tile_bcount, p->tile_counters,
                   p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
-                  p->p_off, p->p_val, p->p_idx, p->gq_a, p->gq_b, p->epart, p->ered,
+                  p->p_off, p->p_val, p->p_idx, p->vol_jm1, p->gq_a, p->gq_b, p->epart, p->ered,
                   p->dstatus, p->node_tmp, p->pen_part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -76,10 +76,13 @@ ib_status check_launch(ib_status st) {
 }
 
 ib_status check_pos(const ib_plan* p, const ib_pos* x) {
-  if (!x) return IB_ERR_INVALID_ARG;
+  if (!x || !std::isfinite(x->grad_unit) || x->grad_unit < 0.0) return IB_ERR_INVALID_ARG;
   if (p->precision == IB_FP64) return x->x64 ? IB_OK : IB_ERR_INVALID_ARG;
   return (x->cell && x->off) ? IB_OK : IB_ERR_INVALID_ARG;
 }
+
+// The length per which position derivatives are returned (ib_pos.grad_unit).
+double gunit(const ib_pos* x) { return x->grad_unit > 0.0 ? x->grad_unit : 1.0; }
 
 const void* pos_a(const ib_plan* p, const ib_pos* x) {
   return p->precision == IB_FP64 ? (const void*)x->x64 : (const void*)x->cell;
@@ -184,9 +187,9 @@ ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
 }
 
 ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, cudaStream_t s,
-                    const void* add = nullptr) {
+                    const void* add = nullptr, double mul = 1.0) {
   Stage sc(p, IB_STAGE_GATHER, s, 1);
-  return launch_node_gather(p, elem, scale, out, s, add);
+  return launch_node_gather(p, elem, scale, out, s, add, mul);
 }
 
 // Coupling-point values gq [3][Q] to nodal values: Gauss rule, the lumped
@@ -256,7 +259,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   if (!out) return IB_ERR_INVALID_ARG;
   *out = nullptr;
   if (!mesh || !grid) return IB_ERR_INVALID_ARG;
-  if (precision != IB_FP32_SPLIT && precision != IB_FP64 && precision != IB_FP32_SPLIT_F32STAB)
+  if (precision != IB_FP32_SPLIT && precision != IB_FP64 && precision != IB_FP32_SPLIT_F32STAB &&
+      precision != IB_FP32_SPLIT_DFVOL)
     return IB_ERR_INVALID_ARG;
   if (quad != IB_QUAD_GAUSS2 && quad != IB_QUAD_NODAL) return IB_ERR_INVALID_ARG;
   if (mesh->n_nodes <= 0 || mesh->n_elems < 0 || (mesh->n_elems > 0 && !mesh->conn) || !mesh->X)
@@ -355,6 +359,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->tile_near, 4 * (size_t)p->ntiles) &&
               dalloc(&p->tile_list, 4 * (size_t)max_work_items(p->ntiles, Q)) &&
               dalloc(&p->tile_list_near, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_vmax, 4 * (size_t)p->ntiles) &&
               dalloc(&p->tile_bcount, 12 * (size_t)classify_blocks(p->ntiles)) &&
               dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
               dalloc(&p->rpart, 8 * kParamRow * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
@@ -369,7 +374,9 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
               dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
               dalloc(&p->ered, 8 * kParamRow * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16) &&
-              dalloc(&p->pen_part, 8 * penalty_scratch_doubles());
+              dalloc(&p->pen_part, 8 * penalty_scratch_doubles()) &&
+              (precision != IB_FP32_SPLIT_DFVOL ||
+               dalloc(&p->vol_jm1, sizeof(float) * 2 * (nc == 8 ? 8 : 4) * (size_t)(E > 0 ? E : 1)));
   if (!good) {
     free_plan(p);
     cudaGetLastError();
@@ -570,7 +577,8 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     st = launch_point_values(p, G, s);
     if (st == IB_OK) st = launch_permute_values(p, s);
   }
-  if (st == IB_OK && gf) st = do_interp(p, gf, 1, ih3, ih3 / h, s);
+  const double gxu = gunit(x);
+  if (st == IB_OK && gf) st = do_interp(p, gf, 1, ih3, ih3 / h * gxu, s);
   if (st == IB_OK && gf) st = to_nodes(p, p->gq_a, p->elem_scratch, p->inv_mass, gGt, s, gG);
   if (st == IB_OK && gf) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   if (st == IB_OK && !gf) {
@@ -589,7 +597,7 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     if (st == IB_OK) st = launch_permute_values(p, b);
   }
   if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b);
-  if (st == IB_OK && gU) st = do_interp(p, u, 2, 0.0, 1.0 / h, b);
+  if (st == IB_OK && gU) st = do_interp(p, u, 2, 0.0, gxu / h, b);
   if (st == IB_OK && gU) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, b, gx);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   // ... beside the force adjoint, whose nodal gather adds into gx after the join
@@ -600,8 +608,8 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
   }
   if (st == IB_OK && force && gparams) st = do_reduce(p, kParamRow, n_mats, s);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
-  if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx);
-  if (st == IB_OK && force) st = launch_penalty_adj(p, gGt, gx, s);
+  if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx, gxu);
+  if (st == IB_OK && force) st = launch_penalty_adj(p, gGt, gx, s, gxu);
   if (st == IB_OK && gparams) {
     const size_t pb = sizeof(double) * kParamRow * (size_t)n_mats;
     if (!ok(force ? cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)
@@ -620,7 +628,7 @@ ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* 
   cudaStream_t s = S(stream);
   const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
   st = do_points_sorted(p, x, G, s);
-  if (st == IB_OK) st = do_interp(p, gf, gx ? 1 : 0, ih3, ih3 / h, s);
+  if (st == IB_OK) st = do_interp(p, gf, gx ? 1 : 0, ih3, ih3 / h * gunit(x), s);
   if (st == IB_OK) st = to_nodes(p, p->gq_a, p->elem_scratch, p->inv_mass, gG, s);
   if (st == IB_OK && gx) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   return check_launch(st);
@@ -636,7 +644,7 @@ ib_status ib_interp_adj(ib_plan* p, const ib_pos* x, const void* u, const void* 
   st = do_points_sorted(p, x, gU, s);
   if (st == IB_OK) st = do_spread(p, 1.0, gu, s);
   if (st == IB_OK && gx) {
-    st = do_interp(p, u, 2, 0.0, 1.0 / p->grid.h, s);
+    st = do_interp(p, u, 2, 0.0, gunit(x) / p->grid.h, s);
     if (st == IB_OK) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   }
   return check_launch(st);
@@ -659,8 +667,8 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
     Stage sc(p, IB_STAGE_FORCE, s, 1);
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, v, p->elem_scratch, params, s);
   }
-  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s);
-  if (st == IB_OK) st = launch_penalty_adj(p, v, Hv, s);
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s, nullptr, gunit(x));
+  if (st == IB_OK) st = launch_penalty_adj(p, v, Hv, s, gunit(x));
   if (st == IB_OK && params) st = do_reduce(p, kParamRow, n_mats, s);
   return check_launch(st);
 }

@@ -68,6 +68,41 @@ __device__ __forceinline__ double sacc(double acc, double a) { return acc + a; }
 __device__ __forceinline__ float dacc(float acc, float a, float b) { return fmaf(a, b, acc); }
 __device__ __forceinline__ float sacc(float acc, float a) { return acc + a; }
 
+// Double-float arithmetic on double-float operands (the kinematics of the
+// exact volumetric invariant): sums of two pairs, products, products with a
+// float, and the quotient, each within a few units of 2^-44 relative (the
+// accumulations below leave the pair unnormalised; norm() restores
+// |lo| <= ulp(hi) / 2).
+__device__ __forceinline__ df norm(df a) { return two_sum(a.hi, a.lo); }
+__device__ __forceinline__ df neg(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df dadd(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df dmul(df a, df b) {
+  const df p = two_prod(a.hi, b.hi);
+  return two_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
+}
+// acc + a b with a double-float a and a float b
+__device__ __forceinline__ df dfma(df acc, df a, float b) {
+  const df p = two_prod(a.hi, b);
+  const df s = two_sum(acc.hi, p.hi);
+  return df(s.hi, __fadd_rn(__fadd_rn(acc.lo, s.lo), fmaf(a.lo, b, p.lo)));
+}
+// acc + a b, both double-float
+__device__ __forceinline__ df dfma(df acc, df a, df b) {
+  const df p = two_prod(a.hi, b.hi);
+  const df s = two_sum(acc.hi, p.hi);
+  return df(s.hi, __fadd_rn(__fadd_rn(acc.lo, s.lo), fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo))));
+}
+// a / b: the float quotient of the leading parts, corrected once by the
+// double-float residual a - b q
+__device__ __forceinline__ df ddiv(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = dadd(a, neg(dmul(b, df(q1))));
+  return two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
 // ln(1 + x) of a double-float argument.  The stress consumes ln J rounded to
 // FP32, so the FP32 logarithm of the correctly rounded argument is as good as
 // an extended one: what must not lose digits is the argument J - 1 itself,

@@ -80,6 +80,20 @@ int law_set(const MatTable& mt, bool params) {
 #define HEX IB_ELEM_HEX8
 
 namespace {
+// IB_FP32_SPLIT_DFVOL plans: every law, the exact volumetric invariant; one
+// instantiation per element and output.
+constexpr int kLawVol = kLawAll | kLawVolX;
+template <int T>
+ib_status vol_force(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
+                    const void* v, void* out, bool energy, bool adj, bool params,
+                    cudaStream_t s) {
+  if (adj)
+    return params ? fe_run<float, df, false, true, true, kLawVol, T>(IBFE_FE_ARGS)
+                  : fe_run<float, df, false, true, false, kLawVol, T>(IBFE_FE_ARGS);
+  return energy ? fe_run<float, df, true, false, false, kLawVol, T>(IBFE_FE_ARGS)
+                : fe_run<float, df, false, false, false, kLawVol, T>(IBFE_FE_ARGS);
+}
+
 // Tetrahedral meshes (P1 and P2): one instantiation per precision and
 // output (all laws).
 template <int T>
@@ -101,6 +115,8 @@ ib_status tet_force(ib_plan* p, const MatTable& mt, const void* xa, const float*
     return energy ? fe_run<float, float, true, false, false, L, T>(IBFE_FE_ARGS)
                   : fe_run<float, float, false, false, false, L, T>(IBFE_FE_ARGS);
   }
+  if (p->precision == IB_FP32_SPLIT_DFVOL) return vol_force<T>(p, mt, xa, off, v, out, energy,
+                                                               adj, params, s);
   if (adj)
     return params ? fe_run<float, df, false, true, true, L, T>(IBFE_FE_ARGS)
                   : fe_run<float, df, false, true, false, L, T>(IBFE_FE_ARGS);
@@ -117,6 +133,8 @@ ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const 
   if (p->elem == IB_ELEM_TET10)
     return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, energy, false, false, s);
   const int set = law_set(mt, false);
+  if (p->precision == IB_FP32_SPLIT_DFVOL)
+    return vol_force<HEX>(p, mt, xa, off, v, out, energy, false, false, s);
   if (p->precision == IB_FP64)
     return energy ? fe_run<double, double, true, false, false, kLawAll, HEX>(IBFE_FE_ARGS)
                   : fe_run<double, double, false, false, false, kLawAll, HEX>(IBFE_FE_ARGS);
@@ -141,6 +159,8 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
   if (p->elem == IB_ELEM_TET10)
     return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, false, true, params, s);
   const int set = law_set(mt, params);
+  if (p->precision == IB_FP32_SPLIT_DFVOL)
+    return vol_force<HEX>(p, mt, xa, off, v, out, false, true, params, s);
   if (p->precision == IB_FP64)
     return params ? fe_run<double, double, false, true, true, kLawAll, HEX>(IBFE_FE_ARGS)
                   : fe_run<double, double, false, true, false, kLawAll, HEX>(IBFE_FE_ARGS);

@@ -1,0 +1,17 @@
+// Instantiations of the force kernel and its adjoint for
+// IB_FP32_SPLIT_DFVOL plans on hexahedra: every law, J - 1 from double-float
+// kinematics (fe_kernel.cuh, exact_jm1).
+#include "fe_kernel.cuh"
+
+namespace ibfe {
+
+#define IBFE_FE_RUN(E, A, P)                                                              \
+  template ib_status fe_run<float, df, E, A, P, kLawAll | kLawVolX, IB_ELEM_HEX8>(        \
+      ib_plan*, const MatTable&, const void*, const float*, const void*, void*, cudaStream_t)
+
+IBFE_FE_RUN(false, false, false);
+IBFE_FE_RUN(true, false, false);
+IBFE_FE_RUN(false, true, false);
+IBFE_FE_RUN(false, true, true);
+
+}  // namespace ibfe

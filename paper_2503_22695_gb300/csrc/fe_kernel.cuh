@@ -57,6 +57,8 @@ struct FeArgs {
   const int32_t* mat_id; // [E] or null
   NodeLoader<Real> pos;
   Real h;
+  float hlo;             // h - float(h) (split-precision plans: h as a double-float)
+  const float2* jx;      // [QF][E] exact J - 1 (IB_FP32_SPLIT_DFVOL) or null
   const Real* v;         // [3][N] direction (adjoint) or null
   Real* out;             // [24][E] corner contributions
   double* epart;         // [kParamRow][E] per-element partial sums or null
@@ -151,6 +153,106 @@ constexpr int fe_min_blocks() {
   return sizeof(Real) == 8 ? 2 : (kAdj ? IBFE_FE_MIN_BLOCKS_ADJ : IBFE_FE_MIN_BLOCKS);
 }
 
+// Exact volumetric invariant (IB_FP32_SPLIT_DFVOL plans): J - 1 at force
+// point q of element e as (det(DX + DU) - det(DX)) / det(DX), with
+// DX = sum_a dX_a (x) dN_a/dxi and DU = sum_a du_a (x) dN_a/dxi, from node
+// differences formed without rounding (integer cells, FP32 offsets, FP32
+// reference coordinates: TwoSum), the expansion
+//   det(A + B) - det(A) = cof(A) : B + A : cof(B) + det(B),
+// and every step in double-float.  Near incompressibility |J - 1| << |F - I|,
+// and J - 1 from the FP32 displacement gradient would carry a relative error
+// near eps |F - I| / |J - 1|; here it is near 2^-44 |F - I| / |J - 1|.  The
+// shape-function derivatives are the force kernel's FP32 constants, so both
+// describe the same element.  One thread per (q, e), q-major; the result is
+// stored as a (hi, lo) pair for the force kernel.
+__device__ __forceinline__ void cof3(const df M[3][3], df C[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      C[i][j] = dadd(dmul(M[i1][j1], M[i2][j2]), neg(dmul(M[i1][j2], M[i2][j1])));
+    }
+}
+
+template <int kEl, int Q>
+__device__ __forceinline__ df exact_jm1_at(const FeArgs<float>& A, int e) {
+  using EL = El<kEl>;
+  const int E = A.E;
+  const int n0 = __ldg(A.conn + e);
+  int c0[3];
+  float o0[3], X0[3];
+  A.pos.load(n0, c0, o0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + n0);
+  const df h(A.h, A.hlo);
+  df M[3][3], B[3][3];
+#pragma unroll
+  for (int a = 1; a < EL::C; ++a) {
+    const int na = __ldg(A.conn + a * E + e);
+    int c[3];
+    float o[3];
+    A.pos.load(na, c, o);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const df od = two_sum(o[d], -o0[d]);                    // exact
+      const df sc = two_sum(float(c[d] - c0[d]), od.hi);      // exact
+      const df dx = dmul(df(sc.hi, __fadd_rn(sc.lo, od.lo)), h);
+      const df dX = two_sum(__ldg(A.X + d * A.N + na), -X0[d]);  // exact
+      const df du = dadd(dx, neg(dX));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        M[d][j] = dfma(M[d][j], dX, float(EL::dxi(a, Q, j)));
+        B[d][j] = dfma(B[d][j], du, float(EL::dxi(a, Q, j)));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      M[i][j] = norm(M[i][j]);
+      B[i][j] = norm(B[i][j]);
+    }
+  df CM[3][3], CB[3][3];
+  cof3(M, CM);
+  cof3(B, CB);
+  df t, j0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      t = dfma(t, CM[i][j], B[i][j]);
+      t = dfma(t, M[i][j], CB[i][j]);
+    }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    t = dfma(t, B[0][j], CB[0][j]);
+    j0 = dfma(j0, M[0][j], CM[0][j]);
+  }
+  return ddiv(norm(t), norm(j0));
+}
+
+template <int kEl>
+__global__ void __launch_bounds__(128) k_exact_jm1(FeArgs<float> A, float2* __restrict__ jx) {
+  using EL = El<kEl>;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)EL::QF * A.E) return;
+  const int q = (int)(t / A.E), e = (int)(t % A.E);
+  df r;
+  switch (q) {  // q is uniform across a warp except where two q blocks meet
+    case 0: r = exact_jm1_at<kEl, 0>(A, e); break;
+    case 1: if constexpr (EL::QF > 1) r = exact_jm1_at<kEl, 1 % EL::QF>(A, e); break;
+    case 2: if constexpr (EL::QF > 2) r = exact_jm1_at<kEl, 2 % EL::QF>(A, e); break;
+    case 3: if constexpr (EL::QF > 3) r = exact_jm1_at<kEl, 3 % EL::QF>(A, e); break;
+    case 4: if constexpr (EL::QF > 4) r = exact_jm1_at<kEl, 4 % EL::QF>(A, e); break;
+    case 5: if constexpr (EL::QF > 5) r = exact_jm1_at<kEl, 5 % EL::QF>(A, e); break;
+    case 6: if constexpr (EL::QF > 6) r = exact_jm1_at<kEl, 6 % EL::QF>(A, e); break;
+    default: if constexpr (EL::QF > 7) r = exact_jm1_at<kEl, 7 % EL::QF>(A, e); break;
+  }
+  jx[t] = make_float2(r.hi, r.lo);
+}
+
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e) {
   using EL = El<kEl>;
@@ -158,6 +260,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   int node[EL::C];
 #pragma unroll
   for (int a = 0; a < EL::C; ++a) node[a] = __ldg(A.conn + a * E + e);
+  constexpr bool volx = (kLaws & kLawVolX) != 0;
+  static_assert(!volx || (std::is_same<Real, float>::value && std::is_same<S, df>::value),
+                "the exact volumetric invariant is a split-precision option");
 
   // reference and current coordinates relative to corner 0
   Real dX[EL::C][3], du[EL::C][3];
@@ -281,13 +386,19 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     // sum in S of the FP32 entries of H and of their exact pairwise products
     // (near incompressibility tr H cancels to |J - 1| << |H|); det H (third
     // order) is taken in Real.
-    S Jm1 = dacc(S(0), H[0][0], H[1][1]);
-    Jm1 = dacc(Jm1, H[0][0], H[2][2]);
-    Jm1 = dacc(Jm1, H[1][1], H[2][2]);
-    Jm1 = dacc(Jm1, -H[0][1], H[1][0]);
-    Jm1 = dacc(Jm1, -H[0][2], H[2][0]);
-    Jm1 = dacc(Jm1, -H[1][2], H[2][1]);
-    Jm1 = sacc(sacc(sacc(sacc(Jm1, H[0][0]), H[1][1]), H[2][2]), det3(H));
+    S Jm1;
+    if constexpr (volx) {
+      const float2 jq = __ldg(A.jx + (int64_t)q * E + e);
+      Jm1 = S(jq.x, jq.y);
+    } else {
+      Jm1 = dacc(S(0), H[0][0], H[1][1]);
+      Jm1 = dacc(Jm1, H[0][0], H[2][2]);
+      Jm1 = dacc(Jm1, H[1][1], H[2][2]);
+      Jm1 = dacc(Jm1, -H[0][1], H[1][0]);
+      Jm1 = dacc(Jm1, -H[0][2], H[2][0]);
+      Jm1 = dacc(Jm1, -H[1][2], H[2][1]);
+      Jm1 = sacc(sacc(sacc(sacc(Jm1, H[0][0]), H[1][1]), H[2][2]), det3(H));
+    }
     const S lnJs = log1p_s(Jm1);
     const Real lnJ = Real(lnJs);
     const Real J = Real(1) + Real(Jm1);
@@ -687,6 +798,8 @@ inline FeArgs<float> make_args<float>(ib_plan* p, const void* xa, const float* o
   A.pos.off = off;
   A.pos.N = p->N;
   A.h = (float)p->grid.h;
+  A.hlo = (float)(p->grid.h - (double)A.h);
+  A.jx = (const float2*)p->vol_jm1;
   A.v = (const float*)v;
   A.out = (float*)out;
   A.epart = p->epart;
@@ -710,6 +823,8 @@ inline FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*
   for (int d = 0; d < 3; ++d) A.pos.origin[d] = p->grid.origin[d];
   A.pos.inv_h = 1.0 / p->grid.h;
   A.h = p->grid.h;
+  A.hlo = 0.f;
+  A.jx = nullptr;
   A.v = (const double*)v;
   A.out = (double*)out;
   A.epart = p->epart;
@@ -731,6 +846,11 @@ ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* of
   const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : p->fe_ctas;
   const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
   if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
+  if constexpr ((kLaws & kLawVolX) != 0) {
+    if (!p->vol_jm1) return IB_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)El<kEl>::QF * p->E;
+    k_exact_jm1<kEl><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, (float2*)p->vol_jm1);
+  }
   k_fe<Real, S, kEnergy, kAdj, kParams, kLaws, kEl><<<blocks, threads, 0, s>>>(A, mt);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }

@@ -44,6 +44,8 @@ constexpr int kLawAct = 1 << 5;
 constexpr int kLawBase = (1 << IB_NEO_HOOKEAN) | (1 << IB_FIBRE1) | (1 << IB_HO);
 constexpr int kLawBaseAct = kLawBase | kLawAct;
 constexpr int kLawAll = kLawBase | (1 << IB_STD_REINF) | (1 << IB_FIBRE2) | kLawAct;
+// Not a law: the exact volumetric invariant of IB_FP32_SPLIT_DFVOL plans.
+constexpr int kLawVolX = 1 << 6;
 
 // Material table passed by value to kernels.
 struct MatTable {
@@ -137,9 +139,10 @@ struct ib_plan {
   int32_t* tile_near;    // [ntiles] 1 if a tile of its 3x3x3 neighbourhood holds points
   int32_t* tile_list;    // [max work items] tile of each work item
   int32_t* tile_list_near;// [ntiles] near tiles, ascending
+  uint32_t* tile_vmax;   // [ntiles] FP32: bits of the largest |carried value| of each tile
   int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
   int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
-                         //     [5] spread absmax bits, [6] FE force block counter
+                         //     [6] FE force block counter
   int32_t* digit_tot;    // [256] radix digit totals
   double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*kParamRow] reduction partials
   cudaStream_t side;     // interpolation branch of ib_forward
@@ -167,6 +170,7 @@ struct ib_plan {
   const void* pen_w;
   double pen_kappa;
   double* pen_part;      // energy partials and their sum
+  void* vol_jm1;         // float2 [force points][E]: exact J - 1 (IB_FP32_SPLIT_DFVOL only)
   void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
   void* gq_b;            // Real [3][Q]
   double* epart;         // [kParamRow][E] per-element partial sums
@@ -206,9 +210,9 @@ ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* of
 // out = add + src over 3 N values (add optional, may be out)
 ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* add,
                            cudaStream_t s);
-// out = add + node_scale * (gather of elem); add optional (may be out)
+// out = add + mul node_scale * (gather of elem); add optional (may be out)
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* node_scale, void* out,
-                             cudaStream_t s, const void* add = nullptr);
+                             cudaStream_t s, const void* add = nullptr, double mul = 1.0);
 ib_status launch_elem_project(ib_plan* p, const void* gq_vals, void* elem_out, cudaStream_t s);
 ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
 
@@ -255,7 +259,9 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
 bool penalty_on(const ib_plan* p);
 ib_status launch_penalty(ib_plan* p, const ib_pos* x, void* G, bool energy, cudaStream_t s);
 const double* penalty_energy_dev(const ib_plan* p);
-ib_status launch_penalty_adj(ib_plan* p, const void* v, void* Hv, cudaStream_t s);
+// Hv -= mul kappa w v at the tethered nodes
+ib_status launch_penalty_adj(ib_plan* p, const void* v, void* Hv, cudaStream_t s,
+                             double mul = 1.0);
 size_t penalty_scratch_doubles();
 
 // fluid.cu

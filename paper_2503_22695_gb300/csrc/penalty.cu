@@ -92,12 +92,12 @@ __global__ void __launch_bounds__(256) k_penalty(PenArgs<Real> A, Real* __restri
 // Hv_a -= kappa w v_a (the tethers' share of the force adjoint)
 template <typename Real>
 __global__ void __launch_bounds__(256) k_penalty_adj(PenArgs<Real> A, const Real* __restrict__ v,
-                                                     Real* __restrict__ Hv) {
+                                                     Real* __restrict__ Hv, Real mul) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.n) return;
   const int a = A.nodes[t];
   if (a < 0 || a >= A.N) return;
-  const Real kw = Real(A.kappa * pen_weight(A, t, a));
+  const Real kw = Real(A.kappa * pen_weight(A, t, a)) * mul;
 #pragma unroll
   for (int d = 0; d < 3; ++d) Hv[d * A.N + a] -= kw * v[d * A.N + a];
 }
@@ -144,16 +144,16 @@ ib_status launch_penalty(ib_plan* p, const ib_pos* x, void* G, bool energy, cuda
 
 const double* penalty_energy_dev(const ib_plan* p) { return p->pen_part + kPenCTAs; }
 
-ib_status launch_penalty_adj(ib_plan* p, const void* v, void* Hv, cudaStream_t s) {
+ib_status launch_penalty_adj(ib_plan* p, const void* v, void* Hv, cudaStream_t s, double mul) {
   if (!penalty_on(p)) return IB_OK;
   const int g = (p->pen_n + 255) / 256;
-  ib_pos none{nullptr, nullptr, nullptr};
+  ib_pos none{nullptr, nullptr, nullptr, 0.0};
   if (p->precision == IB_FP64)
     k_penalty_adj<double><<<g, 256, 0, s>>>(pen_args<double>(p, &none), (const double*)v,
-                                            (double*)Hv);
+                                            (double*)Hv, mul);
   else
     k_penalty_adj<float><<<g, 256, 0, s>>>(pen_args<float>(p, &none), (const float*)v,
-                                           (float*)Hv);
+                                           (float*)Hv, (float)mul);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -224,15 +224,40 @@ __global__ void __launch_bounds__(128) k_point_values(int E, int64_t N,
   }
 }
 
-// Sorted copies of the carried values.
+// Largest |value| of each tile (FP32 binning: the fixed-point exponent of the
+// spreading): one integer maximum of float bit patterns per group of the
+// warp's lanes that share a tile.
+__device__ __forceinline__ void tile_vmax_update(uint32_t* vmax, uint32_t tile, float v0, float v1,
+                                                 float v2) {
+  const uint32_t m = __float_as_uint(fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))));
+  const unsigned peers = __match_any_sync(__activemask(), tile);
+  const uint32_t mx = __reduce_max_sync(peers, m);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(vmax + tile, mx);
+}
+
+// Binned copies of the carried values (and, for FP32 plans, the per-tile
+// maxima of their magnitudes).
 template <typename Real>
 __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
-                                 const Real* __restrict__ q_val, Real* __restrict__ p_val) {
+                                 const Real* __restrict__ q_val, Real* __restrict__ p_val,
+                                 const int32_t* __restrict__ p_cell, GridDev g,
+                                 uint32_t* __restrict__ vmax) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Q) return;
-  const int32_t g = __ldg(p_idx + i);
+  const int32_t gi = __ldg(p_idx + i);
+  Real v[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) p_val[d * Q + i] = __ldg(q_val + d * Q + g);
+  for (int d = 0; d < 3; ++d) {
+    v[d] = __ldg(q_val + d * Q + gi);
+    p_val[d * Q + i] = v[d];
+  }
+  if constexpr (sizeof(Real) == 4) {
+    int cx, cy, cz;
+    unpack_cell(__ldg(p_cell + i), cx, cy, cz);
+    const uint32_t tile = (uint32_t)((cx >> kTileShift) +
+                                     g.nt[0] * ((cy >> kTileShift) + g.nt[1] * (cz >> kTileShift)));
+    tile_vmax_update(vmax, tile, v[0], v[1], v[2]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -347,24 +372,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
 }
 
 // Binning: every point to start[tile] + slot, with its cell, offset, index
-// and (optionally) carried value.
+// and (optionally) carried value and the per-tile maxima of its magnitude.
 template <typename Real>
 __global__ void k_bin_scatter(int64_t Q, const uint32_t* __restrict__ tile,
                               const int32_t* __restrict__ slot, const int32_t* __restrict__ start,
                               const int32_t* __restrict__ q_cell, const Real* __restrict__ q_off,
                               const Real* __restrict__ q_val, int32_t* __restrict__ p_cell,
                               Real* __restrict__ p_off, Real* __restrict__ p_val,
-                              int32_t* __restrict__ p_idx, bool with_val) {
+                              int32_t* __restrict__ p_idx, bool with_val,
+                              uint32_t* __restrict__ vmax) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Q) return;
-  const int64_t i = __ldg(start + __ldg(tile + g)) + __ldg(slot + g);
+  const uint32_t t = __ldg(tile + g);
+  const int64_t i = __ldg(start + t) + __ldg(slot + g);
   p_idx[i] = (int32_t)g;
   p_cell[i] = __ldg(q_cell + g);
 #pragma unroll
   for (int d = 0; d < 3; ++d) p_off[d * Q + i] = __ldg(q_off + d * Q + g);
   if (with_val) {
+    Real v[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) p_val[d * Q + i] = __ldg(q_val + d * Q + g);
+    for (int d = 0; d < 3; ++d) {
+      v[d] = __ldg(q_val + d * Q + g);
+      p_val[d * Q + i] = v[d];
+    }
+    if constexpr (sizeof(Real) == 4) tile_vmax_update(vmax, t, v[0], v[1], v[2]);
   }
 }
 
@@ -483,10 +515,11 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
     if (launch_classify_tiles(p, s) != IB_OK) return IB_ERR_CUDA;  // also the ranges
     if (Q == 0) return IB_OK;
     const int nb = (int)((Q + 255) / 256);
+    if (with_val) cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
     k_bin_scatter<float><<<nb, 256, 0, s>>>(Q, p->keys[0], p->vals[0], p->tile_start, p->q_cell,
                                             (const float*)p->q_off, (const float*)p->q_val,
                                             p->p_cell, (float*)p->p_off, (float*)p->p_val,
-                                            p->p_idx, with_val);
+                                            p->p_idx, with_val, p->tile_vmax);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
   cudaMemsetAsync(p->tile_start, 0, sizeof(int32_t) * p->ntiles, s);
@@ -543,12 +576,14 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
 ib_status launch_permute_values(ib_plan* p, cudaStream_t s) {
   if (p->Q == 0) return IB_OK;
   const int nb = (int)((p->Q + 255) / 256);
-  if (p->precision == IB_FP64)
+  if (p->precision == IB_FP64) {
     k_permute_values<double><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
-                                                (double*)p->p_val);
-  else
+                                                (double*)p->p_val, p->p_cell, p->grid, nullptr);
+  } else {
+    cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
     k_permute_values<float><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val,
-                                               (float*)p->p_val);
+                                               (float*)p->p_val, p->p_cell, p->grid, p->tile_vmax);
+  }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

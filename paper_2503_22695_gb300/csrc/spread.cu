@@ -63,7 +63,7 @@ struct SpreadArgs {
   Real scale;
   Real* scratch;               // [items][3][12^3]
   Real* f;
-  uint32_t* absmax;            // bits of max |value| over all points (fixed-point scale)
+  const uint32_t* tile_vmax;   // FP32: bits of max |value| over each tile's points
 };
 
 // cp.async of 4 bytes global -> shared (completion awaited with cp_async_wait)
@@ -239,65 +239,67 @@ __global__ void __launch_bounds__(kPT) k_spread_push(SpreadArgs<Real> A) {
 // ---------------------------------------------------------------------------
 // FP32 plans: order-independent fixed-point accumulation.
 //
-// Every contribution C = V prod phi of an item, in units of 2^-k, is split into
-// an integer part h = round(C) and a fraction l = round(2^11 (C - h)) (in
-// units of 2^-(k+11)), and both are added with native 32-bit shared-memory
-// atomics into one block per CTA.  Integer addition is exact and associative,
-// so the block is the same whatever the order of the additions.
+// Every contribution C = V scale prod phi of a point of tile t, in units of
+// 2^-k_t, is split into an integer part h = round(C) and a fraction
+// l = round(2^11 (C - h)) (units of 2^-(k_t + 11)), and both are added with
+// native 32-bit shared-memory atomics into the work item's two word blocks.
+// Integer addition is exact and associative, so the blocks do not depend on
+// the order of the additions, on the order of the points or on how a tile's
+// points are cut into work items.
 //
 // Both parts come from the magic-number rounding t = x + 1.5 2^23, whose bit
 // pattern is 0x4B400000 + round(x) for |x| < 2^22; three fmas per
 // contribution give both patterns, which are added as they are:
 //   t1 = C + M                 bits(t1) = Mb + h
-//   z  = M - 2^11 (t1 - M)     (exact: a multiple of 2^11 below 2^32)
+//   z  = M - 2^11 (t1 - M)     (exact: a multiple of 2^11 below 2^33)
 //   t2 = 2^11 C + z            bits(t2) = Mb + l,  |l| <= 2^10
 // After n contributions the words are hi = n Mb + H and lo = n Mb + L (mod
 // 2^32).  Mb = 301 2^22 has zero low 22 bits and |L| <= 2^20 (n <= 1024), so
-// L is the sign-extended low 22 bits of lo, and H = (hi - lo) + L.  k comes
-// from the largest |V| of the call (one integer atomicMax over the float bit
-// patterns) so that |C| < 2^19, since every kernel weight product is at most
-// 1/8; hence |H| < 2^29.  The resolution is 2^-(k+12), about 2^-31 of the
-// largest contribution; each block value H 2^11 + L is rounded to float by
-// one fma of the two parts converted to float (exact conversions while
-// |H| < 2^24); the same integers always give the same float.
+// L is the sign-extended low 22 bits of lo and H = (hi - lo) + L; the item
+// stores S = 2^11 H + L per face, exact.
+//
+// Exponent of a tile (fx_tile_exp): from the largest |V| over the tile's
+// points (an integer maximum of float bit patterns, itself order-independent)
+// and its point count n_t.  Every kernel weight product is at most 1/8, so
+// with cm = max|V| |scale| / 8 < 2^e, n_eff = min(n_t, the largest work
+// item, 1024) <= 2^L and k = min(21, 30 - L) - e, each contribution is below
+// 2^21 and |H| below 2^31 at every face of an item.  The resolution 2^-(k+11)
+// is about 2^-31 of the tile's largest contribution times n_eff / 1024; tiles
+// far from large values keep their own fine resolution.
+//
+// Merge (k_spread_merge_fx): each face sums the items' S of every source tile
+// in 64-bit integers, aligns the source sums to one exponent per destination
+// tile (left shifts that provably fit in 64 bits; finer sources beyond that
+// headroom are shifted right, a loss below 2^-17 of the coarsest source's
+// resolution), adds them and rounds once.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ v, int64_t n,
-                                               uint32_t* __restrict__ out) {
-  float m = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(v[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
-}
-
-constexpr float kMagic = 12582912.0f;            // M = 1.5 * 2^23
-constexpr float kMagicZ = 12582912.0f * 2049.0f; // M (1 + 2^11), exact in float
+constexpr float kMagic = 12582912.0f;             // M = 1.5 * 2^23
+constexpr float kMagicZ = 12582912.0f * 2049.0f;  // M (1 + 2^11), exact in float
 constexpr int kFxThreads = 256;
 constexpr int kFxWarps = kFxThreads / 32;
-constexpr int kFxGroup = 16;  // points a warp stages at a time
+constexpr int kFxGroup = 16;  // points a warp stages at a time: 2 lanes per point
 // Lane mapping: a warp takes one point at a time; lane (dz, dy, xh) adds the
-// faces xh and xh + 2 of stencil row (dz, dy), one instruction per face pair
-// and component.  With y stride 14 and z stride 168 the 16 row offsets
+// faces xh and xh + 2 of stencil row (dz, dy), one instruction per face,
+// word and component.  With y stride 14 and z stride 168 the 16 row offsets
 // 168 dz + 14 dy are the 16 even residues mod 32, so the 32 lanes of every
 // atomic hit 32 distinct banks wherever the point lies.
 constexpr int kFxSY = 14;
 constexpr int kFxSZ = kB * kFxSY;       // 168
 constexpr int kFxAcc = kB * kFxSZ;      // 2016 words per component
-
-// The points a warp has staged, one array per field.  Each warp owns one
-// group: staging needs no CTA barrier, only the warp's own __syncwarp.  The
-// weight arrays are stencil-index major with rows padded by one record, so
-// the staging stores of 16 consecutive points are contiguous and the per-point
-// reads of the 2 or 4 distinct rows fall in distinct banks (one wavefront).
-constexpr int kFxRow = kFxGroup + 1;
-struct FxGroup {
-  float4 val[kFxGroup];     // 2^k V^c * scale, c = 0..2; w: the packed stencil origin (fx_pack_origin)
-  float2 wz[4][kFxRow];     // [dz][pt] = (w_z at s = 0, w_z at s = 1/2)
-  float2 wy[4][kFxRow];     // [dy][pt] likewise
-  float4 wx[2][kFxRow];     // [xh][pt] = (w_x(s 0)[xh], w_x(s 0)[xh + 2], w_x(s 1/2)[xh], w_x(s 1/2)[xh + 2])
-};
+constexpr int kFxWords = 3 * kFxAcc;    // one word block (hi or lo) of a work item
+constexpr int kFxBlk = 3 * kBlk;        // faces of an item's halo'd block: one int64 S each
+// A staged point (9 float4, an odd stride so that the staging stores of the
+// group's points to one slot spread over the banks): [0..3] the rows dz of
+// (v0 w_z(1/2), v1 w_z(1/2), v2 w_z(0), 0) with v = 2^k V scale, [4..5] the
+// pairs (w_y(0)[dy], w_y(1/2)[dy]), [6..7] the x weights of the two lane
+// halves (xh = 0, 1: (s 0 [xh], s 0 [xh + 2], s 1/2 [xh], s 1/2 [xh + 2])),
+// [8] the word offsets of the three components' stencil starts.  Each
+// component takes its own staggering (0: x at 0, y and z at 1/2; 1: y at 0;
+// 2: z at 0); a lane forms its row weight from the z and y parts.
+constexpr int kFxRec = 9;
+constexpr int kFxRecWy = 4;
+constexpr int kFxRecWx = 6;
+constexpr int kFxRecOrg = 8;
 
 // adds the contribution C = w wx (in units of 2^-k) at word offset a
 __device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float w, float w11, float wx) {
@@ -308,23 +310,35 @@ __device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float w, floa
   atomicAdd(lo, __float_as_uint(t2));
 }
 
-// Fixed-point exponent k of the call: |C| = |V scale| prod phi < 2^19 in
-// units of 2^-k, since every kernel weight product is at most 1/8.
-__device__ __forceinline__ int fx_exponent(const SpreadArgs<float>& A) {
-  const float cmax = 0.125f * __uint_as_float(*A.absmax) * fabsf(A.scale);
-  int ex = 0;
-  if (cmax > 0.f) frexpf(cmax, &ex);  // cmax < 2^ex
-  return min(19 - ex, 100);           // keep 2^(k+11) a normal float
+__device__ __forceinline__ int ceil_log2(int n) { return n > 1 ? 32 - __clz(n - 1) : 0; }
+
+// Fixed-point exponent of a tile from the bits of its largest |V|, its point
+// count and the call's scale (see above).  n_eff uses the largest work item
+// any tuning may choose (kChunk), so the exponent, hence the result, does not
+// depend on the plan's tuning.  Values of magnitude up to about 2^120 / |scale|
+// are representable.
+__device__ __forceinline__ int fx_tile_exp(uint32_t vmax_bits, int npts, float scale) {
+  const float cm = 0.125f * __uint_as_float(vmax_bits) * fabsf(scale);
+  if (!(cm > 0.f) || !(cm <= 3.0e38f)) return 0;  // no values, or not finite
+  int e = 0;
+  frexpf(cm, &e);  // cm < 2^e
+  const int k = min(21, 30 - ceil_log2(min(npts, kChunk))) - e;
+  return max(-100, min(k, 100));
 }
 
-// The accumulator offsets of a stencil's first face, one per component, in
-// 14 bits: with b_d the half-shifted (s = 1/2) start along axis d and g_d = 1
-// when the unshifted (s = 0) start is one face further (0 otherwise),
-// B = 168 b_z + 14 b_y + b_x < 2^11 and
-//   o_0 = B + g_x,   o_1 = A + B + 14 g_y,   o_2 = 2 A + B + 168 g_z   (A = kFxAcc).
-__device__ __forceinline__ int fx_pack_origin(const int b[3][2]) {
-  const int B = b[2][1] * kFxSZ + b[1][1] * kFxSY + b[0][1];
-  return B | (b[0][0] - b[0][1]) << 11 | (b[1][0] - b[1][1]) << 12 | (b[2][0] - b[2][1]) << 13;
+// The 4-point weights of delta_weights with the hardware reciprocal square
+// root and reciprocal (a few units in the last place instead of correctly
+// rounded steps): q = (1 + p) rsqrt(1 + p), q - 1 = p / (1 + q).
+__device__ __forceinline__ void fx_weights(float th, float w[4]) {
+  const float om = 1.f - th;
+  const float p = 4.f * th * om;
+  const float s = 1.f + p;
+  const float q = s * rsqrtf(s);
+  const float qm1 = __fdividef(p, 1.f + q);
+  w[0] = (2.f * om - qm1) * 0.125f;
+  w[1] = (2.f * om + 2.f + qm1) * 0.125f;
+  w[2] = (2.f * th + 2.f + qm1) * 0.125f;
+  w[3] = (2.f * th - qm1) * 0.125f;
 }
 
 // Raw data of one point, loaded a group ahead so that the loads are in
@@ -335,22 +349,21 @@ struct FxRaw {
   float val[3];
 };
 
-__device__ __forceinline__ void fx_fetch(const SpreadArgs<float>& A, int i, bool want_val,
-                                         FxRaw& r) {
+__device__ __forceinline__ void fx_fetch(const SpreadArgs<float>& A, int i, FxRaw& r) {
   r.cell = __ldg(A.p_cell + i);
 #pragma unroll
   for (int d = 0; d < 3; ++d) r.off[d] = __ldg(A.p_off + d * A.Q + i);
-  if (want_val) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) r.val[c] = __ldg(A.p_val + c * A.Q + i);
-  }
+  for (int c = 0; c < 3; ++c) r.val[c] = __ldg(A.p_val + c * A.Q + i);
 }
 
-// Lanes pt and pt + 16 stage point pt of the group: each evaluates three of
-// the six 1-D weight sets (lane half 0: x at s = 0 and 1/2, y at s = 0;
-// lane half 1: y at s = 1/2, z at s = 0 and 1/2), so both halves run the
-// same instructions.
-__device__ __forceinline__ void fx_stage(FxGroup& G, int pt, int part, const FxRaw& r,
+// Lanes pt and pt + kFxGroup stage point pt of the group.  Lane half `part`
+// evaluates the 1-D weights of its staggering along all three axes (part 0:
+// s = 0, part 1: s = 1/2), takes the other staggering's y weights and the z
+// weights of its two rows from its partner lane, and writes the rows
+// dz = 2 part, 2 part + 1.  Every lane of the warp runs this (the shuffles
+// need the whole warp); `store` is false for lanes past the group's end.
+__device__ __forceinline__ void fx_stage(float4* rec, int part, bool store, const FxRaw& r,
                                          const int lc0[3], float vscale) {
   int cc[3];
   unpack_cell(r.cell, cc[0], cc[1], cc[2]);
@@ -359,32 +372,52 @@ __device__ __forceinline__ void fx_stage(FxGroup& G, int pt, int part, const FxR
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int hf = 0; hf < 2; ++hf) b[d][hf] = cc[d] - lc0[d] + stencil_axis(r.off[d], hf == 1, th[d][hf]) + 2;
-  float wa[4], wb[4], wc[4];
-  delta_weights(part ? th[1][1] : th[0][0], wa);
-  delta_weights(part ? th[2][0] : th[0][1], wb);
-  delta_weights(part ? th[2][1] : th[1][0], wc);
-  if (part == 0) {
-    G.wx[0][pt] = make_float4(wa[0], wa[2], wb[0], wb[2]);
-    G.wx[1][pt] = make_float4(wa[1], wa[3], wb[1], wb[3]);
+    for (int hf = 0; hf < 2; ++hf)
+      b[d][hf] = cc[d] - lc0[d] + stencil_axis(r.off[d], hf == 1, th[d][hf]) + 2;
+  float w[3][4];  // this half's staggering
 #pragma unroll
-    for (int j = 0; j < 4; ++j) G.wy[j][pt].x = wc[j];
-    G.val[pt] = make_float4(r.val[0] * vscale, r.val[1] * vscale, r.val[2] * vscale,
-                            __int_as_float(fx_pack_origin(b)));
-  } else {
+  for (int d = 0; d < 3; ++d) fx_weights(part ? th[d][1] : th[d][0], w[d]);
+  const unsigned full = 0xffffffffu;
+  float wyo[4];  // the partner's y weights (the other staggering)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      G.wy[j][pt].y = wa[j];
-      G.wz[j][pt] = make_float2(wb[j], wc[j]);
-    }
+  for (int j = 0; j < 4; ++j) wyo[j] = __shfl_xor_sync(full, w[1][j], kFxGroup);
+  // the partner's z weights of this half's rows
+  const float zo0 = __shfl_xor_sync(full, part ? w[2][0] : w[2][2], kFxGroup);
+  const float zo1 = __shfl_xor_sync(full, part ? w[2][1] : w[2][3], kFxGroup);
+  if (!store) return;
+  float wy0[4], wyh[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    wy0[j] = part ? wyo[j] : w[1][j];
+    wyh[j] = part ? w[1][j] : wyo[j];
   }
+  const float v0 = r.val[0] * vscale, v1 = r.val[1] * vscale, v2 = r.val[2] * vscale;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float own = part ? w[2][2 + j] : w[2][j];
+    const float oth = j ? zo1 : zo0;
+    const float wz0 = part ? oth : own, wzh = part ? own : oth;
+    // component 0: z, y at s = 1/2; component 1: z at 1/2, y at 0; component 2: z at 0, y at 1/2
+    const float a0 = v0 * wzh, a1 = v1 * wzh, a2 = v2 * wz0;
+    rec[2 * part + j] = make_float4(a0, a1, a2, 0.f);
+  }
+  rec[kFxRecWy + part] = part ? make_float4(wy0[2], wyh[2], wy0[3], wyh[3])
+                              : make_float4(wy0[0], wyh[0], wy0[1], wyh[1]);
+  reinterpret_cast<float2*>(rec + kFxRecWx)[part] = make_float2(w[0][0], w[0][2]);
+  reinterpret_cast<float2*>(rec + kFxRecWx + 1)[part] = make_float2(w[0][1], w[0][3]);
+  if (part == 0)
+    reinterpret_cast<int4*>(rec)[kFxRecOrg] =
+        make_int4(b[2][1] * kFxSZ + b[1][1] * kFxSY + b[0][0],
+                  kFxAcc + b[2][1] * kFxSZ + b[1][0] * kFxSY + b[0][1],
+                  2 * kFxAcc + b[2][0] * kFxSZ + b[1][1] * kFxSY + b[0][1], 0);
 }
 
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FxGroup* groups = reinterpret_cast<FxGroup*>(smem_raw);
-  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + kFxWarps * sizeof(FxGroup));
-  unsigned* acc_lo = acc_hi + 3 * kFxAcc;
+  float4* groups = reinterpret_cast<float4*>(smem_raw);
+  unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(float4) * kFxWarps * kFxGroup *
+                                                                kFxRec);
+  unsigned* acc_lo = acc_hi + kFxWords;
   __shared__ int next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = A.counters[0];
@@ -393,75 +426,74 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
   const int ldz = lane >> 3, ldy = (lane >> 1) & 3, lxh = lane & 1;
   const int loff = ldz * kFxSZ + ldy * kFxSY + lxh;
   // this lane's staging role: point pt of the group, lane half `part`
-  const int pt = lane & (kFxGroup - 1), part = lane >> 4;
-  FxGroup& G = groups[warp];
-  const int k = fx_exponent(A);
-  const float vscale = A.scale * ldexpf(1.f, k);
+  const int pt = lane & (kFxGroup - 1), part = (lane / kFxGroup) & 1;
+  const bool stager = lane < 2 * kFxGroup;
+  float4* G = groups + warp * kFxGroup * kFxRec;
   for (;;) {
-    __syncthreads();  // previous item decoded
+    __syncthreads();  // previous item written out
     if (tid == 0) next = atomicAdd(A.counters + 1, 1);
     __syncthreads();
     const int slot = next;
     if (slot >= count) break;
     const int tile = A.tile_list[slot];
     const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-    const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
-    const int e = min(A.tile_end[tile], s + A.chunk);
+    const int t0 = A.tile_start[tile], t1 = A.tile_end[tile];
+    const int s = t0 + (slot - A.tile_slot[tile]) * A.chunk;
+    const int e = min(t1, s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
-    // warp w takes the groups starting at s + 16 (w + 8 j)
-    FxRaw raw;
+    const float vscale =
+        A.scale * ldexpf(1.f, fx_tile_exp(A.tile_vmax[tile], t1 - t0, A.scale));
+    // warp w takes the groups starting at s + kFxGroup (w + 8 j)
+    FxRaw raw = {0, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int g0 = s + warp * kFxGroup;
-    if (g0 + pt < e) fx_fetch(A, g0 + pt, part == 0, raw);
-    for (int i = tid; i < 3 * kFxAcc * 2 / 4; i += kFxThreads)
+    if (stager && g0 + pt < e) fx_fetch(A, g0 + pt, raw);
+    for (int i = tid; i < 2 * kFxWords / 4; i += kFxThreads)
       reinterpret_cast<uint4*>(acc_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();  // accumulators zeroed
     for (; g0 < e; g0 += kFxWarps * kFxGroup) {
       const int ng = min(kFxGroup, e - g0);
-      if (pt < ng) fx_stage(G, pt, part, raw, lc0, vscale);
+      fx_stage(G + pt * kFxRec, part, stager && pt < ng, raw, lc0, vscale);
       __syncwarp();
       const int gn = g0 + kFxWarps * kFxGroup;
-      if (gn + pt < e) fx_fetch(A, gn + pt, part == 0, raw);
-      // one point per warp step: lane (dz, dy, xh) adds faces xh and xh + 2 of
-      // its (dz, dy) row, for each component
+      if (stager && gn + pt < e) fx_fetch(A, gn + pt, raw);
+      // one point per warp step: lane (dz, dy, xh) adds faces xh and xh + 2
+      // of its (dz, dy) row, for each component
+#pragma unroll 2
       for (int q = 0; q < ng; ++q) {
-        const float4 v = G.val[q];
-        const int pk = __float_as_int(v.w);
-        const int B = (pk & 0x7FF) + loff;
-        const int4 org = make_int4(B + ((pk >> 11) & 1), kFxAcc + B + kFxSY * ((pk >> 12) & 1),
-                                   2 * kFxAcc + B + kFxSZ * ((pk >> 13) & 1), 0);
-        const float2 wz = G.wz[ldz][q], wy = G.wy[ldy][q];
-        const float4 wx = G.wx[lxh][q];
-        // component 0: z, y at s = 1/2, x at s = 0
-        float wr = v.x * wz.y * wy.y;
-        int a = org.x;
-        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.x);
-        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.y);
-        // component 1: z at s = 1/2, y at s = 0, x at s = 1/2
-        wr = v.y * wz.y * wy.x;
-        a = org.y;
-        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
-        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
-        // component 2: z at s = 0, y, x at s = 1/2
-        wr = v.z * wz.x * wy.y;
-        a = org.z;
-        fx_add(acc_hi + a, acc_lo + a, wr, wr * 2048.0f, wx.z);
-        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr, wr * 2048.0f, wx.w);
+        const float4* rq = G + q * kFxRec;
+        const float4 vz = rq[ldz];
+        const float2 wy = reinterpret_cast<const float2*>(rq + kFxRecWy)[ldy];
+        const float4 wr = make_float4(vz.x * wy.y, vz.y * wy.x, vz.z * wy.y, 0.f);
+        const float4 wx = rq[kFxRecWx + lxh];
+        const int4 og = reinterpret_cast<const int4*>(rq)[kFxRecOrg];
+        int a = og.x + loff;
+        float w11 = wr.x * 2048.0f;
+        fx_add(acc_hi + a, acc_lo + a, wr.x, w11, wx.x);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr.x, w11, wx.y);
+        a = og.y + loff;
+        w11 = wr.y * 2048.0f;
+        fx_add(acc_hi + a, acc_lo + a, wr.y, w11, wx.z);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr.y, w11, wx.w);
+        a = og.z + loff;
+        w11 = wr.z * 2048.0f;
+        fx_add(acc_hi + a, acc_lo + a, wr.z, w11, wx.z);
+        fx_add(acc_hi + a + 2, acc_lo + a + 2, wr.z, w11, wx.w);
       }
       __syncwarp();  // group consumed before it is restaged
     }
     __syncthreads();
-    // decoded words (H, L) of every face, exact; consecutive threads take
-    // consecutive face pairs of the 12-face x-rows (conflict-free reads,
-    // contiguous 16-byte stores)
-    int4* out = reinterpret_cast<int4*>(A.scratch) + (int64_t)slot * (kItemBlk / 2);
-    for (int u = tid; u < 3 * kB * kB * (kB / 2); u += kFxThreads) {
+    // S = 2^11 H + L of every face, exact, in the 12-face rows of the scratch
+    // block; consecutive threads take consecutive face pairs (16-byte stores)
+    longlong2* out = reinterpret_cast<longlong2*>(A.scratch) + (int64_t)slot * (kFxBlk / 2);
+    for (int u = tid; u < kFxBlk / 2; u += kFxThreads) {
       const int row = u / (kB / 2), x = 2 * (u % (kB / 2));
       const int c = row / (kB * kB), zy = row % (kB * kB);
       const int o = c * kFxAcc + (zy / kB) * kFxSZ + (zy % kB) * kFxSY + x;  // even: 8-byte aligned
       const uint2 hw = *reinterpret_cast<const uint2*>(acc_hi + o);
       const uint2 lw = *reinterpret_cast<const uint2*>(acc_lo + o);
       const int L0 = (int)(lw.x << 10) >> 10, L1 = (int)(lw.y << 10) >> 10;
-      out[u] = make_int4((int)(hw.x - lw.x) + L0, L0, (int)(hw.y - lw.y) + L1, L1);
+      const int H0 = (int)(hw.x - lw.x) + L0, H1 = (int)(hw.y - lw.y) + L1;
+      out[u] = make_longlong2((long long)H0 * 2048 + L0, (long long)H1 * 2048 + L1);
     }
   }
 }
@@ -553,22 +585,36 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   }
 }
 
-// FP32 plans: the same fixed-order walk over the covering blocks, summing the
-// exact words of every face in integers (H in 64 bits, L in 32) and rounding
-// once: S = 2^11 sum H + sum L is below 2^47, split as 2^24 hi + lo with both
-// parts exact in float, so one fma gives the correctly rounded S, then scaled
-// by 2^-(k+11).  The result does not depend on how a tile's points were cut
-// into work items.
+// FP32 plans: the same fixed-order walk over the covering blocks, summing
+// every face's S per source tile in 64-bit integers; the source sums are
+// aligned to the destination tile's exponent k_ref (in units of 2^-(k+11)) and
+// added, and the total is rounded once.  With k'_s = k_s + 11 for source s,
+//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
+// so a source sum (below items_s 2^42) shifted left by k_ref - k'_s stays
+// below 2^59 and eight of them below 2^62; a source with k'_s > k_ref is
+// shifted right (floor).  The conversion splits |S| into two 32-bit halves,
+// each converted exactly rounded, joined by one fma: within one unit in the
+// last place, the same bits for the same integers.
+__device__ __forceinline__ float fx_to_float(long long S, float out_scale) {
+  const unsigned long long m = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const float f = fmaf((float)(unsigned)(m >> 32), 4294967296.0f, (float)(unsigned)m);
+  return (S < 0 ? -f : f) * out_scale;
+}
+
+__device__ __forceinline__ long long fx_align(long long v, int sh) {
+  return sh >= 0 ? (long long)((unsigned long long)v << sh) : (v >> -sh);
+}
+
 __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
   static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
-  __shared__ int src_slot[27], src_n[27];
+  __shared__ int src_slot[27], src_n[27], src_sh[27];
+  __shared__ float out_scale;
   const int tid = threadIdx.x;
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int n0 = A.g.n[0], n1 = A.g.n[1];
   const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
   const int count = A.counters[3];
-  const float out_scale = ldexpf(1.f, -(fx_exponent(A) + 11));
-  const int4* scratch = reinterpret_cast<const int4*>(A.scratch);  // 2 faces per int4
+  const longlong2* scratch = reinterpret_cast<const longlong2*>(A.scratch);  // 2 faces each
   // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y), all three components
   const int z = tid >> 5, y = (tid >> 2) & 7, xq = tid & 3;
   const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
@@ -580,48 +626,65 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
     const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
     const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
     __syncthreads();
-    if (tid < 27) {
-      const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
-      const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
-      src_slot[tid] = A.tile_slot[nb];
-      src_n[tid] = A.tile_nitems[nb];
+    if (tid < 32) {
+      int slot = 0, ns = 0, ke = 0, kmax = -1000, kcap = 1000;
+      if (tid < 27) {
+        const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
+        const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
+        slot = A.tile_slot[nb];
+        ns = A.tile_nitems[nb];
+        if (ns > 0) {
+          ke = fx_tile_exp(A.tile_vmax[nb], A.tile_end[nb] - A.tile_start[nb], A.scale) + 11;
+          kmax = ke;
+          kcap = ke + 17 - ceil_log2(ns);
+        }
+      }
+      kmax = __reduce_max_sync(0xffffffffu, kmax);
+      kcap = __reduce_min_sync(0xffffffffu, kcap);
+      const int kref = min(kmax, kcap);
+      if (tid < 27) {
+        src_slot[tid] = slot;
+        src_n[tid] = ns;
+        src_sh[tid] = kref - ke;
+      }
+      if (tid == 0) out_scale = ldexpf(1.f, -kref);
     }
     __syncthreads();
-    long long sh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    int sl[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    long long tot[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     for (int oz = lz; oz <= hz; ++oz)
       for (int oy = ly; oy <= hy; ++oy)
         for (int ox = lx; ox <= hx; ++ox) {
-          // this face pair in the source tile's halo'd block (int4 units)
+          const int src = (oz + 1) * 9 + (oy + 1) * 3 + ox + 1;
+          const int ns = src_n[src];
+          if (ns == 0) continue;
+          // this face pair in the source tile's halo'd block (face-pair units)
           const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
                         (kTile / 2) * ox;
-          const int src = (oz + 1) * 9 + (oy + 1) * 3 + ox + 1;
-          const int slt = src_slot[src], ns = src_n[src];
-          const int4* r = scratch + (int64_t)slt * (kItemBlk / 2) + q;
-#pragma unroll 2
-          for (int j = 0; j < ns; ++j, r += kItemBlk / 2) {
-            int4 v[3];
+          const longlong2* r = scratch + (int64_t)src_slot[src] * (kFxBlk / 2) + q;
+          long long sh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+          for (int j = 0; j < ns; ++j, r += kFxBlk / 2) {
+            longlong2 v[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) v[c] = __ldg(r + c * (kBlk / 2));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              sh[c][0] += v[c].x; sl[c][0] += v[c].y;
-              sh[c][1] += v[c].z; sl[c][1] += v[c].w;
+              sh[c][0] += v[c].x;
+              sh[c][1] += v[c].y;
             }
           }
+          const int s = src_sh[src];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            tot[c][0] += fx_align(sh[c][0], s);
+            tot[c][1] += fx_align(sh[c][1], s);
+          }
         }
+    const float osc = out_scale;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float o[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const long long S = sh[c][i] * 2048 + sl[c][i];
-        const int hi = (int)(S >> 24);  // |S| < 2^47: |hi| < 2^23, exact in float
-        const int lo = (int)(S & 0xFFFFFF);
-        o[i] = fmaf((float)hi, 16777216.0f, (float)lo) * out_scale;
-      }
       float* row = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
-      reinterpret_cast<float2*>(row)[xq] = make_float2(o[0], o[1]);
+      reinterpret_cast<float2*>(row)[xq] =
+          make_float2(fx_to_float(tot[c][0], osc), fx_to_float(tot[c][1], osc));
     }
   }
 }
@@ -631,12 +694,10 @@ size_t push_smem() {
   return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
 }
 
-constexpr size_t kFxSmem = kFxWarps * sizeof(FxGroup) + sizeof(unsigned) * 2 * 3 * kFxAcc;
+constexpr size_t kFxSmem =
+    sizeof(float4) * kFxWarps * kFxGroup * kFxRec + sizeof(unsigned) * 2 * kFxWords;
 
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
-  cudaMemsetAsync(p->tile_counters + 5, 0, sizeof(int32_t), s);
-  if (p->Q > 0)
-    k_absmax<<<p->sm_count * 4, 256, 0, s>>>((const float*)p->p_val, 3 * p->Q, A.absmax);
   p->prof_calls[IB_STAGE_SPREAD_PUSH] += 1;
   const int ev = prof_begin(p, IB_STAGE_SPREAD_PUSH, s);
   k_spread_push_fx<<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads, kFxSmem,
@@ -669,7 +730,7 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f) {
   A.scale = (Real)scale;
   A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;
-  A.absmax = reinterpret_cast<uint32_t*>(p->tile_counters + 5);
+  A.tile_vmax = p->tile_vmax;
   return A;
 }
 
@@ -731,15 +792,16 @@ ib_status prepare_t(ib_plan* p) {
 }  // namespace
 
 size_t spread_scratch_bytes(int precision, int64_t slots) {
-  // FP64: one double per face; FP32: the exact word pair (H, L) per face
-  return (size_t)slots * kItemBlk * (precision == IB_FP64 ? sizeof(double) : sizeof(int2));
+  // FP64: one double per face; FP32: the exact integer S per face
+  return precision == IB_FP64 ? (size_t)slots * kItemBlk * sizeof(double)
+                              : (size_t)slots * kFxBlk * sizeof(long long);
 }
 
 ib_status spread_prepare(ib_plan* p) {
   return p->precision == IB_FP64 ? prepare_t<double>(p) : prepare_t<float>(p);
 }
 
-int spread_launches() { return 4; }
+int spread_launches() { return 3; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill) {
   return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s)

@@ -27,7 +27,7 @@ LIB_PATH = os.path.join(_HERE, "libibfe.so")
 IB_OK, IB_ERR_INVALID_ARG, IB_ERR_CUDA, IB_ERR_NONFINITE = 0, 1, 2, 3
 IB_ERR_CAPACITY, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED, IB_ERR_INVERTED = 4, 5, 6, 7
 IB_NEO_HOOKEAN, IB_FIBRE1, IB_HO, IB_STD_REINF, IB_FIBRE2 = 0, 1, 2, 3, 4
-IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB = 0, 1, 2
+IB_FP32_SPLIT, IB_FP64, IB_FP32_SPLIT_F32STAB, IB_FP32_SPLIT_DFVOL = 0, 1, 2, 3
 IB_QUAD_GAUSS2, IB_QUAD_NODAL = 0, 1
 IB_ELEM_HEX8, IB_ELEM_TET4, IB_ELEM_TET10 = 0, 1, 2
 _ELEM_OF_NODES = {8: IB_ELEM_HEX8, 4: IB_ELEM_TET4, 10: IB_ELEM_TET10}
@@ -56,7 +56,8 @@ class _Grid(C.Structure):
 
 
 class _Pos(C.Structure):
-    _fields_ = [("cell", C.c_void_p), ("off", C.c_void_p), ("x64", C.c_void_p)]
+    _fields_ = [("cell", C.c_void_p), ("off", C.c_void_p), ("x64", C.c_void_p),
+                ("grad_unit", C.c_double)]
 
 
 class _Mat(C.Structure):
@@ -175,14 +176,16 @@ def _mats(mats: Sequence[Material]):
 
 
 class Pos:
-    """Node positions: split (cell int32 [3][N] + off float32 [3][N]) or x64 [3][N]."""
+    """Node positions: split (cell int32 [3][N] + off float32 [3][N]) or x64 [3][N].
+    grad_unit: the length per which the adjoints return position derivatives
+    (0: per unit length, d/dx; the grid's h: per unit of the offset, d/d off)."""
 
     def __init__(self, cell: torch.Tensor = None, off: torch.Tensor = None,
-                 x64: torch.Tensor = None):
+                 x64: torch.Tensor = None, grad_unit: float = 0.0):
         self.cell, self.off, self.x64 = cell, off, x64
         self._s = _Pos(None if cell is None else cell.data_ptr(),
                        None if off is None else off.data_ptr(),
-                       None if x64 is None else x64.data_ptr())
+                       None if x64 is None else x64.data_ptr(), float(grad_unit))
 
 
 class Plan:
@@ -562,7 +565,7 @@ class Batch:
                 for j, v in enumerate(m.params):
                     a.mats[k].params[j] = float(v)
                 a.mats[k].Ta = float(getattr(m, "Ta", 0.0))
-            a.x = _Pos(_p(d.get("cell")), _p(d.get("off")), _p(d.get("x64")))
+            a.x = _Pos(_p(d.get("cell")), _p(d.get("off")), _p(d.get("x64")), 0.0)
             for name in ("u", "G", "f", "U", "gU", "gf", "gG", "gu", "gx"):
                 setattr(a, name, _p(d.get(name)))
         out = C.c_void_p()
@@ -641,10 +644,10 @@ class FEForce(torch.autograd.Function):
     def backward(ctx, gG):
         cell, off, params = ctx.saved_tensors
         plan = ctx.plan
-        x = Pos(cell=cell, off=off.detach())
+        x = Pos(cell=cell, off=off.detach(), grad_unit=plan.h)   # d/d off
         Hv, gp = ib_fe_force_adj(plan, _mats_from(ctx.models, params.detach()), x,
                                  gG.contiguous())
-        return None, None, None, Hv * plan.h, _param_grad(gp, ctx.models, params)
+        return None, None, None, Hv, _param_grad(gp, ctx.models, params)
 
 
 class Spread(torch.autograd.Function):
@@ -659,9 +662,9 @@ class Spread(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gf):
         cell, off, G = ctx.saved_tensors
-        x = Pos(cell=cell, off=off.detach())
+        x = Pos(cell=cell, off=off.detach(), grad_unit=ctx.plan.h)   # d/d off
         gG, gx = ib_spread_adj(ctx.plan, x, G.detach().contiguous(), gf.contiguous())
-        return None, None, gx * ctx.plan.h, gG
+        return None, None, gx, gG
 
 
 class Interp(torch.autograd.Function):
@@ -676,9 +679,9 @@ class Interp(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gU):
         cell, off, u = ctx.saved_tensors
-        x = Pos(cell=cell, off=off.detach())
+        x = Pos(cell=cell, off=off.detach(), grad_unit=ctx.plan.h)   # d/d off
         gu, gx = ib_interp_adj(ctx.plan, x, u.detach().contiguous(), gU.contiguous())
-        return None, None, gx * ctx.plan.h, gu
+        return None, None, gx, gu
 
 
 class Coupling(torch.autograd.Function):
@@ -698,11 +701,11 @@ class Coupling(torch.autograd.Function):
     def backward(ctx, gG, gf, gU):
         cell, off, params, u, G = ctx.saved_tensors
         plan = ctx.plan
-        x = Pos(cell=cell, off=off.detach())
+        x = Pos(cell=cell, off=off.detach(), grad_unit=plan.h)   # d/d off
         c = lambda t: None if t is None else t.contiguous()
         gx, gu, gp = ib_backward(plan, _mats_from(ctx.models, params.detach()), x,
                                  u.detach().contiguous(), G, c(gG), c(gf), c(gU))
-        return None, None, None, gx * plan.h, _param_grad(gp.cpu(), ctx.models, params), gu
+        return None, None, None, gx, _param_grad(gp.cpu(), ctx.models, params), gu
 
 
 class IBCoupling(torch.nn.Module):

@@ -542,6 +542,83 @@ def tet10_problem(base: Problem, seed: int = 77, bend: float = 0.1) -> Problem:
                                cell=np.ascontiguousarray(cell), off=np.ascontiguousarray(off))
 
 
+def grid_aligned_problem(seed: int = 6000, n: int = 32, dims=(8, 8, 8), start=(-3, 5, 12),
+                         u_modes: int = 4) -> Problem:
+    """Hexahedra of edge h whose nodes sit exactly on grid lines (split
+    offsets exactly 0), a seeded half of them moved by -2^-24 h along seeded
+    axes (cell - 1, offset 1 - 2^-24, the largest float32 below 1).  The block
+    spans cells start .. start + dims: by default it straddles the periodic
+    seam in x and tile faces (multiples of 8 cells) in y and z.  FP32 split.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = 1.0 / n
+    grid = Grid((n, n, n), h)
+    ijk = np.stack(np.meshgrid(*[np.arange(dims[d] + 1) + start[d] for d in range(3)],
+                               indexing="ij"), axis=-1)
+    conn, K = _structured_hex(ijk.astype(np.float64))
+    conn = _orient(conn, K)
+    X = K * h
+    move = (rng.uniform(size=K.shape) < 0.5)
+    x = X - move * (2.0 ** -24) * h
+    fib = np.zeros((6, conn.shape[1]))
+    fib[0] = 1.0
+    fib[4] = 1.0
+    mats = [Material(NEO_HOOKEAN, (0.5, 100.0))]
+    return _finish("aligned", grid, conn, X, fib, np.zeros(conn.shape[1]), mats, x, u_modes,
+                   rng)
+
+
+def dense_tile_problem(seed: int = 6100, n: int = 32, dims=(7, 7, 7), tile=(1, 1, 1),
+                       noise: float = 0.2, u_modes: int = 4) -> Problem:
+    """A block of dims hexahedra of edge h packed inside one 8^3-cell tile
+    (7^3 elements: 2,744 Gauss points in that tile), nodes perturbed by
+    +-noise h.  FP32 split."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = 1.0 / n
+    grid = Grid((n, n, n), h)
+    centre = [(8 * tile[d] + 4) * h for d in range(3)]
+    conn, X = box_block(*dims, edge=h, centre=centre)
+    X = X.astype(np.float32).astype(np.float64)
+    x = X + rng.uniform(-noise * h, noise * h, size=X.shape)
+    fib = np.zeros((6, conn.shape[1]))
+    fib[0] = 1.0
+    fib[4] = 1.0
+    mats = [Material(NEO_HOOKEAN, (0.5, 100.0))]
+    return _finish("densetile", grid, conn, X, fib, np.zeros(conn.shape[1]), mats, x, u_modes,
+                   rng)
+
+
+def incompressible_problem(seed: int = 6200, n: int = 32, blocks=(8, 8, 2), kappa: float = 1e4,
+                           model: int = NEO_HOOKEAN, stretch: float = 0.01, angle: float = 0.05,
+                           noise: float = 2e-5, fp64: bool = False) -> Problem:
+    """Nearly incompressible block: x = c + R D (X - c) + noise, D = diag(1 + s,
+    1 + s, (1 + s)^-2) (volume preserving), R a rotation by `angle` about a
+    seeded axis, node noise +-noise h; with kappa = 1e4 the bulk modulus
+    dwarfs the shear modulus (kappa / a = 2e4 for the neo-Hookean block) and
+    |J - 1| stays near 1e-4 while |F - I| is near 5e-2, so tr(F - I) cancels
+    in J - 1.  FP32 split unless fp64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = 1.0 / n
+    grid = Grid((n, n, n), h)
+    c = np.array([0.5, 0.5, 0.5])
+    conn, X = box_block(*blocks, edge=h, centre=c)
+    if not fp64:
+        X = X.astype(np.float32).astype(np.float64)
+    a = rng.normal(size=3)
+    a /= np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    R = np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
+    D = np.diag([1 + stretch, 1 + stretch, (1 + stretch) ** -2])
+    x = c[:, None] + (R @ D) @ (X - c[:, None]) + rng.uniform(-noise * h, noise * h, X.shape)
+    fib = np.zeros((6, conn.shape[1]))
+    fib[0] = 1.0
+    fib[4] = 1.0
+    params = (0.5, kappa) if model == NEO_HOOKEAN else HO_DEFAULT[:8] + (kappa,)
+    mats = [Material(model, params)]
+    return _finish("incompressible", grid, conn, X, fib, np.zeros(conn.shape[1]), mats, x, 4,
+                   rng, fp64)
+
+
 def batch_problems(seed: int = 5000, count: int = 48, sizes=(32, 64, 96, 128),
                    elems=(2000, 20000)) -> List[Problem]:
     """Independent HO shells on their own grids (parameter-sweep batch).
