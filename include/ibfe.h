@@ -280,7 +280,7 @@ ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
 
 /* Autotuner: times ib_forward on the given inputs for candidate tunings
  * (coordinate descent over the four entries in order: items of 1024 or 512
- * points; 2, 1 or 3 force CTAs per SM; spreading and interpolation caps 8, 3
+ * points; 2, 1, 3 or 4 force CTAs per SM; spreading and interpolation caps 8, 3
  * or 2; one warm-up and the median of three timed calls each) and keeps the
  * fastest.  Writes the choice to `tuning` (host, 4 entries) if non-NULL.
  * Allocates temporary output buffers and synchronises `stream`. */
@@ -403,10 +403,11 @@ ib_status ib_step(ib_plan* plan, ib_fluid* fluid, const ib_material* mats, int32
 
 /* Total elastic energy sum_{e,q} Psi(F_q) w_q j0 of an FP32 split-position
  * hexahedral mesh (IB_ERR_UNSUPPORTED for tetrahedra), without a plan and
- * without allocating anything, for callers that cannot call cudaMalloc: code running while a CUDA graph is captured on its
- * stream, runtimes that give all device memory to a fixed pool up front, or
- * loops that must not enter the allocator.  The paper has no counterpart of
- * this entry point; it is a service of this library.
+ * without allocating anything, for callers that cannot call cudaMalloc:
+ * runtimes that hand all device memory to their own pool up front (a
+ * cudaMalloc of theirs would fail or fragment it), and loops that must not
+ * enter the allocator, which may synchronise the device.  The paper has no
+ * counterpart of this entry point; it is a service of this library.
  *   mesh    as for ib_plan_create, X and fibres float; n_elems <= 262144,
  *           else IB_ERR_CAPACITY (nothing is launched).
  *   mats    host material table, n_mats <= IB_MAX_MATERIALS.

@@ -35,7 +35,7 @@ void free_plan(ib_plan* p) {
   void* ptrs[] = {p->inc_off, p->inc_idx, p->mass, p->inv_mass, p->wj0, p->elem_scratch,
                   p->elem_scratch2, p->keys[0], p->keys[1], p->vals[0], p->vals[1], p->hist,
                   p->tile_start, p->tile_end, p->tile_slot, p->tile_nonempty, p->tile_near,
-                  p->tile_list, p->tile_list_near, p->tile_vmax, p->tile_bcount, p->tile_counters,
+                  p->tile_list, p->tile_list_near, p->tile_vmax, p->tile_done, p->tile_sk, p->tile_bcount, p->tile_counters,
                   p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
                   p->p_off, p->p_val, p->p_idx, p->vol_jm1, p->gq_a, p->gq_b, p->epart, p->ered,
                   p->dstatus, p->node_tmp, p->pen_part};
@@ -207,7 +207,7 @@ ib_status to_nodes(ib_plan* p, const void* gq, void* elem, const void* scale, vo
 }
 
 ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true) {
-  Stage sc(p, IB_STAGE_SPREAD, s, spread_launches() - (zero_fill ? 0 : 1));
+  Stage sc(p, IB_STAGE_SPREAD, s, spread_launches(p->precision) - (zero_fill ? 0 : 1));
   return launch_spread(p, scale, f, s, zero_fill);
 }
 
@@ -360,6 +360,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->tile_list, 4 * (size_t)max_work_items(p->ntiles, Q)) &&
               dalloc(&p->tile_list_near, 4 * (size_t)p->ntiles) &&
               dalloc(&p->tile_vmax, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_done, 4 * (size_t)p->ntiles) &&
+              dalloc(&p->tile_sk, 16 * (size_t)p->ntiles) &&
               dalloc(&p->tile_bcount, 12 * (size_t)classify_blocks(p->ntiles)) &&
               dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
               dalloc(&p->rpart, 8 * kParamRow * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
@@ -745,12 +747,12 @@ ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
   };
   int32_t cur[4];
   ib_plan_get_tuning(p, cur);
-  const int32_t cand[4][3] = {{1024, 512, 0}, {2, 1, 3}, {8, 3, 2}, {8, 3, 2}};
+  const int32_t cand[4][4] = {{1024, 512, 0, 0}, {2, 1, 3, 4}, {8, 3, 2, 0}, {8, 3, 2, 0}};
   for (int k = 0; k < 4 && st == IB_OK; ++k) {
     int32_t best = cur[k];
     float best_ms = 0.f;
     bool first = true;
-    for (int j = 0; j < 3 && cand[k][j] && st == IB_OK; ++j) {
+    for (int j = 0; j < 4 && cand[k][j] && st == IB_OK; ++j) {
       int32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
       trial[k] = cand[k][j];
       ib_plan_set_tuning(p, trial);

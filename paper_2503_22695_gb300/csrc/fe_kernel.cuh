@@ -253,48 +253,139 @@ __global__ void __launch_bounds__(128) k_exact_jm1(FeArgs<float> A, float2* __re
   jx[t] = make_float2(r.hi, r.lo);
 }
 
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
-__device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e) {
-  using EL = El<kEl>;
-  const int E = A.E;
-  int node[EL::C];
+// Shape-function derivative dN_a/dxi_j of the trilinear hexahedron at Gauss
+// point q, for a q known only at run time (the lane-per-point kernel): the
+// compile-time table's three magnitudes, chosen by how many of the other two
+// axes' corner signs match the point's, and the corner's sign along j.  The
+// values are the same floats as Real(El<IB_ELEM_HEX8>::dxi(a, q, j)).
+template <typename Real, int a, int j>
+__device__ __forceinline__ Real hex_dxi(int q) {
+  constexpr Real kAA = Real(0.5 * (kA * kA)), kAB = Real(0.5 * (kA * kB)),
+                 kBB = Real(0.5 * (kB * kB));
+  constexpr int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
+  // corner a's sign bits (bit k set: + along axis k); q's bit k set: + along k
+  constexpr int sa = (corner_sign(a, 0) > 0) | (corner_sign(a, 1) > 0) << 1 |
+                     (corner_sign(a, 2) > 0) << 2;
+  const int diff = (sa ^ q) & ((1 << k1) | (1 << k2));  // the other two axes that differ
+  const Real m = diff == 0 ? kAA : (__popc(diff) == 1 ? kAB : kBB);
+  return corner_sign(a, j) > 0 ? m : -m;
+}
+
+// Butterfly reduce-scatter over the 8 lanes of an element (lane = Gauss
+// point g): on entry each lane holds its point's corner contributions
+// G[a][i], a = 0..7; on exit lane g holds the sum over the 8 points of
+// corner g's, summed in a fixed tree (lanes 4 apart, then 2, then 1).
+template <typename Real>
+__device__ __forceinline__ void reduce_scatter8(Real G[8][3], int g, Real out[3]) {
+  const unsigned full = 0xffffffffu;
+  Real h4[4][3];  // after the first level: the 4 corners with bit 2 = g's
 #pragma unroll
-  for (int a = 0; a < EL::C; ++a) node[a] = __ldg(A.conn + a * E + e);
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const bool hi = g & 4;
+      const Real keep = hi ? G[4 + k][i] : G[k][i], send = hi ? G[k][i] : G[4 + k][i];
+      h4[k][i] = keep + __shfl_xor_sync(full, send, 4);
+    }
+  Real h2[2][3];  // corners with bits 2, 1 = g's
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const bool hi = g & 2;
+      const Real keep = hi ? h4[2 + k][i] : h4[k][i], send = hi ? h4[k][i] : h4[2 + k][i];
+      h2[k][i] = keep + __shfl_xor_sync(full, send, 2);
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const bool hi = g & 1;
+    const Real keep = hi ? h2[1][i] : h2[0][i], send = hi ? h2[0][i] : h2[1][i];
+    out[i] = keep + __shfl_xor_sync(full, send, 1);
+  }
+}
+
+// Sum over the 8 lanes of an element, in a fixed tree (every lane gets it).
+template <typename T>
+__device__ __forceinline__ T sum8(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// One element's nodal forces (or their adjoint).  kLanes = false: one thread
+// per element, its force points unrolled with compile-time shape values.
+// kLanes = true (hexahedra): eight consecutive lanes per element, lane g
+// evaluating Gauss point g; the corner data are exchanged by shuffles, and
+// lane g writes corner g's force (valid = false: a lane of a padding element
+// takes part in the shuffles and stores nothing).
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl,
+          bool kLanes = false>
+__device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e,
+                                           bool valid = true) {
+  using EL = El<kEl>;
+  static_assert(!kLanes || kEl == IB_ELEM_HEX8, "eight lanes per element: hexahedra");
+  const int E = A.E;
   constexpr bool volx = (kLaws & kLawVolX) != 0;
   static_assert(!volx || (std::is_same<Real, float>::value && std::is_same<S, df>::value),
                 "the exact volumetric invariant is a split-precision option");
+  const int g = threadIdx.x & 7;  // kLanes: this lane's Gauss point and corner
 
-  // reference and current coordinates relative to corner 0
-  Real dX[EL::C][3], du[EL::C][3];
-  int c0[3];
-  Real o0[3];
-  A.pos.load(node[0], c0, o0);
-  Real X0[3];
+  // reference and current coordinates relative to corner 0 (kLanes: this
+  // lane's corner only; the others arrive by shuffles)
+  constexpr int kNodes = kLanes ? 1 : EL::C;
+  Real dX[kNodes][3], du[kNodes][3];
+  Real vv[kAdj ? kNodes : 1][3];
+  {
+    int node[kNodes];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + node[0]);
+    for (int a = 0; a < kNodes; ++a) node[a] = __ldg(A.conn + (kLanes ? g : a) * E + e);
+    int c0[3];
+    Real o0[3], X0[3];
+    if constexpr (kLanes) {
+      int c[3];
+      Real o[3];
+      A.pos.load(node[0], c, o);
+      const unsigned full = 0xffffffffu;
+      const int src = threadIdx.x & 24;  // lane 0 of this element's group
 #pragma unroll
-  for (int a = 0; a < EL::C; ++a) {
-    int c[3];
-    Real o[3];
-    if (a == 0) {
+      for (int d = 0; d < 3; ++d) {
+        c0[d] = __shfl_sync(full, c[d], src);
+        o0[d] = __shfl_sync(full, o[d], src);
+        const Real X = __ldg(A.X + d * A.N + node[0]);
+        X0[d] = __shfl_sync(full, X, src);
+        dX[0][d] = X - X0[d];
+        const Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
+        du[0][d] = dx - dX[0][d];
+      }
+    } else {
+      A.pos.load(node[0], c0, o0);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) { dX[0][d] = Real(0); du[0][d] = Real(0); }
-      continue;
+      for (int d = 0; d < 3; ++d) X0[d] = __ldg(A.X + d * A.N + node[0]);
+#pragma unroll
+      for (int a = 0; a < kNodes; ++a) {
+        int c[3];
+        Real o[3];
+        if (a == 0) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) { dX[0][d] = Real(0); du[0][d] = Real(0); }
+          continue;
+        }
+        A.pos.load(node[a], c, o);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          dX[a][d] = __ldg(A.X + d * A.N + node[a]) - X0[d];
+          Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
+          du[a][d] = dx - dX[a][d];
+        }
+      }
     }
-    A.pos.load(node[a], c, o);
+    if (kAdj) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      dX[a][d] = __ldg(A.X + d * A.N + node[a]) - X0[d];
-      Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
-      du[a][d] = dx - dX[a][d];
+      for (int a = 0; a < kNodes; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) vv[a][d] = __ldg(A.v + d * A.N + node[a]);
     }
-  }
-  Real vv[kAdj ? EL::C : 1][3];
-  if (kAdj) {
-#pragma unroll
-    for (int a = 0; a < EL::C; ++a)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) vv[a][d] = __ldg(A.v + d * A.N + node[a]);
   }
 
   const int mid = A.mat_id ? __ldg(A.mat_id + e) : 0;
@@ -333,34 +424,18 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real Ta = Real(prm[kTa]);
   const bool act = (kLaws & kLawAct) && (kParams || prm[kTa] != 0.0);
 
-  Real Ge[EL::C][3];
-#pragma unroll
-  for (int a = 0; a < EL::C; ++a)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
   double en = 0.0;
   Real gp[kParamRow];
 #pragma unroll
   for (int k = 0; k < kParamRow; ++k) gp[k] = Real(0);
   bool inverted = false;
 
-#pragma unroll
-  for (int q = 0; q < EL::QF; ++q) {
-    // J0 = sum_a dX_a (x) dN_a/dxi ;  Du = sum_a du_a (x) dN_a/dxi
-    Real J0[3][3], Du[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        Real s = Real(0), t = Real(0);
-#pragma unroll
-        for (int a = 1; a < EL::C; ++a) {
-          s += dX[a][i] * Real(EL::dxi(a, q, j));
-          t += du[a][i] * Real(EL::dxi(a, q, j));
-        }
-        J0[i][j] = s;
-        Du[i][j] = t;
-      }
+  // One force point q: from J0 = sum_a dX_a (x) dN_a/dxi, Du = sum_a du_a (x)
+  // dN_a/dxi and (adjoint) Dvv = sum_a v_a (x) dN_a/dxi, the stress (or its
+  // derivative) as Qm = P J0^-T w j0, whose product with dN_a/dxi is corner
+  // a's contribution; the energy and parameter sums accumulate in en, gp.
+  auto point = [&](int q, const Real (&J0)[3][3], const Real (&Du)[3][3],
+                   const Real (&Dvv)[3][3], Real (&Qm)[3][3]) {
     Real cJ[3][3];
     cofactor(J0, cJ);
     const Real j0 = J0[0][0] * cJ[0][0] + J0[0][1] * cJ[0][1] + J0[0][2] * cJ[0][2];
@@ -568,25 +643,13 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
             P[i][j] += c * f2.Fe[i] * es[j] + k8 * (Fef[i] * es[j] + Fes[i] * ef[j]);
       }
     } else {
-      // dF = Dvv J0^-1 with Dvv = sum_a v_a (x) dN_a/dxi
+      // dF = Dvv J0^-1
       Real dF[3][3];
-      {
-        Real Dvv[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            Real s = Real(0);
-#pragma unroll
-            for (int a = 0; a < EL::C; ++a) s += vv[a][i] * Real(EL::dxi(a, q, j));
-            Dvv[i][j] = s;
-          }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            dF[i][j] = Dvv[i][0] * Ji[0][j] + Dvv[i][1] * Ji[1][j] + Dvv[i][2] * Ji[2][j];
-      }
+        for (int j = 0; j < 3; ++j)
+          dF[i][j] = Dvv[i][0] * Ji[0][j] + Dvv[i][1] * Ji[1][j] + Dvv[i][2] * Ji[2][j];
       // delta = d ln J = F^-T : dF ; dI1 = 2 F : dF ; d F^-T = -F^-T dF^T F^-T
       Real dl = Real(0), dI1 = Real(0), DdF = Real(0);
 #pragma unroll
@@ -735,29 +798,132 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     }
 
     // corner forces: G_a -= (P J0^-T w j0) dN_a/dxi
-    Real Qm[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         Qm[i][k] = (P[i][0] * Ji[k][0] + P[i][1] * Ji[k][1] + P[i][2] * Ji[k][2]) * wj;
+  };
+
+  if constexpr (!kLanes) {
+    Real Ge[EL::C][3];
 #pragma unroll
     for (int a = 0; a < EL::C; ++a)
 #pragma unroll
+      for (int d = 0; d < 3; ++d) Ge[a][d] = Real(0);
+#pragma unroll
+    for (int q = 0; q < EL::QF; ++q) {
+      Real J0[3][3], Du[3][3], Dvv[3][3];
+#pragma unroll
       for (int i = 0; i < 3; ++i)
-        Ge[a][i] -= Qm[i][0] * Real(EL::dxi(a, q, 0)) + Qm[i][1] * Real(EL::dxi(a, q, 1)) +
-                    Qm[i][2] * Real(EL::dxi(a, q, 2));
-  }
-
-  if (inverted) set_status(A.status, kStatInverted);
 #pragma unroll
-  for (int a = 0; a < EL::C; ++a)
+        for (int j = 0; j < 3; ++j) {
+          Real s = Real(0), t = Real(0), w = Real(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) A.out[(a * 3 + i) * E + e] = Ge[a][i];
-  if (kEnergy) A.epart[e] = en;
-  if (kParams) {
+          for (int a = 1; a < EL::C; ++a) {
+            s += dX[a][i] * Real(EL::dxi(a, q, j));
+            t += du[a][i] * Real(EL::dxi(a, q, j));
+          }
+          if (kAdj) {
 #pragma unroll
-    for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+            for (int a = 0; a < EL::C; ++a) w += vv[a][i] * Real(EL::dxi(a, q, j));
+          }
+          J0[i][j] = s;
+          Du[i][j] = t;
+          Dvv[i][j] = w;
+        }
+      Real Qm[3][3];
+      point(q, J0, Du, Dvv, Qm);
+#pragma unroll
+      for (int a = 0; a < EL::C; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          Ge[a][i] -= Qm[i][0] * Real(EL::dxi(a, q, 0)) + Qm[i][1] * Real(EL::dxi(a, q, 1)) +
+                      Qm[i][2] * Real(EL::dxi(a, q, 2));
+    }
+    if (inverted) set_status(A.status, kStatInverted);
+#pragma unroll
+    for (int a = 0; a < EL::C; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) A.out[(a * 3 + i) * E + e] = Ge[a][i];
+    if (kEnergy) A.epart[e] = en;
+    if (kParams) {
+#pragma unroll
+      for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+    }
+  } else {
+    // the corners' data from their lanes, accumulated into this lane's point
+    const unsigned full = 0xffffffffu;
+    const int base = threadIdx.x & 24;
+    Real J0[3][3], Du[3][3], Dvv[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) J0[i][j] = Du[i][j] = Dvv[i][j] = Real(0);
+    auto gather = [&](auto a_) {
+      constexpr int a = decltype(a_)::value;
+      const Real dn[3] = {hex_dxi<Real, a, 0>(g), hex_dxi<Real, a, 1>(g),
+                          hex_dxi<Real, a, 2>(g)};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const Real xa = __shfl_sync(full, dX[0][i], base + a);
+        const Real ua = __shfl_sync(full, du[0][i], base + a);
+        const Real va = kAdj ? __shfl_sync(full, vv[0][i], base + a) : Real(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (a > 0) {
+            J0[i][j] += xa * dn[j];
+            Du[i][j] += ua * dn[j];
+          }
+          if (kAdj) Dvv[i][j] += va * dn[j];
+        }
+      }
+    };
+    gather(std::integral_constant<int, 0>{});
+    gather(std::integral_constant<int, 1>{});
+    gather(std::integral_constant<int, 2>{});
+    gather(std::integral_constant<int, 3>{});
+    gather(std::integral_constant<int, 4>{});
+    gather(std::integral_constant<int, 5>{});
+    gather(std::integral_constant<int, 6>{});
+    gather(std::integral_constant<int, 7>{});
+    Real Qm[3][3];
+    point(g, J0, Du, Dvv, Qm);
+    Real Gq[8][3];
+    auto corner = [&](auto a_) {
+      constexpr int a = decltype(a_)::value;
+      const Real d0 = hex_dxi<Real, a, 0>(g), d1 = hex_dxi<Real, a, 1>(g),
+                 d2 = hex_dxi<Real, a, 2>(g);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Gq[a][i] = -(Qm[i][0] * d0 + Qm[i][1] * d1 + Qm[i][2] * d2);
+    };
+    corner(std::integral_constant<int, 0>{});
+    corner(std::integral_constant<int, 1>{});
+    corner(std::integral_constant<int, 2>{});
+    corner(std::integral_constant<int, 3>{});
+    corner(std::integral_constant<int, 4>{});
+    corner(std::integral_constant<int, 5>{});
+    corner(std::integral_constant<int, 6>{});
+    corner(std::integral_constant<int, 7>{});
+    Real mine[3];
+    reduce_scatter8(Gq, g, mine);
+    if (kEnergy) en = sum8(en);
+    if (kParams) {
+#pragma unroll
+      for (int k = 0; k < kParamRow; ++k) gp[k] = sum8(gp[k]);
+    }
+    if (valid) {
+      if (inverted) set_status(A.status, kStatInverted);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) A.out[(g * 3 + i) * E + e] = mine[i];
+      if (g == 0) {
+        if (kEnergy) A.epart[e] = en;
+        if (kParams) {
+#pragma unroll
+          for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+        }
+      }
+    }
   }
 }
 
@@ -778,6 +944,30 @@ __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
     if (b >= A.E) break;
     if (b + (int)threadIdx.x < A.E)
       fe_element<Real, S, kEnergy, kAdj, kParams, kLaws, kEl>(A, mt, b + (int)threadIdx.x);
+  }
+}
+
+// Hexahedra: eight lanes per element (lane g: Gauss point g), sixteen
+// elements per 128-thread CTA, blocks of elements taken from a counter.
+template <typename Real, bool kAdj>
+constexpr int fe8_min_blocks() {
+  return sizeof(Real) == 8 ? 2 : 4;
+}
+
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+__global__ void __launch_bounds__(128, fe8_min_blocks<Real, kAdj>())
+    k_fe8(FeArgs<Real> A, MatTable mt) {
+  constexpr int kPer = 128 / 8;
+  __shared__ int base;
+  for (;;) {
+    if (threadIdx.x == 0) base = atomicAdd(A.next, 1) * kPer;
+    __syncthreads();
+    const int b = base;
+    __syncthreads();
+    if (b >= A.E) break;
+    const int e = b + (int)(threadIdx.x >> 3);
+    fe_element<Real, S, kEnergy, kAdj, kParams, kLaws, IB_ELEM_HEX8, true>(
+        A, mt, e < A.E ? e : A.E - 1, e < A.E);
   }
 }
 
@@ -842,16 +1032,23 @@ ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* of
   if (p->E == 0) return IB_OK;
   FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
   const int threads = 128;
+  // elements per CTA step: one per thread, or one per eight lanes (hexahedra)
+  constexpr bool lanes = kEl == IB_ELEM_HEX8;
+  const int per_cta = lanes ? threads / 8 : threads;
   // the forward runs beside the sort and interpolation; the adjoint runs alone
-  const int per_sm = kAdj ? fe_min_blocks<Real, kAdj>() : p->fe_ctas;
-  const int blocks = std::min((p->E + threads - 1) / threads, p->sm_count * per_sm);
+  const int per_sm = kAdj ? (lanes ? fe8_min_blocks<Real, kAdj>() : fe_min_blocks<Real, kAdj>())
+                          : p->fe_ctas;
+  const int blocks = std::min((p->E + per_cta - 1) / per_cta, p->sm_count * per_sm);
   if (cudaMemsetAsync(A.next, 0, sizeof(int), s) != cudaSuccess) return IB_ERR_CUDA;
   if constexpr ((kLaws & kLawVolX) != 0) {
     if (!p->vol_jm1) return IB_ERR_INVALID_ARG;
     const int64_t n = (int64_t)El<kEl>::QF * p->E;
     k_exact_jm1<kEl><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, (float2*)p->vol_jm1);
   }
-  k_fe<Real, S, kEnergy, kAdj, kParams, kLaws, kEl><<<blocks, threads, 0, s>>>(A, mt);
+  if constexpr (lanes)
+    k_fe8<Real, S, kEnergy, kAdj, kParams, kLaws><<<blocks, threads, 0, s>>>(A, mt);
+  else
+    k_fe<Real, S, kEnergy, kAdj, kParams, kLaws, kEl><<<blocks, threads, 0, s>>>(A, mt);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -140,6 +140,8 @@ struct ib_plan {
   int32_t* tile_list;    // [max work items] tile of each work item
   int32_t* tile_list_near;// [ntiles] near tiles, ascending
   uint32_t* tile_vmax;   // [ntiles] FP32: bits of the largest |carried value| of each tile
+  int32_t* tile_done;    // [ntiles] work items of the tile written (FP32 spreading, per call)
+  int32_t* tile_sk;      // [4 ntiles] FP32: first block slot, exponent, 0, work items
   int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
   int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
                          //     [6] FE force block counter
@@ -233,7 +235,7 @@ ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool 
 ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s);
 ib_status spread_prepare(ib_plan* p);
 size_t spread_scratch_bytes(int precision, int64_t slots);
-int spread_launches();
+int spread_launches(int precision);
 
 // interp.cu
 // mode 0: out_a[gq] = w j0 * sum u prod phi (U^IB times w j0)

@@ -64,6 +64,8 @@ struct SpreadArgs {
   Real* scratch;               // [items][3][12^3]
   Real* f;
   const uint32_t* tile_vmax;   // FP32: bits of max |value| over each tile's points
+  int32_t* tile_done;          // FP32: work items of each tile written in this call
+  int4* tile_sk;               // FP32: (first block slot or -1, exponent k + 11, 0, items)
 };
 
 // cp.async of 4 bytes global -> shared (completion awaited with cp_async_wait)
@@ -85,8 +87,11 @@ struct alignas(16) Staged {
   int org;
 };
 
+// Tile index of tile coordinates within one tile of the grid's range
+// ([-1, nt]): the periodic wrap is one compare per axis, no division.
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 __device__ __forceinline__ int tile_of(int tx, int ty, int tz, const GridDev& g) {
-  return wrap_idx(tx, g.nt[0]) + g.nt[0] * (wrap_idx(ty, g.nt[1]) + g.nt[1] * wrap_idx(tz, g.nt[2]));
+  return wrap1(tx, g.nt[0]) + g.nt[0] * (wrap1(ty, g.nt[1]) + g.nt[1] * wrap1(tz, g.nt[2]));
 }
 
 // One lane adds into one face per step and steps are ordered by __syncwarp,
@@ -261,11 +266,12 @@ __global__ void __launch_bounds__(kPT) k_spread_push(SpreadArgs<Real> A) {
 // Exponent of a tile (fx_tile_exp): from the largest |V| over the tile's
 // points (an integer maximum of float bit patterns, itself order-independent)
 // and its point count n_t.  Every kernel weight product is at most 1/8, so
-// with cm = max|V| |scale| / 8 < 2^e, n_eff = min(n_t, the largest work
-// item, 1024) <= 2^L and k = min(21, 30 - L) - e, each contribution is below
-// 2^21 and |H| below 2^31 at every face of an item.  The resolution 2^-(k+11)
-// is about 2^-31 of the tile's largest contribution times n_eff / 1024; tiles
-// far from large values keep their own fine resolution.
+// with cm = max|V| |scale| / 8 < 2^e, n_eff = min(n_t, 1024) <= 2^L (1024:
+// the largest work item any tuning may choose) and k = min(21, 30 - L) - e,
+// each contribution is below 2^21 and |H| below 2^31 at every face of an
+// item.  The resolution 2^-(k+11) is about 2^-31 of the tile's largest
+// contribution times n_eff / 1024; tiles far from large values keep their
+// own fine resolution.
 //
 // Merge (k_spread_merge_fx): each face sums the items' S of every source tile
 // in 64-bit integers, aligns the source sums to one exponent per destination
@@ -412,13 +418,36 @@ __device__ __forceinline__ void fx_stage(float4* rec, int part, bool store, cons
                   2 * kFxAcc + b[2][0] * kFxSZ + b[1][1] * kFxSY + b[0][1], 0);
 }
 
+// Merge of the near tiles (FP32 plans): every face adds the S of the covering
+// source tiles (each tile's blocks summed into its first block by the
+// accumulation kernel) in the fixed order (oz, oy, ox), aligned to the
+// destination tile's exponent k_ref (in units of 2^-(k+11)), and is rounded
+// once.  With k'_s = k_s + 11 for source s,
+//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
+// so a source sum (below items_s 2^42) shifted left by k_ref - k'_s stays
+// below 2^59 and eight of them below 2^62; a source with k'_s > k_ref is
+// shifted right (floor).  The conversion splits |S| into two 32-bit halves,
+// each converted exactly rounded, joined by one fma: within one unit in the
+// last place, the same bits for the same integers.
+__device__ __forceinline__ float fx_to_float(long long S, float out_scale) {
+  const unsigned long long m = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const float f = fmaf((float)(unsigned)(m >> 32), 4294967296.0f, (float)(unsigned)m);
+  return (S < 0 ? -f : f) * out_scale;
+}
+
+// v 2^sh, floor for sh < 0 (left shifts never exceed the headroom above; a
+// right shift of 63 or more leaves the sign: floor of |v| < 2^63 over 2^63)
+__device__ __forceinline__ long long fx_align(long long v, int sh) {
+  return sh >= 0 ? (long long)((unsigned long long)v << sh) : (v >> min(-sh, 63));
+}
+
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* groups = reinterpret_cast<float4*>(smem_raw);
   unsigned* acc_hi = reinterpret_cast<unsigned*>(smem_raw + sizeof(float4) * kFxWarps * kFxGroup *
                                                                 kFxRec);
   unsigned* acc_lo = acc_hi + kFxWords;
-  __shared__ int next;
+  __shared__ int next, last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = A.counters[0];
   const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
@@ -441,8 +470,8 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int s = t0 + (slot - A.tile_slot[tile]) * A.chunk;
     const int e = min(t1, s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
-    const float vscale =
-        A.scale * ldexpf(1.f, fx_tile_exp(A.tile_vmax[tile], t1 - t0, A.scale));
+    const int4 tsk = A.tile_sk[tile];
+    const float vscale = A.scale * ldexpf(1.f, tsk.y - 11);
     // warp w takes the groups starting at s + kFxGroup (w + 8 j)
     FxRaw raw = {0, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int g0 = s + warp * kFxGroup;
@@ -495,6 +524,113 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
       const int H0 = (int)(hw.x - lw.x) + L0, H1 = (int)(hw.y - lw.y) + L1;
       out[u] = make_longlong2((long long)H0 * 2048 + L0, (long long)H1 * 2048 + L1);
     }
+    // Tiles cut into several work items: the item whose block completes the
+    // tile's count adds all of the tile's item blocks, in item order and in
+    // exact 64-bit integers, into the tile's first block, while they are
+    // fresh in L2; the merge then reads one block per tile.  Every thread
+    // fences its own block stores before the barrier that precedes the count;
+    // the summing CTA fences after reading it.
+    const int nit = A.tile_nitems[tile];
+    if (nit > 1) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) last = atomicAdd(A.tile_done + tile, 1) + 1 == nit;
+      __syncthreads();
+      if (last) {
+        __threadfence();
+        longlong2* first = reinterpret_cast<longlong2*>(A.scratch) +
+                           (int64_t)A.tile_slot[tile] * (kFxBlk / 2);
+        for (int u = tid; u < kFxBlk / 2; u += kFxThreads) {
+          long long a0 = 0, a1 = 0;
+          for (int j = 0; j < nit; ++j) {
+            const longlong2 v = __ldcg(first + (int64_t)j * (kFxBlk / 2) + u);
+            a0 += v.x;
+            a1 += v.y;
+          }
+          first[u] = make_longlong2(a0, a1);
+        }
+      }
+    }
+  }
+}
+
+// Per tile (FP32 plans), one thread each: the exponent k of its fixed-point
+// words, its first block slot and its work items, read by every push item of
+// the tile and by the merge of each of its 27 neighbours.
+__global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const int ns = A.tile_nitems[t];
+  const int npts = A.tile_end[t] - A.tile_start[t];
+  A.tile_sk[t] = make_int4(ns > 0 ? A.tile_slot[t] : -1,
+                           ns > 0 ? fx_tile_exp(__ldg(A.tile_vmax + t), npts, A.scale) + 11 : 0,
+                           0, ns);
+}
+
+// One CTA per (near tile, component), one thread per face pair, no barrier:
+// lanes 0..26 of each warp load the records of the 27 tiles whose blocks
+// cover the tile, the warp reduces the merge exponent
+//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
+// and each thread takes its up to eight sources' records by shuffle, then
+// loads their blocks together.
+__global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
+  static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
+  const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
+  const int n0 = A.g.n[0], n1 = A.g.n[1];
+  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
+  const int count = 3 * A.counters[3];
+  const longlong2* scratch = reinterpret_cast<const longlong2*>(A.scratch);  // 2 faces each
+  // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y)
+  const int z = tid >> 5, y = (tid >> 2) & 7, xq = tid & 3;
+  // covering sources along each axis: the tile itself, and the lower (upper)
+  // neighbour for the faces 0, 1 (6, 7)
+  const int lz = z <= 1 ? -1 : 0, ly = y <= 1 ? -1 : 0, lx = xq == 0 ? -1 : 0;
+  const int nz = (z <= 1 || z >= 6) ? 2 : 1, ny = (y <= 1 || y >= 6) ? 2 : 1,
+            nx = (xq == 0 || xq == 3) ? 2 : 1;
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const int tile = A.tile_list_near[k / 3], c = k % 3;
+    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    int4 r = make_int4(-1, 0, 0, 0);
+    if (lane < 27)
+      r = __ldg(A.tile_sk + tile_of(tx + lane % 3 - 1, ty + (lane / 3) % 3 - 1,
+                                    tz + lane / 9 - 1, A.g));
+    const int kmax = __reduce_max_sync(full, r.w > 0 ? r.y : -1000);
+    const int kcap = __reduce_min_sync(full, r.w > 0 ? r.y + 17 - ceil_log2(r.w) : 1000);
+    const int kref = min(kmax, kcap);
+    int2 sk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int iz = i >> 2, iy = (i >> 1) & 1, ix = i & 1;
+      const bool use = iz < nz && iy < ny && ix < nx;
+      const int src = (lz + iz + 1) * 9 + (ly + iy + 1) * 3 + lx + ix + 1;
+      const int slot = __shfl_sync(full, r.x, use ? src : 0);
+      const int kx = __shfl_sync(full, r.y, use ? src : 0);
+      sk[i] = make_int2(use ? slot : -1, kx);
+    }
+    longlong2 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int oz = lz + (i >> 2), oy = ly + ((i >> 1) & 1), ox = lx + (i & 1);
+      v[i] = make_longlong2(0, 0);
+      if (sk[i].x >= 0) {
+        // this face pair in the source tile's halo'd block (face-pair units)
+        const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
+                      (kTile / 2) * ox;
+        v[i] = __ldcg(scratch + (int64_t)sk[i].x * (kFxBlk / 2) + c * (kBlk / 2) + q);
+      }
+    }
+    long long t0 = 0, t1 = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      t0 += fx_align(v[i].x, kref - sk[i].y);
+      t1 += fx_align(v[i].y, kref - sk[i].y);
+    }
+    const float osc = ldexpf(1.f, -kref);
+    float* row = A.f + c * cells + ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 +
+                 tx * kTile;
+    reinterpret_cast<float2*>(row)[xq] = make_float2(fx_to_float(t0, osc), fx_to_float(t1, osc));
   }
 }
 
@@ -585,110 +721,6 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   }
 }
 
-// FP32 plans: the same fixed-order walk over the covering blocks, summing
-// every face's S per source tile in 64-bit integers; the source sums are
-// aligned to the destination tile's exponent k_ref (in units of 2^-(k+11)) and
-// added, and the total is rounded once.  With k'_s = k_s + 11 for source s,
-//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
-// so a source sum (below items_s 2^42) shifted left by k_ref - k'_s stays
-// below 2^59 and eight of them below 2^62; a source with k'_s > k_ref is
-// shifted right (floor).  The conversion splits |S| into two 32-bit halves,
-// each converted exactly rounded, joined by one fma: within one unit in the
-// last place, the same bits for the same integers.
-__device__ __forceinline__ float fx_to_float(long long S, float out_scale) {
-  const unsigned long long m = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
-  const float f = fmaf((float)(unsigned)(m >> 32), 4294967296.0f, (float)(unsigned)m);
-  return (S < 0 ? -f : f) * out_scale;
-}
-
-__device__ __forceinline__ long long fx_align(long long v, int sh) {
-  return sh >= 0 ? (long long)((unsigned long long)v << sh) : (v >> -sh);
-}
-
-__global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
-  static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
-  __shared__ int src_slot[27], src_n[27], src_sh[27];
-  __shared__ float out_scale;
-  const int tid = threadIdx.x;
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int n0 = A.g.n[0], n1 = A.g.n[1];
-  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
-  const int count = A.counters[3];
-  const longlong2* scratch = reinterpret_cast<const longlong2*>(A.scratch);  // 2 faces each
-  // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y), all three components
-  const int z = tid >> 5, y = (tid >> 2) & 7, xq = tid & 3;
-  const int ly = y <= 1 ? -1 : 0, lz = z <= 1 ? -1 : 0;
-  const int hy = y >= 6 ? 1 : 0, hz = z >= 6 ? 1 : 0;
-  // x neighbours: the left tile's block reaches faces 0, 1, the right one's 6, 7
-  const int lx = xq == 0 ? -1 : 0, hx = xq == 3 ? 1 : 0;
-  for (int k = blockIdx.x; k < count; k += gridDim.x) {
-    const int tile = A.tile_list_near[k];
-    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-    const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
-    __syncthreads();
-    if (tid < 32) {
-      int slot = 0, ns = 0, ke = 0, kmax = -1000, kcap = 1000;
-      if (tid < 27) {
-        const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
-        const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
-        slot = A.tile_slot[nb];
-        ns = A.tile_nitems[nb];
-        if (ns > 0) {
-          ke = fx_tile_exp(A.tile_vmax[nb], A.tile_end[nb] - A.tile_start[nb], A.scale) + 11;
-          kmax = ke;
-          kcap = ke + 17 - ceil_log2(ns);
-        }
-      }
-      kmax = __reduce_max_sync(0xffffffffu, kmax);
-      kcap = __reduce_min_sync(0xffffffffu, kcap);
-      const int kref = min(kmax, kcap);
-      if (tid < 27) {
-        src_slot[tid] = slot;
-        src_n[tid] = ns;
-        src_sh[tid] = kref - ke;
-      }
-      if (tid == 0) out_scale = ldexpf(1.f, -kref);
-    }
-    __syncthreads();
-    long long tot[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int oz = lz; oz <= hz; ++oz)
-      for (int oy = ly; oy <= hy; ++oy)
-        for (int ox = lx; ox <= hx; ++ox) {
-          const int src = (oz + 1) * 9 + (oy + 1) * 3 + ox + 1;
-          const int ns = src_n[src];
-          if (ns == 0) continue;
-          // this face pair in the source tile's halo'd block (face-pair units)
-          const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
-                        (kTile / 2) * ox;
-          const longlong2* r = scratch + (int64_t)src_slot[src] * (kFxBlk / 2) + q;
-          long long sh[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-          for (int j = 0; j < ns; ++j, r += kFxBlk / 2) {
-            longlong2 v[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[c] = __ldg(r + c * (kBlk / 2));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              sh[c][0] += v[c].x;
-              sh[c][1] += v[c].y;
-            }
-          }
-          const int s = src_sh[src];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            tot[c][0] += fx_align(sh[c][0], s);
-            tot[c][1] += fx_align(sh[c][1], s);
-          }
-        }
-    const float osc = out_scale;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float* row = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
-      reinterpret_cast<float2*>(row)[xq] =
-          make_float2(fx_to_float(tot[c][0], osc), fx_to_float(tot[c][1], osc));
-    }
-  }
-}
-
 template <typename Real>
 size_t push_smem() {
   return sizeof(Staged<Real>) * kBatch + sizeof(Real) * kCopies * kAcc + sizeof(RawItem<Real>);
@@ -698,6 +730,8 @@ constexpr size_t kFxSmem =
     sizeof(float4) * kFxWarps * kFxGroup * kFxRec + sizeof(unsigned) * 2 * kFxWords;
 
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
+  cudaMemsetAsync(p->tile_done, 0, sizeof(int32_t) * p->ntiles, s);
+  k_tile_info<<<(p->ntiles + 255) / 256, 256, 0, s>>>(A, p->ntiles);
   p->prof_calls[IB_STAGE_SPREAD_PUSH] += 1;
   const int ev = prof_begin(p, IB_STAGE_SPREAD_PUSH, s);
   k_spread_push_fx<<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads, kFxSmem,
@@ -731,6 +765,8 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f) {
   A.scratch = (Real*)p->spread_scratch;
   A.f = (Real*)f;
   A.tile_vmax = p->tile_vmax;
+  A.tile_done = p->tile_done;
+  A.tile_sk = reinterpret_cast<int4*>(p->tile_sk);
   return A;
 }
 
@@ -801,7 +837,8 @@ ib_status spread_prepare(ib_plan* p) {
   return p->precision == IB_FP64 ? prepare_t<double>(p) : prepare_t<float>(p);
 }
 
-int spread_launches() { return 3; }
+// zeros, accumulation, merge (FP32: and the merge exponents)
+int spread_launches(int precision) { return precision == IB_FP64 ? 3 : 4; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill) {
   return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s)

@@ -427,7 +427,7 @@ def test_tuning_is_validated_and_changes_no_result():
                     assert np.array_equal(a, b)
         chosen = ibfe.ib_plan_autotune(c.plan, c.mats, c.pos, c.u)
         assert chosen == ibfe.ib_plan_get_tuning(c.plan)
-        assert chosen[0] in (1024, 512) and chosen[1] in (1, 2, 3)
+        assert chosen[0] in (1024, 512) and chosen[1] in (1, 2, 3, 4)
         assert chosen[2] in (8, 3, 2) and chosen[3] in (8, 3, 2)
         out = [np_(v) for v in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
         for a, b in zip(out, ref):

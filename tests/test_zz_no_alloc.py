@@ -1,8 +1,10 @@
 """The plan-free energy entry point, for callers that cannot allocate device
-memory (graph capture in progress, fixed memory pools, allocation-free
-loops).  It is called through the C ABI and must agree with the energy of
-the plan-based ib_fe_force within the energy tolerance of the parity tests,
-on two calls in a row (its scratch array is shared between calls).
+memory (runtimes that own all device memory through their own pool, loops
+that must not enter the allocator).  It is called through the C ABI and must
+agree with the energy of the plan-based ib_fe_force, and with the FP64
+oracle's energy for every material law with and without active tension,
+within the energy tolerance of the parity tests, on two calls in a row (its
+scratch array is shared between calls).
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -11,6 +13,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from paper_2503_22695_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +48,35 @@ def test_noalloc_energy_matches_plan_energy(make):
         assert rc == ibfe.IB_OK
         got = float(out.item())
         assert got == pytest.approx(want, rel=ENERGY_RTOL)
+
+
+LAWS = [
+    (I.NEO_HOOKEAN, (0.5, 100.0)),
+    (I.FIBRE1, I.FIBRE1_LEAFLET),
+    (I.HO, I.HO_DEFAULT),
+    (I.STD_REINF, I.STD_REINF_COOK),
+    (I.FIBRE2, I.FIBRE2_AV),
+]
+
+
+@pytest.mark.parametrize("Ta", [0.0, 5.0])
+@pytest.mark.parametrize("model,params", LAWS)
+def test_noalloc_energy_matches_oracle_for_every_law(model, params, Ta):
+    import torch
+    from paper_2503_22695_gb300 import ibfe
+    p = I.block_problem(seed=1050, fp64=False)
+    p.materials = [I.Material(model, params, Ta)]
+    dev = "cuda"
+    conn = torch.from_numpy(p.conn).to(dev)
+    X = torch.from_numpy(p.X).to(dev)
+    fib = torch.from_numpy(p.fibres).to(dev)
+    pos = ibfe.Pos(cell=torch.from_numpy(p.cell).to(dev), off=torch.from_numpy(p.off).to(dev))
+    mats = [ibfe.Material(model, params, Ta)]
+    _, want = oracle.Model(p).fe_force(I.from_split(p.cell, p.off, p.grid))
+    for _ in range(2):
+        out = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+        ibfe.ib_fe_energy_noalloc(conn, X, mats, pos, p.grid.h, out, fibres=fib)
+        assert float(out.item()) == pytest.approx(want, rel=ENERGY_RTOL)
 
 
 def test_noalloc_rejects_oversized_mesh():
