@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IB force+spread+interp Gauss-pts/s, % HBM roofline; adjoint/forward time ratio"
 # The kernels of the spreading step as ib_spread runs them alone.
-SPREAD_KERNELS = ("k_spread_zero<float>", "k_spread_push_fx", "k_spread_merge_fx")
+SPREAD_KERNELS = ("k_spread_zero<float>", "k_tile_info", "k_spread_push_fx", "k_spread_merge_fx")
 # FE force: FP32 operations per Gauss point (fadd + fmul + 2 ffma, counted by
 # ncu for k_fe<float, df, ..., law set NH/Psi_2/Psi_4> on this workload);
 # FP32 peak = 152 SMs x 128 lanes x 2 (fma) x the SM clock.
@@ -652,14 +652,41 @@ def run_ours(args):
         ms_ba = timed(batch.adjoint, args.steps)
         qb = sum(bp.n_gauss for bp in bprobs)
         tbf, tba = sum(ms_bf) / len(ms_bf), sum(ms_ba) / len(ms_ba)
+        # the plain FP64 GPU form of the same instances: one FP64 plan each,
+        # positions and data widened exactly, ib_forward called in turn
+        f64 = []
+        for bp, d in zip(bprobs, binst):
+            g = bp.grid
+            x64 = torch.from_numpy(I.from_split(bp.cell, bp.off, g)).to(dev)
+            p64 = ibfe.Plan(d["conn"], d["X"].double(), g.n, g.h, g.origin,
+                            fibres=d["fibres"].double(), mat_id=d["mat_id"],
+                            precision=ibfe.IB_FP64)
+            N_i, sh = bp.n_nodes, (3,) + tuple(bp.u.shape[1:])
+            f64.append((p64, d["mats"], ibfe.Pos(x64=x64), d["u"].double(),
+                        torch.empty((3, N_i), device=dev, dtype=torch.float64),
+                        torch.empty(sh, device=dev, dtype=torch.float64),
+                        torch.empty((3, N_i), device=dev, dtype=torch.float64)))
+
+        def fwd64():
+            for (p64, m64, x64, u64, G64, f64_, U64) in f64:
+                ibfe.ib_forward(p64, m64, x64, u64, G64, f64_, U64)
+        for _ in range(args.warmup):
+            fwd64()
+        ms_64 = timed(fwd64, args.steps)
+        t64 = sum(ms_64) / len(ms_64)
         batch_line = {
             "workload": f"{len(bprobs)} HO ventricle-like shells, grids 32^3..128^3, "
                         f"{min(bp.n_elems for bp in bprobs)}..{max(bp.n_elems for bp in bprobs)} "
-                        f"hexes each, {qb} Gauss points; one CUDA-graph launch per pass",
+                        f"hexes each, {qb} Gauss points; one packed plan (one launch per "
+                        f"stage over all instances), one CUDA-graph launch per pass",
             "gauss_points": qb, "forward_ms": tbf, "adjoint_ms": tba,
             "forward_value": qb / (tbf * 1e-3), "unit": UNIT,
-            "adjoint_forward_ratio": tba / tbf}
-        del batch, binst
+            "adjoint_forward_ratio": tba / tbf, "tuning": batch.tuning(),
+            "fp64_gpu_form": {"forward_ms": t64, "forward_value": qb / (t64 * 1e-3),
+                              "note": "one FP64 plan per instance, ib_forward in turn; "
+                                      "accuracy of both forms against the oracle in "
+                                      "tests/test_gpu_batch.py"}}
+        del batch, binst, f64
         barrier()
 
     # --- max over ranks ----------------------------------------------------

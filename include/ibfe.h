@@ -304,16 +304,33 @@ ib_status ib_plan_set_penalty(ib_plan* plan, const int32_t* nodes, int32_t n,
                               const void* weights, double kappa);
 
 /* ---------------------------------------------------------------------------
- * Batched form: many independent structures, each with its own mesh, grid
- * and material table (a parameter sweep, for instance), run together.  The
- * paper runs one structure at a time; batching is a service of this library.
- * ib_batch_create builds one plan per instance and captures two CUDA graphs
- * whose branches are the instances' forward coupling (ib_forward) and
- * backward (ib_backward, parameter gradients kept on the device); each graph
- * is then replayed with one launch.  Each instance's plan is autotuned
- * (ib_plan_autotune on its own inputs) before the capture.  All pointers in ib_instance are device memory that must stay
- * valid and fixed for the batch's lifetime (the graphs bake them in); update
- * the data in place between replays.  Synchronises `stream` at creation.
+ * Batched form: many independent structures, each with its own hexahedral
+ * mesh, periodic grid and material table (a parameter sweep, for instance),
+ * run together.  The paper runs one structure at a time; batching is a
+ * service of this library.
+ *
+ * ib_batch_create packs the instances into one plan: their meshes laid end
+ * to end, their grids' tiles numbered consecutively, with device tables that
+ * give every tile and element its instance.  Each stage of the coupling is
+ * then one launch over all instances (one force kernel over all elements,
+ * one persistent spreading kernel whose work counter spans every instance's
+ * tiles, one merge, one persistent interpolation), with each instance's
+ * fields and h-dependent scales read from per-instance tables.  The forward
+ * (the sequence of ib_forward) and the backward (that of ib_backward, with
+ * the parameter gradients kept on the device) are each captured once in a
+ * CUDA graph and replayed with one launch.  The packed plan's tuning is
+ * chosen by the autotuner of ib_plan_autotune, timed on the batch's own
+ * forward.  Every instance's results equal, bit for bit, those of
+ * ib_forward / ib_backward on a plan of that instance alone.
+ *
+ * Instances: IB_ELEM_HEX8 meshes with n_elems > 0, the Gauss rule, FP32
+ * split positions (precision must be IB_FP32_SPLIT), 1..IB_MAX_MATERIALS
+ * materials each, one common x.grad_unit, f, u (and gf, gu) 16-byte
+ * aligned; penalty tethers are not available.  Violations give
+ * IB_ERR_INVALID_ARG (grids as ib_plan_create: IB_ERR_UNSUPPORTED).  All
+ * pointers in ib_instance are device memory that must stay valid and fixed
+ * for the batch's lifetime (the graphs bake them in); update the data in
+ * place between replays.  Synchronises `stream` at creation.
  * ------------------------------------------------------------------------- */
 typedef struct {
   ib_mesh mesh;
@@ -343,6 +360,8 @@ ib_status ib_batch_adjoint(ib_batch* batch, void* stream);
  * backward replay, host double [n][IB_MAX_MATERIALS][IB_PARAM_ROW] (entries past an
  * instance's n_mats are zero); synchronises `stream`. */
 ib_status ib_batch_gparams(ib_batch* batch, double* gparams, void* stream);
+/* The packed plan's tuning (as ib_plan_get_tuning). */
+ib_status ib_batch_get_tuning(const ib_batch* batch, int32_t tuning[4]);
 ib_status ib_batch_destroy(ib_batch* batch);
 
 /* ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "ib_internal.cuh"
@@ -38,7 +39,8 @@ void free_plan(ib_plan* p) {
                   p->tile_list, p->tile_list_near, p->tile_vmax, p->tile_done, p->tile_sk, p->tile_bcount, p->tile_counters,
                   p->digit_tot, p->rpart, p->spread_scratch, p->q_cell, p->q_off, p->q_val, p->p_cell,
                   p->p_off, p->p_val, p->p_idx, p->vol_jm1, p->gq_a, p->gq_b, p->epart, p->ered,
-                  p->dstatus, p->node_tmp, p->pen_part};
+                  p->dstatus, p->node_tmp, p->pen_part, p->mat_range, p->inst, p->tile_inst,
+                  p->elem_inst, p->mat_dev};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
@@ -176,9 +178,10 @@ ib_status do_points_sorted(ib_plan* p, const ib_pos* x, const void* nodal, cudaS
   return launch_sort_points(p, nodal != nullptr, s);
 }
 
-ib_status do_interp(ib_plan* p, const void* u, int mode, double vs, double gs, cudaStream_t s) {
+ib_status do_interp(ib_plan* p, const void* u, int mode, double vs, double gs, cudaStream_t s,
+                    const GridCall* calls = nullptr, const void* tmaps = nullptr) {
   Stage sc(p, IB_STAGE_INTERP, s, 1);
-  return launch_interp_points(p, u, mode, vs, gs, s);
+  return launch_interp_points(p, u, mode, vs, gs, s, calls, tmaps);
 }
 
 ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
@@ -206,9 +209,10 @@ ib_status to_nodes(ib_plan* p, const void* gq, void* elem, const void* scale, vo
   return st;
 }
 
-ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true) {
+ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true,
+                    const GridCall* calls = nullptr) {
   Stage sc(p, IB_STAGE_SPREAD, s, spread_launches(p->precision) - (zero_fill ? 0 : 1));
-  return launch_spread(p, scale, f, s, zero_fill);
+  return launch_spread(p, scale, f, s, zero_fill, calls);
 }
 
 ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
@@ -217,9 +221,10 @@ ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
 }
 
 ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s,
-                         void* elem = nullptr) {
+                         void* elem = nullptr, const PackedCalls* pc = nullptr) {
   if (!elem) elem = p->elem_scratch;
-  ib_status st = do_interp(p, u, 0, 1.0, 0.0, s);
+  ib_status st = pc ? do_interp(p, u, 0, 1.0, 0.0, s, pc->interp_u, pc->tmaps_u)
+                    : do_interp(p, u, 0, 1.0, 0.0, s);
   if (st == IB_OK) st = to_nodes(p, p->gq_a, elem, p->inv_mass, U, s);
   return st;
 }
@@ -268,17 +273,39 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   if (mesh->elem_type != IB_ELEM_HEX8 && mesh->elem_type != IB_ELEM_TET4 &&
       mesh->elem_type != IB_ELEM_TET10)
     return IB_ERR_INVALID_ARG;
-  // nodes and coupling points per element
-  const int nc = mesh->elem_type == IB_ELEM_TET10 ? 10 : (mesh->elem_type == IB_ELEM_TET4 ? 4 : 8);
-  const int nq = mesh->elem_type == IB_ELEM_HEX8 ? 8 : 4;
+  const ib_status gs = check_grid(grid);
+  if (gs != IB_OK) return gs;
+  GridDev g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = grid->n[d];
+    g.nt[d] = grid->n[d] / kTile;
+    g.origin[d] = grid->origin[d];
+  }
+  g.h = grid->h;
+  return plan_build(mesh, g, g.nt[0] * g.nt[1] * g.nt[2], quad, precision, IB_MAX_MATERIALS,
+                    S(stream), out);
+}
+
+}  // extern "C"
+
+namespace ibfe {
+
+ib_status check_grid(const ib_grid* grid) {
   if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return IB_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (!std::isfinite(grid->origin[d])) return IB_ERR_INVALID_ARG;
     if (grid->n[d] < kTile || grid->n[d] > (1 << kPackBits)) return IB_ERR_UNSUPPORTED;
     if (grid->n[d] % kTile) return IB_ERR_UNSUPPORTED;
   }
+  return IB_OK;
+}
+
+ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32_t quad,
+                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out) {
+  // nodes and coupling points per element
+  const int nc = mesh->elem_type == IB_ELEM_TET10 ? 10 : (mesh->elem_type == IB_ELEM_TET4 ? 4 : 8);
+  const int nq = mesh->elem_type == IB_ELEM_HEX8 ? 8 : 4;
   if ((int64_t)mesh->n_elems >= (1LL << kIncShift) / 8) return IB_ERR_CAPACITY;
-  cudaStream_t s = S(stream);
   // Q coupling points: the element rule's points (8 per hexahedron, 4 per
   // tetrahedron) or the nodes
   const int64_t E = mesh->n_elems, N = mesh->n_nodes;
@@ -300,7 +327,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
     if (conn[k] < 0 || conn[k] >= N) return IB_ERR_INVALID_ARG;
   int max_mid = 0;
   for (int32_t m : mid) {
-    if (m < 0 || m >= IB_MAX_MATERIALS) return IB_ERR_INVALID_ARG;
+    if (m < 0 || m >= mat_cap) return IB_ERR_INVALID_ARG;
     max_mid = m > max_mid ? m : max_mid;
   }
 
@@ -332,13 +359,10 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   p->E = (int)E;
   p->Q = Q;
   p->rsize = precision == IB_FP64 ? sizeof(double) : sizeof(float);
-  for (int d = 0; d < 3; ++d) {
-    p->grid.n[d] = grid->n[d];
-    p->grid.nt[d] = grid->n[d] / kTile;
-    p->grid.origin[d] = grid->origin[d];
-  }
-  p->grid.h = grid->h;
-  p->ntiles = p->grid.nt[0] * p->grid.nt[1] * p->grid.nt[2];
+  p->grid = grid;
+  p->ntiles = ntiles;
+  p->n_inst = 1;
+  p->mat_cap = mat_cap;
   p->conn = mesh->conn;
   p->X = mesh->X;
   p->fibres = mesh->fibres;
@@ -364,7 +388,8 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->tile_sk, 16 * (size_t)p->ntiles) &&
               dalloc(&p->tile_bcount, 12 * (size_t)classify_blocks(p->ntiles)) &&
               dalloc(&p->tile_counters, 32) && dalloc(&p->digit_tot, 4 * 256) &&
-              dalloc(&p->rpart, 8 * kParamRow * IB_MAX_MATERIALS * (size_t)kReduceCTAs) &&
+              dalloc(&p->rpart, 8 * kParamRow * (size_t)mat_cap * kReduceCTAs) &&
+              dalloc(&p->mat_range, sizeof(int2) * (size_t)mat_cap) &&
               dalloc(&p->spread_scratch,
                      spread_scratch_bytes(precision, Q < p->ntiles ? (Q > 0 ? Q : 1)
                                                                    : max_work_items(p->ntiles, Q))) &&
@@ -375,7 +400,7 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
               dalloc(&p->node_tmp, rs * 6 * (size_t)N) &&
               dalloc(&p->gq_a, rs * 3 * Q) && dalloc(&p->gq_b, rs * 3 * Q) &&
               dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
-              dalloc(&p->ered, 8 * kParamRow * IB_MAX_MATERIALS) && dalloc(&p->dstatus, 16) &&
+              dalloc(&p->ered, 8 * kParamRow * (size_t)mat_cap) && dalloc(&p->dstatus, 16) &&
               dalloc(&p->pen_part, 8 * penalty_scratch_doubles()) &&
               (precision != IB_FP32_SPLIT_DFVOL ||
                dalloc(&p->vol_jm1, sizeof(float) * 2 * (nc == 8 ? 8 : 4) * (size_t)(E > 0 ? E : 1)));
@@ -384,7 +409,11 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
     cudaGetLastError();
     return IB_ERR_CUDA;
   }
+  // every material's elements: the whole mesh (packed plans narrow them)
+  const std::vector<int2> ranges(mat_cap, make_int2(0, (int)E));
   good = ok(cudaMemcpyAsync(p->inc_off, inc_off.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s)) &&
+         ok(cudaMemcpyAsync(p->mat_range, ranges.data(), sizeof(int2) * mat_cap,
+                            cudaMemcpyHostToDevice, s)) &&
          (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * nc * E,
                                        cudaMemcpyHostToDevice, s))) &&
          ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
@@ -413,6 +442,12 @@ ib_status ib_plan_create(const ib_mesh* mesh, const ib_grid* grid, int32_t quad,
   *out = p;
   return IB_OK;
 }
+
+void plan_free(ib_plan* p) { free_plan(p); }
+
+}  // namespace ibfe
+
+extern "C" {
 
 ib_status ib_plan_destroy(ib_plan* plan) {
   if (!plan) return IB_ERR_INVALID_ARG;
@@ -483,30 +518,27 @@ ib_status ib_interp(ib_plan* p, const ib_pos* x, const void* u, void* U, void* s
   return check_launch(st);
 }
 
-ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
-                     const void* u, void* G, void* f, void* U, void* stream) {
-  if (const ib_status f = injected("ib_forward")) return f;
-  if (!p || !u || !G || !f || !U || !aligned16(f)) return IB_ERR_INVALID_ARG;
-  ib_status st = check_pos(p, x);
-  if (st != IB_OK) return st;
-  MatTable mt;
-  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
-  cudaStream_t s = S(stream);
+}  // extern "C"
+
+namespace ibfe {
+
+ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const void* u, void* G,
+                       void* f, void* U, cudaStream_t s, const PackedCalls* pc) {
   // Two branches: the Gauss-point sort and the interpolation depend only on
   // x and u and run on the side stream while the FE force (FP64-pipe bound)
   // runs on the caller's stream; the spread waits for both.
   cudaStream_t b = p->side;
   if (!ok(cudaEventRecord(p->ev_ffork, s)) || !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0)))
     return IB_ERR_CUDA;
-  st = do_points_sorted(p, x, nullptr, b);
+  ib_status st = do_points_sorted(p, x, nullptr, b);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fsorted, b))) st = IB_ERR_CUDA;
   // the far-tile zeros of f (HBM writes) on the side branch, beside the
   // force kernel and ahead of the interpolation
   if (st == IB_OK) {
     p->prof_launches[IB_STAGE_SPREAD] += 1;  // overlapped: not in the spread stage's time
-    st = launch_spread_zero(p, f, b);
+    st = launch_spread_zero(p, f, b, pc ? pc->spread_f : nullptr);
   }
-  if (st == IB_OK) st = do_interp_tail(p, u, U, b, p->elem_scratch2);
+  if (st == IB_OK) st = do_interp_tail(p, u, U, b, p->elem_scratch2, pc);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   if (st == IB_OK) {
     Stage sc(p, IB_STAGE_FORCE, s, 1);
@@ -521,9 +553,25 @@ ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const 
     if (st == IB_OK) st = launch_permute_values(p, s);
   }
   if (st == IB_OK)
-    st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s, /*zero_fill=*/false);
+    st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s, /*zero_fill=*/false,
+                   pc ? pc->spread_f : nullptr);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   return check_launch(st);
+}
+
+}  // namespace ibfe
+
+extern "C" {
+
+ib_status ib_forward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                     const void* u, void* G, void* f, void* U, void* stream) {
+  if (const ib_status f = injected("ib_forward")) return f;
+  if (!p || !u || !G || !f || !U || !aligned16(f) || p->n_inst > 1) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  return forward_body(p, mt, x, u, G, f, U, S(stream), nullptr);
 }
 
 ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_mats,
@@ -555,24 +603,21 @@ ib_status ib_step(ib_plan* p, ib_fluid* fl, const ib_material* mats, int32_t n_m
   return check_launch(st);
 }
 
-ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
-                      const void* u, const void* G, const void* gG, const void* gf,
-                      const void* gU, void* gx, void* gu, double* gparams, void* stream) {
-  if (const ib_status f = injected("ib_backward")) return f;
-  if (!p || !gx || (gf && !G) || (gU && (!gu || !u)) || (gu && !aligned16(gu)))
-    return IB_ERR_INVALID_ARG;
-  ib_status st = check_pos(p, x);
-  if (st != IB_OK) return st;
-  MatTable mt;
-  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
-  cudaStream_t s = S(stream);
+}  // extern "C"
+
+namespace ibfe {
+
+ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos* x,
+                        const void* u, const void* G, const void* gG, const void* gf,
+                        const void* gU, void* gx, void* gu, bool params, double* gparams,
+                        cudaStream_t s, const PackedCalls* pc) {
   cudaStream_t b = p->side;
   const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
   const size_t nbytes = p->rsize * 3 * (size_t)p->N;
   void* gGt = p->node_tmp;  // the force cotangent gG + (df/dG)^T gf
   const bool force = gG || gf;
   // Gauss points built and binned once for both transfer adjoints
-  st = do_points_sorted(p, x, nullptr, s);
+  ib_status st = do_points_sorted(p, x, nullptr, s);
   // spreading adjoint: an interpolation of gf (values and position weights)
   if (st == IB_OK && gf) {
     Stage sc(p, IB_STAGE_POINTS, s, 2);
@@ -580,7 +625,9 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     if (st == IB_OK) st = launch_permute_values(p, s);
   }
   const double gxu = gunit(x);
-  if (st == IB_OK && gf) st = do_interp(p, gf, 1, ih3, ih3 / h * gxu, s);
+  if (st == IB_OK && gf)
+    st = pc ? do_interp(p, nullptr, 1, 0.0, 0.0, s, pc->interp_gf, pc->tmaps_gf)
+            : do_interp(p, gf, 1, ih3, ih3 / h * gxu, s);
   if (st == IB_OK && gf) st = to_nodes(p, p->gq_a, p->elem_scratch, p->inv_mass, gGt, s, gG);
   if (st == IB_OK && gf) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, s);
   if (st == IB_OK && !gf) {
@@ -598,27 +645,47 @@ ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const
     st = launch_point_values(p, gU, b);
     if (st == IB_OK) st = launch_permute_values(p, b);
   }
-  if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b);
-  if (st == IB_OK && gU) st = do_interp(p, u, 2, 0.0, gxu / h, b);
+  if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b, true, pc ? pc->spread_gu : nullptr);
+  if (st == IB_OK && gU)
+    st = pc ? do_interp(p, nullptr, 2, 0.0, 0.0, b, pc->interp_ug, pc->tmaps_u)
+            : do_interp(p, u, 2, 0.0, gxu / h, b);
   if (st == IB_OK && gU) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, b, gx);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   // ... beside the force adjoint, whose nodal gather adds into gx after the join
   if (st == IB_OK && force) {
     Stage sc(p, IB_STAGE_FORCE, s, 1);
-    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch,
-                             gparams != nullptr, s);
+    st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch, params, s);
   }
-  if (st == IB_OK && force && gparams) st = do_reduce(p, kParamRow, n_mats, s);
+  if (st == IB_OK && force && params) st = do_reduce(p, kParamRow, n_mats, s);
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx, gxu);
   if (st == IB_OK && force) st = launch_penalty_adj(p, gGt, gx, s, gxu);
-  if (st == IB_OK && gparams) {
+  if (st == IB_OK && params) {
     const size_t pb = sizeof(double) * kParamRow * (size_t)n_mats;
-    if (!ok(force ? cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)
-                  : cudaMemsetAsync(gparams, 0, pb, s)))
+    if (!force && !ok(cudaMemsetAsync(p->ered, 0, pb, s))) st = IB_ERR_CUDA;
+    if (st == IB_OK && gparams &&
+        !ok(cudaMemcpyAsync(gparams, p->ered, pb, cudaMemcpyDeviceToDevice, s)))
       st = IB_ERR_CUDA;
   }
   return check_launch(st);
+}
+
+}  // namespace ibfe
+
+extern "C" {
+
+ib_status ib_backward(ib_plan* p, const ib_material* mats, int32_t n_mats, const ib_pos* x,
+                      const void* u, const void* G, const void* gG, const void* gf,
+                      const void* gU, void* gx, void* gu, double* gparams, void* stream) {
+  if (const ib_status f = injected("ib_backward")) return f;
+  if (!p || !gx || (gf && !G) || (gU && (!gu || !u)) || (gu && !aligned16(gu)) || p->n_inst > 1)
+    return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  MatTable mt;
+  if ((st = make_table(p, mats, n_mats, mt)) != IB_OK) return st;
+  return backward_body(p, mt, n_mats, x, u, G, gG, gf, gU, gx, gu, gparams != nullptr, gparams,
+                       S(stream), nullptr);
 }
 
 ib_status ib_spread_adj(ib_plan* p, const ib_pos* x, const void* G, const void* gf, void* gG,
@@ -715,27 +782,22 @@ ib_status ib_plan_set_tuning(ib_plan* p, const int32_t tuning[4]) {
   return IB_OK;
 }
 
-ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
-                           const ib_pos* x, const void* u, void* stream, int32_t tuning[4]) {
-  if (!p || !u) return IB_ERR_INVALID_ARG;
-  ib_status st = check_pos(p, x);
-  if (st != IB_OK) return st;
-  cudaStream_t s = S(stream);
-  const size_t rs = p->rsize;
-  const size_t field = rs * 3 * (size_t)p->grid.n[0] * p->grid.n[1] * p->grid.n[2];
-  void *G = nullptr, *f = nullptr, *U = nullptr;
+}  // extern "C"
+
+namespace ibfe {
+
+ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>& run,
+                        cudaStream_t s) {
+  ib_status st = IB_OK;
   cudaEvent_t a = nullptr, b = nullptr;
-  if (!ok(cudaMalloc(&G, rs * 3 * (size_t)p->N)) || !ok(cudaMalloc(&f, field)) ||
-      !ok(cudaMalloc(&U, rs * 3 * (size_t)p->N)) || !ok(cudaEventCreate(&a)) ||
-      !ok(cudaEventCreate(&b)))
-    st = IB_ERR_CUDA;
+  if (!ok(cudaEventCreate(&a)) || !ok(cudaEventCreate(&b))) st = IB_ERR_CUDA;
   // one warm-up call, then the median of three timed calls
-  auto time_forward = [&](float& ms) -> ib_status {
-    ib_status r = ib_forward(p, mats, n_mats, x, u, G, f, U, s);
+  auto time_run = [&](float& ms) -> ib_status {
+    ib_status r = run(s);
     float t[3];
     for (int k = 0; k < 3 && r == IB_OK; ++k) {
       if (!ok(cudaEventRecord(a, s))) return IB_ERR_CUDA;
-      r = ib_forward(p, mats, n_mats, x, u, G, f, U, s);
+      r = run(s);
       if (r == IB_OK && (!ok(cudaEventRecord(b, s)) || !ok(cudaEventSynchronize(b)) ||
                          !ok(cudaEventElapsedTime(&t[k], a, b))))
         r = IB_ERR_CUDA;
@@ -757,7 +819,7 @@ ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
       trial[k] = cand[k][j];
       ib_plan_set_tuning(p, trial);
       float ms = 0.f;
-      st = time_forward(ms);
+      st = time_run(ms);
       if (st == IB_OK && (first || ms < best_ms)) {
         best = cand[k][j];
         best_ms = ms;
@@ -767,11 +829,33 @@ ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
     cur[k] = best;
     ib_plan_set_tuning(p, cur);
   }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return st;
+}
+
+}  // namespace ibfe
+
+extern "C" {
+
+ib_status ib_plan_autotune(ib_plan* p, const ib_material* mats, int32_t n_mats,
+                           const ib_pos* x, const void* u, void* stream, int32_t tuning[4]) {
+  if (!p || !u) return IB_ERR_INVALID_ARG;
+  ib_status st = check_pos(p, x);
+  if (st != IB_OK) return st;
+  cudaStream_t s = S(stream);
+  const size_t rs = p->rsize;
+  const size_t field = rs * 3 * (size_t)p->grid.n[0] * p->grid.n[1] * p->grid.n[2];
+  void *G = nullptr, *f = nullptr, *U = nullptr;
+  if (!ok(cudaMalloc(&G, rs * 3 * (size_t)p->N)) || !ok(cudaMalloc(&f, field)) ||
+      !ok(cudaMalloc(&U, rs * 3 * (size_t)p->N)))
+    st = IB_ERR_CUDA;
+  if (st == IB_OK)
+    st = autotune_with(
+        p, [&](cudaStream_t t) { return ib_forward(p, mats, n_mats, x, u, G, f, U, t); }, s);
   if (G) cudaFree(G);
   if (f) cudaFree(f);
   if (U) cudaFree(U);
-  if (a) cudaEventDestroy(a);
-  if (b) cudaEventDestroy(b);
   if (st == IB_OK && tuning) ib_plan_get_tuning(p, tuning);
   return st;
 }

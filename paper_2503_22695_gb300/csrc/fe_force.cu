@@ -10,34 +10,43 @@
 namespace ibfe {
 namespace {
 
-// Deterministic per-material sums of per-element partials in two levels:
-// CTA b reduces a contiguous chunk of elements with a fixed-shape tree
-// (warp shuffles, then warp sums), one (material, value) pair at a time;
-// one CTA then sums the per-CTA partials of each pair with the same tree.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Deterministic per-material sums of per-element partials in two levels.
+// Material m's elements lie in the range mrange[m] (the whole mesh for a
+// plan of one structure; its instance's elements in a packed plan): CTA b
+// reduces chunk b of that range with a fixed-shape tree (warp shuffles, then
+// the warp sums), one (material, value) pair at a time; then one warp per
+// pair sums the per-CTA partials with the same tree.  The partition and the
+// trees depend only on the range, so an instance of a packed plan gets the
+// bits of a plan of its own.
+__device__ __forceinline__ double warp_tree(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;  // valid in lane 0
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_tree(v);
   if (lane == 0) sh[warp] = v;
   __syncthreads();
   double t = 0.0;
-  if (warp == 0) {
-    t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  }
+  if (warp == 0) t = warp_tree(lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0);
   __syncthreads();
   return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) k_reduce_l1(const double* __restrict__ part,
-                                                   const int32_t* __restrict__ mat_id, int E,
-                                                   int nvals, int n_mats,
-                                                   double* __restrict__ rpart) {
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_l1(const double* __restrict__ part,
+                                                           const int32_t* __restrict__ mat_id,
+                                                           const int2* __restrict__ mrange,
+                                                           int E, int nvals, int n_mats,
+                                                           double* __restrict__ rpart) {
   __shared__ double sh[32];
-  const int chunk = (E + gridDim.x - 1) / gridDim.x;
-  const int e0 = blockIdx.x * chunk, e1 = min(E, e0 + chunk);
-  for (int m = 0; m < n_mats; ++m)
+  for (int m = 0; m < n_mats; ++m) {
+    const int2 r = mrange[m];
+    const int chunk = (r.y - r.x + gridDim.x - 1) / gridDim.x;
+    const int e0 = r.x + blockIdx.x * chunk, e1 = min(r.y, e0 + chunk);
     for (int k = 0; k < nvals; ++k) {
       double s = 0.0;
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
@@ -45,26 +54,36 @@ __global__ void __launch_bounds__(256) k_reduce_l1(const double* __restrict__ pa
       s = block_sum(s, sh);
       if (threadIdx.x == 0) rpart[((int64_t)blockIdx.x * n_mats + m) * kParamRow + k] = s;
     }
+  }
 }
 
-__global__ void __launch_bounds__(256) k_reduce_l2(const double* __restrict__ rpart, int nblk,
-                                                   int nvals, int n_mats,
-                                                   double* __restrict__ out) {
-  __shared__ double sh[32];
-  for (int m = 0; m < n_mats; ++m)
-    for (int k = 0; k < nvals; ++k) {
-      double s = 0.0;
-      for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += rpart[((int64_t)b * n_mats + m) * kParamRow + k];
-      s = block_sum(s, sh);
-      if (threadIdx.x == 0) out[m * kParamRow + k] = s;
-    }
+// One warp per (material, value): the block_sum tree of a kRedThreads-thread
+// CTA whose thread t holds partial t (nblk <= kRedThreads), evaluated warp
+// by warp.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_l2(const double* __restrict__ rpart,
+                                                           int nblk, int nvals, int n_mats,
+                                                           double* __restrict__ out) {
+  const int pair = blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);
+  if (pair >= n_mats * nvals) return;
+  const int m = pair / nvals, k = pair % nvals, lane = threadIdx.x & 31;
+  double ws = 0.0;  // lane w: the tree sum of the partials of thread block w
+  for (int w = 0; w < kRedThreads / 32; ++w) {
+    const int b = 32 * w + lane;
+    double v = 0.0;
+    if (b < nblk) v += rpart[((int64_t)b * n_mats + m) * kParamRow + k];
+    v = __shfl_sync(0xffffffffu, warp_tree(v), 0);
+    if (lane == w) ws = v;
+  }
+  const double t = warp_tree(ws);
+  if (lane == 0) out[m * kParamRow + k] = t;
 }
 
 // The smallest instantiated law set covering the material table (every
 // model in it, the active term if a material has T_a != 0 or the parameter
 // gradients are wanted: they include d/dT_a).
-int law_set(const MatTable& mt, bool params) {
+int law_set(const ib_plan* p, const MatTable& mt, bool params) {
   int need = params ? kLawAct : 0;
+  if (p->mat_dev) need |= p->mat_need;  // packed plans: the device table's laws
   for (int m = 0; m < mt.n; ++m) {
     need |= 1 << mt.model[m];
     if (mt.p[m][kTa] != 0.0) need |= kLawAct;
@@ -132,7 +151,7 @@ ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* xa, const 
     return tet_force<IB_ELEM_TET4>(p, mt, xa, off, v, out, energy, false, false, s);
   if (p->elem == IB_ELEM_TET10)
     return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, energy, false, false, s);
-  const int set = law_set(mt, false);
+  const int set = law_set(p, mt, false);
   if (p->precision == IB_FP32_SPLIT_DFVOL)
     return vol_force<HEX>(p, mt, xa, off, v, out, energy, false, false, s);
   if (p->precision == IB_FP64)
@@ -158,7 +177,7 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
     return tet_force<IB_ELEM_TET4>(p, mt, xa, off, v, out, false, true, params, s);
   if (p->elem == IB_ELEM_TET10)
     return tet_force<IB_ELEM_TET10>(p, mt, xa, off, v, out, false, true, params, s);
-  const int set = law_set(mt, params);
+  const int set = law_set(p, mt, params);
   if (p->precision == IB_FP32_SPLIT_DFVOL)
     return vol_force<HEX>(p, mt, xa, off, v, out, false, true, params, s);
   if (p->precision == IB_FP64)
@@ -181,12 +200,17 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
 #undef IBFE_FE_ARGS
 
 ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
+  if (n_mats > p->mat_cap) return IB_ERR_INVALID_ARG;
   if (p->E == 0) {
-    cudaMemsetAsync(p->ered, 0, sizeof(double) * kParamRow * IB_MAX_MATERIALS, s);
+    cudaMemsetAsync(p->ered, 0, sizeof(double) * kParamRow * p->mat_cap, s);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
-  k_reduce_l1<<<kReduceCTAs, 256, 0, s>>>(p->epart, p->mat_id, p->E, nvals, n_mats, p->rpart);
-  k_reduce_l2<<<1, 256, 0, s>>>(p->rpart, kReduceCTAs, nvals, n_mats, p->ered);
+  static_assert(kReduceCTAs <= kRedThreads, "one partial per thread of the second level");
+  k_reduce_l1<<<kReduceCTAs, kRedThreads, 0, s>>>(p->epart, p->mat_id, p->mat_range, p->E, nvals,
+                                                  n_mats, p->rpart);
+  const int pairs = n_mats * nvals, per = kRedThreads / 32;
+  k_reduce_l2<<<(pairs + per - 1) / per, kRedThreads, 0, s>>>(p->rpart, kReduceCTAs, nvals,
+                                                             n_mats, p->ered);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 

@@ -64,6 +64,9 @@ struct FeArgs {
   double* epart;         // [kParamRow][E] per-element partial sums or null
   int* status;
   int* next;             // block counter, zero at launch
+  const InstDev* inst;   // packed plans: instance table (each instance's h), else null
+  const int32_t* elem_inst;  // packed plans: instance of each element
+  const MatRow* mats;    // packed plans: material table in device memory, else null
 };
 
 template <typename T>
@@ -334,6 +337,8 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   // reference and current coordinates relative to corner 0 (kLanes: this
   // lane's corner only; the others arrive by shuffles)
   constexpr int kNodes = kLanes ? 1 : EL::C;
+  // grid spacing of the element's structure (packed plans: its instance's)
+  const Real h = A.inst ? Real(__ldg(&A.inst[__ldg(A.elem_inst + e)].h)) : A.h;
   Real dX[kNodes][3], du[kNodes][3];
   Real vv[kAdj ? kNodes : 1][3];
   {
@@ -355,7 +360,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         const Real X = __ldg(A.X + d * A.N + node[0]);
         X0[d] = __shfl_sync(full, X, src);
         dX[0][d] = X - X0[d];
-        const Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
+        const Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * h;
         du[0][d] = dx - dX[0][d];
       }
     } else {
@@ -375,7 +380,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           dX[a][d] = __ldg(A.X + d * A.N + node[a]) - X0[d];
-          Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * A.h;
+          Real dx = (Real(c[d] - c0[d]) + (o[d] - o0[d])) * h;
           du[a][d] = dx - dX[a][d];
         }
       }
@@ -389,7 +394,23 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   }
 
   const int mid = A.mat_id ? __ldg(A.mat_id + e) : 0;
-  const int model = mt.model[mid];
+  // the material row, from the table passed by value or (packed plans) from
+  // the device table, read in two separate blocks so that no later read
+  // selects between the sources
+  int model;
+  Real mp[kParamRow];
+  if (A.mats) {
+    const MatRow* r = A.mats + mid;
+    model = __ldg(&r->model);
+#pragma unroll
+    for (int k = 0; k < kParamRow; ++k) mp[k] = Real(__ldg(&r->p[k]));
+  } else {
+    model = mt.model[mid];
+#pragma unroll
+    for (int k = 0; k < kParamRow; ++k) mp[k] = Real(mt.p[mid][k]);
+  }
+  // the row in double (the energy's terms)
+  const auto prm = [&](int k) -> double { return A.mats ? __ldg(&A.mats[mid].p[k]) : mt.p[mid][k]; };
   // the laws this instantiation handles (kLaws bit m: ib_model m; bit
   // kLawActBit: the active term); the host picks an instantiation whose set
   // covers the material table, and every other branch compiles away
@@ -398,7 +419,6 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const bool lawHO = (kLaws & 4) && model == IB_HO;
   const bool lawSR = (kLaws & 8) && model == IB_STD_REINF;
   const bool lawF2 = (kLaws & 16) && model == IB_FIBRE2;
-  const double* prm = mt.p[mid];
   Real ef[3] = {Real(1), Real(0), Real(0)}, es[3] = {Real(0), Real(1), Real(0)};
   if (A.fib) {
 #pragma unroll
@@ -414,15 +434,15 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real esn1r = Real(esn1), efesr = Real(efes);
 
   // material constants (unused entries of a model are never read by its branches)
-  const Real kap = Real(prm[lawNH ? 1 : (lawHO ? 8 : (lawF2 ? 4 : 3))]);
-  const Real pa = Real(prm[0]), pb = Real(prm[1]);
-  const Real paf = Real(prm[lawF1 ? 1 : 2]), pbf = Real(prm[lawF1 ? 2 : 3]);
-  const Real pas = Real(prm[4]), pbs = Real(prm[5]), pafs = Real(prm[6]), pbfs = Real(prm[7]);
+  const Real kap = lawNH ? mp[1] : (lawHO ? mp[8] : (lawF2 ? mp[4] : mp[3]));
+  const Real pa = mp[0], pb = mp[1];
+  const Real paf = lawF1 ? mp[1] : mp[2], pbf = lawF1 ? mp[2] : mp[3];
+  const Real pas = mp[4], pbs = mp[5], pafs = mp[6], pbfs = mp[7];
   // active fibre tension (Section 6.1); the parameter adjoint always needs
   // its fibre kinematics for d/dT_a
   static_assert(!kParams || (kLaws & kLawAct), "the parameter adjoint computes d/dT_a");
-  const Real Ta = Real(prm[kTa]);
-  const bool act = (kLaws & kLawAct) && (kParams || prm[kTa] != 0.0);
+  const Real Ta = mp[kTa];
+  const bool act = (kLaws & kLawAct) && (kParams || Ta != Real(0));
 
   double en = 0.0;
   Real gp[kParamRow];
@@ -535,7 +555,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
     // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
     // with C e = e + w, w = H e + H^T e + H^T H e (no cancellation for small H)
-    const Real k4 = lawSR ? Real(0.5) * (Real(prm[2]) + pa - Real(4) * pb) : Real(0);
+    const Real k4 = lawSR ? Real(0.5) * (mp[2] + pa - Real(4) * pb) : Real(0);
     const Real c5 = lawSR ? pa - pb : Real(0);
     Real w5[3] = {Real(0), Real(0), Real(0)}, Fw5[3] = {Real(0), Real(0), Real(0)};
     if (has_f) {
@@ -590,26 +610,26 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
 
     if (kEnergy) {
       double psi = 0.5 * double(kap) * double(lnJs) * double(lnJs);
-      if (lawNH || lawF1) psi += prm[0] * double(Ibm3);
-      else if (lawHO) psi += prm[0] / (2.0 * prm[1]) * expm1(prm[1] * double(Ibm3));
-      else if (lawSR) psi += 0.5 * prm[0] * double(Ibm3);
-      else if (lawF2) psi += prm[0] * expm1(prm[1] * double(Ibm3));
+      if (lawNH || lawF1) psi += prm(0) * double(Ibm3);
+      else if (lawHO) psi += prm(0) / (2.0 * prm(1)) * expm1(prm(1) * double(Ibm3));
+      else if (lawSR) psi += 0.5 * prm(0) * double(Ibm3);
+      else if (lawF2) psi += prm(0) * expm1(prm(1) * double(Ibm3));
       if (lawSR) {
         const double ww = double(w5[0]) * w5[0] + double(w5[1]) * w5[1] + double(w5[2]) * w5[2];
         psi += 0.5 * double(c5) * (double(efn1) - ww) + 0.25 * double(k4) * double(f1.d) * double(f1.d);
       } else if (lawF1 || lawHO || lawF2) {  // the exponential fibre term of Psi_2, Psi_3, Psi_4
-        const double af = prm[lawF1 ? 1 : 2], bf = prm[lawF1 ? 2 : 3];
+        const double af = prm(lawF1 ? 1 : 2), bf = prm(lawF1 ? 2 : 3);
         psi += af / (2.0 * bf) * expm1(bf * double(f1.d) * double(f1.d));
       }
       if (has_s) {
-        psi += prm[4] / (2.0 * prm[5]) * expm1(prm[5] * double(f2.d) * double(f2.d));
-        psi += prm[6] / (2.0 * prm[7]) * expm1(prm[7] * double(I8) * double(I8));
+        psi += prm(4) / (2.0 * prm(5)) * expm1(prm(5) * double(f2.d) * double(f2.d));
+        psi += prm(6) / (2.0 * prm(7)) * expm1(prm(7) * double(I8) * double(I8));
       }
       if (act) {
         // T_a/2 [(1 - 4.9)(I4 - 1) + 4.9 (2/3)(I4^(3/2) - 1)] with
         // I4^(3/2) - 1 = (I4 - 1)(I4 + sqrt(I4) + 1)/(sqrt(I4) + 1)
         const double d4 = double(f1.d4), r = sqrt(1.0 + d4);
-        psi += 0.5 * prm[kTa] * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
+        psi += 0.5 * prm(kTa) * d4 * ((1.0 - 4.9) + 4.9 * (2.0 / 3.0) * (2.0 + d4 + r) / (r + 1.0));
       }
       en += psi * double(wj);
     }
@@ -995,6 +1015,9 @@ inline FeArgs<float> make_args<float>(ib_plan* p, const void* xa, const float* o
   A.epart = p->epart;
   A.status = p->dstatus;
   A.next = p->tile_counters + 6;
+  A.inst = p->n_inst > 1 ? p->inst : nullptr;
+  A.elem_inst = p->n_inst > 1 ? p->elem_inst : nullptr;
+  A.mats = p->mat_dev;
   return A;
 }
 
@@ -1020,6 +1043,9 @@ inline FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*
   A.epart = p->epart;
   A.status = p->dstatus;
   A.next = p->tile_counters + 6;
+  A.inst = nullptr;  // packed plans are FP32
+  A.elem_inst = nullptr;
+  A.mats = nullptr;
   return A;
 }
 

@@ -181,6 +181,48 @@ __device__ __forceinline__ void unpack_cell(int32_t p, int& x, int& y, int& z) {
   z = (p >> (2 * kPackBits)) & ((1 << kPackBits) - 1);
 }
 
+// Grid of the structure that owns a tile: its sizes, tiles per dimension,
+// first tile and instance number (the plan's own grid, 0 and 0 for a plan
+// of one structure; the packed batch's InstDev row otherwise).
+struct TileGeo {
+  int n[3];
+  int nt[3];
+  int base;
+  int inst;
+};
+__device__ __forceinline__ TileGeo tile_geo(const GridDev& g, const InstDev* inst,
+                                            const int32_t* tile_inst, int tile) {
+  TileGeo t;
+  if (inst) {
+    const int i = __ldg(tile_inst + tile);
+    const InstDev* r = inst + i;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      t.n[d] = __ldg(&r->n[d]);
+      t.nt[d] = __ldg(&r->nt[d]);
+    }
+    t.base = __ldg(&r->tile_base);
+    t.inst = i;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      t.n[d] = g.n[d];
+      t.nt[d] = g.nt[d];
+    }
+    t.base = 0;
+    t.inst = 0;
+  }
+  return t;
+}
+// tile coordinates of a tile within its structure's grid
+__device__ __forceinline__ void tile_coords(const TileGeo& t, int tile, int& tx, int& ty,
+                                            int& tz) {
+  const int l = tile - t.base;
+  tx = l % t.nt[0];
+  ty = (l / t.nt[0]) % t.nt[1];
+  tz = l / (t.nt[0] * t.nt[1]);
+}
+
 // Node position as (integer cell, offset in cell units).  FP32 split plans
 // read the stored pair; FP64 plans derive it from the absolute coordinate.
 template <typename Real>

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <functional>
 #include <type_traits>
 
 #include "ibfe.h"
@@ -60,6 +61,36 @@ struct GridDev {
   int nt[3];          // tiles per dimension
   double h;
   double origin[3];
+};
+
+// Packed batches (batch.cu): several structures ("instances"), each with its
+// own mesh, periodic grid and materials, held by one plan whose tiles,
+// elements, nodes and material ids are the instances' ranges laid end to
+// end.  A tile or an element finds its instance through the plan's
+// tile_inst / elem_inst tables and the instance's grid in InstDev; a plan
+// of one structure has no tables and uses its GridDev.
+struct InstDev {
+  int n[3];
+  int nt[3];          // tiles per dimension
+  int tile_base;      // first tile of the instance in the plan's numbering
+  int pad;
+  double h;
+};
+
+// Per-instance operands of one call on a packed plan: the instance's grid
+// array (the spreading's output or the interpolated field) and the call's
+// scalars (spreading: s0 = scale; interpolation: s0 = vscale, s1 = gscale).
+struct GridCall {
+  void* field;
+  double s0, s1;
+};
+
+// One row of a material table in device memory (packed plans; rows indexed
+// by the packed material ids).
+struct MatRow {
+  int model;
+  int pad;
+  double p[kParamRow];
 };
 
 template <typename Real>
@@ -141,7 +172,7 @@ struct ib_plan {
   int32_t* tile_list_near;// [ntiles] near tiles, ascending
   uint32_t* tile_vmax;   // [ntiles] FP32: bits of the largest |carried value| of each tile
   int32_t* tile_done;    // [ntiles] work items of the tile written (FP32 spreading, per call)
-  int32_t* tile_sk;      // [4 ntiles] FP32: first block slot, exponent, 0, work items
+  int32_t* tile_sk;      // [4 ntiles] FP32: first block slot, exponent, item bound, items
   int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
   int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
                          //     [6] FE force block counter
@@ -178,6 +209,16 @@ struct ib_plan {
   double* epart;         // [kParamRow][E] per-element partial sums
   double* ered;          // [IB_MAX_MATERIALS*kParamRow] reduced sums
   int* dstatus;          // device status word
+  // packed batch (batch.cu); n_inst = 1 and null tables for one structure
+  int n_inst;
+  ibfe::InstDev* inst;   // [n_inst]
+  int32_t* tile_inst;    // [ntiles] instance of each tile
+  int32_t* elem_inst;    // [E] instance of each element
+  ibfe::MatRow* mat_dev; // [n_mats_dev] material table (packed plans)
+  int n_mats_dev;
+  int mat_need;          // packed plans: bit m for each ib_model used, kLawAct if a T_a != 0
+  int2* mat_range;       // [mat_cap] element range of each material id (reductions)
+  int mat_cap;           // material ids the reduction buffers hold
 
   // per-stage profiling (host side; events only while prof_on)
   int prof_on;
@@ -230,9 +271,13 @@ ib_status launch_permute_values(ib_plan* p, cudaStream_t s);
 
 // spread.cu
 // zero_fill false: the far-tile zeros were issued by launch_spread_zero
-ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true);
+// calls (packed plans): each instance's output field and scale, replacing
+// f and scale (device array, one GridCall per instance)
+ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true,
+                        const GridCall* calls = nullptr);
 // zeros of the tiles no coupling point reaches (needs the points binned)
-ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s);
+ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s,
+                             const GridCall* calls = nullptr);
 ib_status spread_prepare(ib_plan* p);
 size_t spread_scratch_bytes(int precision, int64_t slots);
 int spread_launches(int precision);
@@ -242,13 +287,55 @@ int spread_launches(int precision);
 // mode 1: out_a[gq] = w j0 * vscale * sum u prod phi,
 //         out_b[gq] = gscale * sum_c val_c * grad_chi(sum u^c prod phi)
 // mode 2: only out_b (gradient) as in mode 1.
+// calls / tmaps (packed plans): each instance's field, vscale and gscale,
+// and each instance's tensor map of its field (device arrays; tmaps null:
+// no TMA staging)
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
-                               double gscale, cudaStream_t s);
+                               double gscale, cudaStream_t s, const GridCall* calls = nullptr,
+                               const void* tmaps = nullptr);
+// the tensor map of a FP32 field [3][n2][n1][n0] for the interpolation's TMA
+// staging, written to `map` (128 bytes, host); false if unavailable
+bool encode_velocity_map(const int n[3], const void* u, void* map);
+constexpr size_t kTensorMapBytes = 128;
 ib_status interp_prepare(ib_plan* p);
 // the bounded-wait diagnostic (latches kStatTimeout into *status after ms)
 ib_status launch_wait_probe(int* status, double ms, cudaStream_t s);
 
 // capi.cu
+// grid validation of ib_plan_create, and the plan builder behind it (also
+// used for packed plans: `grid` is then the first instance's, `ntiles` the
+// instances' total and mat_cap their total material count)
+ib_status check_grid(const ib_grid* grid);
+ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32_t quad,
+                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out);
+void plan_free(ib_plan* p);
+// the autotuner's coordinate descent over the plan's tuning, timing `run`
+// (one warm-up and the median of three calls per candidate)
+ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>& run,
+                        cudaStream_t s);
+// Per-instance operands of the forward and backward of a packed plan
+// (device arrays of one GridCall or tensor map per instance): spread_f
+// (f_i, h_i^-3), interp_u (u_i, 1, 0), tmaps_u, interp_gf (gf_i, h_i^-3,
+// h_i^-4 gunit), tmaps_gf, spread_gu (gu_i, 1), interp_ug (u_i, 0, gunit / h_i).
+struct PackedCalls {
+  const GridCall* spread_f;
+  const GridCall* interp_u;
+  const void* tmaps_u;
+  const GridCall* interp_gf;
+  const void* tmaps_gf;
+  const GridCall* spread_gu;
+  const GridCall* interp_ug;
+};
+// The sequences of ib_forward and ib_backward (pc null: one structure, the
+// fields and scalars are the arguments; pc set: a packed plan, the fields and
+// h-dependent scalars are pc's).  params: compute the parameter gradients
+// into p->ered (copied to gparams when it is not null).
+ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const void* u, void* G,
+                       void* f, void* U, cudaStream_t s, const PackedCalls* pc);
+ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos* x,
+                        const void* u, const void* G, const void* gG, const void* gf,
+                        const void* gU, void* gx, void* gu, bool params, double* gparams,
+                        cudaStream_t s, const PackedCalls* pc);
 // profiler interval around a kernel inside a stage (sub-stage timing; its
 // launches are counted by the enclosing stage)
 int prof_begin(ib_plan* p, int stage, cudaStream_t s);

@@ -43,6 +43,10 @@ constexpr int kComp = kB * kSZ;  // 1740
 template <typename Real>
 struct InterpArgs {
   GridDev g;
+  const InstDev* inst;       // packed plans: instance table, else null
+  const int32_t* tile_inst;  // packed plans: instance of each tile
+  const GridCall* calls;     // packed plans: each instance's u, vscale, gscale, else null
+  const CUtensorMap* tmaps;  // packed plans: each instance's tensor map of u (FP32)
   int64_t Q;
   const int32_t* tile_start;
   const int32_t* tile_end;
@@ -63,6 +67,18 @@ struct InterpArgs {
   int use_tma;            // FP32: interior tiles staged by the tensor map
 };
 
+// The call's field and scalars for the structure `inst`.
+template <typename Real>
+__device__ __forceinline__ const Real* call_u(const InterpArgs<Real>& A, int inst) {
+  return A.calls ? static_cast<const Real*>(A.calls[inst].field) : A.u;
+}
+template <typename Real>
+__device__ __forceinline__ void call_scales(const InterpArgs<Real>& A, int inst, Real& vs,
+                                            Real& gs) {
+  vs = A.calls ? (Real)__ldg(&A.calls[inst].s0) : A.vscale;
+  gs = A.calls ? (Real)__ldg(&A.calls[inst].s1) : A.gscale;
+}
+
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -79,10 +95,12 @@ __device__ __forceinline__ void cp_async_wait_group() {
 template <typename Real>
 __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot, Real* ub, int tid) {
   const int tile = A.tile_list[slot];
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-  const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
+  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  int tx, ty, tz;
+  tile_coords(geo, tile, tx, ty, tz);
+  const int n0 = geo.n[0], n1 = geo.n[1], n2 = geo.n[2];
   const int64_t cells = (int64_t)n0 * n1 * n2;
+  const Real* const u = call_u(A, geo.inst);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   const int bx = tid & 15;
   if (bx >= kB) return;
@@ -93,7 +111,7 @@ __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot,
     gy += gy < 0 ? n1 : (gy >= n1 ? -n1 : 0);
     gz += gz < 0 ? n2 : (gz >= n2 ? -n2 : 0);
     Real* dst = ub + c * kComp + bz * kSZ + by * kSY + bx;
-    const Real* src = A.u + c * cells + ((int64_t)gz * n1 + gy) * n0 + gx;
+    const Real* src = u + c * cells + ((int64_t)gz * n1 + gy) * n0 + gx;
     if (sizeof(Real) == 4) {
       cp_async4(dst, src);
     } else {
@@ -108,7 +126,7 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real* ub,
                                            const int lc[3], const Real off[3], int gq,
-                                           const Real val[3]);
+                                           const Real val[3], Real vs, Real gs);
 
 // Persistent CTAs, two-stage pipeline: the velocity block of the next work
 // item is fetched while the points of the current one are evaluated.
@@ -173,19 +191,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   }
 }
 
-__device__ __forceinline__ bool tile_interior(const GridDev& g, int tile) {
-  const int nt0 = g.nt[0], nt1 = g.nt[1];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
-  return tx > 0 && ty > 0 && tz > 0 && tx < nt0 - 1 && ty < nt1 - 1 && tz < g.nt[2] - 1;
+__device__ __forceinline__ bool tile_interior(const TileGeo& g, int tile) {
+  int tx, ty, tz;
+  tile_coords(g, tile, tx, ty, tz);
+  return tx > 0 && ty > 0 && tz > 0 && tx < g.nt[0] - 1 && ty < g.nt[1] - 1 && tz < g.nt[2] - 1;
 }
 
 // Thread 0: bulk tensor copy of the box around the tile of item `slot`.
 // Only interior tiles: x start 8 tx - 4 >= 0 is a multiple of 4 floats (16
-// bytes) and the box lies inside the grid.
-__device__ __forceinline__ void issue_box(const CUtensorMap* tmap, const GridDev& g, int tile,
-                                          uint32_t dense, uint32_t bar) {
-  const int nt0 = g.nt[0], nt1 = g.nt[1];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+// bytes) and the box lies inside the grid.  A map in global memory (packed
+// plans; written by a copy before the launch) is first acquired by the
+// tensor-map proxy.
+__device__ __forceinline__ void issue_box(const CUtensorMap* tmap, bool global_map,
+                                          const TileGeo& g, int tile, uint32_t dense,
+                                          uint32_t bar) {
+  if (global_map)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap))
+                 : "memory");
+  int tx, ty, tz;
+  tile_coords(g, tile, tx, ty, tz);
   const int x = tx * kTile - 4, y = ty * kTile - 2, z = tz * kTile - 2, c = 0;
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
@@ -235,9 +260,9 @@ __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int 
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int x0 = (tile % nt0) * kTile, y0 = ((tile / nt0) % nt1) * kTile,
-            z0 = (tile / (nt0 * nt1)) * kTile;
+  int tx, ty, tz;
+  tile_coords(tile_geo(A.g, A.inst, A.tile_inst, tile), tile, tx, ty, tz);
+  const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   cnt[tid] = 0;
   cnt[tid + kThreads] = 0;
   __syncthreads();
@@ -278,10 +303,12 @@ __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int 
 }
 
 // Per item: wait for its box (or stage it with cp.async), rewrite it into the
-// padded block, issue the next item's box, evaluate the points.
+// padded block, issue the next item's box, evaluate the points
+// (shared memory holds 3 CTAs per SM in mode 0 and 2 in the gradient modes;
+// the register bounds follow)
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(const __grid_constant__ CUtensorMap tmap,
-                                                         InterpArgs<float> A) {
+__global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
+    k_interp_tma(const __grid_constant__ CUtensorMap tmap, InterpArgs<float> A) {
   extern __shared__ unsigned char smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + kTmaAlign - 1) &
                          ~static_cast<uintptr_t>(kTmaAlign - 1);
@@ -302,16 +329,26 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
   }
   __syncthreads();
   int cur = next;
-  bool cur_tma = cur < count && tile_interior(A.g, A.tile_list[cur]);
-  if (tid == 0 && cur_tma) issue_box(&tmap, A.g, A.tile_list[cur], dense_s, bar);
+  // the tile of an item, its structure's grid and tensor map
+  auto geo_of = [&](int item) { return tile_geo(A.g, A.inst, A.tile_inst, A.tile_list[item]); };
+  auto map_of = [&](const TileGeo& g) { return A.tmaps ? A.tmaps + g.inst : &tmap; };
+  // only the instance of the current item is carried across iterations
+  int cinst = 0;
+  bool cur_tma = false;
+  if (cur < count) {
+    const TileGeo g = geo_of(cur);
+    cinst = g.inst;
+    cur_tma = tile_interior(g, A.tile_list[cur]);
+    if (tid == 0 && cur_tma)
+      issue_box(map_of(g), A.tmaps != nullptr, g, A.tile_list[cur], dense_s, bar);
+  }
   uint32_t parity = 0;
   while (cur < count) {
     const int np = local_cell_stage<MODE>(A, cur, cnt, pts, tmp, tid);  // box in flight
+    // thread 0 alone waits (bounded) for the box; the barrier below hands
+    // the landed data and the outcome to the CTA
     if (cur_tma) {
-      if (mbar_wait(bar, parity))
-        parity ^= 1;
-      else
-        abort_flag = 1;
+      if (tid == 0 && !mbar_wait(bar, parity)) abort_flag = 1;
     } else {
       stage_block(A, cur, ub, tid);
       cp_async_commit();
@@ -321,12 +358,22 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
     __syncthreads();  // box landed everywhere; next item known
     if (abort_flag) break;
     if (cur_tma) {
+      parity ^= 1;
       relayout(dense, ub, tid);
       __syncthreads();  // dense free, padded block complete
     }
     const int nxt = next;
-    const bool nxt_tma = nxt < count && tile_interior(A.g, A.tile_list[nxt]);
-    if (tid == 0 && nxt_tma) issue_box(&tmap, A.g, A.tile_list[nxt], dense_s, bar);
+    int ninst = cinst;
+    bool nxt_tma = false;
+    if (nxt < count) {
+      const TileGeo g = geo_of(nxt);
+      ninst = g.inst;
+      nxt_tma = tile_interior(g, A.tile_list[nxt]);
+      if (tid == 0 && nxt_tma)
+        issue_box(map_of(g), A.tmaps != nullptr, g, A.tile_list[nxt], dense_s, bar);
+    }
+    float vs, gs;
+    call_scales(A, cinst, vs, gs);
     // the points in cell order, from the staged copy
     for (int j = tid; j < np; j += kThreads) {
       const int c = pts.lc[j];
@@ -337,10 +384,11 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
 #pragma unroll
         for (int k = 0; k < 3; ++k) val[k] = pts.val[k][j];
       }
-      interp_one<float, MODE>(A, ub, lc, off, pts.idx[j], val);
+      interp_one<float, MODE>(A, ub, lc, off, pts.idx[j], val, vs, gs);
     }
     __syncthreads();  // padded block free; `next` consumed
     cur = nxt;
+    cinst = ninst;
     cur_tma = nxt_tma;
   }
   if (abort_flag && tid == 0) {
@@ -355,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 4 : 2) k_interp_tma(cons
 template <typename Real, int MODE>
 __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real* ub,
                                            const int lc[3], const Real off[3], int gq,
-                                           const Real val[3]) {
+                                           const Real val[3], Real vs, Real gs) {
   // weights for both staggerings per axis: [d][0] = s 0, [d][1] = s 1/2
   Real w[3][2][4], dw[3][2][4];
   int b[3][2];
@@ -411,13 +459,13 @@ __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real
     }
   }
   if (MODE != 2) {
-    const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * A.vscale : A.vscale;
+    const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * vs : vs;
 #pragma unroll
     for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
   }
   if (MODE != 0) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = A.gscale * grad[d];
+    for (int d = 0; d < 3; ++d) A.out_b[d * A.Q + gq] = gs * grad[d];
   }
 }
 
@@ -428,9 +476,12 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  int tx, ty, tz;
+  tile_coords(geo, tile, tx, ty, tz);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+  Real vs, gs;
+  call_scales(A, geo.inst, vs, gs);
   for (int i = s + tid; i < e; i += kThreads) {
     int cx, cy, cz;
     unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
@@ -442,7 +493,7 @@ __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slo
 #pragma unroll
       for (int c = 0; c < 3; ++c) val[c] = __ldg(A.p_val + c * A.Q + i);
     }
-    interp_one<Real, MODE>(A, ub, lc, off, __ldg(A.p_idx + i), val);
+    interp_one<Real, MODE>(A, ub, lc, off, __ldg(A.p_idx + i), val, vs, gs);
   }
 }
 
@@ -477,10 +528,10 @@ EncodeTiled encode_tiled() {
 
 // Tensor map of the velocity field u [3][n2][n1][n0] (float), box 16 x 12 x 12 x 3.
 // False when the driver function is missing or u is not 16-byte aligned.
-bool make_velocity_map(const ib_plan* p, const void* u, CUtensorMap* m) {
+bool make_velocity_map(const int n[3], const void* u, CUtensorMap* m) {
   const EncodeTiled enc = encode_tiled();
   if (!enc || (reinterpret_cast<uintptr_t>(u) & 15) != 0) return false;
-  const cuuint64_t n0 = p->grid.n[0], n1 = p->grid.n[1], n2 = p->grid.n[2];
+  const cuuint64_t n0 = n[0], n1 = n[1], n2 = n[2];
   const cuuint64_t dims[4] = {n0, n1, n2, 3};
   const cuuint64_t strides[3] = {n0 * 4, n0 * n1 * 4, n0 * n1 * n2 * 4};
   const cuuint32_t box[4] = {kDX, kB, kB, 3};
@@ -492,10 +543,14 @@ bool make_velocity_map(const ib_plan* p, const void* u, CUtensorMap* m) {
 
 template <typename Real>
 ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gscale,
-                   cudaStream_t s) {
+                   cudaStream_t s, const GridCall* calls, const CUtensorMap* tmaps) {
   if (p->Q == 0) return IB_OK;
   InterpArgs<Real> A;
   A.g = p->grid;
+  A.inst = p->n_inst > 1 ? p->inst : nullptr;
+  A.tile_inst = p->n_inst > 1 ? p->tile_inst : nullptr;
+  A.calls = calls;
+  A.tmaps = tmaps;
   A.Q = p->Q;
   A.tile_start = p->tile_start;
   A.tile_end = p->tile_end;
@@ -522,8 +577,9 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   const size_t smem = smem_bytes<Real>();
   cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
   if constexpr (sizeof(Real) == 4) {
-    CUtensorMap tmap;
-    if (p->interp_tma && make_velocity_map(p, u, &tmap)) {
+    // packed plans: the instances' maps in device memory (this one unused)
+    CUtensorMap tmap = {};
+    if (p->interp_tma && (calls ? tmaps != nullptr : make_velocity_map(p->grid.n, u, &tmap))) {
       A.use_tma = 1;
       if (mode == 0)
         k_interp_tma<0><<<cap(p->interp_ctas_tma[0]), kThreads, tma_smem<0>(), s>>>(tmap, A);
@@ -622,9 +678,16 @@ ib_status interp_prepare(ib_plan* p) {
 }
 
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
-                               double gscale, cudaStream_t s) {
-  return p->precision == IB_FP64 ? interp_t<double>(p, u, mode, vscale, gscale, s)
-                                 : interp_t<float>(p, u, mode, vscale, gscale, s);
+                               double gscale, cudaStream_t s, const GridCall* calls,
+                               const void* tmaps) {
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
+  return p->precision == IB_FP64 ? interp_t<double>(p, u, mode, vscale, gscale, s, calls, m)
+                                 : interp_t<float>(p, u, mode, vscale, gscale, s, calls, m);
+}
+
+bool encode_velocity_map(const int n[3], const void* u, void* map) {
+  static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+  return make_velocity_map(n, u, static_cast<CUtensorMap*>(map));
 }
 
 }  // namespace ibfe

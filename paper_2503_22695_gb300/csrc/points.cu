@@ -41,6 +41,8 @@ struct PtArgs {
   const Real* inv_mass;  // [N]
   const Real* wj0;       // [nq][E]
   GridDev g;
+  const InstDev* inst;   // packed plans: instance table, else null
+  const int32_t* elem_inst;  // packed plans: instance of each element
   int32_t* q_cell;
   Real* q_off;           // [3][Q]
   Real* q_val;           // [3][Q]
@@ -53,11 +55,12 @@ struct PtArgs {
 // Packed cell, and the tile key with either the point's slot in its tile
 // (binning: one atomic per distinct tile of the warp) or its index (sorting).
 template <typename Real, bool kBin>
-__device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, const int cw[3]) {
+__device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, const int cw[3],
+                                          const TileGeo& geo) {
   A.q_cell[gq] = pack_cell(cw[0], cw[1], cw[2]);
-  const uint32_t tile = (uint32_t)((cw[0] >> kTileShift) +
-                                   A.g.nt[0] * ((cw[1] >> kTileShift) +
-                                                A.g.nt[1] * (cw[2] >> kTileShift)));
+  const uint32_t tile = (uint32_t)(geo.base + (cw[0] >> kTileShift) +
+                                   geo.nt[0] * ((cw[1] >> kTileShift) +
+                                                geo.nt[1] * (cw[2] >> kTileShift)));
   if (kBin) {
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, tile);
@@ -81,6 +84,7 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   if (e >= A.E) return;
   const int E = A.E;
   const int64_t Q = (int64_t)EL::Q * E;
+  const TileGeo geo = tile_geo(A.g, A.inst, A.elem_inst, e);  // the element's grid
   int c0[3];
   Real o0[3];
   Real dl[EL::C][3];
@@ -138,10 +142,10 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
         off = Real(0);
         k += Real(1);
       }
-      cw[d] = wrap_idx(c0[d] + (int)k, A.g.n[d]);
+      cw[d] = wrap_idx(c0[d] + (int)k, geo.n[d]);
       A.q_off[d * Q + gq] = off;
     }
-    bin_point<Real, kBin>(A, gq, cw);
+    bin_point<Real, kBin>(A, gq, cw, geo);
     if (A.V) {
       const Real w = __ldg(A.wj0 + gq);
 #pragma unroll
@@ -177,13 +181,15 @@ __global__ void __launch_bounds__(256) k_points_nodal(PtArgs<Real> A) {
       o[d] = Real(0);
     }
   }
+  // (packed plans hold Gauss-rule structures only: the plan's grid)
+  const TileGeo geo = tile_geo(A.g, nullptr, nullptr, 0);
   int cw[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    cw[d] = wrap_idx(c[d], A.g.n[d]);
+    cw[d] = wrap_idx(c[d], geo.n[d]);
     A.q_off[d * N + a] = o[d];
   }
-  bin_point<Real, kBin>(A, a, cw);
+  bin_point<Real, kBin>(A, a, cw, geo);
   if (A.V) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) A.q_val[d * N + a] = __ldg(A.V + d * N + a);
@@ -236,11 +242,11 @@ __device__ __forceinline__ void tile_vmax_update(uint32_t* vmax, uint32_t tile, 
 }
 
 // Binned copies of the carried values (and, for FP32 plans, the per-tile
-// maxima of their magnitudes).
+// maxima of their magnitudes; the tile of a binned point is its binning key).
 template <typename Real>
 __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
                                  const Real* __restrict__ q_val, Real* __restrict__ p_val,
-                                 const int32_t* __restrict__ p_cell, GridDev g,
+                                 const uint32_t* __restrict__ key,
                                  uint32_t* __restrict__ vmax) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Q) return;
@@ -251,13 +257,7 @@ __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
     v[d] = __ldg(q_val + d * Q + gi);
     p_val[d * Q + i] = v[d];
   }
-  if constexpr (sizeof(Real) == 4) {
-    int cx, cy, cz;
-    unpack_cell(__ldg(p_cell + i), cx, cy, cz);
-    const uint32_t tile = (uint32_t)((cx >> kTileShift) +
-                                     g.nt[0] * ((cy >> kTileShift) + g.nt[1] * (cz >> kTileShift)));
-    tile_vmax_update(vmax, tile, v[0], v[1], v[2]);
-  }
+  if constexpr (sizeof(Real) == 4) tile_vmax_update(vmax, __ldg(key + gi), v[0], v[1], v[2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,6 +446,8 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   A.inv_mass = (const float*)p->inv_mass;
   A.wj0 = (const float*)p->wj0;
   A.g = p->grid;
+  A.inst = p->n_inst > 1 ? p->inst : nullptr;
+  A.elem_inst = p->n_inst > 1 ? p->elem_inst : nullptr;
   A.q_cell = p->q_cell;
   A.q_off = (float*)p->q_off;
   A.q_val = (float*)p->q_val;
@@ -479,6 +481,8 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
   A.inv_mass = (const double*)p->inv_mass;
   A.wj0 = (const double*)p->wj0;
   A.g = p->grid;
+  A.inst = nullptr;  // packed plans are FP32
+  A.elem_inst = nullptr;
   A.q_cell = p->q_cell;
   A.q_off = (double*)p->q_off;
   A.q_val = (double*)p->q_val;
@@ -578,11 +582,11 @@ ib_status launch_permute_values(ib_plan* p, cudaStream_t s) {
   const int nb = (int)((p->Q + 255) / 256);
   if (p->precision == IB_FP64) {
     k_permute_values<double><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
-                                                (double*)p->p_val, p->p_cell, p->grid, nullptr);
+                                                (double*)p->p_val, nullptr, nullptr);
   } else {
     cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
     k_permute_values<float><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val,
-                                               (float*)p->p_val, p->p_cell, p->grid, p->tile_vmax);
+                                               (float*)p->p_val, p->keys[0], p->tile_vmax);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }

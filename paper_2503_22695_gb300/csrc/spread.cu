@@ -47,6 +47,10 @@ constexpr int kMW = kMT / 32;
 template <typename Real>
 struct SpreadArgs {
   GridDev g;
+  int ntiles;
+  const InstDev* inst;         // packed plans: instance table, else null
+  const int32_t* tile_inst;    // packed plans: instance of each tile
+  const GridCall* calls;       // packed plans: each instance's f and scale, else null
   int64_t Q;
   const int32_t* tile_start;
   const int32_t* tile_end;
@@ -65,7 +69,7 @@ struct SpreadArgs {
   Real* f;
   const uint32_t* tile_vmax;   // FP32: bits of max |value| over each tile's points
   int32_t* tile_done;          // FP32: work items of each tile written in this call
-  int4* tile_sk;               // FP32: (first block slot or -1, exponent k + 11, 0, items)
+  int4* tile_sk;               // FP32: (first block slot or -1, exponent k + 11, item bound, items)
 };
 
 // cp.async of 4 bytes global -> shared (completion awaited with cp_async_wait)
@@ -90,8 +94,19 @@ struct alignas(16) Staged {
 // Tile index of tile coordinates within one tile of the grid's range
 // ([-1, nt]): the periodic wrap is one compare per axis, no division.
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-__device__ __forceinline__ int tile_of(int tx, int ty, int tz, const GridDev& g) {
-  return wrap1(tx, g.nt[0]) + g.nt[0] * (wrap1(ty, g.nt[1]) + g.nt[1] * wrap1(tz, g.nt[2]));
+__device__ __forceinline__ int tile_of(int tx, int ty, int tz, const TileGeo& t) {
+  return t.base + wrap1(tx, t.nt[0]) + t.nt[0] * (wrap1(ty, t.nt[1]) + t.nt[1] * wrap1(tz, t.nt[2]));
+}
+
+// The call's scale and output field for the structure `inst` (packed plans:
+// its row of the call table).
+template <typename Real>
+__device__ __forceinline__ Real call_scale(const SpreadArgs<Real>& A, int inst) {
+  return A.calls ? (Real)__ldg(&A.calls[inst].s0) : A.scale;
+}
+template <typename Real>
+__device__ __forceinline__ Real* call_field(const SpreadArgs<Real>& A, int inst) {
+  return A.calls ? static_cast<Real*>(A.calls[inst].field) : A.f;
 }
 
 // One lane adds into one face per step and steps are ordered by __syncwarp,
@@ -121,9 +136,11 @@ struct RawItem {
 template <typename Real>
 __device__ __forceinline__ void push_item(const SpreadArgs<Real>& A, int slot, Staged<Real>* stage,
                                           Real* acc, RawItem<Real>* raw, int tid) {
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   const int tile = A.tile_list[slot];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  int tx, ty, tz;
+  tile_coords(geo, tile, tx, ty, tz);
+  const Real scale = call_scale(A, geo.inst);
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
@@ -165,7 +182,7 @@ __device__ __forceinline__ void push_item(const SpreadArgs<Real>& A, int slot, S
         delta_weights(th, st.wy);
         const int bz = cz - z0 + stencil_axis(raw->off[2][i], c != 2, th) + 2;
         delta_weights(th, st.wz);
-        st.val = raw->val[c][i] * A.scale;
+        st.val = raw->val[c][i] * scale;
         st.org = bz * kSZ + by * kSY + bx;
         stage[tid] = st;
       }
@@ -422,11 +439,13 @@ __device__ __forceinline__ void fx_stage(float4* rec, int part, bool store, cons
 // source tiles (each tile's blocks summed into its first block by the
 // accumulation kernel) in the fixed order (oz, oy, ox), aligned to the
 // destination tile's exponent k_ref (in units of 2^-(k+11)), and is rounded
-// once.  With k'_s = k_s + 11 for source s,
-//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
-// so a source sum (below items_s 2^42) shifted left by k_ref - k'_s stays
-// below 2^59 and eight of them below 2^62; a source with k'_s > k_ref is
-// shifted right (floor).  The conversion splits |S| into two 32-bit halves,
+// once.  With k'_s = k_s + 11 and m_s = ceil(n_s / 512) for source s (n_s
+// points: m_s bounds its work items under any tuning, whose items hold 512
+// to 1024 points),
+//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(m_s))),
+// so a source sum (below m_s 2^42) shifted left by k_ref - k'_s stays below
+// 2^59 and eight of them below 2^62; a source with k'_s > k_ref is shifted
+// right (floor).  k_ref, like k_s, does not depend on the tuning.  The conversion splits |S| into two 32-bit halves,
 // each converted exactly rounded, joined by one fma: within one unit in the
 // last place, the same bits for the same integers.
 __device__ __forceinline__ float fx_to_float(long long S, float out_scale) {
@@ -450,7 +469,6 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
   __shared__ int next, last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = A.counters[0];
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
   // this lane's (dz, dy, xh) and its offset within a stencil
   const int ldz = lane >> 3, ldy = (lane >> 1) & 3, lxh = lane & 1;
   const int loff = ldz * kFxSZ + ldy * kFxSY + lxh;
@@ -465,13 +483,15 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int slot = next;
     if (slot >= count) break;
     const int tile = A.tile_list[slot];
-    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    int tx, ty, tz;
+    tile_coords(geo, tile, tx, ty, tz);
     const int t0 = A.tile_start[tile], t1 = A.tile_end[tile];
     const int s = t0 + (slot - A.tile_slot[tile]) * A.chunk;
     const int e = min(t1, s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
     const int4 tsk = A.tile_sk[tile];
-    const float vscale = A.scale * ldexpf(1.f, tsk.y - 11);
+    const float vscale = call_scale(A, geo.inst) * ldexpf(1.f, tsk.y - 11);
     // warp w takes the groups starting at s + kFxGroup (w + 8 j)
     FxRaw raw = {0, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int g0 = s + warp * kFxGroup;
@@ -555,31 +575,30 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
 }
 
 // Per tile (FP32 plans), one thread each: the exponent k of its fixed-point
-// words, its first block slot and its work items, read by every push item of
-// the tile and by the merge of each of its 27 neighbours.
+// words, its first block slot, the bound m = ceil(n / 512) on its work items
+// under any tuning, and its work items; read by every push item of the tile
+// and by the merge of each of its 27 neighbours.
 __global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntiles) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntiles) return;
   const int ns = A.tile_nitems[t];
   const int npts = A.tile_end[t] - A.tile_start[t];
+  const float scale = call_scale(A, A.tile_inst ? __ldg(A.tile_inst + t) : 0);
   A.tile_sk[t] = make_int4(ns > 0 ? A.tile_slot[t] : -1,
-                           ns > 0 ? fx_tile_exp(__ldg(A.tile_vmax + t), npts, A.scale) + 11 : 0,
-                           0, ns);
+                           ns > 0 ? fx_tile_exp(__ldg(A.tile_vmax + t), npts, scale) + 11 : 0,
+                           (npts + kMinChunk - 1) / kMinChunk, ns);
 }
 
 // One CTA per (near tile, component), one thread per face pair, no barrier:
 // lanes 0..26 of each warp load the records of the 27 tiles whose blocks
 // cover the tile, the warp reduces the merge exponent
-//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),
+//   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(m_s))),
 // and each thread takes its up to eight sources' records by shuffle, then
 // loads their blocks together.
 __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
   static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
   const unsigned full = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int n0 = A.g.n[0], n1 = A.g.n[1];
-  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
   const int count = 3 * A.counters[3];
   const longlong2* scratch = reinterpret_cast<const longlong2*>(A.scratch);  // 2 faces each
   // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y)
@@ -591,13 +610,15 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
             nx = (xq == 0 || xq == 3) ? 2 : 1;
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
     const int tile = A.tile_list_near[k / 3], c = k % 3;
-    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    int tx, ty, tz;
+    tile_coords(geo, tile, tx, ty, tz);
     int4 r = make_int4(-1, 0, 0, 0);
     if (lane < 27)
       r = __ldg(A.tile_sk + tile_of(tx + lane % 3 - 1, ty + (lane / 3) % 3 - 1,
-                                    tz + lane / 9 - 1, A.g));
+                                    tz + lane / 9 - 1, geo));
     const int kmax = __reduce_max_sync(full, r.w > 0 ? r.y : -1000);
-    const int kcap = __reduce_min_sync(full, r.w > 0 ? r.y + 17 - ceil_log2(r.w) : 1000);
+    const int kcap = __reduce_min_sync(full, r.w > 0 ? r.y + 17 - ceil_log2(r.z) : 1000);
     const int kref = min(kmax, kcap);
     int2 sk[8];
 #pragma unroll
@@ -628,8 +649,10 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
       t1 += fx_align(v[i].y, kref - sk[i].y);
     }
     const float osc = ldexpf(1.f, -kref);
-    float* row = A.f + c * cells + ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 +
-                 tx * kTile;
+    const int n0 = geo.n[0], n1 = geo.n[1];
+    const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
+    float* row = call_field(A, geo.inst) + c * cells +
+                 ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 + tx * kTile;
     reinterpret_cast<float2*>(row)[xq] = make_float2(fx_to_float(t0, osc), fx_to_float(t1, osc));
   }
 }
@@ -639,18 +662,20 @@ template <typename Real>
 __global__ void __launch_bounds__(kMT) k_spread_zero(SpreadArgs<Real> A) {
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * kMW + (threadIdx.x >> 5);
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  if (tile >= nt0 * nt1 * A.g.nt[2] || A.tile_near[tile]) return;
-  const int n0 = A.g.n[0], n1 = A.g.n[1];
-  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
-  const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+  if (tile >= A.ntiles || A.tile_near[tile]) return;
+  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  int tx, ty, tz;
+  tile_coords(geo, tile, tx, ty, tz);
+  const int n0 = geo.n[0], n1 = geo.n[1];
+  const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
+  Real* const f = call_field(A, geo.inst);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   constexpr int kVec = 16 / sizeof(Real);          // reals per 16-byte store
   constexpr int kPerRow = kTile / kVec;
   for (int idx = lane; idx < 3 * 64 * kPerRow; idx += 32) {
     const int c = idx / (64 * kPerRow), r = (idx / kPerRow) % 64, v = idx % kPerRow;
     const int z = r >> 3, y = r & 7;
-    Real* row = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+    Real* row = f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
     reinterpret_cast<float4*>(row)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
@@ -667,18 +692,19 @@ template <typename Real>
 __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   __shared__ int src_slot[27], src_n[27];
   const int tid = threadIdx.x;
-  const int nt0 = A.g.nt[0], nt1 = A.g.nt[1];
-  const int n0 = A.g.n[0], n1 = A.g.n[1];
-  const int64_t cells = (int64_t)n0 * n1 * A.g.n[2];
   const int count = A.counters[3];
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
     const int tile = A.tile_list_near[k];
-    const int tx = tile % nt0, ty = (tile / nt0) % nt1, tz = tile / (nt0 * nt1);
+    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    int tx, ty, tz;
+    tile_coords(geo, tile, tx, ty, tz);
+    const int n0 = geo.n[0], n1 = geo.n[1];
+    const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
     const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
     __syncthreads();
     if (tid < 27) {
       const int a = tid / 9 - 1, b = (tid / 3) % 3 - 1, c = tid % 3 - 1;
-      const int nb = tile_of(tx + c, ty + b, tz + a, A.g);
+      const int nb = tile_of(tx + c, ty + b, tz + a, geo);
       src_slot[tid] = A.tile_slot[nb];
       src_n[tid] = A.tile_nitems[nb];
     }
@@ -714,7 +740,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
             }
           }
         }
-      Real* out = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+      Real* out = call_field(A, geo.inst) + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
 #pragma unroll
       for (int x = 0; x < 8; ++x) out[x] = sum[x];
     }
@@ -745,9 +771,13 @@ void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
 }
 
 template <typename Real>
-SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f) {
+SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* calls) {
   SpreadArgs<Real> A;
   A.g = p->grid;
+  A.ntiles = p->ntiles;
+  A.inst = p->n_inst > 1 ? p->inst : nullptr;
+  A.tile_inst = p->n_inst > 1 ? p->tile_inst : nullptr;
+  A.calls = calls;
   A.Q = p->Q;
   A.tile_start = p->tile_start;
   A.tile_end = p->tile_end;
@@ -771,8 +801,9 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f) {
 }
 
 template <typename Real>
-ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s) {
-  SpreadArgs<Real> A = spread_args<Real>(p, scale, f);
+ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s,
+                   const GridCall* calls) {
+  SpreadArgs<Real> A = spread_args<Real>(p, scale, f, calls);
   cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
   // far-tile zeros on the side stream, concurrent with the push (unless the
   // caller has already issued them)
@@ -840,17 +871,18 @@ ib_status spread_prepare(ib_plan* p) {
 // zeros, accumulation, merge (FP32: and the merge exponents)
 int spread_launches(int precision) { return precision == IB_FP64 ? 3 : 4; }
 
-ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill) {
-  return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s)
-                                 : spread_t<float>(p, scale, f, zero_fill, s);
+ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill,
+                        const GridCall* calls) {
+  return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s, calls)
+                                 : spread_t<float>(p, scale, f, zero_fill, s, calls);
 }
 
-ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s) {
+ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s, const GridCall* calls) {
   if (p->precision == IB_FP64) {
-    SpreadArgs<double> A = spread_args<double>(p, 1.0, f);
+    SpreadArgs<double> A = spread_args<double>(p, 1.0, f, calls);
     k_spread_zero<double><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
   } else {
-    SpreadArgs<float> A = spread_args<float>(p, 1.0, f);
+    SpreadArgs<float> A = spread_args<float>(p, 1.0, f, calls);
     k_spread_zero<float><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;

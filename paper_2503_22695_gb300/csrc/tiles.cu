@@ -1,5 +1,6 @@
 // Classification of the 8^3-cell Eulerian tiles after the Gauss points have
-// been sorted by tile:
+// been sorted by tile (the tiles of a packed plan are those of all its
+// structures, each with the neighbours on its own periodic grid):
 //   non-empty  the tile holds points              -> spread push / interp work
 //   near       a tile of its 3x3x3 neighbourhood holds points
 //                                                   -> its faces are merged
@@ -18,7 +19,9 @@ namespace {
 
 constexpr int kT = 256;  // tiles per CTA
 
-__global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __restrict__ start,
+__global__ void __launch_bounds__(kT) k_classify(GridDev g, const InstDev* __restrict__ inst,
+                                                 const int32_t* __restrict__ tile_inst,
+                                                 const int32_t* __restrict__ start,
                                                  const int32_t* __restrict__ end, int ntiles,
                                                  int32_t* __restrict__ nonempty,
                                                  int32_t* __restrict__ near,
@@ -27,8 +30,10 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
   const int t = blockIdx.x * kT + threadIdx.x;
   int ne = 0, nr = 0, nch = 0, npt = 0;
   if (t < ntiles) {
-    const int nt0 = g.nt[0], nt1 = g.nt[1], nt2 = g.nt[2];
-    const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
+    const TileGeo geo = tile_geo(g, inst, tile_inst, t);
+    const int nt0 = geo.nt[0], nt1 = geo.nt[1], nt2 = geo.nt[2];
+    int tx, ty, tz;
+    tile_coords(geo, t, tx, ty, tz);
     npt = end[t] - start[t];
     ne = npt > 0;
     nch = (npt + chunk - 1) / chunk;
@@ -36,8 +41,8 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const int32_t* __res
     for (int a = -1; a <= 1 && !nr; ++a)
       for (int b = -1; b <= 1 && !nr; ++b)
         for (int c = -1; c <= 1 && !nr; ++c) {
-          const int nb =
-              wrap_idx(tx + c, nt0) + nt0 * (wrap_idx(ty + b, nt1) + nt1 * wrap_idx(tz + a, nt2));
+          const int nb = geo.base + wrap_idx(tx + c, nt0) +
+                         nt0 * (wrap_idx(ty + b, nt1) + nt1 * wrap_idx(tz + a, nt2));
           nr = end[nb] > start[nb];
         }
     nonempty[t] = nch;
@@ -124,8 +129,10 @@ int64_t max_work_items(int ntiles, int64_t Q) { return ntiles + Q / kMinChunk + 
 
 ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s) {
   const int nt = p->ntiles, nb = classify_blocks(nt);
-  k_classify<<<nb, kT, 0, s>>>(p->grid, p->tile_start, p->tile_end, nt, p->tile_nonempty,
-                               p->tile_near, p->tile_bcount, p->chunk);
+  const bool packed = p->n_inst > 1;
+  k_classify<<<nb, kT, 0, s>>>(p->grid, packed ? p->inst : nullptr,
+                               packed ? p->tile_inst : nullptr, p->tile_start, p->tile_end, nt,
+                               p->tile_nonempty, p->tile_near, p->tile_bcount, p->chunk);
   k_compact<<<nb, kT, 0, s>>>(p->tile_nonempty, p->tile_near, nt, p->tile_bcount, nb,
                               p->tile_start, p->tile_end, p->tile_slot, p->tile_list,
                               p->tile_list_near, p->tile_counters);

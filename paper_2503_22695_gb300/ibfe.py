@@ -99,6 +99,7 @@ def _load():
         "ib_batch_forward": [vp, vp],
         "ib_batch_adjoint": [vp, vp],
         "ib_batch_gparams": [vp, dp, vp],
+        "ib_batch_get_tuning": [vp, C.POINTER(i32)],
         "ib_batch_destroy": [vp],
         "ib_fe_energy_noalloc": [C.POINTER(_Mesh), C.POINTER(_Mat), i32, C.POINTER(_Pos),
                                  C.c_double, vp, vp],
@@ -533,7 +534,9 @@ def ib_fe_energy_noalloc(conn, X, mats, x: Pos, h: float, energy, fibres=None, m
 
 
 class Batch:
-    """Independent structures run as the branches of one captured CUDA graph.
+    """Independent hexahedral structures, each on its own grid, packed into one
+    plan: every stage is one launch over all of them, and the forward and the
+    backward are each one captured CUDA graph.
 
     `instances` is a list of dicts with the device tensors of each structure:
     conn, X, fibres (or None), mat_id (or None), n, h, origin, mats (list of
@@ -577,6 +580,13 @@ class Batch:
 
     def adjoint(self):
         _chk(_lib.ib_batch_adjoint(self._h, _stream()), "ib_batch_adjoint")
+
+    def tuning(self):
+        """The packed plan's tuning (points per work item, force CTAs per SM,
+        spreading and interpolation CTA caps per SM)."""
+        t = (C.c_int32 * 4)()
+        _chk(_lib.ib_batch_get_tuning(self._h, t), "ib_batch_get_tuning")
+        return list(t)
 
     def gparams(self):
         out = (C.c_double * (self.n * IB_MAX_MATERIALS * IB_PARAM_ROW))()

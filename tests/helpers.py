@@ -61,3 +61,41 @@ class Case:
 
 def np_(t):
     return t.detach().double().cpu().numpy()
+
+
+def hex_fibre_stretch(prob, x):
+    """I4 - 1 = |F e|^2 - 1 of the fibre (e_f) and sheet (e_s) directions at the
+    2x2x2 Gauss points of a trilinear hexahedral mesh (VTK corner order), in
+    FP64: arrays [8][E] each.  F = (dx/dxi)(dX/dxi)^-1 from the shape-function
+    gradients at xi = +-1/sqrt(3)."""
+    sg = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                   [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], float)
+    g = 1.0 / np.sqrt(3.0)
+    X = prob.X.astype(np.float64)
+    ef = prob.fibres[0:3].astype(np.float64)
+    es = prob.fibres[3:6].astype(np.float64)
+    d4f, d4s = [], []
+    for q in range(8):
+        xi = np.array([(1 if (q >> k) & 1 else -1) * g for k in range(3)])
+        f = (1 + sg * xi) / 2                                   # [8 corners][3]
+        dN = np.stack([sg[:, k] / 2 * np.prod(np.delete(f, k, axis=1), axis=1)
+                       for k in range(3)], axis=1)              # dN_a/dxi_k
+        J0 = np.einsum('iae,ak->eik', X[:, prob.conn], dN)
+        Jx = np.einsum('iae,ak->eik', x[:, prob.conn], dN)
+        F = Jx @ np.linalg.inv(J0)
+        for e_dir, out in ((ef, d4f), (es, d4s)):
+            Fe = np.einsum('eij,je->ei', F, e_dir)
+            out.append((Fe ** 2).sum(axis=1) - 1.0)
+    return np.array(d4f), np.array(d4s)
+
+
+def kink_nodes(prob, x, band=5e-7):
+    """Nodes of the elements with a Gauss point whose fibre or sheet stretch
+    lies within `band` of 1.  The tension-only fibre terms make the Hessian
+    jump at I4 = 1; an FP32 evaluation within rounding of the kink may take
+    either branch, and both are valid for inputs within that rounding (the
+    FP32 displacement gradient moves I4 - 1 by about 1.4e-7 on these
+    meshes; the default band is 3.5 times that)."""
+    d4f, d4s = hex_fibre_stretch(prob, x)
+    near = ((np.abs(d4f) < band) | (np.abs(d4s) < band)).any(axis=0)
+    return np.unique(prob.conn[:, near])

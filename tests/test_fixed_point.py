@@ -15,7 +15,8 @@ keeps every contribution below 2^21 and |H| below 2^31 (1024: the largest
 work item any tuning may choose, so the exponent does not depend on the
 tuning).  The merge sums a face's S per source tile in 64 bits, shifts the
 source sums to one exponent (units of 2^-(k+11))
-    k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(items_s))),  k'_s = k_s + 11,
+    k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(m_s))),  k'_s = k_s + 11,
+(m_s = ceil(n_s / 512) bounds source s's work items under any tuning),
 and converts the total with two exactly rounded 32-bit halves and one fma.
 These tests restate that arithmetic with exact rationals and check each
 claim: the split, the exactness of z, the decoding under wrap-around, the
@@ -190,9 +191,14 @@ def test_merge_alignment_headroom_and_conversion():
     for _ in range(400):
         nsrc = rng.randint(1, 8)
         ks = [rng.randint(-40, 60) + 11 for _ in range(nsrc)]
-        items = [rng.choice([1, 1, 2, 3, 17, 200]) for _ in range(nsrc)]
+        # a source tile of npts points, cut into work items of 512..1024
+        # points by the tuning; the cap uses the tuning-free bound m
+        npts = [rng.choice([1, 300, 1024, 1500, 9000, 102400]) for _ in range(nsrc)]
+        items = [-(-n // rng.choice([512, 700, 1024])) for n in npts]
+        m = [-(-n // 512) for n in npts]
+        assert all(i <= b for i, b in zip(items, m))
         kmax = max(ks)
-        kcap = min(k + 17 - ceil_log2(n) for k, n in zip(ks, items))
+        kcap = min(k + 17 - ceil_log2(b) for k, b in zip(ks, m))
         k_ref = min(kmax, kcap)
         total = 0
         exact = Fr(0)
