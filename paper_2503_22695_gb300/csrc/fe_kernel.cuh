@@ -322,8 +322,10 @@ __device__ __forceinline__ T sum8(T v) {
 // evaluating Gauss point g; the corner data are exchanged by shuffles, and
 // lane g writes corner g's force (valid = false: a lane of a padding element
 // takes part in the shuffles and stores nothing).
+// kPacked: an element of a packed plan (its instance's h; its material row in
+// the device table); false: the plan's h and the table passed by value.
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl,
-          bool kLanes = false>
+          bool kLanes = false, bool kPacked = false>
 __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable& mt, int e,
                                            bool valid = true) {
   using EL = El<kEl>;
@@ -337,8 +339,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   // reference and current coordinates relative to corner 0 (kLanes: this
   // lane's corner only; the others arrive by shuffles)
   constexpr int kNodes = kLanes ? 1 : EL::C;
-  // grid spacing of the element's structure (packed plans: its instance's)
-  const Real h = A.inst ? Real(__ldg(&A.inst[__ldg(A.elem_inst + e)].h)) : A.h;
+  // grid spacing of the element's structure
+  Real h = A.h;
+  if constexpr (kPacked) h = Real(__ldg(&A.inst[__ldg(A.elem_inst + e)].h));
   Real dX[kNodes][3], du[kNodes][3];
   Real vv[kAdj ? kNodes : 1][3];
   {
@@ -394,23 +397,16 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   }
 
   const int mid = A.mat_id ? __ldg(A.mat_id + e) : 0;
-  // the material row, from the table passed by value or (packed plans) from
-  // the device table, read in two separate blocks so that no later read
-  // selects between the sources
+  // the material row: the table passed by value, or the device table
   int model;
-  Real mp[kParamRow];
-  if (A.mats) {
-    const MatRow* r = A.mats + mid;
-    model = __ldg(&r->model);
-#pragma unroll
-    for (int k = 0; k < kParamRow; ++k) mp[k] = Real(__ldg(&r->p[k]));
-  } else {
+  if constexpr (kPacked)
+    model = __ldg(&A.mats[mid].model);
+  else
     model = mt.model[mid];
-#pragma unroll
-    for (int k = 0; k < kParamRow; ++k) mp[k] = Real(mt.p[mid][k]);
-  }
-  // the row in double (the energy's terms)
-  const auto prm = [&](int k) -> double { return A.mats ? __ldg(&A.mats[mid].p[k]) : mt.p[mid][k]; };
+  const auto prm = [&](int k) -> double {
+    if constexpr (kPacked) return __ldg(&A.mats[mid].p[k]);
+    return mt.p[mid][k];
+  };
   // the laws this instantiation handles (kLaws bit m: ib_model m; bit
   // kLawActBit: the active term); the host picks an instantiation whose set
   // covers the material table, and every other branch compiles away
@@ -434,15 +430,15 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real esn1r = Real(esn1), efesr = Real(efes);
 
   // material constants (unused entries of a model are never read by its branches)
-  const Real kap = lawNH ? mp[1] : (lawHO ? mp[8] : (lawF2 ? mp[4] : mp[3]));
-  const Real pa = mp[0], pb = mp[1];
-  const Real paf = lawF1 ? mp[1] : mp[2], pbf = lawF1 ? mp[2] : mp[3];
-  const Real pas = mp[4], pbs = mp[5], pafs = mp[6], pbfs = mp[7];
+  const Real kap = Real(prm(lawNH ? 1 : (lawHO ? 8 : (lawF2 ? 4 : 3))));
+  const Real pa = Real(prm(0)), pb = Real(prm(1));
+  const Real paf = Real(prm(lawF1 ? 1 : 2)), pbf = Real(prm(lawF1 ? 2 : 3));
+  const Real pas = Real(prm(4)), pbs = Real(prm(5)), pafs = Real(prm(6)), pbfs = Real(prm(7));
   // active fibre tension (Section 6.1); the parameter adjoint always needs
   // its fibre kinematics for d/dT_a
   static_assert(!kParams || (kLaws & kLawAct), "the parameter adjoint computes d/dT_a");
-  const Real Ta = mp[kTa];
-  const bool act = (kLaws & kLawAct) && (kParams || Ta != Real(0));
+  const Real Ta = Real(prm(kTa));
+  const bool act = (kLaws & kLawAct) && (kParams || prm(kTa) != 0.0);
 
   double en = 0.0;
   Real gp[kParamRow];
@@ -555,7 +551,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
     // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
     // with C e = e + w, w = H e + H^T e + H^T H e (no cancellation for small H)
-    const Real k4 = lawSR ? Real(0.5) * (mp[2] + pa - Real(4) * pb) : Real(0);
+    const Real k4 = lawSR ? Real(0.5) * (Real(prm(2)) + pa - Real(4) * pb) : Real(0);
     const Real c5 = lawSR ? pa - pb : Real(0);
     Real w5[3] = {Real(0), Real(0), Real(0)}, Fw5[3] = {Real(0), Real(0), Real(0)};
     if (has_f) {
@@ -974,7 +970,8 @@ constexpr int fe8_min_blocks() {
   return sizeof(Real) == 8 ? 2 : 4;
 }
 
-template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws>
+template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws,
+          bool kPacked = false>
 __global__ void __launch_bounds__(128, fe8_min_blocks<Real, kAdj>())
     k_fe8(FeArgs<Real> A, MatTable mt) {
   constexpr int kPer = 128 / 8;
@@ -986,7 +983,7 @@ __global__ void __launch_bounds__(128, fe8_min_blocks<Real, kAdj>())
     __syncthreads();
     if (b >= A.E) break;
     const int e = b + (int)(threadIdx.x >> 3);
-    fe_element<Real, S, kEnergy, kAdj, kParams, kLaws, IB_ELEM_HEX8, true>(
+    fe_element<Real, S, kEnergy, kAdj, kParams, kLaws, IB_ELEM_HEX8, true, kPacked>(
         A, mt, e < A.E ? e : A.E - 1, e < A.E);
   }
 }
@@ -1051,11 +1048,24 @@ inline FeArgs<double> make_args<double>(ib_plan* p, const void* xa, const float*
 
 }  // namespace
 
+// The force launch of packed plans (FP32 split, hexahedra, no energy): declared
+// here, defined and instantiated in fe_force_batch.cu only.
+template <bool kAdj, bool kParams, int kLaws>
+ib_status fe_run_packed(ib_plan* p, const MatTable& mt, const void* xa, const float* off,
+                        const void* v, void* out, cudaStream_t s);
+
 // Launch the force kernel for one (precision, output, law set, element) choice.
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
 ib_status fe_run(ib_plan* p, const MatTable& mt, const void* xa, const float* off, const void* v,
                  void* out, cudaStream_t s) {
   if (p->E == 0) return IB_OK;
+  if (p->n_inst > 1) {  // packed plans: FP32 split hexahedra, no energy
+    if constexpr (kEl == IB_ELEM_HEX8 && std::is_same<Real, float>::value &&
+                  std::is_same<S, df>::value && !kEnergy && (kLaws & kLawVolX) == 0)
+      return fe_run_packed<kAdj, kParams, kLaws>(p, mt, xa, off, v, out, s);
+    else
+      return IB_ERR_INVALID_ARG;
+  }
   FeArgs<Real> A = make_args<Real>(p, xa, off, v, out);
   const int threads = 128;
   // elements per CTA step: one per thread, or one per eight lanes (hexahedra)

@@ -181,20 +181,22 @@ __device__ __forceinline__ void unpack_cell(int32_t p, int& x, int& y, int& z) {
   z = (p >> (2 * kPackBits)) & ((1 << kPackBits) - 1);
 }
 
-// Grid of the structure that owns a tile: its sizes, tiles per dimension,
-// first tile and instance number (the plan's own grid, 0 and 0 for a plan
-// of one structure; the packed batch's InstDev row otherwise).
+// Grid of the structure that owns a tile (or an element): its sizes, tiles
+// per dimension, first tile and instance number.  kPacked false: a plan of
+// one structure, its own grid, 0 and 0 (compile-time; nothing is loaded);
+// true: the packed batch's InstDev row of table[idx].
 struct TileGeo {
   int n[3];
   int nt[3];
   int base;
   int inst;
 };
+template <bool kPacked>
 __device__ __forceinline__ TileGeo tile_geo(const GridDev& g, const InstDev* inst,
-                                            const int32_t* tile_inst, int tile) {
+                                            const int32_t* table, int idx) {
   TileGeo t;
-  if (inst) {
-    const int i = __ldg(tile_inst + tile);
+  if constexpr (kPacked) {
+    const int i = __ldg(table + idx);
     const InstDev* r = inst + i;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

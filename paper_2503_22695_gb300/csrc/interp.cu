@@ -27,6 +27,7 @@
 //   2: b only.
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "ib_device.cuh"
@@ -67,16 +68,23 @@ struct InterpArgs {
   int use_tma;            // FP32: interior tiles staged by the tensor map
 };
 
-// The call's field and scalars for the structure `inst`.
-template <typename Real>
+// The call's field and scalars for the structure `inst` (packed plans: its
+// row of the call table; a plan of one structure: the arguments).
+template <bool kPacked, typename Real>
 __device__ __forceinline__ const Real* call_u(const InterpArgs<Real>& A, int inst) {
-  return A.calls ? static_cast<const Real*>(A.calls[inst].field) : A.u;
+  if constexpr (kPacked) return static_cast<const Real*>(A.calls[inst].field);
+  return A.u;
 }
-template <typename Real>
+template <bool kPacked, typename Real>
 __device__ __forceinline__ void call_scales(const InterpArgs<Real>& A, int inst, Real& vs,
                                             Real& gs) {
-  vs = A.calls ? (Real)__ldg(&A.calls[inst].s0) : A.vscale;
-  gs = A.calls ? (Real)__ldg(&A.calls[inst].s1) : A.gscale;
+  if constexpr (kPacked) {
+    vs = (Real)__ldg(&A.calls[inst].s0);
+    gs = (Real)__ldg(&A.calls[inst].s1);
+  } else {
+    vs = A.vscale;
+    gs = A.gscale;
+  }
 }
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -92,15 +100,15 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // Copy the halo'd 12^3 block of each velocity component around the tile of
 // work item `slot` (faces local -2..9, periodically wrapped) into `ub`,
 // asynchronously: 16 lanes per 12-face x-row, 16 rows per pass.
-template <typename Real>
+template <bool kPacked, typename Real>
 __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot, Real* ub, int tid) {
   const int tile = A.tile_list[slot];
-  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
   int tx, ty, tz;
   tile_coords(geo, tile, tx, ty, tz);
   const int n0 = geo.n[0], n1 = geo.n[1], n2 = geo.n[2];
   const int64_t cells = (int64_t)n0 * n1 * n2;
-  const Real* const u = call_u(A, geo.inst);
+  const Real* const u = call_u<kPacked>(A, geo.inst);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   const int bx = tid & 15;
   if (bx >= kB) return;
@@ -120,7 +128,7 @@ __device__ __forceinline__ void stage_block(const InterpArgs<Real>& A, int slot,
   }
 }
 
-template <typename Real, int MODE>
+template <typename Real, int MODE, bool kPacked>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
                                               int tid);
 template <typename Real, int MODE>
@@ -130,7 +138,7 @@ __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real
 
 // Persistent CTAs, two-stage pipeline: the velocity block of the next work
 // item is fetched while the points of the current one are evaluated.
-template <typename Real, int MODE>
+template <typename Real, int MODE, bool kPacked>
 __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* const buf0 = reinterpret_cast<Real*>(smem_raw);
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
   if (tid == 0) next = atomicAdd(A.counters + 2, 1);
   __syncthreads();
   int cur = next;
-  if (cur < count) stage_block(A, cur, buf0, tid);
+  if (cur < count) stage_block<kPacked>(A, cur, buf0, tid);
   cp_async_commit();
   int b = 0;
   while (cur < count) {
@@ -148,11 +156,11 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
     if (tid == 0) next = atomicAdd(A.counters + 2, 1);
     __syncthreads();
     const int nxt = next;
-    if (nxt < count) stage_block(A, nxt, buf0 + (b ^ 1) * 3 * kComp, tid);
+    if (nxt < count) stage_block<kPacked>(A, nxt, buf0 + (b ^ 1) * 3 * kComp, tid);
     cp_async_commit();
     cp_async_wait_group<1>();  // the current item's block has landed
     __syncthreads();
-    interp_points<Real, MODE>(A, cur, buf0 + b * 3 * kComp, tid);
+    interp_points<Real, MODE, kPacked>(A, cur, buf0 + b * 3 * kComp, tid);
     cur = nxt;
     b ^= 1;
   }
@@ -254,14 +262,14 @@ struct PtStage {
   short lc[kChunk];  // local cell: x + 8 y + 64 z
 };
 
-template <int MODE>
+template <int MODE, bool kPacked>
 __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int slot, int* cnt,
                                                 PtStage<MODE>& P, int* tmp, int tid) {
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
   int tx, ty, tz;
-  tile_coords(tile_geo(A.g, A.inst, A.tile_inst, tile), tile, tx, ty, tz);
+  tile_coords(tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile), tile, tx, ty, tz);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   cnt[tid] = 0;
   cnt[tid + kThreads] = 0;
@@ -306,7 +314,7 @@ __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int 
 // padded block, issue the next item's box, evaluate the points
 // (shared memory holds 3 CTAs per SM in mode 0 and 2 in the gradient modes;
 // the register bounds follow)
-template <int MODE>
+template <int MODE, bool kPacked>
 __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
     k_interp_tma(const __grid_constant__ CUtensorMap tmap, InterpArgs<float> A) {
   extern __shared__ unsigned char smem_raw[];
@@ -330,8 +338,10 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
   __syncthreads();
   int cur = next;
   // the tile of an item, its structure's grid and tensor map
-  auto geo_of = [&](int item) { return tile_geo(A.g, A.inst, A.tile_inst, A.tile_list[item]); };
-  auto map_of = [&](const TileGeo& g) { return A.tmaps ? A.tmaps + g.inst : &tmap; };
+  auto geo_of = [&](int item) {
+    return tile_geo<kPacked>(A.g, A.inst, A.tile_inst, A.tile_list[item]);
+  };
+  auto map_of = [&](const TileGeo& g) { return kPacked ? A.tmaps + g.inst : &tmap; };
   // only the instance of the current item is carried across iterations
   int cinst = 0;
   bool cur_tma = false;
@@ -340,17 +350,17 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
     cinst = g.inst;
     cur_tma = tile_interior(g, A.tile_list[cur]);
     if (tid == 0 && cur_tma)
-      issue_box(map_of(g), A.tmaps != nullptr, g, A.tile_list[cur], dense_s, bar);
+      issue_box(map_of(g), kPacked, g, A.tile_list[cur], dense_s, bar);
   }
   uint32_t parity = 0;
   while (cur < count) {
-    const int np = local_cell_stage<MODE>(A, cur, cnt, pts, tmp, tid);  // box in flight
+    const int np = local_cell_stage<MODE, kPacked>(A, cur, cnt, pts, tmp, tid);  // box in flight
     // thread 0 alone waits (bounded) for the box; the barrier below hands
     // the landed data and the outcome to the CTA
     if (cur_tma) {
       if (tid == 0 && !mbar_wait(bar, parity)) abort_flag = 1;
     } else {
-      stage_block(A, cur, ub, tid);
+      stage_block<kPacked>(A, cur, ub, tid);
       cp_async_commit();
       cp_async_wait_group<0>();
     }
@@ -370,10 +380,10 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
       ninst = g.inst;
       nxt_tma = tile_interior(g, A.tile_list[nxt]);
       if (tid == 0 && nxt_tma)
-        issue_box(map_of(g), A.tmaps != nullptr, g, A.tile_list[nxt], dense_s, bar);
+        issue_box(map_of(g), kPacked, g, A.tile_list[nxt], dense_s, bar);
     }
     float vs, gs;
-    call_scales(A, cinst, vs, gs);
+    call_scales<kPacked>(A, cinst, vs, gs);
     // the points in cell order, from the staged copy
     for (int j = tid; j < np; j += kThreads) {
       const int c = pts.lc[j];
@@ -470,18 +480,18 @@ __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real
 }
 
 // The points of work item `slot`, read from global memory in binned order.
-template <typename Real, int MODE>
+template <typename Real, int MODE, bool kPacked>
 __device__ __forceinline__ void interp_points(const InterpArgs<Real>& A, int slot, const Real* ub,
                                               int tid) {
   const int tile = A.tile_list[slot];
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
-  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
   int tx, ty, tz;
   tile_coords(geo, tile, tx, ty, tz);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   Real vs, gs;
-  call_scales(A, geo.inst, vs, gs);
+  call_scales<kPacked>(A, geo.inst, vs, gs);
   for (int i = s + tid; i < e; i += kThreads) {
     int cx, cy, cz;
     unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
@@ -545,6 +555,7 @@ template <typename Real>
 ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gscale,
                    cudaStream_t s, const GridCall* calls, const CUtensorMap* tmaps) {
   if (p->Q == 0) return IB_OK;
+  if ((p->n_inst > 1) != (calls != nullptr)) return IB_ERR_INVALID_ARG;
   InterpArgs<Real> A;
   A.g = p->grid;
   A.inst = p->n_inst > 1 ? p->inst : nullptr;
@@ -576,71 +587,75 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   auto cap = [cap_ctas](int ctas) { return ctas < cap_ctas ? ctas : cap_ctas; };
   const size_t smem = smem_bytes<Real>();
   cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
+  const bool packed = p->n_inst > 1;
   if constexpr (sizeof(Real) == 4) {
     // packed plans: the instances' maps in device memory (this one unused)
     CUtensorMap tmap = {};
-    if (p->interp_tma && (calls ? tmaps != nullptr : make_velocity_map(p->grid.n, u, &tmap))) {
+    if (p->interp_tma && (packed ? tmaps != nullptr : make_velocity_map(p->grid.n, u, &tmap))) {
       A.use_tma = 1;
+      auto run = [&](auto kernel, int ctas, size_t smem_b) {
+        kernel<<<cap(ctas), kThreads, smem_b, s>>>(tmap, A);
+      };
       if (mode == 0)
-        k_interp_tma<0><<<cap(p->interp_ctas_tma[0]), kThreads, tma_smem<0>(), s>>>(tmap, A);
+        run(packed ? k_interp_tma<0, true> : k_interp_tma<0, false>, p->interp_ctas_tma[0],
+            tma_smem<0>());
       else if (mode == 1)
-        k_interp_tma<1><<<cap(p->interp_ctas_tma[1]), kThreads, tma_smem<1>(), s>>>(tmap, A);
+        run(packed ? k_interp_tma<1, true> : k_interp_tma<1, false>, p->interp_ctas_tma[1],
+            tma_smem<1>());
       else
-        k_interp_tma<2><<<cap(p->interp_ctas_tma[2]), kThreads, tma_smem<2>(), s>>>(tmap, A);
+        run(packed ? k_interp_tma<2, true> : k_interp_tma<2, false>, p->interp_ctas_tma[2],
+            tma_smem<2>());
       return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
     }
   }
+  auto run = [&](auto kernel, int ctas) { kernel<<<cap(ctas), kThreads, smem, s>>>(A); };
   if (mode == 0)
-    k_interp_tile<Real, 0><<<cap(p->interp_ctas[0]), kThreads, smem, s>>>(A);
+    run(packed ? k_interp_tile<Real, 0, true> : k_interp_tile<Real, 0, false>, p->interp_ctas[0]);
   else if (mode == 1)
-    k_interp_tile<Real, 1><<<cap(p->interp_ctas[1]), kThreads, smem, s>>>(A);
+    run(packed ? k_interp_tile<Real, 1, true> : k_interp_tile<Real, 1, false>, p->interp_ctas[1]);
   else
-    k_interp_tile<Real, 2><<<cap(p->interp_ctas[2]), kThreads, smem, s>>>(A);
+    run(packed ? k_interp_tile<Real, 2, true> : k_interp_tile<Real, 2, false>, p->interp_ctas[2]);
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+// Dynamic shared memory opt-in of a kernel and its CTAs per SM (0 on error).
+template <typename K>
+int opt_in(K kernel, size_t smem) {
+  int n = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, smem) != cudaSuccess)
+    return 0;
+  return n;
 }
 
 template <typename Real>
 ib_status prepare_t(ib_plan* p) {
-  const int smem = (int)smem_bytes<Real>();
-  int per_sm[3] = {0, 0, 0};
-  if (cudaFuncSetAttribute(k_interp_tile<Real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_interp_tile<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_interp_tile<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_interp_tile<Real, 0>, kThreads,
-                                                    smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_interp_tile<Real, 1>, kThreads,
-                                                    smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_interp_tile<Real, 2>, kThreads,
-                                                    smem) != cudaSuccess)
-    return IB_ERR_CUDA;
+  // both variants of each kernel (one structure, packed); the persistent
+  // grids take the smaller occupancy of the two
+  const size_t smem = smem_bytes<Real>();
+  const int per_sm[3] = {
+      std::min(opt_in(k_interp_tile<Real, 0, false>, smem), opt_in(k_interp_tile<Real, 0, true>, smem)),
+      std::min(opt_in(k_interp_tile<Real, 1, false>, smem), opt_in(k_interp_tile<Real, 1, true>, smem)),
+      std::min(opt_in(k_interp_tile<Real, 2, false>, smem), opt_in(k_interp_tile<Real, 2, true>, smem))};
   for (int m = 0; m < 3; ++m) {
     if (per_sm[m] < 1) return IB_ERR_CUDA;
     p->interp_ctas[m] = p->sm_count * per_sm[m];
   }
   p->interp_tma = 0;
   if constexpr (sizeof(Real) == 4) {
-    int tma_sm[3] = {0, 0, 0};
-    if (encode_tiled() &&
-        cudaFuncSetAttribute(k_interp_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<0>()) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(k_interp_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<1>()) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(k_interp_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<2>()) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[0], k_interp_tma<0>, kThreads, tma_smem<0>()) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[1], k_interp_tma<1>, kThreads, tma_smem<1>()) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tma_sm[2], k_interp_tma<2>, kThreads, tma_smem<2>()) ==
-            cudaSuccess &&
-        tma_sm[0] > 0 && tma_sm[1] > 0 && tma_sm[2] > 0) {
-      for (int m = 0; m < 3; ++m) p->interp_ctas_tma[m] = p->sm_count * tma_sm[m];
-      p->interp_tma = 1;
+    if (encode_tiled()) {
+      const int tma_sm[3] = {
+          std::min(opt_in(k_interp_tma<0, false>, tma_smem<0>()), opt_in(k_interp_tma<0, true>, tma_smem<0>())),
+          std::min(opt_in(k_interp_tma<1, false>, tma_smem<1>()), opt_in(k_interp_tma<1, true>, tma_smem<1>())),
+          std::min(opt_in(k_interp_tma<2, false>, tma_smem<2>()), opt_in(k_interp_tma<2, true>, tma_smem<2>()))};
+      if (tma_sm[0] > 0 && tma_sm[1] > 0 && tma_sm[2] > 0) {
+        for (int m = 0; m < 3; ++m) p->interp_ctas_tma[m] = p->sm_count * tma_sm[m];
+        p->interp_tma = 1;
+      }
     }
   }
+  cudaGetLastError();
   return IB_OK;
 }
 

@@ -77,14 +77,14 @@ __device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, con
   }
 }
 
-template <typename Real, bool kBin, int kEl>
+template <typename Real, bool kBin, int kEl, bool kPacked>
 __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.E) return;
   const int E = A.E;
   const int64_t Q = (int64_t)EL::Q * E;
-  const TileGeo geo = tile_geo(A.g, A.inst, A.elem_inst, e);  // the element's grid
+  const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.elem_inst, e);  // the element's grid
   int c0[3];
   Real o0[3];
   Real dl[EL::C][3];
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_points_nodal(PtArgs<Real> A) {
     }
   }
   // (packed plans hold Gauss-rule structures only: the plan's grid)
-  const TileGeo geo = tile_geo(A.g, nullptr, nullptr, 0);
+  const TileGeo geo = tile_geo<false>(A.g, nullptr, nullptr, 0);
   int cw[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -242,10 +242,13 @@ __device__ __forceinline__ void tile_vmax_update(uint32_t* vmax, uint32_t tile, 
 }
 
 // Binned copies of the carried values (and, for FP32 plans, the per-tile
-// maxima of their magnitudes; the tile of a binned point is its binning key).
-template <typename Real>
+// maxima of their magnitudes).  The tile of a binned point: from its cell
+// (one structure), or its binning key, read at its original index (packed
+// plans, whose cells are their instance's).
+template <typename Real, bool kPacked>
 __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
                                  const Real* __restrict__ q_val, Real* __restrict__ p_val,
+                                 const int32_t* __restrict__ p_cell, GridDev g,
                                  const uint32_t* __restrict__ key,
                                  uint32_t* __restrict__ vmax) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,7 +260,18 @@ __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
     v[d] = __ldg(q_val + d * Q + gi);
     p_val[d * Q + i] = v[d];
   }
-  if constexpr (sizeof(Real) == 4) tile_vmax_update(vmax, __ldg(key + gi), v[0], v[1], v[2]);
+  if constexpr (sizeof(Real) == 4) {
+    uint32_t tile;
+    if constexpr (kPacked) {
+      tile = __ldg(key + gi);
+    } else {
+      int cx, cy, cz;
+      unpack_cell(__ldg(p_cell + i), cx, cy, cz);
+      tile = (uint32_t)((cx >> kTileShift) +
+                        g.nt[0] * ((cy >> kTileShift) + g.nt[1] * (cz >> kTileShift)));
+    }
+    tile_vmax_update(vmax, tile, v[0], v[1], v[2]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +475,11 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
     k_points_nodal<float, true><<<(p->N + 255) / 256, 256, 0, s>>>(A);
   else
     with_elem(p->elem, [&](auto el) {
-      k_points<float, true, decltype(el)::value><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+      constexpr int kE = decltype(el)::value;
+      if (p->n_inst > 1)
+        k_points<float, true, kE, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+      else
+        k_points<float, true, kE, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
     });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
@@ -494,7 +512,7 @@ ib_status points_t<double>(ib_plan* p, const void* xa, const float*, const void*
     k_points_nodal<double, false><<<(p->N + 255) / 256, 256, 0, s>>>(A);
   else
     with_elem(p->elem, [&](auto el) {
-      k_points<double, false, decltype(el)::value><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+      k_points<double, false, decltype(el)::value, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
     });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
@@ -581,12 +599,14 @@ ib_status launch_permute_values(ib_plan* p, cudaStream_t s) {
   if (p->Q == 0) return IB_OK;
   const int nb = (int)((p->Q + 255) / 256);
   if (p->precision == IB_FP64) {
-    k_permute_values<double><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
-                                                (double*)p->p_val, nullptr, nullptr);
+    k_permute_values<double, false><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
+                                                       (double*)p->p_val, p->p_cell, p->grid,
+                                                       nullptr, nullptr);
   } else {
     cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
-    k_permute_values<float><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val,
-                                               (float*)p->p_val, p->keys[0], p->tile_vmax);
+    auto permute = p->n_inst > 1 ? k_permute_values<float, true> : k_permute_values<float, false>;
+    permute<<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val, (float*)p->p_val,
+                               p->p_cell, p->grid, p->keys[0], p->tile_vmax);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }

@@ -99,14 +99,16 @@ __device__ __forceinline__ int tile_of(int tx, int ty, int tz, const TileGeo& t)
 }
 
 // The call's scale and output field for the structure `inst` (packed plans:
-// its row of the call table).
-template <typename Real>
+// its row of the call table; a plan of one structure: the arguments).
+template <bool kPacked, typename Real>
 __device__ __forceinline__ Real call_scale(const SpreadArgs<Real>& A, int inst) {
-  return A.calls ? (Real)__ldg(&A.calls[inst].s0) : A.scale;
+  if constexpr (kPacked) return (Real)__ldg(&A.calls[inst].s0);
+  return A.scale;
 }
-template <typename Real>
+template <bool kPacked, typename Real>
 __device__ __forceinline__ Real* call_field(const SpreadArgs<Real>& A, int inst) {
-  return A.calls ? static_cast<Real*>(A.calls[inst].field) : A.f;
+  if constexpr (kPacked) return static_cast<Real*>(A.calls[inst].field);
+  return A.f;
 }
 
 // One lane adds into one face per step and steps are ordered by __syncwarp,
@@ -137,10 +139,10 @@ template <typename Real>
 __device__ __forceinline__ void push_item(const SpreadArgs<Real>& A, int slot, Staged<Real>* stage,
                                           Real* acc, RawItem<Real>* raw, int tid) {
   const int tile = A.tile_list[slot];
-  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  const TileGeo geo = tile_geo<false>(A.g, nullptr, nullptr, tile);  // FP64: one structure
   int tx, ty, tz;
   tile_coords(geo, tile, tx, ty, tz);
-  const Real scale = call_scale(A, geo.inst);
+  const Real scale = A.scale;
   const int s = A.tile_start[tile] + (slot - A.tile_slot[tile]) * A.chunk;
   const int e = min(A.tile_end[tile], s + A.chunk);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
@@ -460,6 +462,7 @@ __device__ __forceinline__ long long fx_align(long long v, int sh) {
   return sh >= 0 ? (long long)((unsigned long long)v << sh) : (v >> min(-sh, 63));
 }
 
+template <bool kPacked>
 __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* groups = reinterpret_cast<float4*>(smem_raw);
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int slot = next;
     if (slot >= count) break;
     const int tile = A.tile_list[slot];
-    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
     int tx, ty, tz;
     tile_coords(geo, tile, tx, ty, tz);
     const int t0 = A.tile_start[tile], t1 = A.tile_end[tile];
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
     const int e = min(t1, s + A.chunk);
     const int lc0[3] = {tx * kTile, ty * kTile, tz * kTile};
     const int4 tsk = A.tile_sk[tile];
-    const float vscale = call_scale(A, geo.inst) * ldexpf(1.f, tsk.y - 11);
+    const float vscale = call_scale<kPacked>(A, geo.inst) * ldexpf(1.f, tsk.y - 11);
     // warp w takes the groups starting at s + kFxGroup (w + 8 j)
     FxRaw raw = {0, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int g0 = s + warp * kFxGroup;
@@ -578,12 +581,13 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
 // words, its first block slot, the bound m = ceil(n / 512) on its work items
 // under any tuning, and its work items; read by every push item of the tile
 // and by the merge of each of its 27 neighbours.
+template <bool kPacked>
 __global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntiles) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntiles) return;
   const int ns = A.tile_nitems[t];
   const int npts = A.tile_end[t] - A.tile_start[t];
-  const float scale = call_scale(A, A.tile_inst ? __ldg(A.tile_inst + t) : 0);
+  const float scale = call_scale<kPacked>(A, kPacked ? __ldg(A.tile_inst + t) : 0);
   A.tile_sk[t] = make_int4(ns > 0 ? A.tile_slot[t] : -1,
                            ns > 0 ? fx_tile_exp(__ldg(A.tile_vmax + t), npts, scale) + 11 : 0,
                            (npts + kMinChunk - 1) / kMinChunk, ns);
@@ -595,6 +599,7 @@ __global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntil
 //   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(m_s))),
 // and each thread takes its up to eight sources' records by shuffle, then
 // loads their blocks together.
+template <bool kPacked>
 __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
   static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
   const unsigned full = 0xffffffffu;
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
             nx = (xq == 0 || xq == 3) ? 2 : 1;
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
     const int tile = A.tile_list_near[k / 3], c = k % 3;
-    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
     int tx, ty, tz;
     tile_coords(geo, tile, tx, ty, tz);
     int4 r = make_int4(-1, 0, 0, 0);
@@ -651,24 +656,24 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
     const float osc = ldexpf(1.f, -kref);
     const int n0 = geo.n[0], n1 = geo.n[1];
     const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
-    float* row = call_field(A, geo.inst) + c * cells +
+    float* row = call_field<kPacked>(A, geo.inst) + c * cells +
                  ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 + tx * kTile;
     reinterpret_cast<float2*>(row)[xq] = make_float2(fx_to_float(t0, osc), fx_to_float(t1, osc));
   }
 }
 
 // Far tiles: one warp per tile, 3 components x 64 rows x 16-byte zeros.
-template <typename Real>
+template <typename Real, bool kPacked>
 __global__ void __launch_bounds__(kMT) k_spread_zero(SpreadArgs<Real> A) {
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * kMW + (threadIdx.x >> 5);
   if (tile >= A.ntiles || A.tile_near[tile]) return;
-  const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+  const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
   int tx, ty, tz;
   tile_coords(geo, tile, tx, ty, tz);
   const int n0 = geo.n[0], n1 = geo.n[1];
   const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
-  Real* const f = call_field(A, geo.inst);
+  Real* const f = call_field<kPacked>(A, geo.inst);
   const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
   constexpr int kVec = 16 / sizeof(Real);          // reals per 16-byte store
   constexpr int kPerRow = kTile / kVec;
@@ -695,7 +700,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
   const int count = A.counters[3];
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
     const int tile = A.tile_list_near[k];
-    const TileGeo geo = tile_geo(A.g, A.inst, A.tile_inst, tile);
+    const TileGeo geo = tile_geo<false>(A.g, nullptr, nullptr, tile);  // FP64: one structure
     int tx, ty, tz;
     tile_coords(geo, tile, tx, ty, tz);
     const int n0 = geo.n[0], n1 = geo.n[1];
@@ -740,7 +745,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge(SpreadArgs<Real> A) {
             }
           }
         }
-      Real* out = call_field(A, geo.inst) + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
+      Real* out = A.f + c * cells + ((int64_t)(z0 + z) * n1 + (y0 + y)) * n0 + x0;
 #pragma unroll
       for (int x = 0; x < 8; ++x) out[x] = sum[x];
     }
@@ -755,17 +760,20 @@ size_t push_smem() {
 constexpr size_t kFxSmem =
     sizeof(float4) * kFxWarps * kFxGroup * kFxRec + sizeof(unsigned) * 2 * kFxWords;
 
+template <bool kPacked>
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
   cudaMemsetAsync(p->tile_done, 0, sizeof(int32_t) * p->ntiles, s);
-  k_tile_info<<<(p->ntiles + 255) / 256, 256, 0, s>>>(A, p->ntiles);
+  k_tile_info<kPacked><<<(p->ntiles + 255) / 256, 256, 0, s>>>(A, p->ntiles);
   p->prof_calls[IB_STAGE_SPREAD_PUSH] += 1;
   const int ev = prof_begin(p, IB_STAGE_SPREAD_PUSH, s);
-  k_spread_push_fx<<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads, kFxSmem,
-                     s>>>(A);
+  k_spread_push_fx<kPacked><<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kFxThreads,
+                              kFxSmem, s>>>(A);
   prof_end(p, ev, s);
 }
 
+template <bool kPacked>
 void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
+  static_assert(!kPacked, "packed plans are FP32");
   k_spread_push<double><<<std::min(p->push_ctas, p->push_per_sm * p->sm_count), kPT,
                           push_smem<double>(), s>>>(A);
 }
@@ -800,7 +808,7 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* 
   return A;
 }
 
-template <typename Real>
+template <typename Real, bool kPacked>
 ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s,
                    const GridCall* calls) {
   SpreadArgs<Real> A = spread_args<Real>(p, scale, f, calls);
@@ -810,12 +818,12 @@ ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream
   if (zero_fill) {
     cudaEventRecord(p->ev_fork, s);
     cudaStreamWaitEvent(p->zside, p->ev_fork, 0);
-    k_spread_zero<Real><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
+    k_spread_zero<Real, kPacked><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, p->zside>>>(A);
     cudaEventRecord(p->ev_join, p->zside);
   }
-  launch_push(p, A, s);
+  launch_push<kPacked>(p, A, s);
   if constexpr (sizeof(Real) == 4)
-    k_spread_merge_fx<<<p->merge_ctas, kMT, 0, s>>>(A);
+    k_spread_merge_fx<kPacked><<<p->merge_ctas, kMT, 0, s>>>(A);
   else
     k_spread_merge<Real><<<p->merge_ctas, kMT, 0, s>>>(A);
   if (zero_fill) cudaStreamWaitEvent(s, p->ev_join, 0);
@@ -830,11 +838,21 @@ ib_status prepare_t(ib_plan* p) {
     return IB_ERR_CUDA;
   cudaError_t e;
   if (sizeof(Real) == 4) {
-    e = cudaFuncSetAttribute(k_spread_push_fx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // both variants (one structure, packed): the grid takes the smaller
+    // occupancy of the two
+    int per_sm_packed = 0;
+    e = cudaFuncSetAttribute(k_spread_push_fx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kFxSmem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push_fx, kFxThreads,
-                                                        kFxSmem);
+      e = cudaFuncSetAttribute(k_spread_push_fx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kFxSmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_push_fx<false>,
+                                                        kFxThreads, kFxSmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_packed, k_spread_push_fx<true>,
+                                                        kFxThreads, kFxSmem);
+    per_sm = std::min(per_sm, per_sm_packed);
   } else {
     const int smem = (int)push_smem<Real>();
     e = cudaFuncSetAttribute(k_spread_push<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -844,7 +862,8 @@ ib_status prepare_t(ib_plan* p) {
   }
   if (e == cudaSuccess) {
     if constexpr (sizeof(Real) == 4)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge_fx, kMT, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge_fx<false>,
+                                                        kMT, 0);
     else
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_merge, k_spread_merge<Real>, kMT,
                                                         0);
@@ -873,17 +892,25 @@ int spread_launches(int precision) { return precision == IB_FP64 ? 3 : 4; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill,
                         const GridCall* calls) {
-  return p->precision == IB_FP64 ? spread_t<double>(p, scale, f, zero_fill, s, calls)
-                                 : spread_t<float>(p, scale, f, zero_fill, s, calls);
+  if ((p->n_inst > 1) != (calls != nullptr)) return IB_ERR_INVALID_ARG;
+  if (p->precision == IB_FP64)
+    return p->n_inst > 1 ? IB_ERR_INVALID_ARG
+                         : spread_t<double, false>(p, scale, f, zero_fill, s, calls);
+  return p->n_inst > 1 ? spread_t<float, true>(p, scale, f, zero_fill, s, calls)
+                       : spread_t<float, false>(p, scale, f, zero_fill, s, calls);
 }
 
 ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s, const GridCall* calls) {
+  if ((p->n_inst > 1) != (calls != nullptr)) return IB_ERR_INVALID_ARG;
   if (p->precision == IB_FP64) {
     SpreadArgs<double> A = spread_args<double>(p, 1.0, f, calls);
-    k_spread_zero<double><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
+    k_spread_zero<double, false><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
   } else {
     SpreadArgs<float> A = spread_args<float>(p, 1.0, f, calls);
-    k_spread_zero<float><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
+    if (p->n_inst > 1)
+      k_spread_zero<float, true><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
+    else
+      k_spread_zero<float, false><<<(p->ntiles + kMW - 1) / kMW, kMT, 0, s>>>(A);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }

@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kT = 256;  // tiles per CTA
 
+template <bool kPacked>
 __global__ void __launch_bounds__(kT) k_classify(GridDev g, const InstDev* __restrict__ inst,
                                                  const int32_t* __restrict__ tile_inst,
                                                  const int32_t* __restrict__ start,
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const InstDev* __res
   const int t = blockIdx.x * kT + threadIdx.x;
   int ne = 0, nr = 0, nch = 0, npt = 0;
   if (t < ntiles) {
-    const TileGeo geo = tile_geo(g, inst, tile_inst, t);
+    const TileGeo geo = tile_geo<kPacked>(g, inst, tile_inst, t);
     const int nt0 = geo.nt[0], nt1 = geo.nt[1], nt2 = geo.nt[2];
     int tx, ty, tz;
     tile_coords(geo, t, tx, ty, tz);
@@ -129,10 +130,9 @@ int64_t max_work_items(int ntiles, int64_t Q) { return ntiles + Q / kMinChunk + 
 
 ib_status launch_classify_tiles(ib_plan* p, cudaStream_t s) {
   const int nt = p->ntiles, nb = classify_blocks(nt);
-  const bool packed = p->n_inst > 1;
-  k_classify<<<nb, kT, 0, s>>>(p->grid, packed ? p->inst : nullptr,
-                               packed ? p->tile_inst : nullptr, p->tile_start, p->tile_end, nt,
-                               p->tile_nonempty, p->tile_near, p->tile_bcount, p->chunk);
+  auto classify = p->n_inst > 1 ? k_classify<true> : k_classify<false>;
+  classify<<<nb, kT, 0, s>>>(p->grid, p->inst, p->tile_inst, p->tile_start, p->tile_end, nt,
+                             p->tile_nonempty, p->tile_near, p->tile_bcount, p->chunk);
   k_compact<<<nb, kT, 0, s>>>(p->tile_nonempty, p->tile_near, nt, p->tile_bcount, nb,
                               p->tile_start, p->tile_end, p->tile_slot, p->tile_list,
                               p->tile_list_near, p->tile_counters);
