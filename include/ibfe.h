@@ -267,7 +267,7 @@ ib_status ib_backward(ib_plan* plan, const ib_material* mats, int32_t n_mats, co
 /* Launch tuning of a plan, four entries:
  *   [0] points per work item of spreading and interpolation, 512..1024
  *       (a tile's points are cut into items of at most this many);
- *   [1] FE-force CTAs per SM in ib_forward, 1..4 (its persistent grid leaves
+ *   [1] FE-force CTAs per SM in ib_forward, 1..5 (its persistent grid leaves
  *       the rest of each SM to the binning and interpolation beside it);
  *   [2] cap on the spreading CTAs per SM, 1..8;
  *   [3] cap on the interpolation CTAs per SM, 1..8.
@@ -280,7 +280,7 @@ ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
 
 /* Autotuner: times ib_forward on the given inputs for candidate tunings
  * (coordinate descent over the four entries in order: items of 1024 or 512
- * points; 2, 1, 3 or 4 force CTAs per SM; spreading and interpolation caps 8, 3
+ * points; 2, 1, 3, 4 or 5 force CTAs per SM; spreading and interpolation caps 8, 3
  * or 2; one warm-up and the median of three timed calls each) and keeps the
  * fastest.  Writes the choice to `tuning` (host, 4 entries) if non-NULL.
  * Allocates temporary output buffers and synchronises `stream`. */

@@ -772,7 +772,7 @@ ib_status ib_plan_get_tuning(const ib_plan* p, int32_t tuning[4]) {
 
 ib_status ib_plan_set_tuning(ib_plan* p, const int32_t tuning[4]) {
   if (!p || !tuning) return IB_ERR_INVALID_ARG;
-  if (tuning[0] < kMinChunk || tuning[0] > kChunk || tuning[1] < 1 || tuning[1] > 4 ||
+  if (tuning[0] < kMinChunk || tuning[0] > kChunk || tuning[1] < 1 || tuning[1] > 5 ||
       tuning[2] < 1 || tuning[2] > 8 || tuning[3] < 1 || tuning[3] > 8)
     return IB_ERR_INVALID_ARG;
   p->chunk = tuning[0];
@@ -809,12 +809,13 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
   };
   int32_t cur[4];
   ib_plan_get_tuning(p, cur);
-  const int32_t cand[4][4] = {{1024, 512, 0, 0}, {2, 1, 3, 4}, {8, 3, 2, 0}, {8, 3, 2, 0}};
+  const int32_t cand[4][5] = {
+      {1024, 512, 0, 0, 0}, {2, 1, 3, 4, 5}, {8, 3, 2, 0, 0}, {8, 3, 2, 0, 0}};
   for (int k = 0; k < 4 && st == IB_OK; ++k) {
     int32_t best = cur[k];
     float best_ms = 0.f;
     bool first = true;
-    for (int j = 0; j < 4 && cand[k][j] && st == IB_OK; ++j) {
+    for (int j = 0; j < 5 && cand[k][j] && st == IB_OK; ++j) {
       int32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
       trial[k] = cand[k][j];
       ib_plan_set_tuning(p, trial);

@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(128, fe_min_blocks<Real, kAdj>())
 // elements per 128-thread CTA, blocks of elements taken from a counter.
 template <typename Real, bool kAdj>
 constexpr int fe8_min_blocks() {
-  return sizeof(Real) == 8 ? 2 : 4;
+  return sizeof(Real) == 8 ? 2 : (kAdj ? 4 : 5);
 }
 
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws,

@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
       const int src = (lz + iz + 1) * 9 + (ly + iy + 1) * 3 + lx + ix + 1;
       const int slot = __shfl_sync(full, r.x, use ? src : 0);
       const int kx = __shfl_sync(full, r.y, use ? src : 0);
-      sk[i] = make_int2(use ? slot : -1, kx);
+      sk[i] = make_int2(use ? slot : -1, use ? kx : kref);  // unused: value 0, shift 0
     }
     longlong2 v[8];
 #pragma unroll
@@ -647,11 +647,28 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
         v[i] = __ldcg(scratch + (int64_t)sk[i].x * (kFxBlk / 2) + c * (kBlk / 2) + q);
       }
     }
-    long long t0 = 0, t1 = 0;
+    // The upper z sources (i >= 4) cover only the warps of z rows 0, 1, 6, 7
+    // (nz is uniform in a warp: z = tid / 32).  Unless a covering source is
+    // finer than k_ref (a right shift, rare), the warp aligns by left shifts
+    // alone (exact); otherwise it takes the general alignment.
+    bool finer = false;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      t0 += fx_align(v[i].x, kref - sk[i].y);
-      t1 += fx_align(v[i].y, kref - sk[i].y);
+    for (int i = 0; i < 8; ++i) finer |= sk[i].y > kref;
+    long long t0 = 0, t1 = 0;
+    if (!__any_sync(full, finer)) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (i >= 4 && nz == 1) break;
+        const int sh = kref - sk[i].y;  // 0 .. 17
+        t0 += (long long)((unsigned long long)v[i].x << sh);
+        t1 += (long long)((unsigned long long)v[i].y << sh);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        t0 += fx_align(v[i].x, kref - sk[i].y);
+        t1 += fx_align(v[i].y, kref - sk[i].y);
+      }
     }
     const float osc = ldexpf(1.f, -kref);
     const int n0 = geo.n[0], n1 = geo.n[1];

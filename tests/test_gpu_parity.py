@@ -412,11 +412,12 @@ def test_tuning_is_validated_and_changes_no_result():
         c = case(name)
         base = ibfe.ib_plan_get_tuning(c.plan)
         assert base == [1024, 2, 8, 8]
-        for bad in ([256, 2, 8, 8], [1024, 0, 8, 8], [1024, 2, 9, 8], [1024, 2, 8, 0]):
+        for bad in ([256, 2, 8, 8], [1024, 0, 8, 8], [1024, 6, 8, 8], [1024, 2, 9, 8],
+                    [1024, 2, 8, 0]):
             with pytest.raises(ibfe.IBError):
                 ibfe.ib_plan_set_tuning(c.plan, bad)
         ref = [np_(t) for t in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
-        for t in ([512, 1, 3, 2], [768, 3, 2, 3], [1024, 2, 8, 8]):
+        for t in ([512, 1, 3, 2], [768, 3, 2, 3], [1024, 5, 8, 8], [1024, 2, 8, 8]):
             ibfe.ib_plan_set_tuning(c.plan, t)
             assert ibfe.ib_plan_get_tuning(c.plan) == t
             out = [np_(v) for v in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
@@ -427,7 +428,7 @@ def test_tuning_is_validated_and_changes_no_result():
                     assert np.array_equal(a, b)
         chosen = ibfe.ib_plan_autotune(c.plan, c.mats, c.pos, c.u)
         assert chosen == ibfe.ib_plan_get_tuning(c.plan)
-        assert chosen[0] in (1024, 512) and chosen[1] in (1, 2, 3, 4)
+        assert chosen[0] in (1024, 512) and chosen[1] in (1, 2, 3, 4, 5)
         assert chosen[2] in (8, 3, 2) and chosen[3] in (8, 3, 2)
         out = [np_(v) for v in ibfe.ib_forward(c.plan, c.mats, c.pos, c.u)]
         for a, b in zip(out, ref):
