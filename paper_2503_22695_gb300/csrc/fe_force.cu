@@ -13,46 +13,65 @@ namespace {
 // Deterministic per-material sums of per-element partials in two levels.
 // Material m's elements lie in the range mrange[m] (the whole mesh for a
 // plan of one structure; its instance's elements in a packed plan): CTA b
-// reduces chunk b of that range with a fixed-shape tree (warp shuffles, then
-// the warp sums), one (material, value) pair at a time; then one warp per
-// pair sums the per-CTA partials with the same tree.  The partition and the
-// trees depend only on the range, so an instance of a packed plan gets the
-// bits of a plan of its own.
+// reduces chunk b of that range, all values of the material in one pass, each
+// value with its own fixed-shape tree (warp shuffles, then the warp sums; one
+// barrier pair per material); then one warp per (material, value) pair sums
+// the per-CTA partials with the same tree.  The partition and the trees
+// depend only on the range, so an instance of a packed plan gets the bits of
+// a plan of its own.
 __device__ __forceinline__ double warp_tree(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;  // valid in lane 0
 }
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_tree(v);
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (warp == 0) t = warp_tree(lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0);
-  __syncthreads();
-  return t;  // valid in thread 0
-}
-
 constexpr int kRedThreads = 256;
+
+// The block_sum tree for every value k < nvals of a thread at once (one
+// barrier pair for all of them); value k's sum is bitwise the one block_sum
+// forms for it alone.
+__device__ __forceinline__ void block_sum_row(double (&v)[kParamRow], int nvals,
+                                              double (*sh)[kParamRow]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kParamRow; ++k)
+    if (k < nvals) {
+      v[k] = warp_tree(v[k]);
+      if (lane == 0) sh[warp][k] = v[k];
+    }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kParamRow; ++k)
+      if (k < nvals) v[k] = warp_tree(lane < (int)(blockDim.x >> 5) ? sh[lane][k] : 0.0);
+  }
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_l1(const double* __restrict__ part,
                                                            const int32_t* __restrict__ mat_id,
                                                            const int2* __restrict__ mrange,
                                                            int E, int nvals, int n_mats,
                                                            double* __restrict__ rpart) {
-  __shared__ double sh[32];
+  __shared__ double sh[32][kParamRow];
   for (int m = 0; m < n_mats; ++m) {
     const int2 r = mrange[m];
     const int chunk = (r.y - r.x + gridDim.x - 1) / gridDim.x;
     const int e0 = r.x + blockIdx.x * chunk, e1 = min(r.y, e0 + chunk);
-    for (int k = 0; k < nvals; ++k) {
-      double s = 0.0;
-      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-        if ((mat_id ? __ldg(mat_id + e) : 0) == m) s += __ldg(part + (int64_t)k * E + e);
-      s = block_sum(s, sh);
-      if (threadIdx.x == 0) rpart[((int64_t)blockIdx.x * n_mats + m) * kParamRow + k] = s;
+    double s[kParamRow];
+#pragma unroll
+    for (int k = 0; k < kParamRow; ++k) s[k] = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+      if ((mat_id ? __ldg(mat_id + e) : 0) == m) {
+#pragma unroll
+        for (int k = 0; k < kParamRow; ++k)
+          if (k < nvals) s[k] += __ldg(part + (int64_t)k * E + e);
+      }
+    block_sum_row(s, nvals, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kParamRow; ++k)
+        if (k < nvals) rpart[((int64_t)blockIdx.x * n_mats + m) * kParamRow + k] = s[k];
     }
   }
 }
