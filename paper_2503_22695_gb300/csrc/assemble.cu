@@ -41,19 +41,24 @@ __global__ void __launch_bounds__(256) k_node_gather(const int32_t* __restrict__
   }
 }
 
-// out[(a*NC + c)*E + e] = sum_q N_a(xi_q) vals[c][q*E + e]
+// out[(a*NC + c)*E + e] = sum_q N_a(xi_q) w[q*E + e] vals[c][q*E + e]
+// (w: the points' weights w_q j0, or null for 1)
 template <typename Real, int NC, int kEl>
-__global__ void __launch_bounds__(256) k_elem_project(const Real* __restrict__ vals, int E,
+__global__ void __launch_bounds__(256) k_elem_project(const Real* __restrict__ vals,
+                                                      const Real* __restrict__ w, int E,
                                                       Real* __restrict__ out) {
   using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int64_t Q = (int64_t)EL::Q * E;
+  Real wq[EL::Q];
+#pragma unroll
+  for (int q = 0; q < EL::Q; ++q) wq[q] = w ? __ldg(w + (int64_t)q * E + e) : Real(1);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     Real v[EL::Q];
 #pragma unroll
-    for (int q = 0; q < EL::Q; ++q) v[q] = __ldg(vals + c * Q + (int64_t)q * E + e);
+    for (int q = 0; q < EL::Q; ++q) v[q] = __ldg(vals + c * Q + (int64_t)q * E + e) * wq[q];
 #pragma unroll
     for (int a = 0; a < EL::C; ++a) {
       Real s = Real(0);
@@ -173,15 +178,18 @@ ib_status gather_t(ib_plan* p, const void* elem, const void* scale, const void* 
 }
 
 template <typename Real>
-ib_status project_t(ib_plan* p, const void* vals, void* out, int nc, cudaStream_t s) {
+ib_status project_t(ib_plan* p, const void* vals, const void* w, void* out, int nc,
+                    cudaStream_t s) {
   if (p->E == 0) return IB_OK;
   const int blocks = (p->E + 255) / 256;
   with_elem(p->elem, [&](auto el) {
     constexpr int kE = decltype(el)::value;
     if (nc == 3)
-      k_elem_project<Real, 3, kE><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+      k_elem_project<Real, 3, kE><<<blocks, 256, 0, s>>>((const Real*)vals, (const Real*)w,
+                                                         p->E, (Real*)out);
     else
-      k_elem_project<Real, 1, kE><<<blocks, 256, 0, s>>>((const Real*)vals, p->E, (Real*)out);
+      k_elem_project<Real, 1, kE><<<blocks, 256, 0, s>>>((const Real*)vals, (const Real*)w,
+                                                         p->E, (Real*)out);
   });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
@@ -224,7 +232,7 @@ ib_status static_t(ib_plan* p, cudaStream_t s) {
     cudaFree(md);
     return good && cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
-  ib_status st = project_t<Real>(p, p->wj0, p->elem_scratch, 1, s);
+  ib_status st = project_t<Real>(p, p->wj0, nullptr, p->elem_scratch, 1, s);
   if (st != IB_OK) return st;
   st = gather_t<Real>(p, p->elem_scratch, nullptr, nullptr, p->mass, 1, s);
   if (st != IB_OK) return st;
@@ -256,9 +264,11 @@ ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* a
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
-ib_status launch_elem_project(ib_plan* p, const void* vals, void* out, cudaStream_t s) {
-  return p->precision == IB_FP64 ? project_t<double>(p, vals, out, 3, s)
-                                 : project_t<float>(p, vals, out, 3, s);
+ib_status launch_elem_project(ib_plan* p, const void* vals, bool weighted, void* out,
+                              cudaStream_t s) {
+  const void* w = weighted ? p->wj0 : nullptr;
+  return p->precision == IB_FP64 ? project_t<double>(p, vals, w, out, 3, s)
+                                 : project_t<float>(p, vals, w, out, 3, s);
 }
 
 ib_status launch_plan_static(ib_plan* p, cudaStream_t s) {

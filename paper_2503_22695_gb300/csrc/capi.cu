@@ -186,7 +186,9 @@ ib_status do_interp(ib_plan* p, const void* u, int mode, double vs, double gs, c
 
 ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
   Stage sc(p, IB_STAGE_PROJECT, s, 1);
-  return launch_elem_project(p, vals, elem, s);
+  // the interpolated values (gq_a) carry no w_q j0 yet; the position
+  // gradients (gq_b) already have it through the carried values
+  return launch_elem_project(p, vals, vals == p->gq_a, elem, s);
 }
 
 ib_status do_gather(ib_plan* p, const void* elem, const void* scale, void* out, cudaStream_t s,

@@ -256,7 +256,10 @@ ib_status launch_node_copy(ib_plan* p, const void* src, void* out, const void* a
 // out = add + mul node_scale * (gather of elem); add optional (may be out)
 ib_status launch_node_gather(ib_plan* p, const void* elem, const void* node_scale, void* out,
                              cudaStream_t s, const void* add = nullptr, double mul = 1.0);
-ib_status launch_elem_project(ib_plan* p, const void* gq_vals, void* elem_out, cudaStream_t s);
+// weighted: the values are multiplied by the points' w_q j0 first (the
+// interpolated values gq_a; not the position gradients gq_b)
+ib_status launch_elem_project(ib_plan* p, const void* gq_vals, bool weighted, void* elem_out,
+                              cudaStream_t s);
 ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
 
 // points.cu
@@ -283,8 +286,9 @@ size_t spread_scratch_bytes(int precision, int64_t slots);
 int spread_launches(int precision);
 
 // interp.cu
-// mode 0: out_a[gq] = w j0 * sum u prod phi (U^IB times w j0)
-// mode 1: out_a[gq] = w j0 * vscale * sum u prod phi,
+// mode 0: out_a[gq] = vscale * sum u prod phi (U^IB; the projection to the
+//         nodes applies w_q j0)
+// mode 1: out_a[gq] = vscale * sum u prod phi,
 //         out_b[gq] = gscale * sum_c val_c * grad_chi(sum u^c prod phi)
 // mode 2: only out_b (gradient) as in mode 1.
 // calls / tmaps (packed plans): each instance's field, vscale and gscale,

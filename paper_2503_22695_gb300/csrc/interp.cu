@@ -21,8 +21,8 @@
 // Results are written at the point's original index gq = q*E + e for the
 // element-wise projection that follows.
 //
-// Modes
-//   0: a[c][gq] = w j0 * vscale * S_c                      (S_c = sum u^c prod phi)
+// Modes (the projection to the nodes applies the points' w_q j0 to a)
+//   0: a[c][gq] = vscale * S_c                             (S_c = sum u^c prod phi)
 //   1: a as mode 0, and b[d][gq] = gscale * sum_c val_c dS_c/dr_d
 //   2: b only.
 #include <cuda.h>
@@ -59,7 +59,6 @@ struct InterpArgs {
   const Real* p_val;
   const int32_t* p_idx;
   int chunk;               // points per work item
-  const Real* wj0;        // w_q j0 per Gauss point, or null (nodal rule: weight 1)
   const Real* u;
   Real vscale, gscale;
   Real* out_a;
@@ -469,9 +468,8 @@ __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real
     }
   }
   if (MODE != 2) {
-    const Real wq = A.wj0 ? __ldg(A.wj0 + gq) * vs : vs;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = wq * S[c];
+    for (int c = 0; c < 3; ++c) A.out_a[c * A.Q + gq] = vs * S[c];
   }
   if (MODE != 0) {
 #pragma unroll
@@ -574,7 +572,6 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.p_idx = p->p_idx;
   A.chunk = p->chunk;
   // the projection weight w_q j0 of a Gauss point; none for the nodal rule
-  A.wj0 = p->quad == IB_QUAD_NODAL ? nullptr : (const Real*)p->wj0;
   A.u = (const Real*)u;
   A.vscale = (Real)vscale;
   A.gscale = (Real)gscale;
