@@ -593,18 +593,18 @@ __global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntil
                            (npts + kMinChunk - 1) / kMinChunk, ns);
 }
 
-// One CTA per (near tile, component), one thread per face pair, no barrier:
-// lanes 0..26 of each warp load the records of the 27 tiles whose blocks
-// cover the tile, the warp reduces the merge exponent
+// One CTA per near tile, one thread per face pair of each component, no
+// barrier: lanes 0..26 of each warp load the records of the 27 tiles whose
+// blocks cover the tile, the warp reduces the merge exponent
 //   k_ref = min(max_s k'_s, min_s (k'_s + 17 - ceil_log2(m_s))),
-// and each thread takes its up to eight sources' records by shuffle, then
-// loads their blocks together.
+// and each thread takes its up to eight sources' records by shuffle once,
+// then, component by component, loads their blocks together and sums them.
 template <bool kPacked>
-__global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
+__global__ void __launch_bounds__(kMT, 4) k_spread_merge_fx(SpreadArgs<float> A) {
   static_assert(kMT == 8 * 8 * 4, "one thread per face pair of a tile component");
   const unsigned full = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int count = 3 * A.counters[3];
+  const int count = A.counters[3];
   const longlong2* scratch = reinterpret_cast<const longlong2*>(A.scratch);  // 2 faces each
   // this thread's faces: x = 2 xq and 2 xq + 1 of row (z, y)
   const int z = tid >> 5, y = (tid >> 2) & 7, xq = tid & 3;
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
   const int nz = (z <= 1 || z >= 6) ? 2 : 1, ny = (y <= 1 || y >= 6) ? 2 : 1,
             nx = (xq == 0 || xq == 3) ? 2 : 1;
   for (int k = blockIdx.x; k < count; k += gridDim.x) {
-    const int tile = A.tile_list_near[k / 3], c = k % 3;
+    const int tile = A.tile_list_near[k];
     const TileGeo geo = tile_geo<kPacked>(A.g, A.inst, A.tile_inst, tile);
     int tx, ty, tz;
     tile_coords(geo, tile, tx, ty, tz);
@@ -635,18 +635,6 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
       const int kx = __shfl_sync(full, r.y, use ? src : 0);
       sk[i] = make_int2(use ? slot : -1, use ? kx : kref);  // unused: value 0, shift 0
     }
-    longlong2 v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int oz = lz + (i >> 2), oy = ly + ((i >> 1) & 1), ox = lx + (i & 1);
-      v[i] = make_longlong2(0, 0);
-      if (sk[i].x >= 0) {
-        // this face pair in the source tile's halo'd block (face-pair units)
-        const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
-                      (kTile / 2) * ox;
-        v[i] = __ldcg(scratch + (int64_t)sk[i].x * (kFxBlk / 2) + c * (kBlk / 2) + q);
-      }
-    }
     // The upper z sources (i >= 4) cover only the warps of z rows 0, 1, 6, 7
     // (nz is uniform in a warp: z = tid / 32).  Unless a covering source is
     // finer than k_ref (a right shift, rare), the warp aligns by left shifts
@@ -654,28 +642,45 @@ __global__ void __launch_bounds__(kMT) k_spread_merge_fx(SpreadArgs<float> A) {
     bool finer = false;
 #pragma unroll
     for (int i = 0; i < 8; ++i) finer |= sk[i].y > kref;
-    long long t0 = 0, t1 = 0;
-    if (!__any_sync(full, finer)) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (i >= 4 && nz == 1) break;
-        const int sh = kref - sk[i].y;  // 0 .. 17
-        t0 += (long long)((unsigned long long)v[i].x << sh);
-        t1 += (long long)((unsigned long long)v[i].y << sh);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        t0 += fx_align(v[i].x, kref - sk[i].y);
-        t1 += fx_align(v[i].y, kref - sk[i].y);
-      }
-    }
+    const bool exact_left = !__any_sync(full, finer);
     const float osc = ldexpf(1.f, -kref);
     const int n0 = geo.n[0], n1 = geo.n[1];
     const int64_t cells = (int64_t)n0 * n1 * geo.n[2];
-    float* row = call_field<kPacked>(A, geo.inst) + c * cells +
-                 ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 + tx * kTile;
-    reinterpret_cast<float2*>(row)[xq] = make_float2(fx_to_float(t0, osc), fx_to_float(t1, osc));
+    float* const row0 = call_field<kPacked>(A, geo.inst) +
+                        ((int64_t)(tz * kTile + z) * n1 + (ty * kTile + y)) * n0 + tx * kTile;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      longlong2 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        v[i] = make_longlong2(0, 0);
+        if (sk[i].x >= 0) {
+          // this face pair in the source tile's halo'd block (face-pair units)
+          const int oz = lz + (i >> 2), oy = ly + ((i >> 1) & 1), ox = lx + (i & 1);
+          const int q = ((z - oz * kTile + 2) * kB + (y - oy * kTile + 2)) * (kB / 2) + xq + 1 -
+                        (kTile / 2) * ox;
+          v[i] = __ldcg(scratch + (int64_t)sk[i].x * (kFxBlk / 2) + c * (kBlk / 2) + q);
+        }
+      }
+      long long t0 = 0, t1 = 0;
+      if (exact_left) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (i >= 4 && nz == 1) break;
+          const int sh = kref - sk[i].y;  // 0 .. 17
+          t0 += (long long)((unsigned long long)v[i].x << sh);
+          t1 += (long long)((unsigned long long)v[i].y << sh);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          t0 += fx_align(v[i].x, kref - sk[i].y);
+          t1 += fx_align(v[i].y, kref - sk[i].y);
+        }
+      }
+      reinterpret_cast<float2*>(row0 + c * cells)[xq] =
+          make_float2(fx_to_float(t0, osc), fx_to_float(t1, osc));
+    }
   }
 }
 
