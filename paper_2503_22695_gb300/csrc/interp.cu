@@ -273,13 +273,25 @@ __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int 
   cnt[tid] = 0;
   cnt[tid + kThreads] = 0;
   __syncthreads();
-  int cell[kChunk / kThreads], rank[kChunk / kThreads];
+  // every global load of the item's points is issued here, before the
+  // counting sort's barriers; only the stores wait for the sorted positions
+  constexpr int kPer = kChunk / kThreads;
+  int cell[kPer], rank[kPer], idx[kPer];
+  float off[kPer][3], val[MODE != 0 ? kPer : 1][3];
 #pragma unroll
-  for (int k = 0; k < kChunk / kThreads; ++k) {
+  for (int k = 0; k < kPer; ++k) {
     const int i = s + tid + k * kThreads;
     if (i < e) {
+      const int32_t pc = __ldg(A.p_cell + i);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) off[k][d] = __ldg(A.p_off + d * A.Q + i);
+      if (MODE != 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) val[k][c] = __ldg(A.p_val + c * A.Q + i);
+      }
+      idx[k] = __ldg(A.p_idx + i);
       int cx, cy, cz;
-      unpack_cell(__ldg(A.p_cell + i), cx, cy, cz);
+      unpack_cell(pc, cx, cy, cz);
       cell[k] = ((cz - z0) * kTile + (cy - y0)) * kTile + (cx - x0);
       rank[k] = atomicAdd(cnt + cell[k], 1);
     }
@@ -292,17 +304,17 @@ __device__ __forceinline__ int local_cell_stage(const InterpArgs<float>& A, int 
   cnt[2 * tid + 1] = pre + c0;
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kChunk / kThreads; ++k) {
+  for (int k = 0; k < kPer; ++k) {
     const int i = s + tid + k * kThreads;
     if (i < e) {
       const int q = cnt[cell[k]] + rank[k];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) P.off[d][q] = __ldg(A.p_off + d * A.Q + i);
+      for (int d = 0; d < 3; ++d) P.off[d][q] = off[k][d];
       if (MODE != 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) P.val[c][q] = __ldg(A.p_val + c * A.Q + i);
+        for (int c = 0; c < 3; ++c) P.val[c][q] = val[k][c];
       }
-      P.idx[q] = __ldg(A.p_idx + i);
+      P.idx[q] = idx[k];
       P.lc[q] = (short)cell[k];
     }
   }
