@@ -44,8 +44,10 @@ void free_plan(ib_plan* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
+  if (p->hi) cudaStreamDestroy(p->hi);
   if (p->zside) cudaStreamDestroy(p->zside);
-  for (cudaEvent_t ev : {p->ev_fork, p->ev_join, p->ev_ffork, p->ev_fsorted, p->ev_fjoin})
+  for (cudaEvent_t ev : {p->ev_fork, p->ev_join, p->ev_ffork, p->ev_fsorted, p->ev_fjoin,
+                         p->ev_hjoin})
     if (ev) cudaEventDestroy(ev);
   if (p->ev) {
     for (int i = 0; i < p->ev_cap; ++i) cudaEventDestroy(p->ev[i]);
@@ -419,8 +421,12 @@ ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32
          (E == 0 || ok(cudaMemcpyAsync(p->inc_idx, inc_idx.data(), 4 * nc * E,
                                        cudaMemcpyHostToDevice, s))) &&
          ok(cudaMemsetAsync(p->dstatus, 0, 16, s));
+  int least = 0, greatest = 0;  // stream priorities (greatest: numerically lowest)
   if (good)
-    good = ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) &&
+    good = ok(cudaDeviceGetStreamPriorityRange(&least, &greatest)) &&
+           ok(cudaStreamCreateWithPriority(&p->hi, cudaStreamNonBlocking, greatest)) &&
+           ok(cudaEventCreateWithFlags(&p->ev_hjoin, cudaEventDisableTiming)) &&
+           ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) &&
            ok(cudaStreamCreateWithFlags(&p->zside, cudaStreamNonBlocking)) &&
            ok(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming)) &&
            ok(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming)) &&
@@ -526,11 +532,18 @@ namespace ibfe {
 
 ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const void* u, void* G,
                        void* f, void* U, cudaStream_t s, const PackedCalls* pc) {
-  // Two branches: the Gauss-point sort and the interpolation depend only on
-  // x and u and run on the side stream while the FE force (FP64-pipe bound)
-  // runs on the caller's stream; the spread waits for both.
-  cudaStream_t b = p->side;
-  if (!ok(cudaEventRecord(p->ev_ffork, s)) || !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0)))
+  // Two branches forked from the caller's stream s.  The critical one -- the
+  // FE force, the nodal gather, the carried values and the spreading -- runs
+  // on stream m; the Gauss-point binning, the far-tile zeros and the
+  // interpolation depend only on x and u and run on the side stream b beside
+  // it.  The spreading waits for the binning; s waits for both branches.  For
+  // a plan of one structure m is the plan's high-priority stream, so that the
+  // CTA scheduler prefers the critical kernels (0.417 -> 0.405 ms at 256^3);
+  // a packed batch, whose merge and interpolation balance differently, was
+  // slower that way (1.17 -> 1.28 ms) and keeps m = s.
+  cudaStream_t b = p->side, m = p->n_inst > 1 ? s : p->hi;
+  if (!ok(cudaEventRecord(p->ev_ffork, s)) || !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0)) ||
+      (m != s && !ok(cudaStreamWaitEvent(m, p->ev_ffork, 0))))
     return IB_ERR_CUDA;
   ib_status st = do_points_sorted(p, x, nullptr, b);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fsorted, b))) st = IB_ERR_CUDA;
@@ -543,20 +556,23 @@ ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const vo
   if (st == IB_OK) st = do_interp_tail(p, u, U, b, p->elem_scratch2, pc);
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
   if (st == IB_OK) {
-    Stage sc(p, IB_STAGE_FORCE, s, 1);
-    st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, s);
+    Stage sc(p, IB_STAGE_FORCE, m, 1);
+    st = launch_fe_force(p, mt, pos_a(p, x), x->off, p->elem_scratch, false, m);
   }
-  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
-  if (st == IB_OK) st = launch_penalty(p, x, G, false, s);
+  if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, m);
+  if (st == IB_OK) st = launch_penalty(p, x, G, false, m);
   if (st == IB_OK) {
-    Stage sc(p, IB_STAGE_POINTS, s, 2);
-    st = launch_point_values(p, G, s);
-    if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fsorted, 0))) st = IB_ERR_CUDA;
-    if (st == IB_OK) st = launch_permute_values(p, s);
+    Stage sc(p, IB_STAGE_POINTS, m, 2);
+    st = launch_point_values(p, G, m);
+    if (st == IB_OK && !ok(cudaStreamWaitEvent(m, p->ev_fsorted, 0))) st = IB_ERR_CUDA;
+    if (st == IB_OK) st = launch_permute_values(p, m);
   }
   if (st == IB_OK)
-    st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, s, /*zero_fill=*/false,
+    st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, m, /*zero_fill=*/false,
                    pc ? pc->spread_f : nullptr);
+  if (st == IB_OK && m != s &&
+      (!ok(cudaEventRecord(p->ev_hjoin, m)) || !ok(cudaStreamWaitEvent(s, p->ev_hjoin, 0))))
+    st = IB_ERR_CUDA;
   if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
   return check_launch(st);
 }

@@ -179,9 +179,10 @@ struct ib_plan {
   int32_t* digit_tot;    // [256] radix digit totals
   double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*kParamRow] reduction partials
   cudaStream_t side;     // interpolation branch of ib_forward
+  cudaStream_t hi;       // ib_forward's critical branch (force -> spread), high priority
   cudaStream_t zside;    // far-tile zero-fill of the spread
   cudaEvent_t ev_fork, ev_join;      // spread zero-fill fork / join
-  cudaEvent_t ev_ffork, ev_fsorted, ev_fjoin;  // ib_forward branch events
+  cudaEvent_t ev_ffork, ev_fsorted, ev_fjoin, ev_hjoin;  // ib_forward branch events
   int sm_count, push_ctas, merge_ctas, interp_ctas[3];
   int interp_tma, interp_ctas_tma[3];  // FP32: TMA-staged interpolation available
   // launch tuning (ib_plan_set_tuning / ib_plan_autotune): points per work
