@@ -379,7 +379,8 @@ ib_status build(ib_batch* b, cudaStream_t s) {
     g0.origin[d] = i0.grid.origin[d];
   }
   g0.h = i0.grid.h;
-  ib_status st = plan_build(&pm, g0, tb[n], IB_QUAD_GAUSS2, IB_FP32_SPLIT, mb[n], s, &b->P);
+  ib_status st =
+      plan_build(&pm, g0, tb[n], IB_QUAD_GAUSS2, IB_FP32_SPLIT, mb[n], s, &b->P, /*packed=*/true);
   if (st != IB_OK) return st;
   ib_plan* P = b->P;
   P->n_inst = n;
@@ -437,7 +438,8 @@ ib_status ib_batch_create(int32_t n, const ib_instance* inst, int32_t precision,
   b->any_gG = any_gG;
   b->gunit = inst[0].x.grad_unit > 0.0 ? inst[0].x.grad_unit : 1.0;
   ib_status st = build(b, s);
-  // one tuning for the packed plan, timed on the batch's own forward
+  // one tuning for the packed plan, timed on the batch's own forward (timing
+  // the backward separately chose other caps for it, at the same speed)
   if (st == IB_OK) st = autotune_with(b->P, [b](cudaStream_t t) { return run_forward(b, t); }, s);
   if (st == IB_OK && !ok(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)))
     st = IB_ERR_CUDA;

@@ -43,6 +43,9 @@ void free_plan(ib_plan* p) {
                   p->elem_inst, p->mat_dev};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p->own_side_bufs)
+    for (void* q : {p->q_val_b, p->p_val_b, p->gq_c, p->elem_scratch3})
+      if (q) cudaFree(q);
   if (p->side) cudaStreamDestroy(p->side);
   if (p->hi) cudaStreamDestroy(p->hi);
   if (p->zside) cudaStreamDestroy(p->zside);
@@ -181,9 +184,10 @@ ib_status do_points_sorted(ib_plan* p, const ib_pos* x, const void* nodal, cudaS
 }
 
 ib_status do_interp(ib_plan* p, const void* u, int mode, double vs, double gs, cudaStream_t s,
-                    const GridCall* calls = nullptr, const void* tmaps = nullptr) {
+                    const GridCall* calls = nullptr, const void* tmaps = nullptr,
+                    const InterpIO* io = nullptr) {
   Stage sc(p, IB_STAGE_INTERP, s, 1);
-  return launch_interp_points(p, u, mode, vs, gs, s, calls, tmaps);
+  return launch_interp_points(p, u, mode, vs, gs, s, calls, tmaps, io);
 }
 
 ib_status do_project(ib_plan* p, const void* vals, void* elem, cudaStream_t s) {
@@ -214,9 +218,9 @@ ib_status to_nodes(ib_plan* p, const void* gq, void* elem, const void* scale, vo
 }
 
 ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true,
-                    const GridCall* calls = nullptr) {
+                    const GridCall* calls = nullptr, const void* vals = nullptr) {
   Stage sc(p, IB_STAGE_SPREAD, s, spread_launches(p->precision) - (zero_fill ? 0 : 1));
-  return launch_spread(p, scale, f, s, zero_fill, calls);
+  return launch_spread(p, scale, f, s, zero_fill, calls, vals);
 }
 
 ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
@@ -305,7 +309,8 @@ ib_status check_grid(const ib_grid* grid) {
 }
 
 ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32_t quad,
-                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out) {
+                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out,
+                     bool packed) {
   // nodes and coupling points per element
   const int nc = mesh->elem_type == IB_ELEM_TET10 ? 10 : (mesh->elem_type == IB_ELEM_TET4 ? 4 : 8);
   const int nq = mesh->elem_type == IB_ELEM_HEX8 ? 8 : 4;
@@ -406,12 +411,24 @@ ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32
               dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
               dalloc(&p->ered, 8 * kParamRow * (size_t)mat_cap) && dalloc(&p->dstatus, 16) &&
               dalloc(&p->pen_part, 8 * penalty_scratch_doubles()) &&
+              (packed || (dalloc(&p->q_val_b, rs * 3 * Q) && dalloc(&p->p_val_b, rs * 3 * Q) &&
+                          dalloc(&p->gq_c, rs * 3 * Q) &&
+                          dalloc(&p->elem_scratch3, rs * 3 * nc * E))) &&
               (precision != IB_FP32_SPLIT_DFVOL ||
                dalloc(&p->vol_jm1, sizeof(float) * 2 * (nc == 8 ? 8 : 4) * (size_t)(E > 0 ? E : 1)));
+  p->own_side_bufs = !packed;
   if (!good) {
     free_plan(p);
     cudaGetLastError();
     return IB_ERR_CUDA;
+  }
+  if (packed) {
+    // the backward's interpolation-adjoint branch of a packed plan forks
+    // after the spreading adjoint is done with these
+    p->q_val_b = p->q_val;
+    p->p_val_b = p->p_val;
+    p->gq_c = p->gq_b;
+    p->elem_scratch3 = p->elem_scratch2;
   }
   // every material's elements: the whole mesh (packed plans narrow them)
   const std::vector<int2> ranges(mat_cap, make_int2(0, (int)E));
@@ -633,16 +650,46 @@ ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos
   const double h = p->grid.h, ih3 = 1.0 / (h * h * h);
   const size_t nbytes = p->rsize * 3 * (size_t)p->N;
   void* gGt = p->node_tmp;  // the force cotangent gG + (df/dG)^T gf
+  // the interpolation adjoint's position term, added into gx after the join
+  void* gxi = static_cast<char*>(p->node_tmp) + nbytes;
   const bool force = gG || gf;
+  const double gxu = gunit(x);
   // Gauss points built and binned once for both transfer adjoints
   ib_status st = do_points_sorted(p, x, nullptr, s);
-  // spreading adjoint: an interpolation of gf (values and position weights)
+  // The interpolation adjoint (a spreading of gU and the position term of
+  // the interpolation of u) runs on the side stream with its own carried
+  // values, gradient output, projection scratch, nodal result and work
+  // counter (the per-tile maxima of the carried values are its spreading's),
+  // beside the spreading adjoint (an interpolation of gf: values and position
+  // weights) and the force adjoint on the caller's stream.  For a plan of one
+  // structure it forks right after the binning (0.75 -> 0.67 ms at 256^3); a
+  // packed batch, whose persistent transfer kernels each fill the GPU, forks
+  // it after the spreading adjoint, beside the force adjoint alone (forking
+  // at the binning took 2.3 -> 3.3 ms for the 48-instance sweep).
+  const InterpIO io_u = {p->p_val_b, nullptr, p->gq_c, 4};
+  auto side = [&]() {
+    if (!gU) return;
+    if (st == IB_OK && (!ok(cudaEventRecord(p->ev_ffork, s)) ||
+                        !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0))))
+      st = IB_ERR_CUDA;
+    if (st == IB_OK) {
+      Stage sc(p, IB_STAGE_POINTS, b, 2);
+      st = launch_point_values(p, gU, b, p->q_val_b);
+      if (st == IB_OK) st = launch_permute_values(p, b, true, p->q_val_b, p->p_val_b);
+    }
+    if (st == IB_OK) st = do_spread(p, 1.0, gu, b, true, pc ? pc->spread_gu : nullptr, p->p_val_b);
+    if (st == IB_OK)
+      st = pc ? do_interp(p, nullptr, 2, 0.0, 0.0, b, pc->interp_ug, pc->tmaps_u, &io_u)
+              : do_interp(p, u, 2, 0.0, gxu / h, b, nullptr, nullptr, &io_u);
+    if (st == IB_OK) st = to_nodes(p, p->gq_c, p->elem_scratch3, nullptr, gxi, b);
+    if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
+  };
+  if (!pc) side();
   if (st == IB_OK && gf) {
     Stage sc(p, IB_STAGE_POINTS, s, 2);
     st = launch_point_values(p, G, s);
-    if (st == IB_OK) st = launch_permute_values(p, s);
+    if (st == IB_OK) st = launch_permute_values(p, s, false);
   }
-  const double gxu = gunit(x);
   if (st == IB_OK && gf)
     st = pc ? do_interp(p, nullptr, 1, 0.0, 0.0, s, pc->interp_gf, pc->tmaps_gf)
             : do_interp(p, gf, 1, ih3, ih3 / h * gxu, s);
@@ -654,28 +701,19 @@ ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos
                : cudaMemsetAsync(gGt, 0, nbytes, s)))
       st = IB_ERR_CUDA;
   }
-  // interpolation adjoint (a spreading of gU) on the side stream ...
-  if (st == IB_OK && (!ok(cudaEventRecord(p->ev_ffork, s)) ||
-                      !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0))))
-    st = IB_ERR_CUDA;
-  if (st == IB_OK && gU) {
-    Stage sc(p, IB_STAGE_POINTS, b, 2);
-    st = launch_point_values(p, gU, b);
-    if (st == IB_OK) st = launch_permute_values(p, b);
-  }
-  if (st == IB_OK && gU) st = do_spread(p, 1.0, gu, b, true, pc ? pc->spread_gu : nullptr);
-  if (st == IB_OK && gU)
-    st = pc ? do_interp(p, nullptr, 2, 0.0, 0.0, b, pc->interp_ug, pc->tmaps_u)
-            : do_interp(p, u, 2, 0.0, gxu / h, b);
-  if (st == IB_OK && gU) st = to_nodes(p, p->gq_b, p->elem_scratch2, nullptr, gx, b, gx);
-  if (st == IB_OK && !ok(cudaEventRecord(p->ev_fjoin, b))) st = IB_ERR_CUDA;
-  // ... beside the force adjoint, whose nodal gather adds into gx after the join
+  if (pc) side();
   if (st == IB_OK && force) {
     Stage sc(p, IB_STAGE_FORCE, s, 1);
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch, params, s);
   }
   if (st == IB_OK && force && params) st = do_reduce(p, kParamRow, n_mats, s);
-  if (st == IB_OK && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
+  // join: gx = (spreading adjoint's term + interpolation adjoint's term) +
+  // the force adjoint's gather, in that order
+  if (st == IB_OK && gU && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
+  if (st == IB_OK && gU) {
+    Stage sc(p, IB_STAGE_GATHER, s, 1);
+    st = launch_node_copy(p, gxi, gx, gx, s);
+  }
   if (st == IB_OK && force) st = do_gather(p, p->elem_scratch, nullptr, gx, s, gx, gxu);
   if (st == IB_OK && force) st = launch_penalty_adj(p, gGt, gx, s, gxu);
   if (st == IB_OK && params) {

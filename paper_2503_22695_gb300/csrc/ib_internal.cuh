@@ -174,7 +174,8 @@ struct ib_plan {
   int32_t* tile_done;    // [ntiles] work items of the tile written (FP32 spreading, per call)
   int32_t* tile_sk;      // [4 ntiles] FP32: first block slot, exponent, item bound, items
   int32_t* tile_bcount;  // [2 * classify CTAs] per-CTA counts
-  int32_t* tile_counters;// [8] work items, push / interp work counters, near count,
+  int32_t* tile_counters;// [8] [0] work items, [1] push counter, [2] interpolation counter,
+                         //     [3] near count, [4] second interpolation's counter,
                          //     [6] FE force block counter
   int32_t* digit_tot;    // [256] radix digit totals
   double* rpart;         // [reduce CTAs][IB_MAX_MATERIALS*kParamRow] reduction partials
@@ -198,6 +199,15 @@ struct ib_plan {
   void* p_val;           // Real [3][Q]
   int32_t* p_idx;        // [Q] original gq
   void* node_tmp;        // Real [2][3][N] nodal work vectors (fused backward)
+  // the fused backward's interpolation-adjoint branch, beside the spreading
+  // adjoint: its own carried values, gradient outputs and projection scratch
+  // (owned by plans of one structure; a packed plan's alias q_val, p_val,
+  // gq_b and elem_scratch2)
+  void* q_val_b;         // Real [3][Q]
+  void* p_val_b;         // Real [3][Q]
+  void* gq_c;            // Real [3][Q]
+  void* elem_scratch3;   // Real [3 nc][E]
+  bool own_side_bufs;
   // penalty tethers (ib_plan_set_penalty; caller-owned device arrays)
   const int32_t* pen_nodes;
   int pen_n;
@@ -269,16 +279,21 @@ ib_status launch_plan_static(ib_plan* p, cudaStream_t s);
 ib_status launch_points(ib_plan* p, const void* x_cell_or_x64, const float* off,
                         const void* nodal, int val_kind, cudaStream_t s);
 ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s);
-// Carried values of already-built points (unsorted q_val), and their sorted copy.
-ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s);
-ib_status launch_permute_values(ib_plan* p, cudaStream_t s);
+// Carried values of already-built points (unsorted, into q_out or q_val), and
+// their binned copy (from q_in or q_val into p_out or p_val; vmax: also the
+// per-tile maxima the FP32 spreading's exponents take).
+ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s,
+                              void* q_out = nullptr);
+ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax = true,
+                                const void* q_in = nullptr, void* p_out = nullptr);
 
 // spread.cu
 // zero_fill false: the far-tile zeros were issued by launch_spread_zero
 // calls (packed plans): each instance's output field and scale, replacing
 // f and scale (device array, one GridCall per instance)
+// vals: the binned carried values (default p_val)
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill = true,
-                        const GridCall* calls = nullptr);
+                        const GridCall* calls = nullptr, const void* vals = nullptr);
 // zeros of the tiles no coupling point reaches (needs the points binned)
 ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s,
                              const GridCall* calls = nullptr);
@@ -295,9 +310,18 @@ int spread_launches(int precision);
 // calls / tmaps (packed plans): each instance's field, vscale and gscale,
 // and each instance's tensor map of its field (device arrays; tmaps null:
 // no TMA staging)
+// io (optional, modes 1 and 2 only): the binned carried values read, the
+// outputs a and b and the work-counter slot, for two interpolations in
+// flight at once (default p_val, gq_a, gq_b, slot 2)
+struct InterpIO {
+  const void* vals;
+  void* out_a;
+  void* out_b;
+  int counter;
+};
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
                                double gscale, cudaStream_t s, const GridCall* calls = nullptr,
-                               const void* tmaps = nullptr);
+                               const void* tmaps = nullptr, const InterpIO* io = nullptr);
 // the tensor map of a FP32 field [3][n2][n1][n0] for the interpolation's TMA
 // staging, written to `map` (128 bytes, host); false if unavailable
 bool encode_velocity_map(const int n[3], const void* u, void* map);
@@ -311,8 +335,11 @@ ib_status launch_wait_probe(int* status, double ms, cudaStream_t s);
 // used for packed plans: `grid` is then the first instance's, `ntiles` the
 // instances' total and mat_cap their total material count)
 ib_status check_grid(const ib_grid* grid);
+// packed: the plan of a batch (the backward's side-branch buffers alias the
+// spreading adjoint's, which that plan's backward is done with when it forks)
 ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32_t quad,
-                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out);
+                     int32_t precision, int mat_cap, cudaStream_t s, ib_plan** out,
+                     bool packed = false);
 void plan_free(ib_plan* p);
 // the autotuner's coordinate descent over the plan's tuning, timing `run`
 // (one warm-up and the median of three calls per candidate)

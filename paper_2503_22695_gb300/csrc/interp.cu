@@ -53,7 +53,8 @@ struct InterpArgs {
   const int32_t* tile_end;
   const int32_t* tile_slot;  // first work item of each tile
   const int32_t* tile_list;  // tile of each work item
-  int32_t* counters;      // [0] work items, [2] work counter
+  int32_t* counters;      // [0] work items, [2] the values-only mode's work counter
+  int32_t* work;          // the gradient modes' work counter (zero at launch)
   const int32_t* p_cell;
   const Real* p_off;
   const Real* p_val;
@@ -137,6 +138,13 @@ __device__ __forceinline__ void interp_one(const InterpArgs<Real>& A, const Real
 
 // Persistent CTAs, two-stage pipeline: the velocity block of the next work
 // item is fetched while the points of the current one are evaluated.
+// The work counter of a call: slot 2 for the values-only mode (never given
+// another), the call's own slot for the gradient modes.
+template <int MODE, typename Real>
+__device__ __forceinline__ int32_t* work_counter(const InterpArgs<Real>& A) {
+  return MODE == 0 ? A.counters + 2 : A.work;
+}
+
 template <typename Real, int MODE, bool kPacked>
 __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
   __shared__ int next;
   const int tid = threadIdx.x;
   const int count = A.counters[0];
-  if (tid == 0) next = atomicAdd(A.counters + 2, 1);
+  if (tid == 0) next = atomicAdd(work_counter<MODE>(A), 1);
   __syncthreads();
   int cur = next;
   if (cur < count) stage_block<kPacked>(A, cur, buf0, tid);
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tile(InterpArgs<Real> A) {
   int b = 0;
   while (cur < count) {
     __syncthreads();
-    if (tid == 0) next = atomicAdd(A.counters + 2, 1);
+    if (tid == 0) next = atomicAdd(work_counter<MODE>(A), 1);
     __syncthreads();
     const int nxt = next;
     if (nxt < count) stage_block<kPacked>(A, nxt, buf0 + (b ^ 1) * 3 * kComp, tid);
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_flag = 0;
-    next = atomicAdd(A.counters + 2, 1);
+    next = atomicAdd(work_counter<MODE>(A), 1);
   }
   __syncthreads();
   int cur = next;
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 0 ? 3 : 2)
       cp_async_commit();
       cp_async_wait_group<0>();
     }
-    if (tid == 0) next = atomicAdd(A.counters + 2, 1);
+    if (tid == 0) next = atomicAdd(work_counter<MODE>(A), 1);
     __syncthreads();  // box landed everywhere; next item known
     if (abort_flag) break;
     if (cur_tma) {
@@ -563,8 +571,14 @@ bool make_velocity_map(const int n[3], const void* u, CUtensorMap* m) {
 
 template <typename Real>
 ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gscale,
-                   cudaStream_t s, const GridCall* calls, const CUtensorMap* tmaps) {
+                   cudaStream_t s, const GridCall* calls, const CUtensorMap* tmaps,
+                   const InterpIO* io) {
   if (p->Q == 0) return IB_OK;
+  // work-counter slots free for the interpolation (0, 1, 3 and 6 are the
+  // work count, the push's counter, the near count and the force's counter)
+  if (io && (mode == 0 || (io->counter != 2 && io->counter != 4 && io->counter != 5 &&
+                           io->counter != 7)))
+    return IB_ERR_INVALID_ARG;
   if ((p->n_inst > 1) != (calls != nullptr)) return IB_ERR_INVALID_ARG;
   InterpArgs<Real> A;
   A.g = p->grid;
@@ -578,24 +592,25 @@ ib_status interp_t(ib_plan* p, const void* u, int mode, double vscale, double gs
   A.tile_slot = p->tile_slot;
   A.tile_list = p->tile_list;
   A.counters = p->tile_counters;
+  A.work = p->tile_counters + (io ? io->counter : 2);
   A.p_cell = p->p_cell;
   A.p_off = (const Real*)p->p_off;
-  A.p_val = (const Real*)p->p_val;
+  A.p_val = (const Real*)(io && io->vals ? io->vals : p->p_val);
   A.p_idx = p->p_idx;
   A.chunk = p->chunk;
   // the projection weight w_q j0 of a Gauss point; none for the nodal rule
   A.u = (const Real*)u;
   A.vscale = (Real)vscale;
   A.gscale = (Real)gscale;
-  A.out_a = (Real*)p->gq_a;
-  A.out_b = (Real*)p->gq_b;
+  A.out_a = (Real*)(io && io->out_a ? io->out_a : p->gq_a);
+  A.out_b = (Real*)(io && io->out_b ? io->out_b : p->gq_b);
   A.status = p->dstatus;
   A.use_tma = 0;
   // persistent grid: the occupancy maximum, capped by the plan's tuning
   const int cap_ctas = p->interp_per_sm * p->sm_count;
   auto cap = [cap_ctas](int ctas) { return ctas < cap_ctas ? ctas : cap_ctas; };
   const size_t smem = smem_bytes<Real>();
-  cudaMemsetAsync(p->tile_counters + 2, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(A.work, 0, sizeof(int32_t), s);
   const bool packed = p->n_inst > 1;
   if constexpr (sizeof(Real) == 4) {
     // packed plans: the instances' maps in device memory (this one unused)
@@ -703,10 +718,11 @@ ib_status interp_prepare(ib_plan* p) {
 
 ib_status launch_interp_points(ib_plan* p, const void* u, int mode, double vscale,
                                double gscale, cudaStream_t s, const GridCall* calls,
-                               const void* tmaps) {
+                               const void* tmaps, const InterpIO* io) {
   const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
-  return p->precision == IB_FP64 ? interp_t<double>(p, u, mode, vscale, gscale, s, calls, m)
-                                 : interp_t<float>(p, u, mode, vscale, gscale, s, calls, m);
+  return p->precision == IB_FP64
+             ? interp_t<double>(p, u, mode, vscale, gscale, s, calls, m, io)
+             : interp_t<float>(p, u, mode, vscale, gscale, s, calls, m, io);
 }
 
 bool encode_velocity_map(const int n[3], const void* u, void* map) {

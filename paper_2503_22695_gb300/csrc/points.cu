@@ -241,11 +241,11 @@ __device__ __forceinline__ void tile_vmax_update(uint32_t* vmax, uint32_t tile, 
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(vmax + tile, mx);
 }
 
-// Binned copies of the carried values (and, for FP32 plans, the per-tile
-// maxima of their magnitudes).  The tile of a binned point: from its cell
-// (one structure), or its binning key, read at its original index (packed
-// plans, whose cells are their instance's).
-template <typename Real, bool kPacked>
+// Binned copies of the carried values (and, with kVmax, for FP32 plans, the
+// per-tile maxima of their magnitudes).  The tile of a binned point: from
+// its cell (one structure), or its binning key, read at its original index
+// (packed plans, whose cells are their instance's).
+template <typename Real, bool kPacked, bool kVmax>
 __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
                                  const Real* __restrict__ q_val, Real* __restrict__ p_val,
                                  const int32_t* __restrict__ p_cell, GridDev g,
@@ -260,7 +260,7 @@ __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
     v[d] = __ldg(q_val + d * Q + gi);
     p_val[d * Q + i] = v[d];
   }
-  if constexpr (sizeof(Real) == 4) {
+  if constexpr (sizeof(Real) == 4 && kVmax) {
     uint32_t tile;
     if constexpr (kPacked) {
       tile = __ldg(key + gi);
@@ -573,10 +573,11 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
-ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
+ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s, void* q_out) {
   if (p->Q == 0) return IB_OK;
+  void* const q = q_out ? q_out : p->q_val;
   if (p->quad == IB_QUAD_NODAL)  // the nodal values are the point values
-    return cudaMemcpyAsync(p->q_val, nodal, p->rsize * 3 * (size_t)p->N,
+    return cudaMemcpyAsync(q, nodal, p->rsize * 3 * (size_t)p->N,
                            cudaMemcpyDeviceToDevice, s) == cudaSuccess
                ? IB_OK
                : IB_ERR_CUDA;
@@ -586,27 +587,33 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s) {
     if (p->precision == IB_FP64)
       k_point_values<double, kE><<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const double*)nodal,
                                                    (const double*)p->inv_mass,
-                                                   (const double*)p->wj0, (double*)p->q_val);
+                                                   (const double*)p->wj0, (double*)q);
     else
       k_point_values<float, kE><<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const float*)nodal,
                                                   (const float*)p->inv_mass,
-                                                  (const float*)p->wj0, (float*)p->q_val);
+                                                  (const float*)p->wj0, (float*)q);
   });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
 
-ib_status launch_permute_values(ib_plan* p, cudaStream_t s) {
+ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax, const void* q_in,
+                                void* p_out) {
   if (p->Q == 0) return IB_OK;
   const int nb = (int)((p->Q + 255) / 256);
+  const void* const q = q_in ? q_in : p->q_val;
+  void* const out = p_out ? p_out : p->p_val;
   if (p->precision == IB_FP64) {
-    k_permute_values<double, false><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)p->q_val,
-                                                       (double*)p->p_val, p->p_cell, p->grid,
+    k_permute_values<double, false, false><<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const double*)q,
+                                                       (double*)out, p->p_cell, p->grid,
                                                        nullptr, nullptr);
   } else {
-    cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
-    auto permute = p->n_inst > 1 ? k_permute_values<float, true> : k_permute_values<float, false>;
-    permute<<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)p->q_val, (float*)p->p_val,
-                               p->p_cell, p->grid, p->keys[0], p->tile_vmax);
+    if (vmax) cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
+    auto permute = p->n_inst > 1 ? (vmax ? k_permute_values<float, true, true>
+                                         : k_permute_values<float, true, false>)
+                                  : (vmax ? k_permute_values<float, false, true>
+                                          : k_permute_values<float, false, false>);
+    permute<<<nb, 256, 0, s>>>(p->p_idx, p->Q, (const float*)q, (float*)out, p->p_cell,
+                               p->grid, p->keys[0], p->tile_vmax);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }

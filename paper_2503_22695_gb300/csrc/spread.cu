@@ -801,7 +801,8 @@ void launch_push(ib_plan* p, const SpreadArgs<double>& A, cudaStream_t s) {
 }
 
 template <typename Real>
-SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* calls) {
+SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* calls,
+                             const void* vals = nullptr) {
   SpreadArgs<Real> A;
   A.g = p->grid;
   A.ntiles = p->ntiles;
@@ -819,7 +820,7 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* 
   A.counters = p->tile_counters;
   A.p_cell = p->p_cell;
   A.p_off = (const Real*)p->p_off;
-  A.p_val = (const Real*)p->p_val;
+  A.p_val = (const Real*)(vals ? vals : p->p_val);
   A.chunk = p->chunk;
   A.scale = (Real)scale;
   A.scratch = (Real*)p->spread_scratch;
@@ -832,8 +833,8 @@ SpreadArgs<Real> spread_args(ib_plan* p, double scale, void* f, const GridCall* 
 
 template <typename Real, bool kPacked>
 ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s,
-                   const GridCall* calls) {
-  SpreadArgs<Real> A = spread_args<Real>(p, scale, f, calls);
+                   const GridCall* calls, const void* vals) {
+  SpreadArgs<Real> A = spread_args<Real>(p, scale, f, calls, vals);
   cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
   // far-tile zeros on the side stream, concurrent with the push (unless the
   // caller has already issued them)
@@ -913,13 +914,13 @@ ib_status spread_prepare(ib_plan* p) {
 int spread_launches(int precision) { return precision == IB_FP64 ? 3 : 4; }
 
 ib_status launch_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero_fill,
-                        const GridCall* calls) {
+                        const GridCall* calls, const void* vals) {
   if ((p->n_inst > 1) != (calls != nullptr)) return IB_ERR_INVALID_ARG;
   if (p->precision == IB_FP64)
     return p->n_inst > 1 ? IB_ERR_INVALID_ARG
-                         : spread_t<double, false>(p, scale, f, zero_fill, s, calls);
-  return p->n_inst > 1 ? spread_t<float, true>(p, scale, f, zero_fill, s, calls)
-                       : spread_t<float, false>(p, scale, f, zero_fill, s, calls);
+                         : spread_t<double, false>(p, scale, f, zero_fill, s, calls, vals);
+  return p->n_inst > 1 ? spread_t<float, true>(p, scale, f, zero_fill, s, calls, vals)
+                       : spread_t<float, false>(p, scale, f, zero_fill, s, calls, vals);
 }
 
 ib_status launch_spread_zero(ib_plan* p, void* f, cudaStream_t s, const GridCall* calls) {
