@@ -281,9 +281,12 @@ ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
 /* Autotuner: times ib_forward on the given inputs for candidate tunings
  * (coordinate descent over the four entries in order: items of 1024 or 512
  * points; 2, 1, 3, 4 or 5 force CTAs per SM; spreading and interpolation caps 8, 3
- * or 2; one warm-up and the median of three timed calls each) and keeps the
- * fastest.  Writes the choice to `tuning` (host, 4 entries) if non-NULL.
- * Allocates temporary output buffers and synchronises `stream`. */
+ * or 2; one warm-up and the median of five timed calls each, every timed
+ * call after a write of twice the L2 size, so that it starts from a cold
+ * cache) and keeps the fastest.  Writes the choice to `tuning` (host, 4
+ * entries) if non-NULL.  Allocates temporary output buffers and the L2
+ * scratch (without the scratch, if that allocation fails) and synchronises
+ * `stream`. */
 ib_status ib_plan_autotune(ib_plan* plan, const ib_material* mats, int32_t n_mats,
                            const ib_pos* x, const void* u, void* stream, int32_t tuning[4]);
 

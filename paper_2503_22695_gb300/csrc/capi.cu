@@ -847,11 +847,29 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
   ib_status st = IB_OK;
   cudaEvent_t a = nullptr, b = nullptr;
   if (!ok(cudaEventCreate(&a)) || !ok(cudaEventCreate(&b))) st = IB_ERR_CUDA;
-  // one warm-up call, then the median of three timed calls
+  // A scratch twice the L2 size, written before every timed call, so that
+  // each call starts from a cold cache as a time step streaming the grid
+  // does (back-to-back calls on a warm L2 ranked the candidates differently
+  // from the timed steps).  Without it (allocation refused) the calls run
+  // back to back.
+  int dev = 0, l2 = 0;
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  if (ok(cudaGetDevice(&dev)) && ok(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev)) &&
+      l2 > 0) {
+    flush_bytes = 2 * (size_t)l2;
+    if (!ok(cudaMalloc(&flush, flush_bytes))) {
+      flush = nullptr;
+      cudaGetLastError();
+    }
+  }
+  // one warm-up call, then the median of five timed calls
+  constexpr int kTimed = 5;
   auto time_run = [&](float& ms) -> ib_status {
     ib_status r = run(s);
-    float t[3];
-    for (int k = 0; k < 3 && r == IB_OK; ++k) {
+    float t[kTimed];
+    for (int k = 0; k < kTimed && r == IB_OK; ++k) {
+      if (flush && !ok(cudaMemsetAsync(flush, k, flush_bytes, s))) return IB_ERR_CUDA;
       if (!ok(cudaEventRecord(a, s))) return IB_ERR_CUDA;
       r = run(s);
       if (r == IB_OK && (!ok(cudaEventRecord(b, s)) || !ok(cudaEventSynchronize(b)) ||
@@ -859,8 +877,8 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
         r = IB_ERR_CUDA;
     }
     if (r != IB_OK) return r;
-    std::sort(t, t + 3);
-    ms = t[1];
+    std::sort(t, t + kTimed);
+    ms = t[kTimed / 2];
     return IB_OK;
   };
   int32_t cur[4];
@@ -888,6 +906,7 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
+  if (flush) cudaFree(flush);
   return st;
 }
 

@@ -342,7 +342,7 @@ ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32
                      bool packed = false);
 void plan_free(ib_plan* p);
 // the autotuner's coordinate descent over the plan's tuning, timing `run`
-// (one warm-up and the median of three calls per candidate)
+// (one warm-up and the median of five cold-L2 calls per candidate)
 ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>& run,
                         cudaStream_t s);
 // Per-instance operands of the forward and backward of a packed plan
