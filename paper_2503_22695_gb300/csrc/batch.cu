@@ -285,6 +285,7 @@ ib_status build(ib_batch* b, cudaStream_t s) {
       w.model = in.mats[m].model;
       for (int k = 0; k < in.mats[m].n_params; ++k) w.p[k] = in.mats[m].params[k];
       w.p[kTa] = in.mats[m].Ta;
+      mat_entry_finish(w.p, w.pf, w.act);
       need |= 1 << w.model;
       if (w.p[kTa] != 0.0) need |= kLawAct;
       ranges[mb[i] + m] = make_int2(eb[i], eb[i + 1]);

@@ -106,6 +106,7 @@ ib_status make_table(const ib_plan* p, const ib_material* mats, int32_t n_mats, 
     mt.model[m] = mats[m].model;
     for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
     mt.p[m][kTa] = mats[m].Ta;
+    mat_entry_finish(mt.p[m], mt.pf[m], mt.act[m]);
   }
   return IB_OK;
 }

@@ -407,6 +407,16 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     if constexpr (kPacked) return __ldg(&A.mats[mid].p[k]);
     return mt.p[mid][k];
   };
+  // a parameter in Real: FP32 plans read the table's FP32 roundings (the same
+  // values a conversion here would give, without the FP64-rate conversion)
+  const auto prmr = [&](int k) -> Real {
+    if constexpr (sizeof(Real) == 4) {
+      if constexpr (kPacked) return __ldg(&A.mats[mid].pf[k]);
+      return mt.pf[mid][k];
+    }
+    return Real(prm(k));
+  };
+  const bool ta_on = kPacked ? __ldg(&A.mats[mid].act) != 0 : mt.act[mid] != 0;
   // the laws this instantiation handles (kLaws bit m: ib_model m; bit
   // kLawActBit: the active term); the host picks an instantiation whose set
   // covers the material table, and every other branch compiles away
@@ -430,15 +440,15 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   const Real esn1r = Real(esn1), efesr = Real(efes);
 
   // material constants (unused entries of a model are never read by its branches)
-  const Real kap = Real(prm(lawNH ? 1 : (lawHO ? 8 : (lawF2 ? 4 : 3))));
-  const Real pa = Real(prm(0)), pb = Real(prm(1));
-  const Real paf = Real(prm(lawF1 ? 1 : 2)), pbf = Real(prm(lawF1 ? 2 : 3));
-  const Real pas = Real(prm(4)), pbs = Real(prm(5)), pafs = Real(prm(6)), pbfs = Real(prm(7));
+  const Real kap = prmr(lawNH ? 1 : (lawHO ? 8 : (lawF2 ? 4 : 3)));
+  const Real pa = prmr(0), pb = prmr(1);
+  const Real paf = prmr(lawF1 ? 1 : 2), pbf = prmr(lawF1 ? 2 : 3);
+  const Real pas = prmr(4), pbs = prmr(5), pafs = prmr(6), pbfs = prmr(7);
   // active fibre tension (Section 6.1); the parameter adjoint always needs
   // its fibre kinematics for d/dT_a
   static_assert(!kParams || (kLaws & kLawAct), "the parameter adjoint computes d/dT_a");
-  const Real Ta = Real(prm(kTa));
-  const bool act = (kLaws & kLawAct) && (kParams || prm(kTa) != 0.0);
+  const Real Ta = prmr(kTa);
+  const bool act = (kLaws & kLawAct) && (kParams || ta_on);
 
   double en = 0.0;
   Real gp[kParamRow];
@@ -551,7 +561,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     // k4 = (E_L + G_T - 4 G_L)/2, and the I5f term
     // (G_T - G_L)(2 Fe (x) e - Fe (x) Ce - FCe (x) e) = -(G_T - G_L)(Fe (x) w + Fw (x) e)
     // with C e = e + w, w = H e + H^T e + H^T H e (no cancellation for small H)
-    const Real k4 = lawSR ? Real(0.5) * (Real(prm(2)) + pa - Real(4) * pb) : Real(0);
+    const Real k4 = lawSR ? Real(0.5) * (prmr(2) + pa - Real(4) * pb) : Real(0);
     const Real c5 = lawSR ? pa - pb : Real(0);
     Real w5[3] = {Real(0), Real(0), Real(0)}, Fw5[3] = {Real(0), Real(0), Real(0)};
     if (has_f) {
@@ -943,9 +953,9 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
   }
 }
 
-// Persistent grid (a fixed number of CTAs per SM, fewer than fit): the kernel
-// is bound by the FP64 pipe, and the SM room it leaves lets the Gauss-point
-// binning and the interpolation, issued on another stream, run beside it.
+// Persistent grid (a fixed number of CTAs per SM, fewer than fit): the SM
+// room the kernel leaves lets the Gauss-point binning and the interpolation,
+// issued on another stream, run beside it.
 // CTAs take blocks of elements from a counter, so a CTA that becomes resident
 // late (its SM busy with those kernels) simply takes fewer.
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>

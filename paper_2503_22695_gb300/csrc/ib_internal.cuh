@@ -48,11 +48,16 @@ constexpr int kLawAll = kLawBase | (1 << IB_STD_REINF) | (1 << IB_FIBRE2) | kLaw
 // Not a law: the exact volumetric invariant of IB_FP32_SPLIT_DFVOL plans.
 constexpr int kLawVolX = 1 << 6;
 
-// Material table passed by value to kernels.
+// Material table passed by value to kernels: the parameters in double, their
+// FP32 roundings (read by the FP32 force kernels, which thus convert none on
+// the device: GB300 converts at the FP64 rate), and whether the active
+// tension is nonzero.
 struct MatTable {
   int n;
   int model[IB_MAX_MATERIALS];
+  int act[IB_MAX_MATERIALS];
   double p[IB_MAX_MATERIALS][kParamRow];
+  float pf[IB_MAX_MATERIALS][kParamRow];
 };
 
 // Grid description used on the device.
@@ -86,12 +91,19 @@ struct GridCall {
 };
 
 // One row of a material table in device memory (packed plans; rows indexed
-// by the packed material ids).
+// by the packed material ids), with the fields of a MatTable entry.
 struct MatRow {
   int model;
-  int pad;
+  int act;
   double p[kParamRow];
+  float pf[kParamRow];
 };
+
+// The derived fields of a table entry from its double parameters p.
+inline void mat_entry_finish(const double* p, float* pf, int& act) {
+  for (int k = 0; k < kParamRow; ++k) pf[k] = static_cast<float>(p[k]);
+  act = p[kTa] != 0.0;
+}
 
 template <typename Real>
 struct PosDev {

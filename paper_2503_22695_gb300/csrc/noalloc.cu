@@ -14,6 +14,7 @@
 // contents; each call overwrites every entry it reads, so nothing has to be
 // cleared.  Calls that overlap on the GPU (two streams, or two host threads)
 // race on the scratch and must not be issued.
+#include <cstring>
 #include <mutex>
 
 #include "ib_device.cuh"
@@ -228,16 +229,14 @@ extern "C" ib_status ib_fe_energy_noalloc(const ib_mesh* mesh, const ib_material
   if (mesh->n_elems > kNoAllocMaxElems) return IB_ERR_CAPACITY;
   if (n_mats <= 0 || n_mats > IB_MAX_MATERIALS) return IB_ERR_INVALID_ARG;
   MatTable mt;
+  std::memset(&mt, 0, sizeof(mt));
   mt.n = n_mats;
-  for (int m = 0; m < IB_MAX_MATERIALS; ++m) {
-    mt.model[m] = 0;
-    for (int k = 0; k < kParamRow; ++k) mt.p[m][k] = 0.0;
-  }
   for (int m = 0; m < n_mats; ++m) {
     if (!material_valid(mats[m])) return IB_ERR_INVALID_ARG;
     mt.model[m] = mats[m].model;
     for (int k = 0; k < mats[m].n_params; ++k) mt.p[m][k] = mats[m].params[k];
     mt.p[m][kTa] = mats[m].Ta;
+    mat_entry_finish(mt.p[m], mt.pf[m], mt.act[m]);
   }
   // once per device, with that device current: the device address of the
   // scratch array (host code only sees a host-side stand-in for the symbol)
