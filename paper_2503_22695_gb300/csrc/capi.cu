@@ -224,9 +224,9 @@ ib_status do_spread(ib_plan* p, double scale, void* f, cudaStream_t s, bool zero
   return launch_spread(p, scale, f, s, zero_fill, calls, vals);
 }
 
-ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
+ib_status do_reduce(ib_plan* p, int nvals, int n_mats, cudaStream_t s, bool real_parts) {
   Stage sc(p, IB_STAGE_REDUCE, s, 2);
-  return launch_reduce_parts(p, nvals, n_mats, s);
+  return launch_reduce_parts(p, nvals, n_mats, s, real_parts);
 }
 
 ib_status do_interp_tail(ib_plan* p, const void* u, void* U, cudaStream_t s,
@@ -504,7 +504,7 @@ ib_status ib_fe_force(ib_plan* p, const ib_material* mats, int32_t n_mats, const
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, s);
   if (st == IB_OK) st = launch_penalty(p, x, G, energy != nullptr, s);
   if (st == IB_OK && energy) {
-    st = do_reduce(p, 1, n_mats, s);
+    st = do_reduce(p, 1, n_mats, s, false);
     double red[kParamRow * IB_MAX_MATERIALS];
     double pen = 0.0;
     if (st == IB_OK &&
@@ -707,7 +707,7 @@ ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos
     Stage sc(p, IB_STAGE_FORCE, s, 1);
     st = launch_fe_force_adj(p, mt, pos_a(p, x), x->off, gGt, p->elem_scratch, params, s);
   }
-  if (st == IB_OK && force && params) st = do_reduce(p, kParamRow, n_mats, s);
+  if (st == IB_OK && force && params) st = do_reduce(p, kParamRow, n_mats, s, true);
   // join: gx = (spreading adjoint's term + interpolation adjoint's term) +
   // the force adjoint's gather, in that order
   if (st == IB_OK && gU && !ok(cudaStreamWaitEvent(s, p->ev_fjoin, 0))) st = IB_ERR_CUDA;
@@ -795,7 +795,7 @@ ib_status fe_force_adj_async(ib_plan* p, const ib_material* mats, int32_t n_mats
   }
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, Hv, s, nullptr, gunit(x));
   if (st == IB_OK) st = launch_penalty_adj(p, v, Hv, s, gunit(x));
-  if (st == IB_OK && params) st = do_reduce(p, kParamRow, n_mats, s);
+  if (st == IB_OK && params) st = do_reduce(p, kParamRow, n_mats, s, true);
   return check_launch(st);
 }
 }  // namespace ibfe

@@ -48,7 +48,8 @@ __device__ __forceinline__ void block_sum_row(double (&v)[kParamRow], int nvals,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_reduce_l1(const double* __restrict__ part,
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_l1(const T* __restrict__ part,
                                                            const int32_t* __restrict__ mat_id,
                                                            const int2* __restrict__ mrange,
                                                            int E, int nvals, int n_mats,
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_l1(const double* __restr
       if ((mat_id ? __ldg(mat_id + e) : 0) == m) {
 #pragma unroll
         for (int k = 0; k < kParamRow; ++k)
-          if (k < nvals) s[k] += __ldg(part + (int64_t)k * E + e);
+          if (k < nvals) s[k] += double(__ldg(part + (int64_t)k * E + e));
       }
     block_sum_row(s, nvals, sh);
     if (threadIdx.x == 0) {
@@ -218,15 +219,22 @@ ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* xa, co
 #undef HEX
 #undef IBFE_FE_ARGS
 
-ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s) {
+ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s,
+                              bool real_parts) {
   if (n_mats > p->mat_cap) return IB_ERR_INVALID_ARG;
   if (p->E == 0) {
     cudaMemsetAsync(p->ered, 0, sizeof(double) * kParamRow * p->mat_cap, s);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
   }
   static_assert(kReduceCTAs <= kRedThreads, "one partial per thread of the second level");
-  k_reduce_l1<<<kReduceCTAs, kRedThreads, 0, s>>>(p->epart, p->mat_id, p->mat_range, p->E, nvals,
-                                                  n_mats, p->rpart);
+  // FP32 partials are widened exactly: the sums are those of their doubles
+  if (real_parts && p->precision != IB_FP64)
+    k_reduce_l1<float><<<kReduceCTAs, kRedThreads, 0, s>>>(
+        reinterpret_cast<const float*>(p->epart), p->mat_id, p->mat_range, p->E, nvals, n_mats,
+        p->rpart);
+  else
+    k_reduce_l1<double><<<kReduceCTAs, kRedThreads, 0, s>>>(p->epart, p->mat_id, p->mat_range,
+                                                            p->E, nvals, n_mats, p->rpart);
   const int pairs = n_mats * nvals, per = kRedThreads / 32;
   k_reduce_l2<<<(pairs + per - 1) / per, kRedThreads, 0, s>>>(p->rpart, kReduceCTAs, nvals,
                                                              n_mats, p->ered);

@@ -61,7 +61,8 @@ struct FeArgs {
   const float2* jx;      // [QF][E] exact J - 1 (IB_FP32_SPLIT_DFVOL) or null
   const Real* v;         // [3][N] direction (adjoint) or null
   Real* out;             // [24][E] corner contributions
-  double* epart;         // [kParamRow][E] per-element partial sums or null
+  double* epart;         // per-element partial sums or null: the energy [E] in
+                         // double, the parameter gradients [kParamRow][E] in Real
   int* status;
   int* next;             // block counter, zero at launch
   const InstDev* inst;   // packed plans: instance table (each instance's h), else null
@@ -875,7 +876,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
     if (kEnergy) A.epart[e] = en;
     if (kParams) {
 #pragma unroll
-      for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+      for (int k = 0; k < kParamRow; ++k) reinterpret_cast<Real*>(A.epart)[(int64_t)k * E + e] = gp[k];
     }
   } else {
     // the corners' data from their lanes, accumulated into this lane's point
@@ -946,7 +947,7 @@ __device__ __forceinline__ void fe_element(const FeArgs<Real>& A, const MatTable
         if (kEnergy) A.epart[e] = en;
         if (kParams) {
 #pragma unroll
-          for (int k = 0; k < kParamRow; ++k) A.epart[(int64_t)k * E + e] = double(gp[k]);
+          for (int k = 0; k < kParamRow; ++k) reinterpret_cast<Real*>(A.epart)[(int64_t)k * E + e] = gp[k];
         }
       }
     }

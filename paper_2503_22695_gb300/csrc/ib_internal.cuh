@@ -229,7 +229,8 @@ struct ib_plan {
   void* vol_jm1;         // float2 [force points][E]: exact J - 1 (IB_FP32_SPLIT_DFVOL only)
   void* gq_a;            // Real [3][Q] per-Gauss-point outputs (gq order)
   void* gq_b;            // Real [3][Q]
-  double* epart;         // [kParamRow][E] per-element partial sums
+  double* epart;         // per-element partial sums: energy [E] (double), parameter
+                         // gradients [kParamRow][E] (Real)
   double* ered;          // [IB_MAX_MATERIALS*kParamRow] reduced sums
   int* dstatus;          // device status word
   // packed batch (batch.cu); n_inst = 1 and null tables for one structure
@@ -265,7 +266,10 @@ ib_status launch_fe_force(ib_plan* p, const MatTable& mt, const void* x_cell_or_
 ib_status launch_fe_force_adj(ib_plan* p, const MatTable& mt, const void* x_cell_or_x64,
                               const float* off, const void* v, void* elem_out, bool params,
                               cudaStream_t s);
-ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s);
+// real_parts: the partials are in the plan's Real (parameter gradients),
+// else in double (energy); the sums are in double either way
+ib_status launch_reduce_parts(ib_plan* p, int nvals, int n_mats, cudaStream_t s,
+                              bool real_parts);
 // one instantiation of the force kernel's launcher (fe_kernel.cuh; explicit
 // instantiations in fe_force_f32.cu, fe_force_adj.cu, fe_force_var.cu)
 template <typename Real, typename S, bool kEnergy, bool kAdj, bool kParams, int kLaws, int kEl>
