@@ -19,6 +19,9 @@ namespace {
 
 constexpr int kT = 256;  // tiles per CTA
 
+// i in [-1, n]: its periodic image in [0, n)
+__device__ __forceinline__ int wrap_one(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 template <bool kPacked>
 __global__ void __launch_bounds__(kT) k_classify(GridDev g, const InstDev* __restrict__ inst,
                                                  const int32_t* __restrict__ tile_inst,
@@ -38,13 +41,18 @@ __global__ void __launch_bounds__(kT) k_classify(GridDev g, const InstDev* __res
     npt = end[t] - start[t];
     ne = npt > 0;
     nch = (npt + chunk - 1) / chunk;
-    nr = ne;
-    for (int a = -1; a <= 1 && !nr; ++a)
-      for (int b = -1; b <= 1 && !nr; ++b)
-        for (int c = -1; c <= 1 && !nr; ++c) {
-          const int nb = geo.base + wrap_idx(tx + c, nt0) +
-                         nt0 * (wrap_idx(ty + b, nt1) + nt1 * wrap_idx(tz + a, nt2));
-          nr = end[nb] > start[nb];
+    // all 27 neighbours' ranges loaded at once (most tiles are far from the
+    // structure and would otherwise wait for 27 dependent round trips)
+    nr = 0;
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b)
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) {
+          const int nb = geo.base + wrap_one(tx + c, nt0) +
+                         nt0 * (wrap_one(ty + b, nt1) + nt1 * wrap_one(tz + a, nt2));
+          nr |= __ldg(end + nb) > __ldg(start + nb);
         }
     nonempty[t] = nch;
     near[t] = nr;
