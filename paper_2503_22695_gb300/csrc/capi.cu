@@ -412,7 +412,8 @@ ib_status plan_build(const ib_mesh* mesh, const GridDev& grid, int ntiles, int32
               dalloc(&p->epart, 8 * kParamRow * (size_t)(E > 0 ? E : 1)) &&
               dalloc(&p->ered, 8 * kParamRow * (size_t)mat_cap) && dalloc(&p->dstatus, 16) &&
               dalloc(&p->pen_part, 8 * penalty_scratch_doubles()) &&
-              (packed || (dalloc(&p->q_val_b, rs * 3 * Q) && dalloc(&p->p_val_b, rs * 3 * Q) &&
+              (packed || ((precision != IB_FP64 || dalloc(&p->q_val_b, rs * 3 * Q)) &&
+                          dalloc(&p->p_val_b, rs * 3 * Q) &&
                           dalloc(&p->gq_c, rs * 3 * Q) &&
                           dalloc(&p->elem_scratch3, rs * 3 * nc * E))) &&
               (precision != IB_FP32_SPLIT_DFVOL ||
@@ -580,6 +581,10 @@ ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const vo
   if (st == IB_OK) st = do_gather(p, p->elem_scratch, nullptr, G, m);
   if (st == IB_OK) st = launch_penalty(p, x, G, false, m);
   if (st == IB_OK) {
+    // the carried values before the binning is waited for, then their binned
+    // copy: the values overlap the binning's end (computing them at the binned
+    // positions in one pass after the wait, as the backward does, measured
+    // 0.404 -> 0.418 ms here)
     Stage sc(p, IB_STAGE_POINTS, m, 2);
     st = launch_point_values(p, G, m);
     if (st == IB_OK && !ok(cudaStreamWaitEvent(m, p->ev_fsorted, 0))) st = IB_ERR_CUDA;
@@ -674,9 +679,8 @@ ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos
                         !ok(cudaStreamWaitEvent(b, p->ev_ffork, 0))))
       st = IB_ERR_CUDA;
     if (st == IB_OK) {
-      Stage sc(p, IB_STAGE_POINTS, b, 2);
-      st = launch_point_values(p, gU, b, p->q_val_b);
-      if (st == IB_OK) st = launch_permute_values(p, b, true, p->q_val_b, p->p_val_b);
+      Stage sc(p, IB_STAGE_POINTS, b, binned_values_launches(p));
+      st = launch_binned_values(p, gU, b, true, p->q_val_b, p->p_val_b);
     }
     if (st == IB_OK) st = do_spread(p, 1.0, gu, b, true, pc ? pc->spread_gu : nullptr, p->p_val_b);
     if (st == IB_OK)
@@ -687,9 +691,8 @@ ib_status backward_body(ib_plan* p, const MatTable& mt, int n_mats, const ib_pos
   };
   if (!pc) side();
   if (st == IB_OK && gf) {
-    Stage sc(p, IB_STAGE_POINTS, s, 2);
-    st = launch_point_values(p, G, s);
-    if (st == IB_OK) st = launch_permute_values(p, s, false);
+    Stage sc(p, IB_STAGE_POINTS, s, binned_values_launches(p));
+    st = launch_binned_values(p, G, s, false);
   }
   if (st == IB_OK && gf)
     st = pc ? do_interp(p, nullptr, 1, 0.0, 0.0, s, pc->interp_gf, pc->tmaps_gf)

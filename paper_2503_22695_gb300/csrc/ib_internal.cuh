@@ -215,7 +215,7 @@ struct ib_plan {
   // adjoint: its own carried values, gradient outputs and projection scratch
   // (owned by plans of one structure; a packed plan's alias q_val, p_val,
   // gq_b and elem_scratch2)
-  void* q_val_b;         // Real [3][Q]
+  void* q_val_b;         // Real [3][Q] (FP64 plans; FP32 plans bin the values in one pass)
   void* p_val_b;         // Real [3][Q]
   void* gq_c;            // Real [3][Q]
   void* elem_scratch3;   // Real [3 nc][E]
@@ -302,6 +302,13 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s,
                               void* q_out = nullptr);
 ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax = true,
                                 const void* q_in = nullptr, void* p_out = nullptr);
+// The carried values of the nodal field `nodal` at the binned points, into
+// p_out (or p_val), with the per-tile maxima when vmax: FP32 binning in one
+// pass (needs the binning done); FP64 plans through q_tmp (q_val if null)
+// and a permutation; the nodal rule by a permutation of `nodal` itself.
+ib_status launch_binned_values(ib_plan* p, const void* nodal, cudaStream_t s, bool vmax,
+                               void* q_tmp = nullptr, void* p_out = nullptr);
+int binned_values_launches(const ib_plan* p);
 
 // spread.cu
 // zero_fill false: the far-tile zeros were issued by launch_spread_zero

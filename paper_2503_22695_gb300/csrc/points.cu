@@ -274,6 +274,48 @@ __global__ void k_permute_values(const int32_t* __restrict__ p_idx, int64_t Q,
   }
 }
 
+// The carried values of k_point_values written straight to their binned
+// positions (FP32 binning: a point's position is its tile's start plus its
+// slot in the tile, both known since the binning), with the per-tile maxima
+// of their magnitudes when kVmax: the same values and maxima as
+// k_point_values followed by k_permute_values, one pass instead of two.
+template <int kEl, bool kVmax>
+__global__ void __launch_bounds__(128) k_point_values_binned(
+    int E, int64_t N, const int32_t* __restrict__ conn, const float* __restrict__ V,
+    const float* __restrict__ inv_mass, const float* __restrict__ wj0,
+    const uint32_t* __restrict__ tile, const int32_t* __restrict__ slot,
+    const int32_t* __restrict__ start, float* __restrict__ p_val, uint32_t* __restrict__ vmax) {
+  using EL = El<kEl>;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int64_t Q = (int64_t)EL::Q * E;
+  float Vn[EL::C][3];
+#pragma unroll
+  for (int a = 0; a < EL::C; ++a) {
+    const int node = __ldg(conn + a * E + e);
+    const float im = __ldg(inv_mass + node);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Vn[a][d] = __ldg(V + d * N + node) * im;
+  }
+#pragma unroll
+  for (int q = 0; q < EL::Q; ++q) {
+    const int64_t gq = (int64_t)q * E + e;
+    const uint32_t t = __ldg(tile + gq);
+    const int64_t i = __ldg(start + t) + __ldg(slot + gq);
+    const float w = __ldg(wj0 + gq);
+    float v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float s = 0.f;
+#pragma unroll
+      for (int a = 0; a < EL::C; ++a) s += float(EL::N(a, q)) * Vn[a][d];
+      v[d] = w * s;
+      p_val[d * Q + i] = v[d];
+    }
+    if constexpr (kVmax) tile_vmax_update(vmax, t, v[0], v[1], v[2]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // radix sort pieces
 // ---------------------------------------------------------------------------
@@ -616,6 +658,32 @@ ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax, const voi
                                p->grid, p->keys[0], p->tile_vmax);
   }
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+ib_status launch_binned_values(ib_plan* p, const void* nodal, cudaStream_t s, bool vmax,
+                               void* q_tmp, void* p_out) {
+  if (p->Q == 0) return IB_OK;
+  // the nodal rule's point values are the nodal values: binned directly
+  if (p->quad == IB_QUAD_NODAL) return launch_permute_values(p, s, vmax, nodal, p_out);
+  if (p->precision == IB_FP64) {  // sorted points: values, then their sorted copy
+    const ib_status st = launch_point_values(p, nodal, s, q_tmp);
+    return st == IB_OK ? launch_permute_values(p, s, vmax, q_tmp, p_out) : st;
+  }
+  float* const out = static_cast<float*>(p_out ? p_out : p->p_val);
+  if (vmax) cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
+  const int g = (p->E + 127) / 128;
+  with_elem(p->elem, [&](auto el) {
+    constexpr int kE = decltype(el)::value;
+    auto k = vmax ? k_point_values_binned<kE, true> : k_point_values_binned<kE, false>;
+    k<<<g, 128, 0, s>>>(p->E, p->N, p->conn, (const float*)nodal, (const float*)p->inv_mass,
+                        (const float*)p->wj0, p->keys[0], p->vals[0], p->tile_start, out,
+                        p->tile_vmax);
+  });
+  return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
+}
+
+int binned_values_launches(const ib_plan* p) {
+  return p->quad == IB_QUAD_NODAL || p->precision != IB_FP64 ? 1 : 2;
 }
 
 int sort_hist_blocks(int64_t Q) { return (int)((Q + kSortChunk - 1) / kSortChunk); }
