@@ -361,8 +361,8 @@ def run_ours(args):
     off = torch.from_numpy(prob.off).to(dev)
     pos = ibfe.Pos(cell=cell, off=off)
     u = torch.from_numpy(prob.u).to(dev)
-    tuning = ibfe.ib_plan_autotune(plan, [ibfe.Material(m.model, m.params) for m in prob.materials],
-                                   pos, u)
+    tuning = fixed_or_autotuned(args, plan, [ibfe.Material(m.model, m.params)
+                                             for m in prob.materials], pos, u)
     mats = [ibfe.Material(m.model, m.params) for m in prob.materials]
     G = torch.empty((3, N), device=dev)
     f = torch.empty(plan.grid_shape(), device=dev)
@@ -842,6 +842,17 @@ def run_ours(args):
     return 0
 
 
+def fixed_or_autotuned(args, plan, mats, pos, u):
+    """The plan's launch tuning: --tuning if given, else the autotuner's choice.
+    (A profiler slows the launches it does not capture, so a run under ncu
+    that autotunes may choose differently from the bench; --tuning pins it.)"""
+    if args.tuning:
+        t = [int(v) for v in args.tuning.split(",")]
+        ibfe.ib_plan_set_tuning(plan, t)
+        return t
+    return ibfe.ib_plan_autotune(plan, mats, pos, u)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -855,6 +866,9 @@ def main():
                     help="skip the fluid step and the explicit IB step")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--tuning", default=None,
+                    help="points per item, force CTAs/SM, spread and interp caps, e.g. "
+                         "1024,4,8,3 (default: the autotuner's choice)")
     ap.add_argument("--profile-once", choices=["forward", "backward", "fluid", "step"],
                     help="run one ib_forward (or ib_backward) between cudaProfilerStart/Stop "
                          "after warm-up, for ncu --profile-from-start off; prints no bench line")
@@ -888,7 +902,7 @@ def profile_once(args):
     gU = torch.from_numpy(rng.normal(size=(3, p.n_nodes)).astype(np.float32)).to(dev)
     gf = torch.from_numpy((rng.normal(size=p.u.shape) * 1e-3).astype(np.float32)).to(dev)
 
-    ibfe.ib_plan_autotune(plan, mats, pos, u)   # the launch shapes the bench times
+    fixed_or_autotuned(args, plan, mats, pos, u)   # the launch shapes the bench times
     if args.profile_once in ("fluid", "step"):
         fl = ibfe.Fluid(p.grid.n, p.grid.h, FLUID_RHO, FLUID_MU, FLUID_DT)
         f = torch.from_numpy((rng.normal(size=p.u.shape) * 50.0).astype(np.float32)).to(dev)
