@@ -846,6 +846,7 @@ def fixed_or_autotuned(args, plan, mats, pos, u):
     """The plan's launch tuning: --tuning if given, else the autotuner's choice.
     (A profiler slows the launches it does not capture, so a run under ncu
     that autotunes may choose differently from the bench; --tuning pins it.)"""
+    from paper_2503_22695_gb300 import ibfe
     if args.tuning:
         t = [int(v) for v in args.tuning.split(",")]
         ibfe.ib_plan_set_tuning(plan, t)
