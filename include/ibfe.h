@@ -271,7 +271,7 @@ ib_status ib_backward(ib_plan* plan, const ib_material* mats, int32_t n_mats, co
  *       the rest of each SM to the binning and interpolation beside it);
  *   [2] cap on the spreading CTAs per SM, 1..8;
  *   [3] cap on the interpolation CTAs per SM, 1..8.
- * Defaults {1024, 2, 8, 8} (the caps above the occupancy limits mean none).
+ * Defaults {1024, 4, 8, 3} (a cap above the occupancy limit means none).
  * Results do not depend on the tuning for FP32 plans (bitwise); FP64 plans
  * change only in the summation order of the spreading.  get/set are host
  * operations on the plan; set returns IB_ERR_INVALID_ARG out of range. */
@@ -279,12 +279,13 @@ ib_status ib_plan_get_tuning(const ib_plan* plan, int32_t tuning[4]);
 ib_status ib_plan_set_tuning(ib_plan* plan, const int32_t tuning[4]);
 
 /* Autotuner: times ib_forward on the given inputs for candidate tunings
- * (coordinate descent over the four entries in order: items of 1024 or 512
- * points; 2, 1, 3, 4 or 5 force CTAs per SM; spreading and interpolation caps 8, 3
- * or 2; one warm-up and the median of five timed calls each, every timed
- * call after a write of twice the L2 size, so that it starts from a cold
- * cache) and keeps the fastest.  Writes the choice to `tuning` (host, 4
- * entries) if non-NULL.  Allocates temporary output buffers and the L2
+ * (coordinate descent over the four entries in order, from the plan's
+ * current tuning: items of 1024 or 512 points; 1 to 5 force CTAs per SM;
+ * spreading and interpolation caps 8, 3 or 2; one warm-up and the median of
+ * five timed calls each, every timed call after a write of twice the L2
+ * size, so that it starts from a cold cache).  An entry changes only for a
+ * candidate more than 2% faster than the best so far.  Writes the choice to
+ * `tuning` (host, 4 entries) if non-NULL.  Allocates temporary output buffers and the L2
  * scratch (without the scratch, if that allocation fails) and synchronises
  * `stream`. */
 ib_status ib_plan_autotune(ib_plan* plan, const ib_material* mats, int32_t n_mats,

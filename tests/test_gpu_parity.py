@@ -411,7 +411,7 @@ def test_tuning_is_validated_and_changes_no_result():
     for name in ("shell128", "block64"):
         c = case(name)
         base = ibfe.ib_plan_get_tuning(c.plan)
-        assert base == [1024, 2, 8, 8]
+        assert base == [1024, 4, 8, 3]
         for bad in ([256, 2, 8, 8], [1024, 0, 8, 8], [1024, 6, 8, 8], [1024, 2, 9, 8],
                     [1024, 2, 8, 0]):
             with pytest.raises(ibfe.IBError):
