@@ -855,8 +855,10 @@ namespace ibfe {
 ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>& run,
                         cudaStream_t s) {
   ib_status st = IB_OK;
-  cudaEvent_t a = nullptr, b = nullptr;
-  if (!ok(cudaEventCreate(&a)) || !ok(cudaEventCreate(&b))) st = IB_ERR_CUDA;
+  constexpr int kTimed = 5;
+  cudaEvent_t a[kTimed] = {}, b[kTimed] = {};
+  for (int k = 0; k < kTimed; ++k)
+    if (!ok(cudaEventCreate(&a[k])) || !ok(cudaEventCreate(&b[k]))) st = IB_ERR_CUDA;
   // A scratch twice the L2 size, written before every timed call, so that
   // each call starts from a cold cache as a time step streaming the grid
   // does (back-to-back calls on a warm L2 ranked the candidates differently
@@ -873,20 +875,23 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
       cudaGetLastError();
     }
   }
-  // one warm-up call, then the median of five timed calls
-  constexpr int kTimed = 5;
+  // one warm-up call, then the median of five timed calls, enqueued back to
+  // back as time steps are (a host wait between the calls put the launch
+  // latency of each call's start into its time, which favoured other tunings
+  // than the steps do)
   auto time_run = [&](float& ms) -> ib_status {
     ib_status r = run(s);
-    float t[kTimed];
     for (int k = 0; k < kTimed && r == IB_OK; ++k) {
       if (flush && !ok(cudaMemsetAsync(flush, k, flush_bytes, s))) return IB_ERR_CUDA;
-      if (!ok(cudaEventRecord(a, s))) return IB_ERR_CUDA;
+      if (!ok(cudaEventRecord(a[k], s))) return IB_ERR_CUDA;
       r = run(s);
-      if (r == IB_OK && (!ok(cudaEventRecord(b, s)) || !ok(cudaEventSynchronize(b)) ||
-                         !ok(cudaEventElapsedTime(&t[k], a, b))))
-        r = IB_ERR_CUDA;
+      if (r == IB_OK && !ok(cudaEventRecord(b[k], s))) r = IB_ERR_CUDA;
     }
     if (r != IB_OK) return r;
+    float t[kTimed];
+    if (!ok(cudaEventSynchronize(b[kTimed - 1]))) return IB_ERR_CUDA;
+    for (int k = 0; k < kTimed; ++k)
+      if (!ok(cudaEventElapsedTime(&t[k], a[k], b[k]))) return IB_ERR_CUDA;
     std::sort(t, t + kTimed);
     ms = t[kTimed / 2];
     return IB_OK;
@@ -918,8 +923,10 @@ ib_status autotune_with(ib_plan* p, const std::function<ib_status(cudaStream_t)>
     cur[k] = best;
     ib_plan_set_tuning(p, cur);
   }
-  if (a) cudaEventDestroy(a);
-  if (b) cudaEventDestroy(b);
+  for (int k = 0; k < kTimed; ++k) {
+    if (a[k]) cudaEventDestroy(a[k]);
+    if (b[k]) cudaEventDestroy(b[k]);
+  }
   if (flush) cudaFree(flush);
   return st;
 }
