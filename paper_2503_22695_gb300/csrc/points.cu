@@ -77,7 +77,9 @@ __device__ __forceinline__ void bin_point(const PtArgs<Real>& A, int64_t gq, con
   }
 }
 
-template <typename Real, bool kBin, int kEl, bool kPacked>
+// kVal: the call carries nodal values (A.V); without them the kernel keeps
+// no per-corner values live (fewer registers, more resident warps)
+template <typename Real, bool kBin, int kEl, bool kPacked, bool kVal = true>
 __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
   using EL = El<kEl>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) dl[a][d] = Real(c[d] - c0[d]) + (o[d] - o0[d]);
     }
-    if (A.V) {
+    if (kVal && A.V) {
       const Real im = __ldg(A.inv_mass + node);
 #pragma unroll
       for (int d = 0; d < 3; ++d) Vn[a][d] = __ldg(A.V + d * A.N + node) * im;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(128) k_points(PtArgs<Real> A) {
       A.q_off[d * Q + gq] = off;
     }
     bin_point<Real, kBin>(A, gq, cw, geo);
-    if (A.V) {
+    if (kVal && A.V) {
       const Real w = __ldg(A.wj0 + gq);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -518,10 +520,11 @@ ib_status points_t<float>(ib_plan* p, const void* xa, const float* off, const vo
   else
     with_elem(p->elem, [&](auto el) {
       constexpr int kE = decltype(el)::value;
-      if (p->n_inst > 1)
-        k_points<float, true, kE, true><<<(p->E + 127) / 128, 128, 0, s>>>(A);
-      else
-        k_points<float, true, kE, false><<<(p->E + 127) / 128, 128, 0, s>>>(A);
+      auto k = p->n_inst > 1 ? (nodal ? k_points<float, true, kE, true, true>
+                                      : k_points<float, true, kE, true, false>)
+                             : (nodal ? k_points<float, true, kE, false, true>
+                                      : k_points<float, true, kE, false, false>);
+      k<<<(p->E + 127) / 128, 128, 0, s>>>(A);
     });
   return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ERR_CUDA;
 }
