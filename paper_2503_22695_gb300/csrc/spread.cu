@@ -580,11 +580,15 @@ __global__ void __launch_bounds__(kFxThreads) k_spread_push_fx(SpreadArgs<float>
 // Per tile (FP32 plans), one thread each: the exponent k of its fixed-point
 // words, its first block slot, the bound m = ceil(n / 512) on its work items
 // under any tuning, and its work items; read by every push item of the tile
-// and by the merge of each of its 27 neighbours.
+// and by the merge of each of its 27 neighbours.  Also zeroes the
+// accumulation's counters (its work counter and the tiles' written items),
+// which saves two memsets ahead of the push.
 template <bool kPacked>
 __global__ void __launch_bounds__(256) k_tile_info(SpreadArgs<float> A, int ntiles) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) A.counters[1] = 0;  // the accumulation's work counter
   if (t >= ntiles) return;
+  A.tile_done[t] = 0;             // items of the tile written in this call
   const int ns = A.tile_nitems[t];
   const int npts = A.tile_end[t] - A.tile_start[t];
   const float scale = call_scale<kPacked>(A, kPacked ? __ldg(A.tile_inst + t) : 0);
@@ -784,7 +788,6 @@ constexpr size_t kFxSmem =
 
 template <bool kPacked>
 void launch_push(ib_plan* p, const SpreadArgs<float>& A, cudaStream_t s) {
-  cudaMemsetAsync(p->tile_done, 0, sizeof(int32_t) * p->ntiles, s);
   k_tile_info<kPacked><<<(p->ntiles + 255) / 256, 256, 0, s>>>(A, p->ntiles);
   p->prof_calls[IB_STAGE_SPREAD_PUSH] += 1;
   const int ev = prof_begin(p, IB_STAGE_SPREAD_PUSH, s);
@@ -835,7 +838,8 @@ template <typename Real, bool kPacked>
 ib_status spread_t(ib_plan* p, double scale, void* f, bool zero_fill, cudaStream_t s,
                    const GridCall* calls, const void* vals) {
   SpreadArgs<Real> A = spread_args<Real>(p, scale, f, calls, vals);
-  cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
+  // the FP32 accumulation's counter is reset by k_tile_info
+  if constexpr (sizeof(Real) == 8) cudaMemsetAsync(p->tile_counters + 1, 0, sizeof(int32_t), s);
   // far-tile zeros on the side stream, concurrent with the push (unless the
   // caller has already issued them)
   if (zero_fill) {
