@@ -566,6 +566,11 @@ ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const vo
       (m != s && !ok(cudaStreamWaitEvent(m, p->ev_ffork, 0))))
     return IB_ERR_CUDA;
   ib_status st = do_points_sorted(p, x, nullptr, b);
+  // the spreading's per-tile maxima zeroed here, off the critical stream,
+  // which takes them after waiting for the binning
+  if (st == IB_OK && p->precision != IB_FP64 &&
+      !ok(cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, b)))
+    st = IB_ERR_CUDA;
   if (st == IB_OK && !ok(cudaEventRecord(p->ev_fsorted, b))) st = IB_ERR_CUDA;
   // the far-tile zeros of f (HBM writes) on the side branch, beside the
   // force kernel and ahead of the interpolation
@@ -589,7 +594,7 @@ ib_status forward_body(ib_plan* p, const MatTable& mt, const ib_pos* x, const vo
     Stage sc(p, IB_STAGE_POINTS, m, 2);
     st = launch_point_values(p, G, m);
     if (st == IB_OK && !ok(cudaStreamWaitEvent(m, p->ev_fsorted, 0))) st = IB_ERR_CUDA;
-    if (st == IB_OK) st = launch_permute_values(p, m);
+    if (st == IB_OK) st = launch_permute_values(p, m, true, nullptr, nullptr, false);
   }
   if (st == IB_OK)
     st = do_spread(p, 1.0 / (p->grid.h * p->grid.h * p->grid.h), f, m, /*zero_fill=*/false,

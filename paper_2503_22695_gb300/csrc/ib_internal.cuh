@@ -300,8 +300,11 @@ ib_status launch_sort_points(ib_plan* p, bool with_val, cudaStream_t s);
 // per-tile maxima the FP32 spreading's exponents take).
 ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s,
                               void* q_out = nullptr);
+// zero_vmax false: the maxima were zeroed by the caller, ahead on the stream
+// (or one it waits for)
 ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax = true,
-                                const void* q_in = nullptr, void* p_out = nullptr);
+                                const void* q_in = nullptr, void* p_out = nullptr,
+                                bool zero_vmax = true);
 // The carried values of the nodal field `nodal` at the binned points, into
 // p_out (or p_val), with the per-tile maxima when vmax: FP32 binning in one
 // pass (needs the binning done); FP64 plans through q_tmp (q_val if null)

@@ -642,7 +642,7 @@ ib_status launch_point_values(ib_plan* p, const void* nodal, cudaStream_t s, voi
 }
 
 ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax, const void* q_in,
-                                void* p_out) {
+                                void* p_out, bool zero_vmax) {
   if (p->Q == 0) return IB_OK;
   const int nb = (int)((p->Q + 255) / 256);
   const void* const q = q_in ? q_in : p->q_val;
@@ -652,7 +652,7 @@ ib_status launch_permute_values(ib_plan* p, cudaStream_t s, bool vmax, const voi
                                                        (double*)out, p->p_cell, p->grid,
                                                        nullptr, nullptr);
   } else {
-    if (vmax) cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
+    if (vmax && zero_vmax) cudaMemsetAsync(p->tile_vmax, 0, sizeof(uint32_t) * p->ntiles, s);
     auto permute = p->n_inst > 1 ? (vmax ? k_permute_values<float, true, true>
                                          : k_permute_values<float, true, false>)
                                   : (vmax ? k_permute_values<float, false, true>
