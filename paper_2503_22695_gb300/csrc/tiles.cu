@@ -19,6 +19,46 @@ namespace {
 
 constexpr int kT = 256;  // tiles per CTA
 
+// Block-wide exclusive scans of K integers at once (one pair of barriers for
+// all of them); total[k] receives the block sum of v[k].  tmp: K * 32 ints.
+template <int K>
+__device__ __forceinline__ void block_scan_k(const int (&v)[K], int (&pre)[K], int (&total)[K],
+                                             int* tmp) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    x[k] = v[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(full, x[k], o);
+      if (lane >= o) x[k] += y;
+    }
+    if (lane == 31) tmp[k * 32 + warp] = x[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int w = lane < nw ? tmp[k * 32 + lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, w, o);
+        if (lane >= o) w += y;
+      }
+      tmp[k * 32 + lane] = w;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    total[k] = tmp[k * 32 + nw - 1];
+    pre[k] = (warp > 0 ? tmp[k * 32 + warp - 1] : 0) + x[k] - v[k];
+  }
+  __syncthreads();
+}
+
 // i in [-1, n]: its periodic image in [0, n)
 __device__ __forceinline__ int wrap_one(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -81,40 +121,36 @@ __global__ void __launch_bounds__(kT) k_compact(const int32_t* __restrict__ none
                                                 int32_t* __restrict__ work,
                                                 int32_t* __restrict__ list_near,
                                                 int32_t* __restrict__ counters) {
-  __shared__ int tmp[32];
+  __shared__ int tmp[5 * 32];
   __shared__ int base[3];
-  // offsets: sums of the counts of the CTAs before this one
-  int ne_before = 0, nr_before = 0, np_before = 0, ne_all = 0, nr_all = 0;
+  // offsets: sums of the counts of the CTAs before this one (and of all)
+  int sums[5] = {0, 0, 0, 0, 0};  // ne, nr, np before this CTA; ne, nr of all
   for (int b = threadIdx.x; b < nblocks; b += kT) {
     const int a = bcount[3 * b], c = bcount[3 * b + 1], d = bcount[3 * b + 2];
     if (b < (int)blockIdx.x) {
-      ne_before += a;
-      nr_before += c;
-      np_before += d;
+      sums[0] += a;
+      sums[1] += c;
+      sums[2] += d;
     }
-    ne_all += a;
-    nr_all += c;
+    sums[3] += a;
+    sums[4] += c;
   }
-  int t0, t1, t2, t3, t4;
-  block_exclusive_scan(ne_before, tmp, t0);
-  block_exclusive_scan(nr_before, tmp, t1);
-  block_exclusive_scan(ne_all, tmp, t2);
-  block_exclusive_scan(nr_all, tmp, t3);
-  block_exclusive_scan(np_before, tmp, t4);
+  int spre[5], stot[5];
+  block_scan_k<5>(sums, spre, stot, tmp);
+  const int t2 = stot[3], t3 = stot[4];
   if (threadIdx.x == 0) {
-    base[0] = t0;
-    base[1] = t1;
-    base[2] = t4;
+    base[0] = stot[0];
+    base[1] = stot[1];
+    base[2] = stot[2];
   }
   __syncthreads();
   const int t = blockIdx.x * kT + threadIdx.x;
-  const int ne = t < ntiles ? nonempty[t] : 0;
-  const int nr = t < ntiles ? near[t] : 0;
-  const int np = t < ntiles ? end[t] - start[t] : 0;
-  int tot;
-  const int pne = block_exclusive_scan(ne, tmp, tot);
-  const int pnr = block_exclusive_scan(nr, tmp, tot);
-  const int pnp = block_exclusive_scan(np, tmp, tot);
+  const int cnt[3] = {t < ntiles ? nonempty[t] : 0, t < ntiles ? near[t] : 0,
+                      t < ntiles ? end[t] - start[t] : 0};
+  const int ne = cnt[0], nr = cnt[1], np = cnt[2];
+  int cpre[3], ctot[3];
+  block_scan_k<3>(cnt, cpre, ctot, tmp);
+  const int pne = cpre[0], pnr = cpre[1], pnp = cpre[2];
   if (t < ntiles) {
     start[t] = base[2] + pnp;
     end[t] = base[2] + pnp + np;
